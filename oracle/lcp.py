@@ -1,0 +1,58 @@
+"""Exact solution of the contact problem of one Newton step (Eq. 12-13, 22-23).
+
+With the prescribed DOFs eliminated and K symmetric positive definite, the QP of Eq. 23
+  min 1/2 dx^T K dx + g^T dx   s.t.  A dx <= b
+has the unique minimiser dx = -K^{-1} (g + A^T y), where y >= 0 solves the LCP
+  w = W y + q >= 0,  y >= 0,  y^T w = 0,   W = A K^{-1} A^T,  q = b + A K^{-1} g
+(w is the slack b - A dx of Eq. 8; y the contact forces of Eq. 11).  W is symmetric
+positive definite when the rows of A are independent (one contact per node), so the LCP
+has exactly one solution.  Two exact finite methods are given: Murty's least-index
+principal pivoting (finite for P-matrices) and, for small m, enumeration of all 2^m
+complementary sets.
+"""
+import itertools
+
+import numpy as np
+
+
+def _solve_set(W, q, P):
+    y = np.zeros(len(q))
+    if P.any():
+        y[P] = np.linalg.solve(W[np.ix_(P, P)], -q[P])
+    return y
+
+
+def murty(W, q, tol=0.0, max_pivots=100000):
+    """Least-index principal pivoting (K. G. Murty, 1974).  Start from y = 0; while some
+    complementary variable is negative (y_i < -tol for i in P, w_i < -tol for i not in P),
+    move the lowest such index across.  Returns (y, w, pivots)."""
+    m = len(q)
+    P = np.zeros(m, dtype=bool)
+    for it in range(max_pivots + 1):
+        y = _solve_set(W, q, P)
+        w = W @ y + q
+        w[P] = 0.0
+        bad = np.where((P & (y < -tol)) | (~P & (w < -tol)))[0]
+        if len(bad) == 0:
+            return y, w, it
+        i = bad[0]
+        P[i] = not P[i]
+    raise RuntimeError("LCP pivoting did not terminate")
+
+
+def enumerate_lcp(W, q, tol=1e-12):
+    """All complementary sets P; returns every (y, w) that satisfies the LCP (for m <= 12)."""
+    m = len(q)
+    sols = []
+    scale = max(1.0, np.abs(q).max()) if m else 1.0
+    for bits in itertools.product([False, True], repeat=m):
+        P = np.array(bits, dtype=bool)
+        try:
+            y = _solve_set(W, q, P)
+        except np.linalg.LinAlgError:
+            continue
+        w = W @ y + q
+        w[P] = 0.0
+        if (y >= -tol * scale).all() and (w >= -tol * scale).all():
+            sols.append((y, w))
+    return sols

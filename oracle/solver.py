@@ -1,0 +1,256 @@
+"""Quasi-static Newton solve with contacts (Sec. II-III of the paper), plain FP64.
+
+One call of ``Model.solve`` is one quasi-static step at a given cable tension and insertion:
+
+  * prescribed nodes (Eq. 14-15): the robot is fed through a clamp at the lumen entrance.
+    At insertion delta every node with arc length s_i <= L - delta (count from
+    k = floor((L - delta) M / L + 1e-6)) sits on the entrance axis,
+    x_i = e + (s_i - L + delta) d with the rest triad E0; the remaining nodes are free.
+    Their DOFs are eliminated, which replaces y_fn; the reaction is F(x) at node k.
+  * cable load (Eq. 16-18): cable j at angle phi_j on radius r_c pulls the tip towards the
+    base, F_j = (-tau_j, 0, 0) and d_j = r_c (0, cos phi_j, sin phi_j) in the tip frame; the
+    tip receives T_M F_j and T_M (d_j x F_j), evaluated at the current iterate (follower load).
+  * Newton step (Eq. 20-23): K(x) and F(x) at the current iterate, contact set and A_c, b_c
+    at the current iterate (Eq. 8-10), QP of Eq. 23 solved exactly through its LCP.
+  * step limiter (Eq. 25-27): alpha = min(1, beta0 / max_i |du_i|) scales the whole step and
+    the multipliers; translations add, rotations update as T <- exp([alpha dtheta]x) T.
+  * convergence: unlimited step (alpha = 1) with max_i max(|du_i|, r_o |dtheta_i|) <= tol and
+    the same contact set as the previous iteration.
+  * warm start (follow the path): with a resident state at insertion delta_old, material
+    point s takes the old position of material point s + (delta - delta_old) (linear in x,
+    geodesic in T between nodes; straight along the tip axis beyond the old tip).
+"""
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.linalg as sla
+
+from . import beam, contact, lcp
+from .rotation import expm, logm, to_quat
+
+OK, E_INVALID_ARG, E_NOMEM, E_CUDA, E_NOT_CONVERGED, E_CONTACT_CAPACITY, E_NOT_SPD, E_TIMEOUT, E_PENETRATION = range(9)
+
+
+@dataclass
+class Options:
+    activation_gap: float = 1.0e-3
+    step_limit: float = 5.0e-4
+    newton_tol: float = 1.0e-11
+    contact_tol: float = 1.0e-9
+    max_newton_iters: int = 200
+    max_contact_iters: int = 4000
+    max_contacts: int = 256
+    tangent_mode: int = 0          # 0: material tangent K_M; 1: symmetric part of K_T (K_M if not PD)
+
+
+@dataclass
+class Result:
+    status: int
+    node_pos: np.ndarray
+    node_quat: np.ndarray
+    contacts: list
+    newton_iters: int
+    contact_iters: int
+    residual: float
+    base_reaction: np.ndarray
+
+
+def entrance_frame(lumen):
+    d = np.asarray(lumen.entrance_dir, float)
+    d = d / np.linalg.norm(d)
+    up = np.asarray(lumen.entrance_up, float)
+    up = up - np.dot(up, d) * d
+    up = up / np.linalg.norm(up)
+    return np.column_stack([d, up, np.cross(d, up)])
+
+
+def n_prescribed_last(L, M, delta):
+    """Index k of the last prescribed node."""
+    return int(math.floor((L - delta) * M / L + 1e-6))
+
+
+def cable_load(T_tip, tensions, robot):
+    """Eq. 16-18: tip force and moment in global coordinates."""
+    F = np.zeros(3)
+    Mo = np.zeros(3)
+    for tau, phi in zip(tensions, robot.cable_angles):
+        d_j = robot.cable_radius * np.array([0.0, math.cos(phi), math.sin(phi)])
+        F_j = np.array([-tau, 0.0, 0.0])
+        F += T_tip @ F_j
+        Mo += T_tip @ np.cross(d_j, F_j)
+    return F, Mo
+
+
+class Model:
+    def __init__(self, robot, lumen, options=None):
+        self.robot = robot
+        self.lumen = lumen
+        self.opt = options or Options()
+        self.sec = beam.section_constants(robot)
+        self.M = robot.n_elements
+        self.L = robot.length
+        self.l0 = self.L / self.M
+        self.E0 = entrance_frame(lumen)
+        self.e = np.asarray(lumen.entrance_point, float)
+        self.V = np.asarray(lumen.vertices, float)
+        self.T = np.asarray(lumen.triangles, np.int64).reshape(-1, 3)
+        self.state = None          # (x, R, delta)
+        self.trace = None          # list -> per-iteration (alpha, umax, step, residual, m)
+
+    # ---- configuration helpers -------------------------------------------------------
+    def straight(self, delta):
+        N = self.M + 1
+        x = np.array([self.e + (i * self.l0 - self.L + delta) * self.E0[:, 0] for i in range(N)])
+        R = np.array([self.E0.copy() for _ in range(N)])
+        return x, R
+
+    def follow_path(self, x_old, R_old, delta_old, delta):
+        dd = delta - delta_old
+        N = self.M + 1
+        x = np.zeros((N, 3))
+        R = np.zeros((N, 3, 3))
+        for i in range(N):
+            s = i * self.l0 + dd
+            if s >= self.L:
+                x[i] = x_old[self.M] + (s - self.L) * R_old[self.M][:, 0]
+                R[i] = R_old[self.M]
+            elif s <= 0.0:
+                x[i] = x_old[0] + s * R_old[0][:, 0]
+                R[i] = R_old[0]
+            else:
+                j = min(int(math.floor(s / self.l0)), self.M - 1)
+                f = (s - j * self.l0) / self.l0
+                x[i] = (1.0 - f) * x_old[j] + f * x_old[j + 1]
+                R[i] = R_old[j] @ expm(f * logm(R_old[j].T @ R_old[j + 1]))
+        return x, R
+
+    def clamp(self, x, R, delta, k):
+        for i in range(k + 1):
+            x[i] = self.e + (i * self.l0 - self.L + delta) * self.E0[:, 0]
+            R[i] = self.E0
+        return x, R
+
+    # ---- assembly ----------------------------------------------------------------------
+    def assemble(self, x, R, k, mode):
+        """Internal force F (6N) and the banded upper form of K on the free DOFs."""
+        M = self.M
+        nf = M - k
+        F = np.zeros(6 * (M + 1))
+        u = 11
+        ab = np.zeros((u + 1, 6 * nf))
+        for e in range(k, M):
+            Fe = beam.internal_force(x[e], R[e], x[e + 1], R[e + 1], self.sec)
+            F[6 * e:6 * e + 12] += Fe
+            if mode == 0:
+                Ke = beam.material_tangent(x[e], R[e], x[e + 1], R[e + 1], self.sec)
+            else:
+                Kt = beam.consistent_tangent(x[e], R[e], x[e + 1], R[e + 1], self.sec)
+                Ke = 0.5 * (Kt + Kt.T)
+            base = 6 * (e - (k + 1))          # free dof index of element dof 0
+            for i in range(12):
+                gi = base + i
+                if gi < 0:
+                    continue
+                for j in range(i, 12):
+                    gj = base + j
+                    ab[u + gi - gj, gj] += Ke[i, j]
+        return F, ab
+
+    # ---- one solve ---------------------------------------------------------------------
+    def solve(self, tensions=None, delta=0.0, warm=None, tip_load=None):
+        """``tip_load`` = (f, m, follower) replaces the cable load (test hook)."""
+        opt = self.opt
+        M, L = self.M, self.L
+        if not (0.0 <= delta <= L):
+            raise ValueError("insertion outside [0, L]")
+        k = n_prescribed_last(L, M, delta)
+        if warm is not None:
+            x, R = warm[0].copy(), warm[1].copy()
+        elif self.state is not None:
+            x, R = self.follow_path(*self.state, delta)
+        else:
+            x, R = self.straight(delta)
+        x, R = self.clamp(x, R, delta, k)
+        nf = M - k
+        free = list(range(k + 1, M + 1))
+        r_o = self.robot.outer_radius
+        contacts = []
+        y = np.zeros(0)
+        prev_key = None
+        it = 0
+        piv_total = 0
+        residual = 0.0
+        status = E_NOT_CONVERGED
+        base_reaction = np.zeros(6)
+        if nf == 0:
+            status = OK
+        while nf > 0 and it < opt.max_newton_iters:
+            it += 1
+            F, ab = self.assemble(x, R, k, opt.tangent_mode)
+            # external cable (or test) load at the tip node, Eq. 16-18
+            Fa = np.zeros(6 * (M + 1))
+            if tip_load is None:
+                f, mo = cable_load(R[M], tensions, self.robot)
+            else:
+                f, mo, follower = tip_load
+                f, mo = (R[M] @ self.E0.T @ f, R[M] @ self.E0.T @ mo) if follower else (np.asarray(f), np.asarray(mo))
+            Fa[6 * M:6 * M + 3] = f
+            Fa[6 * M + 3:6 * M + 6] = mo
+            g = (F - Fa)[6 * (k + 1):]
+            try:
+                c = sla.cholesky_banded(ab, lower=False)
+            except np.linalg.LinAlgError:
+                if opt.tangent_mode == 0:
+                    status = E_NOT_SPD
+                    break
+                _, ab = self.assemble(x, R, k, 0)
+                c = sla.cholesky_banded(ab, lower=False)
+            solve = lambda rhs: sla.cho_solve_banded((c, False), rhs)
+            contacts = contact.detect(x, free, self.V, self.T, r_o, opt.activation_gap) if len(self.T) else []
+            m = len(contacts)
+            if m > opt.max_contacts:
+                status = E_CONTACT_CAPACITY
+                break
+            dxf = -solve(g)
+            if m:
+                A = np.zeros((m, 6 * nf))
+                b = np.zeros(m)
+                for i, rec in enumerate(contacts):
+                    col = 6 * (rec["node"] - (k + 1))
+                    A[i, col:col + 3] = rec["normal"]
+                    b[i] = rec["gap"]
+                X = solve(A.T)
+                W = A @ X
+                q = b - A @ dxf
+                y, w, piv = lcp.murty(W, q)
+                piv_total += piv
+                dx = dxf - X @ y
+                r = g + A.T @ y
+            else:
+                y = np.zeros(0)
+                dx = dxf
+                r = g
+            residual = float(np.abs(r).max())
+            base_reaction = F[6 * k:6 * k + 6].copy()
+            du = dx.reshape(nf, 6)[:, :3]
+            dth = dx.reshape(nf, 6)[:, 3:]
+            umax = float(np.sqrt((du * du).sum(axis=1)).max())
+            step = float(max(umax, r_o * np.sqrt((dth * dth).sum(axis=1)).max()))
+            alpha = 1.0 if umax <= opt.step_limit else opt.step_limit / umax
+            for j, i in enumerate(free):
+                x[i] = x[i] + alpha * du[j]
+                R[i] = expm(alpha * dth[j]) @ R[i]
+            y = alpha * y
+            if self.trace is not None:
+                self.trace.append((alpha, umax, step, residual, m))
+            key = tuple((rec["node"], rec["tri"]) for rec in contacts)
+            if alpha == 1.0 and step <= opt.newton_tol and key == prev_key:
+                status = OK
+                break
+            prev_key = key
+        self.state = (x.copy(), R.copy(), delta)
+        for i, rec in enumerate(contacts):
+            rec["force"] = float(y[i]) if i < len(y) else 0.0
+        quat = np.array([to_quat(Ri) for Ri in R])
+        return Result(status, x, quat, contacts, it, piv_total, residual, base_reaction)

@@ -1,0 +1,167 @@
+"""Pins of the oracle's collision detection (Eq. 3-10, Sec. III.C) and contact LCP (Eq. 12-13, 22-23):
+dense sampling, constructed Voronoi regions, plane/crease/ridge closed forms, brute-force
+enumeration of complementary sets."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import contact, lcp
+
+
+def _tri_samples(a, b, c, n):
+    u = np.linspace(0, 1, n)
+    U, V = np.meshgrid(u, u)
+    m = U + V <= 1
+    U, V = U[m], V[m]
+    return a[None] + U[:, None] * (b - a)[None] + V[:, None] * (c - a)[None]
+
+
+def test_closest_point_vs_dense_sampling():
+    rng = np.random.default_rng(10)
+    for _ in range(20):
+        a, b, c = rng.normal(size=(3, 3))
+        S = _tri_samples(a, b, c, 600)
+        for _ in range(5):
+            p = rng.normal(size=3) * 1.5
+            q = contact.closest_point_on_triangle(p, a, b, c)
+            d = np.linalg.norm(p - q)
+            ds = np.linalg.norm(S - p[None], axis=1).min()
+            h = max(np.linalg.norm(b - a), np.linalg.norm(c - a), np.linalg.norm(c - b)) / 599
+            assert d <= ds + 1e-12
+            assert d >= ds - 2 * h
+            # q lies on the triangle: non-negative barycentric coordinates, in plane
+            M = np.column_stack([b - a, c - a])
+            vw, *_ = np.linalg.lstsq(M, q - a, rcond=None)
+            assert vw.min() >= -1e-12 and vw.sum() <= 1 + 1e-12
+            assert np.linalg.norm(M @ vw - (q - a)) <= 1e-12
+
+
+def test_closest_point_all_seven_regions():
+    a, b, c = np.array([0.0, 0, 0]), np.array([1.0, 0, 0]), np.array([0.0, 1, 0])
+    cases = [((-1, -1, 0.3), a), ((2, -0.5, 1), b), ((-0.5, 2, -1), c),
+             ((0.5, -1, 0.2), (0.5, 0, 0)), ((-1, 0.4, 0.7), (0, 0.4, 0)), ((1, 1, 0.5), (0.5, 0.5, 0)),
+             ((0.2, 0.3, 0.9), (0.2, 0.3, 0))]
+    for p, q in cases:
+        assert np.allclose(contact.closest_point_on_triangle(np.array(p, float), a, b, c), q, atol=1e-15)
+    P = np.array([p for p, _ in cases], float)
+    for p, q in cases:
+        cp, d, inside = contact.closest_points_all(np.array(p, float), a[None], b[None], c[None])
+        assert np.allclose(cp[0], q, atol=1e-15)
+        assert inside[0] == (p == (0.2, 0.3, 0.9))
+
+
+def test_vectorised_matches_scalar():
+    rng = np.random.default_rng(11)
+    A, B, C = rng.normal(size=(3, 200, 3))
+    for _ in range(20):
+        p = rng.normal(size=3)
+        cp, d, _ = contact.closest_points_all(p, A, B, C)
+        for t in range(0, 200, 17):
+            q = contact.closest_point_on_triangle(p, A[t], B[t], C[t])
+            assert np.allclose(cp[t], q, atol=1e-13)
+
+
+def test_plane_wall_closed_form():
+    """A node at height h over a flat wall: one face constraint n = wall normal, gap = h - r_o."""
+    lum = wl.plane_lumen(point=(0.05, 0.01, 0.0), normal=(0.0, 1.0, 0.0), size=0.2, n=6)
+    V, T = lum.vertices, lum.triangles
+    r_o, act = 2e-3, 1e-3
+    for h in (0.5e-3, 2.0e-3, 2.9e-3, 3.1e-3):
+        p = np.array([0.0123, 0.01 - h, 0.0071])
+        recs = contact.detect_node(p, V, T, r_o, act)
+        if h <= r_o + act:
+            assert len(recs) == 1
+            assert np.allclose(recs[0]["normal"], [0, 1, 0], atol=1e-15)
+            assert recs[0]["gap"] == pytest.approx(h - r_o, abs=1e-15)
+            assert np.allclose(recs[0]["point"], [0.0123, 0.01, 0.0071], atol=1e-15)
+        else:
+            assert recs == []
+    # penetrated node: same plane, negative gap
+    p = np.array([0.0123, 0.01 + 0.5e-3, 0.0])
+    recs = contact.detect_node(p, V, T, r_o, act)
+    assert len(recs) == 1 and recs[0]["gap"] == pytest.approx(-0.5e-3 - r_o, abs=1e-15)
+
+
+def test_crease_and_ridge_explicit():
+    """Valley (concave crease seen from the lumen): both face planes; ridge (convex edge):
+    one edge constraint with n along c - p."""
+    ca, sa = np.cos(0.3), np.sin(0.3)
+    V = np.array([[0, 0, -1.0], [0, 0, 1.0], [ca, sa, 0.0], [-ca, sa, 0.0]])
+    T = np.array([[0, 2, 1], [0, 1, 3]], np.int32)
+    nf = contact.face_normals(V, T)
+    assert nf[0, 1] < 0 and nf[1, 1] < 0          # outward = below the valley surface
+    p = np.array([0.0, 0.25, 0.0])
+    recs = contact.detect_node(p, V, T, 0.2, 0.2, nf)
+    assert len(recs) == 2 and all(r["face"] for r in recs)
+    for r, n in zip(recs, nf):
+        assert np.allclose(r["normal"], n, atol=1e-15)
+        assert r["gap"] == pytest.approx(abs(np.dot(n, p - V[0])) - 0.2, abs=1e-15)
+    V2 = np.array([[0, 0, -1.0], [0, 0, 1.0], [ca, -sa, 0.0], [-ca, -sa, 0.0]])
+    T2 = np.array([[0, 2, 1], [0, 1, 3]], np.int32)
+    nf2 = contact.face_normals(V2, T2)
+    assert nf2[0, 1] < 0 and nf2[1, 1] < 0
+    p2 = np.array([0.0, 0.3, 0.0])
+    recs2 = contact.detect_node(p2, V2, T2, 0.2, 0.2, nf2)
+    assert len(recs2) == 1 and not recs2[0]["face"]
+    assert np.allclose(recs2[0]["point"], [0, 0, 0], atol=1e-15)
+    assert np.allclose(recs2[0]["normal"], [0, -1, 0], atol=1e-15)
+    assert recs2[0]["gap"] == pytest.approx(0.3 - 0.2, abs=1e-15)
+
+
+def test_detect_matches_naive_loop_on_small_mesh():
+    """P10: brute force over a small random tube mesh with a plain per-triangle loop."""
+    pts = wl.bent_tube_centerline(straight=0.01, arc_angle=0.5, bend_radius=0.02, ds=0.002)
+    V, T, _, _ = wl.tube_mesh(pts, 0.005, 8)
+    rng = np.random.default_rng(12)
+    nf = contact.face_normals(V, T)
+    for _ in range(40):
+        p = pts[rng.integers(len(pts))] + rng.normal(size=3) * 0.002
+        recs = contact.detect_node(p, V, T, 0.002, 0.001, nf)
+        # naive: scalar closest point per triangle
+        best = min(range(len(T)), key=lambda t: (np.linalg.norm(p - contact.closest_point_on_triangle(p, *V[T[t]])), t))
+        cps = [contact.closest_point_on_triangle(p, *V[T[t]]) for t in range(len(T))]
+        d = [np.linalg.norm(p - q) for q in cps]
+        expect = []
+        for t in range(len(T)):
+            if d[t] > 0.003:
+                continue
+            # interior: closest point equals the plane projection
+            proj = p - np.dot(nf[t], p - V[T[t, 0]]) * nf[t]
+            interior = np.linalg.norm(proj - cps[t]) <= 1e-13
+            if interior or t == best:
+                if not any(np.linalg.norm(cps[t] - cps[u]) <= 1e-12 for u in expect):
+                    expect.append(t)
+        # triangle ids may differ only where several triangles share the closest point
+        got = np.array([r["point"] for r in recs]).reshape(-1, 3)
+        exp = np.array([cps[t] for t in expect]).reshape(-1, 3)
+        assert got.shape == exp.shape and np.allclose(got, exp, atol=1e-12)
+
+
+def _spd(rng, m):
+    X = rng.normal(size=(m, m + 2))
+    return X @ X.T / m + 0.05 * np.eye(m)
+
+
+def test_murty_matches_enumeration():
+    """P11: the LCP with SPD W has exactly one solution; pivoting finds it."""
+    rng = np.random.default_rng(13)
+    for m in range(1, 9):
+        for _ in range(6):
+            W = _spd(rng, m)
+            q = rng.normal(size=m)
+            sols = lcp.enumerate_lcp(W, q)
+            assert len(sols) == 1
+            y, w, _ = lcp.murty(W, q)
+            assert np.allclose(y, sols[0][0], atol=1e-12)
+            ww = W @ y + q
+            assert y.min() >= 0 and ww.min() >= -1e-12 and abs(y @ ww) <= 1e-12
+
+
+def test_murty_kkt_larger():
+    rng = np.random.default_rng(14)
+    for m in (20, 60):
+        W = _spd(rng, m)
+        q = rng.normal(size=m)
+        y, w, piv = lcp.murty(W, q)
+        ww = W @ y + q
+        assert y.min() >= 0 and ww.min() >= -1e-11 and np.abs(np.minimum(y, ww)).max() <= 1e-11

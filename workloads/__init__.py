@@ -1,0 +1,251 @@
+"""Seeded synthetic inputs for the contact-FEM hot path (robot, lumen mesh, loads).
+
+This module holds geometry and random draws only -- none of the method's
+arithmetic (no element, contact or solver code).  Both the CPU oracle and the
+CUDA path consume what it produces, so that the two sides see bit-identical
+inputs.  Every draw uses ``numpy.random.default_rng(seed)``.
+
+Workloads (sizes follow the paper's scale, Sec. IV.A: 100-400 nodes; the
+bronchial MRI mesh of the paper is not available, synthetic tubes stand in):
+
+* ``bent_tube_workload``  -- 120 mm rod, 20 elements, tube r = 5 mm made of a
+  40 mm straight run and a 90 deg arc of bend radius 60 mm, 24 around x 1 mm
+  axial; insertion 0 -> 100 mm; tensions U[0, 3] N.
+* ``catmull_rom_workload`` -- 600 mm rod, 300 elements, tube r = 6 mm around a
+  uniform Catmull-Rom centreline through 10 points 70 mm apart along x with
+  lateral offsets U[-25, 25] mm, 48 around x 1 mm axial; insertion swept
+  0 -> 600 mm in 60 steps; tensions U[0, 5] N per step.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "RobotDesc", "LumenDesc", "Workload", "robot_desc", "tube_mesh",
+    "bent_tube_centerline", "catmull_rom_centerline", "bent_tube_workload",
+    "catmull_rom_workload", "plane_lumen", "random_tensions",
+]
+
+
+@dataclass
+class RobotDesc:
+    """Robot geometry and material (Sec. II.A-B; section constants are derived by each side)."""
+    length: float
+    outer_radius: float
+    inner_radius: float
+    youngs_modulus: float
+    poisson_ratio: float
+    n_elements: int
+    n_cables: int = 3
+    cable_radius: float = 1.5e-3
+    cable_angles: np.ndarray = field(default_factory=lambda: np.array([0.0, 2 * math.pi / 3, 4 * math.pi / 3]))
+
+
+@dataclass
+class LumenDesc:
+    """Triangle soup of the lumen wall (outward winding) and the clamp frame at its entrance."""
+    vertices: np.ndarray          # (V, 3) float64, metres
+    triangles: np.ndarray         # (T, 3) int32, counter-clockwise seen from outside the lumen
+    entrance_point: np.ndarray    # (3,)
+    entrance_dir: np.ndarray      # (3,) unit, insertion direction
+    entrance_up: np.ndarray       # (3,) unit, orthogonal to entrance_dir
+
+
+@dataclass
+class Workload:
+    name: str
+    robot: RobotDesc
+    lumen: LumenDesc
+    insertions: np.ndarray        # (S,) insertion depth per solve, metres
+    tensions: np.ndarray          # (S, n_cables) cable tension per solve, newtons
+
+
+def robot_desc(length, n_elements, outer_radius=2e-3, inner_radius=1e-3, youngs_modulus=2.0e9,
+               poisson_ratio=0.35, cable_radius=1.5e-3) -> RobotDesc:
+    return RobotDesc(length=float(length), outer_radius=float(outer_radius), inner_radius=float(inner_radius),
+                     youngs_modulus=float(youngs_modulus), poisson_ratio=float(poisson_ratio),
+                     n_elements=int(n_elements), cable_radius=float(cable_radius))
+
+
+def _rmf(points: np.ndarray, t0_normal: np.ndarray):
+    """Rotation-minimising frames along a polyline by the double-reflection rule
+    (Wang, Juettler, Zheng, Liu 2008).  Returns tangents and normals per point."""
+    n = len(points)
+    tang = np.zeros_like(points)
+    d = np.diff(points, axis=0)
+    tang[1:-1] = points[2:] - points[:-2]
+    tang[0] = d[0]
+    tang[-1] = d[-1]
+    tang /= np.linalg.norm(tang, axis=1, keepdims=True)
+    norm = np.zeros_like(points)
+    r0 = t0_normal - np.dot(t0_normal, tang[0]) * tang[0]
+    norm[0] = r0 / np.linalg.norm(r0)
+    for i in range(n - 1):
+        v1 = points[i + 1] - points[i]
+        c1 = np.dot(v1, v1)
+        rl = norm[i] - (2.0 / c1) * np.dot(v1, norm[i]) * v1
+        tl = tang[i] - (2.0 / c1) * np.dot(v1, tang[i]) * v1
+        v2 = tang[i + 1] - tl
+        c2 = np.dot(v2, v2)
+        r = rl - (2.0 / c2) * np.dot(v2, rl) * v2 if c2 > 1e-30 else rl
+        r = r - np.dot(r, tang[i + 1]) * tang[i + 1]
+        norm[i + 1] = r / np.linalg.norm(r)
+    return tang, norm
+
+
+def tube_mesh(points: np.ndarray, radius: float, n_around: int, t0_normal=(0.0, 1.0, 0.0)):
+    """Open tube of circular section around a sampled centreline.
+
+    Ring k has ``n_around`` vertices at ``c_k + r (cos(phi) N_k + sin(phi) B_k)``;
+    quads between rings are split into two triangles wound counter-clockwise
+    when seen from outside (outward normals)."""
+    points = np.asarray(points, dtype=np.float64)
+    tang, norm = _rmf(points, np.asarray(t0_normal, dtype=np.float64))
+    binorm = np.cross(tang, norm)
+    phi = 2.0 * math.pi * np.arange(n_around) / n_around
+    cph, sph = np.cos(phi), np.sin(phi)
+    verts = (points[:, None, :] + radius * (cph[None, :, None] * norm[:, None, :]
+                                             + sph[None, :, None] * binorm[:, None, :]))
+    verts = verts.reshape(-1, 3)
+    K = len(points)
+    tris = []
+    for k in range(K - 1):
+        for j in range(n_around):
+            a = k * n_around + j
+            b = (k + 1) * n_around + j
+            c = (k + 1) * n_around + (j + 1) % n_around
+            d = k * n_around + (j + 1) % n_around
+            tris.append((a, d, c))
+            tris.append((a, c, b))
+    return verts, np.asarray(tris, dtype=np.int32), tang, norm
+
+
+def bent_tube_centerline(straight=0.040, arc_angle=math.pi / 2, bend_radius=0.060, ds=0.001):
+    """Centreline: straight run along +x from the origin, then a circular arc bending towards +y."""
+    n_s = int(round(straight / ds))
+    pts = [np.array([i * ds, 0.0, 0.0]) for i in range(n_s + 1)]
+    arc_len = arc_angle * bend_radius
+    n_a = int(math.ceil(arc_len / ds))
+    for i in range(1, n_a + 1):
+        a = arc_angle * i / n_a
+        pts.append(np.array([straight + bend_radius * math.sin(a), bend_radius * (1 - math.cos(a)), 0.0]))
+    return np.asarray(pts)
+
+
+def catmull_rom_centerline(seed: int, n_points=10, spacing=0.070, max_offset=0.025, ds=0.001):
+    """Uniform Catmull-Rom curve through ``n_points`` control points ``spacing`` apart along x
+    with lateral (y, z) offsets U[-max_offset, max_offset] (the first point sits at the origin),
+    resampled every ``ds`` of arc length."""
+    rng = np.random.default_rng(seed)
+    P = np.zeros((n_points, 3))
+    P[:, 0] = spacing * np.arange(n_points)
+    P[1:, 1:] = rng.uniform(-max_offset, max_offset, size=(n_points - 1, 2))
+    ext = np.vstack([2 * P[0] - P[1], P, 2 * P[-1] - P[-2]])
+    dense = []
+    sub = 400
+    for i in range(1, n_points):
+        p0, p1, p2, p3 = ext[i - 1], ext[i], ext[i + 1], ext[i + 2]
+        for s in range(sub):
+            t = s / sub
+            dense.append(0.5 * ((2 * p1) + (-p0 + p2) * t + (2 * p0 - 5 * p1 + 4 * p2 - p3) * t * t
+                                + (-p0 + 3 * p1 - 3 * p2 + p3) * t ** 3))
+    dense.append(P[-1])
+    dense = np.asarray(dense)
+    seg = np.linalg.norm(np.diff(dense, axis=0), axis=1)
+    arc = np.concatenate([[0.0], np.cumsum(seg)])
+    n_out = int(arc[-1] / ds)
+    targets = ds * np.arange(n_out + 1)
+    out = np.stack([np.interp(targets, arc, dense[:, k]) for k in range(3)], axis=1)
+    return out
+
+
+def _lumen_from_centerline(points, radius, n_around, up=(0.0, 1.0, 0.0)) -> LumenDesc:
+    verts, tris, tang, norm = tube_mesh(points, radius, n_around, up)
+    return LumenDesc(vertices=verts, triangles=tris, entrance_point=points[0].copy(),
+                     entrance_dir=tang[0].copy(), entrance_up=norm[0].copy())
+
+
+def random_tensions(seed: int, n_steps: int, t_max: float, n_cables: int = 3) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.0, t_max, size=(n_steps, n_cables))
+
+
+def bent_tube_workload(tension_seed: int = 0, n_steps: int = 10, insertion=0.100, n_elements=20,
+                       length=0.120) -> Workload:
+    """120 mm rod in a 5 mm tube with a 90 deg bend; insertion ramps to 100 mm in ``n_steps``
+    equal steps under one seeded tension triple U[0, 3] N."""
+    robot = robot_desc(length, n_elements)
+    lumen = _lumen_from_centerline(bent_tube_centerline(), 0.005, 24)
+    ins = insertion * np.arange(1, n_steps + 1) / n_steps
+    t = random_tensions(tension_seed, 1, 3.0)
+    return Workload("bent_tube_120mm_M%d" % n_elements, robot, lumen, ins, np.repeat(t, n_steps, axis=0))
+
+
+def catmull_rom_workload(lumen_seed: int = 1, tension_seed: int = 2, n_steps: int = 60, length=0.600,
+                         n_elements=300, max_insertion=None) -> Workload:
+    """600 mm rod, 300 elements, in a 6 mm Catmull-Rom tube; insertion swept 0 -> 600 mm in
+    ``n_steps`` warm-started steps with a fresh seeded tension triple U[0, 5] N per step."""
+    robot = robot_desc(length, n_elements)
+    lumen = _lumen_from_centerline(catmull_rom_centerline(lumen_seed), 0.006, 48)
+    top = length if max_insertion is None else max_insertion
+    ins = top * np.arange(1, n_steps + 1) / n_steps
+    t = random_tensions(tension_seed, n_steps, 5.0)
+    return Workload("catmull_rom_600mm_M%d" % n_elements, robot, lumen, ins, t)
+
+
+def plane_lumen(point, normal, size=0.2, n=8, entrance_point=(0.0, 0.0, 0.0), entrance_dir=(1.0, 0.0, 0.0),
+                entrance_up=(0.0, 1.0, 0.0)) -> LumenDesc:
+    """A flat square wall (``n`` x ``n`` quads, two triangles each) through ``point`` with unit
+    ``normal`` pointing away from the robot; used for closed-form contact checks."""
+    normal = np.asarray(normal, dtype=np.float64)
+    normal = normal / np.linalg.norm(normal)
+    a = np.cross(normal, [1.0, 0.0, 0.0])
+    if np.linalg.norm(a) < 1e-6:
+        a = np.cross(normal, [0.0, 1.0, 0.0])
+    a /= np.linalg.norm(a)
+    b = np.cross(normal, a)
+    g = np.linspace(-size / 2, size / 2, n + 1)
+    V = np.array([np.asarray(point) + u * a + v * b for u in g for v in g])
+    T = []
+    for i in range(n):
+        for j in range(n):
+            p00, p01, p10, p11 = i * (n + 1) + j, i * (n + 1) + j + 1, (i + 1) * (n + 1) + j, (i + 1) * (n + 1) + j + 1
+            for tri in ((p00, p10, p11), (p00, p11, p01)):
+                e1 = V[tri[1]] - V[tri[0]]
+                e2 = V[tri[2]] - V[tri[0]]
+                if np.dot(np.cross(e1, e2), normal) < 0:
+                    tri = (tri[0], tri[2], tri[1])
+                T.append(tri)
+    return LumenDesc(vertices=V, triangles=np.asarray(T, dtype=np.int32),
+                     entrance_point=np.asarray(entrance_point, float), entrance_dir=np.asarray(entrance_dir, float),
+                     entrance_up=np.asarray(entrance_up, float))
+
+
+def free_space_lumen(entrance_point=(0.0, 0.0, 0.0), entrance_dir=(1.0, 0.0, 0.0), entrance_up=(0.0, 1.0, 0.0)) -> LumenDesc:
+    """No wall at all (zero triangles): the clamp frame only, for free-space load cases."""
+    return LumenDesc(vertices=np.zeros((0, 3)), triangles=np.zeros((0, 3), np.int32),
+                     entrance_point=np.asarray(entrance_point, float), entrance_dir=np.asarray(entrance_dir, float),
+                     entrance_up=np.asarray(entrance_up, float))
+
+
+def patch_lumen(x0, x1, y, z_half=0.01, n=2) -> LumenDesc:
+    """A flat rectangular wall patch in the plane y = ``y`` over x in [x0, x1], |z| <= z_half,
+    outward normal +y (the robot sits below it); clamp at the origin along +x."""
+    xs = np.linspace(x0, x1, n + 1)
+    zs = np.linspace(-z_half, z_half, n + 1)
+    V = np.array([[x, y, z] for x in xs for z in zs])
+    T = []
+    for i in range(n):
+        for j in range(n):
+            a, b, c, d = i * (n + 1) + j, i * (n + 1) + j + 1, (i + 1) * (n + 1) + j, (i + 1) * (n + 1) + j + 1
+            for tri in ((a, c, d), (a, d, b)):
+                e1 = V[tri[1]] - V[tri[0]]
+                e2 = V[tri[2]] - V[tri[0]]
+                if np.cross(e1, e2)[1] < 0:
+                    tri = (tri[0], tri[2], tri[1])
+                T.append(tri)
+    return LumenDesc(vertices=V, triangles=np.asarray(T, np.int32), entrance_point=np.zeros(3),
+                     entrance_dir=np.array([1.0, 0.0, 0.0]), entrance_up=np.array([0.0, 1.0, 0.0]))
