@@ -194,7 +194,7 @@ class Model:
                 f, mo = cable_load(R[M], tensions, self.robot)
             else:
                 f, mo, follower = tip_load
-                f, mo = (R[M] @ self.E0.T @ f, R[M] @ self.E0.T @ mo) if follower else (np.asarray(f), np.asarray(mo))
+                f, mo = (R[M] @ np.asarray(f), R[M] @ np.asarray(mo)) if follower else (np.asarray(f), np.asarray(mo))
             Fa[6 * M:6 * M + 3] = f
             Fa[6 * M + 3:6 * M + 6] = mo
             g = (F - Fa)[6 * (k + 1):]
