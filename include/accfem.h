@@ -1,0 +1,163 @@
+/*
+ * accfem.h -- C ABI of the GB300 (sm_103a) contact-FEM hot path of Acc-FEM
+ * (H. Chen et al., "Accelerated Quasi-Static FEM for Real-Time Modeling of Continuum
+ * Robots with Multiple Contacts and Large Deformation", arXiv 2503.06922).
+ *
+ * One handle = one robot in one lumen, resident on the current CUDA device.  A call to
+ * accfem_solve is one quasi-static step of the paper (Sec. II-III): Newton iterations, each
+ * made of the corotational element force/tangent and their block-tridiagonal assembly
+ * (Eq. 20, Sec. III.C), node-vs-triangle collision detection (Eq. 3-10, Sec. III.C), the
+ * block factorisation and the contact-space solve of the QP of Eq. 23 through its LCP
+ * (Eq. 12-13, 22), and the step limiter (Eq. 25-27).  Every step runs in CUDA kernels.
+ *
+ * Units: metres, newtons, newton-metres, radians; all reals are IEEE binary64.
+ * Node i has material arc length s_i = i L / M; node 0 is the base, node M the tip.
+ * Quaternions are (w, x, y, z) and map the section triad to global coordinates
+ * (column 0 = robot axis, column 1 = entrance_up at rest).
+ *
+ * Ownership: every pointer argument is host memory owned by the caller, read or written
+ * only during the call (inputs are copied at create); the handle owns all device memory.
+ * Calls are synchronous on the handle's stream.  A handle is not thread-safe: use one
+ * host thread per handle.  No call aborts: every failure is reported as a status and, for
+ * calls taking a handle, a message retrievable with accfem_last_error.
+ */
+#ifndef ACCFEM_H
+#define ACCFEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct accfem_handle accfem_handle;
+
+typedef enum {
+  ACCFEM_OK = 0,
+  ACCFEM_E_INVALID_ARG = 1,     /* a descriptor, option or argument is out of range        */
+  ACCFEM_E_NOMEM = 2,           /* device or host allocation failed                          */
+  ACCFEM_E_CUDA = 3,            /* a CUDA runtime call failed (message has the CUDA error)    */
+  ACCFEM_E_NOT_CONVERGED = 4,   /* max_newton_iters reached; best iterate is still returned   */
+  ACCFEM_E_CONTACT_CAPACITY = 5,/* more constraint rows than max_contacts / result capacity  */
+  ACCFEM_E_NOT_SPD = 6,         /* a non-positive pivot in the tangent factorisation          */
+  ACCFEM_E_TIMEOUT = 7,         /* the contact LCP exceeded max_contact_iters pivots          */
+  ACCFEM_E_PENETRATION = 8      /* reserved: converged state violates non-penetration         */
+} accfem_status;
+
+/* Robot (Sec. II.A-B, Table 1 columns): hollow circular section, M equal two-node 6-DOF
+ * beam elements of length l0 = length / n_elements.  Cables (Eq. 16-18): cable j is welded
+ * to the tip at distance cable_radius from the axis, at angle cable_angles[j] from the
+ * section's second axis towards its third; n_cables <= 8. */
+typedef struct {
+  double length, outer_radius, inner_radius, youngs_modulus, poisson_ratio;
+  int32_t n_elements;           /* M >= 1; N = M + 1 nodes                                  */
+  int32_t n_cables;             /* 0..8                                                       */
+  double cable_radius;
+  const double* cable_angles;   /* n_cables values (radians)                                 */
+} accfem_robot_desc;
+
+/* Lumen (Eq. 3, Sec. III.C): triangle soup, outward winding (counter-clockwise seen from
+ * outside the lumen).  The clamp that feeds the robot sits at entrance_point, pushing along
+ * entrance_dir; entrance_up fixes the rest section triad (orthogonalised against dir). */
+typedef struct {
+  const double* vertices;       /* 3 * n_vertices, xyz                                       */
+  int64_t n_vertices;
+  const int32_t* triangles;     /* 3 * n_triangles vertex indices; n_triangles may be 0       */
+  int64_t n_triangles;
+  double entrance_point[3], entrance_dir[3], entrance_up[3];
+} accfem_lumen_desc;
+
+/* Options.  Defaults (accfem_default_options): activation_gap 1e-3 m (a constraint row is
+ * created when the clearance to a locally closest wall feature is below r_o + gap),
+ * step_limit beta0 = 5e-4 m (Eq. 25-26, applied to the largest nodal translation),
+ * newton_tol 1e-11 m (stop when the unlimited step has max(|du_i|, r_o |dtheta_i|) below it
+ * and the constraint set did not change), contact_tol 1e-13 (relative sign tolerance of the
+ * LCP pivoting), max_newton_iters 200, max_contact_iters 1000, max_contacts 256 (constraint
+ * rows), tangent_mode 0 (material tangent K = B^T K_l B; the only mode on the GPU). */
+typedef struct {
+  double activation_gap, step_limit, newton_tol, contact_tol;
+  int32_t max_newton_iters, max_contact_iters, max_contacts, tangent_mode;
+} accfem_options;
+
+/* Result of one solve.  The caller owns every buffer; node_pos holds 3*(M+1) doubles,
+ * node_quat 4*(M+1); the contact arrays hold contact_capacity entries (contact_point and
+ * contact_normal 3 per entry).  On return n_contacts is the number of constraint rows of
+ * the last Newton iteration (if it exceeds contact_capacity only the first
+ * contact_capacity are written and the status is ACCFEM_E_CONTACT_CAPACITY).
+ * contact_force[i] >= 0 is the multiplier y_i of Eq. 11 (newtons along -normal on the
+ * robot); contact_normal points from the robot to the far side of the wall (Eq. 3).
+ * base_reaction is the force and moment (global) that the clamp exerts on the last
+ * prescribed node, i.e. F(x) at that node (Eq. 14-15).  residual is max |F - F_a + A_c^T y|
+ * over the free DOFs at the last iterate. */
+typedef struct {
+  double* node_pos;
+  double* node_quat;
+  int32_t contact_capacity;
+  int32_t n_contacts;
+  int32_t* contact_node;
+  int32_t* contact_tri;
+  double* contact_point;
+  double* contact_normal;
+  double* contact_force;
+  double base_reaction[6];
+  int32_t newton_iters, contact_iters;
+  double residual;
+} accfem_result;
+
+/* Warm start: full nodal poses to start the Newton iterations from (prescribed nodes are
+ * reset to their clamp poses). */
+typedef struct {
+  const double* node_pos;   /* 3*(M+1) */
+  const double* node_quat;  /* 4*(M+1) */
+} accfem_state;
+
+/* Fills *out with the defaults above.  E_INVALID_ARG if out is NULL. */
+accfem_status accfem_default_options(accfem_options* out);
+
+/* Creates a handle on the current CUDA device: copies robot and lumen, builds the lumen's
+ * uniform grid, allocates all device memory for M elements and max_contacts rows.
+ * options may be NULL (defaults).  On failure *out is NULL and the status says why. */
+accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_desc* lumen,
+                            const accfem_options* options, accfem_handle** out);
+
+/* One quasi-static step (Sec. II-III): cable tensions (n_cables values, >= 0) mapped to the
+ * tip load of Eq. 16-18 (follower), insertion depth in [0, length] (nodes with
+ * s_i <= length - insertion are clamped on the entrance axis), optional warm start (NULL:
+ * the resident state of the previous call moved along the robot's own path by the change of
+ * insertion, or the straight pose on the first call).  Writes *out (see accfem_result).
+ * On E_NOT_CONVERGED the last iterate is still written and becomes the resident state. */
+accfem_status accfem_solve(accfem_handle* h, const double* cable_tensions, double insertion,
+                           const accfem_state* warm, accfem_result* out);
+
+/* Same step with a direct tip load instead of the cables: force f and moment m, given in the
+ * tip section frame and following it (follower != 0) or fixed in global axes (follower == 0).
+ * Used to check the path against closed forms (cantilever, end moment, ...). */
+accfem_status accfem_solve_tip_load(accfem_handle* h, const double f[3], const double m[3],
+                                    int32_t follower, double insertion, const accfem_state* warm,
+                                    accfem_result* out);
+
+/* Same step as accfem_solve, with cable_tensions in DEVICE memory and no result copied back:
+ * the solution stays resident (read it with accfem_get_state).  newton_iters (may be NULL)
+ * receives the iteration count.  For callers that keep their inputs on the GPU. */
+accfem_status accfem_solve_resident(accfem_handle* h, const double* device_cable_tensions,
+                                    double insertion, int32_t* newton_iters);
+
+/* Copies the resident nodal poses (3*(M+1) and 4*(M+1) doubles) to host buffers. */
+accfem_status accfem_get_state(accfem_handle* h, double* node_pos, double* node_quat);
+
+/* Number of kernel launches issued by this handle since creation (for launch accounting). */
+int64_t accfem_kernel_launches(const accfem_handle* h);
+
+/* Frees the handle and its device memory; NULL is a no-op. */
+void accfem_destroy(accfem_handle* h);
+
+/* Static description of a status code. */
+const char* accfem_status_string(accfem_status s);
+
+/* Message of the last failure on this handle ("" if none); valid until the next call. */
+const char* accfem_last_error(const accfem_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACCFEM_H */

@@ -1,0 +1,209 @@
+"""Thin ctypes binding of libaccfem.so (include/accfem.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; there is no Python or CPU fallback.
+Loading fails loudly when the library has not been built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libaccfem.so")
+
+OK, E_INVALID_ARG, E_NOMEM, E_CUDA, E_NOT_CONVERGED, E_CONTACT_CAPACITY, E_NOT_SPD, E_TIMEOUT, E_PENETRATION = range(9)
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+
+class accfem_robot_desc(ctypes.Structure):
+    _fields_ = [("length", ctypes.c_double), ("outer_radius", ctypes.c_double), ("inner_radius", ctypes.c_double),
+                ("youngs_modulus", ctypes.c_double), ("poisson_ratio", ctypes.c_double),
+                ("n_elements", ctypes.c_int32), ("n_cables", ctypes.c_int32), ("cable_radius", ctypes.c_double),
+                ("cable_angles", _dp)]
+
+
+class accfem_lumen_desc(ctypes.Structure):
+    _fields_ = [("vertices", _dp), ("n_vertices", ctypes.c_int64), ("triangles", _ip), ("n_triangles", ctypes.c_int64),
+                ("entrance_point", ctypes.c_double * 3), ("entrance_dir", ctypes.c_double * 3),
+                ("entrance_up", ctypes.c_double * 3)]
+
+
+class accfem_options(ctypes.Structure):
+    _fields_ = [("activation_gap", ctypes.c_double), ("step_limit", ctypes.c_double), ("newton_tol", ctypes.c_double),
+                ("contact_tol", ctypes.c_double), ("max_newton_iters", ctypes.c_int32),
+                ("max_contact_iters", ctypes.c_int32), ("max_contacts", ctypes.c_int32),
+                ("tangent_mode", ctypes.c_int32)]
+
+
+class accfem_result(ctypes.Structure):
+    _fields_ = [("node_pos", _dp), ("node_quat", _dp), ("contact_capacity", ctypes.c_int32),
+                ("n_contacts", ctypes.c_int32), ("contact_node", _ip), ("contact_tri", _ip),
+                ("contact_point", _dp), ("contact_normal", _dp), ("contact_force", _dp),
+                ("base_reaction", ctypes.c_double * 6), ("newton_iters", ctypes.c_int32),
+                ("contact_iters", ctypes.c_int32), ("residual", ctypes.c_double)]
+
+
+class accfem_state(ctypes.Structure):
+    _fields_ = [("node_pos", _dp), ("node_quat", _dp)]
+
+
+EXPORTS = ["accfem_default_options", "accfem_create", "accfem_solve", "accfem_solve_tip_load",
+           "accfem_solve_resident", "accfem_get_state", "accfem_kernel_launches", "accfem_destroy",
+           "accfem_status_string", "accfem_last_error"]
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Loads libaccfem.so and declares the C signatures; raises if the library is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libaccfem.so not built (%s); run paper_2503_06922_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    lib.accfem_default_options.argtypes = [ctypes.POINTER(accfem_options)]
+    lib.accfem_create.argtypes = [ctypes.POINTER(accfem_robot_desc), ctypes.POINTER(accfem_lumen_desc),
+                                  ctypes.POINTER(accfem_options), ctypes.POINTER(H)]
+    lib.accfem_solve.argtypes = [H, _dp, ctypes.c_double, ctypes.POINTER(accfem_state), ctypes.POINTER(accfem_result)]
+    lib.accfem_solve_tip_load.argtypes = [H, _dp, _dp, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(accfem_state),
+                                          ctypes.POINTER(accfem_result)]
+    lib.accfem_solve_resident.argtypes = [H, ctypes.c_void_p, ctypes.c_double, _ip]
+    lib.accfem_get_state.argtypes = [H, _dp, _dp]
+    lib.accfem_kernel_launches.argtypes = [H]
+    lib.accfem_kernel_launches.restype = ctypes.c_int64
+    lib.accfem_destroy.argtypes = [H]
+    lib.accfem_destroy.restype = None
+    lib.accfem_status_string.argtypes = [ctypes.c_int]
+    lib.accfem_status_string.restype = ctypes.c_char_p
+    lib.accfem_last_error.argtypes = [H]
+    lib.accfem_last_error.restype = ctypes.c_char_p
+    for name in ("accfem_default_options", "accfem_create", "accfem_solve", "accfem_solve_tip_load",
+                 "accfem_solve_resident", "accfem_get_state"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a, t=_dp):
+    return a.ctypes.data_as(t)
+
+
+def accfem_default_options(**overrides):
+    lib = load()
+    o = accfem_options()
+    lib.accfem_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def accfem_status_string(s):
+    return load().accfem_status_string(int(s)).decode()
+
+
+class AccFem:
+    """One handle (robot + lumen resident on the current CUDA device)."""
+
+    def __init__(self, robot, lumen, options=None, **overrides):
+        lib = load()
+        self._lib = lib
+        self.robot = robot
+        self.M = int(robot.n_elements)
+        self.N = self.M + 1
+        self._angles = np.ascontiguousarray(robot.cable_angles, dtype=np.float64)
+        self._V = np.ascontiguousarray(np.asarray(lumen.vertices, dtype=np.float64).reshape(-1, 3))
+        self._T = np.ascontiguousarray(np.asarray(lumen.triangles, dtype=np.int32).reshape(-1, 3))
+        rd = accfem_robot_desc(robot.length, robot.outer_radius, robot.inner_radius, robot.youngs_modulus,
+                               robot.poisson_ratio, self.M, len(self._angles), robot.cable_radius,
+                               _ptr(self._angles))
+        ld = accfem_lumen_desc(_ptr(self._V), len(self._V), _ptr(self._T, _ip), len(self._T),
+                               (ctypes.c_double * 3)(*lumen.entrance_point), (ctypes.c_double * 3)(*lumen.entrance_dir),
+                               (ctypes.c_double * 3)(*lumen.entrance_up))
+        opt = options if options is not None else accfem_default_options(**overrides)
+        self.options = opt
+        h = ctypes.c_void_p()
+        st = lib.accfem_create(ctypes.byref(rd), ctypes.byref(ld), ctypes.byref(opt), ctypes.byref(h))
+        if st != OK:
+            raise RuntimeError("accfem_create failed: %s" % accfem_status_string(st))
+        self.h = h
+        self.cap = int(opt.max_contacts)
+        self._pos = np.zeros((self.N, 3))
+        self._quat = np.zeros((self.N, 4))
+        self._cn = np.zeros(self.cap, np.int32)
+        self._ct = np.zeros(self.cap, np.int32)
+        self._cp = np.zeros((self.cap, 3))
+        self._cnrm = np.zeros((self.cap, 3))
+        self._cf = np.zeros(self.cap)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.accfem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _result_struct(self):
+        return accfem_result(_ptr(self._pos), _ptr(self._quat), self.cap, 0, _ptr(self._cn, _ip), _ptr(self._ct, _ip),
+                             _ptr(self._cp), _ptr(self._cnrm), _ptr(self._cf))
+
+    def _pack(self, st, r):
+        m = min(int(r.n_contacts), self.cap)
+        return {"status": int(st), "node_pos": self._pos.copy(), "node_quat": self._quat.copy(),
+                "n_contacts": int(r.n_contacts),
+                "contacts": [{"node": int(self._cn[i]), "tri": int(self._ct[i]), "point": self._cp[i].copy(),
+                              "normal": self._cnrm[i].copy(), "force": float(self._cf[i])} for i in range(m)],
+                "base_reaction": np.array(r.base_reaction[:]), "newton_iters": int(r.newton_iters),
+                "contact_iters": int(r.contact_iters), "residual": float(r.residual),
+                "error": self._lib.accfem_last_error(self.h).decode()}
+
+    @staticmethod
+    def _warm(warm):
+        if warm is None:
+            return None, None
+        pos = np.ascontiguousarray(warm[0], dtype=np.float64)
+        quat = np.ascontiguousarray(warm[1], dtype=np.float64)
+        return accfem_state(_ptr(pos), _ptr(quat)), (pos, quat)
+
+    def accfem_solve(self, tensions, insertion, warm=None):
+        t = np.ascontiguousarray(tensions, dtype=np.float64)
+        ws, keep = self._warm(warm)
+        r = self._result_struct()
+        st = self._lib.accfem_solve(self.h, _ptr(t), float(insertion), ctypes.byref(ws) if ws else None, ctypes.byref(r))
+        return self._pack(st, r)
+
+    def accfem_solve_tip_load(self, f, m, follower, insertion, warm=None):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        m = np.ascontiguousarray(m, dtype=np.float64)
+        ws, keep = self._warm(warm)
+        r = self._result_struct()
+        st = self._lib.accfem_solve_tip_load(self.h, _ptr(f), _ptr(m), int(bool(follower)), float(insertion),
+                                             ctypes.byref(ws) if ws else None, ctypes.byref(r))
+        return self._pack(st, r)
+
+    def accfem_solve_resident(self, device_tensions_ptr, insertion):
+        it = ctypes.c_int32(0)
+        st = self._lib.accfem_solve_resident(self.h, ctypes.c_void_p(int(device_tensions_ptr)), float(insertion),
+                                             ctypes.byref(it))
+        return int(st), int(it.value)
+
+    def accfem_get_state(self):
+        pos = np.zeros((self.N, 3))
+        quat = np.zeros((self.N, 4))
+        st = self._lib.accfem_get_state(self.h, _ptr(pos), _ptr(quat))
+        if st != OK:
+            raise RuntimeError("accfem_get_state failed: %s" % accfem_status_string(st))
+        return pos, quat
+
+    def accfem_kernel_launches(self):
+        return int(self._lib.accfem_kernel_launches(self.h))
+
+    def accfem_last_error(self):
+        return self._lib.accfem_last_error(self.h).decode()

@@ -1,0 +1,572 @@
+// C ABI of the Acc-FEM hot path (see include/accfem.h): handle set-up, lumen grid, and the Newton
+// driver that launches the per-iteration kernels on the handle's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "../../include/accfem.h"
+#include "common.cuh"
+
+namespace accfem {
+__global__ void element_kernel(Params p, Dev d);
+__global__ void collide_kernel(Params p, Dev d);
+__global__ void compact_kernel(Params p, Dev d);
+__global__ void assemble_kernel(Params p, Dev d);
+__global__ void rhs_kernel(Params p, Dev d);
+__global__ void bcr_elim_kernel(Params p, Dev d, int s);
+__global__ void bcr_keep_kernel(Params p, Dev d, int s);
+__global__ void bcr_root_kernel(Params p, Dev d);
+__global__ void bcr_fwd_kernel(Params p, Dev d, int s);
+__global__ void bcr_rootsolve_kernel(Params p, Dev d);
+__global__ void bcr_bwd_kernel(Params p, Dev d, int s);
+__global__ void contact_kernel(Params p, Dev d);
+__global__ void step_kernel(Params p, Dev d);
+__global__ void apply_kernel(Params p, Dev d);
+__global__ void start_kernel(Params p, Dev d, int mode, double delta, double delta_old, int k);
+void upload_element_tables();
+}  // namespace accfem
+
+using namespace accfem;
+
+struct accfem_handle {
+  Params p;
+  Dev d;
+  cudaStream_t stream = nullptr;
+  std::vector<void*> allocs;
+  Ctl* h_ctl = nullptr;            // pinned host mirror of the control block
+  double* h_stage = nullptr;       // pinned staging for results
+  size_t stage_bytes = 0;
+  bool has_state = false;
+  double delta = 0.0;
+  int64_t launches = 0;
+  int nf_cap = 0;
+  int max_newton = 200;
+  std::string err;
+};
+
+namespace {
+
+accfem_status fail(accfem_handle* h, accfem_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+bool cuda_ok(accfem_handle* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return true;
+  if (h) h->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return false;
+}
+
+template <typename T>
+bool dalloc(accfem_handle* h, T** ptr, size_t count) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+    h->err = "cudaMalloc failed";
+    return false;
+  }
+  cudaMemset(p, 0, count * sizeof(T));
+  h->allocs.push_back(p);
+  *ptr = (T*)p;
+  return true;
+}
+
+void quat_of_matrix(const double* R, double* q) {   // R row-major, Shepperd branch choice, w >= 0
+  double tr = R[0] + R[4] + R[8];
+  double c[4] = {tr, R[0], R[4], R[8]};
+  int k = 0;
+  for (int i = 1; i < 4; ++i)
+    if (c[i] > c[k]) k = i;
+  if (k == 0) {
+    double w = 0.5 * std::sqrt(1.0 + tr);
+    q[0] = w; q[1] = (R[7] - R[5]) / (4 * w); q[2] = (R[2] - R[6]) / (4 * w); q[3] = (R[3] - R[1]) / (4 * w);
+  } else if (k == 1) {
+    double x = 0.5 * std::sqrt(1.0 + 2 * R[0] - tr);
+    q[0] = (R[7] - R[5]) / (4 * x); q[1] = x; q[2] = (R[1] + R[3]) / (4 * x); q[3] = (R[2] + R[6]) / (4 * x);
+  } else if (k == 2) {
+    double y = 0.5 * std::sqrt(1.0 + 2 * R[4] - tr);
+    q[0] = (R[2] - R[6]) / (4 * y); q[1] = (R[1] + R[3]) / (4 * y); q[2] = y; q[3] = (R[5] + R[7]) / (4 * y);
+  } else {
+    double z = 0.5 * std::sqrt(1.0 + 2 * R[8] - tr);
+    q[0] = (R[3] - R[1]) / (4 * z); q[1] = (R[2] + R[6]) / (4 * z); q[2] = (R[5] + R[7]) / (4 * z); q[3] = z;
+  }
+  if (q[0] < 0) for (int i = 0; i < 4; ++i) q[i] = -q[i];
+  double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (int i = 0; i < 4; ++i) q[i] /= n;
+}
+
+int last_prescribed(double L, int M, double delta) {
+  return (int)std::floor((L - delta) * M / L + 1e-6);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* accfem_status_string(accfem_status s) {
+  switch (s) {
+    case ACCFEM_OK: return "ok";
+    case ACCFEM_E_INVALID_ARG: return "invalid argument";
+    case ACCFEM_E_NOMEM: return "out of memory";
+    case ACCFEM_E_CUDA: return "CUDA error";
+    case ACCFEM_E_NOT_CONVERGED: return "Newton iterations did not converge";
+    case ACCFEM_E_CONTACT_CAPACITY: return "contact capacity exceeded";
+    case ACCFEM_E_NOT_SPD: return "tangent or contact matrix not positive definite";
+    case ACCFEM_E_TIMEOUT: return "contact LCP pivot limit reached";
+    case ACCFEM_E_PENETRATION: return "penetration at convergence";
+  }
+  return "unknown status";
+}
+
+const char* accfem_last_error(const accfem_handle* h) { return h ? h->err.c_str() : ""; }
+
+int64_t accfem_kernel_launches(const accfem_handle* h) { return h ? h->launches : 0; }
+
+accfem_status accfem_default_options(accfem_options* o) {
+  if (!o) return ACCFEM_E_INVALID_ARG;
+  o->activation_gap = 1.0e-3;
+  o->step_limit = 5.0e-4;
+  o->newton_tol = 1.0e-11;
+  o->contact_tol = 1.0e-13;
+  o->max_newton_iters = 200;
+  o->max_contact_iters = 1000;
+  o->max_contacts = 256;
+  o->tangent_mode = 0;
+  return ACCFEM_OK;
+}
+
+void accfem_destroy(accfem_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->h_ctl) cudaFreeHost(h->h_ctl);
+  if (h->h_stage) cudaFreeHost(h->h_stage);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_desc* lumen,
+                            const accfem_options* options, accfem_handle** out) {
+  if (!out) return ACCFEM_E_INVALID_ARG;
+  *out = nullptr;
+  if (!robot || !lumen) return ACCFEM_E_INVALID_ARG;
+  accfem_options opt;
+  accfem_default_options(&opt);
+  if (options) opt = *options;
+  const auto& r = *robot;
+  if (!(r.length > 0) || !(r.outer_radius > 0) || !(r.inner_radius >= 0) || !(r.inner_radius < r.outer_radius) ||
+      !(r.youngs_modulus > 0) || !(r.poisson_ratio > -1.0 && r.poisson_ratio < 0.5) || r.n_elements < 1 ||
+      r.n_elements > (1 << 20) || r.n_cables < 0 || r.n_cables > kMaxCables || (r.n_cables > 0 && !r.cable_angles) ||
+      !(r.cable_radius >= 0))
+    return ACCFEM_E_INVALID_ARG;
+  if (lumen->n_vertices < 0 || lumen->n_triangles < 0 || lumen->n_triangles > (int64_t)INT32_MAX / 3 ||
+      (lumen->n_triangles > 0 && (!lumen->vertices || !lumen->triangles)))
+    return ACCFEM_E_INVALID_ARG;
+  if (!(opt.activation_gap >= 0) || !(opt.step_limit > 0) || !(opt.newton_tol > 0) || !(opt.contact_tol >= 0) ||
+      opt.max_newton_iters < 1 || opt.max_contact_iters < 1 || opt.max_contacts < 1 || opt.max_contacts > 4096 ||
+      opt.tangent_mode != 0)
+    return ACCFEM_E_INVALID_ARG;
+  // entrance frame
+  double dvec[3] = {lumen->entrance_dir[0], lumen->entrance_dir[1], lumen->entrance_dir[2]};
+  double dn = std::sqrt(dvec[0] * dvec[0] + dvec[1] * dvec[1] + dvec[2] * dvec[2]);
+  if (!(dn > 0)) return ACCFEM_E_INVALID_ARG;
+  for (double& v : dvec) v /= dn;
+  double up[3] = {lumen->entrance_up[0], lumen->entrance_up[1], lumen->entrance_up[2]};
+  double ud = up[0] * dvec[0] + up[1] * dvec[1] + up[2] * dvec[2];
+  for (int i = 0; i < 3; ++i) up[i] -= ud * dvec[i];
+  double un = std::sqrt(up[0] * up[0] + up[1] * up[1] + up[2] * up[2]);
+  if (!(un > 1e-12)) return ACCFEM_E_INVALID_ARG;
+  for (double& v : up) v /= un;
+  double th[3] = {dvec[1] * up[2] - dvec[2] * up[1], dvec[2] * up[0] - dvec[0] * up[2], dvec[0] * up[1] - dvec[1] * up[0]};
+
+  accfem_handle* h = new accfem_handle();
+  Params& p = h->p;
+  std::memset(&p, 0, sizeof(p));
+  p.M = r.n_elements;
+  p.N = r.n_elements + 1;
+  p.L = r.length;
+  p.l0 = r.length / r.n_elements;
+  const double PI = 3.14159265358979323846;
+  double A = PI * (r.outer_radius * r.outer_radius - r.inner_radius * r.inner_radius);
+  double I = PI * (std::pow(r.outer_radius, 4) - std::pow(r.inner_radius, 4)) / 4.0;
+  double G = r.youngs_modulus / (2.0 * (1.0 + r.poisson_ratio));
+  p.EA = r.youngs_modulus * A;
+  p.EI = r.youngs_modulus * I;
+  p.GJ = G * 2.0 * I;
+  p.r_o = r.outer_radius;
+  p.act = opt.activation_gap;
+  p.beta0 = opt.step_limit;
+  p.tol = opt.newton_tol;
+  p.lcp_tol = opt.contact_tol;
+  p.max_lcp_iters = opt.max_contact_iters;
+  for (int i = 0; i < 3; ++i) p.e[i] = lumen->entrance_point[i];
+  for (int i = 0; i < 3; ++i) { p.E0[3 * i] = dvec[i]; p.E0[3 * i + 1] = up[i]; p.E0[3 * i + 2] = th[i]; }
+  quat_of_matrix(p.E0, p.q0);
+  p.n_cables = r.n_cables;
+  p.r_c = r.cable_radius;
+  for (int j = 0; j < r.n_cables; ++j) { p.cable_cos[j] = std::cos(r.cable_angles[j]); p.cable_sin[j] = std::sin(r.cable_angles[j]); }
+  p.m_cap = opt.max_contacts;
+  p.nrhs_cap = opt.max_contacts + 1;
+  p.eps_d = 1e-6;
+  p.eps_b = 1e-3f;
+  h->nf_cap = p.M;
+  h->max_newton = opt.max_newton_iters;
+
+  // ---- lumen grid (host): triangles binned by centroid
+  const int64_t T = lumen->n_triangles;
+  const int64_t NV = lumen->n_vertices;
+  std::vector<double> cen(3 * T), nface(3 * T);
+  double rmax = 0.0;
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int64_t t = 0; t < T; ++t) {
+    const int32_t* tv = lumen->triangles + 3 * t;
+    for (int k = 0; k < 3; ++k)
+      if (tv[k] < 0 || tv[k] >= NV) { delete h; return ACCFEM_E_INVALID_ARG; }
+    const double* a = lumen->vertices + 3 * tv[0];
+    const double* b = lumen->vertices + 3 * tv[1];
+    const double* c = lumen->vertices + 3 * tv[2];
+    double ab[3], ac[3], n[3];
+    for (int k = 0; k < 3; ++k) { ab[k] = b[k] - a[k]; ac[k] = c[k] - a[k]; cen[3 * t + k] = (a[k] + b[k] + c[k]) / 3.0; }
+    n[0] = ab[1] * ac[2] - ab[2] * ac[1]; n[1] = ab[2] * ac[0] - ab[0] * ac[2]; n[2] = ab[0] * ac[1] - ab[1] * ac[0];
+    double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (!(nn > 0) || !std::isfinite(nn)) { delete h; return ACCFEM_E_INVALID_ARG; }
+    for (int k = 0; k < 3; ++k) nface[3 * t + k] = n[k] / nn;
+    for (const double* v : {a, b, c}) {
+      double dx = v[0] - cen[3 * t], dy = v[1] - cen[3 * t + 1], dz = v[2] - cen[3 * t + 2];
+      rmax = std::max(rmax, std::sqrt(dx * dx + dy * dy + dz * dz));
+    }
+    for (int k = 0; k < 3; ++k) {
+      if (t == 0 || cen[3 * t + k] < lo[k]) lo[k] = cen[3 * t + k];
+      if (t == 0 || cen[3 * t + k] > hi[k]) hi[k] = cen[3 * t + k];
+    }
+  }
+  p.g_rq = p.r_o + p.act + rmax + 1e-9;
+  double hcell = p.g_rq;
+  int64_t ncell = 1;
+  for (int it = 0; it < 64; ++it) {
+    ncell = 1;
+    for (int k = 0; k < 3; ++k) {
+      p.g_dim[k] = (int)std::floor((hi[k] - lo[k]) / hcell) + 1;
+      ncell *= p.g_dim[k];
+    }
+    if (ncell <= (int64_t)(1 << 24)) break;
+    hcell *= 1.26;
+  }
+  p.g_h = hcell;
+  for (int k = 0; k < 3; ++k) p.g_org[k] = lo[k];
+  p.n_tri = (int)T;
+  std::vector<int> cell_of(T), cstart(ncell + 1, 0), ctri(T);
+  for (int64_t t = 0; t < T; ++t) {
+    int ci[3];
+    for (int k = 0; k < 3; ++k) {
+      ci[k] = (int)std::floor((cen[3 * t + k] - p.g_org[k]) / p.g_h);
+      ci[k] = std::min(std::max(ci[k], 0), p.g_dim[k] - 1);
+    }
+    cell_of[t] = (ci[2] * p.g_dim[1] + ci[1]) * p.g_dim[0] + ci[0];
+    cstart[cell_of[t] + 1]++;
+  }
+  for (int64_t c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
+  {
+    std::vector<int> fillp(cstart.begin(), cstart.end() - 1);
+    for (int64_t t = 0; t < T; ++t) ctri[fillp[cell_of[t]]++] = (int)t;
+  }
+  std::vector<float> tri32(9 * std::max<int64_t>(T, 1));
+  for (int64_t c = 0; c < ncell; ++c) {
+    int cz = (int)(c / ((int64_t)p.g_dim[0] * p.g_dim[1]));
+    int cy = (int)((c / p.g_dim[0]) % p.g_dim[1]);
+    int cx = (int)(c % p.g_dim[0]);
+    double ctr[3] = {p.g_org[0] + (cx + 0.5) * p.g_h, p.g_org[1] + (cy + 0.5) * p.g_h, p.g_org[2] + (cz + 0.5) * p.g_h};
+    for (int s = cstart[c]; s < cstart[c + 1]; ++s) {
+      const int32_t* tv = lumen->triangles + 3 * (int64_t)ctri[s];
+      for (int v = 0; v < 3; ++v)
+        for (int k = 0; k < 3; ++k) tri32[9 * (int64_t)s + 3 * v + k] = (float)(lumen->vertices[3 * tv[v] + k] - ctr[k]);
+    }
+  }
+
+  // ---- device memory
+  if (!cuda_ok(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate")) {
+    accfem_destroy(h);
+    return ACCFEM_E_CUDA;
+  }
+  upload_element_tables();
+  Dev& d = h->d;
+  const int N = p.N, M = p.M, nfc = h->nf_cap, mc = p.m_cap;
+  bool ok = dalloc(h, &d.px, N) && dalloc(h, &d.py, N) && dalloc(h, &d.pz, N) && dalloc(h, &d.qw, N) &&
+            dalloc(h, &d.qx, N) && dalloc(h, &d.qy, N) && dalloc(h, &d.qz, N) && dalloc(h, &d.ox, N) &&
+            dalloc(h, &d.oy, N) && dalloc(h, &d.oz, N) && dalloc(h, &d.ow, N) && dalloc(h, &d.oqx, N) &&
+            dalloc(h, &d.oqy, N) && dalloc(h, &d.oqz, N) && dalloc(h, &d.elem, (size_t)M * kElemStride);
+  int *cs = nullptr, *ct = nullptr, *tv = nullptr;
+  float* t32 = nullptr;
+  double *vv = nullptr, *nfc_d = nullptr;
+  ok = ok && dalloc(h, &cs, ncell + 1) && dalloc(h, &ct, std::max<int64_t>(T, 1)) && dalloc(h, &t32, tri32.size()) &&
+       dalloc(h, &vv, std::max<int64_t>(3 * NV, 1)) && dalloc(h, &tv, std::max<int64_t>(3 * T, 1)) &&
+       dalloc(h, &nfc_d, std::max<int64_t>(3 * T, 1));
+  ok = ok && dalloc(h, &d.ncon, nfc) && dalloc(h, &d.con_tri, (size_t)nfc * kCpn) &&
+       dalloc(h, &d.con_pt, (size_t)nfc * kCpn * 3) && dalloc(h, &d.con_n, (size_t)nfc * kCpn * 3) &&
+       dalloc(h, &d.con_gap, (size_t)nfc * kCpn) && dalloc(h, &d.c_node, mc) && dalloc(h, &d.c_tri, mc) &&
+       dalloc(h, &d.c_pt, 3 * mc) && dalloc(h, &d.c_n, 3 * mc) && dalloc(h, &d.c_gap, mc) &&
+       dalloc(h, &d.c_first, nfc + 1) && dalloc(h, &d.p_node, mc) && dalloc(h, &d.p_tri, mc) &&
+       dalloc(h, &d.D, (size_t)nfc * 36) && dalloc(h, &d.U, (size_t)nfc * 36) && dalloc(h, &d.P, (size_t)nfc * 36) &&
+       dalloc(h, &d.Lm, (size_t)nfc * 36) && dalloc(h, &d.Rm, (size_t)nfc * 36) &&
+       dalloc(h, &d.B, (size_t)nfc * 6 * p.nrhs_cap) && dalloc(h, &d.g, (size_t)nfc * 6) &&
+       dalloc(h, &d.dx, (size_t)nfc * 6) && dalloc(h, &d.W, (size_t)mc * mc) && dalloc(h, &d.q, mc) &&
+       dalloc(h, &d.y, mc) && dalloc(h, &d.w, mc) && dalloc(h, &d.gj, (size_t)mc * (mc + 2)) &&
+       dalloc(h, &d.inP, mc) && dalloc(h, &d.plist, mc) && dalloc(h, &d.ctl, 1);
+  if (!ok) {
+    accfem_destroy(h);
+    return ACCFEM_E_NOMEM;
+  }
+  ok = cuda_ok(h, cudaMemcpy(cs, cstart.data(), sizeof(int) * (ncell + 1), cudaMemcpyHostToDevice), "upload grid") &&
+       (T == 0 || cuda_ok(h, cudaMemcpy(ct, ctri.data(), sizeof(int) * T, cudaMemcpyHostToDevice), "upload grid")) &&
+       (T == 0 || cuda_ok(h, cudaMemcpy(t32, tri32.data(), sizeof(float) * 9 * T, cudaMemcpyHostToDevice), "upload grid")) &&
+       (NV == 0 || cuda_ok(h, cudaMemcpy(vv, lumen->vertices, sizeof(double) * 3 * NV, cudaMemcpyHostToDevice), "upload mesh")) &&
+       (T == 0 || cuda_ok(h, cudaMemcpy(tv, lumen->triangles, sizeof(int) * 3 * T, cudaMemcpyHostToDevice), "upload mesh")) &&
+       (T == 0 || cuda_ok(h, cudaMemcpy(nfc_d, nface.data(), sizeof(double) * 3 * T, cudaMemcpyHostToDevice), "upload mesh"));
+  if (!ok) {
+    accfem_destroy(h);
+    return ACCFEM_E_CUDA;
+  }
+  d.cell_start = cs; d.cell_tri = ct; d.tri32 = t32; d.V = vv; d.T = tv; d.nface = nfc_d;
+  if (cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess) { accfem_destroy(h); return ACCFEM_E_NOMEM; }
+  h->stage_bytes = sizeof(double) * (size_t)std::max<int64_t>(7 * N, 16 * (int64_t)mc + 64);
+  if (cudaMallocHost(&h->h_stage, h->stage_bytes) != cudaSuccess) { accfem_destroy(h); return ACCFEM_E_NOMEM; }
+  std::memset(h->h_ctl, 0, sizeof(Ctl));
+  *out = h;
+  return ACCFEM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+#define LAUNCH(h, ...)                                  \
+  do {                                                  \
+    __VA_ARGS__;                                        \
+    ++(h)->launches;                                    \
+  } while (0)
+
+// Runs one solve on the device; the solution stays resident.  Returns the status.
+accfem_status run_solve(accfem_handle* h, int load_mode, const double* tensions_host, const double* tensions_dev,
+                        const double* tip_f, const double* tip_m, double insertion, const accfem_state* warm) {
+  Params& p = h->p;
+  Dev& d = h->d;
+  if (!(insertion >= 0.0 && insertion <= p.L)) return fail(h, ACCFEM_E_INVALID_ARG, "insertion outside [0, length]");
+  const int k = std::min(std::max(last_prescribed(p.L, p.M, insertion), 0), p.M);
+  const int nf = p.M - k;
+  Ctl& c = *h->h_ctl;
+  std::memset(&c, 0, sizeof(Ctl));
+  c.k = k;
+  c.nf = nf;
+  c.m_prev = -1;
+  c.load_mode = load_mode;
+  c.delta = insertion;
+  if (load_mode == 0 && tensions_host) {
+    for (int j = 0; j < p.n_cables; ++j) {
+      if (!(tensions_host[j] >= 0.0) || !std::isfinite(tensions_host[j]))
+        return fail(h, ACCFEM_E_INVALID_ARG, "cable tensions must be finite and non-negative");
+      c.tension[j] = tensions_host[j];
+    }
+  }
+  if (load_mode != 0)
+    for (int a = 0; a < 3; ++a) {
+      if (!std::isfinite(tip_f[a]) || !std::isfinite(tip_m[a])) return fail(h, ACCFEM_E_INVALID_ARG, "tip load not finite");
+      c.tip_f[a] = tip_f[a];
+      c.tip_m[a] = tip_m[a];
+    }
+  cudaStream_t st = h->stream;
+  if (!cuda_ok(h, cudaMemcpyAsync(d.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st), "upload control")) return ACCFEM_E_CUDA;
+  if (load_mode == 0 && tensions_dev && p.n_cables > 0) {
+    if (!cuda_ok(h, cudaMemcpyAsync(&d.ctl->tension[0], tensions_dev, sizeof(double) * p.n_cables, cudaMemcpyDeviceToDevice, st),
+                 "copy tensions"))
+      return ACCFEM_E_CUDA;
+  }
+  int mode = 0;
+  const size_t nb = sizeof(double) * p.N;
+  if (warm) {
+    if (!warm->node_pos || !warm->node_quat) return fail(h, ACCFEM_E_INVALID_ARG, "warm state has NULL arrays");
+    double* s = h->h_stage;
+    for (int comp = 0; comp < 7; ++comp)
+      for (int i = 0; i < p.N; ++i)
+        s[comp * p.N + i] = comp < 3 ? warm->node_pos[3 * i + comp] : warm->node_quat[4 * i + comp - 3];
+    double* dst[7] = {d.px, d.py, d.pz, d.qw, d.qx, d.qy, d.qz};
+    for (int comp = 0; comp < 7; ++comp)
+      if (!cuda_ok(h, cudaMemcpyAsync(dst[comp], s + comp * p.N, nb, cudaMemcpyHostToDevice, st), "upload warm state"))
+        return ACCFEM_E_CUDA;
+    mode = 2;
+  } else if (h->has_state) {
+    double* src[7] = {d.px, d.py, d.pz, d.qw, d.qx, d.qy, d.qz};
+    double* dst[7] = {d.ox, d.oy, d.oz, d.ow, d.oqx, d.oqy, d.oqz};
+    for (int comp = 0; comp < 7; ++comp)
+      if (!cuda_ok(h, cudaMemcpyAsync(dst[comp], src[comp], nb, cudaMemcpyDeviceToDevice, st), "copy state")) return ACCFEM_E_CUDA;
+    mode = 1;
+  }
+  LAUNCH(h, start_kernel<<<(p.N + 127) / 128, 128, 0, st>>>(p, d, mode, insertion, h->delta, k));
+  h->has_state = true;
+  h->delta = insertion;
+  accfem_status status = ACCFEM_OK;
+  if (nf > 0) {
+    const int ne = p.M - k;
+    const int rhs_blocks = (p.nrhs_cap + 31) / 32;
+    std::vector<int> strides;
+    for (int s = 1; s < nf; s *= 2) strides.push_back(s);
+    status = ACCFEM_E_NOT_CONVERGED;
+    for (int it = 0; it < h->max_newton; ++it) {
+      LAUNCH(h, element_kernel<<<(ne + kWarpsPerElemBlock - 1) / kWarpsPerElemBlock, 32 * kWarpsPerElemBlock, 0, st>>>(p, d));
+      LAUNCH(h, collide_kernel<<<(nf + 3) / 4, 128, 0, st>>>(p, d));
+      LAUNCH(h, compact_kernel<<<1, 1024, 0, st>>>(p, d));
+      LAUNCH(h, assemble_kernel<<<nf, 96, 0, st>>>(p, d));
+      LAUNCH(h, rhs_kernel<<<dim3(nf, rhs_blocks), dim3(32, 6), 0, st>>>(p, d));
+      for (int s : strides) {
+        int ne_ = (nf - s - 1) / (2 * s) + 1;
+        int nk = (nf - 1) / (2 * s) + 1;
+        LAUNCH(h, bcr_elim_kernel<<<ne_, 64, 0, st>>>(p, d, s));
+        LAUNCH(h, bcr_keep_kernel<<<nk, 64, 0, st>>>(p, d, s));
+      }
+      LAUNCH(h, bcr_root_kernel<<<1, 64, 0, st>>>(p, d));
+      for (int s : strides) {
+        int nk = (nf - 1) / (2 * s) + 1;
+        LAUNCH(h, bcr_fwd_kernel<<<dim3(nk, rhs_blocks), dim3(32, 6), 0, st>>>(p, d, s));
+      }
+      LAUNCH(h, bcr_rootsolve_kernel<<<dim3(1, rhs_blocks), dim3(32, 6), 0, st>>>(p, d));
+      for (int si = (int)strides.size() - 1; si >= 0; --si) {
+        int s = strides[si];
+        int ne_ = (nf - s - 1) / (2 * s) + 1;
+        LAUNCH(h, bcr_bwd_kernel<<<dim3(ne_, rhs_blocks), dim3(32, 6), 0, st>>>(p, d, s));
+      }
+      LAUNCH(h, contact_kernel<<<1, 1024, 0, st>>>(p, d));
+      LAUNCH(h, step_kernel<<<(nf + 31) / 32, dim3(32, 6), 0, st>>>(p, d));
+      LAUNCH(h, apply_kernel<<<(nf + 127) / 128, 128, 0, st>>>(p, d));
+      if (!cuda_ok(h, cudaGetLastError(), "kernel launch")) return ACCFEM_E_CUDA;
+      if (!cuda_ok(h, cudaMemcpyAsync(h->h_ctl, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st), "read control") ||
+          !cuda_ok(h, cudaStreamSynchronize(st), "Newton iteration"))
+        return ACCFEM_E_CUDA;
+      if (c.status != 0) {
+        status = (accfem_status)c.status;
+        break;
+      }
+      if (c.converged) {
+        status = ACCFEM_OK;
+        break;
+      }
+    }
+    if (status == ACCFEM_E_NOT_CONVERGED) h->err = "Newton iterations did not converge";
+    else if (status != ACCFEM_OK) h->err = accfem_status_string(status);
+  } else {
+    if (!cuda_ok(h, cudaMemcpyAsync(h->h_ctl, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st), "read control") ||
+        !cuda_ok(h, cudaStreamSynchronize(st), "start pose"))
+      return ACCFEM_E_CUDA;
+  }
+  return status;
+}
+
+// Copies the resident solution into *out.
+accfem_status download(accfem_handle* h, accfem_status status, accfem_result* out) {
+  Params& p = h->p;
+  Dev& d = h->d;
+  Ctl& c = *h->h_ctl;
+  cudaStream_t st = h->stream;
+  const int N = p.N;
+  double* s = h->h_stage;
+  const double* src[7] = {d.px, d.py, d.pz, d.qw, d.qx, d.qy, d.qz};
+  for (int comp = 0; comp < 7; ++comp)
+    if (!cuda_ok(h, cudaMemcpyAsync(s + comp * N, src[comp], sizeof(double) * N, cudaMemcpyDeviceToHost, st), "download state"))
+      return ACCFEM_E_CUDA;
+  if (!cuda_ok(h, cudaStreamSynchronize(st), "download state")) return ACCFEM_E_CUDA;
+  if (out->node_pos)
+    for (int i = 0; i < N; ++i)
+      for (int a = 0; a < 3; ++a) out->node_pos[3 * i + a] = s[a * N + i];
+  if (out->node_quat)
+    for (int i = 0; i < N; ++i)
+      for (int a = 0; a < 4; ++a) out->node_quat[4 * i + a] = s[(3 + a) * N + i];
+  out->newton_iters = c.iter;
+  out->contact_iters = c.lcp_pivots;
+  out->residual = c.nf > 0 ? __builtin_bit_cast(double, (unsigned long long)c.res_bits) : 0.0;
+  for (int a = 0; a < 6; ++a) out->base_reaction[a] = 0.0;
+  const int m = (c.nf > 0 && c.iter > 0) ? c.m : 0;
+  out->n_contacts = m;
+  if (c.nf > 0 && c.iter > 0) {
+    // base reaction: F(x) at the last prescribed node = element k's a-end force/moment
+    if (!cuda_ok(h, cudaMemcpyAsync(s, d.elem + (size_t)c.k * kElemStride + 78, sizeof(double) * 6, cudaMemcpyDeviceToHost, st),
+                 "download reaction"))
+      return ACCFEM_E_CUDA;
+    if (!cuda_ok(h, cudaStreamSynchronize(st), "download reaction")) return ACCFEM_E_CUDA;
+    for (int a = 0; a < 6; ++a) out->base_reaction[a] = s[a];
+  }
+  if (m > 0) {
+    const int nw = std::min(m, std::max(out->contact_capacity, 0));
+    if (nw > 0) {
+      std::vector<int> node(m), tri(m);
+      std::vector<double> pt(3 * m), nn(3 * m), y(m);
+      bool ok = cuda_ok(h, cudaMemcpyAsync(node.data(), d.c_node, sizeof(int) * m, cudaMemcpyDeviceToHost, st), "download") &&
+                cuda_ok(h, cudaMemcpyAsync(tri.data(), d.c_tri, sizeof(int) * m, cudaMemcpyDeviceToHost, st), "download") &&
+                cuda_ok(h, cudaMemcpyAsync(pt.data(), d.c_pt, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, st), "download") &&
+                cuda_ok(h, cudaMemcpyAsync(nn.data(), d.c_n, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, st), "download") &&
+                cuda_ok(h, cudaMemcpyAsync(y.data(), d.y, sizeof(double) * m, cudaMemcpyDeviceToHost, st), "download") &&
+                cuda_ok(h, cudaStreamSynchronize(st), "download contacts");
+      if (!ok) return ACCFEM_E_CUDA;
+      for (int i = 0; i < nw; ++i) {
+        if (out->contact_node) out->contact_node[i] = c.k + 1 + node[i];
+        if (out->contact_tri) out->contact_tri[i] = tri[i];
+        for (int a = 0; a < 3; ++a) {
+          if (out->contact_point) out->contact_point[3 * i + a] = pt[3 * i + a];
+          if (out->contact_normal) out->contact_normal[3 * i + a] = nn[3 * i + a];
+        }
+        if (out->contact_force) out->contact_force[i] = c.alpha * y[i];
+      }
+    }
+    if (m > out->contact_capacity && status == ACCFEM_OK) {
+      h->err = "result contact capacity too small";
+      return ACCFEM_E_CONTACT_CAPACITY;
+    }
+  }
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+accfem_status accfem_solve(accfem_handle* h, const double* cable_tensions, double insertion, const accfem_state* warm,
+                           accfem_result* out) {
+  if (!h || !out || (h->p.n_cables > 0 && !cable_tensions)) return fail(h, ACCFEM_E_INVALID_ARG, "NULL argument");
+  h->err.clear();
+  accfem_status s = run_solve(h, 0, cable_tensions, nullptr, nullptr, nullptr, insertion, warm);
+  if (s == ACCFEM_E_INVALID_ARG || s == ACCFEM_E_CUDA) return s;
+  return download(h, s, out);
+}
+
+accfem_status accfem_solve_tip_load(accfem_handle* h, const double f[3], const double m[3], int32_t follower,
+                                    double insertion, const accfem_state* warm, accfem_result* out) {
+  if (!h || !out || !f || !m) return fail(h, ACCFEM_E_INVALID_ARG, "NULL argument");
+  h->err.clear();
+  accfem_status s = run_solve(h, follower ? 2 : 1, nullptr, nullptr, f, m, insertion, warm);
+  if (s == ACCFEM_E_INVALID_ARG || s == ACCFEM_E_CUDA) return s;
+  return download(h, s, out);
+}
+
+accfem_status accfem_solve_resident(accfem_handle* h, const double* device_cable_tensions, double insertion,
+                                    int32_t* newton_iters) {
+  if (!h || (h->p.n_cables > 0 && !device_cable_tensions)) return fail(h, ACCFEM_E_INVALID_ARG, "NULL argument");
+  h->err.clear();
+  accfem_status s = run_solve(h, 0, nullptr, device_cable_tensions, nullptr, nullptr, insertion, nullptr);
+  if (newton_iters) *newton_iters = h->h_ctl->iter;
+  return s;
+}
+
+accfem_status accfem_get_state(accfem_handle* h, double* node_pos, double* node_quat) {
+  if (!h || !node_pos || !node_quat) return fail(h, ACCFEM_E_INVALID_ARG, "NULL argument");
+  accfem_result r;
+  std::memset(&r, 0, sizeof(r));
+  r.node_pos = node_pos;
+  r.node_quat = node_quat;
+  Ctl saved = *h->h_ctl;
+  h->h_ctl->nf = 0;   // poses only
+  accfem_status s = download(h, ACCFEM_OK, &r);
+  *h->h_ctl = saved;
+  return s;
+}
+
+}  // extern "C"

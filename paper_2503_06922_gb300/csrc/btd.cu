@@ -1,0 +1,352 @@
+// Assembly of the block-tridiagonal tangent over the free nodes (Eq. 20-23; Sec. III.C "assemble
+// them into a tangent stiffness matrix") and its factorisation / multi-RHS solve by block cyclic
+// reduction (6x6 blocks, depth ceil(log2 nf)).
+//
+// Free node f = node - k - 1 (f = 0 .. nf-1).  D_f = K_bb(elem node-1) + K_aa(elem node);
+// U_f = K_{f,f+1} = K_ab(elem node); g_f = F(node) - F_a(node).  The prescribed DOFs are eliminated
+// (Eq. 14-15), so the system is K dx = rhs on 6 nf unknowns.
+//
+// Cyclic reduction, level with stride s (s = 1, 2, 4, .. < nf): nodes j = s (mod 2s) are
+// eliminated, nodes i = 0 (mod 2s) kept.  For eliminated j: P_j = D_j^{-1}, L_j = U_{j-s} P_j,
+// R_j = U_j^T P_j.  For kept i: D_i -= R_{i-s} U_{i-s} + L_{i+s} U_i^T, U_i <- -L_{i+s} U_{i+s}.
+// Solve: forward b_i -= R_{i-s} b_{i-s} + L_{i+s} b_{i+s} (kept), root x_0 = P_0 b_0, backward
+// x_j = P_j b_j - L_j^T x_{j-s} - R_j^T x_{j+s} (eliminated).
+#include "common.cuh"
+
+namespace accfem {
+
+__device__ __forceinline__ int up_index(int i, int j) {   // upper triangle, row-major, i <= j < 12
+  return i * 12 - (i * (i - 1)) / 2 + (j - i);
+}
+__device__ __forceinline__ double kval(const double* rec, int i, int j) {
+  return i <= j ? rec[up_index(i, j)] : rec[up_index(j, i)];
+}
+
+// ------------------------------------------------------------------ constraint compaction
+// One CTA: exclusive scan of the per-node row counts, row arrays in (node, triangle) order,
+// comparison with the previous iteration's rows, copy to "previous".
+__global__ void __launch_bounds__(1024) compact_kernel(Params p, Dev d) {
+  __shared__ int s_part[1024];
+  __shared__ int s_warp[32];
+  __shared__ int s_same;
+  Ctl* ctl = d.ctl;
+  if (ctl->status != 0 || ctl->converged) return;
+  const int nf = ctl->nf;
+  const int tid = threadIdx.x;
+  const int per = (nf + 1023) / 1024;
+  const int f0 = tid * per, f1 = min(f0 + per, nf);
+  int loc = 0;
+  for (int f = f0; f < f1; ++f) loc += d.ncon[f];
+  // block exclusive scan of loc
+  int v = loc;
+  const int lane = tid & 31, w = tid >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) s_warp[w] = v;
+  if (tid == 0) s_same = 1;
+  __syncthreads();
+  if (w == 0) {
+    int x = s_warp[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    s_warp[lane] = x;
+  }
+  __syncthreads();
+  int excl = v - loc + (w > 0 ? s_warp[w - 1] : 0);
+  const int m = s_warp[31];
+  if (m > p.m_cap) {
+    if (tid == 0) atomicCAS(&ctl->status, 0, ST_CAPACITY);
+    return;
+  }
+  int row = excl;
+  for (int f = f0; f < f1; ++f) {
+    d.c_first[f] = row;
+    int nc = d.ncon[f];
+    for (int r = 0; r < nc; ++r, ++row) {
+      d.c_node[row] = f;
+      d.c_tri[row] = d.con_tri[f * kCpn + r];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        d.c_pt[3 * row + c] = d.con_pt[(f * kCpn + r) * 3 + c];
+        d.c_n[3 * row + c] = d.con_n[(f * kCpn + r) * 3 + c];
+      }
+      d.c_gap[row] = d.con_gap[f * kCpn + r];
+    }
+  }
+  if (tid == 0) d.c_first[nf] = m;
+  __syncthreads();
+  const int mp = ctl->m_prev;
+  if (mp != m) {
+    if (tid == 0) s_same = 0;
+  } else {
+    for (int r = tid; r < m; r += 1024)
+      if (d.p_node[r] != d.c_node[r] || d.p_tri[r] != d.c_tri[r]) s_same = 0;
+  }
+  __syncthreads();
+  for (int r = tid; r < m; r += 1024) { d.p_node[r] = d.c_node[r]; d.p_tri[r] = d.c_tri[r]; }
+  if (tid == 0) { ctl->same_set = s_same; ctl->m = m; ctl->m_prev = m; }
+}
+
+// ------------------------------------------------------------------ assembly
+// grid: nf blocks of 96 threads: 36 threads for D, 36 for U, 6 for g.
+__global__ void __launch_bounds__(96) assemble_kernel(Params p, Dev d) {
+  Ctl* ctl = d.ctl;
+  if (ctl->status != 0 || ctl->converged) return;
+  const int f = blockIdx.x;
+  const int nf = ctl->nf;
+  if (f >= nf) return;
+  const int node = ctl->k + 1 + f;
+  const int tid = threadIdx.x;
+  const double* eb = d.elem + (size_t)(node - 1) * kElemStride;   // element node-1: node is its b end
+  const double* ea = d.elem + (size_t)node * kElemStride;         // element node: node is its a end
+  const bool has_a = node < p.M;
+  if (tid < 36) {
+    int r = tid / 6, c = tid % 6;
+    double v = kval(eb, 6 + r, 6 + c);
+    if (has_a) v += kval(ea, r, c);
+    d.D[(size_t)f * 36 + tid] = v;
+  } else if (tid < 72) {
+    int q = tid - 36, r = q / 6, c = q % 6;
+    d.U[(size_t)f * 36 + q] = has_a ? kval(ea, r, 6 + c) : 0.0;
+  } else if (tid < 78) {
+    int c = tid - 72;
+    double F = eb[78 + 6 + c] + (has_a ? ea[78 + c] : 0.0);
+    double Fa = 0.0;
+    if (node == p.M) {
+      double T[9];
+      quat_to_mat(d.qw[node], d.qx[node], d.qy[node], d.qz[node], T);
+      double fl[3] = {0.0, 0.0, 0.0}, ml[3] = {0.0, 0.0, 0.0};
+      if (ctl->load_mode == 0) {
+        // Eq. 16-18: F_j = (-tau_j, 0, 0), d_j = r_c (0, cos phi_j, sin phi_j), M_j = d_j x F_j
+        double st = 0.0, ss = 0.0, sc = 0.0;
+        for (int j = 0; j < p.n_cables; ++j) {
+          st += ctl->tension[j];
+          ss += ctl->tension[j] * p.cable_sin[j];
+          sc += ctl->tension[j] * p.cable_cos[j];
+        }
+        fl[0] = -st; ml[1] = -p.r_c * ss; ml[2] = p.r_c * sc;
+      } else {
+        for (int a = 0; a < 3; ++a) { fl[a] = ctl->tip_f[a]; ml[a] = ctl->tip_m[a]; }
+      }
+      if (ctl->load_mode == 1) {
+        Fa = c < 3 ? fl[c] : ml[c - 3];
+      } else {
+        const double* v = c < 3 ? fl : ml;
+        int r = c % 3;
+        Fa = fma(T[3 * r], v[0], fma(T[3 * r + 1], v[1], T[3 * r + 2] * v[2]));
+      }
+    }
+    d.g[(size_t)f * 6 + c] = F - Fa;
+  }
+}
+
+// RHS columns: 0 = -g, 1 + row = A^T e_row (unit normal on the row's node translation).
+// grid (nf, ceil(nrhs_cap / 32)), block (32, 6).
+__global__ void __launch_bounds__(192) rhs_kernel(Params p, Dev d) {
+  Ctl* ctl = d.ctl;
+  if (ctl->status != 0 || ctl->converged) return;
+  const int f = blockIdx.x, c = threadIdx.y, r = blockIdx.y * 32 + threadIdx.x;
+  if (f >= ctl->nf || r > ctl->m) return;
+  double v;
+  if (r == 0) v = -d.g[(size_t)f * 6 + c];
+  else v = (d.c_node[r - 1] == f && c < 3) ? d.c_n[3 * (r - 1) + c] : 0.0;
+  d.B[((size_t)f * 6 + c) * p.nrhs_cap + r] = v;
+}
+
+// ------------------------------------------------------------------ 6x6 helpers (64-thread team)
+// In-place Gauss-Jordan inverse of the SPD matrix in sA (6x6, row-major); threads 0..35 own one
+// entry each.  Returns false (for all threads) when a pivot is not positive.
+__device__ bool team_inverse6(double* sA, int tid, double* s_piv) {
+  const int r = tid / 6, c = tid % 6;
+  for (int k = 0; k < 6; ++k) {
+    __syncthreads();
+    double akk = sA[k * 6 + k];
+    if (!(akk > 0.0)) return false;
+    double pk = 1.0 / akk;
+    double v = 0.0;
+    if (tid < 36) {
+      double aij = sA[r * 6 + c], aik = sA[r * 6 + k], akj = sA[k * 6 + c];
+      if (r == k && c == k) v = pk;
+      else if (r == k) v = akj * pk;
+      else if (c == k) v = -aik * pk;
+      else v = aij - aik * akj * pk;
+    }
+    __syncthreads();
+    if (tid < 36) sA[r * 6 + c] = v;
+  }
+  __syncthreads();
+  return true;
+}
+
+// Phase A: eliminated nodes j = s + 2 s blockIdx.x.
+__global__ void __launch_bounds__(64) bcr_elim_kernel(Params p, Dev d, int s) {
+  __shared__ double sA[36], sX[36], sY[36];
+  __shared__ double s_piv[1];
+  Ctl* ctl = d.ctl;
+  if (ctl->status != 0 || ctl->converged) return;
+  const int nf = ctl->nf;
+  const int j = s + 2 * s * blockIdx.x;
+  if (j >= nf) return;
+  const int tid = threadIdx.x;
+  if (tid < 36) sA[tid] = d.D[(size_t)j * 36 + tid];
+  bool ok = team_inverse6(sA, tid, s_piv);
+  if (!ok) {
+    if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
+    return;
+  }
+  const int r = tid / 6, c = tid % 6;
+  if (tid < 36) {
+    d.P[(size_t)j * 36 + tid] = sA[tid];
+    sX[tid] = d.U[(size_t)(j - s) * 36 + tid];                  // U_{j-s} = K_{j-s, j}
+    sY[tid] = (j + s < nf) ? d.U[(size_t)j * 36 + tid] : 0.0;   // U_j = K_{j, j+s}
+  }
+  __syncthreads();
+  if (tid < 36) {
+    double l = 0.0, rr = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      l = fma(sX[r * 6 + k], sA[k * 6 + c], l);     // (U_{j-s} P_j)[r][c]
+      rr = fma(sY[k * 6 + r], sA[k * 6 + c], rr);   // (U_j^T P_j)[r][c]
+    }
+    d.Lm[(size_t)j * 36 + tid] = l;
+    d.Rm[(size_t)j * 36 + tid] = rr;
+  }
+}
+
+// Phase B: kept nodes i = 2 s blockIdx.x.
+__global__ void __launch_bounds__(64) bcr_keep_kernel(Params p, Dev d, int s) {
+  __shared__ double sRl[36], sUl[36], sLr[36], sUi[36], sUr[36];
+  Ctl* ctl = d.ctl;
+  if (ctl->status != 0 || ctl->converged) return;
+  const int nf = ctl->nf;
+  const int i = 2 * s * blockIdx.x;
+  if (i >= nf) return;
+  const int tid = threadIdx.x;
+  const bool hl = i >= s, hr = i + s < nf, hr2 = i + 2 * s < nf;
+  if (tid < 36) {
+    sRl[tid] = hl ? d.Rm[(size_t)(i - s) * 36 + tid] : 0.0;
+    sUl[tid] = hl ? d.U[(size_t)(i - s) * 36 + tid] : 0.0;
+    sLr[tid] = hr ? d.Lm[(size_t)(i + s) * 36 + tid] : 0.0;
+    sUi[tid] = hr ? d.U[(size_t)i * 36 + tid] : 0.0;
+    sUr[tid] = hr2 ? d.U[(size_t)(i + s) * 36 + tid] : 0.0;
+  }
+  __syncthreads();
+  if (tid < 36) {
+    const int r = tid / 6, c = tid % 6;
+    double dd = d.D[(size_t)i * 36 + tid];
+    double un = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      dd = fma(-sRl[r * 6 + k], sUl[k * 6 + c], dd);
+      dd = fma(-sLr[r * 6 + k], sUi[c * 6 + k], dd);
+      un = fma(-sLr[r * 6 + k], sUr[k * 6 + c], un);
+    }
+    d.D[(size_t)i * 36 + tid] = dd;
+    if (hr) d.U[(size_t)i * 36 + tid] = hr2 ? un : 0.0;
+  }
+}
+
+// Root: P_0 = D_0^{-1}.
+__global__ void __launch_bounds__(64) bcr_root_kernel(Params p, Dev d) {
+  __shared__ double sA[36];
+  __shared__ double s_piv[1];
+  Ctl* ctl = d.ctl;
+  if (ctl->status != 0 || ctl->converged || ctl->nf == 0) return;
+  const int tid = threadIdx.x;
+  if (tid < 36) sA[tid] = d.D[tid];
+  bool ok = team_inverse6(sA, tid, s_piv);
+  if (!ok) {
+    if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
+    return;
+  }
+  if (tid < 36) d.P[tid] = sA[tid];
+}
+
+// Forward reduction at stride s for kept nodes i = 2 s blockIdx.x; block (32 rhs, 6 comps).
+__global__ void __launch_bounds__(192) bcr_fwd_kernel(Params p, Dev d, int s) {
+  Ctl* ctl = d.ctl;
+  if (ctl->status != 0 || ctl->converged) return;
+  const int nf = ctl->nf, nrhs = ctl->m + 1;
+  const int i = 2 * s * blockIdx.x;
+  const int r = blockIdx.y * 32 + threadIdx.x, c = threadIdx.y;
+  if (i >= nf || r >= nrhs) return;
+  const size_t ld = p.nrhs_cap;
+  double acc = d.B[((size_t)i * 6 + c) * ld + r];
+  if (i >= s) {
+    const double* R = d.Rm + (size_t)(i - s) * 36 + c * 6;
+    const double* b = d.B + (size_t)(i - s) * 6 * ld + r;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc = fma(-R[k], b[k * ld], acc);
+  }
+  if (i + s < nf) {
+    const double* L = d.Lm + (size_t)(i + s) * 36 + c * 6;
+    const double* b = d.B + (size_t)(i + s) * 6 * ld + r;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc = fma(-L[k], b[k * ld], acc);
+  }
+  d.B[((size_t)i * 6 + c) * ld + r] = acc;
+}
+
+// Root solve x_0 = P_0 b_0; grid (1, ceil(nrhs_cap/32)), block (32, 6).
+__global__ void __launch_bounds__(192) bcr_rootsolve_kernel(Params p, Dev d) {
+  Ctl* ctl = d.ctl;
+  if (ctl->status != 0 || ctl->converged || ctl->nf == 0) return;
+  const int nrhs = ctl->m + 1;
+  const int r = blockIdx.y * 32 + threadIdx.x, c = threadIdx.y;
+  const size_t ld = p.nrhs_cap;
+  const bool act = r < nrhs;
+  double b[6];
+  if (act)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) b[k] = d.B[(size_t)k * ld + r];
+  __syncthreads();
+  if (act) {
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc = fma(d.P[c * 6 + k], b[k], acc);
+    d.B[(size_t)c * ld + r] = acc;
+  }
+}
+
+// Back substitution at stride s for eliminated nodes j = s + 2 s blockIdx.x.
+__global__ void __launch_bounds__(192) bcr_bwd_kernel(Params p, Dev d, int s) {
+  Ctl* ctl = d.ctl;
+  if (ctl->status != 0 || ctl->converged) return;
+  const int nf = ctl->nf, nrhs = ctl->m + 1;
+  const int j = s + 2 * s * blockIdx.x;
+  if (j >= nf) return;
+  const int r = blockIdx.y * 32 + threadIdx.x, c = threadIdx.y;
+  const bool act = r < nrhs;
+  const size_t ld = p.nrhs_cap;
+  double b[6];
+  if (act)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) b[k] = d.B[((size_t)j * 6 + k) * ld + r];
+  __syncthreads();
+  if (!act) return;
+  double acc = 0.0;
+  const double* P = d.P + (size_t)j * 36 + c * 6;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) acc = fma(P[k], b[k], acc);
+  {
+    const double* L = d.Lm + (size_t)j * 36;   // -L_j^T x_{j-s}: (L^T)[c][k] = L[k][c]
+    const double* x = d.B + (size_t)(j - s) * 6 * ld + r;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc = fma(-L[k * 6 + c], x[k * ld], acc);
+  }
+  if (j + s < nf) {
+    const double* R = d.Rm + (size_t)j * 36;
+    const double* x = d.B + (size_t)(j + s) * 6 * ld + r;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc = fma(-R[k * 6 + c], x[k * ld], acc);
+  }
+  d.B[((size_t)j * 6 + c) * ld + r] = acc;
+}
+
+}  // namespace accfem

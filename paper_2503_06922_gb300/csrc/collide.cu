@@ -1,0 +1,234 @@
+// Robot-node vs lumen-triangle collision detection (Eq. 3-10; Sec. III.C: nodes are matched
+// with the triangles in parallel and each match yields its constraint).  One warp per free node.
+//
+// Constraint rule (identical to an all-pairs FP64 scan): with c_t the closest point of triangle
+// t to the node p, d_t = |c_t - p| and g the triangle of smallest d_t (lowest index on ties),
+// (node, t) is a constraint row when d_t <= r_o + activation_gap and c_t is locally closest:
+// interior to t's face (plane projection inside, edges included), or t == g (edge/vertex point).
+// Rows with the same closest point (within 1e-12 m) are merged, keeping the lowest index.
+//
+// Work split: triangles are binned by centroid in a uniform grid; a node scans the cells of the
+// box p +- (r_o + gap + max triangle radius).  Pass 1 computes FP32 distances (coordinates
+// relative to the cell centre, so |x| is a few mm and the FP32 error a few 1e-9 m) and their
+// warp minimum; pass 2 keeps a triangle for the exact FP64 test when its FP32 distance is within
+// eps_d of the activation distance AND (its FP32 barycentrics are inside up to eps_b, or its
+// FP32 distance is within 2 eps_d of the minimum).  Every triangle that can form a row in FP64
+// passes, so the FP64 decisions below see the same candidates as a full scan.
+#include "common.cuh"
+
+namespace accfem {
+
+// FP32 squared distance from p to triangle (a, b, c) and the unnormalised barycentrics of the
+// plane projection (va, vb, vc) with va + vb + vc = |ab x ac|^2.
+__device__ __forceinline__ float tri_dist2_f32(const float* p, const float* t, float& va, float& vb, float& vc) {
+  float ab[3] = {t[3] - t[0], t[4] - t[1], t[5] - t[2]};
+  float ac[3] = {t[6] - t[0], t[7] - t[1], t[8] - t[2]};
+  float ap[3] = {p[0] - t[0], p[1] - t[1], p[2] - t[2]};
+  float d1 = ab[0] * ap[0] + ab[1] * ap[1] + ab[2] * ap[2];
+  float d2 = ac[0] * ap[0] + ac[1] * ap[1] + ac[2] * ap[2];
+  float bp[3] = {ap[0] - ab[0], ap[1] - ab[1], ap[2] - ab[2]};
+  float d3 = ab[0] * bp[0] + ab[1] * bp[1] + ab[2] * bp[2];
+  float d4 = ac[0] * bp[0] + ac[1] * bp[1] + ac[2] * bp[2];
+  float cp[3] = {ap[0] - ac[0], ap[1] - ac[1], ap[2] - ac[2]};
+  float d5 = ab[0] * cp[0] + ab[1] * cp[1] + ab[2] * cp[2];
+  float d6 = ac[0] * cp[0] + ac[1] * cp[1] + ac[2] * cp[2];
+  va = d3 * d6 - d5 * d4;
+  vb = d5 * d2 - d1 * d6;
+  vc = d1 * d4 - d3 * d2;
+  float q[3];
+  if (d1 <= 0.f && d2 <= 0.f) { q[0] = 0.f; q[1] = 0.f; q[2] = 0.f; }
+  else if (d3 >= 0.f && d4 <= d3) { q[0] = ab[0]; q[1] = ab[1]; q[2] = ab[2]; }
+  else if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
+    float v = d1 / (d1 - d3); q[0] = v * ab[0]; q[1] = v * ab[1]; q[2] = v * ab[2];
+  } else if (d6 >= 0.f && d5 <= d6) { q[0] = ac[0]; q[1] = ac[1]; q[2] = ac[2]; }
+  else if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
+    float w = d2 / (d2 - d6); q[0] = w * ac[0]; q[1] = w * ac[1]; q[2] = w * ac[2];
+  } else if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
+    float w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+    q[0] = ab[0] + w * (ac[0] - ab[0]); q[1] = ab[1] + w * (ac[1] - ab[1]); q[2] = ab[2] + w * (ac[2] - ab[2]);
+  } else {
+    float den = 1.f / (va + vb + vc);
+    float v = vb * den, w = vc * den;
+    q[0] = v * ab[0] + w * ac[0]; q[1] = v * ab[1] + w * ac[1]; q[2] = v * ab[2] + w * ac[2];
+  }
+  float r[3] = {ap[0] - q[0], ap[1] - q[1], ap[2] - q[2]};
+  return r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+}
+
+// FP64 closest point of triangle (A, B, C) to p (the Voronoi-region method of Ericson, Real-Time
+// Collision Detection, 2005, Sec. 5.1.5), with "interior" = all three unnormalised barycentrics of
+// the plane projection >= 0.  Returns the closest point in c (absolute), |c - p|^2, interior flag.
+__device__ double tri_closest_f64(const double* p, const double* A, const double* B, const double* C,
+                                  double* c, int* interior) {
+  double ab[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+  double ac[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+  double ap[3] = {p[0] - A[0], p[1] - A[1], p[2] - A[2]};
+  double bp[3] = {ap[0] - ab[0], ap[1] - ab[1], ap[2] - ab[2]};
+  double cp[3] = {ap[0] - ac[0], ap[1] - ac[1], ap[2] - ac[2]};
+  double d1 = dot3(ab, ap), d2 = dot3(ac, ap), d3 = dot3(ab, bp), d4 = dot3(ac, bp), d5 = dot3(ab, cp),
+         d6 = dot3(ac, cp);
+  double va = d3 * d6 - d5 * d4, vb = d5 * d2 - d1 * d6, vc = d1 * d4 - d3 * d2;
+  double q[3];
+  *interior = 0;
+  if (va >= 0.0 && vb >= 0.0 && vc >= 0.0) {
+    *interior = 1;
+    double den = 1.0 / (va + vb + vc);
+    double v = vb * den, w = vc * den;
+    q[0] = v * ab[0] + w * ac[0]; q[1] = v * ab[1] + w * ac[1]; q[2] = v * ab[2] + w * ac[2];
+  } else if (d1 <= 0.0 && d2 <= 0.0) { q[0] = 0.0; q[1] = 0.0; q[2] = 0.0; }
+  else if (d3 >= 0.0 && d4 <= d3) { q[0] = ab[0]; q[1] = ab[1]; q[2] = ab[2]; }
+  else if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {
+    double v = d1 / (d1 - d3); q[0] = v * ab[0]; q[1] = v * ab[1]; q[2] = v * ab[2];
+  } else if (d6 >= 0.0 && d5 <= d6) { q[0] = ac[0]; q[1] = ac[1]; q[2] = ac[2]; }
+  else if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
+    double w = d2 / (d2 - d6); q[0] = w * ac[0]; q[1] = w * ac[1]; q[2] = w * ac[2];
+  } else {
+    double den = (d4 - d3) + (d5 - d6);
+    double w = den > 0.0 ? (d4 - d3) / den : 0.0;
+    q[0] = ab[0] + w * (ac[0] - ab[0]); q[1] = ab[1] + w * (ac[1] - ab[1]); q[2] = ab[2] + w * (ac[2] - ab[2]);
+  }
+  double r[3] = {ap[0] - q[0], ap[1] - q[1], ap[2] - q[2]};
+  c[0] = A[0] + q[0]; c[1] = A[1] + q[1]; c[2] = A[2] + q[2];
+  return dot3(r, r);
+}
+
+struct Surv {
+  int t;
+  int interior;
+  double d2;
+  double c[3];
+};
+
+__global__ void __launch_bounds__(128) collide_kernel(Params p, Dev d) {
+  __shared__ Surv s_surv[4][kSurvCap];
+  __shared__ int s_ns[4];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  Ctl* ctl = d.ctl;
+  const int f = blockIdx.x * 4 + wib;
+  if (ctl->status != 0 || ctl->converged || f >= ctl->nf) return;
+  const int node = ctl->k + 1 + f;
+  if (lane == 0) s_ns[wib] = 0;
+  __syncwarp();
+  const double pn[3] = {d.px[node], d.py[node], d.pz[node]};
+  const double thr = p.r_o + p.act;
+  int lo[3], hi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = (int)floor((pn[a] - p.g_rq - p.g_org[a]) / p.g_h);
+    hi[a] = (int)floor((pn[a] + p.g_rq - p.g_org[a]) / p.g_h);
+    lo[a] = max(lo[a], 0); hi[a] = min(hi[a], p.g_dim[a] - 1);
+  }
+  const float thr32 = (float)(thr + p.eps_d);
+  // ---- pass 1: FP32 minimum distance over the candidates
+  float dmin = 3.0e38f;
+  for (int cz = lo[2]; cz <= hi[2]; ++cz)
+    for (int cy = lo[1]; cy <= hi[1]; ++cy)
+      for (int cx = lo[0]; cx <= hi[0]; ++cx) {
+        int cell = (cz * p.g_dim[1] + cy) * p.g_dim[0] + cx;
+        int s0 = d.cell_start[cell], s1 = d.cell_start[cell + 1];
+        if (s0 == s1) continue;
+        float pc[3] = {(float)(pn[0] - (p.g_org[0] + (cx + 0.5) * p.g_h)),
+                       (float)(pn[1] - (p.g_org[1] + (cy + 0.5) * p.g_h)),
+                       (float)(pn[2] - (p.g_org[2] + (cz + 0.5) * p.g_h))};
+        for (int s = s0 + lane; s < s1; s += 32) {
+          float va, vb, vc;
+          float d2 = tri_dist2_f32(pc, d.tri32 + (size_t)s * 9, va, vb, vc);
+          dmin = fminf(dmin, sqrtf(d2));
+        }
+      }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+  const float dmin_keep = dmin + (float)(2.0 * p.eps_d);
+  // ---- pass 2: survivors -> exact FP64 closest points
+  for (int cz = lo[2]; cz <= hi[2]; ++cz)
+    for (int cy = lo[1]; cy <= hi[1]; ++cy)
+      for (int cx = lo[0]; cx <= hi[0]; ++cx) {
+        int cell = (cz * p.g_dim[1] + cy) * p.g_dim[0] + cx;
+        int s0 = d.cell_start[cell], s1 = d.cell_start[cell + 1];
+        if (s0 == s1) continue;
+        float pc[3] = {(float)(pn[0] - (p.g_org[0] + (cx + 0.5) * p.g_h)),
+                       (float)(pn[1] - (p.g_org[1] + (cy + 0.5) * p.g_h)),
+                       (float)(pn[2] - (p.g_org[2] + (cz + 0.5) * p.g_h))};
+        for (int s0l = s0; s0l < s1; s0l += 32) {
+          int s = s0l + lane;
+          bool keep = false;
+          if (s < s1) {
+            float va, vb, vc;
+            float dd = sqrtf(tri_dist2_f32(pc, d.tri32 + (size_t)s * 9, va, vb, vc));
+            float den = va + vb + vc;
+            float tol = -p.eps_b * den;
+            bool near_in = (va >= tol) && (vb >= tol) && (vc >= tol);
+            keep = (dd <= thr32) && (near_in || dd <= dmin_keep);
+          }
+          if (keep) {
+            int t = d.cell_tri[s];
+            const int* tv = d.T + 3 * (size_t)t;
+            double A[3] = {d.V[3 * tv[0]], d.V[3 * tv[0] + 1], d.V[3 * tv[0] + 2]};
+            double Bv[3] = {d.V[3 * tv[1]], d.V[3 * tv[1] + 1], d.V[3 * tv[1] + 2]};
+            double Cv[3] = {d.V[3 * tv[2]], d.V[3 * tv[2] + 1], d.V[3 * tv[2] + 2]};
+            Surv sv;
+            sv.t = t;
+            sv.d2 = tri_closest_f64(pn, A, Bv, Cv, sv.c, &sv.interior);
+            int slot = atomicAdd(&s_ns[wib], 1);
+            if (slot < kSurvCap) s_surv[wib][slot] = sv;
+          }
+        }
+      }
+  __syncwarp();
+  const int ns = s_ns[wib];
+  if (ns > kSurvCap) {
+    if (lane == 0) atomicCAS(&ctl->status, 0, ST_CAPACITY);
+    return;
+  }
+  // ---- lane 0: global argmin, rows, merge, order by triangle index
+  if (lane == 0) {
+    int g = -1;
+    double gd = 0.0;
+    for (int i = 0; i < ns; ++i) {
+      const Surv& sv = s_surv[wib][i];
+      if (g < 0 || sv.d2 < gd || (sv.d2 == gd && sv.t < s_surv[wib][g].t)) { g = i; gd = sv.d2; }
+    }
+    // insertion sort survivors by triangle index
+    int ord[kSurvCap];
+    for (int i = 0; i < ns; ++i) {
+      int j = i;
+      while (j > 0 && s_surv[wib][ord[j - 1]].t > s_surv[wib][i].t) { ord[j] = ord[j - 1]; --j; }
+      ord[j] = i;
+    }
+    int nc = 0;
+    int* ctri = d.con_tri + (size_t)f * kCpn;
+    double* cpt = d.con_pt + (size_t)f * kCpn * 3;
+    double* cn = d.con_n + (size_t)f * kCpn * 3;
+    double* cg = d.con_gap + (size_t)f * kCpn;
+    for (int oi = 0; oi < ns; ++oi) {
+      const Surv& sv = s_surv[wib][ord[oi]];
+      double dist = sqrt(sv.d2);
+      if (!(dist <= thr)) continue;
+      if (!(sv.interior || ord[oi] == g)) continue;
+      bool dup = false;
+      for (int r = 0; r < nc; ++r) {
+        double dx = cpt[3 * r] - sv.c[0], dy = cpt[3 * r + 1] - sv.c[1], dz = cpt[3 * r + 2] - sv.c[2];
+        if (sqrt(dx * dx + dy * dy + dz * dz) <= 1e-12) { dup = true; break; }
+      }
+      if (dup) continue;
+      if (nc >= kCpn) { atomicCAS(&ctl->status, 0, ST_CAPACITY); break; }
+      const double* nf = d.nface + 3 * (size_t)sv.t;
+      double n[3];
+      double cmp[3] = {sv.c[0] - pn[0], sv.c[1] - pn[1], sv.c[2] - pn[2]};
+      if (sv.interior || dist < 1e-12) { n[0] = nf[0]; n[1] = nf[1]; n[2] = nf[2]; }
+      else {
+        double sgn = (dot3(nf, cmp) > 0.0) ? 1.0 : -1.0;
+        double id = sgn / dist;
+        n[0] = cmp[0] * id; n[1] = cmp[1] * id; n[2] = cmp[2] * id;
+      }
+      ctri[nc] = sv.t;
+      cpt[3 * nc] = sv.c[0]; cpt[3 * nc + 1] = sv.c[1]; cpt[3 * nc + 2] = sv.c[2];
+      cn[3 * nc] = n[0]; cn[3 * nc + 1] = n[1]; cn[3 * nc + 2] = n[2];
+      cg[nc] = dot3(n, sv.c) - dot3(n, pn) - p.r_o;
+      ++nc;
+    }
+    d.ncon[f] = nc;
+  }
+}
+
+}  // namespace accfem

@@ -1,0 +1,172 @@
+// Corotational beam element: internal force and material tangent (Sec. II.B, Eq. 20; the
+// element-level parallel update of Sec. III.C).  One warp per element.
+//
+// Element e joins nodes a = e and b = e + 1.  Rigid frame R_r = [e1 e2 e3]: e1 along the chord,
+// e3 normal to e1 and the mean q of the nodal second section axes.  Local deformations
+// d_l = [l - l0, log(R_r^T T_a), log(R_r^T T_b)], constant local stiffness K_l (EA/l0, GJ/l0,
+// EI/l0 [[4 2][2 4]] per bending plane).  With B = dd_l/dd (spatial spins, local components):
+//   F = E B^T K_l d_l,   K = E B^T K_l B E^T,   E = blockdiag(R_r, R_r, R_r, R_r).
+// Output record (doubles): [0, 78) upper triangle of K row-major, [78, 90) F = [F_a M_a F_b M_b].
+#include "common.cuh"
+
+namespace accfem {
+
+__constant__ unsigned char c_up_i[78];
+__constant__ unsigned char c_up_j[78];
+
+__global__ void __launch_bounds__(32 * kWarpsPerElemBlock)
+element_kernel(Params p, Dev d) {
+  __shared__ double sB[kWarpsPerElemBlock][7][12];   // B (local), then B E^T (global comps)
+  __shared__ double sH[kWarpsPerElemBlock][7][12];   // K_l B E^T
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  Ctl* ctl = d.ctl;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {         // reset the per-iteration reductions
+    ctl->umax_bits = 0ull; ctl->step_bits = 0ull; ctl->res_bits = 0ull;
+  }
+  const int e = ctl->k + blockIdx.x * kWarpsPerElemBlock + wib;
+  if (e >= p.M || ctl->status != 0 || ctl->converged) return;
+  const int a = e, b = e + 1;
+
+  // ---- scalar prelude (every lane: a warp FP64 instruction costs the same with 1 or 32 lanes)
+  double xa[3] = {d.px[a], d.py[a], d.pz[a]};
+  double xb[3] = {d.px[b], d.py[b], d.pz[b]};
+  double Ta[9], Tb[9];
+  quat_to_mat(d.qw[a], d.qx[a], d.qy[a], d.qz[a], Ta);
+  quat_to_mat(d.qw[b], d.qx[b], d.qy[b], d.qz[b], Tb);
+  double dv[3] = {xb[0] - xa[0], xb[1] - xa[1], xb[2] - xa[2]};
+  double l2 = dot3(dv, dv);
+  double l = sqrt(l2);
+  double il = 1.0 / l;
+  double e1[3] = {dv[0] * il, dv[1] * il, dv[2] * il};
+  double qv[3] = {0.5 * (Ta[1] + Tb[1]), 0.5 * (Ta[4] + Tb[4]), 0.5 * (Ta[7] + Tb[7])};
+  double v3[3];
+  cross3(e1, qv, v3);
+  double iv = rsqrt(dot3(v3, v3));
+  double e3[3] = {v3[0] * iv, v3[1] * iv, v3[2] * iv};
+  double e2[3];
+  cross3(e3, e1, e2);
+  // Rr row-major: Rr[r][c], columns e1 e2 e3
+  double Rr[9] = {e1[0], e2[0], e3[0], e1[1], e2[1], e3[1], e1[2], e2[2], e3[2]};
+  double Ra[9], Rb[9];   // R_r^T T
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Ra[3 * i + j] = fma(Rr[i], Ta[j], fma(Rr[3 + i], Ta[3 + j], Rr[6 + i] * Ta[6 + j]));
+      Rb[3 * i + j] = fma(Rr[i], Tb[j], fma(Rr[3 + i], Tb[3 + j], Rr[6 + i] * Tb[6 + j]));
+    }
+  double tha[3], thb[3];
+  rotvec_of_mat(Ra, tha);
+  rotvec_of_mat(Rb, thb);
+  double Tia[9], Tib[9];
+  tsinv_mat(tha, Tia);
+  tsinv_mat(thb, Tib);
+  const double u = (l2 - p.l0 * p.l0) / (l + p.l0);
+  const double qb1 = dot3(e1, qv), qb2 = dot3(e2, qv);   // local components of q (third is 0)
+  const double iq2 = 1.0 / qb2;
+  // local force vector f_l = K_l d_l
+  const double ka = p.EA / p.l0, kt = p.GJ / p.l0, kb = p.EI / p.l0;
+  double fl[7];
+  fl[0] = ka * u;
+  fl[1] = kt * (tha[0] - thb[0]);
+  fl[2] = kb * (4.0 * tha[1] + 2.0 * thb[1]);
+  fl[3] = kb * (4.0 * tha[2] + 2.0 * thb[2]);
+  fl[4] = -fl[1];
+  fl[5] = kb * (2.0 * tha[1] + 4.0 * thb[1]);
+  fl[6] = kb * (2.0 * tha[2] + 4.0 * thb[2]);
+
+  // ---- column j of B (local components): lanes 0..11
+  if (lane < 12) {
+    const int j = lane;
+    // G^T column j: spin of the rigid frame per unit local variation j
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    if (j == 2) { g0 = qb1 * iq2 * il; g1 = il; }
+    else if (j == 8) { g0 = -qb1 * iq2 * il; g1 = -il; }
+    else if (j == 1) { g2 = -il; }
+    else if (j == 7) { g2 = il; }
+    else if (j == 3) { g0 = 0.5 * Ra[4] * iq2; }     // qa_bar = column 1 of Ra: (Ra[1], Ra[4], Ra[7])
+    else if (j == 4) { g0 = -0.5 * Ra[1] * iq2; }
+    else if (j == 9) { g0 = 0.5 * Rb[4] * iq2; }
+    else if (j == 10) { g0 = -0.5 * Rb[1] * iq2; }
+    double ca0 = -g0, ca1 = -g1, ca2 = -g2;   // (E_a - G^T) column j
+    double cb0 = -g0, cb1 = -g1, cb2 = -g2;   // (E_b - G^T) column j
+    if (j >= 3 && j < 6) { if (j == 3) ca0 += 1.0; else if (j == 4) ca1 += 1.0; else ca2 += 1.0; }
+    if (j >= 9) { if (j == 9) cb0 += 1.0; else if (j == 10) cb1 += 1.0; else cb2 += 1.0; }
+    sB[wib][0][j] = (j == 0) ? -1.0 : ((j == 6) ? 1.0 : 0.0);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      sB[wib][1 + r][j] = fma(Tia[3 * r], ca0, fma(Tia[3 * r + 1], ca1, Tia[3 * r + 2] * ca2));
+      sB[wib][4 + r][j] = fma(Tib[3 * r], cb0, fma(Tib[3 * r + 1], cb1, Tib[3 * r + 2] * cb2));
+    }
+  }
+  __syncwarp();
+  // ---- B E^T: global components, entries idx = lane + 32 t < 84
+  double bg[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    int idx = lane + 32 * t;
+    bg[t] = 0.0;
+    if (idx < 84) {
+      int k = idx / 12, col = idx % 12, s = col / 3, c = col % 3;
+      bg[t] = fma(sB[wib][k][3 * s], Rr[3 * c], fma(sB[wib][k][3 * s + 1], Rr[3 * c + 1], sB[wib][k][3 * s + 2] * Rr[3 * c + 2]));
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    int idx = lane + 32 * t;
+    if (idx < 84) sB[wib][idx / 12][idx % 12] = bg[t];
+  }
+  __syncwarp();
+  // ---- H = K_l (B E^T)
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    int idx = lane + 32 * t;
+    if (idx < 84) {
+      int k = idx / 12, col = idx % 12;
+      double h;
+      switch (k) {
+        case 0: h = ka * sB[wib][0][col]; break;
+        case 1: h = kt * (sB[wib][1][col] - sB[wib][4][col]); break;
+        case 4: h = kt * (sB[wib][4][col] - sB[wib][1][col]); break;
+        case 2: h = kb * fma(4.0, sB[wib][2][col], 2.0 * sB[wib][5][col]); break;
+        case 5: h = kb * fma(2.0, sB[wib][2][col], 4.0 * sB[wib][5][col]); break;
+        case 3: h = kb * fma(4.0, sB[wib][3][col], 2.0 * sB[wib][6][col]); break;
+        default: h = kb * fma(2.0, sB[wib][3][col], 4.0 * sB[wib][6][col]); break;
+      }
+      sH[wib][k][col] = h;
+    }
+  }
+  __syncwarp();
+  // ---- K (upper triangle) and F
+  double* out = d.elem + (size_t)e * kElemStride;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    int idx = lane + 32 * t;
+    if (idx < 78) {
+      int i = c_up_i[idx], j = c_up_j[idx];
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) s = fma(sB[wib][k][i], sH[wib][k][j], s);
+      out[idx] = s;
+    }
+  }
+  if (lane < 12) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) s = fma(sB[wib][k][lane], fl[k], s);
+    out[78 + lane] = s;
+  }
+}
+
+void upload_element_tables() {
+  unsigned char ui[78], uj[78];
+  int n = 0;
+  for (int i = 0; i < 12; ++i)
+    for (int j = i; j < 12; ++j) { ui[n] = (unsigned char)i; uj[n] = (unsigned char)j; ++n; }
+  cudaMemcpyToSymbol(c_up_i, ui, sizeof(ui));
+  cudaMemcpyToSymbol(c_up_j, uj, sizeof(uj));
+}
+
+}  // namespace accfem

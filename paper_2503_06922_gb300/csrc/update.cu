@@ -1,0 +1,134 @@
+// Newton update with the step limiter (Eq. 25-27), convergence test, and the start pose of a
+// solve (prescribed feed, Eq. 14-15; warm start from the resident pose).
+#include "common.cuh"
+
+namespace accfem {
+
+// dx = dx_free - X y over the active rows; per-node maxima of |du|, max(|du|, r_o |dtheta|) and
+// of the residual g + A^T y.  Block: 32 nodes x 6 components.
+__global__ void __launch_bounds__(192) step_kernel(Params p, Dev d) {
+  __shared__ double s_dx[32][6];
+  __shared__ double s_r[32][6];
+  Ctl* ctl = d.ctl;
+  if (ctl->status != 0 || ctl->converged) return;
+  const int nf = ctl->nf;
+  const int fl = threadIdx.x, c = threadIdx.y;
+  const int f = blockIdx.x * 32 + fl;
+  const bool act = f < nf;
+  const size_t ld = p.nrhs_cap;
+  if (act) {
+    double v = d.B[((size_t)f * 6 + c) * ld];
+    const int na = ctl->n_active;
+    for (int a = 0; a < na; ++a) {
+      int j = d.plist[a];
+      v = fma(-d.B[((size_t)f * 6 + c) * ld + 1 + j], d.y[j], v);
+    }
+    s_dx[fl][c] = v;
+    d.dx[(size_t)f * 6 + c] = v;
+    double r = d.g[(size_t)f * 6 + c];
+    if (c < 3) {
+      for (int row = d.c_first[f]; row < d.c_first[f + 1]; ++row) r = fma(d.c_n[3 * row + c], d.y[row], r);
+    }
+    s_r[fl][c] = fabs(r);
+  }
+  __syncthreads();
+  if (act && c == 0) {
+    double du = sqrt(s_dx[fl][0] * s_dx[fl][0] + s_dx[fl][1] * s_dx[fl][1] + s_dx[fl][2] * s_dx[fl][2]);
+    double dt = sqrt(s_dx[fl][3] * s_dx[fl][3] + s_dx[fl][4] * s_dx[fl][4] + s_dx[fl][5] * s_dx[fl][5]);
+    double st = fmax(du, p.r_o * dt);
+    double rr = fmax(fmax(fmax(s_r[fl][0], s_r[fl][1]), fmax(s_r[fl][2], s_r[fl][3])), fmax(s_r[fl][4], s_r[fl][5]));
+    atomicMax(&ctl->umax_bits, dbits(du));
+    atomicMax(&ctl->step_bits, dbits(st));
+    atomicMax(&ctl->res_bits, dbits(rr));
+  }
+}
+
+// x <- x + alpha du, T <- exp([alpha dtheta]x) T, alpha = min(1, beta0 / max |du|).
+__global__ void __launch_bounds__(128) apply_kernel(Params p, Dev d) {
+  Ctl* ctl = d.ctl;
+  if (ctl->status != 0 || ctl->converged) return;
+  const int nf = ctl->nf;
+  const double umax = __longlong_as_double((long long)ctl->umax_bits);
+  const double alpha = umax <= p.beta0 ? 1.0 : p.beta0 / umax;
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f < nf) {
+    const int node = ctl->k + 1 + f;
+    const double* dx = d.dx + (size_t)f * 6;
+    d.px[node] += alpha * dx[0];
+    d.py[node] += alpha * dx[1];
+    d.pz[node] += alpha * dx[2];
+    double th[3] = {alpha * dx[3], alpha * dx[4], alpha * dx[5]};
+    double dq[4], q[4] = {d.qw[node], d.qx[node], d.qy[node], d.qz[node]}, r[4];
+    quat_exp(th, dq);
+    quat_mul(dq, q, r);
+    double in = rsqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+    if (r[0] < 0.0) in = -in;
+    d.qw[node] = r[0] * in; d.qx[node] = r[1] * in; d.qy[node] = r[2] * in; d.qz[node] = r[3] * in;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const double step = __longlong_as_double((long long)ctl->step_bits);
+    ctl->alpha = alpha;
+    ctl->iter += 1;
+    if (alpha == 1.0 && step <= p.tol && ctl->same_set) ctl->converged = 1;
+  }
+}
+
+// Start pose of a solve.  mode 0: straight on the entrance axis; mode 1: follow the path of the
+// previous pose (material point s takes the old pose of material point s + (delta - delta_old):
+// linear in x, geodesic in the rotation between nodes, straight along the tip axis beyond the
+// old tip); mode 2: poses already uploaded.  Nodes i <= k are then clamped on the axis.
+__global__ void __launch_bounds__(128) start_kernel(Params p, Dev d, int mode, double delta, double delta_old, int k) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.N) return;
+  const double* dir = p.E0;    // column 0 of E0: (E0[0], E0[3], E0[6])
+  double x[3], q[4];
+  if (mode == 1) {
+    const double s = i * p.l0 + (delta - delta_old);
+    if (s >= p.L) {
+      const int t = p.M;
+      double T[9];
+      quat_to_mat(d.ow[t], d.oqx[t], d.oqy[t], d.oqz[t], T);
+      double e = s - p.L;
+      x[0] = d.ox[t] + e * T[0]; x[1] = d.oy[t] + e * T[3]; x[2] = d.oz[t] + e * T[6];
+      q[0] = d.ow[t]; q[1] = d.oqx[t]; q[2] = d.oqy[t]; q[3] = d.oqz[t];
+    } else if (s <= 0.0) {
+      double T[9];
+      quat_to_mat(d.ow[0], d.oqx[0], d.oqy[0], d.oqz[0], T);
+      x[0] = d.ox[0] + s * T[0]; x[1] = d.oy[0] + s * T[3]; x[2] = d.oz[0] + s * T[6];
+      q[0] = d.ow[0]; q[1] = d.oqx[0]; q[2] = d.oqy[0]; q[3] = d.oqz[0];
+    } else {
+      int j = (int)floor(s / p.l0);
+      if (j > p.M - 1) j = p.M - 1;
+      const double f = (s - j * p.l0) / p.l0;
+      x[0] = (1.0 - f) * d.ox[j] + f * d.ox[j + 1];
+      x[1] = (1.0 - f) * d.oy[j] + f * d.oy[j + 1];
+      x[2] = (1.0 - f) * d.oz[j] + f * d.oz[j + 1];
+      double qa[4] = {d.ow[j], d.oqx[j], d.oqy[j], d.oqz[j]};
+      double qb[4] = {d.ow[j + 1], d.oqx[j + 1], d.oqy[j + 1], d.oqz[j + 1]};
+      double qai[4] = {qa[0], -qa[1], -qa[2], -qa[3]}, rel[4], th[3], dq[4];
+      quat_mul(qai, qb, rel);               // body-frame relative rotation
+      quat_log(rel, th);
+      th[0] *= f; th[1] *= f; th[2] *= f;
+      quat_exp(th, dq);
+      quat_mul(qa, dq, q);
+    }
+  } else if (mode == 0) {
+    double s = (i * p.l0 - p.L) + delta;
+    x[0] = p.e[0] + s * dir[0]; x[1] = p.e[1] + s * dir[3]; x[2] = p.e[2] + s * dir[6];
+    q[0] = p.q0[0]; q[1] = p.q0[1]; q[2] = p.q0[2]; q[3] = p.q0[3];
+  } else {
+    x[0] = d.px[i]; x[1] = d.py[i]; x[2] = d.pz[i];
+    q[0] = d.qw[i]; q[1] = d.qx[i]; q[2] = d.qy[i]; q[3] = d.qz[i];
+  }
+  if (i <= k) {
+    double s = (i * p.l0 - p.L) + delta;
+    x[0] = p.e[0] + s * dir[0]; x[1] = p.e[1] + s * dir[3]; x[2] = p.e[2] + s * dir[6];
+    q[0] = p.q0[0]; q[1] = p.q0[1]; q[2] = p.q0[2]; q[3] = p.q0[3];
+  }
+  double in = rsqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  if (q[0] < 0.0) in = -in;
+  d.px[i] = x[0]; d.py[i] = x[1]; d.pz[i] = x[2];
+  d.qw[i] = q[0] * in; d.qx[i] = q[1] * in; d.qy[i] = q[2] * in; d.qz[i] = q[3] * in;
+}
+
+}  // namespace accfem
