@@ -11,7 +11,9 @@ One call of ``Model.solve`` is one quasi-static step at a given cable tension an
     base, F_j = (-tau_j, 0, 0) and d_j = r_c (0, cos phi_j, sin phi_j) in the tip frame; the
     tip receives T_M F_j and T_M (d_j x F_j), evaluated at the current iterate (follower load).
   * Newton step (Eq. 20-23): K(x) and F(x) at the current iterate, contact set and A_c, b_c
-    at the current iterate (Eq. 8-10), QP of Eq. 23 solved exactly through its LCP.
+    at the current iterate (Eq. 8-10), QP of Eq. 23 solved exactly through its LCP, whose
+    matrix W = A K^-1 A^T carries the compliance 1e-12 max(diag W) on its diagonal (rows of
+    one node are dependent where four or more wall faces meet).
   * step limiter (Eq. 25-27): alpha = min(1, beta0 / max_i |du_i|) scales the whole step and
     the multipliers; translations add, rotations update as T <- exp([alpha dtheta]x) T.
   * convergence: unlimited step (alpha = 1) with max_i max(|du_i|, r_o |dtheta_i|) <= tol and
@@ -28,6 +30,8 @@ import scipy.linalg as sla
 
 from . import beam, contact, lcp
 from .rotation import expm, logm, to_quat
+
+CONTACT_COMPLIANCE = 1e-12
 
 OK, E_INVALID_ARG, E_NOMEM, E_CUDA, E_NOT_CONVERGED, E_CONTACT_CAPACITY, E_NOT_SPD, E_TIMEOUT, E_PENETRATION = range(9)
 
@@ -222,6 +226,10 @@ class Model:
                     b[i] = rec["gap"]
                 X = solve(A.T)
                 W = A @ X
+                # rows of one node can be linearly dependent (four or more wall faces meeting at a
+                # mesh vertex), which leaves W singular; a contact compliance eps = 1e-12 max W_ii
+                # makes the LCP uniquely solvable (interpenetration at most eps * y)
+                W = W + CONTACT_COMPLIANCE * np.max(np.diag(W)) * np.eye(m)
                 q = b - A @ dxf
                 y, w, piv = lcp.murty(W, q)
                 piv_total += piv

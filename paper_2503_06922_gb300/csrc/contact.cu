@@ -4,7 +4,8 @@
 // dx = dx_free - X y where y >= 0 solves the LCP
 //     w = W y + q >= 0,  y >= 0,  y^T w = 0,     W = A X,  q = b - A dx_free,
 // w being the slack b - A dx of Eq. 8 and y the contact forces of Eq. 11-12.  W is symmetric
-// positive definite (one row per locally closest wall feature, K SPD), so the solution is unique.
+// positive semi-definite; with the contact compliance 1e-12 max(diag W) added to its diagonal it is
+// positive definite, so the solution is unique.
 // It is found exactly by principal pivoting: from the guess P = {q_i < 0}, solve W_PP y_P = -q_P
 // in FP64 (Gauss-Jordan over the whole CTA), test the complementary variables, flip every
 // infeasible index (block pivoting, Judice-Pires); when the count of infeasible indices stops
@@ -68,7 +69,7 @@ __device__ __forceinline__ int block_min_int(int v, int* s_ired) {
 __global__ void __launch_bounds__(1024) contact_kernel(Params p, Dev d) {
   __shared__ double s_red[33];
   __shared__ int s_ired[33];
-  __shared__ int s_np, s_bad;
+  __shared__ int s_np;
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
   const int m = ctl->m;
@@ -97,6 +98,13 @@ __global__ void __launch_bounds__(1024) contact_kernel(Params p, Dev d) {
     d.q[i] = d.c_gap[i] - s;
     d.inP[i] = d.q[i] < 0.0 ? 1 : 0;
   }
+  __syncthreads();
+  // contact compliance eps = 1e-12 max_i W_ii on the diagonal: rows of one node are linearly
+  // dependent where four or more wall faces meet, which leaves W singular without it
+  double wd = 0.0;
+  for (int i = tid; i < m; i += nt) wd = fmax(wd, d.W[(size_t)i * m + i]);
+  wd = block_max(wd, s_red);
+  for (int i = tid; i < m; i += nt) d.W[(size_t)i * m + i] += 1e-12 * wd;
   __syncthreads();
   double qmax = 0.0;
   for (int i = tid; i < m; i += nt) qmax = fmax(qmax, fabs(d.q[i]));

@@ -1,9 +1,9 @@
 """GPU path (through the C ABI) vs the CPU FP64 oracle on the same seeded inputs.
 
 Tolerances: nodal positions 1e-9 relative (the parity target of the path), contact rows identical
-as (node, closest point) apart from rows within 1e-9 m of the activation distance, contact forces
-1e-6 relative to the largest force (the force is the multiplier of an LCP whose matrix conditioning
-amplifies rounding by up to ~1e3 here)."""
+as (node, closest point) apart from rows within 1e-9 m of the activation distance, net contact force
+per node (sum of y_i n_i) 1e-6 relative to the largest one (the multipliers solve an LCP whose
+conditioning amplifies rounding; the per-node net force is unique even where rows are dependent)."""
 import numpy as np
 import pytest
 
@@ -45,15 +45,15 @@ def _compare(g, o, act_thr, tag=""):
             p = o.node_pos[node] if node < len(o.node_pos) else None
             d = np.linalg.norm(np.array(pt) - p)
             assert abs(d - act_thr) <= 1e-9, (tag, "contact set differs", node, d)
-    fo = {c["node"]: 0.0 for c in o.contacts}
+    # net contact force on each node, sum_i y_i n_i (unique even where rows of a node are dependent)
+    fo, fg = {}, {}
     for c in o.contacts:
-        fo[c["node"]] += c["force"]
-    fg = {c["node"]: 0.0 for c in g["contacts"]}
+        fo[c["node"]] = fo.get(c["node"], 0.0) + c["force"] * np.asarray(c["normal"])
     for c in g["contacts"]:
-        fg[c["node"]] += c["force"]
-    fmax = max([abs(v) for v in fo.values()] + [1e-300])
+        fg[c["node"]] = fg.get(c["node"], 0.0) + c["force"] * np.asarray(c["normal"])
+    fmax = max([np.linalg.norm(v) for v in fo.values()] + [1e-300])
     for n in set(fo) | set(fg):
-        assert abs(fo.get(n, 0.0) - fg.get(n, 0.0)) <= 1e-6 * fmax, (tag, n, fo.get(n), fg.get(n))
+        assert np.linalg.norm(fo.get(n, 0.0) - fg.get(n, 0.0)) <= 1e-6 * fmax, (tag, n, fo.get(n), fg.get(n))
     return err
 
 
