@@ -71,7 +71,7 @@ typedef struct {
  * created when the clearance to a locally closest wall feature is below r_o + gap),
  * step_limit beta0 = 5e-4 m (Eq. 25-26, applied to the largest nodal translation),
  * newton_tol 1e-11 m (stop when the unlimited step has max(|du_i|, r_o |dtheta_i|) below it
- * and the constraint set did not change), contact_tol 1e-13 (relative sign tolerance of the
+ * and the constraint set did not change), contact_tol 1e-11 (relative sign tolerance of the
  * LCP pivoting), max_newton_iters 200, max_contact_iters 1000, max_contacts 256 (constraint
  * rows), tangent_mode 0 (material tangent K = B^T K_l B; the only mode on the GPU). */
 typedef struct {
@@ -141,6 +141,29 @@ accfem_status accfem_solve_tip_load(accfem_handle* h, const double f[3], const d
  * receives the iteration count.  For callers that keep their inputs on the GPU. */
 accfem_status accfem_solve_resident(accfem_handle* h, const double* device_cable_tensions,
                                     double insertion, int32_t* newton_iters);
+
+/* Forgets the resident state: the next solve without warm start begins from the straight pose. */
+accfem_status accfem_reset(accfem_handle* h);
+
+/* Makes the handle enqueue its work on the caller's CUDA stream (a cudaStream_t passed as
+ * void*; NULL restores the handle's own stream).  Calls stay synchronous with respect to it. */
+accfem_status accfem_set_stream(accfem_handle* h, void* stream);
+
+/* Cumulative bytes copied host->device and device->host by this handle's solve and state calls. */
+accfem_status accfem_transfer_bytes(const accfem_handle* h, int64_t* h2d, int64_t* d2h);
+
+/* Hot-path kernels that accfem_time_kernel can time standalone on the resident state. */
+typedef enum {
+  ACCFEM_KERNEL_ELEMENT = 0,    /* corotational force + tangent, one warp per element            */
+  ACCFEM_KERNEL_COLLIDE = 1,    /* node-vs-triangle detection, one warp per free node            */
+  ACCFEM_KERNEL_ASSEMBLE = 2,   /* block-tridiagonal assembly                                    */
+  ACCFEM_KERNEL_CONTACT = 3     /* W = A K^-1 A^T and the contact LCP (needs a completed solve)  */
+} accfem_kernel;
+
+/* Launches one hot-path kernel reps times on the resident state of the last solve (the listed
+ * kernels only read the poses and rewrite their own outputs) and returns the mean device time
+ * of one launch in *us, measured with CUDA events on the handle's stream.  For measurement. */
+accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t reps, double* us);
 
 /* Copies the resident nodal poses (3*(M+1) and 4*(M+1) doubles) to host buffers. */
 accfem_status accfem_get_state(accfem_handle* h, double* node_pos, double* node_quat);

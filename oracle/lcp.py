@@ -7,12 +7,29 @@ has the unique minimiser dx = -K^{-1} (g + A^T y), where y >= 0 solves the LCP
 (w is the slack b - A dx of Eq. 8; y the contact forces of Eq. 11).  W is symmetric
 positive definite when the rows of A are independent (one contact per node), so the LCP
 has exactly one solution.  Two exact finite methods are given: Murty's least-index
-principal pivoting (finite for P-matrices) and, for small m, enumeration of all 2^m
-complementary sets.
+principal pivoting (finite for P-matrices in exact arithmetic) and, for small m, enumeration of all
+2^m complementary sets; the solver uses the QP form (non-negative least squares), which stays
+robust when W is ill-conditioned.
 """
 import itertools
 
 import numpy as np
+import scipy.linalg as sla
+from scipy.optimize import nnls
+
+
+def qp_nnls(W, q):
+    """The LCP solution as the minimiser of the convex QP 1/2 y^T W y + q^T y over y >= 0 (its KKT
+    conditions are the LCP): with W = L L^T, min |L^T y + L^-1 q|^2 subject to y >= 0, solved by
+    the Lawson-Hanson non-negative least squares routine of scipy.  Returns (y, w, iterations)."""
+    m = len(q)
+    if m == 0:
+        return np.zeros(0), np.zeros(0), 0
+    L = sla.cholesky(W, lower=True)
+    b = -sla.solve_triangular(L, q, lower=True)
+    y, _ = nnls(L.T, b, maxiter=50 * m + 100)
+    w = W @ y + q
+    return y, w, 0
 
 
 def _solve_set(W, q, P):

@@ -50,8 +50,11 @@ class accfem_state(ctypes.Structure):
 
 
 EXPORTS = ["accfem_default_options", "accfem_create", "accfem_solve", "accfem_solve_tip_load",
-           "accfem_solve_resident", "accfem_get_state", "accfem_kernel_launches", "accfem_destroy",
+           "accfem_solve_resident", "accfem_reset", "accfem_set_stream", "accfem_transfer_bytes",
+           "accfem_time_kernel", "accfem_get_state", "accfem_kernel_launches", "accfem_destroy",
            "accfem_status_string", "accfem_last_error"]
+
+KERNEL_ELEMENT, KERNEL_COLLIDE, KERNEL_ASSEMBLE, KERNEL_CONTACT = range(4)
 
 _lib = None
 
@@ -73,6 +76,10 @@ def load(path=LIB_PATH):
                                           ctypes.POINTER(accfem_result)]
     lib.accfem_solve_resident.argtypes = [H, ctypes.c_void_p, ctypes.c_double, _ip]
     lib.accfem_get_state.argtypes = [H, _dp, _dp]
+    lib.accfem_reset.argtypes = [H]
+    lib.accfem_set_stream.argtypes = [H, ctypes.c_void_p]
+    lib.accfem_transfer_bytes.argtypes = [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.accfem_time_kernel.argtypes = [H, ctypes.c_int, ctypes.c_int32, _dp]
     lib.accfem_kernel_launches.argtypes = [H]
     lib.accfem_kernel_launches.restype = ctypes.c_int64
     lib.accfem_destroy.argtypes = [H]
@@ -82,7 +89,8 @@ def load(path=LIB_PATH):
     lib.accfem_last_error.argtypes = [H]
     lib.accfem_last_error.restype = ctypes.c_char_p
     for name in ("accfem_default_options", "accfem_create", "accfem_solve", "accfem_solve_tip_load",
-                 "accfem_solve_resident", "accfem_get_state"):
+                 "accfem_solve_resident", "accfem_get_state", "accfem_reset", "accfem_set_stream",
+                 "accfem_transfer_bytes", "accfem_time_kernel"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -201,6 +209,24 @@ class AccFem:
         if st != OK:
             raise RuntimeError("accfem_get_state failed: %s" % accfem_status_string(st))
         return pos, quat
+
+    def accfem_reset(self):
+        return int(self._lib.accfem_reset(self.h))
+
+    def accfem_set_stream(self, stream_ptr):
+        return int(self._lib.accfem_set_stream(self.h, ctypes.c_void_p(int(stream_ptr)) if stream_ptr else None))
+
+    def accfem_transfer_bytes(self):
+        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        self._lib.accfem_transfer_bytes(self.h, ctypes.byref(a), ctypes.byref(b))
+        return int(a.value), int(b.value)
+
+    def accfem_time_kernel(self, kernel, reps=20):
+        us = ctypes.c_double(0.0)
+        st = self._lib.accfem_time_kernel(self.h, int(kernel), int(reps), ctypes.byref(us))
+        if st != OK:
+            raise RuntimeError("accfem_time_kernel failed: %s" % self.accfem_last_error())
+        return float(us.value)
 
     def accfem_kernel_launches(self):
         return int(self._lib.accfem_kernel_launches(self.h))

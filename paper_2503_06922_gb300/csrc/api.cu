@@ -2,10 +2,12 @@
 // driver that launches the per-iteration kernels on the handle's stream.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 #include <algorithm>
+#include <map>
 
 #include "../../include/accfem.h"
 #include "common.cuh"
@@ -19,13 +21,14 @@ __global__ void rhs_kernel(Params p, Dev d);
 __global__ void bcr_elim_kernel(Params p, Dev d, int s);
 __global__ void bcr_keep_kernel(Params p, Dev d, int s);
 __global__ void bcr_root_kernel(Params p, Dev d);
-__global__ void bcr_fwd_kernel(Params p, Dev d, int s);
-__global__ void bcr_rootsolve_kernel(Params p, Dev d);
 __global__ void bcr_bwd_kernel(Params p, Dev d, int s);
 __global__ void contact_kernel(Params p, Dev d);
 __global__ void step_kernel(Params p, Dev d);
 __global__ void apply_kernel(Params p, Dev d);
 __global__ void start_kernel(Params p, Dev d, int mode, double delta, double delta_old, int k);
+__global__ void loop_ctl_kernel(Dev d, cudaGraphConditionalHandle h, int max_iter);
+__global__ void limiter_kernel(Params p, Dev d);
+__global__ void finish_kernel(Dev d);
 void upload_element_tables();
 }  // namespace accfem
 
@@ -45,6 +48,13 @@ struct accfem_handle {
   int nf_cap = 0;
   int max_newton = 200;
   std::string err;
+  struct LoopGraph { cudaGraph_t graph = nullptr; cudaGraphExec_t exec = nullptr; int body_kernels = 0; };
+  std::map<int, LoopGraph> graphs;   // device-side Newton loop, one per number of free nodes
+  bool stream_mode = false;          // ACCFEM_LAUNCH=stream: host-driven loop (kernels visible to profilers)
+  bool trace = false;                // ACCFEM_TRACE=1 (with stream mode): one line per Newton iteration on stderr
+  cudaStream_t user_stream = nullptr; // caller's stream (accfem_set_stream), else the handle's own
+  int64_t h2d = 0, d2h = 0;          // bytes copied by solve / state calls
+  cudaStream_t work() const { return user_stream ? user_stream : stream; }
 };
 
 namespace {
@@ -130,7 +140,7 @@ accfem_status accfem_default_options(accfem_options* o) {
   o->activation_gap = 1.0e-3;
   o->step_limit = 5.0e-4;
   o->newton_tol = 1.0e-11;
-  o->contact_tol = 1.0e-13;
+  o->contact_tol = 1.0e-11;
   o->max_newton_iters = 200;
   o->max_contact_iters = 1000;
   o->max_contacts = 256;
@@ -141,6 +151,10 @@ accfem_status accfem_default_options(accfem_options* o) {
 void accfem_destroy(accfem_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& kv : h->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
   if (h->h_stage) cudaFreeHost(h->h_stage);
@@ -214,6 +228,12 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
   p.eps_b = 1e-3f;
   h->nf_cap = p.M;
   h->max_newton = opt.max_newton_iters;
+  {
+    const char* lm = std::getenv("ACCFEM_LAUNCH");
+    h->stream_mode = lm && std::strcmp(lm, "stream") == 0;
+    const char* tr = std::getenv("ACCFEM_TRACE");
+    h->trace = tr && tr[0] == '1';
+  }
 
   // ---- lumen grid (host): triangles binned by centroid
   const int64_t T = lumen->n_triangles;
@@ -309,10 +329,12 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
        dalloc(h, &d.con_gap, (size_t)nfc * kCpn) && dalloc(h, &d.c_node, mc) && dalloc(h, &d.c_tri, mc) &&
        dalloc(h, &d.c_pt, 3 * mc) && dalloc(h, &d.c_n, 3 * mc) && dalloc(h, &d.c_gap, mc) &&
        dalloc(h, &d.c_first, nfc + 1) && dalloc(h, &d.p_node, mc) && dalloc(h, &d.p_tri, mc) &&
+       dalloc(h, &d.p_act, mc) && dalloc(h, &d.init_act, mc) &&
        dalloc(h, &d.D, (size_t)nfc * 36) && dalloc(h, &d.U, (size_t)nfc * 36) && dalloc(h, &d.P, (size_t)nfc * 36) &&
        dalloc(h, &d.Lm, (size_t)nfc * 36) && dalloc(h, &d.Rm, (size_t)nfc * 36) &&
        dalloc(h, &d.B, (size_t)nfc * 6 * p.nrhs_cap) && dalloc(h, &d.g, (size_t)nfc * 6) &&
-       dalloc(h, &d.dx, (size_t)nfc * 6) && dalloc(h, &d.W, (size_t)mc * mc) && dalloc(h, &d.q, mc) &&
+       dalloc(h, &d.dx, (size_t)nfc * 6) && dalloc(h, &d.du_prev, (size_t)nfc * 3) &&
+       dalloc(h, &d.rev_part, (size_t)nfc / 32 + 2) && dalloc(h, &d.W, (size_t)mc * mc) && dalloc(h, &d.q, mc) &&
        dalloc(h, &d.y, mc) && dalloc(h, &d.w, mc) && dalloc(h, &d.gj, (size_t)mc * (mc + 2)) &&
        dalloc(h, &d.inP, mc) && dalloc(h, &d.plist, mc) && dalloc(h, &d.ctl, 1);
   if (!ok) {
@@ -348,6 +370,73 @@ namespace {
     ++(h)->launches;                                    \
   } while (0)
 
+// Enqueues the kernels of one Newton iteration for nf free nodes on stream st; returns the count.
+int enqueue_iteration(accfem_handle* h, int nf, cudaStream_t st, cudaGraphConditionalHandle cond) {
+  Params& p = h->p;
+  Dev& d = h->d;
+  int n = 0;
+  element_kernel<<<(nf + kWarpsPerElemBlock - 1) / kWarpsPerElemBlock, 32 * kWarpsPerElemBlock, 0, st>>>(p, d); ++n;
+  collide_kernel<<<(nf + 3) / 4, 128, 0, st>>>(p, d); ++n;
+  compact_kernel<<<1, 1024, 0, st>>>(p, d); ++n;
+  assemble_kernel<<<nf, 96, 0, st>>>(p, d); ++n;
+  rhs_kernel<<<nf, dim3(32, 6), 0, st>>>(p, d); ++n;
+  std::vector<int> strides;
+  for (int s = 1; s < nf; s *= 2) strides.push_back(s);
+  for (int s : strides) {
+    bcr_elim_kernel<<<(nf - s - 1) / (2 * s) + 1, 64, 0, st>>>(p, d, s); ++n;
+    bcr_keep_kernel<<<(nf - 1) / (2 * s) + 1, 192, 0, st>>>(p, d, s); ++n;
+  }
+  bcr_root_kernel<<<1, 192, 0, st>>>(p, d); ++n;
+  for (int si = (int)strides.size() - 1; si >= 0; --si) {
+    int s = strides[si];
+    bcr_bwd_kernel<<<(nf - s - 1) / (2 * s) + 1, 192, 0, st>>>(p, d, s); ++n;
+  }
+  contact_kernel<<<1, 1024, 0, st>>>(p, d); ++n;
+  step_kernel<<<(nf + 31) / 32, dim3(32, 6), 0, st>>>(p, d); ++n;
+  limiter_kernel<<<1, 32, 0, st>>>(p, d); ++n;
+  apply_kernel<<<(nf + 127) / 128, 128, 0, st>>>(p, d); ++n;
+  finish_kernel<<<1, 32, 0, st>>>(d); ++n;
+  if (!h->stream_mode) { loop_ctl_kernel<<<1, 1, 0, st>>>(d, cond, h->max_newton); ++n; }
+  return n;
+}
+
+// Device-side Newton loop for nf free nodes: a graph whose WHILE node runs the iteration body until
+// loop_ctl_kernel clears the condition (converged, error, or the iteration cap).  Built once per nf.
+const accfem_handle::LoopGraph* newton_graph(accfem_handle* h, int nf) {
+  auto it = h->graphs.find(nf);
+  if (it != h->graphs.end()) return &it->second;
+  accfem_handle::LoopGraph lg;
+  cudaGraphConditionalHandle cond;
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t node;
+  if (!cuda_ok(h, cudaGraphCreate(&lg.graph, 0), "cudaGraphCreate") ||
+      !cuda_ok(h, cudaGraphConditionalHandleCreate(&cond, lg.graph, 1, cudaGraphCondAssignDefault), "conditional handle"))
+    return nullptr;
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (!cuda_ok(h, cudaGraphAddNode(&node, lg.graph, nullptr, nullptr, 0, &cp), "conditional node")) {
+    cudaGraphDestroy(lg.graph);
+    return nullptr;
+  }
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (!cuda_ok(h, cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
+               "begin capture")) {
+    cudaGraphDestroy(lg.graph);
+    return nullptr;
+  }
+  lg.body_kernels = enqueue_iteration(h, nf, h->stream, cond);
+  cudaError_t ce = cudaStreamEndCapture(h->stream, &body);
+  if (!cuda_ok(h, ce, "end capture") || !cuda_ok(h, cudaGraphInstantiate(&lg.exec, lg.graph, 0), "instantiate graph")) {
+    cudaGetLastError();
+    cudaGraphDestroy(lg.graph);
+    return nullptr;
+  }
+  auto res = h->graphs.emplace(nf, lg);
+  return &res.first->second;
+}
+
 // Runs one solve on the device; the solution stays resident.  Returns the status.
 accfem_status run_solve(accfem_handle* h, int load_mode, const double* tensions_host, const double* tensions_dev,
                         const double* tip_f, const double* tip_m, double insertion, const accfem_state* warm) {
@@ -361,6 +450,7 @@ accfem_status run_solve(accfem_handle* h, int load_mode, const double* tensions_
   c.k = k;
   c.nf = nf;
   c.m_prev = -1;
+  c.rho = p.beta0;
   c.load_mode = load_mode;
   c.delta = insertion;
   if (load_mode == 0 && tensions_host) {
@@ -376,8 +466,9 @@ accfem_status run_solve(accfem_handle* h, int load_mode, const double* tensions_
       c.tip_f[a] = tip_f[a];
       c.tip_m[a] = tip_m[a];
     }
-  cudaStream_t st = h->stream;
+  cudaStream_t st = h->work();
   if (!cuda_ok(h, cudaMemcpyAsync(d.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st), "upload control")) return ACCFEM_E_CUDA;
+  h->h2d += sizeof(Ctl);
   if (load_mode == 0 && tensions_dev && p.n_cables > 0) {
     if (!cuda_ok(h, cudaMemcpyAsync(&d.ctl->tension[0], tensions_dev, sizeof(double) * p.n_cables, cudaMemcpyDeviceToDevice, st),
                  "copy tensions"))
@@ -395,6 +486,7 @@ accfem_status run_solve(accfem_handle* h, int load_mode, const double* tensions_
     for (int comp = 0; comp < 7; ++comp)
       if (!cuda_ok(h, cudaMemcpyAsync(dst[comp], s + comp * p.N, nb, cudaMemcpyHostToDevice, st), "upload warm state"))
         return ACCFEM_E_CUDA;
+    h->h2d += 7 * nb;
     mode = 2;
   } else if (h->has_state) {
     double* src[7] = {d.px, d.py, d.pz, d.qw, d.qx, d.qy, d.qz};
@@ -407,57 +499,43 @@ accfem_status run_solve(accfem_handle* h, int load_mode, const double* tensions_
   h->has_state = true;
   h->delta = insertion;
   accfem_status status = ACCFEM_OK;
-  if (nf > 0) {
-    const int ne = p.M - k;
-    const int rhs_blocks = (p.nrhs_cap + 31) / 32;
-    std::vector<int> strides;
-    for (int s = 1; s < nf; s *= 2) strides.push_back(s);
+  if (nf > 0 && h->stream_mode) {
     status = ACCFEM_E_NOT_CONVERGED;
     for (int it = 0; it < h->max_newton; ++it) {
-      LAUNCH(h, element_kernel<<<(ne + kWarpsPerElemBlock - 1) / kWarpsPerElemBlock, 32 * kWarpsPerElemBlock, 0, st>>>(p, d));
-      LAUNCH(h, collide_kernel<<<(nf + 3) / 4, 128, 0, st>>>(p, d));
-      LAUNCH(h, compact_kernel<<<1, 1024, 0, st>>>(p, d));
-      LAUNCH(h, assemble_kernel<<<nf, 96, 0, st>>>(p, d));
-      LAUNCH(h, rhs_kernel<<<dim3(nf, rhs_blocks), dim3(32, 6), 0, st>>>(p, d));
-      for (int s : strides) {
-        int ne_ = (nf - s - 1) / (2 * s) + 1;
-        int nk = (nf - 1) / (2 * s) + 1;
-        LAUNCH(h, bcr_elim_kernel<<<ne_, 64, 0, st>>>(p, d, s));
-        LAUNCH(h, bcr_keep_kernel<<<nk, 64, 0, st>>>(p, d, s));
-      }
-      LAUNCH(h, bcr_root_kernel<<<1, 64, 0, st>>>(p, d));
-      for (int s : strides) {
-        int nk = (nf - 1) / (2 * s) + 1;
-        LAUNCH(h, bcr_fwd_kernel<<<dim3(nk, rhs_blocks), dim3(32, 6), 0, st>>>(p, d, s));
-      }
-      LAUNCH(h, bcr_rootsolve_kernel<<<dim3(1, rhs_blocks), dim3(32, 6), 0, st>>>(p, d));
-      for (int si = (int)strides.size() - 1; si >= 0; --si) {
-        int s = strides[si];
-        int ne_ = (nf - s - 1) / (2 * s) + 1;
-        LAUNCH(h, bcr_bwd_kernel<<<dim3(ne_, rhs_blocks), dim3(32, 6), 0, st>>>(p, d, s));
-      }
-      LAUNCH(h, contact_kernel<<<1, 1024, 0, st>>>(p, d));
-      LAUNCH(h, step_kernel<<<(nf + 31) / 32, dim3(32, 6), 0, st>>>(p, d));
-      LAUNCH(h, apply_kernel<<<(nf + 127) / 128, 128, 0, st>>>(p, d));
-      if (!cuda_ok(h, cudaGetLastError(), "kernel launch")) return ACCFEM_E_CUDA;
-      if (!cuda_ok(h, cudaMemcpyAsync(h->h_ctl, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st), "read control") ||
+      h->launches += enqueue_iteration(h, nf, st, cudaGraphConditionalHandle());
+      if (!cuda_ok(h, cudaGetLastError(), "kernel launch") ||
+          !cuda_ok(h, cudaMemcpyAsync(h->h_ctl, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st), "read control") ||
           !cuda_ok(h, cudaStreamSynchronize(st), "Newton iteration"))
         return ACCFEM_E_CUDA;
-      if (c.status != 0) {
-        status = (accfem_status)c.status;
-        break;
-      }
-      if (c.converged) {
-        status = ACCFEM_OK;
-        break;
-      }
+      h->d2h += sizeof(Ctl);
+      if (h->trace)
+        std::fprintf(stderr, "accfem it %d alpha %.4f umax %.3e step %.3e res %.3e m %d same %d active %d lcp %d\n",
+                     c.iter, c.alpha, __builtin_bit_cast(double, (unsigned long long)c.umax_bits),
+                     __builtin_bit_cast(double, (unsigned long long)c.step_bits),
+                     __builtin_bit_cast(double, (unsigned long long)c.res_bits), c.m, c.same_set, c.n_active,
+                     c.lcp_pivots);
+      if (c.status != 0) { status = (accfem_status)c.status; break; }
+      if (c.converged) { status = ACCFEM_OK; break; }
     }
+  } else if (nf > 0) {
+    const accfem_handle::LoopGraph* lg = newton_graph(h, nf);
+    if (!lg) return ACCFEM_E_CUDA;
+    if (!cuda_ok(h, cudaGraphLaunch(lg->exec, st), "launch Newton graph") ||
+        !cuda_ok(h, cudaMemcpyAsync(h->h_ctl, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st), "read control") ||
+        !cuda_ok(h, cudaStreamSynchronize(st), "Newton loop"))
+      return ACCFEM_E_CUDA;
+    h->d2h += sizeof(Ctl);
+    h->launches += (int64_t)c.loops * lg->body_kernels;
+    if (c.status != 0) status = (accfem_status)c.status;
+    else if (c.converged) status = ACCFEM_OK;
+    else status = ACCFEM_E_NOT_CONVERGED;
     if (status == ACCFEM_E_NOT_CONVERGED) h->err = "Newton iterations did not converge";
     else if (status != ACCFEM_OK) h->err = accfem_status_string(status);
   } else {
     if (!cuda_ok(h, cudaMemcpyAsync(h->h_ctl, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st), "read control") ||
         !cuda_ok(h, cudaStreamSynchronize(st), "start pose"))
       return ACCFEM_E_CUDA;
+    h->d2h += sizeof(Ctl);
   }
   return status;
 }
@@ -467,9 +545,10 @@ accfem_status download(accfem_handle* h, accfem_status status, accfem_result* ou
   Params& p = h->p;
   Dev& d = h->d;
   Ctl& c = *h->h_ctl;
-  cudaStream_t st = h->stream;
+  cudaStream_t st = h->work();
   const int N = p.N;
   double* s = h->h_stage;
+  h->d2h += 7 * sizeof(double) * (size_t)N;
   const double* src[7] = {d.px, d.py, d.pz, d.qw, d.qx, d.qy, d.qz};
   for (int comp = 0; comp < 7; ++comp)
     if (!cuda_ok(h, cudaMemcpyAsync(s + comp * N, src[comp], sizeof(double) * N, cudaMemcpyDeviceToHost, st), "download state"))
@@ -494,6 +573,7 @@ accfem_status download(accfem_handle* h, accfem_status status, accfem_result* ou
       return ACCFEM_E_CUDA;
     if (!cuda_ok(h, cudaStreamSynchronize(st), "download reaction")) return ACCFEM_E_CUDA;
     for (int a = 0; a < 6; ++a) out->base_reaction[a] = s[a];
+    h->d2h += 6 * sizeof(double);
   }
   if (m > 0) {
     const int nw = std::min(m, std::max(out->contact_capacity, 0));
@@ -507,6 +587,7 @@ accfem_status download(accfem_handle* h, accfem_status status, accfem_result* ou
                 cuda_ok(h, cudaMemcpyAsync(y.data(), d.y, sizeof(double) * m, cudaMemcpyDeviceToHost, st), "download") &&
                 cuda_ok(h, cudaStreamSynchronize(st), "download contacts");
       if (!ok) return ACCFEM_E_CUDA;
+      h->d2h += (size_t)m * (2 * sizeof(int) + 7 * sizeof(double));
       for (int i = 0; i < nw; ++i) {
         if (out->contact_node) out->contact_node[i] = c.k + 1 + node[i];
         if (out->contact_tri) out->contact_tri[i] = tri[i];
@@ -554,6 +635,70 @@ accfem_status accfem_solve_resident(accfem_handle* h, const double* device_cable
   accfem_status s = run_solve(h, 0, nullptr, device_cable_tensions, nullptr, nullptr, insertion, nullptr);
   if (newton_iters) *newton_iters = h->h_ctl->iter;
   return s;
+}
+
+accfem_status accfem_reset(accfem_handle* h) {
+  if (!h) return ACCFEM_E_INVALID_ARG;
+  h->has_state = false;
+  h->delta = 0.0;
+  return ACCFEM_OK;
+}
+
+accfem_status accfem_set_stream(accfem_handle* h, void* stream) {
+  if (!h) return ACCFEM_E_INVALID_ARG;
+  h->user_stream = (cudaStream_t)stream;
+  return ACCFEM_OK;
+}
+
+accfem_status accfem_transfer_bytes(const accfem_handle* h, int64_t* h2d, int64_t* d2h) {
+  if (!h || !h2d || !d2h) return ACCFEM_E_INVALID_ARG;
+  *h2d = h->h2d;
+  *d2h = h->d2h;
+  return ACCFEM_OK;
+}
+
+accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t reps, double* us) {
+  if (!h || !us || reps < 1) return fail(h, ACCFEM_E_INVALID_ARG, "NULL argument or reps < 1");
+  Params& p = h->p;
+  Dev& d = h->d;
+  Ctl& c = *h->h_ctl;
+  const int nf = c.nf;
+  if (nf <= 0 || !h->has_state) return fail(h, ACCFEM_E_INVALID_ARG, "no resident solve with free nodes");
+  if (kernel == ACCFEM_KERNEL_CONTACT && c.iter < 1) return fail(h, ACCFEM_E_INVALID_ARG, "no completed iteration");
+  cudaStream_t st = h->work();
+  // the kernels return early on a converged control block: run them on a copy flagged "iterating"
+  Ctl run = c;
+  run.converged = 0;
+  run.status = 0;
+  if (!cuda_ok(h, cudaMemcpyAsync(d.ctl, &run, sizeof(Ctl), cudaMemcpyHostToDevice, st), "upload control")) return ACCFEM_E_CUDA;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto launch = [&]() {
+    switch (kernel) {
+      case ACCFEM_KERNEL_ELEMENT:
+        element_kernel<<<(nf + kWarpsPerElemBlock - 1) / kWarpsPerElemBlock, 32 * kWarpsPerElemBlock, 0, st>>>(p, d); break;
+      case ACCFEM_KERNEL_COLLIDE: collide_kernel<<<(nf + 3) / 4, 128, 0, st>>>(p, d); break;
+      case ACCFEM_KERNEL_ASSEMBLE: assemble_kernel<<<nf, 96, 0, st>>>(p, d); break;
+      default: contact_kernel<<<1, 1024, 0, st>>>(p, d); break;
+    }
+  };
+  launch();
+  cudaEventRecord(e0, st);
+  for (int i = 0; i < reps; ++i) launch();
+  cudaEventRecord(e1, st);
+  h->launches += reps + 1;
+  bool ok = cuda_ok(h, cudaEventSynchronize(e1), "time kernel");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // restore the control block of the solve
+  ok = ok && cuda_ok(h, cudaMemcpyAsync(d.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st), "restore control") &&
+       cuda_ok(h, cudaStreamSynchronize(st), "restore control");
+  if (!ok) return ACCFEM_E_CUDA;
+  *us = 1000.0 * ms / reps;
+  return ACCFEM_OK;
 }
 
 accfem_status accfem_get_state(accfem_handle* h, double* node_pos, double* node_quat) {

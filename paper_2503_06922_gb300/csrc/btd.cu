@@ -26,7 +26,6 @@ __device__ __forceinline__ double kval(const double* rec, int i, int j) {
 // One CTA: exclusive scan of the per-node row counts, row arrays in (node, triangle) order,
 // comparison with the previous iteration's rows, copy to "previous".
 __global__ void __launch_bounds__(1024) compact_kernel(Params p, Dev d) {
-  __shared__ int s_part[1024];
   __shared__ int s_warp[32];
   __shared__ int s_same;
   Ctl* ctl = d.ctl;
@@ -82,6 +81,17 @@ __global__ void __launch_bounds__(1024) compact_kernel(Params p, Dev d) {
   if (tid == 0) d.c_first[nf] = m;
   __syncthreads();
   const int mp = ctl->m_prev;
+  // active-set warm start: a row seen in the previous iteration keeps its active flag
+  for (int r = tid; r < m; r += 1024) {
+    int nd = d.c_node[r], tr = d.c_tri[r], lo = 0, hi = mp - 1, found = -1;
+    while (lo <= hi) {                       // previous rows are ordered by (node, triangle)
+      int mid = (lo + hi) >> 1;
+      int pn = d.p_node[mid], pt = d.p_tri[mid];
+      if (pn == nd && pt == tr) { found = mid; break; }
+      if (pn < nd || (pn == nd && pt < tr)) lo = mid + 1; else hi = mid - 1;
+    }
+    d.init_act[r] = found >= 0 ? d.p_act[found] : -1;
+  }
   if (mp != m) {
     if (tid == 0) s_same = 0;
   } else {
@@ -89,7 +99,7 @@ __global__ void __launch_bounds__(1024) compact_kernel(Params p, Dev d) {
       if (d.p_node[r] != d.c_node[r] || d.p_tri[r] != d.c_tri[r]) s_same = 0;
   }
   __syncthreads();
-  for (int r = tid; r < m; r += 1024) { d.p_node[r] = d.c_node[r]; d.p_tri[r] = d.c_tri[r]; }
+  for (int r = tid; r < m; r += 1024) { d.p_node[r] = d.c_node[r]; d.p_tri[r] = d.c_tri[r]; d.p_act[r] = 0; }
   if (tid == 0) { ctl->same_set = s_same; ctl->m = m; ctl->m_prev = m; }
 }
 
@@ -147,16 +157,19 @@ __global__ void __launch_bounds__(96) assemble_kernel(Params p, Dev d) {
 }
 
 // RHS columns: 0 = -g, 1 + row = A^T e_row (unit normal on the row's node translation).
-// grid (nf, ceil(nrhs_cap / 32)), block (32, 6).
+// One block of (32 rhs, 6 comps) per free node, looping over chunks of 32 columns.
 __global__ void __launch_bounds__(192) rhs_kernel(Params p, Dev d) {
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
-  const int f = blockIdx.x, c = threadIdx.y, r = blockIdx.y * 32 + threadIdx.x;
-  if (f >= ctl->nf || r > ctl->m) return;
-  double v;
-  if (r == 0) v = -d.g[(size_t)f * 6 + c];
-  else v = (d.c_node[r - 1] == f && c < 3) ? d.c_n[3 * (r - 1) + c] : 0.0;
-  d.B[((size_t)f * 6 + c) * p.nrhs_cap + r] = v;
+  const int f = blockIdx.x, c = threadIdx.y;
+  if (f >= ctl->nf) return;
+  const int nrhs = ctl->m + 1;
+  for (int r = threadIdx.x; r < nrhs; r += 32) {
+    double v;
+    if (r == 0) v = -d.g[(size_t)f * 6 + c];
+    else v = (d.c_node[r - 1] == f && c < 3) ? d.c_n[3 * (r - 1) + c] : 0.0;
+    d.B[((size_t)f * 6 + c) * p.nrhs_cap + r] = v;
+  }
 }
 
 // ------------------------------------------------------------------ 6x6 helpers (64-thread team)
@@ -219,8 +232,9 @@ __global__ void __launch_bounds__(64) bcr_elim_kernel(Params p, Dev d, int s) {
   }
 }
 
-// Phase B: kept nodes i = 2 s blockIdx.x.
-__global__ void __launch_bounds__(64) bcr_keep_kernel(Params p, Dev d, int s) {
+// Phase B: kept nodes i = 2 s blockIdx.x, fused with the forward reduction of every RHS column.
+// Block: 192 threads = (32 rhs lanes, 6 comps); threads 0..35 update the 6x6 blocks.
+__global__ void __launch_bounds__(192) bcr_keep_kernel(Params p, Dev d, int s) {
   __shared__ double sRl[36], sUl[36], sLr[36], sUi[36], sUr[36];
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
@@ -250,10 +264,28 @@ __global__ void __launch_bounds__(64) bcr_keep_kernel(Params p, Dev d, int s) {
     d.D[(size_t)i * 36 + tid] = dd;
     if (hr) d.U[(size_t)i * 36 + tid] = hr2 ? un : 0.0;
   }
+  // forward reduction: b_i -= R_{i-s} b_{i-s} + L_{i+s} b_{i+s}
+  const int lane = tid & 31, c = tid >> 5;
+  const int nrhs = ctl->m + 1;
+  const size_t ld = p.nrhs_cap;
+  for (int r = lane; r < nrhs; r += 32) {
+    double acc = d.B[((size_t)i * 6 + c) * ld + r];
+    if (hl) {
+      const double* b = d.B + (size_t)(i - s) * 6 * ld + r;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc = fma(-sRl[c * 6 + k], b[k * ld], acc);
+    }
+    if (hr) {
+      const double* b = d.B + (size_t)(i + s) * 6 * ld + r;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc = fma(-sLr[c * 6 + k], b[k * ld], acc);
+    }
+    d.B[((size_t)i * 6 + c) * ld + r] = acc;
+  }
 }
 
-// Root: P_0 = D_0^{-1}.
-__global__ void __launch_bounds__(64) bcr_root_kernel(Params p, Dev d) {
+// Root: P_0 = D_0^{-1} and x_0 = P_0 b_0 for every RHS column.  Block: 192 threads.
+__global__ void __launch_bounds__(192) bcr_root_kernel(Params p, Dev d) {
   __shared__ double sA[36];
   __shared__ double s_piv[1];
   Ctl* ctl = d.ctl;
@@ -266,87 +298,70 @@ __global__ void __launch_bounds__(64) bcr_root_kernel(Params p, Dev d) {
     return;
   }
   if (tid < 36) d.P[tid] = sA[tid];
-}
-
-// Forward reduction at stride s for kept nodes i = 2 s blockIdx.x; block (32 rhs, 6 comps).
-__global__ void __launch_bounds__(192) bcr_fwd_kernel(Params p, Dev d, int s) {
-  Ctl* ctl = d.ctl;
-  if (ctl->status != 0 || ctl->converged) return;
-  const int nf = ctl->nf, nrhs = ctl->m + 1;
-  const int i = 2 * s * blockIdx.x;
-  const int r = blockIdx.y * 32 + threadIdx.x, c = threadIdx.y;
-  if (i >= nf || r >= nrhs) return;
-  const size_t ld = p.nrhs_cap;
-  double acc = d.B[((size_t)i * 6 + c) * ld + r];
-  if (i >= s) {
-    const double* R = d.Rm + (size_t)(i - s) * 36 + c * 6;
-    const double* b = d.B + (size_t)(i - s) * 6 * ld + r;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) acc = fma(-R[k], b[k * ld], acc);
-  }
-  if (i + s < nf) {
-    const double* L = d.Lm + (size_t)(i + s) * 36 + c * 6;
-    const double* b = d.B + (size_t)(i + s) * 6 * ld + r;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) acc = fma(-L[k], b[k * ld], acc);
-  }
-  d.B[((size_t)i * 6 + c) * ld + r] = acc;
-}
-
-// Root solve x_0 = P_0 b_0; grid (1, ceil(nrhs_cap/32)), block (32, 6).
-__global__ void __launch_bounds__(192) bcr_rootsolve_kernel(Params p, Dev d) {
-  Ctl* ctl = d.ctl;
-  if (ctl->status != 0 || ctl->converged || ctl->nf == 0) return;
+  const int lane = tid & 31, c = tid >> 5;
   const int nrhs = ctl->m + 1;
-  const int r = blockIdx.y * 32 + threadIdx.x, c = threadIdx.y;
   const size_t ld = p.nrhs_cap;
-  const bool act = r < nrhs;
-  double b[6];
-  if (act)
+  for (int r0 = 0; r0 < nrhs; r0 += 32) {
+    const int r = r0 + lane;
+    const bool act = r < nrhs;
+    double b[6];
+    if (act)
 #pragma unroll
-    for (int k = 0; k < 6; ++k) b[k] = d.B[(size_t)k * ld + r];
-  __syncthreads();
-  if (act) {
-    double acc = 0.0;
+      for (int k = 0; k < 6; ++k) b[k] = d.B[(size_t)k * ld + r];
+    __syncthreads();
+    if (act) {
+      double acc = 0.0;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc = fma(d.P[c * 6 + k], b[k], acc);
-    d.B[(size_t)c * ld + r] = acc;
+      for (int k = 0; k < 6; ++k) acc = fma(sA[c * 6 + k], b[k], acc);
+      d.B[(size_t)c * ld + r] = acc;
+    }
+    __syncthreads();
   }
 }
 
-// Back substitution at stride s for eliminated nodes j = s + 2 s blockIdx.x.
+// Back substitution at stride s for eliminated nodes j = s + 2 s blockIdx.x (192 threads).
 __global__ void __launch_bounds__(192) bcr_bwd_kernel(Params p, Dev d, int s) {
+  __shared__ double sP[36], sL[36], sR[36];
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
-  const int nf = ctl->nf, nrhs = ctl->m + 1;
+  const int nf = ctl->nf;
   const int j = s + 2 * s * blockIdx.x;
   if (j >= nf) return;
-  const int r = blockIdx.y * 32 + threadIdx.x, c = threadIdx.y;
-  const bool act = r < nrhs;
-  const size_t ld = p.nrhs_cap;
-  double b[6];
-  if (act)
-#pragma unroll
-    for (int k = 0; k < 6; ++k) b[k] = d.B[((size_t)j * 6 + k) * ld + r];
+  const int tid = threadIdx.x;
+  const bool hr = j + s < nf;
+  if (tid < 36) {
+    sP[tid] = d.P[(size_t)j * 36 + tid];
+    sL[tid] = d.Lm[(size_t)j * 36 + tid];
+    sR[tid] = hr ? d.Rm[(size_t)j * 36 + tid] : 0.0;
+  }
   __syncthreads();
-  if (!act) return;
-  double acc = 0.0;
-  const double* P = d.P + (size_t)j * 36 + c * 6;
+  const int lane = tid & 31, c = tid >> 5;
+  const int nrhs = ctl->m + 1;
+  const size_t ld = p.nrhs_cap;
+  for (int r0 = 0; r0 < nrhs; r0 += 32) {
+    const int r = r0 + lane;
+    const bool act = r < nrhs;
+    double b[6];
+    if (act)
 #pragma unroll
-  for (int k = 0; k < 6; ++k) acc = fma(P[k], b[k], acc);
-  {
-    const double* L = d.Lm + (size_t)j * 36;   // -L_j^T x_{j-s}: (L^T)[c][k] = L[k][c]
-    const double* x = d.B + (size_t)(j - s) * 6 * ld + r;
+      for (int k = 0; k < 6; ++k) b[k] = d.B[((size_t)j * 6 + k) * ld + r];
+    __syncthreads();
+    if (act) {
+      double acc = 0.0;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc = fma(-L[k * 6 + c], x[k * ld], acc);
+      for (int k = 0; k < 6; ++k) acc = fma(sP[c * 6 + k], b[k], acc);
+      const double* x = d.B + (size_t)(j - s) * 6 * ld + r;     // - L_j^T x_{j-s}
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc = fma(-sL[k * 6 + c], x[k * ld], acc);
+      if (hr) {
+        const double* x2 = d.B + (size_t)(j + s) * 6 * ld + r;  // - R_j^T x_{j+s}
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc = fma(-sR[k * 6 + c], x2[k * ld], acc);
+      }
+      d.B[((size_t)j * 6 + c) * ld + r] = acc;
+    }
+    __syncthreads();
   }
-  if (j + s < nf) {
-    const double* R = d.Rm + (size_t)j * 36;
-    const double* x = d.B + (size_t)(j + s) * 6 * ld + r;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) acc = fma(-R[k * 6 + c], x[k * ld], acc);
-  }
-  d.B[((size_t)j * 6 + c) * ld + r] = acc;
 }
 
 }  // namespace accfem

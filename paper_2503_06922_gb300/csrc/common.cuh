@@ -49,9 +49,12 @@ struct Ctl {
   int lcp_pivots;        // LCP pivot steps in this solve
   int n_active;
   int load_mode;         // 0 cables, 1 dead tip load (global), 2 follower tip load (tip frame)
-  int pad0;
+  int loops;             // passes of the device-side Newton loop
   unsigned long long umax_bits, step_bits, res_bits;   // atomicMax on non-negative doubles
   double alpha;
+  double rho;            // step bound of the limiter (starts at beta0)
+  int has_prev;          // a previous Newton step exists in this solve
+  int pad1;
   double delta;          // insertion of the resident state
   double tension[kMaxCables];
   double tip_f[3], tip_m[3];
@@ -81,11 +84,15 @@ struct Dev {
   double *c_pt, *c_n, *c_gap;                        // m_cap * 3, * 3, * 1
   int *c_first;                                      // nf_cap + 1: rows of node f = [c_first[f], c_first[f+1])
   int *p_node, *p_tri;                               // previous iteration's rows
+  int *p_act;                                        // previous rows: multiplier > 0
+  int *init_act;                                     // current rows: 1/0 from the previous iteration, -1 new
   // block-tridiagonal system (free nodes)
   double *D, *U, *P, *Lm, *Rm;                       // nf_cap * 36 each, row-major 6x6
   double* B;                                         // nf_cap * 6 * nrhs_cap, [(f*6+c)*nrhs_cap + r]
   double* g;                                         // nf_cap * 6 : F - F_a on free DOFs
   double* dx;                                        // nf_cap * 6 : Newton step
+  double* du_prev;                                   // nf_cap * 3 : previous Newton step (translations)
+  double* rev_part;                                  // per step_kernel block: sum du . du_prev
   // contact LCP
   double *W, *q, *y, *w, *gj;                        // m_cap^2, m_cap, m_cap, m_cap, m_cap*(m_cap+1)
   int *inP, *plist;                                  // m_cap

@@ -32,24 +32,59 @@ __global__ void __launch_bounds__(192) step_kernel(Params p, Dev d) {
     s_r[fl][c] = fabs(r);
   }
   __syncthreads();
+  double rr_node = 0.0;
+  if (act && c == 0)
+    rr_node = fmax(fmax(fmax(s_r[fl][0], s_r[fl][1]), fmax(s_r[fl][2], s_r[fl][3])), fmax(s_r[fl][4], s_r[fl][5]));
+  __syncthreads();
+  if (act && c < 3) {
+    // reversal test of the limiter: this step against the previous one (translations)
+    s_r[fl][c] = s_dx[fl][c] * d.du_prev[(size_t)f * 3 + c];
+    d.du_prev[(size_t)f * 3 + c] = s_dx[fl][c];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double rev = 0.0;
+    for (int k = 0; k < 32 && blockIdx.x * 32 + k < nf; ++k) rev += s_r[k][0] + s_r[k][1] + s_r[k][2];
+    d.rev_part[blockIdx.x] = rev;
+  }
   if (act && c == 0) {
     double du = sqrt(s_dx[fl][0] * s_dx[fl][0] + s_dx[fl][1] * s_dx[fl][1] + s_dx[fl][2] * s_dx[fl][2]);
     double dt = sqrt(s_dx[fl][3] * s_dx[fl][3] + s_dx[fl][4] * s_dx[fl][4] + s_dx[fl][5] * s_dx[fl][5]);
     double st = fmax(du, p.r_o * dt);
-    double rr = fmax(fmax(fmax(s_r[fl][0], s_r[fl][1]), fmax(s_r[fl][2], s_r[fl][3])), fmax(s_r[fl][4], s_r[fl][5]));
     atomicMax(&ctl->umax_bits, dbits(du));
     atomicMax(&ctl->step_bits, dbits(st));
-    atomicMax(&ctl->res_bits, dbits(rr));
+    atomicMax(&ctl->res_bits, dbits(rr_node));
   }
 }
 
-// x <- x + alpha du, T <- exp([alpha dtheta]x) T, alpha = min(1, beta0 / max |du|).
+// Step limiter (Eq. 25-27 with an adaptive bound): rho is halved when the Newton step reverses
+// against the previous one (sum_i du_i . du_i^prev < 0, summed over the step blocks in a fixed
+// order), doubled back towards beta0 otherwise; alpha = min(1, rho / max |du|).  Also counts the
+// iteration and decides convergence (unlimited step below tol with an unchanged constraint set).
+__global__ void limiter_kernel(Params p, Dev d) {
+  Ctl* ctl = d.ctl;
+  if (ctl->status != 0 || ctl->converged || threadIdx.x != 0) return;
+  const int nb = (ctl->nf + 31) / 32;
+  double rev = 0.0;
+  for (int b = 0; b < nb; ++b) rev += d.rev_part[b];
+  double rho = ctl->rho;
+  if (ctl->has_prev) rho = rev < 0.0 ? fmax(0.5 * rho, p.beta0 * 9.5367431640625e-07) : fmin(2.0 * rho, p.beta0);
+  const double umax = __longlong_as_double((long long)ctl->umax_bits);
+  const double step = __longlong_as_double((long long)ctl->step_bits);
+  const double alpha = umax <= rho ? 1.0 : rho / umax;
+  ctl->rho = rho;
+  ctl->has_prev = 1;
+  ctl->alpha = alpha;
+  ctl->iter += 1;
+  if (alpha == 1.0 && step <= p.tol && ctl->same_set) ctl->converged = 2;   // 2: apply this last step
+}
+
+// x <- x + alpha du, T <- exp([alpha dtheta]x) T.
 __global__ void __launch_bounds__(128) apply_kernel(Params p, Dev d) {
   Ctl* ctl = d.ctl;
-  if (ctl->status != 0 || ctl->converged) return;
+  if (ctl->status != 0 || ctl->converged == 1) return;
   const int nf = ctl->nf;
-  const double umax = __longlong_as_double((long long)ctl->umax_bits);
-  const double alpha = umax <= p.beta0 ? 1.0 : p.beta0 / umax;
+  const double alpha = ctl->alpha;
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f < nf) {
     const int node = ctl->k + 1 + f;
@@ -65,12 +100,21 @@ __global__ void __launch_bounds__(128) apply_kernel(Params p, Dev d) {
     if (r[0] < 0.0) in = -in;
     d.qw[node] = r[0] * in; d.qx[node] = r[1] * in; d.qy[node] = r[2] * in; d.qz[node] = r[3] * in;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const double step = __longlong_as_double((long long)ctl->step_bits);
-    ctl->alpha = alpha;
-    ctl->iter += 1;
-    if (alpha == 1.0 && step <= p.tol && ctl->same_set) ctl->converged = 1;
-  }
+}
+
+// Marks a converged solve final once its last step is applied.
+__global__ void finish_kernel(Dev d) {
+  if (threadIdx.x == 0 && d.ctl->converged == 2) d.ctl->converged = 1;
+}
+
+// Newton loop control (last node of the loop body): keep iterating while no error, not converged
+// and fewer than max_iter iterations; a separate count of loop passes bounds the loop whatever the
+// other kernels did.
+__global__ void loop_ctl_kernel(Dev d, cudaGraphConditionalHandle h, int max_iter) {
+  Ctl* c = d.ctl;
+  c->loops += 1;
+  unsigned int cont = (c->status == 0 && !c->converged && c->iter < max_iter && c->loops < max_iter) ? 1u : 0u;
+  cudaGraphSetConditional(h, cont);
 }
 
 // Start pose of a solve.  mode 0: straight on the entrance axis; mode 1: follow the path of the

@@ -157,6 +157,24 @@ def test_murty_matches_enumeration():
             assert y.min() >= 0 and ww.min() >= -1e-12 and abs(y @ ww) <= 1e-12
 
 
+def test_qp_nnls_matches_murty_and_enumeration():
+    """The QP (NNLS) form returns the unique LCP solution found by pivoting and enumeration."""
+    rng = np.random.default_rng(15)
+    for m in range(1, 9):
+        for _ in range(6):
+            W = _spd(rng, m)
+            q = rng.normal(size=m)
+            y, w, _ = lcp.qp_nnls(W, q)
+            ye = lcp.enumerate_lcp(W, q)[0][0]
+            assert np.allclose(y, ye, atol=1e-12)
+    for m in (20, 60):
+        W = _spd(rng, m)
+        q = rng.normal(size=m)
+        y, _, _ = lcp.qp_nnls(W, q)
+        ym, _, _ = lcp.murty(W, q)
+        assert np.allclose(y, ym, atol=1e-11)
+
+
 def test_murty_kkt_larger():
     rng = np.random.default_rng(14)
     for m in (20, 60):
