@@ -85,7 +85,7 @@ typedef struct {
  * the last Newton iteration (if it exceeds contact_capacity only the first
  * contact_capacity are written and the status is ACCFEM_E_CONTACT_CAPACITY).
  * contact_force[i] >= 0 is the multiplier y_i of Eq. 11 (newtons along -normal on the
- * robot); contact_normal points from the robot to the far side of the wall (Eq. 3).
+ * robot) of the last Newton step (at convergence: the equilibrium contact force); contact_normal points from the robot to the far side of the wall (Eq. 3).
  * base_reaction is the force and moment (global) that the clamp exerts on the last
  * prescribed node, i.e. F(x) at that node (Eq. 14-15).  residual is max |F - F_a + A_c^T y|
  * over the free DOFs at the last iterate. */

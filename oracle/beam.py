@@ -141,19 +141,6 @@ def consistent_tangent(xa, Ta, xb, Tb, sec, h=1e-30):
     return K
 
 
-def axial_geometric_stiffness(xa, Ta, xb, Tb, sec):
-    """Derivative of F through the chord direction only, at fixed axial force N:
-    N/l [[P, -P], [-P, P]] on the translations, P = I - e1 e1^T (exact K_T - K_M when the
-    element carries axial force alone)."""
-    dl, l, Rr = local_deformation(xa, Ta, xb, Tb, sec["l0"])
-    N = sec["EA"] / sec["l0"] * dl[0]
-    e1 = Rr[:, 0]
-    P = np.eye(3) - np.outer(e1, e1)
-    K = np.zeros((12, 12))
-    K[0:3, 0:3] = P; K[6:9, 6:9] = P; K[0:3, 6:9] = -P; K[6:9, 0:3] = -P
-    return N / l * K
-
-
 def linear_beam_stiffness(sec, axis, up):
     """Textbook 12 x 12 linear Euler-Bernoulli stiffness of a straight element along unit
     ``axis`` with section axis ``up`` (used to pin K_M at the undeformed state)."""

@@ -15,12 +15,13 @@ One call of ``Model.solve`` is one quasi-static step at a given cable tension an
     matrix W = A K^-1 A^T carries the compliance 1e-12 max(diag W) on its diagonal (rows of
     one node are dependent where four or more wall faces meet).
   * step limiter (Eq. 25-27): alpha = min(1, rho / max_i |du_i|) scales the whole step and
-    the multipliers; translations add, rotations update as T <- exp([alpha dtheta]x) T.  The
-    bound rho starts at beta0 and is halved whenever two consecutive Newton steps point against
-    each other (sum_i du_i . du_i^prev < 0), doubled back towards beta0 otherwise; a fixed beta0
-    lets a node on a faceted wall overshoot the crease between two facets forever.
-  * convergence: unlimited step (alpha = 1) with max_i max(|du_i|, r_o |dtheta_i|) <= tol and
-    the same contact set as the previous iteration.
+    the multipliers; translations add, rotations update as T <- exp([alpha dtheta]x) T.  A step
+    that points against the previous one (sum_i du_i . du_i^prev < 0) is an overshoot: it is
+    halved, and when it was clipped the bound rho is halved too; otherwise rho doubles back
+    towards beta0.  (A fixed beta0 lets a node on a faceted wall overshoot the crease between two
+    facets forever, and the material tangent overshoots the twist of a long bent span by ~2x.)
+  * convergence: unscaled step max_i max(|du_i|, r_o |dtheta_i|) <= tol and the same contact
+    set as the previous iteration.
   * warm start (follow the path): with a resident state at insertion delta_old, material
     point s takes the old position of material point s + (delta - delta_old) (linear in x,
     geodesic in T between nodes; straight along the tip axis beyond the old tip).
@@ -48,9 +49,7 @@ class Options:
     max_newton_iters: int = 200
     max_contact_iters: int = 4000
     max_contacts: int = 256
-    tangent_mode: int = 0          # 0: material tangent K_M; 1: symmetric part of K_T (K_M if not PD);
-                                   # 2: J = sym(K_T) - dF_a/dx (follower-load stiffness at the tip)
-                                   # 3: J = K_M + N/l (I - e1 e1^T) - dF_a/dx (axial geometric stiffness)
+    tangent_mode: int = 0          # 0: material tangent K_M; 1: symmetric part of K_T (K_M if not PD)
 
 
 @dataclass
@@ -153,12 +152,6 @@ class Model:
             F[6 * e:6 * e + 12] += Fe
             if mode == 0:
                 Ke = beam.material_tangent(x[e], R[e], x[e + 1], R[e + 1], self.sec)
-            elif mode == 2:
-                Kt = beam.consistent_tangent(x[e], R[e], x[e + 1], R[e + 1], self.sec)
-                Ke = 0.5 * (Kt + Kt.T)
-            elif mode == 3:
-                Ke = beam.material_tangent(x[e], R[e], x[e + 1], R[e + 1], self.sec)
-                Ke = Ke + beam.axial_geometric_stiffness(x[e], R[e], x[e + 1], R[e + 1], self.sec)
             else:
                 Kt = beam.consistent_tangent(x[e], R[e], x[e + 1], R[e + 1], self.sec)
                 Ke = 0.5 * (Kt + Kt.T)
@@ -215,29 +208,15 @@ class Model:
             Fa[6 * M:6 * M + 3] = f
             Fa[6 * M + 3:6 * M + 6] = mo
             g = (F - Fa)[6 * (k + 1):]
-            if opt.tangent_mode in (2, 3):
-                # J = K - dF_a/dx; the tip load T_M v has spin derivative -[T_M v]x
-                J = np.zeros((6 * nf, 6 * nf))
-                u = 11
-                for j in range(6 * nf):
-                    for i in range(max(0, j - u), j + 1):
-                        J[i, j] = ab[u + i - j, j]
-                        J[j, i] = ab[u + i - j, j]
-                t0 = 6 * (M - (k + 1))
-                J[t0:t0 + 3, t0 + 3:t0 + 6] += beam.skew(Fa[6 * M:6 * M + 3])
-                J[t0 + 3:t0 + 6, t0 + 3:t0 + 6] += beam.skew(Fa[6 * M + 3:6 * M + 6])
-                lu = sla.lu_factor(J)
-                solve = lambda rhs: sla.lu_solve(lu, rhs)
-            else:
-                try:
-                    c = sla.cholesky_banded(ab, lower=False)
-                except np.linalg.LinAlgError:
-                    if opt.tangent_mode == 0:
-                        status = E_NOT_SPD
-                        break
-                    _, ab = self.assemble(x, R, k, 0)
-                    c = sla.cholesky_banded(ab, lower=False)
-                solve = lambda rhs: sla.cho_solve_banded((c, False), rhs)
+            try:
+                c = sla.cholesky_banded(ab, lower=False)
+            except np.linalg.LinAlgError:
+                if opt.tangent_mode == 0:
+                    status = E_NOT_SPD
+                    break
+                _, ab = self.assemble(x, R, k, 0)
+                c = sla.cholesky_banded(ab, lower=False)
+            solve = lambda rhs: sla.cho_solve_banded((c, False), rhs)
             contacts = contact.detect(x, free, self.V, self.T, r_o, opt.activation_gap) if len(self.T) else []
             m = len(contacts)
             if m > opt.max_contacts:
@@ -258,7 +237,7 @@ class Model:
                 # makes the LCP uniquely solvable (interpenetration at most eps * y)
                 W = W + CONTACT_COMPLIANCE * np.max(np.diag(W)) * np.eye(m)
                 q = b - A @ dxf
-                y, w, piv = lcp.qp_nnls(W, q) if opt.tangent_mode in (0, 1) else lcp.murty(W, q)
+                y, w, piv = lcp.qp_nnls(W, q)
                 piv_total += piv
                 dx = dxf - X @ y
                 r = g + A.T @ y
@@ -272,23 +251,29 @@ class Model:
             dth = dx.reshape(nf, 6)[:, 3:]
             umax = float(np.sqrt((du * du).sum(axis=1)).max())
             step = float(max(umax, r_o * np.sqrt((dth * dth).sum(axis=1)).max()))
+            reverse = du_prev is not None and float(np.sum(du * du_prev)) < 0.0
             if du_prev is not None:
-                rev = float(np.sum(du * du_prev))
-                rho = max(0.5 * rho, opt.step_limit * 2.0 ** -20) if rev < 0.0 else min(2.0 * rho, opt.step_limit)
+                if not reverse:
+                    rho = min(2.0 * rho, opt.step_limit)
+                elif umax > rho:
+                    rho = max(0.5 * rho, opt.step_limit * 2.0 ** -20)
             du_prev = du.copy()
             alpha = 1.0 if umax <= rho else rho / umax
+            if reverse:
+                alpha *= 0.5
             for j, i in enumerate(free):
                 x[i] = x[i] + alpha * du[j]
                 R[i] = expm(alpha * dth[j]) @ R[i]
-            y = alpha * y
+            # Eq. 27 scales the multipliers of a limited step by alpha; the reported forces are the
+            # multipliers of the last (converged, sub-tolerance) step, i.e. the equilibrium forces
             if self.trace is not None:
                 self.trace.append((alpha, umax, step, residual, m))
             if getattr(self, "trace_detail", None) is not None:
                 jmax = int(np.argmax(np.sqrt((du * du).sum(axis=1))))
-                act = [(rec["node"], rec["tri"], round(float(yy), 4)) for rec, yy in zip(contacts, y / alpha if alpha > 0 else y) if yy > 0]
+                act = [(rec["node"], rec["tri"], round(float(yy), 4)) for rec, yy in zip(contacts, y) if yy > 0]
                 self.trace_detail.append((free[jmax], du[jmax].copy(), act))
             key = tuple((rec["node"], rec["tri"]) for rec in contacts)
-            if alpha == 1.0 and step <= opt.newton_tol and key == prev_key:
+            if step <= opt.newton_tol and key == prev_key:
                 status = OK
                 break
             prev_key = key

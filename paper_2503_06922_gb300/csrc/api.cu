@@ -595,7 +595,7 @@ accfem_status download(accfem_handle* h, accfem_status status, accfem_result* ou
           if (out->contact_point) out->contact_point[3 * i + a] = pt[3 * i + a];
           if (out->contact_normal) out->contact_normal[3 * i + a] = nn[3 * i + a];
         }
-        if (out->contact_force) out->contact_force[i] = c.alpha * y[i];
+        if (out->contact_force) out->contact_force[i] = y[i];
       }
     }
     if (m > out->contact_capacity && status == ACCFEM_OK) {

@@ -57,10 +57,11 @@ __global__ void __launch_bounds__(192) step_kernel(Params p, Dev d) {
   }
 }
 
-// Step limiter (Eq. 25-27 with an adaptive bound): rho is halved when the Newton step reverses
-// against the previous one (sum_i du_i . du_i^prev < 0, summed over the step blocks in a fixed
-// order), doubled back towards beta0 otherwise; alpha = min(1, rho / max |du|).  Also counts the
-// iteration and decides convergence (unlimited step below tol with an unchanged constraint set).
+// Step limiter (Eq. 25-27 with an adaptive bound): alpha = min(1, rho / max |du|).  A step that
+// points against the previous one (sum_i du_i . du_i^prev < 0, summed over the step blocks in a
+// fixed order) is an overshoot: it is halved, and when it was clipped rho is halved too; otherwise
+// rho doubles back towards beta0.  Also counts the iteration and decides convergence (unscaled
+// step below tol with an unchanged constraint set).
 __global__ void limiter_kernel(Params p, Dev d) {
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged || threadIdx.x != 0) return;
@@ -68,15 +69,20 @@ __global__ void limiter_kernel(Params p, Dev d) {
   double rev = 0.0;
   for (int b = 0; b < nb; ++b) rev += d.rev_part[b];
   double rho = ctl->rho;
-  if (ctl->has_prev) rho = rev < 0.0 ? fmax(0.5 * rho, p.beta0 * 9.5367431640625e-07) : fmin(2.0 * rho, p.beta0);
   const double umax = __longlong_as_double((long long)ctl->umax_bits);
   const double step = __longlong_as_double((long long)ctl->step_bits);
-  const double alpha = umax <= rho ? 1.0 : rho / umax;
+  const bool reverse = ctl->has_prev && rev < 0.0;
+  if (ctl->has_prev) {
+    if (!reverse) rho = fmin(2.0 * rho, p.beta0);
+    else if (umax > rho) rho = fmax(0.5 * rho, p.beta0 * 9.5367431640625e-07);   // beta0 / 2^20
+  }
+  double alpha = umax <= rho ? 1.0 : rho / umax;
+  if (reverse) alpha *= 0.5;
   ctl->rho = rho;
   ctl->has_prev = 1;
   ctl->alpha = alpha;
   ctl->iter += 1;
-  if (alpha == 1.0 && step <= p.tol && ctl->same_set) ctl->converged = 2;   // 2: apply this last step
+  if (step <= p.tol && ctl->same_set) ctl->converged = 2;   // 2: apply this last step
 }
 
 // x <- x + alpha du, T <- exp([alpha dtheta]x) T.
