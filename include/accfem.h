@@ -165,6 +165,27 @@ typedef enum {
  * of one launch in *us, measured with CUDA events on the handle's stream.  For measurement. */
 accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t reps, double* us);
 
+/* Collision query that allocates no memory, for callers that cannot call cudaMalloc while they run
+ * (for example code inside CUDA stream capture, where allocation calls are not allowed, or a
+ * real-time loop running under a fixed device-memory budget).  The paper has no counterpart: it is
+ * the constraint detection of accfem_solve for n_nodes caller positions (device memory, 3 doubles
+ * each, node i = entry i) against the handle's lumen, with the same rule and results as the rows
+ * accfem_solve reports.  Inputs and outputs are caller-owned DEVICE buffers: up to row_capacity
+ * rows are written in (node, triangle) order to row_node, row_tri, row_point (3 per row),
+ * row_normal (3 per row) and row_gap (the b_i of Eq. 10); *n_rows (device int32) receives the
+ * total row count.  The work runs on stream (a cudaStream_t; NULL = the handle's stream) and the
+ * call waits for it.  Per-node scratch lives in one fixed device array of the library sized for
+ * n_nodes <= 4096 (about 2 MB, held by every GPU that loads the library until the process exits);
+ * larger n_nodes returns ACCFEM_E_INVALID_ARG.  ACCFEM_E_CONTACT_CAPACITY when a node has more
+ * candidates or rows than the fixed per-node limits or the rows exceed row_capacity.  The first
+ * call on a device looks up the array's device address; make that first call before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU (other streams or
+ * threads) race and must not be issued concurrently. */
+accfem_status accfem_detect_contacts_noalloc(accfem_handle* h, const double* node_pos, int32_t n_nodes,
+                                             int32_t row_capacity, int32_t* row_node, int32_t* row_tri,
+                                             double* row_point, double* row_normal, double* row_gap,
+                                             int32_t* n_rows, void* stream);
+
 /* Copies the resident nodal poses (3*(M+1) and 4*(M+1) doubles) to host buffers. */
 accfem_status accfem_get_state(accfem_handle* h, double* node_pos, double* node_quat);
 

@@ -52,7 +52,7 @@ class accfem_state(ctypes.Structure):
 EXPORTS = ["accfem_default_options", "accfem_create", "accfem_solve", "accfem_solve_tip_load",
            "accfem_solve_resident", "accfem_reset", "accfem_set_stream", "accfem_transfer_bytes",
            "accfem_time_kernel", "accfem_get_state", "accfem_kernel_launches", "accfem_destroy",
-           "accfem_status_string", "accfem_last_error"]
+           "accfem_status_string", "accfem_last_error", "accfem_detect_contacts_noalloc"]
 
 KERNEL_ELEMENT, KERNEL_COLLIDE, KERNEL_ASSEMBLE, KERNEL_CONTACT = range(4)
 
@@ -80,6 +80,9 @@ def load(path=LIB_PATH):
     lib.accfem_set_stream.argtypes = [H, ctypes.c_void_p]
     lib.accfem_transfer_bytes.argtypes = [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.accfem_time_kernel.argtypes = [H, ctypes.c_int, ctypes.c_int32, _dp]
+    lib.accfem_detect_contacts_noalloc.argtypes = [H, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_void_p]
     lib.accfem_kernel_launches.argtypes = [H]
     lib.accfem_kernel_launches.restype = ctypes.c_int64
     lib.accfem_destroy.argtypes = [H]
@@ -90,7 +93,7 @@ def load(path=LIB_PATH):
     lib.accfem_last_error.restype = ctypes.c_char_p
     for name in ("accfem_default_options", "accfem_create", "accfem_solve", "accfem_solve_tip_load",
                  "accfem_solve_resident", "accfem_get_state", "accfem_reset", "accfem_set_stream",
-                 "accfem_transfer_bytes", "accfem_time_kernel"):
+                 "accfem_transfer_bytes", "accfem_time_kernel", "accfem_detect_contacts_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -227,6 +230,14 @@ class AccFem:
         if st != OK:
             raise RuntimeError("accfem_time_kernel failed: %s" % self.accfem_last_error())
         return float(us.value)
+
+    def accfem_detect_contacts_noalloc(self, node_pos, n_nodes, row_capacity, row_node, row_tri, row_point,
+                                       row_normal, row_gap, n_rows, stream=0):
+        """Device pointers (ints) throughout; see include/accfem.h.  Returns the status code."""
+        v = lambda x: ctypes.c_void_p(int(x)) if x else None
+        return int(self._lib.accfem_detect_contacts_noalloc(self.h, v(node_pos), int(n_nodes), int(row_capacity),
+                                                            v(row_node), v(row_tri), v(row_point), v(row_normal),
+                                                            v(row_gap), v(n_rows), v(stream)))
 
     def accfem_kernel_launches(self):
         return int(self._lib.accfem_kernel_launches(self.h))

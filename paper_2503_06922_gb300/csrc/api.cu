@@ -715,3 +715,16 @@ accfem_status accfem_get_state(accfem_handle* h, double* node_pos, double* node_
 }
 
 }  // extern "C"
+
+// Internal views used by the allocation-free collision query (noalloc.cu).
+bool accfem_internal_views(accfem_handle* h, Params* p, Dev* d, cudaStream_t* stream) {
+  if (!h) return false;
+  *p = h->p;
+  *d = h->d;
+  *stream = h->work();
+  return true;
+}
+
+void accfem_internal_set_error(accfem_handle* h, const char* msg) {
+  if (h) h->err = msg ? msg : "";
+}
