@@ -73,7 +73,7 @@ typedef struct {
  * newton_tol 1e-11 m (stop when the unlimited step has max(|du_i|, r_o |dtheta_i|) below it
  * and the constraint set did not change), contact_tol 1e-11 (relative sign tolerance of the
  * LCP pivoting), max_newton_iters 200, max_contact_iters 1000, max_contacts 256 (constraint
- * rows), tangent_mode 0 (material tangent K = B^T K_l B; the only mode on the GPU). */
+ * rows, at most 512), tangent_mode 0 (material tangent K = B^T K_l B; the only mode on the GPU). */
 typedef struct {
   double activation_gap, step_limit, newton_tol, contact_tol;
   int32_t max_newton_iters, max_contact_iters, max_contacts, tangent_mode;

@@ -180,7 +180,7 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
       (lumen->n_triangles > 0 && (!lumen->vertices || !lumen->triangles)))
     return ACCFEM_E_INVALID_ARG;
   if (!(opt.activation_gap >= 0) || !(opt.step_limit > 0) || !(opt.newton_tol > 0) || !(opt.contact_tol >= 0) ||
-      opt.max_newton_iters < 1 || opt.max_contact_iters < 1 || opt.max_contacts < 1 || opt.max_contacts > 4096 ||
+      opt.max_newton_iters < 1 || opt.max_contact_iters < 1 || opt.max_contacts < 1 || opt.max_contacts > 512 ||
       opt.tangent_mode != 0)
     return ACCFEM_E_INVALID_ARG;
   // entrance frame
@@ -294,15 +294,26 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
     for (int64_t t = 0; t < T; ++t) ctri[fillp[cell_of[t]]++] = (int)t;
   }
   std::vector<float> tri32(9 * std::max<int64_t>(T, 1));
+  std::vector<float> sph32(4 * std::max<int64_t>(T, 1));
   for (int64_t c = 0; c < ncell; ++c) {
     int cz = (int)(c / ((int64_t)p.g_dim[0] * p.g_dim[1]));
     int cy = (int)((c / p.g_dim[0]) % p.g_dim[1]);
     int cx = (int)(c % p.g_dim[0]);
     double ctr[3] = {p.g_org[0] + (cx + 0.5) * p.g_h, p.g_org[1] + (cy + 0.5) * p.g_h, p.g_org[2] + (cz + 0.5) * p.g_h};
     for (int s = cstart[c]; s < cstart[c + 1]; ++s) {
-      const int32_t* tv = lumen->triangles + 3 * (int64_t)ctri[s];
+      const int64_t t = ctri[s];
+      const int32_t* tv = lumen->triangles + 3 * t;
       for (int v = 0; v < 3; ++v)
         for (int k = 0; k < 3; ++k) tri32[9 * (int64_t)s + 3 * v + k] = (float)(lumen->vertices[3 * tv[v] + k] - ctr[k]);
+      // bounding sphere about the centroid, radius rounded up so the FP32 test stays conservative
+      double rad = 0.0;
+      for (int v = 0; v < 3; ++v) {
+        double dx = lumen->vertices[3 * tv[v]] - cen[3 * t], dy = lumen->vertices[3 * tv[v] + 1] - cen[3 * t + 1],
+               dz = lumen->vertices[3 * tv[v] + 2] - cen[3 * t + 2];
+        rad = std::max(rad, std::sqrt(dx * dx + dy * dy + dz * dz));
+      }
+      for (int k = 0; k < 3; ++k) sph32[4 * (int64_t)s + k] = (float)(cen[3 * t + k] - ctr[k]);
+      sph32[4 * (int64_t)s + 3] = (float)(rad * (1.0 + 1e-6) + 1e-9);
     }
   }
 
@@ -320,8 +331,9 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
             dalloc(h, &d.oqy, N) && dalloc(h, &d.oqz, N) && dalloc(h, &d.elem, (size_t)M * kElemStride);
   int *cs = nullptr, *ct = nullptr, *tv = nullptr;
   float* t32 = nullptr;
+  float* s32 = nullptr;
   double *vv = nullptr, *nfc_d = nullptr;
-  ok = ok && dalloc(h, &cs, ncell + 1) && dalloc(h, &ct, std::max<int64_t>(T, 1)) && dalloc(h, &t32, tri32.size()) &&
+  ok = ok && dalloc(h, &cs, ncell + 1) && dalloc(h, &ct, std::max<int64_t>(T, 1)) && dalloc(h, &t32, tri32.size()) && dalloc(h, &s32, sph32.size()) &&
        dalloc(h, &vv, std::max<int64_t>(3 * NV, 1)) && dalloc(h, &tv, std::max<int64_t>(3 * T, 1)) &&
        dalloc(h, &nfc_d, std::max<int64_t>(3 * T, 1));
   ok = ok && dalloc(h, &d.ncon, nfc) && dalloc(h, &d.con_tri, (size_t)nfc * kCpn) &&
@@ -336,7 +348,7 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
        dalloc(h, &d.dx, (size_t)nfc * 6) && dalloc(h, &d.du_prev, (size_t)nfc * 3) &&
        dalloc(h, &d.rev_part, (size_t)nfc / 32 + 2) && dalloc(h, &d.W, (size_t)mc * mc) && dalloc(h, &d.q, mc) &&
        dalloc(h, &d.y, mc) && dalloc(h, &d.w, mc) && dalloc(h, &d.gj, (size_t)mc * (mc + 2)) &&
-       dalloc(h, &d.inP, mc) && dalloc(h, &d.plist, mc) && dalloc(h, &d.ctl, 1);
+       dalloc(h, &d.inP, mc) && dalloc(h, &d.plist, mc) && dalloc(h, &d.wcol, mc) && dalloc(h, &d.ctl, 1);
   if (!ok) {
     accfem_destroy(h);
     return ACCFEM_E_NOMEM;
@@ -344,6 +356,7 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
   ok = cuda_ok(h, cudaMemcpy(cs, cstart.data(), sizeof(int) * (ncell + 1), cudaMemcpyHostToDevice), "upload grid") &&
        (T == 0 || cuda_ok(h, cudaMemcpy(ct, ctri.data(), sizeof(int) * T, cudaMemcpyHostToDevice), "upload grid")) &&
        (T == 0 || cuda_ok(h, cudaMemcpy(t32, tri32.data(), sizeof(float) * 9 * T, cudaMemcpyHostToDevice), "upload grid")) &&
+       (T == 0 || cuda_ok(h, cudaMemcpy(s32, sph32.data(), sizeof(float) * 4 * T, cudaMemcpyHostToDevice), "upload grid")) &&
        (NV == 0 || cuda_ok(h, cudaMemcpy(vv, lumen->vertices, sizeof(double) * 3 * NV, cudaMemcpyHostToDevice), "upload mesh")) &&
        (T == 0 || cuda_ok(h, cudaMemcpy(tv, lumen->triangles, sizeof(int) * 3 * T, cudaMemcpyHostToDevice), "upload mesh")) &&
        (T == 0 || cuda_ok(h, cudaMemcpy(nfc_d, nface.data(), sizeof(double) * 3 * T, cudaMemcpyHostToDevice), "upload mesh"));
@@ -351,7 +364,7 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
     accfem_destroy(h);
     return ACCFEM_E_CUDA;
   }
-  d.cell_start = cs; d.cell_tri = ct; d.tri32 = t32; d.V = vv; d.T = tv; d.nface = nfc_d;
+  d.cell_start = cs; d.cell_tri = ct; d.tri32 = t32; d.sph32 = s32; d.V = vv; d.T = tv; d.nface = nfc_d;
   if (cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess) { accfem_destroy(h); return ACCFEM_E_NOMEM; }
   h->stage_bytes = sizeof(double) * (size_t)std::max<int64_t>(7 * N, 16 * (int64_t)mc + 64);
   if (cudaMallocHost(&h->h_stage, h->stage_bytes) != cudaSuccess) { accfem_destroy(h); return ACCFEM_E_NOMEM; }
@@ -379,19 +392,19 @@ int enqueue_iteration(accfem_handle* h, int nf, cudaStream_t st, cudaGraphCondit
   collide_kernel<<<(nf + 3) / 4, 128, 0, st>>>(p, d); ++n;
   compact_kernel<<<1, 1024, 0, st>>>(p, d); ++n;
   assemble_kernel<<<nf, 96, 0, st>>>(p, d); ++n;
-  rhs_kernel<<<nf, dim3(32, 6), 0, st>>>(p, d); ++n;
+  rhs_kernel<<<dim3(nf, kRhsSplit), dim3(32, 6), 0, st>>>(p, d); ++n;
   std::vector<int> strides;
   for (int s = 1; s < nf; s *= 2) strides.push_back(s);
   for (int s : strides) {
     bcr_elim_kernel<<<(nf - s - 1) / (2 * s) + 1, 64, 0, st>>>(p, d, s); ++n;
-    bcr_keep_kernel<<<(nf - 1) / (2 * s) + 1, 192, 0, st>>>(p, d, s); ++n;
+    bcr_keep_kernel<<<dim3((nf - 1) / (2 * s) + 1, kRhsSplit), 192, 0, st>>>(p, d, s); ++n;
   }
-  bcr_root_kernel<<<1, 192, 0, st>>>(p, d); ++n;
+  bcr_root_kernel<<<dim3(1, kRhsSplit), 192, 0, st>>>(p, d); ++n;
   for (int si = (int)strides.size() - 1; si >= 0; --si) {
     int s = strides[si];
-    bcr_bwd_kernel<<<(nf - s - 1) / (2 * s) + 1, 192, 0, st>>>(p, d, s); ++n;
+    bcr_bwd_kernel<<<dim3((nf - s - 1) / (2 * s) + 1, kRhsSplit), 192, 0, st>>>(p, d, s); ++n;
   }
-  contact_kernel<<<1, 1024, 0, st>>>(p, d); ++n;
+  contact_kernel<<<1, 256, 0, st>>>(p, d); ++n;
   step_kernel<<<(nf + 31) / 32, dim3(32, 6), 0, st>>>(p, d); ++n;
   limiter_kernel<<<1, 32, 0, st>>>(p, d); ++n;
   apply_kernel<<<(nf + 127) / 128, 128, 0, st>>>(p, d); ++n;
@@ -680,7 +693,7 @@ accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t
         element_kernel<<<(nf + kWarpsPerElemBlock - 1) / kWarpsPerElemBlock, 32 * kWarpsPerElemBlock, 0, st>>>(p, d); break;
       case ACCFEM_KERNEL_COLLIDE: collide_kernel<<<(nf + 3) / 4, 128, 0, st>>>(p, d); break;
       case ACCFEM_KERNEL_ASSEMBLE: assemble_kernel<<<nf, 96, 0, st>>>(p, d); break;
-      default: contact_kernel<<<1, 1024, 0, st>>>(p, d); break;
+      default: contact_kernel<<<1, 256, 0, st>>>(p, d); break;
     }
   };
   launch();

@@ -157,14 +157,14 @@ __global__ void __launch_bounds__(96) assemble_kernel(Params p, Dev d) {
 }
 
 // RHS columns: 0 = -g, 1 + row = A^T e_row (unit normal on the row's node translation).
-// One block of (32 rhs, 6 comps) per free node, looping over chunks of 32 columns.
+// Blocks (node, y) of (32 rhs, 6 comps); block y handles the column chunks y, y + kRhsSplit, ...
 __global__ void __launch_bounds__(192) rhs_kernel(Params p, Dev d) {
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
   const int f = blockIdx.x, c = threadIdx.y;
   if (f >= ctl->nf) return;
   const int nrhs = ctl->m + 1;
-  for (int r = threadIdx.x; r < nrhs; r += 32) {
+  for (int r = blockIdx.y * 32 + threadIdx.x; r < nrhs; r += 32 * kRhsSplit) {
     double v;
     if (r == 0) v = -d.g[(size_t)f * 6 + c];
     else v = (d.c_node[r - 1] == f && c < 3) ? d.c_n[3 * (r - 1) + c] : 0.0;
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(192) bcr_keep_kernel(Params p, Dev d, int s) {
     sUr[tid] = hr2 ? d.U[(size_t)(i + s) * 36 + tid] : 0.0;
   }
   __syncthreads();
-  if (tid < 36) {
+  if (tid < 36 && blockIdx.y == 0) {
     const int r = tid / 6, c = tid % 6;
     double dd = d.D[(size_t)i * 36 + tid];
     double un = 0.0;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(192) bcr_keep_kernel(Params p, Dev d, int s) {
   const int lane = tid & 31, c = tid >> 5;
   const int nrhs = ctl->m + 1;
   const size_t ld = p.nrhs_cap;
-  for (int r = lane; r < nrhs; r += 32) {
+  for (int r = blockIdx.y * 32 + lane; r < nrhs; r += 32 * kRhsSplit) {
     double acc = d.B[((size_t)i * 6 + c) * ld + r];
     if (hl) {
       const double* b = d.B + (size_t)(i - s) * 6 * ld + r;
@@ -297,11 +297,11 @@ __global__ void __launch_bounds__(192) bcr_root_kernel(Params p, Dev d) {
     if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
     return;
   }
-  if (tid < 36) d.P[tid] = sA[tid];
+  if (tid < 36 && blockIdx.y == 0) d.P[tid] = sA[tid];
   const int lane = tid & 31, c = tid >> 5;
   const int nrhs = ctl->m + 1;
   const size_t ld = p.nrhs_cap;
-  for (int r0 = 0; r0 < nrhs; r0 += 32) {
+  for (int r0 = blockIdx.y * 32; r0 < nrhs; r0 += 32 * kRhsSplit) {
     const int r = r0 + lane;
     const bool act = r < nrhs;
     double b[6];
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(192) bcr_bwd_kernel(Params p, Dev d, int s) {
   const int lane = tid & 31, c = tid >> 5;
   const int nrhs = ctl->m + 1;
   const size_t ld = p.nrhs_cap;
-  for (int r0 = 0; r0 < nrhs; r0 += 32) {
+  for (int r0 = blockIdx.y * 32; r0 < nrhs; r0 += 32 * kRhsSplit) {
     const int r = r0 + lane;
     const bool act = r < nrhs;
     double b[6];

@@ -8,147 +8,226 @@
 // Rows with the same closest point (within 1e-12 m) are merged, keeping the lowest index.
 //
 // Work split: triangles are binned by centroid in a uniform grid; a node scans the cells of the
-// box p +- (r_o + gap + max triangle radius).  Pass 1 computes FP32 distances (coordinates
+// box p +- (r_o + gap + max triangle radius).  A triangle whose FP32 bounding sphere stays beyond
+// the activation distance (+ eps_d) is skipped.  Pass 1 computes FP32 distances (coordinates
 // relative to the cell centre, so |x| is a few mm and the FP32 error a few 1e-9 m) and their
 // warp minimum; pass 2 keeps a triangle for the exact FP64 test when its FP32 distance is within
 // eps_d of the activation distance AND (its FP32 barycentrics are inside up to eps_b, or its
-// FP32 distance is within 2 eps_d of the minimum).  Every triangle that can form a row in FP64
-// passes, so the FP64 decisions below see the same candidates as a full scan.
+// FP32 distance is within 2 eps_d of the minimum); survivors are compacted by warp ballot.  Every
+// triangle that can form a row in FP64 passes, so the FP64 decisions below see the same candidates
+// as a full scan.  The FP64 closest points, the overall minimum, the merge of equal points and the
+// ordering by triangle index are spread over the lanes (one survivor per lane).
 #include "common.cuh"
 #include "collide_geom.cuh"
 
 namespace accfem {
 
 __global__ void __launch_bounds__(128) collide_kernel(Params p, Dev d) {
+  __shared__ int s_list[4][kSurvCap];                 // sorted slots kept for the FP64 test
   __shared__ Surv s_surv[4][kSurvCap];
-  __shared__ int s_ns[4];
+  __shared__ int s_cand[4][kCandCap];                 // slots whose bounding sphere reaches thr
+  __shared__ float s_cd[4][kCandCap];                 // their FP32 distances (negative: near-inside flag)
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
   Ctl* ctl = d.ctl;
   const int f = blockIdx.x * 4 + wib;
   if (ctl->status != 0 || ctl->converged || f >= ctl->nf) return;
   const int node = ctl->k + 1 + f;
-  if (lane == 0) s_ns[wib] = 0;
-  __syncwarp();
   const double pn[3] = {d.px[node], d.py[node], d.pz[node]};
   const double thr = p.r_o + p.act;
-  int lo[3], hi[3];
+  int lo[3], nc3[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     lo[a] = (int)floor((pn[a] - p.g_rq - p.g_org[a]) / p.g_h);
-    hi[a] = (int)floor((pn[a] + p.g_rq - p.g_org[a]) / p.g_h);
-    lo[a] = max(lo[a], 0); hi[a] = min(hi[a], p.g_dim[a] - 1);
+    int hi = (int)floor((pn[a] + p.g_rq - p.g_org[a]) / p.g_h);
+    lo[a] = max(lo[a], 0); hi = min(hi, p.g_dim[a] - 1);
+    nc3[a] = max(hi - lo[a] + 1, 0);
   }
+  const int ncell = nc3[0] * nc3[1] * nc3[2];
   const float thr32 = (float)(thr + p.eps_d);
-  // ---- pass 1: FP32 minimum distance over the candidates
-  float dmin = 3.0e38f;
-  for (int cz = lo[2]; cz <= hi[2]; ++cz)
-    for (int cy = lo[1]; cy <= hi[1]; ++cy)
-      for (int cx = lo[0]; cx <= hi[0]; ++cx) {
-        int cell = (cz * p.g_dim[1] + cy) * p.g_dim[0] + cx;
-        int s0 = d.cell_start[cell], s1 = d.cell_start[cell + 1];
-        if (s0 == s1) continue;
-        float pc[3] = {(float)(pn[0] - (p.g_org[0] + (cx + 0.5) * p.g_h)),
-                       (float)(pn[1] - (p.g_org[1] + (cy + 0.5) * p.g_h)),
-                       (float)(pn[2] - (p.g_org[2] + (cz + 0.5) * p.g_h))};
-        for (int s = s0 + lane; s < s1; s += 32) {
-          float va, vb, vc;
-          float d2 = tri_dist2_f32(pc, d.tri32 + (size_t)s * 9, va, vb, vc);
-          dmin = fminf(dmin, sqrtf(d2));
+  // ---- one sweep: cell ranges loaded by the lanes, triangles by the lanes, candidates compacted
+  int nca = 0;
+  for (int c0 = 0; c0 < ncell; c0 += 32) {
+    int cs0 = 0, cs1 = 0, cx = 0, cy = 0, cz = 0;
+    if (c0 + lane < ncell) {
+      int q = c0 + lane;
+      cx = lo[0] + q % nc3[0];
+      cy = lo[1] + (q / nc3[0]) % nc3[1];
+      cz = lo[2] + q / (nc3[0] * nc3[1]);
+      int cell = (cz * p.g_dim[1] + cy) * p.g_dim[0] + cx;
+      cs0 = d.cell_start[cell];
+      cs1 = d.cell_start[cell + 1];
+    }
+    unsigned nonempty = __ballot_sync(0xffffffffu, cs1 > cs0);
+    while (nonempty) {
+      const int src = __ffs(nonempty) - 1;
+      nonempty &= nonempty - 1;
+      const int s0 = __shfl_sync(0xffffffffu, cs0, src), s1 = __shfl_sync(0xffffffffu, cs1, src);
+      const int gx = __shfl_sync(0xffffffffu, cx, src), gy = __shfl_sync(0xffffffffu, cy, src),
+                gz = __shfl_sync(0xffffffffu, cz, src);
+      const float pc[3] = {(float)(pn[0] - (p.g_org[0] + (gx + 0.5) * p.g_h)),
+                           (float)(pn[1] - (p.g_org[1] + (gy + 0.5) * p.g_h)),
+                           (float)(pn[2] - (p.g_org[2] + (gz + 0.5) * p.g_h))};
+      for (int s0l = s0; s0l < s1; s0l += 32) {
+        const int s = s0l + lane;
+        bool keep = false;
+        float code = 0.f;
+        if (s < s1) {
+          float4 sp = reinterpret_cast<const float4*>(d.sph32)[s];
+          float dx = pc[0] - sp.x, dy = pc[1] - sp.y, dz = pc[2] - sp.z, rr = thr32 + sp.w;
+          if (dx * dx + dy * dy + dz * dz <= rr * rr) {
+            float va, vb, vc;
+            float dd = sqrtf(tri_dist2_f32(pc, d.tri32 + (size_t)s * 9, va, vb, vc));
+            float tol = -p.eps_b * (va + vb + vc);
+            bool near_in = (va >= tol) && (vb >= tol) && (vc >= tol);
+            keep = dd <= thr32;
+            code = near_in ? -1.f - dd : dd;             // sign carries the near-inside flag
+          }
         }
+        unsigned mk = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+          int pos = nca + __popc(mk & lt_mask);
+          if (pos < kCandCap) { s_cand[wib][pos] = s; s_cd[wib][pos] = code; }
+        }
+        nca += __popc(mk);
       }
+    }
+  }
+  __syncwarp();
+  if (nca > kCandCap) {
+    if (lane == 0) atomicCAS(&ctl->status, 0, ST_CAPACITY);
+    return;
+  }
+  // ---- FP32 minimum and the exact-test filter
+  float dmin = 3.0e38f;
+  for (int i = lane; i < nca; i += 32) {
+    float c = s_cd[wib][i];
+    dmin = fminf(dmin, c < 0.f ? -1.f - c : c);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
   const float dmin_keep = dmin + (float)(2.0 * p.eps_d);
-  // ---- pass 2: survivors -> exact FP64 closest points
-  for (int cz = lo[2]; cz <= hi[2]; ++cz)
-    for (int cy = lo[1]; cy <= hi[1]; ++cy)
-      for (int cx = lo[0]; cx <= hi[0]; ++cx) {
-        int cell = (cz * p.g_dim[1] + cy) * p.g_dim[0] + cx;
-        int s0 = d.cell_start[cell], s1 = d.cell_start[cell + 1];
-        if (s0 == s1) continue;
-        float pc[3] = {(float)(pn[0] - (p.g_org[0] + (cx + 0.5) * p.g_h)),
-                       (float)(pn[1] - (p.g_org[1] + (cy + 0.5) * p.g_h)),
-                       (float)(pn[2] - (p.g_org[2] + (cz + 0.5) * p.g_h))};
-        for (int s0l = s0; s0l < s1; s0l += 32) {
-          int s = s0l + lane;
-          bool keep = false;
-          if (s < s1) {
-            float va, vb, vc;
-            float dd = sqrtf(tri_dist2_f32(pc, d.tri32 + (size_t)s * 9, va, vb, vc));
-            float den = va + vb + vc;
-            float tol = -p.eps_b * den;
-            bool near_in = (va >= tol) && (vb >= tol) && (vc >= tol);
-            keep = (dd <= thr32) && (near_in || dd <= dmin_keep);
-          }
-          if (keep) {
-            int t = d.cell_tri[s];
-            const int* tv = d.T + 3 * (size_t)t;
-            double A[3] = {d.V[3 * tv[0]], d.V[3 * tv[0] + 1], d.V[3 * tv[0] + 2]};
-            double Bv[3] = {d.V[3 * tv[1]], d.V[3 * tv[1] + 1], d.V[3 * tv[1] + 2]};
-            double Cv[3] = {d.V[3 * tv[2]], d.V[3 * tv[2] + 1], d.V[3 * tv[2] + 2]};
-            Surv sv;
-            sv.t = t;
-            sv.d2 = tri_closest_f64(pn, A, Bv, Cv, sv.c, &sv.interior);
-            int slot = atomicAdd(&s_ns[wib], 1);
-            if (slot < kSurvCap) s_surv[wib][slot] = sv;
-          }
-        }
-      }
+  int ns = 0;
+  for (int i0 = 0; i0 < nca; i0 += 32) {
+    const int i = i0 + lane;
+    bool keep = false;
+    if (i < nca) {
+      float c = s_cd[wib][i];
+      keep = c < 0.f || c <= dmin_keep;
+    }
+    unsigned mk = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      int pos = ns + __popc(mk & lt_mask);
+      if (pos < kSurvCap) s_list[wib][pos] = s_cand[wib][i];
+    }
+    ns += __popc(mk);
+  }
   __syncwarp();
-  const int ns = s_ns[wib];
   if (ns > kSurvCap) {
     if (lane == 0) atomicCAS(&ctl->status, 0, ST_CAPACITY);
     return;
   }
-  // ---- lane 0: global argmin, rows, merge, order by triangle index
-  if (lane == 0) {
-    int g = -1;
-    double gd = 0.0;
-    for (int i = 0; i < ns; ++i) {
+  // ---- exact FP64 closest points, one survivor per lane
+  for (int i = lane; i < ns; i += 32) {
+    int t = d.cell_tri[s_list[wib][i]];
+    const int* tv = d.T + 3 * (size_t)t;
+    double A[3] = {d.V[3 * tv[0]], d.V[3 * tv[0] + 1], d.V[3 * tv[0] + 2]};
+    double Bv[3] = {d.V[3 * tv[1]], d.V[3 * tv[1] + 1], d.V[3 * tv[1] + 2]};
+    double Cv[3] = {d.V[3 * tv[2]], d.V[3 * tv[2] + 1], d.V[3 * tv[2] + 2]};
+    Surv sv;
+    sv.t = t;
+    sv.d2 = tri_closest_f64(pn, A, Bv, Cv, sv.c, &sv.interior);
+    s_surv[wib][i] = sv;
+  }
+  __syncwarp();
+  // ---- overall closest survivor g: (d2, triangle index) minimum
+  double gd = 1.0e300;
+  int gt = 0x7fffffff;
+  for (int i = lane; i < ns; i += 32) {
+    const Surv& sv = s_surv[wib][i];
+    if (sv.d2 < gd || (sv.d2 == gd && sv.t < gt)) { gd = sv.d2; gt = sv.t; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double od = __shfl_xor_sync(0xffffffffu, gd, o);
+    int ot = __shfl_xor_sync(0xffffffffu, gt, o);
+    if (od < gd || (od == gd && ot < gt)) { gd = od; gt = ot; }
+  }
+  // ---- qualifying survivors: within r_o + gap, and interior or the overall closest
+  bool qual[2] = {false, false};
+  double dist[2] = {0.0, 0.0};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    int i = lane + 32 * h;
+    if (i < ns) {
       const Surv& sv = s_surv[wib][i];
-      if (g < 0 || sv.d2 < gd || (sv.d2 == gd && sv.t < s_surv[wib][g].t)) { g = i; gd = sv.d2; }
+      dist[h] = sqrt(sv.d2);
+      qual[h] = (dist[h] <= thr) && (sv.interior || sv.t == gt);
     }
-    // insertion sort survivors by triangle index
-    int ord[kSurvCap];
-    for (int i = 0; i < ns; ++i) {
-      int j = i;
-      while (j > 0 && s_surv[wib][ord[j - 1]].t > s_surv[wib][i].t) { ord[j] = ord[j - 1]; --j; }
-      ord[j] = i;
-    }
-    int nc = 0;
-    int* ctri = d.con_tri + (size_t)f * kCpn;
-    double* cpt = d.con_pt + (size_t)f * kCpn * 3;
-    double* cn = d.con_n + (size_t)f * kCpn * 3;
-    double* cg = d.con_gap + (size_t)f * kCpn;
-    for (int oi = 0; oi < ns; ++oi) {
-      const Surv& sv = s_surv[wib][ord[oi]];
-      double dist = sqrt(sv.d2);
-      if (!(dist <= thr)) continue;
-      if (!(sv.interior || ord[oi] == g)) continue;
-      bool dup = false;
-      for (int r = 0; r < nc; ++r) {
-        double dx = cpt[3 * r] - sv.c[0], dy = cpt[3 * r + 1] - sv.c[1], dz = cpt[3 * r + 2] - sv.c[2];
+  }
+  // ---- merge equal closest points (lowest triangle index stays), rank by triangle index
+  unsigned qm0 = __ballot_sync(0xffffffffu, qual[0]);
+  unsigned qm1 = __ballot_sync(0xffffffffu, qual[1]);
+  bool kept[2] = {false, false};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    int i = lane + 32 * h;
+    if (!qual[h]) continue;
+    const Surv& si = s_surv[wib][i];
+    bool dup = false;
+    for (int hh = 0; hh < 2 && !dup; ++hh) {
+      unsigned mk = hh == 0 ? qm0 : qm1;
+      while (mk) {
+        int jl = __ffs(mk) - 1;
+        mk &= mk - 1;
+        int j = jl + 32 * hh;
+        const Surv& sj = s_surv[wib][j];
+        if (sj.t >= si.t) continue;
+        double dx = sj.c[0] - si.c[0], dy = sj.c[1] - si.c[1], dz = sj.c[2] - si.c[2];
         if (sqrt(dx * dx + dy * dy + dz * dz) <= 1e-12) { dup = true; break; }
       }
-      if (dup) continue;
-      if (nc >= kCpn) { atomicCAS(&ctl->status, 0, ST_CAPACITY); break; }
-      const double* nf = d.nface + 3 * (size_t)sv.t;
-      double n[3];
-      double cmp[3] = {sv.c[0] - pn[0], sv.c[1] - pn[1], sv.c[2] - pn[2]};
-      if (sv.interior || dist < 1e-12) { n[0] = nf[0]; n[1] = nf[1]; n[2] = nf[2]; }
-      else {
-        double sgn = (dot3(nf, cmp) > 0.0) ? 1.0 : -1.0;
-        double id = sgn / dist;
-        n[0] = cmp[0] * id; n[1] = cmp[1] * id; n[2] = cmp[2] * id;
-      }
-      ctri[nc] = sv.t;
-      cpt[3 * nc] = sv.c[0]; cpt[3 * nc + 1] = sv.c[1]; cpt[3 * nc + 2] = sv.c[2];
-      cn[3 * nc] = n[0]; cn[3 * nc + 1] = n[1]; cn[3 * nc + 2] = n[2];
-      cg[nc] = dot3(n, sv.c) - dot3(n, pn) - p.r_o;
-      ++nc;
     }
-    d.ncon[f] = nc;
+    kept[h] = !dup;
   }
+  unsigned km0 = __ballot_sync(0xffffffffu, kept[0]);
+  unsigned km1 = __ballot_sync(0xffffffffu, kept[1]);
+  const int nc = __popc(km0) + __popc(km1);
+  if (nc > kCpn) {
+    if (lane == 0) atomicCAS(&ctl->status, 0, ST_CAPACITY);
+    return;
+  }
+  int* ctri = d.con_tri + (size_t)f * kCpn;
+  double* cpt = d.con_pt + (size_t)f * kCpn * 3;
+  double* cn = d.con_n + (size_t)f * kCpn * 3;
+  double* cg = d.con_gap + (size_t)f * kCpn;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (!kept[h]) continue;
+    const Surv& sv = s_surv[wib][lane + 32 * h];
+    int rank = 0;
+    for (int hh = 0; hh < 2; ++hh) {
+      unsigned mk = hh == 0 ? km0 : km1;
+      while (mk) {
+        int jl = __ffs(mk) - 1;
+        mk &= mk - 1;
+        if (s_surv[wib][jl + 32 * hh].t < sv.t) ++rank;
+      }
+    }
+    const double* nf = d.nface + 3 * (size_t)sv.t;
+    double n[3];
+    double cmp[3] = {sv.c[0] - pn[0], sv.c[1] - pn[1], sv.c[2] - pn[2]};
+    if (sv.interior || dist[h] < 1e-12) { n[0] = nf[0]; n[1] = nf[1]; n[2] = nf[2]; }
+    else {
+      double sgn = (dot3(nf, cmp) > 0.0) ? 1.0 : -1.0;
+      double id = sgn / dist[h];
+      n[0] = cmp[0] * id; n[1] = cmp[1] * id; n[2] = cmp[2] * id;
+    }
+    ctri[rank] = sv.t;
+    cpt[3 * rank] = sv.c[0]; cpt[3 * rank + 1] = sv.c[1]; cpt[3 * rank + 2] = sv.c[2];
+    cn[3 * rank] = n[0]; cn[3 * rank + 1] = n[1]; cn[3 * rank + 2] = n[2];
+    cg[rank] = dot3(n, sv.c) - dot3(n, pn) - p.r_o;
+  }
+  if (lane == 0) d.ncon[f] = nc;
 }
 
 }  // namespace accfem

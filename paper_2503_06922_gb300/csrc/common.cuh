@@ -8,8 +8,10 @@ namespace accfem {
 constexpr int kMaxCables = 8;
 constexpr int kCpn = 8;            // constraint rows per node (locally closest wall features)
 constexpr int kSurvCap = 64;       // FP64 candidates per node after the FP32 prefilter
+constexpr int kCandCap = 256;      // triangles per node within the activation distance (FP32)
 constexpr int kElemStride = 96;    // doubles per element record: 78 K (upper) + 12 F + pad
 constexpr int kWarpsPerElemBlock = 2;
+constexpr int kRhsSplit = 4;       // blocks per node that share the RHS columns (chunks of 32)
 
 // Status codes mirrored from accfem.h
 enum : int { ST_OK = 0, ST_INVALID = 1, ST_NOMEM = 2, ST_CUDA = 3, ST_NOT_CONVERGED = 4,
@@ -68,6 +70,7 @@ struct Dev {
   // lumen
   const int* cell_start;                             // ncells + 1
   const float* tri32;                                // T * 9: vertices relative to the cell centre
+  const float* sph32;                                // T * 4: bounding sphere (centre rel. cell centre, radius)
   const int* cell_tri;                               // T: triangle id of sorted slot
   const double* V;                                   // n_vertices * 3
   const int* T;                                      // n_tri * 3
@@ -96,6 +99,7 @@ struct Dev {
   // contact LCP
   double *W, *q, *y, *w, *gj;                        // m_cap^2, m_cap, m_cap, m_cap, m_cap*(m_cap+1)
   int *inP, *plist;                                  // m_cap
+  int *wcol;                                         // m_cap: column j of W formed in this iteration
   Ctl* ctl;
 };
 

@@ -92,164 +92,213 @@ __device__ __forceinline__ void block_argmin(double& v, int& idx, double* s_red,
   idx = s_ired[32];
 }
 
-// Solves W_PP z_P = -q_P for the rows flagged in inP (Gauss-Jordan over the CTA, FP64) and writes
-// z into d.w (0 outside P).  Returns the size of P, or -1 on a non-positive pivot.
-__device__ int solve_on_set(const Dev& d, int m, int* s_np) {
+constexpr int kLcpThreads = 256;
+constexpr int kLcpSmemRows = 512;      // rows kept in shared memory (m_cap <= 4096; larger m reads global)
+constexpr int kLcpSmemGJ = 48;         // active rows solved in shared memory (else in global memory)
+
+struct LcpShared {
+  double q[kLcpSmemRows], y[kLcpSmemRows], z[kLcpSmemRows];
+  int inP[kLcpSmemRows], wcol[kLcpSmemRows], plist[kLcpSmemRows];
+  double gj[kLcpSmemGJ * (kLcpSmemGJ + 1)];
+  double red[33];
+  int ired[33];
+  int np;
+};
+
+// Forms column j of W = A X (with the compliance eps on its diagonal) for every active row j whose
+// column is not formed yet: W_ij = n_i . X_j[node_i].  W is symmetric, so the rows of the active
+// columns give every entry the active-set method reads.
+__device__ void ensure_columns(const Dev& d, LcpShared& S, int m, size_t ld, double eps_w) {
   const int tid = threadIdx.x, nt = blockDim.x;
   __syncthreads();
-  if (tid == 0) {
-    int np = 0;
-    for (int i = 0; i < m; ++i)
-      if (d.inP[i]) d.plist[np++] = i;
-    *s_np = np;
+  for (int a = 0; a < S.np; ++a) {
+    const int j = S.plist[a];
+    if (S.wcol[j]) continue;
+    for (int i = tid; i < m; i += nt) {
+      const int fi = d.c_node[i];
+      const double* n = d.c_n + 3 * i;
+      double s = 0.0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) s = fma(n[c], d.B[((size_t)fi * 6 + c) * ld + 1 + j], s);
+      if (i == j) s += eps_w;
+      d.W[(size_t)i * m + j] = s;
+    }
   }
   __syncthreads();
-  const int np = *s_np;
+  for (int a = tid; a < S.np; a += nt) S.wcol[S.plist[a]] = 1;
+  __syncthreads();
+}
+
+// Rebuilds the active list from the flags (thread 0; rows in increasing order).
+__device__ void rebuild_plist(LcpShared& S, int m) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int np = 0;
+    for (int i = 0; i < m; ++i)
+      if (S.inP[i]) S.plist[np++] = i;
+    S.np = np;
+  }
+  __syncthreads();
+}
+
+// Solves W_PP z_P = -q_P for the active list (Gauss-Jordan over the CTA, FP64; shared memory for up
+// to kLcpSmemGJ rows) and writes z (0 outside P).  Returns false on a non-positive pivot.
+__device__ bool solve_on_set(const Dev& d, LcpShared& S, int m) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int np = S.np;
   const int ldg = np + 1;
+  double* G = np <= kLcpSmemGJ ? S.gj : d.gj;
   for (int idx = tid; idx < np * ldg; idx += nt) {
     int r = idx / ldg, c = idx % ldg;
-    int i = d.plist[r];
-    d.gj[idx] = (c < np) ? d.W[(size_t)i * m + d.plist[c]] : -d.q[i];
+    int i = S.plist[r];
+    G[idx] = (c < np) ? d.W[(size_t)i * m + S.plist[c]] : -S.q[i];
   }
-  bool spd = true;
   for (int k = 0; k < np; ++k) {
     __syncthreads();
-    double akk = d.gj[(size_t)k * ldg + k];
-    if (!(akk > 0.0)) { spd = false; break; }
-    double rp = 1.0 / akk;
-    for (int c = k + 1 + tid; c < ldg; c += nt) d.gj[(size_t)k * ldg + c] *= rp;
+    const double akk = G[(size_t)k * ldg + k];
+    if (!(akk > 0.0)) return false;
+    const double rp = 1.0 / akk;
+    for (int c = k + 1 + tid; c < ldg; c += nt) G[(size_t)k * ldg + c] *= rp;
     __syncthreads();
     const int wdt = ldg - k - 1;
     for (int idx = tid; idx < np * wdt; idx += nt) {
       int r = idx / wdt, c = k + 1 + idx % wdt;
       if (r == k) continue;
-      d.gj[(size_t)r * ldg + c] = fma(-d.gj[(size_t)r * ldg + k], d.gj[(size_t)k * ldg + c], d.gj[(size_t)r * ldg + c]);
+      G[(size_t)r * ldg + c] = fma(-G[(size_t)r * ldg + k], G[(size_t)k * ldg + c], G[(size_t)r * ldg + c]);
     }
   }
   __syncthreads();
-  if (!spd) return -1;
-  for (int i = tid; i < m; i += nt) d.w[i] = 0.0;
+  for (int i = tid; i < m; i += nt) S.z[i] = 0.0;
   __syncthreads();
-  for (int r = tid; r < np; r += nt) d.w[d.plist[r]] = d.gj[(size_t)r * ldg + np];
+  for (int r = tid; r < np; r += nt) S.z[S.plist[r]] = G[(size_t)r * ldg + np];
   __syncthreads();
-  return np;
+  return true;
 }
 
 // LCP by a primal active-set method for the bound-constrained QP min 1/2 y^T W y + q^T y, y >= 0
 // (the Lawson-Hanson NNLS scheme with W SPD): keep y feasible with y_P > 0; add the row of most
 // negative w = W y + q; when the subproblem solution z_P has non-positive entries, step from y
 // towards z up to the first bound and release the rows that reach zero.  Finite for SPD W; starts
-// from the rows active in the previous Newton iteration.  d.w holds z, d.y holds y.
-__global__ void __launch_bounds__(1024) contact_kernel(Params p, Dev d) {
-  __shared__ double s_red[33];
-  __shared__ int s_ired[33];
-  __shared__ int s_np;
+// from the rows active in the previous Newton iteration.  Rows beyond kLcpSmemRows are not
+// supported in shared memory: the kernel flags ST_CAPACITY for such m (max_contacts caps m).
+__global__ void __launch_bounds__(kLcpThreads) contact_kernel(Params p, Dev d) {
+  __shared__ LcpShared S;
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
   const int m = ctl->m;
   const int tid = threadIdx.x, nt = blockDim.x;
   const size_t ld = p.nrhs_cap;
   if (m == 0) {
-    if (tid == 0) { ctl->n_active = 0; }
+    if (tid == 0) ctl->n_active = 0;
     return;
   }
-  // ---- W and q
-  for (int idx = tid; idx < m * m; idx += nt) {
-    int i = idx / m, j = idx % m;
-    int fi = d.c_node[i];
-    const double* n = d.c_n + 3 * i;
-    double s = 0.0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) s = fma(n[c], d.B[((size_t)fi * 6 + c) * ld + 1 + j], s);
-    d.W[(size_t)i * m + j] = s;
+  if (m > kLcpSmemRows) {
+    if (tid == 0) atomicCAS(&ctl->status, 0, ST_CAPACITY);
+    return;
   }
+  // ---- q = b - A dx_free; compliance from the largest W_ii
+  double wd = 0.0, qmax = 0.0;
   for (int i = tid; i < m; i += nt) {
-    int fi = d.c_node[i];
+    const int fi = d.c_node[i];
     const double* n = d.c_n + 3 * i;
-    double s = 0.0;
+    double s = 0.0, wii = 0.0;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) s = fma(n[c], d.B[((size_t)fi * 6 + c) * ld], s);
-    d.q[i] = d.c_gap[i] - s;
-    d.inP[i] = d.init_act[i] > 0 ? 1 : 0;
-    d.y[i] = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      s = fma(n[c], d.B[((size_t)fi * 6 + c) * ld], s);
+      wii = fma(n[c], d.B[((size_t)fi * 6 + c) * ld + 1 + i], wii);
+    }
+    S.q[i] = d.c_gap[i] - s;
+    S.y[i] = 0.0;
+    S.wcol[i] = 0;
+    S.inP[i] = d.init_act[i] > 0 ? 1 : 0;
+    wd = fmax(wd, wii);
+    qmax = fmax(qmax, fabs(S.q[i]));
   }
-  __syncthreads();
-  // contact compliance eps = 1e-12 max_i W_ii on the diagonal: rows of one node are linearly
-  // dependent where four or more wall faces meet, which leaves W singular without it
-  double wd = 0.0;
-  for (int i = tid; i < m; i += nt) wd = fmax(wd, d.W[(size_t)i * m + i]);
-  wd = block_max(wd, s_red);
-  for (int i = tid; i < m; i += nt) d.W[(size_t)i * m + i] += 1e-12 * wd;
-  double qmax = 0.0;
-  for (int i = tid; i < m; i += nt) qmax = fmax(qmax, fabs(d.q[i]));
-  qmax = block_max(qmax, s_red);
+  wd = block_max(wd, S.red);
+  qmax = block_max(qmax, S.red);
+  const double eps_w = 1e-12 * wd;
   const double tol_w = p.lcp_tol * fmax(qmax, 1e-300);
   int solves = 0;
   bool done = false, fail = false;
   // ---- feasible start: drop warm rows until the subproblem solution is positive
   for (;;) {
     if (solves >= p.max_lcp_iters) break;
-    int np = solve_on_set(d, m, &s_np);
+    rebuild_plist(S, m);
+    ensure_columns(d, S, m, ld, eps_w);
     ++solves;
-    if (np < 0) { fail = true; break; }
+    if (!solve_on_set(d, S, m)) { fail = true; break; }
     int nneg = 0;
-    for (int i = tid; i < m; i += nt)
-      if (d.inP[i] && !(d.w[i] > 0.0)) { d.inP[i] = 0; ++nneg; }
-    nneg = block_sum_int(nneg, s_ired);
+    for (int a = tid; a < S.np; a += nt) {
+      const int i = S.plist[a];
+      if (!(S.z[i] > 0.0)) { S.inP[i] = 0; ++nneg; }
+    }
+    nneg = block_sum_int(nneg, S.ired);
     if (nneg == 0) {
-      for (int i = tid; i < m; i += nt) d.y[i] = d.w[i];
+      for (int i = tid; i < m; i += nt) S.y[i] = S.z[i];
       break;
     }
   }
   // ---- main loop
   while (!fail && solves < p.max_lcp_iters) {
-    __syncthreads();
-    // w = W y + q outside P; most negative entry
+    rebuild_plist(S, m);
+    // w = W y + q outside P (over the active columns); most negative entry
     double best = 1.0e300;
     int bi = 0x7fffffff;
     for (int i = tid; i < m; i += nt) {
-      if (d.inP[i]) continue;
-      double s = d.q[i];
-      for (int j = 0; j < m; ++j)
-        if (d.inP[j]) s = fma(d.W[(size_t)i * m + j], d.y[j], s);
+      if (S.inP[i]) continue;
+      double s = S.q[i];
+      for (int a = 0; a < S.np; ++a) {
+        const int j = S.plist[a];
+        s = fma(d.W[(size_t)i * m + j], S.y[j], s);
+      }
       if (s < -tol_w && (s < best || (s == best && i < bi))) { best = s; bi = i; }
     }
-    block_argmin(best, bi, s_red, s_ired);
+    block_argmin(best, bi, S.red, S.ired);
     if (bi == 0x7fffffff) { done = true; break; }
-    if (tid == 0) d.inP[bi] = 1;
+    if (tid == 0) S.inP[bi] = 1;
     // inner loop: restore y_P > 0
     for (;;) {
       if (solves >= p.max_lcp_iters) break;
-      int np = solve_on_set(d, m, &s_np);
+      rebuild_plist(S, m);
+      ensure_columns(d, S, m, ld, eps_w);
       ++solves;
-      if (np < 0) { fail = true; break; }
+      if (!solve_on_set(d, S, m)) { fail = true; break; }
       // alpha = min over P with z_i <= 0 of y_i / (y_i - z_i)
       double amin = 1.0e300;
       int dummy = 0;
-      for (int i = tid; i < m; i += nt)
-        if (d.inP[i] && !(d.w[i] > 0.0)) {
-          double yi = d.y[i], zi = d.w[i];
-          double a = (yi - zi) > 0.0 ? yi / (yi - zi) : 0.0;
-          amin = fmin(amin, a);
+      for (int a = tid; a < S.np; a += nt) {
+        const int i = S.plist[a];
+        if (!(S.z[i] > 0.0)) {
+          const double yi = S.y[i], zi = S.z[i];
+          amin = fmin(amin, (yi - zi) > 0.0 ? yi / (yi - zi) : 0.0);
         }
-      block_argmin(amin, dummy, s_red, s_ired);
+      }
+      block_argmin(amin, dummy, S.red, S.ired);
       if (amin >= 1.0e300) {
-        for (int i = tid; i < m; i += nt) d.y[i] = d.w[i];
+        for (int i = tid; i < m; i += nt) S.y[i] = S.z[i];
         break;
       }
       double ymax = 0.0;
-      for (int i = tid; i < m; i += nt) {
-        if (d.inP[i]) {
-          double v = d.y[i] + amin * (d.w[i] - d.y[i]);
-          d.y[i] = v;
-          ymax = fmax(ymax, v);
-        }
+      for (int a = tid; a < S.np; a += nt) {
+        const int i = S.plist[a];
+        const double v = S.y[i] + amin * (S.z[i] - S.y[i]);
+        S.y[i] = v;
+        ymax = fmax(ymax, v);
       }
-      ymax = block_max(ymax, s_red);
+      ymax = block_max(ymax, S.red);
       const double tol_y = p.lcp_tol * fmax(ymax, 1e-300);
-      for (int i = tid; i < m; i += nt)
-        if (d.inP[i] && d.y[i] <= tol_y) { d.inP[i] = 0; d.y[i] = 0.0; }
+      for (int a = tid; a < S.np; a += nt) {
+        const int i = S.plist[a];
+        if (S.y[i] <= tol_y) { S.inP[i] = 0; S.y[i] = 0.0; }
+      }
     }
+  }
+  __syncthreads();
+  // ---- results: multipliers, active flags for the next iteration, active list
+  for (int i = tid; i < m; i += nt) {
+    const bool a = S.inP[i] && S.y[i] > 0.0;
+    d.y[i] = a ? S.y[i] : 0.0;
+    d.p_act[i] = a ? 1 : 0;
   }
   __syncthreads();
   if (tid == 0) {
@@ -257,12 +306,8 @@ __global__ void __launch_bounds__(1024) contact_kernel(Params p, Dev d) {
     if (fail) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
     else if (!done) atomicCAS(&ctl->status, 0, ST_TIMEOUT);
     int na = 0;
-    for (int i = 0; i < m; ++i) {
-      const bool a = d.inP[i] && d.y[i] > 0.0;
-      d.p_act[i] = a ? 1 : 0;
-      if (a) d.plist[na++] = i;
-      else d.y[i] = 0.0;
-    }
+    for (int i = 0; i < m; ++i)
+      if (S.inP[i] && S.y[i] > 0.0) d.plist[na++] = i;
     ctl->n_active = na;
   }
 }

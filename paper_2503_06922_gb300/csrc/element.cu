@@ -14,12 +14,24 @@ namespace accfem {
 __constant__ unsigned char c_up_i[78];
 __constant__ unsigned char c_up_j[78];
 
+// Per-warp scratch for the prelude: every FP64 warp instruction occupies the SMSP's FP64 pipe for
+// 64 cycles whatever its lane mask, so independent entries go to different lanes.
+struct ElemShared {
+  double T[2][9];      // nodal triads a, b (row-major)
+  double Rr[9];        // rigid frame, row-major, columns e1 e2 e3
+  double Rab[2][9];    // R_r^T T_a, R_r^T T_b
+  double th[2][3];     // local rotations
+  double Ti[2][9];     // Tsinv(theta_a), Tsinv(theta_b)
+  double B[7][12];     // B (local), then B E^T (global comps)
+  double H[7][12];     // K_l B E^T
+};
+
 __global__ void __launch_bounds__(32 * kWarpsPerElemBlock)
 element_kernel(Params p, Dev d) {
-  __shared__ double sB[kWarpsPerElemBlock][7][12];   // B (local), then B E^T (global comps)
-  __shared__ double sH[kWarpsPerElemBlock][7][12];   // K_l B E^T
+  __shared__ ElemShared sm[kWarpsPerElemBlock];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
+  ElemShared& S = sm[wib];
   Ctl* ctl = d.ctl;
   if (blockIdx.x == 0 && threadIdx.x == 0) {         // reset the per-iteration reductions
     ctl->umax_bits = 0ull; ctl->step_bits = 0ull; ctl->res_bits = 0ull;
@@ -27,44 +39,71 @@ element_kernel(Params p, Dev d) {
   const int e = ctl->k + blockIdx.x * kWarpsPerElemBlock + wib;
   if (e >= p.M || ctl->status != 0 || ctl->converged) return;
   const int a = e, b = e + 1;
-
-  // ---- scalar prelude (every lane: a warp FP64 instruction costs the same with 1 or 32 lanes)
-  double xa[3] = {d.px[a], d.py[a], d.pz[a]};
-  double xb[3] = {d.px[b], d.py[b], d.pz[b]};
-  double Ta[9], Tb[9];
-  quat_to_mat(d.qw[a], d.qx[a], d.qy[a], d.qz[a], Ta);
-  quat_to_mat(d.qw[b], d.qx[b], d.qy[b], d.qz[b], Tb);
-  double dv[3] = {xb[0] - xa[0], xb[1] - xa[1], xb[2] - xa[2]};
-  double l2 = dot3(dv, dv);
-  double l = sqrt(l2);
-  double il = 1.0 / l;
-  double e1[3] = {dv[0] * il, dv[1] * il, dv[2] * il};
-  double qv[3] = {0.5 * (Ta[1] + Tb[1]), 0.5 * (Ta[4] + Tb[4]), 0.5 * (Ta[7] + Tb[7])};
+  // ---- nodal triads: lane 0..17 -> entry (node lane/9, index lane%9)
+  if (lane < 18) {
+    const int nd = lane < 9 ? a : b, idx = lane % 9, r = idx / 3, c = idx % 3;
+    const double w = d.qw[nd], x = d.qx[nd], y = d.qy[nd], z = d.qz[nd];
+    const double q[4] = {w, x, y, z};
+    // R[r][c] of the unit quaternion: diagonal 1 - 2(q_j^2 + q_k^2), off-diagonal 2(q_r q_c -+ w q_k)
+    double v;
+    if (r == c) {
+      const int j = (r + 1) % 3 + 1, k = (r + 2) % 3 + 1;
+      v = 1.0 - 2.0 * (q[j] * q[j] + q[k] * q[k]);
+    } else {
+      const int k = 3 - r - c;                       // the third axis
+      const double sgn = ((c - r + 3) % 3 == 1) ? -1.0 : 1.0;   // R[0][1] = 2(xy - wz), R[1][0] = 2(xy + wz)
+      v = 2.0 * fma(q[r + 1], q[c + 1], sgn * w * q[k + 1]);
+    }
+    S.T[lane / 9][idx] = v;
+  }
+  __syncwarp();
+  // ---- chord and rigid frame (scalar chain, lane-uniform)
+  const double xa[3] = {d.px[a], d.py[a], d.pz[a]};
+  const double dv[3] = {d.px[b] - xa[0], d.py[b] - xa[1], d.pz[b] - xa[2]};
+  const double l2 = dot3(dv, dv);
+  const double l = sqrt(l2);
+  const double il = 1.0 / l;
+  const double e1[3] = {dv[0] * il, dv[1] * il, dv[2] * il};
+  const double qv[3] = {0.5 * (S.T[0][1] + S.T[1][1]), 0.5 * (S.T[0][4] + S.T[1][4]), 0.5 * (S.T[0][7] + S.T[1][7])};
   double v3[3];
   cross3(e1, qv, v3);
-  double iv = rsqrt(dot3(v3, v3));
-  double e3[3] = {v3[0] * iv, v3[1] * iv, v3[2] * iv};
+  const double iv = rsqrt(dot3(v3, v3));
+  const double e3[3] = {v3[0] * iv, v3[1] * iv, v3[2] * iv};
   double e2[3];
   cross3(e3, e1, e2);
-  // Rr row-major: Rr[r][c], columns e1 e2 e3
-  double Rr[9] = {e1[0], e2[0], e3[0], e1[1], e2[1], e3[1], e1[2], e2[2], e3[2]};
-  double Ra[9], Rb[9];   // R_r^T T
+  if (lane < 9) {
+    const int r = lane / 3, c = lane % 3;
+    S.Rr[lane] = c == 0 ? e1[r] : (c == 1 ? e2[r] : e3[r]);
+  }
+  __syncwarp();
+  // ---- R_r^T T for both nodes: lanes 0..17
+  if (lane < 18) {
+    const int nd = lane / 9, idx = lane % 9, i = idx / 3, j = idx % 3;
+    const double* T = S.T[nd];
+    S.Rab[nd][idx] = fma(S.Rr[i], T[j], fma(S.Rr[3 + i], T[3 + j], S.Rr[6 + i] * T[6 + j]));
+  }
+  __syncwarp();
+  // ---- local rotations and Tsinv: lane 0 node a, lane 1 node b
+  if (lane < 2) {
+    double th[3], Ti[9];
+    rotvec_of_mat(S.Rab[lane], th);
+    tsinv_mat(th, Ti);
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) S.th[lane][k] = th[k];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      Ra[3 * i + j] = fma(Rr[i], Ta[j], fma(Rr[3 + i], Ta[3 + j], Rr[6 + i] * Ta[6 + j]));
-      Rb[3 * i + j] = fma(Rr[i], Tb[j], fma(Rr[3 + i], Tb[3 + j], Rr[6 + i] * Tb[6 + j]));
-    }
-  double tha[3], thb[3];
-  rotvec_of_mat(Ra, tha);
-  rotvec_of_mat(Rb, thb);
-  double Tia[9], Tib[9];
-  tsinv_mat(tha, Tia);
-  tsinv_mat(thb, Tib);
+    for (int k = 0; k < 9; ++k) S.Ti[lane][k] = Ti[k];
+  }
+  __syncwarp();
   const double u = (l2 - p.l0 * p.l0) / (l + p.l0);
   const double qb1 = dot3(e1, qv), qb2 = dot3(e2, qv);   // local components of q (third is 0)
   const double iq2 = 1.0 / qb2;
+  const double* tha = S.th[0];
+  const double* thb = S.th[1];
+  const double* Tia = S.Ti[0];
+  const double* Tib = S.Ti[1];
+  const double* Ra = S.Rab[0];
+  const double* Rb = S.Rab[1];
+  const double* Rr = S.Rr;
   // local force vector f_l = K_l d_l
   const double ka = p.EA / p.l0, kt = p.GJ / p.l0, kb = p.EI / p.l0;
   double fl[7];
@@ -75,6 +114,8 @@ element_kernel(Params p, Dev d) {
   fl[4] = -fl[1];
   fl[5] = kb * (2.0 * tha[1] + 4.0 * thb[1]);
   fl[6] = kb * (2.0 * tha[2] + 4.0 * thb[2]);
+  auto& sB = S.B;
+  auto& sH = S.H;
 
   // ---- column j of B (local components): lanes 0..11
   if (lane < 12) {
@@ -93,11 +134,11 @@ element_kernel(Params p, Dev d) {
     double cb0 = -g0, cb1 = -g1, cb2 = -g2;   // (E_b - G^T) column j
     if (j >= 3 && j < 6) { if (j == 3) ca0 += 1.0; else if (j == 4) ca1 += 1.0; else ca2 += 1.0; }
     if (j >= 9) { if (j == 9) cb0 += 1.0; else if (j == 10) cb1 += 1.0; else cb2 += 1.0; }
-    sB[wib][0][j] = (j == 0) ? -1.0 : ((j == 6) ? 1.0 : 0.0);
+    sB[0][j] = (j == 0) ? -1.0 : ((j == 6) ? 1.0 : 0.0);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      sB[wib][1 + r][j] = fma(Tia[3 * r], ca0, fma(Tia[3 * r + 1], ca1, Tia[3 * r + 2] * ca2));
-      sB[wib][4 + r][j] = fma(Tib[3 * r], cb0, fma(Tib[3 * r + 1], cb1, Tib[3 * r + 2] * cb2));
+      sB[1 + r][j] = fma(Tia[3 * r], ca0, fma(Tia[3 * r + 1], ca1, Tia[3 * r + 2] * ca2));
+      sB[4 + r][j] = fma(Tib[3 * r], cb0, fma(Tib[3 * r + 1], cb1, Tib[3 * r + 2] * cb2));
     }
   }
   __syncwarp();
@@ -109,14 +150,14 @@ element_kernel(Params p, Dev d) {
     bg[t] = 0.0;
     if (idx < 84) {
       int k = idx / 12, col = idx % 12, s = col / 3, c = col % 3;
-      bg[t] = fma(sB[wib][k][3 * s], Rr[3 * c], fma(sB[wib][k][3 * s + 1], Rr[3 * c + 1], sB[wib][k][3 * s + 2] * Rr[3 * c + 2]));
+      bg[t] = fma(sB[k][3 * s], Rr[3 * c], fma(sB[k][3 * s + 1], Rr[3 * c + 1], sB[k][3 * s + 2] * Rr[3 * c + 2]));
     }
   }
   __syncwarp();
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
     int idx = lane + 32 * t;
-    if (idx < 84) sB[wib][idx / 12][idx % 12] = bg[t];
+    if (idx < 84) sB[idx / 12][idx % 12] = bg[t];
   }
   __syncwarp();
   // ---- H = K_l (B E^T)
@@ -127,15 +168,15 @@ element_kernel(Params p, Dev d) {
       int k = idx / 12, col = idx % 12;
       double h;
       switch (k) {
-        case 0: h = ka * sB[wib][0][col]; break;
-        case 1: h = kt * (sB[wib][1][col] - sB[wib][4][col]); break;
-        case 4: h = kt * (sB[wib][4][col] - sB[wib][1][col]); break;
-        case 2: h = kb * fma(4.0, sB[wib][2][col], 2.0 * sB[wib][5][col]); break;
-        case 5: h = kb * fma(2.0, sB[wib][2][col], 4.0 * sB[wib][5][col]); break;
-        case 3: h = kb * fma(4.0, sB[wib][3][col], 2.0 * sB[wib][6][col]); break;
-        default: h = kb * fma(2.0, sB[wib][3][col], 4.0 * sB[wib][6][col]); break;
+        case 0: h = ka * sB[0][col]; break;
+        case 1: h = kt * (sB[1][col] - sB[4][col]); break;
+        case 4: h = kt * (sB[4][col] - sB[1][col]); break;
+        case 2: h = kb * fma(4.0, sB[2][col], 2.0 * sB[5][col]); break;
+        case 5: h = kb * fma(2.0, sB[2][col], 4.0 * sB[5][col]); break;
+        case 3: h = kb * fma(4.0, sB[3][col], 2.0 * sB[6][col]); break;
+        default: h = kb * fma(2.0, sB[3][col], 4.0 * sB[6][col]); break;
       }
-      sH[wib][k][col] = h;
+      sH[k][col] = h;
     }
   }
   __syncwarp();
@@ -148,14 +189,14 @@ element_kernel(Params p, Dev d) {
       int i = c_up_i[idx], j = c_up_j[idx];
       double s = 0.0;
 #pragma unroll
-      for (int k = 0; k < 7; ++k) s = fma(sB[wib][k][i], sH[wib][k][j], s);
+      for (int k = 0; k < 7; ++k) s = fma(sB[k][i], sH[k][j], s);
       out[idx] = s;
     }
   }
   if (lane < 12) {
     double s = 0.0;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) s = fma(sB[wib][k][lane], fl[k], s);
+    for (int k = 0; k < 7; ++k) s = fma(sB[k][lane], fl[k], s);
     out[78 + lane] = s;
   }
 }
