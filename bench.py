@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile", type=int, default=0,
+                    help="run the first N solves of the sweep once (for profilers) and exit")
     return ap.parse_args()
 
 
@@ -154,10 +156,33 @@ def reference_arm(args, rank):
     return 0
 
 
-# Algorithmic FP64 flops of one element-kernel unit (one element) and of one collide unit (one free
-# node); counted from the formulas, see the design doc (roofline section).
-ELEMENT_FLOPS = 2 * 1510
-MEASURED_FP64_GFLOPS = 1201.7   # DFMA throughput probe on this machine's GB300 (all SMs, 4+ warps per SM)
+# Algorithmic FP64 flops per unit (formulas in the design doc, roofline section):
+#  element kernel, per element: B (7x12) from Tsinv and G, B E^T, K_l B E^T, the 78 tangent entries
+#  and the 12 forces;
+#  contact kernel, per launch with m rows and np active rows: the active W columns 6 m np, the
+#  elimination of W_PP np^3 and the optimality check 2 m np.
+ELEMENT_FLOPS = 2 * (216 + 252 + 168 + 546 + 84 + 120)
+# FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clock x 2 flops x 2.07 GHz (the 1.25 TFLOP/s
+# nominal FP64 rate of GB300; a DFMA throughput loop on this machine's GB300 reached 1.20 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def contact_flops(m, npa):
+    return 6.0 * m * npa + float(npa) ** 3 + 2.0 * m * npa
+
+
+def profile_run(args):
+    """The first N solves of the sweep, once, on the library's stream (for ncu captures)."""
+    import torch
+    from paper_2503_06922_gb300 import accfem as af
+    w = workload()
+    h = af.AccFem(w.robot, w.lumen)
+    for s in range(min(args.profile, len(w.insertions))):
+        r = h.accfem_solve(w.tensions[s], w.insertions[s])
+        print("solve %d status %d newton %d rows %d" % (s, r["status"], r["newton_iters"], r["n_contacts"]), flush=True)
+    torch.cuda.synchronize()
+    h.close()
+    return 0
 
 
 def ours(args, rank, world, local_rank):
@@ -240,10 +265,13 @@ def ours(args, rank, world, local_rank):
         b1 = h.accfem_transfer_bytes()
         h2d_step = (b1[0] - b0[0]) / args.steps + row_bytes * S
         d2h_step = (b1[1] - b0[1]) / args.steps
-        # ---- roofline of the element kernel (timed standalone on the resident final state)
+        # ---- kernels timed standalone on the resident final state (the last solve of the sweep)
+        last = r
+        m_last = int(last["n_contacts"])
+        np_last = int(sum(1 for c in last["contacts"] if c["force"] > 0.0))
         el_us = h.accfem_time_kernel(af.KERNEL_ELEMENT, 50)
         co_us = h.accfem_time_kernel(af.KERNEL_COLLIDE, 20)
-        ct_us = h.accfem_time_kernel(af.KERNEL_CONTACT, 5)
+        ct_us = h.accfem_time_kernel(af.KERNEL_CONTACT, 20)
     # max over ranks
     t_max = total_ms
     e2e_max = e2e_s
@@ -255,8 +283,9 @@ def ours(args, rank, world, local_rank):
     value = n_solves / (t_max / 1000.0)
     e2e_value = n_solves / e2e_max
     nf = w.robot.n_elements
-    achieved = ELEMENT_FLOPS * nf / (el_us * 1e-6) / 1e12
-    peak = MEASURED_FP64_GFLOPS / 1000.0
+    el_achieved = ELEMENT_FLOPS * nf / (el_us * 1e-6) / 1e12
+    achieved = contact_flops(m_last, np_last) / (ct_us * 1e-6) / 1e12
+    peak = FP64_PEAK_TFLOPS
     if rank == 0:
         cpu_n, cpu_dt = oracle_sample(w, 15.0)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -269,11 +298,15 @@ def ours(args, rank, world, local_rank):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d_step),
                         "d2h_bytes_per_step": int(d2h_step), "failed_solves": int(e2e_fail)},
                 "gpu_launches": int(launches),
-                "roofline": {"kernel": "element_kernel (corotational force + material tangent, M=300)",
+                "roofline": {"kernel": "contact_kernel (W columns + LCP active-set solve, m=%d rows, %d active)"
+                                       % (m_last, np_last),
                              "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s FP64",
-                             "frac": achieved / peak, "traffic": None,
-                             "launch_us": el_us, "note": "FP64 ALU roofline, peak = measured DFMA throughput"},
+                             "frac": achieved / peak, "traffic": None, "launch_us": ct_us,
+                             "note": "one-CTA latency-bound FP64 kernel; peak = FP64 rate derived from 152 SMs x "
+                                     "2 DFMA/clk x 2.07 GHz (of derived)"},
                 "kernel_us": {"element": el_us, "collide": co_us, "contact": ct_us},
+                "element_roofline": {"achieved": el_achieved, "peak": peak, "unit": "TFLOP/s FP64",
+                                     "frac": el_achieved / peak, "flops_per_element": ELEMENT_FLOPS},
                 "clocks": clk.summary(),
                 "cpu_baseline": {"value": cpu_n / cpu_dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                  "sample": "first %d solves of the sweep (insertion 10..%d mm), %.1f s, numpy FP64 "
@@ -295,6 +328,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return reference_arm(args, rank)
+    if args.profile:
+        return profile_run(args)
     return ours(args, rank, world, local_rank)
 
 
