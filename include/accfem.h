@@ -156,7 +156,7 @@ accfem_status accfem_transfer_bytes(const accfem_handle* h, int64_t* h2d, int64_
 typedef enum {
   ACCFEM_KERNEL_ELEMENT = 0,    /* corotational force + tangent, one warp per element            */
   ACCFEM_KERNEL_COLLIDE = 1,    /* node-vs-triangle detection, one warp per free node            */
-  ACCFEM_KERNEL_ASSEMBLE = 2,   /* block-tridiagonal assembly                                    */
+  ACCFEM_KERNEL_ASSEMBLE = 2,   /* block-tridiagonal assembly and RHS columns                     */
   ACCFEM_KERNEL_CONTACT = 3     /* W = A K^-1 A^T and the contact LCP (needs a completed solve)  */
 } accfem_kernel;
 

@@ -16,19 +16,15 @@ namespace accfem {
 __global__ void element_kernel(Params p, Dev d);
 __global__ void collide_kernel(Params p, Dev d);
 __global__ void compact_kernel(Params p, Dev d);
-__global__ void assemble_kernel(Params p, Dev d);
-__global__ void rhs_kernel(Params p, Dev d);
 __global__ void bcr_elim_kernel(Params p, Dev d, int s);
-__global__ void bcr_keep_kernel(Params p, Dev d, int s);
-__global__ void bcr_root_kernel(Params p, Dev d);
 __global__ void bcr_bwd_kernel(Params p, Dev d, int s);
 __global__ void contact_kernel(Params p, Dev d);
 __global__ void step_kernel(Params p, Dev d);
 __global__ void apply_kernel(Params p, Dev d);
 __global__ void start_kernel(Params p, Dev d, int mode, double delta, double delta_old, int k);
-__global__ void loop_ctl_kernel(Dev d, cudaGraphConditionalHandle h, int max_iter);
-__global__ void limiter_kernel(Params p, Dev d);
-__global__ void finish_kernel(Dev d);
+__global__ void ctl_kernel(Params p, Dev d, cudaGraphConditionalHandle h, int max_iter, int set_cond);
+__global__ void assemble_rhs_kernel(Params p, Dev d);
+__global__ void bcr_level_kernel(Params p, Dev d, int s);
 void upload_element_tables();
 }  // namespace accfem
 
@@ -391,30 +387,29 @@ int enqueue_iteration(accfem_handle* h, int nf, cudaStream_t st, cudaGraphCondit
   element_kernel<<<(nf + kWarpsPerElemBlock - 1) / kWarpsPerElemBlock, 32 * kWarpsPerElemBlock, 0, st>>>(p, d); ++n;
   collide_kernel<<<(nf + 3) / 4, 128, 0, st>>>(p, d); ++n;
   compact_kernel<<<1, 1024, 0, st>>>(p, d); ++n;
-  assemble_kernel<<<nf, 96, 0, st>>>(p, d); ++n;
-  rhs_kernel<<<dim3(nf, kRhsSplit), dim3(32, 6), 0, st>>>(p, d); ++n;
+  assemble_rhs_kernel<<<dim3(nf, kRhsSplit), dim3(32, 6), 0, st>>>(p, d); ++n;
+  // block cyclic reduction: level-1 eliminations, then one kernel per level s that updates the kept
+  // nodes, eliminates the next level's nodes (or the root) and reduces the RHS; back substitution
   std::vector<int> strides;
   for (int s = 1; s < nf; s *= 2) strides.push_back(s);
+  if (nf >= 2) { bcr_elim_kernel<<<(nf - 2) / 2 + 1, 64, 0, st>>>(p, d, 1); ++n; }
+  if (strides.empty()) { bcr_level_kernel<<<dim3(1, kRhsSplit), 192, 0, st>>>(p, d, 1); ++n; }
   for (int s : strides) {
-    bcr_elim_kernel<<<(nf - s - 1) / (2 * s) + 1, 64, 0, st>>>(p, d, s); ++n;
-    bcr_keep_kernel<<<dim3((nf - 1) / (2 * s) + 1, kRhsSplit), 192, 0, st>>>(p, d, s); ++n;
+    bcr_level_kernel<<<dim3((nf - 1) / (2 * s) + 1, kRhsSplit), 192, 0, st>>>(p, d, s); ++n;
   }
-  bcr_root_kernel<<<dim3(1, kRhsSplit), 192, 0, st>>>(p, d); ++n;
   for (int si = (int)strides.size() - 1; si >= 0; --si) {
     int s = strides[si];
     bcr_bwd_kernel<<<dim3((nf - s - 1) / (2 * s) + 1, kRhsSplit), 192, 0, st>>>(p, d, s); ++n;
   }
   contact_kernel<<<1, 256, 0, st>>>(p, d); ++n;
   step_kernel<<<(nf + 31) / 32, dim3(32, 6), 0, st>>>(p, d); ++n;
-  limiter_kernel<<<1, 32, 0, st>>>(p, d); ++n;
   apply_kernel<<<(nf + 127) / 128, 128, 0, st>>>(p, d); ++n;
-  finish_kernel<<<1, 32, 0, st>>>(d); ++n;
-  if (!h->stream_mode) { loop_ctl_kernel<<<1, 1, 0, st>>>(d, cond, h->max_newton); ++n; }
+  ctl_kernel<<<1, 1, 0, st>>>(p, d, cond, h->max_newton, h->stream_mode ? 0 : 1); ++n;
   return n;
 }
 
 // Device-side Newton loop for nf free nodes: a graph whose WHILE node runs the iteration body until
-// loop_ctl_kernel clears the condition (converged, error, or the iteration cap).  Built once per nf.
+// ctl_kernel clears the condition (converged, error, or the iteration cap).  Built once per nf.
 const accfem_handle::LoopGraph* newton_graph(accfem_handle* h, int nf) {
   auto it = h->graphs.find(nf);
   if (it != h->graphs.end()) return &it->second;
@@ -692,7 +687,7 @@ accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t
       case ACCFEM_KERNEL_ELEMENT:
         element_kernel<<<(nf + kWarpsPerElemBlock - 1) / kWarpsPerElemBlock, 32 * kWarpsPerElemBlock, 0, st>>>(p, d); break;
       case ACCFEM_KERNEL_COLLIDE: collide_kernel<<<(nf + 3) / 4, 128, 0, st>>>(p, d); break;
-      case ACCFEM_KERNEL_ASSEMBLE: assemble_kernel<<<nf, 96, 0, st>>>(p, d); break;
+      case ACCFEM_KERNEL_ASSEMBLE: assemble_rhs_kernel<<<dim3(nf, kRhsSplit), dim3(32, 6), 0, st>>>(p, d); break;
       default: contact_kernel<<<1, 256, 0, st>>>(p, d); break;
     }
   };

@@ -10,7 +10,9 @@
 // eliminated, nodes i = 0 (mod 2s) kept.  For eliminated j: P_j = D_j^{-1}, L_j = U_{j-s} P_j,
 // R_j = U_j^T P_j.  For kept i: D_i -= R_{i-s} U_{i-s} + L_{i+s} U_i^T, U_i <- -L_{i+s} U_{i+s}.
 // Solve: forward b_i -= R_{i-s} b_{i-s} + L_{i+s} b_{i+s} (kept), root x_0 = P_0 b_0, backward
-// x_j = P_j b_j - L_j^T x_{j-s} - R_j^T x_{j+s} (eliminated).
+// x_j = P_j b_j - L_j^T x_{j-s} - R_j^T x_{j+s} (eliminated).  Launches per factor-and-solve:
+// bcr_elim_kernel (level 1), one bcr_level_kernel per level (kept-node update + next level's
+// eliminations + forward RHS; root at the last level), one bcr_bwd_kernel per level.
 #include "common.cuh"
 
 namespace accfem {
@@ -104,27 +106,30 @@ __global__ void __launch_bounds__(1024) compact_kernel(Params p, Dev d) {
 }
 
 // ------------------------------------------------------------------ assembly
-// grid: nf blocks of 96 threads: 36 threads for D, 36 for U, 6 for g.
-__global__ void __launch_bounds__(96) assemble_kernel(Params p, Dev d) {
+// Assembly and RHS columns of one free node (blocks (node, y), 32 x 6 threads): D, U and g = F - F_a
+// with the tip load of Eq. 16-18, then RHS columns 0 = -g and 1 + row = A^T e_row (block y takes the
+// column chunks y, y + kRhsSplit, ...).
+__global__ void __launch_bounds__(192) assemble_rhs_kernel(Params p, Dev d) {
+  __shared__ double s_g[6];
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
   const int f = blockIdx.x;
   const int nf = ctl->nf;
   if (f >= nf) return;
   const int node = ctl->k + 1 + f;
-  const int tid = threadIdx.x;
-  const double* eb = d.elem + (size_t)(node - 1) * kElemStride;   // element node-1: node is its b end
-  const double* ea = d.elem + (size_t)node * kElemStride;         // element node: node is its a end
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const double* eb = d.elem + (size_t)(node - 1) * kElemStride;
+  const double* ea = d.elem + (size_t)node * kElemStride;
   const bool has_a = node < p.M;
-  if (tid < 36) {
+  if (tid < 36 && blockIdx.y == 0) {
     int r = tid / 6, c = tid % 6;
     double v = kval(eb, 6 + r, 6 + c);
     if (has_a) v += kval(ea, r, c);
     d.D[(size_t)f * 36 + tid] = v;
-  } else if (tid < 72) {
+  } else if (tid >= 36 && tid < 72 && blockIdx.y == 0) {
     int q = tid - 36, r = q / 6, c = q % 6;
     d.U[(size_t)f * 36 + q] = has_a ? kval(ea, r, 6 + c) : 0.0;
-  } else if (tid < 78) {
+  } else if (tid >= 72 && tid < 78) {
     int c = tid - 72;
     double F = eb[78 + 6 + c] + (has_a ? ea[78 + c] : 0.0);
     double Fa = 0.0;
@@ -133,7 +138,6 @@ __global__ void __launch_bounds__(96) assemble_kernel(Params p, Dev d) {
       quat_to_mat(d.qw[node], d.qx[node], d.qy[node], d.qz[node], T);
       double fl[3] = {0.0, 0.0, 0.0}, ml[3] = {0.0, 0.0, 0.0};
       if (ctl->load_mode == 0) {
-        // Eq. 16-18: F_j = (-tau_j, 0, 0), d_j = r_c (0, cos phi_j, sin phi_j), M_j = d_j x F_j
         double st = 0.0, ss = 0.0, sc = 0.0;
         for (int j = 0; j < p.n_cables; ++j) {
           st += ctl->tension[j];
@@ -142,7 +146,7 @@ __global__ void __launch_bounds__(96) assemble_kernel(Params p, Dev d) {
         }
         fl[0] = -st; ml[1] = -p.r_c * ss; ml[2] = p.r_c * sc;
       } else {
-        for (int a = 0; a < 3; ++a) { fl[a] = ctl->tip_f[a]; ml[a] = ctl->tip_m[a]; }
+        for (int a2 = 0; a2 < 3; ++a2) { fl[a2] = ctl->tip_f[a2]; ml[a2] = ctl->tip_m[a2]; }
       }
       if (ctl->load_mode == 1) {
         Fa = c < 3 ? fl[c] : ml[c - 3];
@@ -152,21 +156,15 @@ __global__ void __launch_bounds__(96) assemble_kernel(Params p, Dev d) {
         Fa = fma(T[3 * r], v[0], fma(T[3 * r + 1], v[1], T[3 * r + 2] * v[2]));
       }
     }
-    d.g[(size_t)f * 6 + c] = F - Fa;
+    s_g[c] = F - Fa;
+    if (blockIdx.y == 0) d.g[(size_t)f * 6 + c] = F - Fa;
   }
-}
-
-// RHS columns: 0 = -g, 1 + row = A^T e_row (unit normal on the row's node translation).
-// Blocks (node, y) of (32 rhs, 6 comps); block y handles the column chunks y, y + kRhsSplit, ...
-__global__ void __launch_bounds__(192) rhs_kernel(Params p, Dev d) {
-  Ctl* ctl = d.ctl;
-  if (ctl->status != 0 || ctl->converged) return;
-  const int f = blockIdx.x, c = threadIdx.y;
-  if (f >= ctl->nf) return;
+  __syncthreads();
+  const int c = threadIdx.y;
   const int nrhs = ctl->m + 1;
   for (int r = blockIdx.y * 32 + threadIdx.x; r < nrhs; r += 32 * kRhsSplit) {
     double v;
-    if (r == 0) v = -d.g[(size_t)f * 6 + c];
+    if (r == 0) v = -s_g[c];
     else v = (d.c_node[r - 1] == f && c < 3) ? d.c_n[3 * (r - 1) + c] : 0.0;
     d.B[((size_t)f * 6 + c) * p.nrhs_cap + r] = v;
   }
@@ -197,7 +195,7 @@ __device__ bool team_inverse6(double* sA, int tid, double* s_piv) {
   return true;
 }
 
-// Phase A: eliminated nodes j = s + 2 s blockIdx.x.
+// Eliminations of level 1 (nodes j = 1 + 2 blockIdx.x; later levels are fused into bcr_level_kernel).
 __global__ void __launch_bounds__(64) bcr_elim_kernel(Params p, Dev d, int s) {
   __shared__ double sA[36], sX[36], sY[36];
   __shared__ double s_piv[1];
@@ -232,10 +230,15 @@ __global__ void __launch_bounds__(64) bcr_elim_kernel(Params p, Dev d, int s) {
   }
 }
 
-// Phase B: kept nodes i = 2 s blockIdx.x, fused with the forward reduction of every RHS column.
-// Block: 192 threads = (32 rhs lanes, 6 comps); threads 0..35 update the 6x6 blocks.
-__global__ void __launch_bounds__(192) bcr_keep_kernel(Params p, Dev d, int s) {
-  __shared__ double sRl[36], sUl[36], sLr[36], sUi[36], sUr[36];
+// Level s of the reduction, fused with the elimination at level 2s.  Blocks (kept node i = 2 s x,
+// y = RHS split), 192 threads.  Block y == 0: Schur update of D_i and U_i (kept nodes i: D_i and U_i as above);
+// when i = 2s (mod 4s) it then eliminates i at level 2s: its new left coupling
+// U_{i-2s} <- -L_{i-s} U_{i-s} is rebuilt from level-s data, P_i = D_i^{-1}, L_i = U_{i-2s} P_i,
+// R_i = U_i^T P_i.  Every block applies the level-s forward reduction to its RHS chunks.  When
+// 2s >= nf only node 0 is kept: every block inverts D_0 itself (root) and solves x_0 = P_0 b_0.
+__global__ void __launch_bounds__(192) bcr_level_kernel(Params p, Dev d, int s) {
+  __shared__ double sRl[36], sUl[36], sLr[36], sUi[36], sUr[36], sA[36], sX[36], sY[36];
+  __shared__ double s_piv[1];
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
   const int nf = ctl->nf;
@@ -243,6 +246,8 @@ __global__ void __launch_bounds__(192) bcr_keep_kernel(Params p, Dev d, int s) {
   if (i >= nf) return;
   const int tid = threadIdx.x;
   const bool hl = i >= s, hr = i + s < nf, hr2 = i + 2 * s < nf;
+  const bool root = 2 * s >= nf;                       // only node 0 remains after this level
+  const bool elim2 = !root && (i % (4 * s)) == 2 * s;   // i is eliminated at level 2s
   if (tid < 36) {
     sRl[tid] = hl ? d.Rm[(size_t)(i - s) * 36 + tid] : 0.0;
     sUl[tid] = hl ? d.U[(size_t)(i - s) * 36 + tid] : 0.0;
@@ -251,7 +256,8 @@ __global__ void __launch_bounds__(192) bcr_keep_kernel(Params p, Dev d, int s) {
     sUr[tid] = hr2 ? d.U[(size_t)(i + s) * 36 + tid] : 0.0;
   }
   __syncthreads();
-  if (tid < 36 && blockIdx.y == 0) {
+  const bool matrix = blockIdx.y == 0 || root;
+  if (tid < 36 && matrix) {
     const int r = tid / 6, c = tid % 6;
     double dd = d.D[(size_t)i * 36 + tid];
     double un = 0.0;
@@ -261,58 +267,94 @@ __global__ void __launch_bounds__(192) bcr_keep_kernel(Params p, Dev d, int s) {
       dd = fma(-sLr[r * 6 + k], sUi[c * 6 + k], dd);
       un = fma(-sLr[r * 6 + k], sUr[k * 6 + c], un);
     }
-    d.D[(size_t)i * 36 + tid] = dd;
-    if (hr) d.U[(size_t)i * 36 + tid] = hr2 ? un : 0.0;
+    sA[tid] = dd;
+    sY[tid] = hr2 ? un : 0.0;                        // new U_i = K_{i, i+2s}
+    if (blockIdx.y == 0) {
+      d.D[(size_t)i * 36 + tid] = dd;
+      if (hr) d.U[(size_t)i * 36 + tid] = hr2 ? un : 0.0;
+    }
   }
-  // forward reduction: b_i -= R_{i-s} b_{i-s} + L_{i+s} b_{i+s}
+  if (elim2 && blockIdx.y == 0) {
+    // new left coupling K_{i-2s, i} = -L_{i-s} U_{i-s}: node i-s was eliminated at level s
+    __syncthreads();
+    if (tid < 36) {
+      const int r = tid / 6, c = tid % 6;
+      const double* Lm1 = d.Lm + (size_t)(i - s) * 36;
+      const double* Um1 = d.U + (size_t)(i - s) * 36;
+      double v = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) v = fma(-Lm1[r * 6 + k], Um1[k * 6 + c], v);
+      sX[tid] = v;
+    }
+    const bool ok = team_inverse6(sA, tid, s_piv);
+    if (!ok) {
+      if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
+    } else if (tid < 36) {
+      const int r = tid / 6, c = tid % 6;
+      d.P[(size_t)i * 36 + tid] = sA[tid];
+      double l = 0.0, rr = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        l = fma(sX[r * 6 + k], sA[k * 6 + c], l);     // U_{i-2s} P_i
+        rr = fma(sY[k * 6 + r], sA[k * 6 + c], rr);   // U_i^T P_i
+      }
+      d.Lm[(size_t)i * 36 + tid] = l;
+      d.Rm[(size_t)i * 36 + tid] = rr;
+    }
+  }
+  // forward reduction of level s: b_i -= R_{i-s} b_{i-s} + L_{i+s} b_{i+s}
   const int lane = tid & 31, c = tid >> 5;
   const int nrhs = ctl->m + 1;
   const size_t ld = p.nrhs_cap;
-  for (int r = blockIdx.y * 32 + lane; r < nrhs; r += 32 * kRhsSplit) {
-    double acc = d.B[((size_t)i * 6 + c) * ld + r];
-    if (hl) {
-      const double* b = d.B + (size_t)(i - s) * 6 * ld + r;
+  if (!root) {
+    for (int r = blockIdx.y * 32 + lane; r < nrhs; r += 32 * kRhsSplit) {
+      double acc = d.B[((size_t)i * 6 + c) * ld + r];
+      if (hl) {
+        const double* b = d.B + (size_t)(i - s) * 6 * ld + r;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) acc = fma(-sRl[c * 6 + k], b[k * ld], acc);
-    }
-    if (hr) {
-      const double* b = d.B + (size_t)(i + s) * 6 * ld + r;
+        for (int k = 0; k < 6; ++k) acc = fma(-sRl[c * 6 + k], b[k * ld], acc);
+      }
+      if (hr) {
+        const double* b = d.B + (size_t)(i + s) * 6 * ld + r;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) acc = fma(-sLr[c * 6 + k], b[k * ld], acc);
+        for (int k = 0; k < 6; ++k) acc = fma(-sLr[c * 6 + k], b[k * ld], acc);
+      }
+      d.B[((size_t)i * 6 + c) * ld + r] = acc;
     }
-    d.B[((size_t)i * 6 + c) * ld + r] = acc;
+    return;
   }
-}
-
-// Root: P_0 = D_0^{-1} and x_0 = P_0 b_0 for every RHS column.  Block: 192 threads.
-__global__ void __launch_bounds__(192) bcr_root_kernel(Params p, Dev d) {
-  __shared__ double sA[36];
-  __shared__ double s_piv[1];
-  Ctl* ctl = d.ctl;
-  if (ctl->status != 0 || ctl->converged || ctl->nf == 0) return;
-  const int tid = threadIdx.x;
-  if (tid < 36) sA[tid] = d.D[tid];
-  bool ok = team_inverse6(sA, tid, s_piv);
+  // root: node 0 after its last update; every block inverts D_0 and solves its chunks
+  __syncthreads();
+  const bool ok = team_inverse6(sA, tid, s_piv);
   if (!ok) {
     if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
     return;
   }
   if (tid < 36 && blockIdx.y == 0) d.P[tid] = sA[tid];
-  const int lane = tid & 31, c = tid >> 5;
-  const int nrhs = ctl->m + 1;
-  const size_t ld = p.nrhs_cap;
   for (int r0 = blockIdx.y * 32; r0 < nrhs; r0 += 32 * kRhsSplit) {
     const int r = r0 + lane;
     const bool act = r < nrhs;
-    double b[6];
+    double acc0 = 0.0;
+    if (act) {
+      acc0 = d.B[(size_t)c * ld + r];
+      if (hr) {
+        const double* b = d.B + (size_t)s * 6 * ld + r;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc0 = fma(-sLr[c * 6 + k], b[k * ld], acc0);
+      }
+    }
+    __syncthreads();
+    if (act) d.B[(size_t)c * ld + r] = acc0;          // b_0 after the last forward step
+    __syncthreads();
+    double bb[6];
     if (act)
 #pragma unroll
-      for (int k = 0; k < 6; ++k) b[k] = d.B[(size_t)k * ld + r];
+      for (int k = 0; k < 6; ++k) bb[k] = d.B[(size_t)k * ld + r];
     __syncthreads();
     if (act) {
       double acc = 0.0;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) acc = fma(sA[c * 6 + k], b[k], acc);
+      for (int k = 0; k < 6; ++k) acc = fma(sA[c * 6 + k], bb[k], acc);
       d.B[(size_t)c * ld + r] = acc;
     }
     __syncthreads();

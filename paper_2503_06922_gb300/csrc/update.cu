@@ -60,37 +60,36 @@ __global__ void __launch_bounds__(192) step_kernel(Params p, Dev d) {
 // Step limiter (Eq. 25-27 with an adaptive bound): alpha = min(1, rho / max |du|).  A step that
 // points against the previous one (sum_i du_i . du_i^prev < 0, summed over the step blocks in a
 // fixed order) is an overshoot: it is halved, and when it was clipped rho is halved too; otherwise
-// rho doubles back towards beta0.  Also counts the iteration and decides convergence (unscaled
-// step below tol with an unchanged constraint set).
-__global__ void limiter_kernel(Params p, Dev d) {
-  Ctl* ctl = d.ctl;
-  if (ctl->status != 0 || ctl->converged || threadIdx.x != 0) return;
+// rho doubles back towards beta0.  Every reader evaluates this from the same inputs.
+__device__ __forceinline__ void limiter(const Params& p, const Dev& d, const Ctl* ctl, double* rho_new, double* alpha) {
   const int nb = (ctl->nf + 31) / 32;
   double rev = 0.0;
   for (int b = 0; b < nb; ++b) rev += d.rev_part[b];
   double rho = ctl->rho;
   const double umax = __longlong_as_double((long long)ctl->umax_bits);
-  const double step = __longlong_as_double((long long)ctl->step_bits);
   const bool reverse = ctl->has_prev && rev < 0.0;
   if (ctl->has_prev) {
     if (!reverse) rho = fmin(2.0 * rho, p.beta0);
     else if (umax > rho) rho = fmax(0.5 * rho, p.beta0 * 9.5367431640625e-07);   // beta0 / 2^20
   }
-  double alpha = umax <= rho ? 1.0 : rho / umax;
-  if (reverse) alpha *= 0.5;
-  ctl->rho = rho;
-  ctl->has_prev = 1;
-  ctl->alpha = alpha;
-  ctl->iter += 1;
-  if (step <= p.tol && ctl->same_set) ctl->converged = 2;   // 2: apply this last step
+  double a = umax <= rho ? 1.0 : rho / umax;
+  if (reverse) a *= 0.5;
+  *rho_new = rho;
+  *alpha = a;
 }
 
 // x <- x + alpha du, T <- exp([alpha dtheta]x) T.
 __global__ void __launch_bounds__(128) apply_kernel(Params p, Dev d) {
+  __shared__ double s_alpha;
   Ctl* ctl = d.ctl;
-  if (ctl->status != 0 || ctl->converged == 1) return;
+  if (ctl->status != 0 || ctl->converged) return;
   const int nf = ctl->nf;
-  const double alpha = ctl->alpha;
+  if (threadIdx.x == 0) {
+    double rho;
+    limiter(p, d, ctl, &rho, &s_alpha);
+  }
+  __syncthreads();
+  const double alpha = s_alpha;
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f < nf) {
     const int node = ctl->k + 1 + f;
@@ -108,19 +107,27 @@ __global__ void __launch_bounds__(128) apply_kernel(Params p, Dev d) {
   }
 }
 
-// Marks a converged solve final once its last step is applied.
-__global__ void finish_kernel(Dev d) {
-  if (threadIdx.x == 0 && d.ctl->converged == 2) d.ctl->converged = 1;
-}
-
-// Newton loop control (last node of the loop body): keep iterating while no error, not converged
-// and fewer than max_iter iterations; a separate count of loop passes bounds the loop whatever the
-// other kernels did.
-__global__ void loop_ctl_kernel(Dev d, cudaGraphConditionalHandle h, int max_iter) {
+// End of an iteration (one thread): limiter bookkeeping, iteration count, convergence (unscaled
+// step below tol with an unchanged constraint set), and -- inside the device-side Newton graph --
+// the loop condition: keep iterating while no error, not converged and fewer than max_iter
+// iterations; a separate count of loop passes bounds the loop whatever the other kernels did.
+__global__ void ctl_kernel(Params p, Dev d, cudaGraphConditionalHandle h, int max_iter, int set_cond) {
   Ctl* c = d.ctl;
+  if (c->status == 0 && !c->converged) {
+    double rho, alpha;
+    limiter(p, d, c, &rho, &alpha);
+    const double step = __longlong_as_double((long long)c->step_bits);
+    c->rho = rho;
+    c->alpha = alpha;
+    c->has_prev = 1;
+    c->iter += 1;
+    if (step <= p.tol && c->same_set) c->converged = 1;
+  }
   c->loops += 1;
-  unsigned int cont = (c->status == 0 && !c->converged && c->iter < max_iter && c->loops < max_iter) ? 1u : 0u;
-  cudaGraphSetConditional(h, cont);
+  if (set_cond) {
+    unsigned int cont = (c->status == 0 && !c->converged && c->iter < max_iter && c->loops < max_iter) ? 1u : 0u;
+    cudaGraphSetConditional(h, cont);
+  }
 }
 
 // Start pose of a solve.  mode 0: straight on the entrance axis; mode 1: follow the path of the
