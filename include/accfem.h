@@ -32,6 +32,8 @@ extern "C" {
 
 typedef struct accfem_handle accfem_handle;
 
+#define ACCFEM_MAX_CABLES 8     /* cables per robot; also the row stride of batched tensions     */
+
 typedef enum {
   ACCFEM_OK = 0,
   ACCFEM_E_INVALID_ARG = 1,     /* a descriptor, option or argument is out of range        */
@@ -47,7 +49,7 @@ typedef enum {
 /* Robot (Sec. II.A-B, Table 1 columns): hollow circular section, M equal two-node 6-DOF
  * beam elements of length l0 = length / n_elements.  Cables (Eq. 16-18): cable j is welded
  * to the tip at distance cable_radius from the axis, at angle cable_angles[j] from the
- * section's second axis towards its third; n_cables <= 8. */
+ * section's second axis towards its third; n_cables <= ACCFEM_MAX_CABLES. */
 typedef struct {
   double length, outer_radius, inner_radius, youngs_modulus, poisson_ratio;
   int32_t n_elements;           /* M >= 1; N = M + 1 nodes                                  */
@@ -185,6 +187,68 @@ accfem_status accfem_detect_contacts_noalloc(accfem_handle* h, const double* nod
                                              int32_t row_capacity, int32_t* row_node, int32_t* row_tri,
                                              double* row_point, double* row_normal, double* row_gap,
                                              int32_t* n_rows, void* stream);
+
+/* ---- Batched solves.  The paper solves one robot at a time; these calls are an extension for
+ * throughput with no counterpart in it.  A batch groups member handles (each its own robot and
+ * lumen, created by accfem_create on the current device) and advances every member that has a
+ * solve in flight with one persistent kernel launch per Newton phase: each member runs exactly the
+ * kernel code of accfem_solve on its own buffers, so its results are the ones accfem_solve gives.
+ * Solves start and finish independently (continuous batching): stage solves on idle members with
+ * accfem_batch_begin, run accfem_batch_advance, collect the finished ones with accfem_batch_poll and
+ * accfem_batch_results, stage more.  The members stay owned by the caller and must outlive the
+ * batch; a member must not be passed to other calls while a batch solve of it is staged or in
+ * flight (between those solves it may be used alone; its resident state is shared).  Batch calls are
+ * synchronous on the batch's stream; a batch is not thread-safe. */
+typedef struct accfem_batch accfem_batch;
+
+/* Groups members[0..n_members), 1 <= n_members <= 1024 distinct handles.  Builds the batch's CUDA
+ * graph once (one iteration of all members as a conditional loop body). */
+accfem_status accfem_batch_create(accfem_handle* const* members, int32_t n_members, accfem_batch** out);
+
+/* Stages one quasi-static solve of member `member`, as accfem_solve with warm = NULL: cable_tensions
+ * holds the member's n_cables values (host), insertion in [0, length]; the start pose follows the
+ * member's resident state (straight on its first solve).  The solve starts at the next advance.
+ * ACCFEM_E_INVALID_ARG if the member already has a solve staged or in flight. */
+accfem_status accfem_batch_begin(accfem_batch* b, int32_t member, const double* cable_tensions, double insertion);
+
+/* Starts the staged solves, then runs up to max_iters (>= 1) Newton iterations of every solve in
+ * flight and waits; a solve stops at convergence, at an error or at its member's max_newton_iters.
+ * *n_in_flight (may be NULL) receives the number of solves still unfinished. */
+accfem_status accfem_batch_advance(accfem_batch* b, int32_t max_iters, int32_t* n_in_flight);
+
+/* *done = 1 when member `member` has no solve staged or in flight; then *solve_status and
+ * *newton_iters (either may be NULL) describe its last finished solve (ACCFEM_OK and 0 if none). */
+accfem_status accfem_batch_poll(const accfem_batch* b, int32_t member, int32_t* done, accfem_status* solve_status,
+                                int32_t* newton_iters);
+
+/* Copies the results of the last finished solves of members[0..count) into out[0..count) (fields as
+ * accfem_solve fills them) through one device gather and one device-to-host copy; statuses[j] (may
+ * be NULL) receives member j's solve status.  Returns the first non-OK solve status, or an argument
+ * or CUDA error. */
+accfem_status accfem_batch_results(accfem_batch* b, const int32_t* members, int32_t count, accfem_result* out,
+                                   accfem_status* statuses);
+
+/* One solve of every member i with mask[i] != 0 (mask NULL = all members): tensions of member i at
+ * cable_tensions[ACCFEM_MAX_CABLES * i ...], insertion insertions[i]; begins them, advances until
+ * all finished and, if results is not NULL, fills results[i] (indexed by member).  statuses[i] (may be
+ * NULL) receives each solved member's status.  Returns the first non-OK solve status. */
+accfem_status accfem_batch_solve(accfem_batch* b, const double* cable_tensions, const double* insertions,
+                                 const int32_t* mask, accfem_status* statuses, accfem_result* results);
+
+/* Work stream of the batch's calls (a cudaStream_t; NULL = the batch's own stream). */
+accfem_status accfem_batch_set_stream(accfem_batch* b, void* stream);
+
+/* Cumulative bytes copied host->device and device->host by this batch's calls. */
+accfem_status accfem_batch_transfer_bytes(const accfem_batch* b, int64_t* h2d, int64_t* d2h);
+
+/* Number of kernel launches issued by this batch since creation. */
+int64_t accfem_batch_kernel_launches(const accfem_batch* b);
+
+/* Message of the last failure on this batch ("" if none). */
+const char* accfem_batch_last_error(const accfem_batch* b);
+
+/* Frees the batch (not its members); NULL is a no-op. */
+void accfem_batch_destroy(accfem_batch* b);
 
 /* Copies the resident nodal poses (3*(M+1) and 4*(M+1) doubles) to host buffers. */
 accfem_status accfem_get_state(accfem_handle* h, double* node_pos, double* node_quat);

@@ -52,7 +52,12 @@ class accfem_state(ctypes.Structure):
 EXPORTS = ["accfem_default_options", "accfem_create", "accfem_solve", "accfem_solve_tip_load",
            "accfem_solve_resident", "accfem_reset", "accfem_set_stream", "accfem_transfer_bytes",
            "accfem_time_kernel", "accfem_get_state", "accfem_kernel_launches", "accfem_destroy",
-           "accfem_status_string", "accfem_last_error", "accfem_detect_contacts_noalloc"]
+           "accfem_status_string", "accfem_last_error", "accfem_detect_contacts_noalloc",
+           "accfem_batch_create", "accfem_batch_begin", "accfem_batch_advance", "accfem_batch_poll",
+           "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream", "accfem_batch_transfer_bytes",
+           "accfem_batch_kernel_launches", "accfem_batch_last_error", "accfem_batch_destroy"]
+
+MAX_CABLES = 8
 
 KERNEL_ELEMENT, KERNEL_COLLIDE, KERNEL_ASSEMBLE, KERNEL_CONTACT = range(4)
 
@@ -91,9 +96,28 @@ def load(path=LIB_PATH):
     lib.accfem_status_string.restype = ctypes.c_char_p
     lib.accfem_last_error.argtypes = [H]
     lib.accfem_last_error.restype = ctypes.c_char_p
+    B = ctypes.c_void_p
+    lib.accfem_batch_create.argtypes = [ctypes.POINTER(H), ctypes.c_int32, ctypes.POINTER(B)]
+    lib.accfem_batch_begin.argtypes = [B, ctypes.c_int32, _dp, ctypes.c_double]
+    lib.accfem_batch_advance.argtypes = [B, ctypes.c_int32, _ip]
+    lib.accfem_batch_poll.argtypes = [B, ctypes.c_int32, _ip, ctypes.POINTER(ctypes.c_int), _ip]
+    lib.accfem_batch_results.argtypes = [B, _ip, ctypes.c_int32, ctypes.POINTER(accfem_result),
+                                         ctypes.POINTER(ctypes.c_int)]
+    lib.accfem_batch_solve.argtypes = [B, _dp, _dp, _ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(accfem_result)]
+    lib.accfem_batch_set_stream.argtypes = [B, ctypes.c_void_p]
+    lib.accfem_batch_transfer_bytes.argtypes = [B, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.accfem_batch_kernel_launches.argtypes = [B]
+    lib.accfem_batch_kernel_launches.restype = ctypes.c_int64
+    lib.accfem_batch_last_error.argtypes = [B]
+    lib.accfem_batch_last_error.restype = ctypes.c_char_p
+    lib.accfem_batch_destroy.argtypes = [B]
+    lib.accfem_batch_destroy.restype = None
     for name in ("accfem_default_options", "accfem_create", "accfem_solve", "accfem_solve_tip_load",
                  "accfem_solve_resident", "accfem_get_state", "accfem_reset", "accfem_set_stream",
-                 "accfem_transfer_bytes", "accfem_time_kernel", "accfem_detect_contacts_noalloc"):
+                 "accfem_transfer_bytes", "accfem_time_kernel", "accfem_detect_contacts_noalloc",
+                 "accfem_batch_create", "accfem_batch_begin", "accfem_batch_advance", "accfem_batch_poll",
+                 "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream",
+                 "accfem_batch_transfer_bytes"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -244,3 +268,99 @@ class AccFem:
 
     def accfem_last_error(self):
         return self._lib.accfem_last_error(self.h).decode()
+
+
+class AccFemBatch:
+    """A batch over AccFem members (accfem_batch_* in include/accfem.h): solves of all members advance
+    together, one kernel launch per Newton phase; members start and finish solves independently."""
+
+    def __init__(self, members):
+        lib = load()
+        self._lib = lib
+        self.members = list(members)
+        n = len(self.members)
+        arr = (ctypes.c_void_p * n)(*[m.h.value for m in self.members])
+        b = ctypes.c_void_p()
+        st = lib.accfem_batch_create(ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), n, ctypes.byref(b))
+        if st != OK:
+            raise RuntimeError("accfem_batch_create failed: %s" % accfem_status_string(st))
+        self.b = b
+        self.n = n
+
+    def close(self):
+        if getattr(self, "b", None):
+            self._lib.accfem_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def accfem_batch_begin(self, member, tensions, insertion):
+        t = np.ascontiguousarray(tensions, dtype=np.float64)
+        return int(self._lib.accfem_batch_begin(self.b, int(member), _ptr(t), float(insertion)))
+
+    def accfem_batch_advance(self, max_iters):
+        left = ctypes.c_int32(0)
+        st = self._lib.accfem_batch_advance(self.b, int(max_iters), ctypes.byref(left))
+        return int(st), int(left.value)
+
+    def accfem_batch_poll(self, member):
+        done, st, it = ctypes.c_int32(0), ctypes.c_int(0), ctypes.c_int32(0)
+        self._lib.accfem_batch_poll(self.b, int(member), ctypes.byref(done), ctypes.byref(st), ctypes.byref(it))
+        return bool(done.value), int(st.value), int(it.value)
+
+    def accfem_batch_results(self, members):
+        """Results of the last finished solves of `members` as dicts (same keys as AccFem.accfem_solve)."""
+        members = [int(i) for i in members]
+        k = len(members)
+        rs = (accfem_result * max(k, 1))()
+        for j, i in enumerate(members):
+            rs[j] = self.members[i]._result_struct()
+        sts = (ctypes.c_int * max(k, 1))()
+        ids = np.ascontiguousarray(members, dtype=np.int32)
+        self._lib.accfem_batch_results(self.b, _ptr(ids, _ip), k, rs, sts)
+        out = []
+        for j, i in enumerate(members):
+            d = self.members[i]._pack(sts[j], rs[j])
+            d["error"] = self.accfem_batch_last_error()
+            out.append(d)
+        return out
+
+    def accfem_batch_solve(self, tensions, insertions, mask=None, results=True):
+        """One solve of every (masked) member; tensions is (n, k <= 8), insertions (n,).  Returns
+        (first status, per-member statuses, per-member result dicts or None)."""
+        t = np.zeros((self.n, MAX_CABLES))
+        ta = np.asarray(tensions, dtype=np.float64).reshape(self.n, -1)
+        t[:, :ta.shape[1]] = ta
+        ins = np.ascontiguousarray(insertions, dtype=np.float64)
+        mk = None if mask is None else np.ascontiguousarray(mask, dtype=np.int32)
+        sts = (ctypes.c_int * self.n)()
+        rs = None
+        if results:
+            rs = (accfem_result * self.n)()
+            for i, m in enumerate(self.members):
+                rs[i] = m._result_struct()
+        st = self._lib.accfem_batch_solve(self.b, _ptr(t), _ptr(ins), _ptr(mk, _ip) if mk is not None else None, sts, rs)
+        statuses = [int(sts[i]) for i in range(self.n)]
+        out = None
+        if results:
+            sel = range(self.n) if mask is None else [i for i in range(self.n) if mask[i]]
+            out = {i: self.members[i]._pack(statuses[i], rs[i]) for i in sel}
+        return int(st), statuses, out
+
+    def accfem_batch_set_stream(self, stream_ptr):
+        return int(self._lib.accfem_batch_set_stream(self.b, ctypes.c_void_p(int(stream_ptr)) if stream_ptr else None))
+
+    def accfem_batch_transfer_bytes(self):
+        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        self._lib.accfem_batch_transfer_bytes(self.b, ctypes.byref(a), ctypes.byref(b))
+        return int(a.value), int(b.value)
+
+    def accfem_batch_kernel_launches(self):
+        return int(self._lib.accfem_batch_kernel_launches(self.b))
+
+    def accfem_batch_last_error(self):
+        return self._lib.accfem_batch_last_error(self.b).decode()

@@ -11,9 +11,13 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libaccfem.so")
-UNITS = ["element", "collide", "btd", "contact", "update", "api", "noalloc"]
+UNITS = ["element", "collide", "btd", "contact", "update", "api", "batch", "noalloc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+# -fmad=false: no implicit contraction of a * b + c into a fused multiply-add; every FMA of the
+# kernels is an explicit fma() in the source, so the rounding of each expression is fixed by the
+# source alone (the same block body gives the same bits in its single-instance and batched kernels,
+# and the collision predicates round like a plain FP64 evaluation).
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
 
 def _nvcc():

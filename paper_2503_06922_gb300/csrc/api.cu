@@ -10,7 +10,8 @@
 #include <map>
 
 #include "../../include/accfem.h"
-#include "common.cuh"
+#include "handle.h"
+#include "batch.cuh"
 
 namespace accfem {
 __global__ void element_kernel(Params p, Dev d);
@@ -29,29 +30,6 @@ void upload_element_tables();
 }  // namespace accfem
 
 using namespace accfem;
-
-struct accfem_handle {
-  Params p;
-  Dev d;
-  cudaStream_t stream = nullptr;
-  std::vector<void*> allocs;
-  Ctl* h_ctl = nullptr;            // pinned host mirror of the control block
-  double* h_stage = nullptr;       // pinned staging for results
-  size_t stage_bytes = 0;
-  bool has_state = false;
-  double delta = 0.0;
-  int64_t launches = 0;
-  int nf_cap = 0;
-  int max_newton = 200;
-  std::string err;
-  struct LoopGraph { cudaGraph_t graph = nullptr; cudaGraphExec_t exec = nullptr; int body_kernels = 0; };
-  std::map<int, LoopGraph> graphs;   // device-side Newton loop, one per number of free nodes
-  bool stream_mode = false;          // ACCFEM_LAUNCH=stream: host-driven loop (kernels visible to profilers)
-  bool trace = false;                // ACCFEM_TRACE=1 (with stream mode): one line per Newton iteration on stderr
-  cudaStream_t user_stream = nullptr; // caller's stream (accfem_set_stream), else the handle's own
-  int64_t h2d = 0, d2h = 0;          // bytes copied by solve / state calls
-  cudaStream_t work() const { return user_stream ? user_stream : stream; }
-};
 
 namespace {
 
@@ -102,10 +80,6 @@ void quat_of_matrix(const double* R, double* q) {   // R row-major, Shepperd bra
   if (q[0] < 0) for (int i = 0; i < 4; ++i) q[i] = -q[i];
   double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
   for (int i = 0; i < 4; ++i) q[i] /= n;
-}
-
-int last_prescribed(double L, int M, double delta) {
-  return (int)std::floor((L - delta) * M / L + 1e-6);
 }
 
 }  // namespace
@@ -222,6 +196,7 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
   p.nrhs_cap = opt.max_contacts + 1;
   p.eps_d = 1e-6;
   p.eps_b = 1e-3f;
+  p.max_newton = opt.max_newton_iters;
   h->nf_cap = p.M;
   h->max_newton = opt.max_newton_iters;
   {
@@ -384,26 +359,22 @@ int enqueue_iteration(accfem_handle* h, int nf, cudaStream_t st, cudaGraphCondit
   Params& p = h->p;
   Dev& d = h->d;
   int n = 0;
-  element_kernel<<<(nf + kWarpsPerElemBlock - 1) / kWarpsPerElemBlock, 32 * kWarpsPerElemBlock, 0, st>>>(p, d); ++n;
-  collide_kernel<<<(nf + 3) / 4, 128, 0, st>>>(p, d); ++n;
+  auto grid = [nf](int ph) { return dim3(phase_gx(ph, nf), phase_gy(ph)); };
+  element_kernel<<<grid(PH_ELEM), 32 * kWarpsPerElemBlock, 0, st>>>(p, d); ++n;
+  collide_kernel<<<grid(PH_COLL), 128, 0, st>>>(p, d); ++n;
   compact_kernel<<<1, 1024, 0, st>>>(p, d); ++n;
-  assemble_rhs_kernel<<<dim3(nf, kRhsSplit), dim3(32, 6), 0, st>>>(p, d); ++n;
+  assemble_rhs_kernel<<<grid(PH_ASM), dim3(32, 6), 0, st>>>(p, d); ++n;
   // block cyclic reduction: level-1 eliminations, then one kernel per level s that updates the kept
   // nodes, eliminates the next level's nodes (or the root) and reduces the RHS; back substitution
-  std::vector<int> strides;
-  for (int s = 1; s < nf; s *= 2) strides.push_back(s);
-  if (nf >= 2) { bcr_elim_kernel<<<(nf - 2) / 2 + 1, 64, 0, st>>>(p, d, 1); ++n; }
-  if (strides.empty()) { bcr_level_kernel<<<dim3(1, kRhsSplit), 192, 0, st>>>(p, d, 1); ++n; }
-  for (int s : strides) {
-    bcr_level_kernel<<<dim3((nf - 1) / (2 * s) + 1, kRhsSplit), 192, 0, st>>>(p, d, s); ++n;
-  }
-  for (int si = (int)strides.size() - 1; si >= 0; --si) {
-    int s = strides[si];
-    bcr_bwd_kernel<<<dim3((nf - s - 1) / (2 * s) + 1, kRhsSplit), 192, 0, st>>>(p, d, s); ++n;
-  }
+  if (nf >= 2) { bcr_elim_kernel<<<grid(PH_ELIM1), 64, 0, st>>>(p, d, 1); ++n; }
+  int levels = 0;
+  while (levels < kMaxLevels && phase_gx(PH_LEV0 + levels, nf) > 0) ++levels;
+  for (int j = 0; j < levels; ++j) { bcr_level_kernel<<<grid(PH_LEV0 + j), 192, 0, st>>>(p, d, 1 << j); ++n; }
+  for (int j = levels - 1; j >= 0; --j)
+    if (phase_gx(PH_BWD0 + j, nf) > 0) { bcr_bwd_kernel<<<grid(PH_BWD0 + j), 192, 0, st>>>(p, d, 1 << j); ++n; }
   contact_kernel<<<1, 256, 0, st>>>(p, d); ++n;
-  step_kernel<<<(nf + 31) / 32, dim3(32, 6), 0, st>>>(p, d); ++n;
-  apply_kernel<<<(nf + 127) / 128, 128, 0, st>>>(p, d); ++n;
+  step_kernel<<<grid(PH_STEP), dim3(32, 6), 0, st>>>(p, d); ++n;
+  apply_kernel<<<grid(PH_APPLY), 128, 0, st>>>(p, d); ++n;
   ctl_kernel<<<1, 1, 0, st>>>(p, d, cond, h->max_newton, h->stream_mode ? 0 : 1); ++n;
   return n;
 }
@@ -451,7 +422,7 @@ accfem_status run_solve(accfem_handle* h, int load_mode, const double* tensions_
   Params& p = h->p;
   Dev& d = h->d;
   if (!(insertion >= 0.0 && insertion <= p.L)) return fail(h, ACCFEM_E_INVALID_ARG, "insertion outside [0, length]");
-  const int k = std::min(std::max(last_prescribed(p.L, p.M, insertion), 0), p.M);
+  const int k = std::min(std::max(accfem_last_prescribed(p.L, p.M, insertion), 0), p.M);
   const int nf = p.M - k;
   Ctl& c = *h->h_ctl;
   std::memset(&c, 0, sizeof(Ctl));
@@ -685,9 +656,10 @@ accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t
   auto launch = [&]() {
     switch (kernel) {
       case ACCFEM_KERNEL_ELEMENT:
-        element_kernel<<<(nf + kWarpsPerElemBlock - 1) / kWarpsPerElemBlock, 32 * kWarpsPerElemBlock, 0, st>>>(p, d); break;
-      case ACCFEM_KERNEL_COLLIDE: collide_kernel<<<(nf + 3) / 4, 128, 0, st>>>(p, d); break;
-      case ACCFEM_KERNEL_ASSEMBLE: assemble_rhs_kernel<<<dim3(nf, kRhsSplit), dim3(32, 6), 0, st>>>(p, d); break;
+        element_kernel<<<phase_gx(PH_ELEM, nf), 32 * kWarpsPerElemBlock, 0, st>>>(p, d); break;
+      case ACCFEM_KERNEL_COLLIDE: collide_kernel<<<phase_gx(PH_COLL, nf), 128, 0, st>>>(p, d); break;
+      case ACCFEM_KERNEL_ASSEMBLE:
+        assemble_rhs_kernel<<<dim3(phase_gx(PH_ASM, nf), phase_gy(PH_ASM)), dim3(32, 6), 0, st>>>(p, d); break;
       default: contact_kernel<<<1, 256, 0, st>>>(p, d); break;
     }
   };

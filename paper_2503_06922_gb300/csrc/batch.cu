@@ -1,0 +1,503 @@
+// Batched solves (include/accfem.h, accfem_batch_*): many handles advanced together, one persistent
+// launch per Newton phase.  The paper solves one robot at a time; every member of a batch runs the
+// block bodies of the single-instance kernels on its own buffers, so its iterates are those of
+// accfem_solve.  Solves start and finish independently (continuous batching): accfem_batch_begin
+// stages a solve, accfem_batch_advance starts the staged solves and runs a bounded number of
+// iterations of everything in flight inside one CUDA graph (a conditional WHILE node whose body
+// ends with the plan kernel), and finished members are collected with one gather and one copy.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/accfem.h"
+#include "handle.h"
+#include "batch.cuh"
+
+namespace accfem {
+__global__ void element_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
+__global__ void collide_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
+__global__ void compact_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
+__global__ void assemble_rhs_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
+__global__ void bcr_elim_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
+__global__ void bcr_level_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j);
+__global__ void bcr_bwd_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j);
+__global__ void contact_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
+__global__ void step_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
+__global__ void apply_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
+__global__ void batch_begin_kernel(const Inst* __restrict__ tab, const Ctl* __restrict__ staged,
+                                   const BatchBegin* __restrict__ bg);
+__global__ void start_batch(const Inst* __restrict__ tab, const BatchBegin* __restrict__ bg);
+__global__ void batch_plan_kernel(const Inst* __restrict__ tab, Plan* plan, int n_inst, int do_ctl, int max_passes,
+                                  cudaGraphConditionalHandle h, int set_cond);
+
+// Result gather: block j packs member members[j] at out + off[j]: 7 N poses (x, y, z, qw, qx, qy,
+// qz, each N long), 6 base reaction values, then m rows of 9 values (free-node index, triangle,
+// point 3, normal 3, force).
+__global__ void __launch_bounds__(256) batch_pack_kernel(const Inst* __restrict__ tab, const int* __restrict__ members,
+                                                         const long long* __restrict__ off, double* out) {
+  const int mb = members[blockIdx.x];
+  const Params& p = tab[mb].p;
+  const Dev& d = tab[mb].d;
+  const Ctl* c = d.ctl;
+  double* o = out + off[blockIdx.x];
+  const int N = p.N;
+  const double* src[7] = {d.px, d.py, d.pz, d.qw, d.qx, d.qy, d.qz};
+  for (int i = threadIdx.x; i < N; i += blockDim.x)
+#pragma unroll
+    for (int a = 0; a < 7; ++a) o[(size_t)a * N + i] = src[a][i];
+  o += (size_t)7 * N;
+  const bool iterated = c->nf > 0 && c->iter > 0;
+  if (threadIdx.x < 6) o[threadIdx.x] = iterated ? d.elem[(size_t)c->k * kElemStride + 78 + threadIdx.x] : 0.0;
+  o += 6;
+  const int m = iterated ? c->m : 0;
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    double* q = o + 9 * (size_t)r;
+    q[0] = (double)d.c_node[r];
+    q[1] = (double)d.c_tri[r];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { q[2 + a] = d.c_pt[3 * r + a]; q[5 + a] = d.c_n[3 * r + a]; }
+    q[8] = d.y[r];
+  }
+}
+}  // namespace accfem
+
+using namespace accfem;
+
+struct accfem_batch {
+  std::vector<accfem_handle*> members;
+  int n = 0;
+  int max_nodes = 0;
+  int levels = 0;
+  cudaStream_t stream = nullptr, user_stream = nullptr;
+  Inst* d_tab = nullptr;
+  Plan* d_plan = nullptr;
+  Ctl* d_ctl = nullptr;             // control block of member i (the batch's own)
+  Ctl* d_stage = nullptr;           // staged control blocks of the solves begun since the last advance
+  BatchBegin* d_begin = nullptr;
+  int* d_members = nullptr;         // result gather: member list, offsets, packed values
+  long long* d_off = nullptr;
+  double* d_pack = nullptr;
+  size_t pack_cap = 0;              // doubles
+  Ctl* h_ctl = nullptr;             // pinned host mirrors
+  Ctl* h_stage = nullptr;
+  BatchBegin* h_begin = nullptr;
+  int* h_members = nullptr;
+  long long* h_off = nullptr;
+  double* h_pack = nullptr;
+  int* h_passes = nullptr;
+  int n_begin = 0;
+  std::vector<int> state;           // 0 idle, 1 staged, 2 in flight
+  std::vector<int> solved;          // member finished at least one solve in this batch
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int body_kernels = 0;
+  int grid[kPhases] = {};
+  int64_t launches = 0, h2d = 0, d2h = 0;
+  std::string err;
+  cudaStream_t work() const { return user_stream ? user_stream : stream; }
+};
+
+namespace {
+
+accfem_status bfail(accfem_batch* b, accfem_status s, const std::string& msg) {
+  if (b) b->err = msg;
+  return s;
+}
+
+bool bok(accfem_batch* b, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return true;
+  if (b) b->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return false;
+}
+
+accfem_status outcome(const Ctl& c) {
+  if (c.status != 0) return (accfem_status)c.status;
+  if (c.nf == 0 || c.converged) return ACCFEM_OK;
+  return ACCFEM_E_NOT_CONVERGED;
+}
+
+// Persistent grid of a batched phase kernel: resident blocks on every SM, at most the largest
+// number of units the members can produce.
+template <class K>
+int persistent_grid(K kernel, int threads, long long max_units) {
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0);
+  long long g = (long long)std::max(sms, 1) * std::max(occ, 1);
+  g = std::min(g, std::max(max_units, 1ll));
+  return (int)g;
+}
+
+bool build_graph(accfem_batch* b) {
+  long long units[kPhases] = {};
+  for (accfem_handle* h : b->members)
+    for (int ph = 0; ph < kPhases; ++ph) units[ph] += (long long)phase_gx(ph, h->p.M) * phase_gy(ph);
+  b->grid[PH_ELEM] = persistent_grid(element_batch, 32 * kWarpsPerElemBlock, units[PH_ELEM]);
+  b->grid[PH_COLL] = persistent_grid(collide_batch, 128, units[PH_COLL]);
+  b->grid[PH_COMPACT] = persistent_grid(compact_batch, 1024, units[PH_COMPACT]);
+  b->grid[PH_ASM] = persistent_grid(assemble_rhs_batch, 192, units[PH_ASM]);
+  b->grid[PH_ELIM1] = persistent_grid(bcr_elim_batch, 64, units[PH_ELIM1]);
+  b->grid[PH_CONTACT] = persistent_grid(contact_batch, 256, units[PH_CONTACT]);
+  b->grid[PH_STEP] = persistent_grid(step_batch, 192, units[PH_STEP]);
+  b->grid[PH_APPLY] = persistent_grid(apply_batch, 128, units[PH_APPLY]);
+  for (int j = 0; j < b->levels; ++j) {
+    b->grid[PH_LEV0 + j] = persistent_grid(bcr_level_batch, 192, units[PH_LEV0 + j]);
+    b->grid[PH_BWD0 + j] = persistent_grid(bcr_bwd_batch, 192, units[PH_BWD0 + j]);
+  }
+  cudaGraphConditionalHandle cond;
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t node;
+  if (!bok(b, cudaGraphCreate(&b->graph, 0), "cudaGraphCreate") ||
+      !bok(b, cudaGraphConditionalHandleCreate(&cond, b->graph, 1, cudaGraphCondAssignDefault), "conditional handle"))
+    return false;
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (!bok(b, cudaGraphAddNode(&node, b->graph, nullptr, nullptr, 0, &cp), "conditional node")) return false;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t st = b->stream;
+  if (!bok(b, cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed), "begin capture"))
+    return false;
+  const Inst* tab = b->d_tab;
+  Plan* plan = b->d_plan;
+  const int* g = b->grid;
+  int n = 0;
+  element_batch<<<g[PH_ELEM], 32 * kWarpsPerElemBlock, 0, st>>>(tab, plan); ++n;
+  collide_batch<<<g[PH_COLL], 128, 0, st>>>(tab, plan); ++n;
+  compact_batch<<<g[PH_COMPACT], 1024, 0, st>>>(tab, plan); ++n;
+  assemble_rhs_batch<<<g[PH_ASM], dim3(32, 6), 0, st>>>(tab, plan); ++n;
+  bcr_elim_batch<<<g[PH_ELIM1], 64, 0, st>>>(tab, plan); ++n;
+  for (int j = 0; j < b->levels; ++j) { bcr_level_batch<<<g[PH_LEV0 + j], 192, 0, st>>>(tab, plan, j); ++n; }
+  for (int j = b->levels - 1; j >= 0; --j) { bcr_bwd_batch<<<g[PH_BWD0 + j], 192, 0, st>>>(tab, plan, j); ++n; }
+  contact_batch<<<g[PH_CONTACT], 256, 0, st>>>(tab, plan); ++n;
+  step_batch<<<g[PH_STEP], dim3(32, 6), 0, st>>>(tab, plan); ++n;
+  apply_batch<<<g[PH_APPLY], 128, 0, st>>>(tab, plan); ++n;
+  batch_plan_kernel<<<1, 1024, 0, st>>>(tab, plan, b->n, 1, 0, cond, 1); ++n;
+  cudaError_t ce = cudaStreamEndCapture(st, &body);
+  if (!bok(b, ce, "end capture") || !bok(b, cudaGraphInstantiate(&b->exec, b->graph, 0), "instantiate graph")) {
+    cudaGetLastError();
+    return false;
+  }
+  b->body_kernels = n;
+  return true;
+}
+
+template <typename T>
+bool balloc(accfem_batch* b, T** dptr, size_t count) {
+  if (count == 0) count = 1;
+  if (cudaMalloc((void**)dptr, count * sizeof(T)) != cudaSuccess) {
+    b->err = "cudaMalloc failed";
+    return false;
+  }
+  cudaMemset(*dptr, 0, count * sizeof(T));
+  return true;
+}
+
+template <typename T>
+bool bhost(accfem_batch* b, T** hptr, size_t count) {
+  if (count == 0) count = 1;
+  if (cudaMallocHost((void**)hptr, count * sizeof(T)) != cudaSuccess) {
+    b->err = "cudaMallocHost failed";
+    return false;
+  }
+  std::memset(*hptr, 0, count * sizeof(T));
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void accfem_batch_destroy(accfem_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (void* p : {(void*)b->d_tab, (void*)b->d_plan, (void*)b->d_ctl, (void*)b->d_stage, (void*)b->d_begin,
+                  (void*)b->d_members, (void*)b->d_off, (void*)b->d_pack})
+    if (p) cudaFree(p);
+  for (void* p : {(void*)b->h_ctl, (void*)b->h_stage, (void*)b->h_begin, (void*)b->h_members, (void*)b->h_off,
+                  (void*)b->h_pack, (void*)b->h_passes})
+    if (p) cudaFreeHost(p);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+accfem_status accfem_batch_create(accfem_handle* const* members, int32_t n_members, accfem_batch** out) {
+  if (!out) return ACCFEM_E_INVALID_ARG;
+  *out = nullptr;
+  if (!members || n_members < 1 || n_members > kMaxBatch) return ACCFEM_E_INVALID_ARG;
+  for (int i = 0; i < n_members; ++i) {
+    if (!members[i]) return ACCFEM_E_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (members[j] == members[i]) return ACCFEM_E_INVALID_ARG;
+  }
+  accfem_batch* b = new accfem_batch();
+  b->members.assign(members, members + n_members);
+  b->n = n_members;
+  b->state.assign(n_members, 0);
+  b->solved.assign(n_members, 0);
+  size_t pack = 0;
+  int max_m = 0;
+  for (accfem_handle* h : b->members) {
+    b->max_nodes = std::max(b->max_nodes, h->p.N);
+    max_m = std::max(max_m, h->p.M);
+    pack += (size_t)7 * h->p.N + 6 + (size_t)9 * h->p.m_cap;
+  }
+  while (b->levels < kMaxLevels && phase_gx(PH_LEV0 + b->levels, max_m) > 0) ++b->levels;
+  b->pack_cap = pack;
+  bool ok = bok(b, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "cudaStreamCreate") &&
+            balloc(b, &b->d_tab, b->n) && balloc(b, &b->d_plan, 1) && balloc(b, &b->d_ctl, b->n) &&
+            balloc(b, &b->d_stage, b->n) && balloc(b, &b->d_begin, b->n) && balloc(b, &b->d_members, b->n) &&
+            balloc(b, &b->d_off, b->n) && balloc(b, &b->d_pack, pack) && bhost(b, &b->h_ctl, b->n) &&
+            bhost(b, &b->h_stage, b->n) && bhost(b, &b->h_begin, b->n) && bhost(b, &b->h_members, b->n) &&
+            bhost(b, &b->h_off, b->n) && bhost(b, &b->h_pack, pack) && bhost(b, &b->h_passes, 4);
+  if (!ok) {
+    accfem_batch_destroy(b);
+    return ACCFEM_E_NOMEM;
+  }
+  std::vector<Inst> tab(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    tab[i].p = b->members[i]->p;
+    tab[i].d = b->members[i]->d;
+    tab[i].d.ctl = b->d_ctl + i;
+  }
+  if (!bok(b, cudaMemcpy(b->d_tab, tab.data(), sizeof(Inst) * b->n, cudaMemcpyHostToDevice), "upload batch table") ||
+      !build_graph(b)) {
+    accfem_batch_destroy(b);
+    return ACCFEM_E_CUDA;
+  }
+  *out = b;
+  return ACCFEM_OK;
+}
+
+accfem_status accfem_batch_set_stream(accfem_batch* b, void* stream) {
+  if (!b) return ACCFEM_E_INVALID_ARG;
+  b->user_stream = (cudaStream_t)stream;
+  return ACCFEM_OK;
+}
+
+accfem_status accfem_batch_begin(accfem_batch* b, int32_t member, const double* cable_tensions, double insertion) {
+  if (!b) return ACCFEM_E_INVALID_ARG;
+  if (member < 0 || member >= b->n) return bfail(b, ACCFEM_E_INVALID_ARG, "member index out of range");
+  if (b->state[member] != 0) return bfail(b, ACCFEM_E_INVALID_ARG, "member has a solve staged or in flight");
+  accfem_handle* h = b->members[member];
+  const Params& p = h->p;
+  if (!(insertion >= 0.0 && insertion <= p.L)) return bfail(b, ACCFEM_E_INVALID_ARG, "insertion outside [0, length]");
+  if (p.n_cables > 0 && !cable_tensions) return bfail(b, ACCFEM_E_INVALID_ARG, "NULL cable tensions");
+  for (int j = 0; j < p.n_cables; ++j)
+    if (!(cable_tensions[j] >= 0.0) || !std::isfinite(cable_tensions[j]))
+      return bfail(b, ACCFEM_E_INVALID_ARG, "cable tensions must be finite and non-negative");
+  const int k = std::min(std::max(accfem_last_prescribed(p.L, p.M, insertion), 0), p.M);
+  Ctl& c = b->h_stage[b->n_begin];
+  std::memset(&c, 0, sizeof(Ctl));
+  c.k = k;
+  c.nf = p.M - k;
+  c.m_prev = -1;
+  c.rho = p.beta0;
+  c.load_mode = 0;
+  c.delta = insertion;
+  c.live = c.nf > 0 ? 1 : 0;
+  for (int j = 0; j < p.n_cables; ++j) c.tension[j] = cable_tensions[j];
+  BatchBegin& g = b->h_begin[b->n_begin];
+  g.member = member;
+  g.mode = h->has_state ? 1 : 0;
+  g.k = k;
+  g.pad = 0;
+  g.delta = insertion;
+  g.delta_old = h->delta;
+  ++b->n_begin;
+  h->has_state = true;
+  h->delta = insertion;
+  b->state[member] = 1;
+  return ACCFEM_OK;
+}
+
+accfem_status accfem_batch_advance(accfem_batch* b, int32_t max_iters, int32_t* n_in_flight) {
+  if (!b || max_iters < 1) return bfail(b, ACCFEM_E_INVALID_ARG, "NULL batch or max_iters < 1");
+  b->err.clear();
+  cudaStream_t st = b->work();
+  if (b->n_begin > 0) {
+    const int nb = b->n_begin;
+    if (!bok(b, cudaMemcpyAsync(b->d_stage, b->h_stage, sizeof(Ctl) * nb, cudaMemcpyHostToDevice, st), "upload control") ||
+        !bok(b, cudaMemcpyAsync(b->d_begin, b->h_begin, sizeof(BatchBegin) * nb, cudaMemcpyHostToDevice, st), "upload begin"))
+      return ACCFEM_E_CUDA;
+    b->h2d += (sizeof(Ctl) + sizeof(BatchBegin)) * nb;
+    const dim3 grid((b->max_nodes + 127) / 128, nb);
+    batch_begin_kernel<<<grid, 128, 0, st>>>(b->d_tab, b->d_stage, b->d_begin);
+    start_batch<<<grid, 128, 0, st>>>(b->d_tab, b->d_begin);
+    b->launches += 2;
+    for (int i = 0; i < nb; ++i) b->state[b->h_begin[i].member] = 2;
+    b->n_begin = 0;
+  }
+  int flying = 0;
+  for (int i = 0; i < b->n; ++i) flying += b->state[i] == 2;
+  if (flying > 0) {
+    batch_plan_kernel<<<1, 1024, 0, st>>>(b->d_tab, b->d_plan, b->n, 0, max_iters, cudaGraphConditionalHandle(), 0);
+    ++b->launches;
+    if (!bok(b, cudaGetLastError(), "kernel launch") || !bok(b, cudaGraphLaunch(b->exec, st), "launch batch graph"))
+      return ACCFEM_E_CUDA;
+  }
+  if (!bok(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(Ctl) * b->n, cudaMemcpyDeviceToHost, st), "read control") ||
+      !bok(b, cudaMemcpyAsync(b->h_passes, &b->d_plan->passes, sizeof(int), cudaMemcpyDeviceToHost, st), "read plan") ||
+      !bok(b, cudaStreamSynchronize(st), "batch advance"))
+    return ACCFEM_E_CUDA;
+  b->d2h += sizeof(Ctl) * b->n + sizeof(int);
+  if (flying > 0) b->launches += (int64_t)b->body_kernels * std::max(*b->h_passes, 1);
+  int left = 0;
+  for (int i = 0; i < b->n; ++i) {
+    if (b->state[i] != 2) {
+      left += b->state[i] == 1;
+      continue;
+    }
+    if (b->h_ctl[i].live) {
+      ++left;
+      continue;
+    }
+    b->state[i] = 0;
+    b->solved[i] = 1;
+    *b->members[i]->h_ctl = b->h_ctl[i];
+  }
+  if (n_in_flight) *n_in_flight = left;
+  return ACCFEM_OK;
+}
+
+accfem_status accfem_batch_poll(const accfem_batch* b, int32_t member, int32_t* done, accfem_status* solve_status,
+                                int32_t* newton_iters) {
+  if (!b || member < 0 || member >= b->n || !done) return ACCFEM_E_INVALID_ARG;
+  *done = b->state[member] == 0 ? 1 : 0;
+  const Ctl& c = b->h_ctl[member];
+  const bool have = *done && b->solved[member];
+  if (solve_status) *solve_status = have ? outcome(c) : ACCFEM_OK;
+  if (newton_iters) *newton_iters = have ? c.iter : 0;
+  return ACCFEM_OK;
+}
+
+accfem_status accfem_batch_results(accfem_batch* b, const int32_t* members, int32_t count, accfem_result* out,
+                                   accfem_status* statuses) {
+  if (!b || count < 0 || count > b->n || (count > 0 && (!members || !out))) return bfail(b, ACCFEM_E_INVALID_ARG, "bad arguments");
+  if (count == 0) return ACCFEM_OK;
+  long long off = 0;
+  std::vector<int> ms(count);
+  for (int j = 0; j < count; ++j) {
+    const int i = members[j];
+    if (i < 0 || i >= b->n || b->state[i] != 0 || !b->solved[i])
+      return bfail(b, ACCFEM_E_INVALID_ARG, "member has no finished solve");
+    const Ctl& c = b->h_ctl[i];
+    const int m = (c.nf > 0 && c.iter > 0) ? c.m : 0;
+    b->h_members[j] = i;
+    b->h_off[j] = off;
+    ms[j] = m;
+    off += (long long)7 * b->members[i]->p.N + 6 + 9ll * m;
+  }
+  if ((size_t)off > b->pack_cap) return bfail(b, ACCFEM_E_INVALID_ARG, "result larger than the gather buffer");
+  cudaStream_t st = b->work();
+  if (!bok(b, cudaMemcpyAsync(b->d_members, b->h_members, sizeof(int) * count, cudaMemcpyHostToDevice, st), "upload list") ||
+      !bok(b, cudaMemcpyAsync(b->d_off, b->h_off, sizeof(long long) * count, cudaMemcpyHostToDevice, st), "upload offsets"))
+    return ACCFEM_E_CUDA;
+  batch_pack_kernel<<<count, 256, 0, st>>>(b->d_tab, b->d_members, b->d_off, b->d_pack);
+  ++b->launches;
+  if (!bok(b, cudaGetLastError(), "gather results") ||
+      !bok(b, cudaMemcpyAsync(b->h_pack, b->d_pack, sizeof(double) * off, cudaMemcpyDeviceToHost, st), "download results") ||
+      !bok(b, cudaStreamSynchronize(st), "download results"))
+    return ACCFEM_E_CUDA;
+  b->h2d += (sizeof(int) + sizeof(long long)) * count;
+  b->d2h += sizeof(double) * off;
+  accfem_status first = ACCFEM_OK;
+  for (int j = 0; j < count; ++j) {
+    const int i = members[j];
+    const Ctl& c = b->h_ctl[i];
+    const int N = b->members[i]->p.N, m = ms[j];
+    const double* s = b->h_pack + b->h_off[j];
+    accfem_result& r = out[j];
+    accfem_status st_j = outcome(c);
+    if (r.node_pos)
+      for (int n = 0; n < N; ++n)
+        for (int a = 0; a < 3; ++a) r.node_pos[3 * n + a] = s[(size_t)a * N + n];
+    if (r.node_quat)
+      for (int n = 0; n < N; ++n)
+        for (int a = 0; a < 4; ++a) r.node_quat[4 * n + a] = s[(size_t)(3 + a) * N + n];
+    s += (size_t)7 * N;
+    for (int a = 0; a < 6; ++a) r.base_reaction[a] = s[a];
+    s += 6;
+    r.newton_iters = c.iter;
+    r.contact_iters = c.lcp_pivots;
+    r.residual = c.nf > 0 ? __builtin_bit_cast(double, (unsigned long long)c.res_bits) : 0.0;
+    r.n_contacts = m;
+    const int nw = std::min(m, std::max(r.contact_capacity, 0));
+    for (int q = 0; q < nw; ++q) {
+      const double* row = s + 9 * (size_t)q;
+      if (r.contact_node) r.contact_node[q] = c.k + 1 + (int)row[0];
+      if (r.contact_tri) r.contact_tri[q] = (int)row[1];
+      for (int a = 0; a < 3; ++a) {
+        if (r.contact_point) r.contact_point[3 * q + a] = row[2 + a];
+        if (r.contact_normal) r.contact_normal[3 * q + a] = row[5 + a];
+      }
+      if (r.contact_force) r.contact_force[q] = row[8];
+    }
+    if (m > r.contact_capacity && st_j == ACCFEM_OK) st_j = ACCFEM_E_CONTACT_CAPACITY;
+    if (statuses) statuses[j] = st_j;
+    if (first == ACCFEM_OK && st_j != ACCFEM_OK) first = st_j;
+  }
+  return first;
+}
+
+accfem_status accfem_batch_solve(accfem_batch* b, const double* cable_tensions, const double* insertions,
+                                 const int32_t* mask, accfem_status* statuses, accfem_result* results) {
+  if (!b || !insertions) return bfail(b, ACCFEM_E_INVALID_ARG, "NULL argument");
+  std::vector<int32_t> list;
+  for (int i = 0; i < b->n; ++i) {
+    if (mask && !mask[i]) continue;
+    if (b->state[i] != 0) return bfail(b, ACCFEM_E_INVALID_ARG, "member has a solve staged or in flight");
+    list.push_back(i);
+  }
+  for (int32_t i : list) {
+    accfem_status s = accfem_batch_begin(b, i, cable_tensions ? cable_tensions + (size_t)ACCFEM_MAX_CABLES * i : nullptr,
+                                         insertions[i]);
+    if (s != ACCFEM_OK) return s;
+  }
+  int cap = 1;
+  for (int32_t i : list) cap = std::max(cap, b->members[i]->max_newton);
+  int32_t left = 0;
+  accfem_status s = accfem_batch_advance(b, cap, &left);
+  for (int guard = 0; s == ACCFEM_OK && left > 0 && guard < 4; ++guard) s = accfem_batch_advance(b, cap, &left);
+  if (s != ACCFEM_OK) return s;
+  if (left > 0) return bfail(b, ACCFEM_E_CUDA, "batch did not finish within its iteration caps");
+  accfem_status first = ACCFEM_OK;
+  if (results) {
+    std::vector<accfem_result> tmp(list.size());
+    std::vector<accfem_status> st(list.size());
+    for (size_t j = 0; j < list.size(); ++j) tmp[j] = results[list[j]];
+    accfem_status r = accfem_batch_results(b, list.data(), (int32_t)list.size(), tmp.data(), st.data());
+    if (r == ACCFEM_E_CUDA || r == ACCFEM_E_INVALID_ARG) return r;
+    first = r;
+    for (size_t j = 0; j < list.size(); ++j) {
+      results[list[j]] = tmp[j];
+      if (statuses) statuses[list[j]] = st[j];
+    }
+  } else {
+    for (int32_t i : list) {
+      accfem_status o = outcome(b->h_ctl[i]);
+      if (statuses) statuses[i] = o;
+      if (first == ACCFEM_OK && o != ACCFEM_OK) first = o;
+    }
+  }
+  return first;
+}
+
+accfem_status accfem_batch_transfer_bytes(const accfem_batch* b, int64_t* h2d, int64_t* d2h) {
+  if (!b || !h2d || !d2h) return ACCFEM_E_INVALID_ARG;
+  *h2d = b->h2d;
+  *d2h = b->d2h;
+  return ACCFEM_OK;
+}
+
+int64_t accfem_batch_kernel_launches(const accfem_batch* b) { return b ? b->launches : 0; }
+
+const char* accfem_batch_last_error(const accfem_batch* b) { return b ? b->err.c_str() : ""; }
+
+}  // extern "C"

@@ -13,7 +13,7 @@
 // x_j = P_j b_j - L_j^T x_{j-s} - R_j^T x_{j+s} (eliminated).  Launches per factor-and-solve:
 // bcr_elim_kernel (level 1), one bcr_level_kernel per level (kept-node update + next level's
 // eliminations + forward RHS; root at the last level), one bcr_bwd_kernel per level.
-#include "common.cuh"
+#include "batch.cuh"
 
 namespace accfem {
 
@@ -27,7 +27,7 @@ __device__ __forceinline__ double kval(const double* rec, int i, int j) {
 // ------------------------------------------------------------------ constraint compaction
 // One CTA: exclusive scan of the per-node row counts, row arrays in (node, triangle) order,
 // comparison with the previous iteration's rows, copy to "previous".
-__global__ void __launch_bounds__(1024) compact_kernel(Params p, Dev d) {
+__device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   __shared__ int s_warp[32];
   __shared__ int s_same;
   Ctl* ctl = d.ctl;
@@ -105,15 +105,21 @@ __global__ void __launch_bounds__(1024) compact_kernel(Params p, Dev d) {
   if (tid == 0) { ctl->same_set = s_same; ctl->m = m; ctl->m_prev = m; }
 }
 
+__global__ void __launch_bounds__(1024) compact_kernel(Params p, Dev d) { compact_body(p, d); }
+
+__global__ void __launch_bounds__(1024) compact_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
+  for_units(tab, plan, PH_COMPACT, [](const Inst& in, int, int) { compact_body(in.p, in.d); });
+}
+
 // ------------------------------------------------------------------ assembly
 // Assembly and RHS columns of one free node (blocks (node, y), 32 x 6 threads): D, U and g = F - F_a
 // with the tip load of Eq. 16-18, then RHS columns 0 = -g and 1 + row = A^T e_row (block y takes the
 // column chunks y, y + kRhsSplit, ...).
-__global__ void __launch_bounds__(192) assemble_rhs_kernel(Params p, Dev d) {
+__device__ __forceinline__ void assemble_rhs_body(const Params& p, const Dev& d, int bx, int by) {
   __shared__ double s_g[6];
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
-  const int f = blockIdx.x;
+  const int f = bx;
   const int nf = ctl->nf;
   if (f >= nf) return;
   const int node = ctl->k + 1 + f;
@@ -121,12 +127,12 @@ __global__ void __launch_bounds__(192) assemble_rhs_kernel(Params p, Dev d) {
   const double* eb = d.elem + (size_t)(node - 1) * kElemStride;
   const double* ea = d.elem + (size_t)node * kElemStride;
   const bool has_a = node < p.M;
-  if (tid < 36 && blockIdx.y == 0) {
+  if (tid < 36 && by == 0) {
     int r = tid / 6, c = tid % 6;
     double v = kval(eb, 6 + r, 6 + c);
     if (has_a) v += kval(ea, r, c);
     d.D[(size_t)f * 36 + tid] = v;
-  } else if (tid >= 36 && tid < 72 && blockIdx.y == 0) {
+  } else if (tid >= 36 && tid < 72 && by == 0) {
     int q = tid - 36, r = q / 6, c = q % 6;
     d.U[(size_t)f * 36 + q] = has_a ? kval(ea, r, 6 + c) : 0.0;
   } else if (tid >= 72 && tid < 78) {
@@ -157,17 +163,25 @@ __global__ void __launch_bounds__(192) assemble_rhs_kernel(Params p, Dev d) {
       }
     }
     s_g[c] = F - Fa;
-    if (blockIdx.y == 0) d.g[(size_t)f * 6 + c] = F - Fa;
+    if (by == 0) d.g[(size_t)f * 6 + c] = F - Fa;
   }
   __syncthreads();
   const int c = threadIdx.y;
   const int nrhs = ctl->m + 1;
-  for (int r = blockIdx.y * 32 + threadIdx.x; r < nrhs; r += 32 * kRhsSplit) {
+  for (int r = by * 32 + threadIdx.x; r < nrhs; r += 32 * kRhsSplit) {
     double v;
     if (r == 0) v = -s_g[c];
     else v = (d.c_node[r - 1] == f && c < 3) ? d.c_n[3 * (r - 1) + c] : 0.0;
     d.B[((size_t)f * 6 + c) * p.nrhs_cap + r] = v;
   }
+}
+
+__global__ void __launch_bounds__(192) assemble_rhs_kernel(Params p, Dev d) {
+  assemble_rhs_body(p, d, blockIdx.x, blockIdx.y);
+}
+
+__global__ void __launch_bounds__(192) assemble_rhs_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
+  for_units(tab, plan, PH_ASM, [](const Inst& in, int bx, int by) { assemble_rhs_body(in.p, in.d, bx, by); });
 }
 
 // ------------------------------------------------------------------ 6x6 helpers (64-thread team)
@@ -196,13 +210,13 @@ __device__ bool team_inverse6(double* sA, int tid, double* s_piv) {
 }
 
 // Eliminations of level 1 (nodes j = 1 + 2 blockIdx.x; later levels are fused into bcr_level_kernel).
-__global__ void __launch_bounds__(64) bcr_elim_kernel(Params p, Dev d, int s) {
+__device__ __forceinline__ void bcr_elim_body(const Params& p, const Dev& d, int bx, int s) {
   __shared__ double sA[36], sX[36], sY[36];
   __shared__ double s_piv[1];
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
   const int nf = ctl->nf;
-  const int j = s + 2 * s * blockIdx.x;
+  const int j = s + 2 * s * bx;
   if (j >= nf) return;
   const int tid = threadIdx.x;
   if (tid < 36) sA[tid] = d.D[(size_t)j * 36 + tid];
@@ -230,19 +244,25 @@ __global__ void __launch_bounds__(64) bcr_elim_kernel(Params p, Dev d, int s) {
   }
 }
 
+__global__ void __launch_bounds__(64) bcr_elim_kernel(Params p, Dev d, int s) { bcr_elim_body(p, d, blockIdx.x, s); }
+
+__global__ void __launch_bounds__(64) bcr_elim_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
+  for_units(tab, plan, PH_ELIM1, [](const Inst& in, int bx, int) { bcr_elim_body(in.p, in.d, bx, 1); });
+}
+
 // Level s of the reduction, fused with the elimination at level 2s.  Blocks (kept node i = 2 s x,
 // y = RHS split), 192 threads.  Block y == 0: Schur update of D_i and U_i (kept nodes i: D_i and U_i as above);
 // when i = 2s (mod 4s) it then eliminates i at level 2s: its new left coupling
 // U_{i-2s} <- -L_{i-s} U_{i-s} is rebuilt from level-s data, P_i = D_i^{-1}, L_i = U_{i-2s} P_i,
 // R_i = U_i^T P_i.  Every block applies the level-s forward reduction to its RHS chunks.  When
 // 2s >= nf only node 0 is kept: every block inverts D_0 itself (root) and solves x_0 = P_0 b_0.
-__global__ void __launch_bounds__(192) bcr_level_kernel(Params p, Dev d, int s) {
+__device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, int bx, int by, int s) {
   __shared__ double sRl[36], sUl[36], sLr[36], sUi[36], sUr[36], sA[36], sX[36], sY[36];
   __shared__ double s_piv[1];
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
   const int nf = ctl->nf;
-  const int i = 2 * s * blockIdx.x;
+  const int i = 2 * s * bx;
   if (i >= nf) return;
   const int tid = threadIdx.x;
   const bool hl = i >= s, hr = i + s < nf, hr2 = i + 2 * s < nf;
@@ -256,7 +276,7 @@ __global__ void __launch_bounds__(192) bcr_level_kernel(Params p, Dev d, int s) 
     sUr[tid] = hr2 ? d.U[(size_t)(i + s) * 36 + tid] : 0.0;
   }
   __syncthreads();
-  const bool matrix = blockIdx.y == 0 || root;
+  const bool matrix = by == 0 || root;
   if (tid < 36 && matrix) {
     const int r = tid / 6, c = tid % 6;
     double dd = d.D[(size_t)i * 36 + tid];
@@ -269,12 +289,12 @@ __global__ void __launch_bounds__(192) bcr_level_kernel(Params p, Dev d, int s) 
     }
     sA[tid] = dd;
     sY[tid] = hr2 ? un : 0.0;                        // new U_i = K_{i, i+2s}
-    if (blockIdx.y == 0) {
+    if (by == 0) {
       d.D[(size_t)i * 36 + tid] = dd;
       if (hr) d.U[(size_t)i * 36 + tid] = hr2 ? un : 0.0;
     }
   }
-  if (elim2 && blockIdx.y == 0) {
+  if (elim2 && by == 0) {
     // new left coupling K_{i-2s, i} = -L_{i-s} U_{i-s}: node i-s was eliminated at level s
     __syncthreads();
     if (tid < 36) {
@@ -307,7 +327,7 @@ __global__ void __launch_bounds__(192) bcr_level_kernel(Params p, Dev d, int s) 
   const int nrhs = ctl->m + 1;
   const size_t ld = p.nrhs_cap;
   if (!root) {
-    for (int r = blockIdx.y * 32 + lane; r < nrhs; r += 32 * kRhsSplit) {
+    for (int r = by * 32 + lane; r < nrhs; r += 32 * kRhsSplit) {
       double acc = d.B[((size_t)i * 6 + c) * ld + r];
       if (hl) {
         const double* b = d.B + (size_t)(i - s) * 6 * ld + r;
@@ -330,8 +350,8 @@ __global__ void __launch_bounds__(192) bcr_level_kernel(Params p, Dev d, int s) 
     if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
     return;
   }
-  if (tid < 36 && blockIdx.y == 0) d.P[tid] = sA[tid];
-  for (int r0 = blockIdx.y * 32; r0 < nrhs; r0 += 32 * kRhsSplit) {
+  if (tid < 36 && by == 0) d.P[tid] = sA[tid];
+  for (int r0 = by * 32; r0 < nrhs; r0 += 32 * kRhsSplit) {
     const int r = r0 + lane;
     const bool act = r < nrhs;
     double acc0 = 0.0;
@@ -361,13 +381,22 @@ __global__ void __launch_bounds__(192) bcr_level_kernel(Params p, Dev d, int s) 
   }
 }
 
+__global__ void __launch_bounds__(192) bcr_level_kernel(Params p, Dev d, int s) {
+  bcr_level_body(p, d, blockIdx.x, blockIdx.y, s);
+}
+
+// level j (stride 2^j) of every iterating instance
+__global__ void __launch_bounds__(192) bcr_level_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j) {
+  for_units(tab, plan, PH_LEV0 + j, [j](const Inst& in, int bx, int by) { bcr_level_body(in.p, in.d, bx, by, 1 << j); });
+}
+
 // Back substitution at stride s for eliminated nodes j = s + 2 s blockIdx.x (192 threads).
-__global__ void __launch_bounds__(192) bcr_bwd_kernel(Params p, Dev d, int s) {
+__device__ __forceinline__ void bcr_bwd_body(const Params& p, const Dev& d, int bx, int by, int s) {
   __shared__ double sP[36], sL[36], sR[36];
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
   const int nf = ctl->nf;
-  const int j = s + 2 * s * blockIdx.x;
+  const int j = s + 2 * s * bx;
   if (j >= nf) return;
   const int tid = threadIdx.x;
   const bool hr = j + s < nf;
@@ -380,7 +409,7 @@ __global__ void __launch_bounds__(192) bcr_bwd_kernel(Params p, Dev d, int s) {
   const int lane = tid & 31, c = tid >> 5;
   const int nrhs = ctl->m + 1;
   const size_t ld = p.nrhs_cap;
-  for (int r0 = blockIdx.y * 32; r0 < nrhs; r0 += 32 * kRhsSplit) {
+  for (int r0 = by * 32; r0 < nrhs; r0 += 32 * kRhsSplit) {
     const int r = r0 + lane;
     const bool act = r < nrhs;
     double b[6];
@@ -404,6 +433,12 @@ __global__ void __launch_bounds__(192) bcr_bwd_kernel(Params p, Dev d, int s) {
     }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(192) bcr_bwd_kernel(Params p, Dev d, int s) { bcr_bwd_body(p, d, blockIdx.x, blockIdx.y, s); }
+
+__global__ void __launch_bounds__(192) bcr_bwd_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j) {
+  for_units(tab, plan, PH_BWD0 + j, [j](const Inst& in, int bx, int by) { bcr_bwd_body(in.p, in.d, bx, by, 1 << j); });
 }
 
 }  // namespace accfem

@@ -17,12 +17,13 @@
 // triangle that can form a row in FP64 passes, so the FP64 decisions below see the same candidates
 // as a full scan.  The FP64 closest points, the overall minimum, the merge of equal points and the
 // ordering by triangle index are spread over the lanes (one survivor per lane).
-#include "common.cuh"
+#include "batch.cuh"
 #include "collide_geom.cuh"
 
 namespace accfem {
 
-__global__ void __launch_bounds__(128) collide_kernel(Params p, Dev d) {
+// Block body: free nodes 4 bx .. 4 bx + 3, one per warp.
+__device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int bx) {
   __shared__ int s_list[4][kSurvCap];                 // sorted slots kept for the FP64 test
   __shared__ Surv s_surv[4][kSurvCap];
   __shared__ int s_cand[4][kCandCap];                 // slots whose bounding sphere reaches thr
@@ -30,7 +31,7 @@ __global__ void __launch_bounds__(128) collide_kernel(Params p, Dev d) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   Ctl* ctl = d.ctl;
-  const int f = blockIdx.x * 4 + wib;
+  const int f = bx * 4 + wib;
   if (ctl->status != 0 || ctl->converged || f >= ctl->nf) return;
   const int node = ctl->k + 1 + f;
   const double pn[3] = {d.px[node], d.py[node], d.pz[node]};
@@ -228,6 +229,12 @@ __global__ void __launch_bounds__(128) collide_kernel(Params p, Dev d) {
     cg[rank] = dot3(n, sv.c) - dot3(n, pn) - p.r_o;
   }
   if (lane == 0) d.ncon[f] = nc;
+}
+
+__global__ void __launch_bounds__(128) collide_kernel(Params p, Dev d) { collide_body(p, d, blockIdx.x); }
+
+__global__ void __launch_bounds__(128) collide_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
+  for_units(tab, plan, PH_COLL, [](const Inst& in, int bx, int) { collide_body(in.p, in.d, bx); });
 }
 
 }  // namespace accfem

@@ -36,6 +36,7 @@ struct Params {
   float eps_b;                   // FP32 relative barycentric margin
   int m_cap;                     // max constraint rows
   int nrhs_cap;                  // 1 + m_cap
+  int max_newton;                // Newton iteration cap of a solve
 };
 
 // Control block, resident on the device; one per handle.
@@ -56,7 +57,7 @@ struct Ctl {
   double alpha;
   double rho;            // step bound of the limiter (starts at beta0)
   int has_prev;          // a previous Newton step exists in this solve
-  int pad1;
+  int live;              // batch: a solve of this instance is in flight
   double delta;          // insertion of the resident state
   double tension[kMaxCables];
   double tip_f[3], tip_m[3];

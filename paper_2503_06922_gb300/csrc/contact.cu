@@ -7,9 +7,10 @@
 // positive semi-definite; with the contact compliance 1e-12 max(diag W) added to its diagonal it is
 // positive definite, so the solution is unique.
 // It is found exactly by the primal active-set method below; every subproblem W_PP z_P = -q_P is
-// solved in FP64 by Gauss-Jordan over the whole CTA.  One CTA of 1024 threads; W and the
-// elimination matrix live in global memory (L2 resident).
-#include "common.cuh"
+// solved in FP64 by Gauss-Jordan over the whole CTA.  One CTA per instance; the columns of W that
+// the active set touches are formed on demand in global memory (L2 resident), the Gauss-Jordan
+// matrix of subproblems up to kLcpSmemGJ rows lives in shared memory.
+#include "batch.cuh"
 
 namespace accfem {
 
@@ -47,23 +48,6 @@ __device__ __forceinline__ int block_sum_int(int v, int* s_ired) {
   return s_ired[32];
 }
 
-__device__ __forceinline__ int block_min_int_unused(int v, int* s_ired) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-  __syncthreads();
-  if (lane == 0) s_ired[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    int x = lane < (blockDim.x >> 5) ? s_ired[lane] : 0x7fffffff;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
-    if (lane == 0) s_ired[32] = x;
-  }
-  __syncthreads();
-  return s_ired[32];
-}
-
 // (value, index) minimum over the block; ties resolved to the lowest index.
 __device__ __forceinline__ void block_argmin(double& v, int& idx, double* s_red, int* s_ired) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -93,7 +77,7 @@ __device__ __forceinline__ void block_argmin(double& v, int& idx, double* s_red,
 }
 
 constexpr int kLcpThreads = 256;
-constexpr int kLcpSmemRows = 512;      // rows kept in shared memory (m_cap <= 4096; larger m reads global)
+constexpr int kLcpSmemRows = 512;      // rows kept in shared memory (max_contacts <= 512)
 constexpr int kLcpSmemGJ = 48;         // active rows solved in shared memory (else in global memory)
 
 struct LcpShared {
@@ -181,7 +165,7 @@ __device__ bool solve_on_set(const Dev& d, LcpShared& S, int m) {
 // towards z up to the first bound and release the rows that reach zero.  Finite for SPD W; starts
 // from the rows active in the previous Newton iteration.  Rows beyond kLcpSmemRows are not
 // supported in shared memory: the kernel flags ST_CAPACITY for such m (max_contacts caps m).
-__global__ void __launch_bounds__(kLcpThreads) contact_kernel(Params p, Dev d) {
+__device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
   __shared__ LcpShared S;
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
@@ -310,6 +294,12 @@ __global__ void __launch_bounds__(kLcpThreads) contact_kernel(Params p, Dev d) {
       if (S.inP[i] && S.y[i] > 0.0) d.plist[na++] = i;
     ctl->n_active = na;
   }
+}
+
+__global__ void __launch_bounds__(kLcpThreads) contact_kernel(Params p, Dev d) { contact_body(p, d); }
+
+__global__ void __launch_bounds__(kLcpThreads) contact_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
+  for_units(tab, plan, PH_CONTACT, [](const Inst& in, int, int) { contact_body(in.p, in.d); });
 }
 
 }  // namespace accfem

@@ -7,7 +7,7 @@
 // EI/l0 [[4 2][2 4]] per bending plane).  With B = dd_l/dd (spatial spins, local components):
 //   F = E B^T K_l d_l,   K = E B^T K_l B E^T,   E = blockdiag(R_r, R_r, R_r, R_r).
 // Output record (doubles): [0, 78) upper triangle of K row-major, [78, 90) F = [F_a M_a F_b M_b].
-#include "common.cuh"
+#include "batch.cuh"
 
 namespace accfem {
 
@@ -26,17 +26,17 @@ struct ElemShared {
   double H[7][12];     // K_l B E^T
 };
 
-__global__ void __launch_bounds__(32 * kWarpsPerElemBlock)
-element_kernel(Params p, Dev d) {
+// Block body: elements k + bx * kWarpsPerElemBlock + warp.
+__device__ __forceinline__ void element_body(const Params& p, const Dev& d, int bx) {
   __shared__ ElemShared sm[kWarpsPerElemBlock];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   ElemShared& S = sm[wib];
   Ctl* ctl = d.ctl;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {         // reset the per-iteration reductions
+  if (bx == 0 && threadIdx.x == 0) {                 // reset the per-iteration reductions
     ctl->umax_bits = 0ull; ctl->step_bits = 0ull; ctl->res_bits = 0ull;
   }
-  const int e = ctl->k + blockIdx.x * kWarpsPerElemBlock + wib;
+  const int e = ctl->k + bx * kWarpsPerElemBlock + wib;
   if (e >= p.M || ctl->status != 0 || ctl->converged) return;
   const int a = e, b = e + 1;
   // ---- nodal triads: lane 0..17 -> entry (node lane/9, index lane%9)
@@ -199,6 +199,14 @@ element_kernel(Params p, Dev d) {
     for (int k = 0; k < 7; ++k) s = fma(sB[k][lane], fl[k], s);
     out[78 + lane] = s;
   }
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerElemBlock) element_kernel(Params p, Dev d) {
+  element_body(p, d, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerElemBlock) element_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
+  for_units(tab, plan, PH_ELEM, [](const Inst& in, int bx, int) { element_body(in.p, in.d, bx); });
 }
 
 void upload_element_tables() {

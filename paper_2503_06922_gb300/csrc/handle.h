@@ -1,0 +1,41 @@
+// Host-side state of one handle (internal; shared by the single-instance driver and the batch).
+#pragma once
+#include <cmath>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/accfem.h"
+#include "common.cuh"
+
+using accfem::Params;
+using accfem::Dev;
+using accfem::Ctl;
+
+struct accfem_handle {
+  Params p;
+  Dev d;
+  cudaStream_t stream = nullptr;
+  std::vector<void*> allocs;
+  Ctl* h_ctl = nullptr;            // pinned host mirror of the control block
+  double* h_stage = nullptr;       // pinned staging for results
+  size_t stage_bytes = 0;
+  bool has_state = false;
+  double delta = 0.0;
+  int64_t launches = 0;
+  int nf_cap = 0;
+  int max_newton = 200;
+  std::string err;
+  struct LoopGraph { cudaGraph_t graph = nullptr; cudaGraphExec_t exec = nullptr; int body_kernels = 0; };
+  std::map<int, LoopGraph> graphs;   // device-side Newton loop, one per number of free nodes
+  bool stream_mode = false;          // ACCFEM_LAUNCH=stream: host-driven loop (kernels visible to profilers)
+  bool trace = false;                // ACCFEM_TRACE=1 (with stream mode): one line per Newton iteration on stderr
+  cudaStream_t user_stream = nullptr; // caller's stream (accfem_set_stream), else the handle's own
+  int64_t h2d = 0, d2h = 0;          // bytes copied by solve / state calls
+  cudaStream_t work() const { return user_stream ? user_stream : stream; }
+};
+
+// Last prescribed node at insertion delta: nodes 0..k sit in the feeder, k = floor((L - delta) M / L).
+inline int accfem_last_prescribed(double L, int M, double delta) {
+  return (int)std::floor((L - delta) * M / L + 1e-6);
+}

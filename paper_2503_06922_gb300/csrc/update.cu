@@ -1,19 +1,19 @@
 // Newton update with the step limiter (Eq. 25-27), convergence test, and the start pose of a
 // solve (prescribed feed, Eq. 14-15; warm start from the resident pose).
-#include "common.cuh"
+#include "batch.cuh"
 
 namespace accfem {
 
 // dx = dx_free - X y over the active rows; per-node maxima of |du|, max(|du|, r_o |dtheta|) and
 // of the residual g + A^T y.  Block: 32 nodes x 6 components.
-__global__ void __launch_bounds__(192) step_kernel(Params p, Dev d) {
+__device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx) {
   __shared__ double s_dx[32][6];
   __shared__ double s_r[32][6];
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
   const int nf = ctl->nf;
   const int fl = threadIdx.x, c = threadIdx.y;
-  const int f = blockIdx.x * 32 + fl;
+  const int f = bx * 32 + fl;
   const bool act = f < nf;
   const size_t ld = p.nrhs_cap;
   if (act) {
@@ -44,8 +44,8 @@ __global__ void __launch_bounds__(192) step_kernel(Params p, Dev d) {
   __syncthreads();
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     double rev = 0.0;
-    for (int k = 0; k < 32 && blockIdx.x * 32 + k < nf; ++k) rev += s_r[k][0] + s_r[k][1] + s_r[k][2];
-    d.rev_part[blockIdx.x] = rev;
+    for (int k = 0; k < 32 && bx * 32 + k < nf; ++k) rev += s_r[k][0] + s_r[k][1] + s_r[k][2];
+    d.rev_part[bx] = rev;
   }
   if (act && c == 0) {
     double du = sqrt(s_dx[fl][0] * s_dx[fl][0] + s_dx[fl][1] * s_dx[fl][1] + s_dx[fl][2] * s_dx[fl][2]);
@@ -55,6 +55,12 @@ __global__ void __launch_bounds__(192) step_kernel(Params p, Dev d) {
     atomicMax(&ctl->step_bits, dbits(st));
     atomicMax(&ctl->res_bits, dbits(rr_node));
   }
+}
+
+__global__ void __launch_bounds__(192) step_kernel(Params p, Dev d) { step_body(p, d, blockIdx.x); }
+
+__global__ void __launch_bounds__(192) step_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
+  for_units(tab, plan, PH_STEP, [](const Inst& in, int bx, int) { step_body(in.p, in.d, bx); });
 }
 
 // Step limiter (Eq. 25-27 with an adaptive bound): alpha = min(1, rho / max |du|).  A step that
@@ -79,7 +85,7 @@ __device__ __forceinline__ void limiter(const Params& p, const Dev& d, const Ctl
 }
 
 // x <- x + alpha du, T <- exp([alpha dtheta]x) T.
-__global__ void __launch_bounds__(128) apply_kernel(Params p, Dev d) {
+__device__ __forceinline__ void apply_body(const Params& p, const Dev& d, int bx) {
   __shared__ double s_alpha;
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
@@ -90,7 +96,7 @@ __global__ void __launch_bounds__(128) apply_kernel(Params p, Dev d) {
   }
   __syncthreads();
   const double alpha = s_alpha;
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = bx * 128 + threadIdx.x;
   if (f < nf) {
     const int node = ctl->k + 1 + f;
     const double* dx = d.dx + (size_t)f * 6;
@@ -107,11 +113,17 @@ __global__ void __launch_bounds__(128) apply_kernel(Params p, Dev d) {
   }
 }
 
+__global__ void __launch_bounds__(128) apply_kernel(Params p, Dev d) { apply_body(p, d, blockIdx.x); }
+
+__global__ void __launch_bounds__(128) apply_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
+  for_units(tab, plan, PH_APPLY, [](const Inst& in, int bx, int) { apply_body(in.p, in.d, bx); });
+}
+
 // End of an iteration (one thread): limiter bookkeeping, iteration count, convergence (unscaled
 // step below tol with an unchanged constraint set), and -- inside the device-side Newton graph --
 // the loop condition: keep iterating while no error, not converged and fewer than max_iter
 // iterations; a separate count of loop passes bounds the loop whatever the other kernels did.
-__global__ void ctl_kernel(Params p, Dev d, cudaGraphConditionalHandle h, int max_iter, int set_cond) {
+__device__ __forceinline__ void ctl_update(const Params& p, const Dev& d) {
   Ctl* c = d.ctl;
   if (c->status == 0 && !c->converged) {
     double rho, alpha;
@@ -124,6 +136,11 @@ __global__ void ctl_kernel(Params p, Dev d, cudaGraphConditionalHandle h, int ma
     if (step <= p.tol && c->same_set) c->converged = 1;
   }
   c->loops += 1;
+}
+
+__global__ void ctl_kernel(Params p, Dev d, cudaGraphConditionalHandle h, int max_iter, int set_cond) {
+  Ctl* c = d.ctl;
+  ctl_update(p, d);
   if (set_cond) {
     unsigned int cont = (c->status == 0 && !c->converged && c->iter < max_iter && c->loops < max_iter) ? 1u : 0u;
     cudaGraphSetConditional(h, cont);
@@ -134,8 +151,7 @@ __global__ void ctl_kernel(Params p, Dev d, cudaGraphConditionalHandle h, int ma
 // previous pose (material point s takes the old pose of material point s + (delta - delta_old):
 // linear in x, geodesic in the rotation between nodes, straight along the tip axis beyond the
 // old tip); mode 2: poses already uploaded.  Nodes i <= k are then clamped on the axis.
-__global__ void __launch_bounds__(128) start_kernel(Params p, Dev d, int mode, double delta, double delta_old, int k) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void start_body(const Params& p, const Dev& d, int mode, double delta, double delta_old, int k, int i) {
   if (i >= p.N) return;
   const double* dir = p.E0;    // column 0 of E0: (E0[0], E0[3], E0[6])
   double x[3], q[4];
@@ -186,6 +202,103 @@ __global__ void __launch_bounds__(128) start_kernel(Params p, Dev d, int mode, d
   if (q[0] < 0.0) in = -in;
   d.px[i] = x[0]; d.py[i] = x[1]; d.pz[i] = x[2];
   d.qw[i] = q[0] * in; d.qx[i] = q[1] * in; d.qy[i] = q[2] * in; d.qz[i] = q[3] * in;
+}
+
+__global__ void __launch_bounds__(128) start_kernel(Params p, Dev d, int mode, double delta, double delta_old, int k) {
+  start_body(p, d, mode, delta, delta_old, k, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Start of the batched solves: block (x, j) sets up begun instance bg[j].member: block 0 copies its
+// staged control block; for a warm start the resident pose is saved as the path to follow.
+__global__ void __launch_bounds__(128) batch_begin_kernel(const Inst* __restrict__ tab, const Ctl* __restrict__ staged,
+                                                          const BatchBegin* __restrict__ bg) {
+  const BatchBegin b = bg[blockIdx.y];
+  const Dev& d = tab[b.member].d;
+  const int n_nodes = tab[b.member].p.N;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *d.ctl = staged[blockIdx.y];
+  const int i = blockIdx.x * 128 + threadIdx.x;
+  if (b.mode == 1 && i < n_nodes) {
+    d.ox[i] = d.px[i]; d.oy[i] = d.py[i]; d.oz[i] = d.pz[i];
+    d.ow[i] = d.qw[i]; d.oqx[i] = d.qx[i]; d.oqy[i] = d.qy[i]; d.oqz[i] = d.qz[i];
+  }
+}
+
+__global__ void __launch_bounds__(128) start_batch(const Inst* __restrict__ tab, const BatchBegin* __restrict__ bg) {
+  const BatchBegin b = bg[blockIdx.y];
+  start_body(tab[b.member].p, tab[b.member].d, b.mode, b.delta, b.delta_old, b.k, blockIdx.x * 128 + threadIdx.x);
+}
+
+// End of a batched iteration (one block of 1024 threads, thread i = instance i): the control update
+// of every instance in flight (as ctl_kernel when do_ctl), then the plan of the next iteration --
+// the instances that keep iterating (no error, not converged, under the iteration cap) and per
+// phase the exclusive prefix of their unit counts.  An instance that stops leaves the flight.
+// Without do_ctl (start of an advance) it records the iteration budget max_passes; in the batch
+// graph it sets the loop condition: some instance iterates and fewer than that many iterations
+// were run by this advance.
+__global__ void __launch_bounds__(1024) batch_plan_kernel(const Inst* __restrict__ tab, Plan* plan, int n_inst, int do_ctl,
+                                                          int max_passes, cudaGraphConditionalHandle h, int set_cond) {
+  __shared__ int s_warp[32];
+  __shared__ int s_nf[kMaxBatch];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  int go = 0, nf = 0;
+  if (tid < n_inst) {
+    const Params& p = tab[tid].p;
+    const Dev& d = tab[tid].d;
+    Ctl* c = d.ctl;
+    if (c->live) {
+      if (do_ctl) ctl_update(p, d);
+      go = (c->status == 0 && !c->converged && c->iter < p.max_newton && c->loops < p.max_newton) ? 1 : 0;
+      if (!go) c->live = 0;
+      nf = c->nf;
+    }
+  }
+  int v = go;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) s_warp[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int x = s_warp[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    s_warp[lane] = x;
+  }
+  __syncthreads();
+  const int pos = v - go + (w > 0 ? s_warp[w - 1] : 0);
+  const int n_act = s_warp[31];
+  if (go) {
+    plan->act[pos] = tid;
+    s_nf[pos] = nf;
+  }
+  __syncthreads();
+  for (int ph = w; ph < kPhases; ph += 32) {
+    int run = 0;
+    if (lane == 0) plan->pre[ph][0] = 0;
+    for (int base = 0; base < n_act; base += 32) {
+      const int j = base + lane;
+      int u = j < n_act ? phase_gx(ph, s_nf[j]) * phase_gy(ph) : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, u, o);
+        if (lane >= o) u += t;
+      }
+      if (j < n_act) plan->pre[ph][j + 1] = run + u;
+      run += __shfl_sync(0xffffffffu, u, 31);
+    }
+  }
+  if (tid == 0) {
+    plan->n_act = n_act;
+    const int passes = do_ctl ? plan->passes + 1 : 0;
+    plan->passes = passes;
+    if (!do_ctl) plan->max_passes = max_passes;
+    if (set_cond) cudaGraphSetConditional(h, (n_act > 0 && passes < plan->max_passes) ? 1u : 0u);
+  }
 }
 
 }  // namespace accfem

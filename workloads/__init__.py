@@ -196,6 +196,28 @@ def catmull_rom_workload(lumen_seed: int = 1, tension_seed: int = 2, n_steps: in
     return Workload("catmull_rom_600mm_M%d" % n_elements, robot, lumen, ins, t)
 
 
+def batch_workloads(n_instances: int = 256, seed: int = 3, step=0.010, length=0.600, m_min=50, m_max=2000,
+                    t_max=5.0, first=0, count=None):
+    """Uneven instances for batched solves: element count log-uniform in [m_min, m_max], a lumen
+    from the Catmull-Rom generator with the instance's own seed (10000 + i), a target insertion
+    U[0.3, 1] x length reached by warm-started steps of about ``step``, and a fresh tension triple
+    U[0, t_max] N per step.  Instances first .. first + count - 1 are generated (all by default);
+    instance i is the same whatever subset is asked for."""
+    rng = np.random.default_rng(seed)
+    M = np.round(np.exp(rng.uniform(np.log(m_min), np.log(m_max), n_instances))).astype(int)
+    target = rng.uniform(0.3, 1.0, n_instances) * length
+    count = n_instances - first if count is None else count
+    out = []
+    for i in range(first, first + count):
+        n_steps = int(np.ceil(target[i] / step - 1e-9))
+        robot = robot_desc(length, int(M[i]))
+        lumen = _lumen_from_centerline(catmull_rom_centerline(10000 + i), 0.006, 48)
+        ins = target[i] * np.arange(1, n_steps + 1) / n_steps
+        t = random_tensions(seed * 100003 + i, n_steps, t_max)
+        out.append(Workload("batch%d_M%d" % (i, M[i]), robot, lumen, ins, t))
+    return out
+
+
 def plane_lumen(point, normal, size=0.2, n=8, entrance_point=(0.0, 0.0, 0.0), entrance_dir=(1.0, 0.0, 0.0),
                 entrance_up=(0.0, 1.0, 0.0)) -> LumenDesc:
     """A flat square wall (``n`` x ``n`` quads, two triangles each) through ``point`` with unit
