@@ -289,7 +289,9 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
     }
     sA[tid] = dd;
     sY[tid] = hr2 ? un : 0.0;                        // new U_i = K_{i, i+2s}
-    if (by == 0) {
+    // the root's D_0 and U_0 are read by every block of this level and needed by no later step:
+    // only non-root levels store the updated blocks (for the next level's kernel)
+    if (by == 0 && !root) {
       d.D[(size_t)i * 36 + tid] = dd;
       if (hr) d.U[(size_t)i * 36 + tid] = hr2 ? un : 0.0;
     }
