@@ -235,6 +235,41 @@ accfem_status accfem_batch_results(accfem_batch* b, const int32_t* members, int3
 accfem_status accfem_batch_solve(accfem_batch* b, const double* cable_tensions, const double* insertions,
                                  const int32_t* mask, accfem_status* statuses, accfem_result* results);
 
+/* One timed request for accfem_batch_serve: a quasi-static solve of scene `member` with the given
+ * cable tensions (the member's n_cables values; the rest are ignored) and insertion, arriving
+ * `arrival` seconds after the start of the run. */
+typedef struct {
+  double arrival;
+  int32_t member;
+  int32_t pad;
+  double cable_tensions[ACCFEM_MAX_CABLES];
+  double insertion;
+} accfem_request;
+
+/* Answer to one request: solve status and Newton iterations, the times (seconds after the start of
+ * the run) at which its solve began and its answer was ready (latency = t_end - arrival), the tip
+ * node pose (position 3, quaternion 4) and the constraint-row count. */
+typedef struct {
+  accfem_status status;
+  int32_t newton_iters;
+  double t_begin, t_end;
+  double tip[7];
+  int32_t n_contacts;
+  int32_t pad;
+} accfem_response;
+
+/* Serves requests[0..n_requests) (non-decreasing arrival times) in real time by continuous batching:
+ * a request waits until it has arrived and its scene is idle (requests of one scene are solved in
+ * arrival order, each warm started from the scene's resident state left by the previous one), then
+ * joins the solves in flight; everything in flight advances chunk_iters Newton iterations per
+ * launch, and a solve's answer is ready after the launch in which it finished.  Admission by device
+ * footprint: the batch's own memory, then members in index order while the total stays within
+ * hbm_cap_bytes (<= 0: no cap); requests of members left out are answered ACCFEM_E_NOMEM without a
+ * solve.  Returns when every request is answered (responses[k] for requests[k]); all members must
+ * be idle at the call. */
+accfem_status accfem_batch_serve(accfem_batch* b, const accfem_request* requests, int32_t n_requests,
+                                 int32_t chunk_iters, int64_t hbm_cap_bytes, accfem_response* responses);
+
 /* Work stream of the batch's calls (a cudaStream_t; NULL = the batch's own stream). */
 accfem_status accfem_batch_set_stream(accfem_batch* b, void* stream);
 
@@ -249,6 +284,9 @@ const char* accfem_batch_last_error(const accfem_batch* b);
 
 /* Frees the batch (not its members); NULL is a no-op. */
 void accfem_batch_destroy(accfem_batch* b);
+
+/* Device memory held by the handle, in bytes. */
+accfem_status accfem_device_bytes(const accfem_handle* h, int64_t* bytes);
 
 /* Copies the resident nodal poses (3*(M+1) and 4*(M+1) doubles) to host buffers. */
 accfem_status accfem_get_state(accfem_handle* h, double* node_pos, double* node_quat);

@@ -15,11 +15,13 @@ One call of ``Model.solve`` is one quasi-static step at a given cable tension an
     matrix W = A K^-1 A^T carries the compliance 1e-12 max(diag W) on its diagonal (rows of
     one node are dependent where four or more wall faces meet).
   * step limiter (Eq. 25-27): alpha = min(1, rho / max_i |du_i|) scales the whole step and
-    the multipliers; translations add, rotations update as T <- exp([alpha dtheta]x) T.  A step
-    that points against the previous one (sum_i du_i . du_i^prev < 0) is an overshoot: it is
-    halved, and when it was clipped the bound rho is halved too; otherwise rho doubles back
-    towards beta0.  (A fixed beta0 lets a node on a faceted wall overshoot the crease between two
-    facets forever, and the material tangent overshoots the twist of a long bent span by ~2x.)
+    the multipliers; translations add, rotations update as T <- exp([alpha dtheta]x) T.  The
+    bound rho starts at beta0.  A step that points against the previous one
+    (sum_i du_i . du_i^prev < 0) is an overshoot: rho drops to half of the smaller of rho and
+    that step (so the step is at most halved, and a repeating cycle shrinks geometrically);
+    otherwise rho grows by 1.5 back towards beta0.  (A fixed beta0 lets a node on a faceted wall
+    overshoot the crease between two facets forever, and the material tangent overshoots the
+    twist of a long bent span by ~2x.)
   * convergence: unscaled step max_i max(|du_i|, r_o |dtheta_i|) <= tol and the same contact
     set as the previous iteration.
   * warm start (follow the path): with a resident state at insertion delta_old, material
@@ -189,7 +191,7 @@ class Model:
         it = 0
         piv_total = 0
         residual = 0.0
-        rho = opt.step_limit           # step bound of the limiter, halved when consecutive steps reverse
+        rho = opt.step_limit           # step bound of the limiter (shrinks when consecutive steps reverse)
         du_prev = None
         status = E_NOT_CONVERGED
         base_reaction = np.zeros(6)
@@ -253,14 +255,12 @@ class Model:
             step = float(max(umax, r_o * np.sqrt((dth * dth).sum(axis=1)).max()))
             reverse = du_prev is not None and float(np.sum(du * du_prev)) < 0.0
             if du_prev is not None:
-                if not reverse:
-                    rho = min(2.0 * rho, opt.step_limit)
-                elif umax > rho:
-                    rho = max(0.5 * rho, opt.step_limit * 2.0 ** -20)
+                if reverse:
+                    rho = max(0.5 * min(rho, umax), opt.step_limit * 2.0 ** -40)
+                else:
+                    rho = min(1.5 * rho, opt.step_limit)
             du_prev = du.copy()
             alpha = 1.0 if umax <= rho else rho / umax
-            if reverse:
-                alpha *= 0.5
             for j, i in enumerate(free):
                 x[i] = x[i] + alpha * du[j]
                 R[i] = expm(alpha * dth[j]) @ R[i]

@@ -45,6 +45,17 @@ class accfem_result(ctypes.Structure):
                 ("contact_iters", ctypes.c_int32), ("residual", ctypes.c_double)]
 
 
+class accfem_request(ctypes.Structure):
+    _fields_ = [("arrival", ctypes.c_double), ("member", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("cable_tensions", ctypes.c_double * 8), ("insertion", ctypes.c_double)]
+
+
+class accfem_response(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("newton_iters", ctypes.c_int32), ("t_begin", ctypes.c_double),
+                ("t_end", ctypes.c_double), ("tip", ctypes.c_double * 7), ("n_contacts", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
 class accfem_state(ctypes.Structure):
     _fields_ = [("node_pos", _dp), ("node_quat", _dp)]
 
@@ -55,7 +66,8 @@ EXPORTS = ["accfem_default_options", "accfem_create", "accfem_solve", "accfem_so
            "accfem_status_string", "accfem_last_error", "accfem_detect_contacts_noalloc",
            "accfem_batch_create", "accfem_batch_begin", "accfem_batch_advance", "accfem_batch_poll",
            "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream", "accfem_batch_transfer_bytes",
-           "accfem_batch_kernel_launches", "accfem_batch_last_error", "accfem_batch_destroy"]
+           "accfem_batch_kernel_launches", "accfem_batch_last_error", "accfem_batch_destroy", "accfem_batch_serve",
+           "accfem_device_bytes"]
 
 MAX_CABLES = 8
 
@@ -110,6 +122,9 @@ def load(path=LIB_PATH):
     lib.accfem_batch_kernel_launches.restype = ctypes.c_int64
     lib.accfem_batch_last_error.argtypes = [B]
     lib.accfem_batch_last_error.restype = ctypes.c_char_p
+    lib.accfem_batch_serve.argtypes = [B, ctypes.POINTER(accfem_request), ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int64, ctypes.POINTER(accfem_response)]
+    lib.accfem_device_bytes.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
     lib.accfem_batch_destroy.argtypes = [B]
     lib.accfem_batch_destroy.restype = None
     for name in ("accfem_default_options", "accfem_create", "accfem_solve", "accfem_solve_tip_load",
@@ -117,7 +132,7 @@ def load(path=LIB_PATH):
                  "accfem_transfer_bytes", "accfem_time_kernel", "accfem_detect_contacts_noalloc",
                  "accfem_batch_create", "accfem_batch_begin", "accfem_batch_advance", "accfem_batch_poll",
                  "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream",
-                 "accfem_batch_transfer_bytes"):
+                 "accfem_batch_transfer_bytes", "accfem_batch_serve", "accfem_device_bytes"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -266,6 +281,11 @@ class AccFem:
     def accfem_kernel_launches(self):
         return int(self._lib.accfem_kernel_launches(self.h))
 
+    def accfem_device_bytes(self):
+        v = ctypes.c_int64(0)
+        self._lib.accfem_device_bytes(self.h, ctypes.byref(v))
+        return int(v.value)
+
     def accfem_last_error(self):
         return self._lib.accfem_last_error(self.h).decode()
 
@@ -350,6 +370,31 @@ class AccFemBatch:
             sel = range(self.n) if mask is None else [i for i in range(self.n) if mask[i]]
             out = {i: self.members[i]._pack(statuses[i], rs[i]) for i in sel}
         return int(st), statuses, out
+
+    def accfem_batch_serve(self, arrivals, members, tensions, insertions, chunk_iters=4, hbm_cap_bytes=0):
+        """Serves the requests (arrays of equal length, arrival-sorted) in real time; returns a dict of
+        numpy arrays: status, newton_iters, t_begin, t_end, latency, tip (k, 7), n_contacts, and the
+        call's status."""
+        k = len(arrivals)
+        req = (accfem_request * max(k, 1))()
+        ta = np.asarray(tensions, dtype=np.float64).reshape(k, -1) if k else np.zeros((0, 1))
+        for j in range(k):
+            req[j].arrival = float(arrivals[j])
+            req[j].member = int(members[j])
+            for c in range(ta.shape[1]):
+                req[j].cable_tensions[c] = float(ta[j, c])
+            req[j].insertion = float(insertions[j])
+        resp = (accfem_response * max(k, 1))()
+        st = self._lib.accfem_batch_serve(self.b, req, k, int(chunk_iters), int(hbm_cap_bytes), resp)
+        out = {"call_status": int(st),
+               "status": np.array([resp[j].status for j in range(k)], dtype=np.int32),
+               "newton_iters": np.array([resp[j].newton_iters for j in range(k)], dtype=np.int32),
+               "t_begin": np.array([resp[j].t_begin for j in range(k)]),
+               "t_end": np.array([resp[j].t_end for j in range(k)]),
+               "tip": np.array([list(resp[j].tip) for j in range(k)]).reshape(k, 7),
+               "n_contacts": np.array([resp[j].n_contacts for j in range(k)], dtype=np.int32)}
+        out["latency"] = out["t_end"] - np.asarray(arrivals, dtype=np.float64)
+        return out
 
     def accfem_batch_set_stream(self, stream_ptr):
         return int(self._lib.accfem_batch_set_stream(self.b, ctypes.c_void_p(int(stream_ptr)) if stream_ptr else None))

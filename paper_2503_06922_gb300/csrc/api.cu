@@ -54,6 +54,7 @@ bool dalloc(accfem_handle* h, T** ptr, size_t count) {
   }
   cudaMemset(p, 0, count * sizeof(T));
   h->allocs.push_back(p);
+  h->dev_bytes += (int64_t)(count * sizeof(T));
   *ptr = (T*)p;
   return true;
 }
@@ -493,7 +494,11 @@ accfem_status run_solve(accfem_handle* h, int load_mode, const double* tensions_
                      __builtin_bit_cast(double, (unsigned long long)c.step_bits),
                      __builtin_bit_cast(double, (unsigned long long)c.res_bits), c.m, c.same_set, c.n_active,
                      c.lcp_pivots);
-      if (c.status != 0) { status = (accfem_status)c.status; break; }
+      if (c.status != 0) {
+        status = (accfem_status)c.status;
+        h->err = accfem_solve_message(c, status);
+        break;
+      }
       if (c.converged) { status = ACCFEM_OK; break; }
     }
   } else if (nf > 0) {
@@ -508,8 +513,7 @@ accfem_status run_solve(accfem_handle* h, int load_mode, const double* tensions_
     if (c.status != 0) status = (accfem_status)c.status;
     else if (c.converged) status = ACCFEM_OK;
     else status = ACCFEM_E_NOT_CONVERGED;
-    if (status == ACCFEM_E_NOT_CONVERGED) h->err = "Newton iterations did not converge";
-    else if (status != ACCFEM_OK) h->err = accfem_status_string(status);
+    if (status != ACCFEM_OK) h->err = accfem_solve_message(c, status);
   } else {
     if (!cuda_ok(h, cudaMemcpyAsync(h->h_ctl, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st), "read control") ||
         !cuda_ok(h, cudaStreamSynchronize(st), "start pose"))
@@ -678,6 +682,12 @@ accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t
        cuda_ok(h, cudaStreamSynchronize(st), "restore control");
   if (!ok) return ACCFEM_E_CUDA;
   *us = 1000.0 * ms / reps;
+  return ACCFEM_OK;
+}
+
+accfem_status accfem_device_bytes(const accfem_handle* h, int64_t* bytes) {
+  if (!h || !bytes) return ACCFEM_E_INVALID_ARG;
+  *bytes = h->dev_bytes;
   return ACCFEM_OK;
 }
 

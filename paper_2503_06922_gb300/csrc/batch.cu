@@ -12,8 +12,7 @@
 #include <vector>
 
 #include "../../include/accfem.h"
-#include "handle.h"
-#include "batch.cuh"
+#include "batch_host.h"
 
 namespace accfem {
 __global__ void element_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
@@ -65,58 +64,7 @@ __global__ void __launch_bounds__(256) batch_pack_kernel(const Inst* __restrict_
 
 using namespace accfem;
 
-struct accfem_batch {
-  std::vector<accfem_handle*> members;
-  int n = 0;
-  int max_nodes = 0;
-  int levels = 0;
-  cudaStream_t stream = nullptr, user_stream = nullptr;
-  Inst* d_tab = nullptr;
-  Plan* d_plan = nullptr;
-  Ctl* d_ctl = nullptr;             // control block of member i (the batch's own)
-  Ctl* d_stage = nullptr;           // staged control blocks of the solves begun since the last advance
-  BatchBegin* d_begin = nullptr;
-  int* d_members = nullptr;         // result gather: member list, offsets, packed values
-  long long* d_off = nullptr;
-  double* d_pack = nullptr;
-  size_t pack_cap = 0;              // doubles
-  Ctl* h_ctl = nullptr;             // pinned host mirrors
-  Ctl* h_stage = nullptr;
-  BatchBegin* h_begin = nullptr;
-  int* h_members = nullptr;
-  long long* h_off = nullptr;
-  double* h_pack = nullptr;
-  int* h_passes = nullptr;
-  int n_begin = 0;
-  std::vector<int> state;           // 0 idle, 1 staged, 2 in flight
-  std::vector<int> solved;          // member finished at least one solve in this batch
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  int body_kernels = 0;
-  int grid[kPhases] = {};
-  int64_t launches = 0, h2d = 0, d2h = 0;
-  std::string err;
-  cudaStream_t work() const { return user_stream ? user_stream : stream; }
-};
-
 namespace {
-
-accfem_status bfail(accfem_batch* b, accfem_status s, const std::string& msg) {
-  if (b) b->err = msg;
-  return s;
-}
-
-bool bok(accfem_batch* b, cudaError_t e, const char* what) {
-  if (e == cudaSuccess) return true;
-  if (b) b->err = std::string(what) + ": " + cudaGetErrorString(e);
-  return false;
-}
-
-accfem_status outcome(const Ctl& c) {
-  if (c.status != 0) return (accfem_status)c.status;
-  if (c.nf == 0 || c.converged) return ACCFEM_OK;
-  return ACCFEM_E_NOT_CONVERGED;
-}
 
 // Persistent grid of a batched phase kernel: resident blocks on every SM, at most the largest
 // number of units the members can produce.
@@ -194,6 +142,7 @@ bool balloc(accfem_batch* b, T** dptr, size_t count) {
     return false;
   }
   cudaMemset(*dptr, 0, count * sizeof(T));
+  b->dev_bytes += (int64_t)(count * sizeof(T));
   return true;
 }
 
@@ -218,10 +167,10 @@ void accfem_batch_destroy(accfem_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (void* p : {(void*)b->d_tab, (void*)b->d_plan, (void*)b->d_ctl, (void*)b->d_stage, (void*)b->d_begin,
-                  (void*)b->d_members, (void*)b->d_off, (void*)b->d_pack})
+                  (void*)b->d_members, (void*)b->d_off, (void*)b->d_pack, (void*)b->d_tips})
     if (p) cudaFree(p);
   for (void* p : {(void*)b->h_ctl, (void*)b->h_stage, (void*)b->h_begin, (void*)b->h_members, (void*)b->h_off,
-                  (void*)b->h_pack, (void*)b->h_passes})
+                  (void*)b->h_pack, (void*)b->h_passes, (void*)b->h_tips})
     if (p) cudaFreeHost(p);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -253,7 +202,8 @@ accfem_status accfem_batch_create(accfem_handle* const* members, int32_t n_membe
   bool ok = bok(b, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "cudaStreamCreate") &&
             balloc(b, &b->d_tab, b->n) && balloc(b, &b->d_plan, 1) && balloc(b, &b->d_ctl, b->n) &&
             balloc(b, &b->d_stage, b->n) && balloc(b, &b->d_begin, b->n) && balloc(b, &b->d_members, b->n) &&
-            balloc(b, &b->d_off, b->n) && balloc(b, &b->d_pack, pack) && bhost(b, &b->h_ctl, b->n) &&
+            balloc(b, &b->d_off, b->n) && balloc(b, &b->d_pack, pack) && balloc(b, &b->d_tips, (size_t)8 * b->n) &&
+            bhost(b, &b->h_tips, (size_t)8 * b->n) && bhost(b, &b->h_ctl, b->n) &&
             bhost(b, &b->h_stage, b->n) && bhost(b, &b->h_begin, b->n) && bhost(b, &b->h_members, b->n) &&
             bhost(b, &b->h_off, b->n) && bhost(b, &b->h_pack, pack) && bhost(b, &b->h_passes, 4);
   if (!ok) {
@@ -379,6 +329,7 @@ accfem_status accfem_batch_poll(const accfem_batch* b, int32_t member, int32_t* 
 
 accfem_status accfem_batch_results(accfem_batch* b, const int32_t* members, int32_t count, accfem_result* out,
                                    accfem_status* statuses) {
+  if (b) b->err.clear();
   if (!b || count < 0 || count > b->n || (count > 0 && (!members || !out))) return bfail(b, ACCFEM_E_INVALID_ARG, "bad arguments");
   if (count == 0) return ACCFEM_OK;
   long long off = 0;
@@ -441,7 +392,10 @@ accfem_status accfem_batch_results(accfem_batch* b, const int32_t* members, int3
     }
     if (m > r.contact_capacity && st_j == ACCFEM_OK) st_j = ACCFEM_E_CONTACT_CAPACITY;
     if (statuses) statuses[j] = st_j;
-    if (first == ACCFEM_OK && st_j != ACCFEM_OK) first = st_j;
+    if (first == ACCFEM_OK && st_j != ACCFEM_OK) {
+      first = st_j;
+      b->err = "member " + std::to_string(i) + ": " + accfem_solve_message(c, st_j);
+    }
   }
   return first;
 }

@@ -62,7 +62,7 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   int excl = v - loc + (w > 0 ? s_warp[w - 1] : 0);
   const int m = s_warp[31];
   if (m > p.m_cap) {
-    if (tid == 0) atomicCAS(&ctl->status, 0, ST_CAPACITY);
+    if (tid == 0) flag_capacity(ctl, CAP_ROWS);
     return;
   }
   int row = excl;

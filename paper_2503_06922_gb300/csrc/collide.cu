@@ -96,7 +96,7 @@ __device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int 
   }
   __syncwarp();
   if (nca > kCandCap) {
-    if (lane == 0) atomicCAS(&ctl->status, 0, ST_CAPACITY);
+    if (lane == 0) flag_capacity(ctl, CAP_CANDIDATES);
     return;
   }
   // ---- FP32 minimum and the exact-test filter
@@ -125,7 +125,7 @@ __device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int 
   }
   __syncwarp();
   if (ns > kSurvCap) {
-    if (lane == 0) atomicCAS(&ctl->status, 0, ST_CAPACITY);
+    if (lane == 0) flag_capacity(ctl, CAP_SURVIVORS);
     return;
   }
   // ---- exact FP64 closest points, one survivor per lane
@@ -194,7 +194,7 @@ __device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int 
   unsigned km1 = __ballot_sync(0xffffffffu, kept[1]);
   const int nc = __popc(km0) + __popc(km1);
   if (nc > kCpn) {
-    if (lane == 0) atomicCAS(&ctl->status, 0, ST_CAPACITY);
+    if (lane == 0) flag_capacity(ctl, CAP_NODE_ROWS);
     return;
   }
   int* ctri = d.con_tri + (size_t)f * kCpn;

@@ -17,6 +17,9 @@ constexpr int kRhsSplit = 4;       // blocks per node that share the RHS columns
 enum : int { ST_OK = 0, ST_INVALID = 1, ST_NOMEM = 2, ST_CUDA = 3, ST_NOT_CONVERGED = 4,
              ST_CAPACITY = 5, ST_NOT_SPD = 6, ST_TIMEOUT = 7 };
 
+// Which limit raised ST_CAPACITY (Ctl::cap_code).
+enum : int { CAP_ROWS = 1, CAP_CANDIDATES = 2, CAP_SURVIVORS = 3, CAP_NODE_ROWS = 4, CAP_LCP_ROWS = 5 };
+
 // Constants of one handle, passed by value to every kernel.
 struct Params {
   int M, N;                      // elements, nodes
@@ -58,10 +61,17 @@ struct Ctl {
   double rho;            // step bound of the limiter (starts at beta0)
   int has_prev;          // a previous Newton step exists in this solve
   int live;              // batch: a solve of this instance is in flight
+  int cap_code;          // CAP_* cause of an ST_CAPACITY status
+  int pad2;
   double delta;          // insertion of the resident state
   double tension[kMaxCables];
   double tip_f[3], tip_m[3];
 };
+
+// Flags ST_CAPACITY (the first error of an iteration wins) and records its cause.
+__device__ __forceinline__ void flag_capacity(Ctl* c, int code) {
+  if (atomicCAS(&c->status, 0, ST_CAPACITY) == 0) c->cap_code = code;
+}
 
 // Device buffers of one handle (all device pointers).
 struct Dev {

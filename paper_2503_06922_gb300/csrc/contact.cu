@@ -177,7 +177,7 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
     return;
   }
   if (m > kLcpSmemRows) {
-    if (tid == 0) atomicCAS(&ctl->status, 0, ST_CAPACITY);
+    if (tid == 0) flag_capacity(ctl, CAP_LCP_ROWS);
     return;
   }
   // ---- q = b - A dx_free; compliance from the largest W_ii

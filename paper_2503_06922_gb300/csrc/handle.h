@@ -32,10 +32,27 @@ struct accfem_handle {
   bool trace = false;                // ACCFEM_TRACE=1 (with stream mode): one line per Newton iteration on stderr
   cudaStream_t user_stream = nullptr; // caller's stream (accfem_set_stream), else the handle's own
   int64_t h2d = 0, d2h = 0;          // bytes copied by solve / state calls
+  int64_t dev_bytes = 0;             // device memory held by the handle
   cudaStream_t work() const { return user_stream ? user_stream : stream; }
 };
 
 // Last prescribed node at insertion delta: nodes 0..k sit in the feeder, k = floor((L - delta) M / L).
 inline int accfem_last_prescribed(double L, int M, double delta) {
   return (int)std::floor((L - delta) * M / L + 1e-6);
+}
+
+// Message of a solve's failure status, with the limit that raised a capacity error.
+inline std::string accfem_solve_message(const Ctl& c, accfem_status s) {
+  std::string m = accfem_status_string(s);
+  if (s == ACCFEM_E_CONTACT_CAPACITY) {
+    switch (c.cap_code) {
+      case accfem::CAP_ROWS: m += ": constraint rows above max_contacts"; break;
+      case accfem::CAP_CANDIDATES: m += ": a node has more than 256 triangles within the activation distance"; break;
+      case accfem::CAP_SURVIVORS: m += ": a node has more than 64 triangles for the exact distance test"; break;
+      case accfem::CAP_NODE_ROWS: m += ": a node has more than 8 constraint rows"; break;
+      case accfem::CAP_LCP_ROWS: m += ": constraint rows above the contact solver's 512"; break;
+      default: break;
+    }
+  }
+  return m;
 }

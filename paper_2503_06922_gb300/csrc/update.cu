@@ -65,8 +65,9 @@ __global__ void __launch_bounds__(192) step_batch(const Inst* __restrict__ tab, 
 
 // Step limiter (Eq. 25-27 with an adaptive bound): alpha = min(1, rho / max |du|).  A step that
 // points against the previous one (sum_i du_i . du_i^prev < 0, summed over the step blocks in a
-// fixed order) is an overshoot: it is halved, and when it was clipped rho is halved too; otherwise
-// rho doubles back towards beta0.  Every reader evaluates this from the same inputs.
+// fixed order) is an overshoot: rho drops to half of min(rho, max |du|), so the step is at most
+// halved and a repeating cycle shrinks geometrically; otherwise rho grows by 1.5 back towards
+// beta0.  Every reader evaluates this from the same inputs.
 __device__ __forceinline__ void limiter(const Params& p, const Dev& d, const Ctl* ctl, double* rho_new, double* alpha) {
   const int nb = (ctl->nf + 31) / 32;
   double rev = 0.0;
@@ -75,11 +76,10 @@ __device__ __forceinline__ void limiter(const Params& p, const Dev& d, const Ctl
   const double umax = __longlong_as_double((long long)ctl->umax_bits);
   const bool reverse = ctl->has_prev && rev < 0.0;
   if (ctl->has_prev) {
-    if (!reverse) rho = fmin(2.0 * rho, p.beta0);
-    else if (umax > rho) rho = fmax(0.5 * rho, p.beta0 * 9.5367431640625e-07);   // beta0 / 2^20
+    if (reverse) rho = fmax(0.5 * fmin(rho, umax), p.beta0 * 9.094947017729282e-13);   // beta0 / 2^40
+    else rho = fmin(1.5 * rho, p.beta0);
   }
-  double a = umax <= rho ? 1.0 : rho / umax;
-  if (reverse) a *= 0.5;
+  const double a = umax <= rho ? 1.0 : rho / umax;
   *rho_new = rho;
   *alpha = a;
 }

@@ -163,3 +163,38 @@ def test_mask_leaves_members_untouched_and_errors(af):
     b.close()
     for h in hs:
         h.close()
+
+
+def test_served_requests_equal_solves_alone(af):
+    """Continuous-batching server: a request stream over three scenes (arrivals close enough that
+    solves of different scenes overlap) gives, per request, the tip pose and iteration count of the
+    same sequence of solves run alone; a scene left out by the memory cap is answered NOMEM."""
+    ws = _mixed_workloads()[:3]
+    hs = [af.AccFem(w.robot, w.lumen) for w in ws]
+    b = af.AccFemBatch(hs)
+    for s in range(3):
+        b.accfem_batch_solve([w.tensions[s] for w in ws], [w.insertions[s] for w in ws])
+    arr, sc, ten, ins = wl.serve_trace([w.tensions[2] for w in ws], [w.insertions[2] for w in ws],
+                                       [w.robot.length for w in ws], rate=4000.0, duration=0.01, seed=11)
+    assert len(arr) >= 20
+    out = b.accfem_batch_serve(arr, sc, ten, ins, chunk_iters=3)
+    assert out["call_status"] == af.OK
+    assert np.all(out["t_end"] >= out["t_begin"]) and np.all(out["t_begin"] >= arr - 1e-9)
+    # the same requests, scene by scene, alone
+    for j, w in enumerate(ws):
+        h = af.AccFem(w.robot, w.lumen)
+        for s in range(3):
+            h.accfem_solve(w.tensions[s], w.insertions[s])
+        for k in np.nonzero(sc == j)[0]:
+            r = h.accfem_solve(ten[k], ins[k])
+            assert r["status"] == out["status"][k] and r["newton_iters"] == out["newton_iters"][k], (j, k)
+            tip = np.concatenate([r["node_pos"][-1], r["node_quat"][-1]])
+            assert np.array_equal(tip, out["tip"][k]), (j, k, np.abs(tip - out["tip"][k]).max())
+            assert r["n_contacts"] == out["n_contacts"][k]
+        h.close()
+    # memory cap that admits nobody: every request answered NOMEM without a solve
+    out2 = b.accfem_batch_serve(arr[:5], sc[:5], ten[:5], ins[:5], chunk_iters=3, hbm_cap_bytes=1)
+    assert out2["call_status"] == af.OK and np.all(out2["status"] == af.E_NOMEM)
+    b.close()
+    for h in hs:
+        h.close()

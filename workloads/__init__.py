@@ -218,6 +218,34 @@ def batch_workloads(n_instances: int = 256, seed: int = 3, step=0.010, length=0.
     return out
 
 
+def serve_trace(start_tensions, start_insertions, lengths, rate, duration, seed=4, dt_max=0.2, dins=0.0005):
+    """Poisson request stream (``rate`` requests/s for ``duration`` s) over scenes whose commands
+    start at ``start_tensions`` (S, k) and ``start_insertions`` (S,): each request picks a scene
+    uniformly and is, with equal probability, a tension increment U[-dt_max, dt_max] N per cable
+    (tensions kept >= 0) or an insertion step of +-dins (kept within [0.3, 1] x length).  Returns
+    arrival times, scene indices, and the absolute tensions and insertion each request asks for."""
+    rng = np.random.default_rng(seed)
+    n = rng.poisson(rate * duration)
+    arrivals = np.sort(rng.uniform(0.0, duration, n))
+    scenes = rng.integers(0, len(start_insertions), n)
+    kinds = rng.integers(0, 2, n)
+    dts = rng.uniform(-dt_max, dt_max, (n, np.asarray(start_tensions).shape[1]))
+    signs = rng.choice([-1.0, 1.0], n)
+    ten = np.array(start_tensions, dtype=np.float64).copy()
+    ins = np.array(start_insertions, dtype=np.float64).copy()
+    out_t = np.zeros((n, ten.shape[1]))
+    out_i = np.zeros(n)
+    for k in range(n):
+        sc = scenes[k]
+        if kinds[k] == 0:
+            ten[sc] = np.maximum(ten[sc] + dts[k], 0.0)
+        else:
+            ins[sc] = min(max(ins[sc] + signs[k] * dins, 0.3 * lengths[sc]), lengths[sc])
+        out_t[k] = ten[sc]
+        out_i[k] = ins[sc]
+    return arrivals, scenes, out_t, out_i
+
+
 def plane_lumen(point, normal, size=0.2, n=8, entrance_point=(0.0, 0.0, 0.0), entrance_dir=(1.0, 0.0, 0.0),
                 entrance_up=(0.0, 1.0, 0.0)) -> LumenDesc:
     """A flat square wall (``n`` x ``n`` quads, two triangles each) through ``point`` with unit
