@@ -32,6 +32,7 @@ if ROOT not in sys.path:
 import workloads as wl  # noqa: E402
 
 METRIC = "solves/s (plain FP64 single-instance GPU path, 600 mm robot, 300 elements, insertion sweep)"
+MAX_CONTACTS = 512          # constraint-row capacity of the benchmark handles
 UNIT = "solves/s"
 
 
@@ -43,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", type=int, default=0,
                     help="run the first N solves of the sweep once (for profilers) and exit")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of each served request stream")
     return ap.parse_args()
 
 
@@ -176,13 +179,128 @@ def profile_run(args):
     import torch
     from paper_2503_06922_gb300 import accfem as af
     w = workload()
-    h = af.AccFem(w.robot, w.lumen)
+    h = af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS)
     for s in range(min(args.profile, len(w.insertions))):
         r = h.accfem_solve(w.tensions[s], w.insertions[s])
         print("solve %d status %d newton %d rows %d" % (s, r["status"], r["newton_iters"], r["n_contacts"]), flush=True)
     torch.cuda.synchronize()
     h.close()
     return 0
+
+
+def batched_run(af, n_inst=256, chunk=8, seq_sample=16):
+    """Uneven batched workload: n_inst instances (element counts log-uniform 50-2000, own lumens,
+    target insertion U[0.3, 1] x 600 mm in ~10 mm warm-started steps), every step of every
+    instance solved by continuous batching (a member begins its next step as soon as its previous
+    one finished; chunk Newton iterations per launch).  Compared with the plain single-instance
+    path on every (n_inst / seq_sample)-th instance's full sweep."""
+    ws = wl.batch_workloads(n_instances=n_inst)
+    hs = [af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS) for w in ws]
+    b = af.AccFemBatch(hs)
+    total = sum(len(w.insertions) for w in ws)
+    # every step of every instance as a request at time 0: the native server runs each member's
+    # steps in order and admits a member's next step as soon as its previous one finished
+    mem = np.concatenate([np.full(len(w.insertions), i) for i, w in enumerate(ws)])
+    step = np.concatenate([np.arange(len(w.insertions)) for w in ws])
+    ten = np.array([ws[i].tensions[k] for i, k in zip(mem, step)])
+    ins = np.array([ws[i].insertions[k] for i, k in zip(mem, step)])
+    l0 = b.accfem_batch_kernel_launches()
+    res = b.accfem_batch_serve(np.zeros(total), mem, ten, ins, chunk_iters=chunk)
+    dt = float(res["t_end"].max())
+    launches = b.accfem_batch_kernel_launches() - l0
+    lat = res["t_end"] - res["t_begin"]
+    iters = res["newton_iters"]
+    fails = int(np.sum(res["status"] != af.OK))
+    # plain path: full sweeps of a sample of the instances, one solve at a time
+    sample = list(range(0, n_inst, max(1, n_inst // seq_sample)))
+    t1 = time.perf_counter()
+    cnt, seq_fail = 0, 0
+    for i in sample:
+        h = af.AccFem(ws[i].robot, ws[i].lumen, max_contacts=MAX_CONTACTS)
+        for s in range(len(ws[i].insertions)):
+            r = h.accfem_solve(ws[i].tensions[s], ws[i].insertions[s])
+            cnt += 1
+            seq_fail += r["status"] != af.OK
+        h.close()
+    seq_dt = time.perf_counter() - t1
+    b.close()
+    for h in hs:
+        h.close()
+    lat = np.asarray(lat) * 1e3
+    return {"workload": "%d uneven instances: elements log-uniform 50-2000, own Catmull-Rom lumens, target insertion "
+                        "U[0.3,1] x 600 mm in ~10 mm warm-started steps (%d solves)" % (n_inst, total),
+            "solves_per_s": total / dt, "seconds": dt, "chunk_iters": chunk,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "newton_iters_per_solve": float(np.mean(iters)), "failed_solves": int(fails), "gpu_launches": int(launches),
+            "plain_sequential": {"solves_per_s": cnt / seq_dt, "solves": cnt, "failed_solves": int(seq_fail),
+                                 "sample": "full sweeps of instances %s" % sample[:4] + "... every %d-th" % (n_inst // seq_sample)},
+            "speedup_vs_plain": (total / dt) / (cnt / seq_dt)}
+
+
+def served_run(af, rates=(2000.0, 5000.0, 10000.0), seconds=10.0, n_scenes=16, chunk=4, plain_requests=1000):
+    """Serving: n_scenes resident scenes drawn as in the batched workload, each first swept to its
+    target insertion; per rate a Poisson request stream (tension increments +-0.2 N per cable or
+    insertion steps of +-0.5 mm) served in real time by accfem_batch_serve.  The plain path serves the
+    first plain_requests requests of the same stream one at a time (measured solve times, FIFO queue
+    at the same arrival times)."""
+    ws = wl.batch_workloads(n_instances=256, count=n_scenes)
+    hs = [af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS) for w in ws]
+    ps = [af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS) for w in ws]
+    b = af.AccFemBatch(hs)
+    S = max(len(w.insertions) for w in ws)
+    for s in range(S):
+        mask = [1 if s < len(w.insertions) else 0 for w in ws]
+        t = [w.tensions[min(s, len(w.insertions) - 1)] for w in ws]
+        ins = [w.insertions[min(s, len(w.insertions) - 1)] for w in ws]
+        b.accfem_batch_solve(t, ins, mask=mask, results=False)
+        for i, w in enumerate(ws):
+            if mask[i]:
+                ps[i].accfem_solve(t[i], ins[i])
+    ten0 = np.array([w.tensions[-1] for w in ws])
+    ins0 = np.array([w.insertions[-1] for w in ws])
+    lengths = [w.robot.length for w in ws]
+    out = []
+    l0 = b.accfem_batch_kernel_launches()
+    for k, rate in enumerate(rates):
+        arr, sc, ten, ins = wl.serve_trace(ten0, ins0, lengths, rate, seconds, seed=100 + k)
+        res = b.accfem_batch_serve(arr, sc, ten, ins, chunk_iters=chunk, hbm_cap_bytes=40 * 1024 ** 3)
+        lat = res["latency"] * 1e3
+        span = float(res["t_end"].max()) if len(arr) else 0.0
+        # plain path on the first requests of the same stream
+        npl = min(plain_requests, len(arr))
+        svc = np.zeros(npl)
+        for j in range(npl):
+            t0 = time.perf_counter()
+            ps[sc[j]].accfem_solve(ten[j], ins[j])
+            svc[j] = time.perf_counter() - t0
+        fin = np.zeros(npl)
+        tprev = 0.0
+        for j in range(npl):
+            tprev = max(arr[j], tprev) + svc[j]
+            fin[j] = tprev
+        plat = (fin - arr[:npl]) * 1e3
+        # the batch scenes continue from where this stream left them; so do the plain ones
+        for i in range(n_scenes):
+            last = np.nonzero(sc == i)[0]
+            if len(last):
+                ten0[i], ins0[i] = ten[last[-1]], ins[last[-1]]
+        out.append({"offered_req_per_s": rate, "requests": int(len(arr)), "solves_per_s": len(arr) / max(span, 1e-9),
+                    "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                    "newton_iters_per_solve": float(res["newton_iters"].mean()),
+                    "failed_solves": int(np.sum(res["status"] != af.OK)),
+                    "plain": {"requests": int(npl), "capacity_solves_per_s": npl / svc.sum(),
+                              "latency_ms": {"p50": float(np.percentile(plat, 50)), "p99": float(np.percentile(plat, 99))}}})
+        # bring the plain scenes to the batch scenes' commands for the next rate
+        for i in range(n_scenes):
+            ps[i].accfem_solve(ten0[i], ins0[i])
+    launches = b.accfem_batch_kernel_launches() - l0
+    b.close()
+    for h in hs + ps:
+        h.close()
+    return {"workload": "%d scenes as in the batched workload, swept to their target insertion; Poisson requests, "
+                        "%.0f s per rate, tension increments U[-0.2,0.2] N per cable or insertion steps +-0.5 mm"
+                        % (n_scenes, seconds),
+            "chunk_iters": chunk, "hbm_cap_gb": 40, "rates": out, "gpu_launches": int(launches)}
 
 
 def ours(args, rank, world, local_rank):
@@ -194,7 +312,7 @@ def ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     from paper_2503_06922_gb300 import accfem as af
     w = workload()
-    h = af.AccFem(w.robot, w.lumen)
+    h = af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS)
     stream = torch.cuda.Stream()
     h.accfem_set_stream(stream.cuda_stream)
     tens_dev = torch.tensor(w.tensions, dtype=torch.float64, device="cuda")
@@ -255,17 +373,24 @@ def ours(args, rank, world, local_rank):
             dist.barrier()
         t0 = time.perf_counter()
         e2e_fail = 0
+        last_ok = 0
         for _ in range(args.steps):
             h.accfem_reset()
             for s in range(S):
                 r = h.accfem_solve(w.tensions[s], w.insertions[s])
                 e2e_fail += r["status"] != af.OK
+                if r["status"] == af.OK:
+                    last_ok = s
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         b1 = h.accfem_transfer_bytes()
         h2d_step = (b1[0] - b0[0]) / args.steps + row_bytes * S
         d2h_step = (b1[1] - b0[1]) / args.steps
-        # ---- kernels timed standalone on the resident final state (the last solve of the sweep)
+        # ---- kernels timed standalone on the resident state of the last converged solve of the sweep
+        if r["status"] != af.OK:
+            h.accfem_reset()
+            for s in range(last_ok + 1):
+                r = h.accfem_solve(w.tensions[s], w.insertions[s])
         last = r
         m_last = int(last["n_contacts"])
         np_last = int(sum(1 for c in last["contacts"] if c["force"] > 0.0))
@@ -286,6 +411,10 @@ def ours(args, rank, world, local_rank):
     el_achieved = ELEMENT_FLOPS * nf / (el_us * 1e-6) / 1e12
     achieved = contact_flops(m_last, np_last) / (ct_us * 1e-6) / 1e12
     peak = FP64_PEAK_TFLOPS
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        extra["batched"] = batched_run(af)
+        extra["served"] = served_run(af, seconds=args.serve_seconds)
     if rank == 0:
         cpu_n, cpu_dt = oracle_sample(w, 15.0)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -311,6 +440,7 @@ def ours(args, rank, world, local_rank):
                 "cpu_baseline": {"value": cpu_n / cpu_dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                  "sample": "first %d solves of the sweep (insertion 10..%d mm), %.1f s, numpy FP64 "
                                            "oracle, single thread" % (cpu_n, 10 * cpu_n, cpu_dt)}}
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

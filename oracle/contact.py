@@ -4,11 +4,16 @@ Contacts are node based: the contact point of Eq. 4 sits at xi = 0 of an element
 N_i(0) B_i selects the translation of one node and row i of A_c is n_i^T on that node.
 
 Per free node p, over ALL triangles (brute force), every locally closest feature within
-r_o + activation gap is one constraint row (``detect_node``).  The contact normal n points
+r_o + activation gap is one constraint row (``detect_node``).  "Over the face" allows the plane
+projection a barycentric margin FACE_BAND outside the triangle, so that a node near an edge shared
+by two faces keeps a row for each (every triangle's distance constraint is a valid wall
+constraint; the margin removes the row switching at face edges that stalls Newton iterations).  The contact normal n points
 from the robot towards the far side of the wall (Eq. 3 wording) and the robot radius r_o
 enters the gap of Eq. 10: b_i = n . c - n . p - r_o.
 """
 import numpy as np
+
+FACE_BAND = 0.1
 
 
 def closest_point_on_triangle(p, a, b, c):
@@ -38,8 +43,10 @@ def closest_point_on_triangle(p, a, b, c):
 
 def closest_points_all(p, A, B, C):
     """Vectorised ``closest_point_on_triangle`` over triangles (rows of A, B, C).
-    Returns the closest points, distances, and whether each point is interior to its face
-    (the plane projection falls inside the triangle, edges included)."""
+    Returns the closest points, distances, whether each point is interior to its face (the plane
+    projection falls inside the triangle, edges included), and whether the plane projection falls
+    inside the triangle enlarged by the barycentric margin FACE_BAND (all three barycentric
+    coordinates >= -FACE_BAND)."""
     ab = B - A
     ac = C - A
     n = np.cross(ab, ac)
@@ -52,6 +59,7 @@ def closest_points_all(p, A, B, C):
     v = (m11 * r0 - m01 * r1) / det
     w = (m00 * r1 - m01 * r0) / det
     inside = (v >= 0) & (w >= 0) & (v + w <= 1)
+    near = (v >= -FACE_BAND) & (w >= -FACE_BAND) & (v + w <= 1 + FACE_BAND)
     best = proj.copy()
     bd = np.where(inside, np.linalg.norm(p[None, :] - proj, axis=1), np.inf)
     for S0, S1 in ((A, B), (B, C), (C, A)):
@@ -62,7 +70,7 @@ def closest_points_all(p, A, B, C):
         upd = (~inside) & (d < bd)
         best[upd] = q[upd]
         bd = np.where(upd, d, bd)
-    return best, bd, inside
+    return best, bd, inside, near
 
 
 def face_normals(V, T):
@@ -88,8 +96,9 @@ def detect_node(p, V, T, r_o, activation_gap, nf=None):
     With c_t the closest point of triangle t, d_t = |c_t - p| and g the triangle of smallest
     d_t (lowest index on ties), the pair (node, t) is a constraint when d_t <= r_o + activation
     gap and c_t is a locally closest point of the mesh:
-      * c_t interior to its face (the node lies over the face; edges count as interior):
-        the face plane, n = outward face normal;
+      * the node lies over t's face: its plane projection is inside the triangle enlarged by the
+        barycentric margin FACE_BAND.  Interior projection (edges included): the face plane,
+        n = outward face normal; projection in the margin: c_t on an edge, n as below;
       * t = g with c_t on an edge or a vertex (a convex feature): n along c_t - p, flipped
         to the outside when the node has crossed the wall.
     Faces meeting at a concave crease thus each contribute their plane (one plane per node
@@ -100,12 +109,12 @@ def detect_node(p, V, T, r_o, activation_gap, nf=None):
     if nf is None:
         nf = face_normals(V, T)
     A, B, C = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
-    cp, d, inside = closest_points_all(p, A, B, C)
+    cp, d, inside, near = closest_points_all(p, A, B, C)
     g = int(np.argmin(d))
     thr = r_o + activation_gap
     recs = []
     for t in np.where(d <= thr)[0]:
-        if not (inside[t] or t == g):
+        if not (near[t] or t == g):
             continue
         rec = _record(p, t, cp[t], d[t], bool(inside[t]), nf[t], r_o)
         if any(np.linalg.norm(r["point"] - rec["point"]) <= 1e-12 for r in recs):

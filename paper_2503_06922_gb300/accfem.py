@@ -56,6 +56,15 @@ class accfem_response(ctypes.Structure):
                 ("pad", ctypes.c_int32)]
 
 
+REQUEST_DTYPE = np.dtype([("arrival", np.float64), ("member", np.int32), ("pad", np.int32),
+                          ("cable_tensions", np.float64, (8,)), ("insertion", np.float64)], align=True)
+RESPONSE_DTYPE = np.dtype([("status", np.int32), ("newton_iters", np.int32), ("t_begin", np.float64),
+                           ("t_end", np.float64), ("tip", np.float64, (7,)), ("n_contacts", np.int32),
+                           ("pad", np.int32)], align=True)
+assert REQUEST_DTYPE.itemsize == ctypes.sizeof(accfem_request)
+assert RESPONSE_DTYPE.itemsize == ctypes.sizeof(accfem_response)
+
+
 class accfem_state(ctypes.Structure):
     _fields_ = [("node_pos", _dp), ("node_quat", _dp)]
 
@@ -376,23 +385,21 @@ class AccFemBatch:
         numpy arrays: status, newton_iters, t_begin, t_end, latency, tip (k, 7), n_contacts, and the
         call's status."""
         k = len(arrivals)
-        req = (accfem_request * max(k, 1))()
-        ta = np.asarray(tensions, dtype=np.float64).reshape(k, -1) if k else np.zeros((0, 1))
-        for j in range(k):
-            req[j].arrival = float(arrivals[j])
-            req[j].member = int(members[j])
-            for c in range(ta.shape[1]):
-                req[j].cable_tensions[c] = float(ta[j, c])
-            req[j].insertion = float(insertions[j])
-        resp = (accfem_response * max(k, 1))()
-        st = self._lib.accfem_batch_serve(self.b, req, k, int(chunk_iters), int(hbm_cap_bytes), resp)
-        out = {"call_status": int(st),
-               "status": np.array([resp[j].status for j in range(k)], dtype=np.int32),
-               "newton_iters": np.array([resp[j].newton_iters for j in range(k)], dtype=np.int32),
-               "t_begin": np.array([resp[j].t_begin for j in range(k)]),
-               "t_end": np.array([resp[j].t_end for j in range(k)]),
-               "tip": np.array([list(resp[j].tip) for j in range(k)]).reshape(k, 7),
-               "n_contacts": np.array([resp[j].n_contacts for j in range(k)], dtype=np.int32)}
+        req = np.zeros(max(k, 1), dtype=REQUEST_DTYPE)
+        if k:
+            ta = np.asarray(tensions, dtype=np.float64).reshape(k, -1)
+            req["arrival"][:k] = arrivals
+            req["member"][:k] = members
+            req["cable_tensions"][:k, :ta.shape[1]] = ta
+            req["insertion"][:k] = insertions
+        resp = np.zeros(max(k, 1), dtype=RESPONSE_DTYPE)
+        st = self._lib.accfem_batch_serve(self.b, req.ctypes.data_as(ctypes.POINTER(accfem_request)), k,
+                                          int(chunk_iters), int(hbm_cap_bytes),
+                                          resp.ctypes.data_as(ctypes.POINTER(accfem_response)))
+        resp = resp[:k]
+        out = {"call_status": int(st), "status": resp["status"].copy(), "newton_iters": resp["newton_iters"].copy(),
+               "t_begin": resp["t_begin"].copy(), "t_end": resp["t_end"].copy(), "tip": resp["tip"].copy(),
+               "n_contacts": resp["n_contacts"].copy()}
         out["latency"] = out["t_end"] - np.asarray(arrivals, dtype=np.float64)
         return out
 

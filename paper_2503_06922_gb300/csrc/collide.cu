@@ -3,16 +3,18 @@
 //
 // Constraint rule (identical to an all-pairs FP64 scan): with c_t the closest point of triangle
 // t to the node p, d_t = |c_t - p| and g the triangle of smallest d_t (lowest index on ties),
-// (node, t) is a constraint row when d_t <= r_o + activation_gap and c_t is locally closest:
-// interior to t's face (plane projection inside, edges included), or t == g (edge/vertex point).
-// Rows with the same closest point (within 1e-12 m) are merged, keeping the lowest index.
+// (node, t) is a constraint row when d_t <= r_o + activation_gap and the node lies over t's face
+// (plane projection inside the triangle enlarged by the barycentric margin kFaceBand), or t == g.
+// The row's normal is the face normal when the projection is inside the triangle itself, else
+// along c_t - p (edge/vertex point).  Rows with the same closest point (within 1e-12 m) are
+// merged, keeping the lowest index.
 //
 // Work split: triangles are binned by centroid in a uniform grid; a node scans the cells of the
 // box p +- (r_o + gap + max triangle radius).  A triangle whose FP32 bounding sphere stays beyond
 // the activation distance (+ eps_d) is skipped.  Pass 1 computes FP32 distances (coordinates
 // relative to the cell centre, so |x| is a few mm and the FP32 error a few 1e-9 m) and their
 // warp minimum; pass 2 keeps a triangle for the exact FP64 test when its FP32 distance is within
-// eps_d of the activation distance AND (its FP32 barycentrics are inside up to eps_b, or its
+// eps_d of the activation distance AND (its FP32 barycentrics are inside the band up to eps_b, or its
 // FP32 distance is within 2 eps_d of the minimum); survivors are compacted by warp ballot.  Every
 // triangle that can form a row in FP64 passes, so the FP64 decisions below see the same candidates
 // as a full scan.  The FP64 closest points, the overall minimum, the merge of equal points and the
@@ -79,10 +81,10 @@ __device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int 
           if (dx * dx + dy * dy + dz * dz <= rr * rr) {
             float va, vb, vc;
             float dd = sqrtf(tri_dist2_f32(pc, d.tri32 + (size_t)s * 9, va, vb, vc));
-            float tol = -p.eps_b * (va + vb + vc);
+            float tol = -((float)kFaceBand + p.eps_b) * (va + vb + vc);
             bool near_in = (va >= tol) && (vb >= tol) && (vc >= tol);
             keep = dd <= thr32;
-            code = near_in ? -1.f - dd : dd;             // sign carries the near-inside flag
+            code = near_in ? -1.f - dd : dd;             // sign carries the near-the-face flag
           }
         }
         unsigned mk = __ballot_sync(0xffffffffu, keep);
@@ -137,7 +139,7 @@ __device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int 
     double Cv[3] = {d.V[3 * tv[2]], d.V[3 * tv[2] + 1], d.V[3 * tv[2] + 2]};
     Surv sv;
     sv.t = t;
-    sv.d2 = tri_closest_f64(pn, A, Bv, Cv, sv.c, &sv.interior);
+    sv.d2 = tri_closest_f64(pn, A, Bv, Cv, sv.c, &sv.interior, &sv.near);
     s_surv[wib][i] = sv;
   }
   __syncwarp();
@@ -154,7 +156,7 @@ __device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int 
     int ot = __shfl_xor_sync(0xffffffffu, gt, o);
     if (od < gd || (od == gd && ot < gt)) { gd = od; gt = ot; }
   }
-  // ---- qualifying survivors: within r_o + gap, and interior or the overall closest
+  // ---- qualifying survivors: within r_o + gap, and over the face (within the band) or the overall closest
   bool qual[2] = {false, false};
   double dist[2] = {0.0, 0.0};
 #pragma unroll
@@ -163,7 +165,7 @@ __device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int 
     if (i < ns) {
       const Surv& sv = s_surv[wib][i];
       dist[h] = sqrt(sv.d2);
-      qual[h] = (dist[h] <= thr) && (sv.interior || sv.t == gt);
+      qual[h] = (dist[h] <= thr) && (sv.near || sv.t == gt);
     }
   }
   // ---- merge equal closest points (lowest triangle index stays), rank by triangle index

@@ -43,9 +43,10 @@ __device__ __forceinline__ float tri_dist2_f32(const float* p, const float* t, f
 
 // FP64 closest point of triangle (A, B, C) to p (the Voronoi-region method of Ericson, Real-Time
 // Collision Detection, 2005, Sec. 5.1.5), with "interior" = all three unnormalised barycentrics of
-// the plane projection >= 0.  Returns the closest point in c (absolute), |c - p|^2, interior flag.
+// the plane projection >= 0 and "near" = all three >= -kFaceBand times their sum.  Returns the
+// closest point in c (absolute), |c - p|^2, and the two flags.
 static __device__ double tri_closest_f64(const double* p, const double* A, const double* B, const double* C,
-                                  double* c, int* interior) {
+                                  double* c, int* interior, int* near) {
   double ab[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
   double ac[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
   double ap[3] = {p[0] - A[0], p[1] - A[1], p[2] - A[2]};
@@ -54,6 +55,8 @@ static __device__ double tri_closest_f64(const double* p, const double* A, const
   double d1 = dot3(ab, ap), d2 = dot3(ac, ap), d3 = dot3(ab, bp), d4 = dot3(ac, bp), d5 = dot3(ab, cp),
          d6 = dot3(ac, cp);
   double va = d3 * d6 - d5 * d4, vb = d5 * d2 - d1 * d6, vc = d1 * d4 - d3 * d2;
+  const double band = -kFaceBand * (va + vb + vc);
+  *near = (va >= band && vb >= band && vc >= band) ? 1 : 0;
   double q[3];
   *interior = 0;
   if (va >= 0.0 && vb >= 0.0 && vc >= 0.0) {
@@ -80,7 +83,9 @@ static __device__ double tri_closest_f64(const double* p, const double* A, const
 
 struct Surv {
   int t;
-  int interior;
+  int interior;     // plane projection inside the triangle
+  int near;         // plane projection inside the triangle enlarged by kFaceBand
+  int pad;
   double d2;
   double c[3];
 };

@@ -12,6 +12,9 @@ constexpr int kCandCap = 256;      // triangles per node within the activation d
 constexpr int kElemStride = 96;    // doubles per element record: 78 K (upper) + 12 F + pad
 constexpr int kWarpsPerElemBlock = 2;
 constexpr int kRhsSplit = 4;       // blocks per node that share the RHS columns (chunks of 32)
+// A triangle whose plane projection of the node lies inside it enlarged by this barycentric margin
+// ("over the face") gives a constraint row; the same value is used by the CPU oracle.
+constexpr double kFaceBand = 0.1;
 
 // Status codes mirrored from accfem.h
 enum : int { ST_OK = 0, ST_INVALID = 1, ST_NOMEM = 2, ST_CUDA = 3, ST_NOT_CONVERGED = 4,

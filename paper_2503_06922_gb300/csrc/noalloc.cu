@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(128) detect_noalloc_kernel(Params p, Dev d, co
           if (s < s1) {
             float va, vb, vc;
             float dd = sqrtf(tri_dist2_f32(pc, d.tri32 + (size_t)s * 9, va, vb, vc));
-            float tol = -p.eps_b * (va + vb + vc);
+            float tol = -((float)kFaceBand + p.eps_b) * (va + vb + vc);
             bool near_in = (va >= tol) && (vb >= tol) && (vc >= tol);
             keep = (dd <= thr32) && (near_in || dd <= dmin_keep);
           }
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(128) detect_noalloc_kernel(Params p, Dev d, co
             double Cv[3] = {d.V[3 * tv[2]], d.V[3 * tv[2] + 1], d.V[3 * tv[2] + 2]};
             Surv sv;
             sv.t = t;
-            sv.d2 = tri_closest_f64(pn, A, Bv, Cv, sv.c, &sv.interior);
+            sv.d2 = tri_closest_f64(pn, A, Bv, Cv, sv.c, &sv.interior, &sv.near);
             int slot = atomicAdd(&s_ns[wib], 1);
             if (slot < kSurvCap) s_surv[wib][slot] = sv;
           }
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(128) detect_noalloc_kernel(Params p, Dev d, co
     const Surv& sv = s_surv[wib][ord[oi]];
     double dist = sqrt(sv.d2);
     if (!(dist <= thr)) continue;
-    if (!(sv.interior || ord[oi] == g)) continue;
+    if (!(sv.near || ord[oi] == g)) continue;
     bool dup = false;
     for (int r = 0; r < nc; ++r) {
       double dx = cpt[3 * r] - sv.c[0], dy = cpt[3 * r + 1] - sv.c[1], dz = cpt[3 * r + 2] - sv.c[2];

@@ -45,7 +45,7 @@ def test_closest_point_all_seven_regions():
         assert np.allclose(contact.closest_point_on_triangle(np.array(p, float), a, b, c), q, atol=1e-15)
     P = np.array([p for p, _ in cases], float)
     for p, q in cases:
-        cp, d, inside = contact.closest_points_all(np.array(p, float), a[None], b[None], c[None])
+        cp, d, inside, _ = contact.closest_points_all(np.array(p, float), a[None], b[None], c[None])
         assert np.allclose(cp[0], q, atol=1e-15)
         assert inside[0] == (p == (0.2, 0.3, 0.9))
 
@@ -55,7 +55,7 @@ def test_vectorised_matches_scalar():
     A, B, C = rng.normal(size=(3, 200, 3))
     for _ in range(20):
         p = rng.normal(size=3)
-        cp, d, _ = contact.closest_points_all(p, A, B, C)
+        cp, d, _, _ = contact.closest_points_all(p, A, B, C)
         for t in range(0, 200, 17):
             q = contact.closest_point_on_triangle(p, A[t], B[t], C[t])
             assert np.allclose(cp[t], q, atol=1e-13)
@@ -84,7 +84,8 @@ def test_plane_wall_closed_form():
 
 def test_crease_and_ridge_explicit():
     """Valley (concave crease seen from the lumen): both face planes; ridge (convex edge):
-    one edge constraint with n along c - p."""
+    one edge constraint with n along c - p (both faces reach the ridge point within the band,
+    and rows with the same closest point are one)."""
     ca, sa = np.cos(0.3), np.sin(0.3)
     V = np.array([[0, 0, -1.0], [0, 0, 1.0], [ca, sa, 0.0], [-ca, sa, 0.0]])
     T = np.array([[0, 2, 1], [0, 1, 3]], np.int32)
@@ -108,6 +109,30 @@ def test_crease_and_ridge_explicit():
     assert recs2[0]["gap"] == pytest.approx(0.3 - 0.2, abs=1e-15)
 
 
+def test_face_band_rows_closed_form():
+    """Two coplanar triangles sharing the diagonal of the unit square (z = 0).  A node over the
+    first triangle within the barycentric band of the second has two rows: the first face's plane
+    (foot of the perpendicular) and the second triangle's edge point (projection onto the shared
+    diagonal, normal along c - p); farther from the diagonal it has the face row only."""
+    V = np.array([[0, 0, 0.0], [1, 0, 0.0], [1, 1, 0.0], [0, 1, 0.0]])
+    T = np.array([[0, 2, 1], [0, 3, 2]], np.int32)      # outward normal -z (the node is at z > 0)
+    nf = contact.face_normals(V, T)
+    assert np.allclose(nf, [[0, 0, -1], [0, 0, -1]])
+    p = np.array([0.5, 0.45, 0.2])                       # second triangle's coordinate w = -0.05
+    recs = contact.detect_node(p, V, T, 0.15, 0.1, nf)
+    assert [r["tri"] for r in recs] == [0, 1]
+    assert recs[0]["face"] and np.allclose(recs[0]["point"], [0.5, 0.45, 0.0], atol=1e-15)
+    assert recs[0]["gap"] == pytest.approx(0.2 - 0.15, abs=1e-15)
+    c = np.array([0.475, 0.475, 0.0])
+    assert not recs[1]["face"] and np.allclose(recs[1]["point"], c, atol=1e-15)
+    dist = np.linalg.norm(c - p)
+    assert np.allclose(recs[1]["normal"], (c - p) / dist, atol=1e-15)
+    assert recs[1]["gap"] == pytest.approx(dist - 0.15, abs=1e-15)
+    p2 = np.array([0.5, 0.3, 0.2])                       # w = -0.2: outside the band
+    recs2 = contact.detect_node(p2, V, T, 0.15, 0.1, nf)
+    assert [r["tri"] for r in recs2] == [0] and recs2[0]["face"]
+
+
 def test_detect_matches_naive_loop_on_small_mesh():
     """P10: brute force over a small random tube mesh with a plain per-triangle loop."""
     pts = wl.bent_tube_centerline(straight=0.01, arc_angle=0.5, bend_radius=0.02, ds=0.002)
@@ -125,10 +150,15 @@ def test_detect_matches_naive_loop_on_small_mesh():
         for t in range(len(T)):
             if d[t] > 0.003:
                 continue
-            # interior: closest point equals the plane projection
-            proj = p - np.dot(nf[t], p - V[T[t, 0]]) * nf[t]
-            interior = np.linalg.norm(proj - cps[t]) <= 1e-13
-            if interior or t == best:
+            # over the face: barycentric coordinates of the plane projection, each >= -FACE_BAND
+            a0, a1, a2 = V[T[t, 0]], V[T[t, 1]], V[T[t, 2]]
+            proj = p - np.dot(nf[t], p - a0) * nf[t]
+            G = np.array([[np.dot(a1 - a0, a1 - a0), np.dot(a1 - a0, a2 - a0)],
+                          [np.dot(a1 - a0, a2 - a0), np.dot(a2 - a0, a2 - a0)]])
+            bv, bw = np.linalg.solve(G, [np.dot(a1 - a0, proj - a0), np.dot(a2 - a0, proj - a0)])
+            band = contact.FACE_BAND
+            over = bv >= -band and bw >= -band and 1.0 - bv - bw >= -band
+            if over or t == best:
                 if not any(np.linalg.norm(cps[t] - cps[u]) <= 1e-12 for u in expect):
                     expect.append(t)
         # triangle ids may differ only where several triangles share the closest point

@@ -163,7 +163,7 @@ def test_non_penetration_and_complementarity(bent_sweep):
     nf = contact.face_normals(V, T)
     for i in range(k + 1, w.robot.n_elements + 1):
         p = r.node_pos[i]
-        cp, d, _ = contact.closest_points_all(p, A, B, C)
+        cp, d, _, _ = contact.closest_points_all(p, A, B, C)
         t = int(np.argmin(d))
         assert d[t] >= w.robot.outer_radius - 1e-9
         assert np.dot(nf[t], cp[t] - p) > 0           # on the lumen side
