@@ -32,8 +32,16 @@ if ROOT not in sys.path:
 import workloads as wl  # noqa: E402
 
 METRIC = "solves/s (plain FP64 single-instance GPU path, 600 mm robot, 300 elements, insertion sweep)"
-MAX_CONTACTS = 512          # constraint-row capacity of the benchmark handles
+MAX_CONTACTS = 4096         # constraint-row capacity of the benchmark handles
 UNIT = "solves/s"
+
+
+T_START = time.perf_counter()
+
+
+def progress(msg):
+    """Timestamped progress on stderr (the JSON line alone goes to stdout)."""
+    print("[bench %7.1fs] %s" % (time.perf_counter() - T_START, msg), file=sys.stderr, flush=True)
 
 
 def parse():
@@ -45,7 +53,7 @@ def parse():
     ap.add_argument("--profile", type=int, default=0,
                     help="run the first N solves of the sweep once (for profilers) and exit")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and served measurements")
-    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of each served request stream")
+    ap.add_argument("--serve-requests", type=int, default=1200, help="requests of each served request stream")
     return ap.parse_args()
 
 
@@ -198,6 +206,7 @@ def batched_run(af, n_inst=256, chunk=8, seq_sample=16):
     hs = [af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS) for w in ws]
     b = af.AccFemBatch(hs)
     total = sum(len(w.insertions) for w in ws)
+    progress("batched: %d instances created, %d solves" % (n_inst, total))
     # every step of every instance as a request at time 0: the native server runs each member's
     # steps in order and admits a member's next step as soon as its previous one finished
     mem = np.concatenate([np.full(len(w.insertions), i) for i, w in enumerate(ws)])
@@ -211,6 +220,7 @@ def batched_run(af, n_inst=256, chunk=8, seq_sample=16):
     lat = res["t_end"] - res["t_begin"]
     iters = res["newton_iters"]
     fails = int(np.sum(res["status"] != af.OK))
+    progress("batched: served in %.1f s, %d failed" % (dt, fails))
     # plain path: full sweeps of a sample of the instances, one solve at a time
     sample = list(range(0, n_inst, max(1, n_inst // seq_sample)))
     t1 = time.perf_counter()
@@ -223,6 +233,7 @@ def batched_run(af, n_inst=256, chunk=8, seq_sample=16):
             seq_fail += r["status"] != af.OK
         h.close()
     seq_dt = time.perf_counter() - t1
+    progress("batched: plain sample %d solves in %.1f s" % (cnt, seq_dt))
     b.close()
     for h in hs:
         h.close()
@@ -237,12 +248,12 @@ def batched_run(af, n_inst=256, chunk=8, seq_sample=16):
             "speedup_vs_plain": (total / dt) / (cnt / seq_dt)}
 
 
-def served_run(af, rates=(2000.0, 5000.0, 10000.0), seconds=10.0, n_scenes=16, chunk=4, plain_requests=1000):
+def served_run(af, rates=(2000.0, 5000.0, 10000.0), requests=1200, n_scenes=16, chunk=4, plain_requests=300):
     """Serving: n_scenes resident scenes drawn as in the batched workload, each first swept to its
-    target insertion; per rate a Poisson request stream (tension increments +-0.2 N per cable or
-    insertion steps of +-0.5 mm) served in real time by accfem_batch_serve.  The plain path serves the
-    first plain_requests requests of the same stream one at a time (measured solve times, FIFO queue
-    at the same arrival times)."""
+    target insertion; per rate a Poisson request stream of about `requests` requests (tension
+    increments +-0.2 N per cable or insertion steps of +-0.5 mm) served in real time by
+    accfem_batch_serve.  The plain path serves the first plain_requests requests of the same stream
+    one at a time (measured solve times, FIFO queue at the same arrival times)."""
     ws = wl.batch_workloads(n_instances=256, count=n_scenes)
     hs = [af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS) for w in ws]
     ps = [af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS) for w in ws]
@@ -256,14 +267,17 @@ def served_run(af, rates=(2000.0, 5000.0, 10000.0), seconds=10.0, n_scenes=16, c
         for i, w in enumerate(ws):
             if mask[i]:
                 ps[i].accfem_solve(t[i], ins[i])
+    progress("served: %d scenes set up" % n_scenes)
     ten0 = np.array([w.tensions[-1] for w in ws])
     ins0 = np.array([w.insertions[-1] for w in ws])
     lengths = [w.robot.length for w in ws]
     out = []
     l0 = b.accfem_batch_kernel_launches()
     for k, rate in enumerate(rates):
-        arr, sc, ten, ins = wl.serve_trace(ten0, ins0, lengths, rate, seconds, seed=100 + k)
+        arr, sc, ten, ins = wl.serve_trace(ten0, ins0, lengths, rate, requests / rate, seed=100 + k)
+        progress("served: rate %.0f, %d requests" % (rate, len(arr)))
         res = b.accfem_batch_serve(arr, sc, ten, ins, chunk_iters=chunk, hbm_cap_bytes=40 * 1024 ** 3)
+        progress("served: done in %.1f s" % (float(res["t_end"].max()) if len(arr) else 0.0))
         lat = res["latency"] * 1e3
         span = float(res["t_end"].max()) if len(arr) else 0.0
         # plain path on the first requests of the same stream
@@ -279,6 +293,7 @@ def served_run(af, rates=(2000.0, 5000.0, 10000.0), seconds=10.0, n_scenes=16, c
             tprev = max(arr[j], tprev) + svc[j]
             fin[j] = tprev
         plat = (fin - arr[:npl]) * 1e3
+        progress("served: plain path %d requests in %.1f s" % (npl, svc.sum()))
         # the batch scenes continue from where this stream left them; so do the plain ones
         for i in range(n_scenes):
             last = np.nonzero(sc == i)[0]
@@ -298,8 +313,8 @@ def served_run(af, rates=(2000.0, 5000.0, 10000.0), seconds=10.0, n_scenes=16, c
     for h in hs + ps:
         h.close()
     return {"workload": "%d scenes as in the batched workload, swept to their target insertion; Poisson requests, "
-                        "%.0f s per rate, tension increments U[-0.2,0.2] N per cable or insertion steps +-0.5 mm"
-                        % (n_scenes, seconds),
+                        "about %d per rate, tension increments U[-0.2,0.2] N per cable or insertion steps +-0.5 mm"
+                        % (n_scenes, requests),
             "chunk_iters": chunk, "hbm_cap_gb": 40, "rates": out, "gpu_launches": int(launches)}
 
 
@@ -338,6 +353,7 @@ def ours(args, rank, world, local_rank):
             its += it
         return bad, its
 
+    progress("plain sweep: warm-up")
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             sweep_resident()
@@ -366,6 +382,7 @@ def ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         launches = h.accfem_kernel_launches() - launches0
         solve_ms = np.array([a.elapsed_time(b) for a, b in lat])
+        progress("plain sweep: timed %d steps, %.1f ms/step, %d failed" % (args.steps, total_ms / args.steps, fails))
         # ---- e2e: host buffers through accfem_solve, copies inside the timed region
         b0 = h.accfem_transfer_bytes()
         torch.cuda.synchronize()
@@ -414,7 +431,7 @@ def ours(args, rank, world, local_rank):
     extra = {}
     if rank == 0 and not args.no_extra:
         extra["batched"] = batched_run(af)
-        extra["served"] = served_run(af, seconds=args.serve_seconds)
+        extra["served"] = served_run(af, requests=args.serve_requests)
     if rank == 0:
         cpu_n, cpu_dt = oracle_sample(w, 15.0)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -75,7 +75,12 @@ typedef struct {
  * newton_tol 1e-11 m (stop when the unlimited step has max(|du_i|, r_o |dtheta_i|) below it
  * and the constraint set did not change), contact_tol 1e-11 (relative sign tolerance of the
  * LCP pivoting), max_newton_iters 200, max_contact_iters 1000, max_contacts 256 (constraint
- * rows, at most 512), tangent_mode 0 (material tangent K = B^T K_l B; the only mode on the GPU). */
+ * rows, at most 8192), tangent_mode 0 (material tangent K = B^T K_l B; the only mode on the GPU).
+ * The contact solve of a Newton iteration runs over a working set of at most min(max_contacts, 512)
+ * rows: the rows active, in the working set or violated in the previous iteration of the solve and
+ * the rows whose gap is at most step_limit / 2; every other row is checked against the step (a
+ * violated row joins the working set and the iteration cannot converge), so a converged solve
+ * solves the contact problem of all rows. */
 typedef struct {
   double activation_gap, step_limit, newton_tol, contact_tol;
   int32_t max_newton_iters, max_contact_iters, max_contacts, tangent_mode;
@@ -284,6 +289,10 @@ const char* accfem_batch_last_error(const accfem_batch* b);
 
 /* Frees the batch (not its members); NULL is a no-op. */
 void accfem_batch_destroy(accfem_batch* b);
+
+/* Sizes of the contact problem in the last Newton iteration of the handle's last solve: constraint
+ * rows, rows of the working set, active rows (y > 0); any pointer may be NULL. */
+accfem_status accfem_solve_stats(const accfem_handle* h, int32_t* rows, int32_t* working_rows, int32_t* active_rows);
 
 /* Device memory held by the handle, in bytes. */
 accfem_status accfem_device_bytes(const accfem_handle* h, int64_t* bytes);

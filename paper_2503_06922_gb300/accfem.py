@@ -76,7 +76,7 @@ EXPORTS = ["accfem_default_options", "accfem_create", "accfem_solve", "accfem_so
            "accfem_batch_create", "accfem_batch_begin", "accfem_batch_advance", "accfem_batch_poll",
            "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream", "accfem_batch_transfer_bytes",
            "accfem_batch_kernel_launches", "accfem_batch_last_error", "accfem_batch_destroy", "accfem_batch_serve",
-           "accfem_device_bytes"]
+           "accfem_device_bytes", "accfem_solve_stats"]
 
 MAX_CABLES = 8
 
@@ -134,6 +134,7 @@ def load(path=LIB_PATH):
     lib.accfem_batch_serve.argtypes = [B, ctypes.POINTER(accfem_request), ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int64, ctypes.POINTER(accfem_response)]
     lib.accfem_device_bytes.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
+    lib.accfem_solve_stats.argtypes = [H, _ip, _ip, _ip]
     lib.accfem_batch_destroy.argtypes = [B]
     lib.accfem_batch_destroy.restype = None
     for name in ("accfem_default_options", "accfem_create", "accfem_solve", "accfem_solve_tip_load",
@@ -141,7 +142,7 @@ def load(path=LIB_PATH):
                  "accfem_transfer_bytes", "accfem_time_kernel", "accfem_detect_contacts_noalloc",
                  "accfem_batch_create", "accfem_batch_begin", "accfem_batch_advance", "accfem_batch_poll",
                  "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream",
-                 "accfem_batch_transfer_bytes", "accfem_batch_serve", "accfem_device_bytes"):
+                 "accfem_batch_transfer_bytes", "accfem_batch_serve", "accfem_device_bytes", "accfem_solve_stats"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -289,6 +290,12 @@ class AccFem:
 
     def accfem_kernel_launches(self):
         return int(self._lib.accfem_kernel_launches(self.h))
+
+    def accfem_solve_stats(self):
+        """(constraint rows, working-set rows, active rows) of the last Newton iteration."""
+        a, b, c = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        self._lib.accfem_solve_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        return int(a.value), int(b.value), int(c.value)
 
     def accfem_device_bytes(self):
         v = ctypes.c_int64(0)

@@ -151,7 +151,7 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
       (lumen->n_triangles > 0 && (!lumen->vertices || !lumen->triangles)))
     return ACCFEM_E_INVALID_ARG;
   if (!(opt.activation_gap >= 0) || !(opt.step_limit > 0) || !(opt.newton_tol > 0) || !(opt.contact_tol >= 0) ||
-      opt.max_newton_iters < 1 || opt.max_contact_iters < 1 || opt.max_contacts < 1 || opt.max_contacts > 512 ||
+      opt.max_newton_iters < 1 || opt.max_contact_iters < 1 || opt.max_contacts < 1 || opt.max_contacts > 8192 ||
       opt.tangent_mode != 0)
     return ACCFEM_E_INVALID_ARG;
   // entrance frame
@@ -194,7 +194,9 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
   p.r_c = r.cable_radius;
   for (int j = 0; j < r.n_cables; ++j) { p.cable_cos[j] = std::cos(r.cable_angles[j]); p.cable_sin[j] = std::sin(r.cable_angles[j]); }
   p.m_cap = opt.max_contacts;
-  p.nrhs_cap = opt.max_contacts + 1;
+  p.ws_cap = std::min(opt.max_contacts, kMaxWorking);
+  p.nrhs_cap = p.ws_cap + 1;
+  p.ws_gap = 0.5 * opt.step_limit;
   p.eps_d = 1e-6;
   p.eps_b = 1e-3f;
   p.max_newton = opt.max_newton_iters;
@@ -296,7 +298,7 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
   }
   upload_element_tables();
   Dev& d = h->d;
-  const int N = p.N, M = p.M, nfc = h->nf_cap, mc = p.m_cap;
+  const int N = p.N, M = p.M, nfc = h->nf_cap, mc = p.m_cap, wc = p.ws_cap;
   bool ok = dalloc(h, &d.px, N) && dalloc(h, &d.py, N) && dalloc(h, &d.pz, N) && dalloc(h, &d.qw, N) &&
             dalloc(h, &d.qx, N) && dalloc(h, &d.qy, N) && dalloc(h, &d.qz, N) && dalloc(h, &d.ox, N) &&
             dalloc(h, &d.oy, N) && dalloc(h, &d.oz, N) && dalloc(h, &d.ow, N) && dalloc(h, &d.oqx, N) &&
@@ -313,14 +315,15 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
        dalloc(h, &d.con_gap, (size_t)nfc * kCpn) && dalloc(h, &d.c_node, mc) && dalloc(h, &d.c_tri, mc) &&
        dalloc(h, &d.c_pt, 3 * mc) && dalloc(h, &d.c_n, 3 * mc) && dalloc(h, &d.c_gap, mc) &&
        dalloc(h, &d.c_first, nfc + 1) && dalloc(h, &d.p_node, mc) && dalloc(h, &d.p_tri, mc) &&
-       dalloc(h, &d.p_act, mc) && dalloc(h, &d.init_act, mc) &&
+       dalloc(h, &d.p_flag, mc) && dalloc(h, &d.init_flag, mc) && dalloc(h, &d.wrow, wc) &&
+       dalloc(h, &d.rslot, mc) &&
        dalloc(h, &d.D, (size_t)nfc * 36) && dalloc(h, &d.U, (size_t)nfc * 36) && dalloc(h, &d.P, (size_t)nfc * 36) &&
        dalloc(h, &d.Lm, (size_t)nfc * 36) && dalloc(h, &d.Rm, (size_t)nfc * 36) &&
        dalloc(h, &d.B, (size_t)nfc * 6 * p.nrhs_cap) && dalloc(h, &d.g, (size_t)nfc * 6) &&
        dalloc(h, &d.dx, (size_t)nfc * 6) && dalloc(h, &d.du_prev, (size_t)nfc * 3) &&
-       dalloc(h, &d.rev_part, (size_t)nfc / 32 + 2) && dalloc(h, &d.W, (size_t)mc * mc) && dalloc(h, &d.q, mc) &&
-       dalloc(h, &d.y, mc) && dalloc(h, &d.w, mc) && dalloc(h, &d.gj, (size_t)mc * (mc + 2)) &&
-       dalloc(h, &d.inP, mc) && dalloc(h, &d.plist, mc) && dalloc(h, &d.wcol, mc) && dalloc(h, &d.ctl, 1);
+       dalloc(h, &d.rev_part, (size_t)nfc / 32 + 2) && dalloc(h, &d.W, (size_t)wc * wc) &&
+       dalloc(h, &d.y, mc) && dalloc(h, &d.gj, (size_t)wc * (wc + 2)) && dalloc(h, &d.plist, wc) &&
+       dalloc(h, &d.ctl, 1);
   if (!ok) {
     accfem_destroy(h);
     return ACCFEM_E_NOMEM;
@@ -489,11 +492,12 @@ accfem_status run_solve(accfem_handle* h, int load_mode, const double* tensions_
         return ACCFEM_E_CUDA;
       h->d2h += sizeof(Ctl);
       if (h->trace)
-        std::fprintf(stderr, "accfem it %d alpha %.4f umax %.3e step %.3e res %.3e m %d same %d active %d lcp %d\n",
+        std::fprintf(stderr, "accfem it %d alpha %.4f umax %.3e step %.3e res %.3e m %d working %d same %d "
+                     "incomplete %d active %d lcp %d\n",
                      c.iter, c.alpha, __builtin_bit_cast(double, (unsigned long long)c.umax_bits),
                      __builtin_bit_cast(double, (unsigned long long)c.step_bits),
-                     __builtin_bit_cast(double, (unsigned long long)c.res_bits), c.m, c.same_set, c.n_active,
-                     c.lcp_pivots);
+                     __builtin_bit_cast(double, (unsigned long long)c.res_bits), c.m, c.mc, c.same_set, c.incomplete,
+                     c.n_active, c.lcp_pivots);
       if (c.status != 0) {
         status = (accfem_status)c.status;
         h->err = accfem_solve_message(c, status);
@@ -682,6 +686,16 @@ accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t
        cuda_ok(h, cudaStreamSynchronize(st), "restore control");
   if (!ok) return ACCFEM_E_CUDA;
   *us = 1000.0 * ms / reps;
+  return ACCFEM_OK;
+}
+
+accfem_status accfem_solve_stats(const accfem_handle* h, int32_t* rows, int32_t* working_rows, int32_t* active_rows) {
+  if (!h) return ACCFEM_E_INVALID_ARG;
+  const Ctl& c = *h->h_ctl;
+  const bool it = c.nf > 0 && c.iter > 0;
+  if (rows) *rows = it ? c.m : 0;
+  if (working_rows) *working_rows = it ? c.mc : 0;
+  if (active_rows) *active_rows = it ? c.n_active : 0;
   return ACCFEM_OK;
 }
 

@@ -25,8 +25,37 @@ __device__ __forceinline__ double kval(const double* rec, int i, int j) {
 }
 
 // ------------------------------------------------------------------ constraint compaction
+// Exclusive prefix over the 1024 threads of v; *total receives the sum (s_warp: 32 ints).
+__device__ __forceinline__ int block_excl_scan_1024(int v, int* s_warp, int* total) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  __syncthreads();
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int y = s_warp[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += t;
+    }
+    s_warp[lane] = y;
+  }
+  __syncthreads();
+  *total = s_warp[31];
+  return x - v + (w > 0 ? s_warp[w - 1] : 0);
+}
+
 // One CTA: exclusive scan of the per-node row counts, row arrays in (node, triangle) order,
-// comparison with the previous iteration's rows, copy to "previous".
+// comparison with the previous iteration's rows (flags carried by identity), the working set of
+// the contact solve, copy to "previous".  Working set: rows that were in it, active or violated in
+// the previous iteration of this solve (so it only grows), and rows whose gap is at most ws_gap;
+// slots follow the row order.
 __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   __shared__ int s_warp[32];
   __shared__ int s_same;
@@ -38,29 +67,9 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   const int f0 = tid * per, f1 = min(f0 + per, nf);
   int loc = 0;
   for (int f = f0; f < f1; ++f) loc += d.ncon[f];
-  // block exclusive scan of loc
-  int v = loc;
-  const int lane = tid & 31, w = tid >> 5;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int t = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += t;
-  }
-  if (lane == 31) s_warp[w] = v;
   if (tid == 0) s_same = 1;
-  __syncthreads();
-  if (w == 0) {
-    int x = s_warp[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int t = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += t;
-    }
-    s_warp[lane] = x;
-  }
-  __syncthreads();
-  int excl = v - loc + (w > 0 ? s_warp[w - 1] : 0);
-  const int m = s_warp[31];
+  int m = 0;
+  const int excl = block_excl_scan_1024(loc, s_warp, &m);
   if (m > p.m_cap) {
     if (tid == 0) flag_capacity(ctl, CAP_ROWS);
     return;
@@ -83,7 +92,7 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   if (tid == 0) d.c_first[nf] = m;
   __syncthreads();
   const int mp = ctl->m_prev;
-  // active-set warm start: a row seen in the previous iteration keeps its active flag
+  // flags of the same row (node, triangle) in the previous iteration; -1 for a new row
   for (int r = tid; r < m; r += 1024) {
     int nd = d.c_node[r], tr = d.c_tri[r], lo = 0, hi = mp - 1, found = -1;
     while (lo <= hi) {                       // previous rows are ordered by (node, triangle)
@@ -92,7 +101,7 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
       if (pn == nd && pt == tr) { found = mid; break; }
       if (pn < nd || (pn == nd && pt < tr)) lo = mid + 1; else hi = mid - 1;
     }
-    d.init_act[r] = found >= 0 ? d.p_act[found] : -1;
+    d.init_flag[r] = found >= 0 ? d.p_flag[found] : -1;
   }
   if (mp != m) {
     if (tid == 0) s_same = 0;
@@ -101,8 +110,36 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
       if (d.p_node[r] != d.c_node[r] || d.p_tri[r] != d.c_tri[r]) s_same = 0;
   }
   __syncthreads();
-  for (int r = tid; r < m; r += 1024) { d.p_node[r] = d.c_node[r]; d.p_tri[r] = d.c_tri[r]; d.p_act[r] = 0; }
-  if (tid == 0) { ctl->same_set = s_same; ctl->m = m; ctl->m_prev = m; }
+  // working set: contiguous row chunks per thread, slots in row order
+  const int rper = (m + 1023) / 1024;
+  const int r0 = min(tid * rper, m), r1 = min(r0 + rper, m);
+  int nw = 0;
+  for (int r = r0; r < r1; ++r) {
+    const int fl = d.init_flag[r];
+    nw += ((fl > 0) || d.c_gap[r] <= p.ws_gap) ? 1 : 0;
+  }
+  int mc = 0;
+  int slot = block_excl_scan_1024(nw, s_warp, &mc);
+  if (mc > p.ws_cap) {
+    if (tid == 0) flag_capacity(ctl, CAP_WORKING);
+    return;
+  }
+  for (int r = r0; r < r1; ++r) {
+    const int fl = d.init_flag[r];
+    if ((fl > 0) || d.c_gap[r] <= p.ws_gap) {
+      d.wrow[slot] = r;
+      d.rslot[r] = slot++;
+    } else {
+      d.rslot[r] = -1;
+    }
+  }
+  __syncthreads();
+  for (int r = tid; r < m; r += 1024) {
+    d.p_node[r] = d.c_node[r];
+    d.p_tri[r] = d.c_tri[r];
+    d.p_flag[r] = d.rslot[r] >= 0 ? RF_WORKING : 0;
+  }
+  if (tid == 0) { ctl->same_set = s_same; ctl->m = m; ctl->m_prev = m; ctl->mc = mc; }
 }
 
 __global__ void __launch_bounds__(1024) compact_kernel(Params p, Dev d) { compact_body(p, d); }
@@ -113,8 +150,8 @@ __global__ void __launch_bounds__(1024) compact_batch(const Inst* __restrict__ t
 
 // ------------------------------------------------------------------ assembly
 // Assembly and RHS columns of one free node (blocks (node, y), 32 x 6 threads): D, U and g = F - F_a
-// with the tip load of Eq. 16-18, then RHS columns 0 = -g and 1 + row = A^T e_row (block y takes the
-// column chunks y, y + kRhsSplit, ...).
+// with the tip load of Eq. 16-18, then RHS columns 0 = -g and 1 + k = A^T e_row for the row of
+// working-set slot k (block y takes the column chunks y, y + kRhsSplit, ...).
 __device__ __forceinline__ void assemble_rhs_body(const Params& p, const Dev& d, int bx, int by) {
   __shared__ double s_g[6];
   Ctl* ctl = d.ctl;
@@ -167,11 +204,15 @@ __device__ __forceinline__ void assemble_rhs_body(const Params& p, const Dev& d,
   }
   __syncthreads();
   const int c = threadIdx.y;
-  const int nrhs = ctl->m + 1;
+  const int nrhs = ctl->mc + 1;
   for (int r = by * 32 + threadIdx.x; r < nrhs; r += 32 * kRhsSplit) {
     double v;
-    if (r == 0) v = -s_g[c];
-    else v = (d.c_node[r - 1] == f && c < 3) ? d.c_n[3 * (r - 1) + c] : 0.0;
+    if (r == 0) {
+      v = -s_g[c];
+    } else {
+      const int row = d.wrow[r - 1];
+      v = (d.c_node[row] == f && c < 3) ? d.c_n[3 * row + c] : 0.0;
+    }
     d.B[((size_t)f * 6 + c) * p.nrhs_cap + r] = v;
   }
 }
@@ -326,7 +367,7 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
   }
   // forward reduction of level s: b_i -= R_{i-s} b_{i-s} + L_{i+s} b_{i+s}
   const int lane = tid & 31, c = tid >> 5;
-  const int nrhs = ctl->m + 1;
+  const int nrhs = ctl->mc + 1;
   const size_t ld = p.nrhs_cap;
   if (!root) {
     for (int r = by * 32 + lane; r < nrhs; r += 32 * kRhsSplit) {
@@ -409,7 +450,7 @@ __device__ __forceinline__ void bcr_bwd_body(const Params& p, const Dev& d, int 
   }
   __syncthreads();
   const int lane = tid & 31, c = tid >> 5;
-  const int nrhs = ctl->m + 1;
+  const int nrhs = ctl->mc + 1;
   const size_t ld = p.nrhs_cap;
   for (int r0 = by * 32; r0 < nrhs; r0 += 32 * kRhsSplit) {
     const int r = r0 + lane;

@@ -12,6 +12,7 @@ constexpr int kCandCap = 256;      // triangles per node within the activation d
 constexpr int kElemStride = 96;    // doubles per element record: 78 K (upper) + 12 F + pad
 constexpr int kWarpsPerElemBlock = 2;
 constexpr int kRhsSplit = 4;       // blocks per node that share the RHS columns (chunks of 32)
+constexpr int kMaxWorking = 512;   // rows of the contact working set (RHS columns, LCP size)
 // A triangle whose plane projection of the node lies inside it enlarged by this barycentric margin
 // ("over the face") gives a constraint row; the same value is used by the CPU oracle.
 constexpr double kFaceBand = 0.1;
@@ -21,7 +22,11 @@ enum : int { ST_OK = 0, ST_INVALID = 1, ST_NOMEM = 2, ST_CUDA = 3, ST_NOT_CONVER
              ST_CAPACITY = 5, ST_NOT_SPD = 6, ST_TIMEOUT = 7 };
 
 // Which limit raised ST_CAPACITY (Ctl::cap_code).
-enum : int { CAP_ROWS = 1, CAP_CANDIDATES = 2, CAP_SURVIVORS = 3, CAP_NODE_ROWS = 4, CAP_LCP_ROWS = 5 };
+enum : int { CAP_ROWS = 1, CAP_CANDIDATES = 2, CAP_SURVIVORS = 3, CAP_NODE_ROWS = 4, CAP_LCP_ROWS = 5,
+             CAP_WORKING = 6 };
+
+// Flags of a constraint row, carried from one Newton iteration to the next by (node, triangle).
+enum : int { RF_ACTIVE = 1, RF_WORKING = 2, RF_VIOLATED = 4 };
 
 // Constants of one handle, passed by value to every kernel.
 struct Params {
@@ -41,7 +46,9 @@ struct Params {
   double eps_d;                  // FP32 distance margin (m)
   float eps_b;                   // FP32 relative barycentric margin
   int m_cap;                     // max constraint rows
-  int nrhs_cap;                  // 1 + m_cap
+  int ws_cap;                    // max rows of the working set (<= kMaxWorking)
+  int nrhs_cap;                  // 1 + ws_cap RHS columns
+  double ws_gap;                 // a row whose gap is at most this joins the working set
   int max_newton;                // Newton iteration cap of a solve
 };
 
@@ -65,7 +72,9 @@ struct Ctl {
   int has_prev;          // a previous Newton step exists in this solve
   int live;              // batch: a solve of this instance is in flight
   int cap_code;          // CAP_* cause of an ST_CAPACITY status
-  int pad2;
+  int mc;                // rows of the working set (RHS columns 1..mc)
+  int incomplete;        // a row outside the working set is violated by this iteration's step
+  int pad3;
   double delta;          // insertion of the resident state
   double tension[kMaxCables];
   double tip_f[3], tip_m[3];
@@ -101,19 +110,21 @@ struct Dev {
   double *c_pt, *c_n, *c_gap;                        // m_cap * 3, * 3, * 1
   int *c_first;                                      // nf_cap + 1: rows of node f = [c_first[f], c_first[f+1])
   int *p_node, *p_tri;                               // previous iteration's rows
-  int *p_act;                                        // previous rows: multiplier > 0
-  int *init_act;                                     // current rows: 1/0 from the previous iteration, -1 new
+  int *p_flag;                                       // previous rows: RF_* flags
+  int *init_flag;                                    // current rows: flags of the same row in the previous iteration, -1 new
+  int *wrow;                                         // ws_cap: row of working-set slot k (rows in order)
+  int *rslot;                                        // m_cap: working-set slot of row r, -1 outside
   // block-tridiagonal system (free nodes)
   double *D, *U, *P, *Lm, *Rm;                       // nf_cap * 36 each, row-major 6x6
-  double* B;                                         // nf_cap * 6 * nrhs_cap, [(f*6+c)*nrhs_cap + r]
+  double* B;                                         // nf_cap * 6 * nrhs_cap, [(f*6+c)*nrhs_cap + r]; column 0 -g,
+                                                     // column 1 + k: A^T e_row for working-set slot k
   double* g;                                         // nf_cap * 6 : F - F_a on free DOFs
   double* dx;                                        // nf_cap * 6 : Newton step
   double* du_prev;                                   // nf_cap * 3 : previous Newton step (translations)
   double* rev_part;                                  // per step_kernel block: sum du . du_prev
   // contact LCP
-  double *W, *q, *y, *w, *gj;                        // m_cap^2, m_cap, m_cap, m_cap, m_cap*(m_cap+1)
-  int *inP, *plist;                                  // m_cap
-  int *wcol;                                         // m_cap: column j of W formed in this iteration
+  double *W, *y, *gj;                                // ws_cap^2 (slots), m_cap (rows), ws_cap*(ws_cap+2)
+  int *plist;                                        // ws_cap: active slots
   Ctl* ctl;
 };
 

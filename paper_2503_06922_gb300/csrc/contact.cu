@@ -77,7 +77,7 @@ __device__ __forceinline__ void block_argmin(double& v, int& idx, double* s_red,
 }
 
 constexpr int kLcpThreads = 256;
-constexpr int kLcpSmemRows = 512;      // rows kept in shared memory (max_contacts <= 512)
+constexpr int kLcpSmemRows = kMaxWorking;   // working-set rows kept in shared memory
 constexpr int kLcpSmemGJ = 48;         // active rows solved in shared memory (else in global memory)
 
 struct LcpShared {
@@ -89,9 +89,9 @@ struct LcpShared {
   int np;
 };
 
-// Forms column j of W = A X (with the compliance eps on its diagonal) for every active row j whose
-// column is not formed yet: W_ij = n_i . X_j[node_i].  W is symmetric, so the rows of the active
-// columns give every entry the active-set method reads.
+// Forms column j of W = A X (with the compliance eps on its diagonal) for every active slot j whose
+// column is not formed yet: W_ij = n_i . X_j[node_i] over the working-set slots i (row wrow[i]).
+// W is symmetric, so the rows of the active columns give every entry the active-set method reads.
 __device__ void ensure_columns(const Dev& d, LcpShared& S, int m, size_t ld, double eps_w) {
   const int tid = threadIdx.x, nt = blockDim.x;
   __syncthreads();
@@ -99,8 +99,9 @@ __device__ void ensure_columns(const Dev& d, LcpShared& S, int m, size_t ld, dou
     const int j = S.plist[a];
     if (S.wcol[j]) continue;
     for (int i = tid; i < m; i += nt) {
-      const int fi = d.c_node[i];
-      const double* n = d.c_n + 3 * i;
+      const int row = d.wrow[i];
+      const int fi = d.c_node[row];
+      const double* n = d.c_n + 3 * row;
       double s = 0.0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) s = fma(n[c], d.B[((size_t)fi * 6 + c) * ld + 1 + j], s);
@@ -163,15 +164,18 @@ __device__ bool solve_on_set(const Dev& d, LcpShared& S, int m) {
 // (the Lawson-Hanson NNLS scheme with W SPD): keep y feasible with y_P > 0; add the row of most
 // negative w = W y + q; when the subproblem solution z_P has non-positive entries, step from y
 // towards z up to the first bound and release the rows that reach zero.  Finite for SPD W; starts
-// from the rows active in the previous Newton iteration.  Rows beyond kLcpSmemRows are not
-// supported in shared memory: the kernel flags ST_CAPACITY for such m (max_contacts caps m).
+// from the rows active in the previous Newton iteration.  The LCP runs over the working set (slot i
+// = row wrow[i], column 1 + i of the RHS); rows outside it get y = 0 and are checked against the
+// step afterwards (step kernel).
 __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
   __shared__ LcpShared S;
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
-  const int m = ctl->m;
+  const int m = ctl->mc;
   const int tid = threadIdx.x, nt = blockDim.x;
   const size_t ld = p.nrhs_cap;
+  for (int r = tid; r < ctl->m; r += nt)
+    if (d.rslot[r] < 0) d.y[r] = 0.0;
   if (m == 0) {
     if (tid == 0) ctl->n_active = 0;
     return;
@@ -183,18 +187,20 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
   // ---- q = b - A dx_free; compliance from the largest W_ii
   double wd = 0.0, qmax = 0.0;
   for (int i = tid; i < m; i += nt) {
-    const int fi = d.c_node[i];
-    const double* n = d.c_n + 3 * i;
+    const int row = d.wrow[i];
+    const int fi = d.c_node[row];
+    const double* n = d.c_n + 3 * row;
     double s = 0.0, wii = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       s = fma(n[c], d.B[((size_t)fi * 6 + c) * ld], s);
       wii = fma(n[c], d.B[((size_t)fi * 6 + c) * ld + 1 + i], wii);
     }
-    S.q[i] = d.c_gap[i] - s;
+    const int fl = d.init_flag[row];
+    S.q[i] = d.c_gap[row] - s;
     S.y[i] = 0.0;
     S.wcol[i] = 0;
-    S.inP[i] = d.init_act[i] > 0 ? 1 : 0;
+    S.inP[i] = (fl > 0 && (fl & RF_ACTIVE)) ? 1 : 0;
     wd = fmax(wd, wii);
     qmax = fmax(qmax, fabs(S.q[i]));
   }
@@ -278,11 +284,12 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
     }
   }
   __syncthreads();
-  // ---- results: multipliers, active flags for the next iteration, active list
+  // ---- results: multipliers (by row), active flags for the next iteration, active slots
   for (int i = tid; i < m; i += nt) {
     const bool a = S.inP[i] && S.y[i] > 0.0;
-    d.y[i] = a ? S.y[i] : 0.0;
-    d.p_act[i] = a ? 1 : 0;
+    const int row = d.wrow[i];
+    d.y[row] = a ? S.y[i] : 0.0;
+    d.p_flag[row] = RF_WORKING | (a ? RF_ACTIVE : 0);
   }
   __syncthreads();
   if (tid == 0) {

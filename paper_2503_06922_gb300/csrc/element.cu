@@ -35,6 +35,7 @@ __device__ __forceinline__ void element_body(const Params& p, const Dev& d, int 
   Ctl* ctl = d.ctl;
   if (bx == 0 && threadIdx.x == 0) {                 // reset the per-iteration reductions
     ctl->umax_bits = 0ull; ctl->step_bits = 0ull; ctl->res_bits = 0ull;
+    ctl->incomplete = 0;
   }
   const int e = ctl->k + bx * kWarpsPerElemBlock + wib;
   if (e >= p.M || ctl->status != 0 || ctl->converged) return;

@@ -4,8 +4,10 @@
 
 namespace accfem {
 
-// dx = dx_free - X y over the active rows; per-node maxima of |du|, max(|du|, r_o |dtheta|) and
-// of the residual g + A^T y.  Block: 32 nodes x 6 components.
+// dx = dx_free - X y over the active working-set slots; per-node maxima of |du|,
+// max(|du|, r_o |dtheta|) and of the residual g + A^T y; every row outside the working set is
+// checked against the step: w = b - n . du < -tol marks it violated (it joins the working set in
+// the next iteration, and this iteration cannot converge).  Block: 32 nodes x 6 components.
 __device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx) {
   __shared__ double s_dx[32][6];
   __shared__ double s_r[32][6];
@@ -20,8 +22,8 @@ __device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx)
     double v = d.B[((size_t)f * 6 + c) * ld];
     const int na = ctl->n_active;
     for (int a = 0; a < na; ++a) {
-      int j = d.plist[a];
-      v = fma(-d.B[((size_t)f * 6 + c) * ld + 1 + j], d.y[j], v);
+      const int j = d.plist[a];
+      v = fma(-d.B[((size_t)f * 6 + c) * ld + 1 + j], d.y[d.wrow[j]], v);
     }
     s_dx[fl][c] = v;
     d.dx[(size_t)f * 6 + c] = v;
@@ -32,6 +34,17 @@ __device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx)
     s_r[fl][c] = fabs(r);
   }
   __syncthreads();
+  if (act && c == 0) {
+    for (int row = d.c_first[f]; row < d.c_first[f + 1]; ++row) {
+      if (d.rslot[row] >= 0) continue;
+      const double* n = d.c_n + 3 * row;
+      const double w = d.c_gap[row] - fma(n[0], s_dx[fl][0], fma(n[1], s_dx[fl][1], n[2] * s_dx[fl][2]));
+      if (w < -p.tol) {
+        d.p_flag[row] = RF_VIOLATED;
+        ctl->incomplete = 1;
+      }
+    }
+  }
   double rr_node = 0.0;
   if (act && c == 0)
     rr_node = fmax(fmax(fmax(s_r[fl][0], s_r[fl][1]), fmax(s_r[fl][2], s_r[fl][3])), fmax(s_r[fl][4], s_r[fl][5]));
@@ -120,7 +133,9 @@ __global__ void __launch_bounds__(128) apply_batch(const Inst* __restrict__ tab,
 }
 
 // End of an iteration (one thread): limiter bookkeeping, iteration count, convergence (unscaled
-// step below tol with an unchanged constraint set), and -- inside the device-side Newton graph --
+// step below tol with an unchanged constraint set and no violated row outside the working set, so
+// that the working-set LCP solution solves the LCP of all rows), and -- inside the device-side
+// Newton graph --
 // the loop condition: keep iterating while no error, not converged and fewer than max_iter
 // iterations; a separate count of loop passes bounds the loop whatever the other kernels did.
 __device__ __forceinline__ void ctl_update(const Params& p, const Dev& d) {
@@ -133,7 +148,7 @@ __device__ __forceinline__ void ctl_update(const Params& p, const Dev& d) {
     c->alpha = alpha;
     c->has_prev = 1;
     c->iter += 1;
-    if (step <= p.tol && c->same_set) c->converged = 1;
+    if (step <= p.tol && c->same_set && !c->incomplete) c->converged = 1;
   }
   c->loops += 1;
 }

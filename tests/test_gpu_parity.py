@@ -70,7 +70,12 @@ def test_bent_tube_sweep_matches_oracle(af):
         assert g["status"] == af.OK and o.status == solver.OK, (s, g["status"], g["error"])
         worst = max(worst, _compare(g, o, thr, "step %d" % s))
         assert abs(g["newton_iters"] - o.newton_iters) <= 3
-        assert np.allclose(g["base_reaction"], o.base_reaction, rtol=1e-6, atol=1e-9 * np.abs(o.base_reaction).max())
+        # both solves stop within newton_tol of the equilibrium along different paths (the GPU
+        # solves the contact problem over a working set): the clamp force may differ by the axial
+        # stiffness times twice that tolerance
+        l0 = w.robot.length / w.robot.n_elements
+        EA = w.robot.youngs_modulus * np.pi * (w.robot.outer_radius ** 2 - w.robot.inner_radius ** 2)
+        assert np.allclose(g["base_reaction"], o.base_reaction, rtol=0.0, atol=2.0 * EA / l0 * 1e-11)
     assert len(g["contacts"]) >= 4
     gpu.close()
 
