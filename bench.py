@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", type=int, default=0,
                     help="run the first N solves of the sweep once (for profilers) and exit")
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="run N instances of the batched workload through their first steps (for profilers) and exit")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--serve-requests", type=int, default=1200, help="requests of each served request stream")
     return ap.parse_args()
@@ -318,6 +320,24 @@ def served_run(af, rates=(2000.0, 5000.0, 10000.0), requests=1200, n_scenes=16, 
             "chunk_iters": chunk, "hbm_cap_gb": 40, "rates": out, "gpu_launches": int(launches)}
 
 
+def profile_batch_run(args):
+    """The first 6 steps of the first N instances of the batched workload, in one batch (for ncu
+    captures; with ACCFEM_LAUNCH=stream the phase kernels are launched from a host loop)."""
+    import torch
+    from paper_2503_06922_gb300 import accfem as af
+    ws = wl.batch_workloads(n_instances=256, count=args.profile_batch)
+    hs = [af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS) for w in ws]
+    b = af.AccFemBatch(hs)
+    for s in range(6):
+        st, sts, _ = b.accfem_batch_solve([w.tensions[s] for w in ws], [w.insertions[s] for w in ws], results=False)
+        print("step %d status %d launches %d" % (s, st, b.accfem_batch_kernel_launches()), flush=True)
+    torch.cuda.synchronize()
+    b.close()
+    for h in hs:
+        h.close()
+    return 0
+
+
 def ours(args, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
@@ -477,6 +497,8 @@ def main():
         return reference_arm(args, rank)
     if args.profile:
         return profile_run(args)
+    if args.profile_batch:
+        return profile_batch_run(args)
     return ours(args, rank, world, local_rank)
 
 

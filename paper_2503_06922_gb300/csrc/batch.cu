@@ -7,6 +7,7 @@
 // ends with the plan kernel), and finished members are collected with one gather and one copy.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -79,6 +80,27 @@ int persistent_grid(K kernel, int threads, long long max_units) {
   return (int)g;
 }
 
+// Enqueues one Newton iteration of every instance in flight on st (the body of the batch graph);
+// returns the number of kernels.
+int enqueue_batch_iteration(accfem_batch* b, cudaStream_t st, cudaGraphConditionalHandle cond, int set_cond) {
+  const Inst* tab = b->d_tab;
+  Plan* plan = b->d_plan;
+  const int* g = b->grid;
+  int n = 0;
+  element_batch<<<g[PH_ELEM], 32 * kWarpsPerElemBlock, 0, st>>>(tab, plan); ++n;
+  collide_batch<<<g[PH_COLL], 128, 0, st>>>(tab, plan); ++n;
+  compact_batch<<<g[PH_COMPACT], 1024, 0, st>>>(tab, plan); ++n;
+  assemble_rhs_batch<<<g[PH_ASM], dim3(32, 6), 0, st>>>(tab, plan); ++n;
+  bcr_elim_batch<<<g[PH_ELIM1], 64, 0, st>>>(tab, plan); ++n;
+  for (int j = 0; j < b->levels; ++j) { bcr_level_batch<<<g[PH_LEV0 + j], 192, 0, st>>>(tab, plan, j); ++n; }
+  for (int j = b->levels - 1; j >= 0; --j) { bcr_bwd_batch<<<g[PH_BWD0 + j], 192, 0, st>>>(tab, plan, j); ++n; }
+  contact_batch<<<g[PH_CONTACT], 256, 0, st>>>(tab, plan); ++n;
+  step_batch<<<g[PH_STEP], dim3(32, 6), 0, st>>>(tab, plan); ++n;
+  apply_batch<<<g[PH_APPLY], 128, 0, st>>>(tab, plan); ++n;
+  batch_plan_kernel<<<1, 1024, 0, st>>>(tab, plan, b->n, 1, 0, cond, set_cond); ++n;
+  return n;
+}
+
 bool build_graph(accfem_batch* b) {
   long long units[kPhases] = {};
   for (accfem_handle* h : b->members)
@@ -110,27 +132,12 @@ bool build_graph(accfem_batch* b) {
   cudaStream_t st = b->stream;
   if (!bok(b, cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed), "begin capture"))
     return false;
-  const Inst* tab = b->d_tab;
-  Plan* plan = b->d_plan;
-  const int* g = b->grid;
-  int n = 0;
-  element_batch<<<g[PH_ELEM], 32 * kWarpsPerElemBlock, 0, st>>>(tab, plan); ++n;
-  collide_batch<<<g[PH_COLL], 128, 0, st>>>(tab, plan); ++n;
-  compact_batch<<<g[PH_COMPACT], 1024, 0, st>>>(tab, plan); ++n;
-  assemble_rhs_batch<<<g[PH_ASM], dim3(32, 6), 0, st>>>(tab, plan); ++n;
-  bcr_elim_batch<<<g[PH_ELIM1], 64, 0, st>>>(tab, plan); ++n;
-  for (int j = 0; j < b->levels; ++j) { bcr_level_batch<<<g[PH_LEV0 + j], 192, 0, st>>>(tab, plan, j); ++n; }
-  for (int j = b->levels - 1; j >= 0; --j) { bcr_bwd_batch<<<g[PH_BWD0 + j], 192, 0, st>>>(tab, plan, j); ++n; }
-  contact_batch<<<g[PH_CONTACT], 256, 0, st>>>(tab, plan); ++n;
-  step_batch<<<g[PH_STEP], dim3(32, 6), 0, st>>>(tab, plan); ++n;
-  apply_batch<<<g[PH_APPLY], 128, 0, st>>>(tab, plan); ++n;
-  batch_plan_kernel<<<1, 1024, 0, st>>>(tab, plan, b->n, 1, 0, cond, 1); ++n;
+  b->body_kernels = enqueue_batch_iteration(b, st, cond, 1);
   cudaError_t ce = cudaStreamEndCapture(st, &body);
   if (!bok(b, ce, "end capture") || !bok(b, cudaGraphInstantiate(&b->exec, b->graph, 0), "instantiate graph")) {
     cudaGetLastError();
     return false;
   }
-  b->body_kernels = n;
   return true;
 }
 
@@ -199,6 +206,10 @@ accfem_status accfem_batch_create(accfem_handle* const* members, int32_t n_membe
   }
   while (b->levels < kMaxLevels && phase_gx(PH_LEV0 + b->levels, max_m) > 0) ++b->levels;
   b->pack_cap = pack;
+  {
+    const char* lm = std::getenv("ACCFEM_LAUNCH");
+    b->stream_mode = lm && std::strcmp(lm, "stream") == 0;
+  }
   bool ok = bok(b, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "cudaStreamCreate") &&
             balloc(b, &b->d_tab, b->n) && balloc(b, &b->d_plan, 1) && balloc(b, &b->d_ctl, b->n) &&
             balloc(b, &b->d_stage, b->n) && balloc(b, &b->d_begin, b->n) && balloc(b, &b->d_members, b->n) &&
@@ -289,15 +300,27 @@ accfem_status accfem_batch_advance(accfem_batch* b, int32_t max_iters, int32_t* 
   if (flying > 0) {
     batch_plan_kernel<<<1, 1024, 0, st>>>(b->d_tab, b->d_plan, b->n, 0, max_iters, cudaGraphConditionalHandle(), 0);
     ++b->launches;
-    if (!bok(b, cudaGetLastError(), "kernel launch") || !bok(b, cudaGraphLaunch(b->exec, st), "launch batch graph"))
+    if (!bok(b, cudaGetLastError(), "kernel launch")) return ACCFEM_E_CUDA;
+    if (b->stream_mode) {
+      // host-driven passes (kernels visible to profilers): stop when nothing iterates
+      for (int pass = 0; pass < max_iters; ++pass) {
+        b->launches += enqueue_batch_iteration(b, st, cudaGraphConditionalHandle(), 0);
+        if (!bok(b, cudaMemcpyAsync(b->h_passes + 1, &b->d_plan->n_act, sizeof(int), cudaMemcpyDeviceToHost, st),
+                 "read plan") ||
+            !bok(b, cudaStreamSynchronize(st), "batch iteration"))
+          return ACCFEM_E_CUDA;
+        if (b->h_passes[1] == 0) break;
+      }
+    } else if (!bok(b, cudaGraphLaunch(b->exec, st), "launch batch graph")) {
       return ACCFEM_E_CUDA;
+    }
   }
   if (!bok(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(Ctl) * b->n, cudaMemcpyDeviceToHost, st), "read control") ||
       !bok(b, cudaMemcpyAsync(b->h_passes, &b->d_plan->passes, sizeof(int), cudaMemcpyDeviceToHost, st), "read plan") ||
       !bok(b, cudaStreamSynchronize(st), "batch advance"))
     return ACCFEM_E_CUDA;
   b->d2h += sizeof(Ctl) * b->n + sizeof(int);
-  if (flying > 0) b->launches += (int64_t)b->body_kernels * std::max(*b->h_passes, 1);
+  if (flying > 0 && !b->stream_mode) b->launches += (int64_t)b->body_kernels * std::max(*b->h_passes, 1);
   int left = 0;
   for (int i = 0; i < b->n; ++i) {
     if (b->state[i] != 2) {

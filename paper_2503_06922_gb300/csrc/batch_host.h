@@ -37,6 +37,7 @@ struct accfem_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int body_kernels = 0;
+  bool stream_mode = false;         // ACCFEM_LAUNCH=stream: host-driven passes (kernels visible to profilers)
   int grid[accfem::kPhases] = {};
   int64_t launches = 0, h2d = 0, d2h = 0;
   std::string err;
