@@ -164,12 +164,15 @@ typedef enum {
   ACCFEM_KERNEL_ELEMENT = 0,    /* corotational force + tangent, one warp per element            */
   ACCFEM_KERNEL_COLLIDE = 1,    /* node-vs-triangle detection, one warp per free node            */
   ACCFEM_KERNEL_ASSEMBLE = 2,   /* block-tridiagonal assembly and RHS columns                     */
-  ACCFEM_KERNEL_CONTACT = 3     /* W = A K^-1 A^T and the contact LCP (needs a completed solve)  */
+  ACCFEM_KERNEL_CONTACT = 3,    /* W = A K^-1 A^T and the contact LCP (needs a completed solve)  */
+  ACCFEM_KERNEL_FACTOR = 4      /* assembly + block cyclic reduction factor and multi-RHS solve:
+                                   every launch of one iteration's sequence, timed as one unit   */
 } accfem_kernel;
 
-/* Launches one hot-path kernel reps times on the resident state of the last solve (the listed
- * kernels only read the poses and rewrite their own outputs) and returns the mean device time
- * of one launch in *us, measured with CUDA events on the handle's stream.  For measurement. */
+/* Launches one hot-path kernel (or, for ACCFEM_KERNEL_FACTOR, the whole assembly + factor + solve
+ * sequence) reps times on the resident state of the last solve (the listed kernels only read the
+ * poses and rewrite their own outputs) and returns the mean device time of one launch (sequence)
+ * in *us, measured with CUDA events on the handle's stream.  For measurement. */
 accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t reps, double* us);
 
 /* Collision query that allocates no memory, for callers that cannot call cudaMalloc while they run

@@ -80,7 +80,7 @@ EXPORTS = ["accfem_default_options", "accfem_create", "accfem_solve", "accfem_so
 
 MAX_CABLES = 8
 
-KERNEL_ELEMENT, KERNEL_COLLIDE, KERNEL_ASSEMBLE, KERNEL_CONTACT = range(4)
+KERNEL_ELEMENT, KERNEL_COLLIDE, KERNEL_ASSEMBLE, KERNEL_CONTACT, KERNEL_FACTOR = range(5)
 
 _lib = None
 

@@ -359,6 +359,22 @@ namespace {
   } while (0)
 
 // Enqueues the kernels of one Newton iteration for nf free nodes on stream st; returns the count.
+// Assembly and RHS columns, then the block cyclic reduction: level-1 eliminations, one kernel per
+// level s that updates the kept nodes, eliminates the next level's nodes (or the root) and reduces
+// the RHS, and the back substitution.  Returns the number of kernels.
+int enqueue_factor(const Params& p, const Dev& d, int nf, cudaStream_t st) {
+  int n = 0;
+  auto grid = [nf](int ph) { return dim3(phase_gx(ph, nf), phase_gy(ph)); };
+  assemble_rhs_kernel<<<grid(PH_ASM), dim3(32, 6), 0, st>>>(p, d); ++n;
+  if (nf >= 2) { bcr_elim_kernel<<<grid(PH_ELIM1), 64, 0, st>>>(p, d, 1); ++n; }
+  int levels = 0;
+  while (levels < kMaxLevels && phase_gx(PH_LEV0 + levels, nf) > 0) ++levels;
+  for (int j = 0; j < levels; ++j) { bcr_level_kernel<<<grid(PH_LEV0 + j), 192, 0, st>>>(p, d, 1 << j); ++n; }
+  for (int j = levels - 1; j >= 0; --j)
+    if (phase_gx(PH_BWD0 + j, nf) > 0) { bcr_bwd_kernel<<<grid(PH_BWD0 + j), 192, 0, st>>>(p, d, 1 << j); ++n; }
+  return n;
+}
+
 int enqueue_iteration(accfem_handle* h, int nf, cudaStream_t st, cudaGraphConditionalHandle cond) {
   Params& p = h->p;
   Dev& d = h->d;
@@ -367,15 +383,7 @@ int enqueue_iteration(accfem_handle* h, int nf, cudaStream_t st, cudaGraphCondit
   element_kernel<<<grid(PH_ELEM), 32 * kWarpsPerElemBlock, 0, st>>>(p, d); ++n;
   collide_kernel<<<grid(PH_COLL), 128, 0, st>>>(p, d); ++n;
   compact_kernel<<<1, 1024, 0, st>>>(p, d); ++n;
-  assemble_rhs_kernel<<<grid(PH_ASM), dim3(32, 6), 0, st>>>(p, d); ++n;
-  // block cyclic reduction: level-1 eliminations, then one kernel per level s that updates the kept
-  // nodes, eliminates the next level's nodes (or the root) and reduces the RHS; back substitution
-  if (nf >= 2) { bcr_elim_kernel<<<grid(PH_ELIM1), 64, 0, st>>>(p, d, 1); ++n; }
-  int levels = 0;
-  while (levels < kMaxLevels && phase_gx(PH_LEV0 + levels, nf) > 0) ++levels;
-  for (int j = 0; j < levels; ++j) { bcr_level_kernel<<<grid(PH_LEV0 + j), 192, 0, st>>>(p, d, 1 << j); ++n; }
-  for (int j = levels - 1; j >= 0; --j)
-    if (phase_gx(PH_BWD0 + j, nf) > 0) { bcr_bwd_kernel<<<grid(PH_BWD0 + j), 192, 0, st>>>(p, d, 1 << j); ++n; }
+  n += enqueue_factor(p, d, nf, st);
   contact_kernel<<<1, 256, 0, st>>>(p, d); ++n;
   step_kernel<<<grid(PH_STEP), dim3(32, 6), 0, st>>>(p, d); ++n;
   apply_kernel<<<grid(PH_APPLY), 128, 0, st>>>(p, d); ++n;
@@ -651,7 +659,9 @@ accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t
   Ctl& c = *h->h_ctl;
   const int nf = c.nf;
   if (nf <= 0 || !h->has_state) return fail(h, ACCFEM_E_INVALID_ARG, "no resident solve with free nodes");
-  if (kernel == ACCFEM_KERNEL_CONTACT && c.iter < 1) return fail(h, ACCFEM_E_INVALID_ARG, "no completed iteration");
+  if ((kernel == ACCFEM_KERNEL_CONTACT || kernel == ACCFEM_KERNEL_FACTOR) && c.iter < 1)
+    return fail(h, ACCFEM_E_INVALID_ARG, "no completed iteration");
+  if (kernel < ACCFEM_KERNEL_ELEMENT || kernel > ACCFEM_KERNEL_FACTOR) return fail(h, ACCFEM_E_INVALID_ARG, "unknown kernel");
   cudaStream_t st = h->work();
   // the kernels return early on a converged control block: run them on a copy flagged "iterating"
   Ctl run = c;
@@ -661,6 +671,7 @@ accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  int per_launch = 1;
   auto launch = [&]() {
     switch (kernel) {
       case ACCFEM_KERNEL_ELEMENT:
@@ -668,6 +679,7 @@ accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t
       case ACCFEM_KERNEL_COLLIDE: collide_kernel<<<phase_gx(PH_COLL, nf), 128, 0, st>>>(p, d); break;
       case ACCFEM_KERNEL_ASSEMBLE:
         assemble_rhs_kernel<<<dim3(phase_gx(PH_ASM, nf), phase_gy(PH_ASM)), dim3(32, 6), 0, st>>>(p, d); break;
+      case ACCFEM_KERNEL_FACTOR: per_launch = enqueue_factor(p, d, nf, st); break;
       default: contact_kernel<<<1, 256, 0, st>>>(p, d); break;
     }
   };
@@ -675,7 +687,7 @@ accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t
   cudaEventRecord(e0, st);
   for (int i = 0; i < reps; ++i) launch();
   cudaEventRecord(e1, st);
-  h->launches += reps + 1;
+  h->launches += (int64_t)(reps + 1) * per_launch;
   bool ok = cuda_ok(h, cudaEventSynchronize(e1), "time kernel");
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
