@@ -339,6 +339,52 @@ def served_run(af, rates=(2000.0, 5000.0, 10000.0), requests=1200, n_scenes=16, 
             "chunk_iters": chunk, "hbm_cap_gb": 40, "rates": out, "gpu_launches": int(launches)}
 
 
+def tree_precision_run(af):
+    """The precision configuration: 2000-element robot in the seeded 3-generation branching tube tree
+    (~388k triangles), insertion swept to 0.9 x the shortest root-to-leaf path in ~10 mm steps, once in
+    FP64 and once with the FP32 element tangent; every solve compared (no CPU oracle at this size: the
+    FP64 GPU path, which matches the oracle on the smaller workloads, is the reference)."""
+    w = wl.tree_workload()
+    out = {}
+    runs = {}
+    for mode in (af.PRECISION_FP64, af.PRECISION_MIXED):
+        h = af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS)
+        h.accfem_set_precision(mode)
+        res, t0 = [], time.perf_counter()
+        for s in range(len(w.insertions)):
+            res.append(h.accfem_solve(w.tensions[s], w.insertions[s]))
+        dt = time.perf_counter() - t0
+        runs[mode] = res
+        out["fp64" if mode == af.PRECISION_FP64 else "mixed"] = {
+            "solves_per_s": len(res) / dt, "newton_iters_per_solve": float(np.mean([r["newton_iters"] for r in res])),
+            "failed_solves": int(sum(r["status"] != af.OK for r in res)),
+            "max_rows": int(max(r["n_contacts"] for r in res))}
+        h.close()
+    tip, ferr, same, both = 0.0, 0.0, 0, 0
+    for r6, rm in zip(runs[af.PRECISION_FP64], runs[af.PRECISION_MIXED]):
+        if r6["status"] != af.OK or rm["status"] != af.OK:
+            continue
+        both += 1
+        tip = max(tip, float(np.linalg.norm(rm["node_pos"][-1] - r6["node_pos"][-1])))
+        same += sorted((c["node"], tuple(np.round(c["point"], 9))) for c in rm["contacts"]) == \
+            sorted((c["node"], tuple(np.round(c["point"], 9))) for c in r6["contacts"])
+        f6, fm = {}, {}
+        for c in r6["contacts"]:
+            f6[c["node"]] = f6.get(c["node"], 0.0) + c["force"] * np.asarray(c["normal"])
+        for c in rm["contacts"]:
+            fm[c["node"]] = fm.get(c["node"], 0.0) + c["force"] * np.asarray(c["normal"])
+        fmax = max([np.linalg.norm(v) for v in f6.values()] + [1e-300])
+        for n in set(f6) | set(fm):
+            ferr = max(ferr, float(np.linalg.norm(f6.get(n, 0.0) - fm.get(n, 0.0))) / fmax)
+    out["workload"] = ("%s: 2000 elements, %d triangles, insertion to %.0f mm in %d steps (e2e through accfem_solve)"
+                       % (w.name, len(w.lumen.triangles), 1e3 * w.insertions[-1], len(w.insertions)))
+    out["mixed_vs_fp64"] = {"solves_compared": both, "max_tip_error_m": tip, "max_node_force_rel_error": ferr,
+                            "identical_contact_sets": int(same)}
+    progress("precision tree: fp64 %.1f, mixed %.1f solves/s, tip error %.2e m" %
+             (out["fp64"]["solves_per_s"], out["mixed"]["solves_per_s"], tip))
+    return out
+
+
 def profile_batch_run(args):
     """The first 6 steps of the first N instances of the batched workload, in one batch (for ncu
     captures; with ACCFEM_LAUNCH=stream the phase kernels are launched from a host loop)."""
@@ -430,11 +476,14 @@ def ours(args, rank, world, local_rank):
         t0 = time.perf_counter()
         e2e_fail = 0
         last_ok = 0
+        fp64_runs = None
         for _ in range(args.steps):
             h.accfem_reset()
+            fp64_runs = []
             for s in range(S):
                 r = h.accfem_solve(w.tensions[s], w.insertions[s])
                 e2e_fail += r["status"] != af.OK
+                fp64_runs.append(r)
                 if r["status"] == af.OK:
                     last_ok = s
         torch.cuda.synchronize()
@@ -455,6 +504,53 @@ def ours(args, rank, world, local_rank):
         co_us = h.accfem_time_kernel(af.KERNEL_COLLIDE, 20)
         ct_us = h.accfem_time_kernel(af.KERNEL_CONTACT, 20)
         fa_us = h.accfem_time_kernel(af.KERNEL_FACTOR, 20)
+        # ---- mixed precision: the same sweep with the FP32 element tangent, timed like `value`, and
+        #      every solve compared with the FP64 solve of the same step
+        progress("precision: mixed sweep")
+        h.accfem_set_precision(af.PRECISION_MIXED)
+        sweep_resident()
+        mixed_ms, mixed_fail, mixed_iters = 0.0, 0, 0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            b_, it_ = sweep_resident()
+            t1.record(stream)
+            t1.synchronize()
+            mixed_ms += t0.elapsed_time(t1)
+            mixed_fail += b_
+            mixed_iters += it_
+        h.accfem_reset()
+        tip_err, force_err, same_sets, both_ok = 0.0, 0.0, 0, 0
+        for s in range(S):
+            rm = h.accfem_solve(w.tensions[s], w.insertions[s])
+            r6 = fp64_runs[s]
+            if rm["status"] != af.OK or r6["status"] != af.OK:
+                continue
+            both_ok += 1
+            tip_err = max(tip_err, float(np.linalg.norm(rm["node_pos"][-1] - r6["node_pos"][-1])))
+            km = sorted((c["node"], tuple(np.round(c["point"], 9))) for c in rm["contacts"])
+            k6 = sorted((c["node"], tuple(np.round(c["point"], 9))) for c in r6["contacts"])
+            same_sets += km == k6
+            fm, f6 = {}, {}
+            for c in rm["contacts"]:
+                fm[c["node"]] = fm.get(c["node"], 0.0) + c["force"] * np.asarray(c["normal"])
+            for c in r6["contacts"]:
+                f6[c["node"]] = f6.get(c["node"], 0.0) + c["force"] * np.asarray(c["normal"])
+            fmax = max([np.linalg.norm(v) for v in f6.values()] + [1e-300])
+            for n in set(fm) | set(f6):
+                force_err = max(force_err, float(np.linalg.norm(fm.get(n, 0.0) - f6.get(n, 0.0))) / fmax)
+        h.accfem_set_precision(af.PRECISION_FP64)
+        precision = {"mode": "mixed: FP32 element tangent (FP32 operands and accumulation); FP64 element force, "
+                             "residual, factor, contact Schur complement and contact solve",
+                     "solves_per_s": S * args.steps / (mixed_ms / 1000.0),
+                     "ms_per_step": mixed_ms / args.steps, "newton_iters_per_solve": mixed_iters / (S * args.steps),
+                     "failed_solves": int(mixed_fail),
+                     "vs_fp64_gpu": {"solves_compared": both_ok, "max_tip_error_m": tip_err,
+                                     "max_node_force_rel_error": force_err, "identical_contact_sets": int(same_sets)}}
+        progress("precision: %.1f solves/s, tip error %.2e m" % (precision["solves_per_s"], tip_err))
     # max over ranks
     t_max = total_ms
     e2e_max = e2e_s
@@ -475,6 +571,7 @@ def ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_extra:
         extra["batched"] = batched_run(af)
         extra["served"] = served_run(af, requests=args.serve_requests)
+        extra["precision_tree"] = tree_precision_run(af)
     if rank == 0:
         cpu_n, cpu_dt = oracle_sample(w, 15.0)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -507,6 +604,7 @@ def ours(args, rank, world, local_rank):
                 "cpu_baseline": {"value": cpu_n / cpu_dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                  "sample": "first %d solves of the sweep (insertion 10..%d mm), %.1f s, numpy FP64 "
                                            "oracle, single thread" % (cpu_n, 10 * cpu_n, cpu_dt)}}
+        line["precision"] = precision
         line.update(extra)
         print(json.dumps(line), flush=True)
     if dist:

@@ -156,6 +156,17 @@ accfem_status accfem_reset(accfem_handle* h);
  * void*; NULL restores the handle's own stream).  Calls stay synchronous with respect to it. */
 accfem_status accfem_set_stream(accfem_handle* h, void* stream);
 
+/* Arithmetic of the element kernel.  ACCFEM_PRECISION_FP64 (the default): everything FP64.
+ * ACCFEM_PRECISION_MIXED: the element tangent products (K_l B E^T and the 78 entries of
+ * K = (B E^T)^T K_l B E^T) take FP32 operands with FP32 accumulation; the element force (the
+ * Newton residual), the factorisation, the contact Schur complement and the contact solve stay
+ * FP64.  Collision always prunes in FP32 and decides in FP64.  The tangent only steers the Newton
+ * iteration, whose FP64 residual refines every step, so a converged solve meets the same
+ * tolerance in both modes.  A batch takes each member's mode when the batch is created. */
+#define ACCFEM_PRECISION_FP64 0
+#define ACCFEM_PRECISION_MIXED 1
+accfem_status accfem_set_precision(accfem_handle* h, int32_t mode);
+
 /* Cumulative bytes copied host->device and device->host by this handle's solve and state calls. */
 accfem_status accfem_transfer_bytes(const accfem_handle* h, int64_t* h2d, int64_t* d2h);
 

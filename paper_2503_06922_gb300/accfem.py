@@ -76,7 +76,9 @@ EXPORTS = ["accfem_default_options", "accfem_create", "accfem_solve", "accfem_so
            "accfem_batch_create", "accfem_batch_begin", "accfem_batch_advance", "accfem_batch_poll",
            "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream", "accfem_batch_transfer_bytes",
            "accfem_batch_kernel_launches", "accfem_batch_last_error", "accfem_batch_destroy", "accfem_batch_serve",
-           "accfem_device_bytes", "accfem_solve_stats"]
+           "accfem_device_bytes", "accfem_solve_stats", "accfem_set_precision"]
+
+PRECISION_FP64, PRECISION_MIXED = 0, 1
 
 MAX_CABLES = 8
 
@@ -135,6 +137,7 @@ def load(path=LIB_PATH):
                                        ctypes.c_int64, ctypes.POINTER(accfem_response)]
     lib.accfem_device_bytes.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
     lib.accfem_solve_stats.argtypes = [H, _ip, _ip, _ip]
+    lib.accfem_set_precision.argtypes = [H, ctypes.c_int32]
     lib.accfem_batch_destroy.argtypes = [B]
     lib.accfem_batch_destroy.restype = None
     for name in ("accfem_default_options", "accfem_create", "accfem_solve", "accfem_solve_tip_load",
@@ -142,7 +145,7 @@ def load(path=LIB_PATH):
                  "accfem_transfer_bytes", "accfem_time_kernel", "accfem_detect_contacts_noalloc",
                  "accfem_batch_create", "accfem_batch_begin", "accfem_batch_advance", "accfem_batch_poll",
                  "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream",
-                 "accfem_batch_transfer_bytes", "accfem_batch_serve", "accfem_device_bytes", "accfem_solve_stats"):
+                 "accfem_batch_transfer_bytes", "accfem_batch_serve", "accfem_device_bytes", "accfem_solve_stats", "accfem_set_precision"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -290,6 +293,9 @@ class AccFem:
 
     def accfem_kernel_launches(self):
         return int(self._lib.accfem_kernel_launches(self.h))
+
+    def accfem_set_precision(self, mode):
+        return int(self._lib.accfem_set_precision(self.h, int(mode)))
 
     def accfem_solve_stats(self):
         """(constraint rows, working-set rows, active rows) of the last Newton iteration."""

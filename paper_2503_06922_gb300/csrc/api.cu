@@ -639,6 +639,19 @@ accfem_status accfem_reset(accfem_handle* h) {
   return ACCFEM_OK;
 }
 
+accfem_status accfem_set_precision(accfem_handle* h, int32_t mode) {
+  if (!h || (mode != ACCFEM_PRECISION_FP64 && mode != ACCFEM_PRECISION_MIXED)) return ACCFEM_E_INVALID_ARG;
+  if (h->p.precision == mode) return ACCFEM_OK;
+  if (h->stream) cudaStreamSynchronize(h->work());
+  for (auto& kv : h->graphs) {     // the Newton graphs captured the handle's constants
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  h->graphs.clear();
+  h->p.precision = mode;
+  return ACCFEM_OK;
+}
+
 accfem_status accfem_set_stream(accfem_handle* h, void* stream) {
   if (!h) return ACCFEM_E_INVALID_ARG;
   h->user_stream = (cudaStream_t)stream;

@@ -8,11 +8,12 @@ namespace accfem {
 constexpr int kMaxCables = 8;
 constexpr int kCpn = 8;            // constraint rows per node (locally closest wall features)
 constexpr int kSurvCap = 64;       // FP64 candidates per node after the FP32 prefilter
-constexpr int kCandCap = 256;      // triangles per node within the activation distance (FP32)
+constexpr int kCandCap = 768;      // triangles per node within the activation distance (FP32)
 constexpr int kElemStride = 96;    // doubles per element record: 78 K (upper) + 12 F + pad
 constexpr int kWarpsPerElemBlock = 2;
 constexpr int kRhsSplit = 4;       // blocks per node that share the RHS columns (chunks of 32)
 constexpr int kMaxWorking = 512;   // rows of the contact working set (RHS columns, LCP size)
+constexpr int kPrecisionFP64 = 0, kPrecisionMixed = 1;
 // A triangle whose plane projection of the node lies inside it enlarged by this barycentric margin
 // ("over the face") gives a constraint row; the same value is used by the CPU oracle.
 constexpr double kFaceBand = 0.1;
@@ -50,6 +51,7 @@ struct Params {
   int nrhs_cap;                  // 1 + ws_cap RHS columns
   double ws_gap;                 // a row whose gap is at most this joins the working set
   int max_newton;                // Newton iteration cap of a solve
+  int precision;                 // kPrecisionFP64 or kPrecisionMixed (FP32 element tangent)
 };
 
 // Control block, resident on the device; one per handle.

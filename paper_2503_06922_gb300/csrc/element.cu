@@ -24,9 +24,14 @@ struct ElemShared {
   double Ti[2][9];     // Tsinv(theta_a), Tsinv(theta_b)
   double B[7][12];     // B (local), then B E^T (global comps)
   double H[7][12];     // K_l B E^T
+  float B32[7][12];    // mixed precision: B E^T and K_l B E^T in FP32
+  float H32[7][12];
 };
 
-// Block body: elements k + bx * kWarpsPerElemBlock + warp.
+// Block body: elements k + bx * kWarpsPerElemBlock + warp.  kMixed: the tangent products
+// H = K_l (B E^T) and K = (B E^T)^T H take FP32 operands and FP32 accumulation; the element force
+// (the Newton residual) stays FP64.
+template <bool kMixed>
 __device__ __forceinline__ void element_body(const Params& p, const Dev& d, int bx) {
   __shared__ ElemShared sm[kWarpsPerElemBlock];
   const int lane = threadIdx.x & 31;
@@ -161,39 +166,82 @@ __device__ __forceinline__ void element_body(const Params& p, const Dev& d, int 
     if (idx < 84) sB[idx / 12][idx % 12] = bg[t];
   }
   __syncwarp();
-  // ---- H = K_l (B E^T)
-#pragma unroll
-  for (int t = 0; t < 3; ++t) {
-    int idx = lane + 32 * t;
-    if (idx < 84) {
-      int k = idx / 12, col = idx % 12;
-      double h;
-      switch (k) {
-        case 0: h = ka * sB[0][col]; break;
-        case 1: h = kt * (sB[1][col] - sB[4][col]); break;
-        case 4: h = kt * (sB[4][col] - sB[1][col]); break;
-        case 2: h = kb * fma(4.0, sB[2][col], 2.0 * sB[5][col]); break;
-        case 5: h = kb * fma(2.0, sB[2][col], 4.0 * sB[5][col]); break;
-        case 3: h = kb * fma(4.0, sB[3][col], 2.0 * sB[6][col]); break;
-        default: h = kb * fma(2.0, sB[3][col], 4.0 * sB[6][col]); break;
-      }
-      sH[k][col] = h;
-    }
-  }
-  __syncwarp();
-  // ---- K (upper triangle) and F
   double* out = d.elem + (size_t)e * kElemStride;
+  if constexpr (kMixed) {
+    // ---- FP32 tangent: H = K_l (B E^T), K (upper triangle) = (B E^T)^T H
+    const float ka32 = (float)ka, kt32 = (float)kt, kb32 = (float)kb;
 #pragma unroll
-  for (int t = 0; t < 3; ++t) {
-    int idx = lane + 32 * t;
-    if (idx < 78) {
-      int i = c_up_i[idx], j = c_up_j[idx];
-      double s = 0.0;
+    for (int t = 0; t < 3; ++t) {
+      int idx = lane + 32 * t;
+      if (idx < 84) S.B32[idx / 12][idx % 12] = (float)sB[idx / 12][idx % 12];
+    }
+    __syncwarp();
 #pragma unroll
-      for (int k = 0; k < 7; ++k) s = fma(sB[k][i], sH[k][j], s);
-      out[idx] = s;
+    for (int t = 0; t < 3; ++t) {
+      int idx = lane + 32 * t;
+      if (idx < 84) {
+        int k = idx / 12, col = idx % 12;
+        const auto& b = S.B32;
+        float h;
+        switch (k) {
+          case 0: h = ka32 * b[0][col]; break;
+          case 1: h = kt32 * (b[1][col] - b[4][col]); break;
+          case 4: h = kt32 * (b[4][col] - b[1][col]); break;
+          case 2: h = kb32 * fmaf(4.0f, b[2][col], 2.0f * b[5][col]); break;
+          case 5: h = kb32 * fmaf(2.0f, b[2][col], 4.0f * b[5][col]); break;
+          case 3: h = kb32 * fmaf(4.0f, b[3][col], 2.0f * b[6][col]); break;
+          default: h = kb32 * fmaf(2.0f, b[3][col], 4.0f * b[6][col]); break;
+        }
+        S.H32[k][col] = h;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      int idx = lane + 32 * t;
+      if (idx < 78) {
+        int i = c_up_i[idx], j = c_up_j[idx];
+        float s = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s = fmaf(S.B32[k][i], S.H32[k][j], s);
+        out[idx] = (double)s;
+      }
+    }
+  } else {
+    // ---- H = K_l (B E^T)
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      int idx = lane + 32 * t;
+      if (idx < 84) {
+        int k = idx / 12, col = idx % 12;
+        double h;
+        switch (k) {
+          case 0: h = ka * sB[0][col]; break;
+          case 1: h = kt * (sB[1][col] - sB[4][col]); break;
+          case 4: h = kt * (sB[4][col] - sB[1][col]); break;
+          case 2: h = kb * fma(4.0, sB[2][col], 2.0 * sB[5][col]); break;
+          case 5: h = kb * fma(2.0, sB[2][col], 4.0 * sB[5][col]); break;
+          case 3: h = kb * fma(4.0, sB[3][col], 2.0 * sB[6][col]); break;
+          default: h = kb * fma(2.0, sB[3][col], 4.0 * sB[6][col]); break;
+        }
+        sH[k][col] = h;
+      }
+    }
+    __syncwarp();
+    // ---- K (upper triangle)
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      int idx = lane + 32 * t;
+      if (idx < 78) {
+        int i = c_up_i[idx], j = c_up_j[idx];
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s = fma(sB[k][i], sH[k][j], s);
+        out[idx] = s;
+      }
     }
   }
+  // ---- F = (B E^T)^T f_l, FP64 in both modes
   if (lane < 12) {
     double s = 0.0;
 #pragma unroll
@@ -203,11 +251,15 @@ __device__ __forceinline__ void element_body(const Params& p, const Dev& d, int 
 }
 
 __global__ void __launch_bounds__(32 * kWarpsPerElemBlock) element_kernel(Params p, Dev d) {
-  element_body(p, d, blockIdx.x);
+  if (p.precision == kPrecisionMixed) element_body<true>(p, d, blockIdx.x);
+  else element_body<false>(p, d, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(32 * kWarpsPerElemBlock) element_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
-  for_units(tab, plan, PH_ELEM, [](const Inst& in, int bx, int) { element_body(in.p, in.d, bx); });
+  for_units(tab, plan, PH_ELEM, [](const Inst& in, int bx, int) {
+    if (in.p.precision == kPrecisionMixed) element_body<true>(in.p, in.d, bx);
+    else element_body<false>(in.p, in.d, bx);
+  });
 }
 
 void upload_element_tables() {

@@ -196,6 +196,103 @@ def catmull_rom_workload(lumen_seed: int = 1, tension_seed: int = 2, n_steps: in
     return Workload("catmull_rom_600mm_M%d" % n_elements, robot, lumen, ins, t)
 
 
+def _straight_tube(start, d, length, radius, n_around, ds, back=0.0):
+    """Tube mesh (as tube_mesh, vectorised) around the straight axis from start - back d to
+    start + length d, rings every ds."""
+    n = max(int(math.ceil((length + back) / ds)), 1)
+    ts = -back + (length + back) * np.arange(n + 1) / n
+    pts = start[None, :] + ts[:, None] * d[None, :]
+    up = np.cross(d, [0.0, 0.0, 1.0])
+    if np.linalg.norm(up) < 1e-6:
+        up = np.cross(d, [0.0, 1.0, 0.0])
+    up /= np.linalg.norm(up)
+    bi = np.cross(d, up)
+    phi = 2.0 * math.pi * np.arange(n_around) / n_around
+    ring = np.cos(phi)[:, None] * up[None, :] + np.sin(phi)[:, None] * bi[None, :]
+    verts = (pts[:, None, :] + radius * ring[None, :, :]).reshape(-1, 3)
+    k = np.arange(n)[:, None]
+    j = np.arange(n_around)[None, :]
+    a_ = k * n_around + j
+    b_ = (k + 1) * n_around + j
+    c_ = (k + 1) * n_around + (j + 1) % n_around
+    d_ = k * n_around + (j + 1) % n_around
+    tris = np.stack([np.stack([a_, d_, c_], -1), np.stack([a_, c_, b_], -1)], axis=2).reshape(-1, 3)
+    return verts, tris.astype(np.int32)
+
+
+def branching_tree_lumen(seed: int = 3, radii=(0.008, 0.0055, 0.004), n_around=80, ds=0.00025, overlap=1.5):
+    """Seeded 3-generation binary tube tree: a root segment along +x from the origin; each segment
+    ends in two children turned by U[25, 45] deg from its axis, on either side of a random plane
+    through it; segment lengths U[60, 120] mm; radii by generation.  Each tube is meshed with rings
+    every ds and n_around vertices per ring (outward winding); a child's tube starts `overlap`
+    parent radii back inside its parent, and every triangle whose centroid lies inside another tube
+    (within its radius of its axis, between its end rings) is removed.  Returns the lumen and the
+    root-to-leaf path lengths (sum of segment lengths)."""
+    rng = np.random.default_rng(seed)
+    segs = []
+
+    def add(start, d, gen, parent):
+        length = rng.uniform(0.060, 0.120)
+        segs.append((start, d, length, radii[gen], parent))
+        me = len(segs) - 1
+        if gen < len(radii) - 1:
+            end = start + length * d
+            a = np.cross(d, rng.normal(size=3))
+            a /= np.linalg.norm(a)
+            for sgn in (1.0, -1.0):
+                ang = math.radians(rng.uniform(25.0, 45.0))
+                add(end, math.cos(ang) * d + sgn * math.sin(ang) * a, gen + 1, me)
+
+    add(np.zeros(3), np.array([1.0, 0.0, 0.0]), 0, -1)
+    tubes = []
+    for start, d, length, r, parent in segs:
+        back = overlap * segs[parent][3] if parent >= 0 else 0.0
+        v, t = _straight_tube(start, d, length, r, n_around, ds, back)
+        tubes.append((v, t, start, d, length, r, back))
+    V, T = [], []
+    off = 0
+    for i, (v, t, *_rest) in enumerate(tubes):
+        cen = v[t].mean(axis=1)
+        keep = np.ones(len(t), dtype=bool)
+        for j, (_v, _t, s_j, d_j, l_j, r_j, b_j) in enumerate(tubes):
+            if j == i:
+                continue
+            rel = cen - s_j[None, :]
+            ax = rel @ d_j
+            rad = np.linalg.norm(rel - ax[:, None] * d_j[None, :], axis=1)
+            keep &= ~((ax > -b_j) & (ax < l_j) & (rad < r_j))
+        V.append(v)
+        T.append(t[keep] + off)
+        off += len(v)
+    V = np.concatenate(V)
+    T = np.concatenate(T).astype(np.int32)
+    # root-to-leaf path lengths
+    paths = []
+    for i, (start, d, length, r, parent) in enumerate(segs):
+        if any(p == i for *_x, p in segs):
+            continue
+        total, k = 0.0, i
+        while k >= 0:
+            total += segs[k][2]
+            k = segs[k][4]
+        paths.append(total)
+    lumen = LumenDesc(vertices=V, triangles=T, entrance_point=np.zeros(3), entrance_dir=np.array([1.0, 0.0, 0.0]),
+                      entrance_up=np.array([0.0, 1.0, 0.0]))
+    return lumen, paths
+
+
+def tree_workload(seed: int = 3, n_elements=2000, length=0.600, step=0.010, t_max=5.0) -> Workload:
+    """600 mm robot in the seeded branching tube tree; the robot is longer than every root-to-leaf
+    path, so the insertion is swept up to 0.9 x the shortest path in ~10 mm warm-started steps, with a
+    fresh tension triple U[0, t_max] N per step."""
+    lumen, paths = branching_tree_lumen(seed)
+    top = 0.9 * min(paths)
+    n_steps = int(math.ceil(top / step - 1e-9))
+    ins = top * np.arange(1, n_steps + 1) / n_steps
+    t = random_tensions(seed + 7, n_steps, t_max)
+    return Workload("tree%d_M%d" % (seed, n_elements), robot_desc(length, n_elements), lumen, ins, t)
+
+
 def batch_workloads(n_instances: int = 256, seed: int = 3, step=0.010, length=0.600, m_min=50, m_max=2000,
                     t_max=5.0, first=0, count=None):
     """Uneven instances for batched solves: element count log-uniform in [m_min, m_max], a lumen
