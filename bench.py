@@ -235,8 +235,10 @@ def batched_run(af, n_inst=256, chunk=8, seq_sample=16):
     ten = np.array([ws[i].tensions[k] for i, k in zip(mem, step)])
     ins = np.array([ws[i].insertions[k] for i, k in zip(mem, step)])
     l0 = b.accfem_batch_kernel_launches()
+    b.accfem_batch_autotune(3)
     res = b.accfem_batch_serve(np.zeros(total), mem, ten, ins, chunk_iters=chunk)
     dt = float(res["t_end"].max())
+    variant, ms_pass = b.accfem_batch_tuning()
     launches = b.accfem_batch_kernel_launches() - l0
     lat = res["t_end"] - res["t_begin"]
     iters = res["newton_iters"]
@@ -262,6 +264,8 @@ def batched_run(af, n_inst=256, chunk=8, seq_sample=16):
     return {"workload": "%d uneven instances: elements log-uniform 50-2000, own Catmull-Rom lumens, target insertion "
                         "U[0.3,1] x 600 mm in ~10 mm warm-started steps (%d solves)" % (n_inst, total),
             "solves_per_s": total / dt, "seconds": dt, "chunk_iters": chunk,
+            "autotune": {"variant": variant, "grid_divisor": 2 ** max(variant, 0),
+                         "ms_per_iteration_by_variant": [float(x) for x in ms_pass]},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "newton_iters_per_solve": float(np.mean(iters)), "failed_solves": int(fails), "gpu_launches": int(launches),
             "plain_sequential": {"solves_per_s": cnt / seq_dt, "solves": cnt, "failed_solves": int(seq_fail),
@@ -339,6 +343,29 @@ def served_run(af, rates=(2000.0, 5000.0, 10000.0), requests=1200, n_scenes=16, 
             "chunk_iters": chunk, "hbm_cap_gb": 40, "rates": out, "gpu_launches": int(launches)}
 
 
+def same_rows(ca, cb, tol=1e-9):
+    """Two contact sets agree: per node the same number of rows, and their closest points pair up
+    within tol (rows of one node sorted by point)."""
+    def group(cs):
+        g = {}
+        for c in cs:
+            g.setdefault(c["node"], []).append(np.asarray(c["point"], dtype=np.float64))
+        return {n: sorted(v, key=lambda x: tuple(x)) for n, v in g.items()}
+    ga, gb = group(ca), group(cb)
+    if set(ga) != set(gb):
+        return False
+    for n in ga:
+        if len(ga[n]) != len(gb[n]):
+            return False
+        used = [False] * len(gb[n])
+        for pa in ga[n]:
+            k = next((j for j, pb in enumerate(gb[n]) if not used[j] and np.linalg.norm(pa - pb) <= tol), -1)
+            if k < 0:
+                return False
+            used[k] = True
+    return True
+
+
 def tree_precision_run(af):
     """The precision configuration: 2000-element robot in the seeded 3-generation branching tube tree
     (~388k triangles), insertion swept to 0.9 x the shortest root-to-leaf path in ~10 mm steps, once in
@@ -348,17 +375,18 @@ def tree_precision_run(af):
     out = {}
     runs = {}
     for mode in (af.PRECISION_FP64, af.PRECISION_MIXED):
-        h = af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS)
+        h = af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS, max_contact_iters=5000)
         h.accfem_set_precision(mode)
-        res, t0 = [], time.perf_counter()
+        res, fb, t0 = [], 0, time.perf_counter()
         for s in range(len(w.insertions)):
             res.append(h.accfem_solve(w.tensions[s], w.insertions[s]))
+            fb += h.accfem_solve_stats()[3]
         dt = time.perf_counter() - t0
         runs[mode] = res
         out["fp64" if mode == af.PRECISION_FP64 else "mixed"] = {
             "solves_per_s": len(res) / dt, "newton_iters_per_solve": float(np.mean([r["newton_iters"] for r in res])),
             "failed_solves": int(sum(r["status"] != af.OK for r in res)),
-            "max_rows": int(max(r["n_contacts"] for r in res))}
+            "max_rows": int(max(r["n_contacts"] for r in res)), "fp64_tangent_fallbacks": int(fb)}
         h.close()
     tip, ferr, same, both = 0.0, 0.0, 0, 0
     for r6, rm in zip(runs[af.PRECISION_FP64], runs[af.PRECISION_MIXED]):
@@ -366,8 +394,7 @@ def tree_precision_run(af):
             continue
         both += 1
         tip = max(tip, float(np.linalg.norm(rm["node_pos"][-1] - r6["node_pos"][-1])))
-        same += sorted((c["node"], tuple(np.round(c["point"], 9))) for c in rm["contacts"]) == \
-            sorted((c["node"], tuple(np.round(c["point"], 9))) for c in r6["contacts"])
+        same += same_rows(rm["contacts"], r6["contacts"])
         f6, fm = {}, {}
         for c in r6["contacts"]:
             f6[c["node"]] = f6.get(c["node"], 0.0) + c["force"] * np.asarray(c["normal"])
@@ -497,7 +524,7 @@ def ours(args, rank, world, local_rank):
             for s in range(last_ok + 1):
                 r = h.accfem_solve(w.tensions[s], w.insertions[s])
         last = r
-        m_last, mc_last, np_last = h.accfem_solve_stats()
+        m_last, mc_last, np_last, _fb = h.accfem_solve_stats()
         nf_last = w.robot.n_elements - int(math.floor((w.robot.length - w.insertions[last_ok]) * w.robot.n_elements
                                                       / w.robot.length + 1e-6))
         el_us = h.accfem_time_kernel(af.KERNEL_ELEMENT, 50)
@@ -523,17 +550,16 @@ def ours(args, rank, world, local_rank):
             mixed_fail += b_
             mixed_iters += it_
         h.accfem_reset()
-        tip_err, force_err, same_sets, both_ok = 0.0, 0.0, 0, 0
+        tip_err, force_err, same_sets, both_ok, fallbacks = 0.0, 0.0, 0, 0, 0
         for s in range(S):
             rm = h.accfem_solve(w.tensions[s], w.insertions[s])
+            fallbacks += h.accfem_solve_stats()[3]
             r6 = fp64_runs[s]
             if rm["status"] != af.OK or r6["status"] != af.OK:
                 continue
             both_ok += 1
             tip_err = max(tip_err, float(np.linalg.norm(rm["node_pos"][-1] - r6["node_pos"][-1])))
-            km = sorted((c["node"], tuple(np.round(c["point"], 9))) for c in rm["contacts"])
-            k6 = sorted((c["node"], tuple(np.round(c["point"], 9))) for c in r6["contacts"])
-            same_sets += km == k6
+            same_sets += same_rows(rm["contacts"], r6["contacts"])
             fm, f6 = {}, {}
             for c in rm["contacts"]:
                 fm[c["node"]] = fm.get(c["node"], 0.0) + c["force"] * np.asarray(c["normal"])
@@ -547,7 +573,7 @@ def ours(args, rank, world, local_rank):
                              "residual, factor, contact Schur complement and contact solve",
                      "solves_per_s": S * args.steps / (mixed_ms / 1000.0),
                      "ms_per_step": mixed_ms / args.steps, "newton_iters_per_solve": mixed_iters / (S * args.steps),
-                     "failed_solves": int(mixed_fail),
+                     "failed_solves": int(mixed_fail), "fp64_tangent_fallbacks": int(fallbacks),
                      "vs_fp64_gpu": {"solves_compared": both_ok, "max_tip_error_m": tip_err,
                                      "max_node_force_rel_error": force_err, "identical_contact_sets": int(same_sets)}}
         progress("precision: %.1f solves/s, tip error %.2e m" % (precision["solves_per_s"], tip_err))

@@ -162,7 +162,10 @@ accfem_status accfem_set_stream(accfem_handle* h, void* stream);
  * Newton residual), the factorisation, the contact Schur complement and the contact solve stay
  * FP64.  Collision always prunes in FP32 and decides in FP64.  The tangent only steers the Newton
  * iteration, whose FP64 residual refines every step, so a converged solve meets the same
- * tolerance in both modes.  A batch takes each member's mode when the batch is created. */
+ * tolerance in both modes.  The assembled tangent's condition number grows like the cube of the
+ * element count, past FP32 precision from a few hundred elements: when the FP32 tangent gives a
+ * non-positive pivot, the solve switches to the FP64 tangent and repeats that iteration
+ * (accfem_solve_stats reports it).  A batch takes each member's mode when the batch is created. */
 #define ACCFEM_PRECISION_FP64 0
 #define ACCFEM_PRECISION_MIXED 1
 accfem_status accfem_set_precision(accfem_handle* h, int32_t mode);
@@ -289,6 +292,16 @@ typedef struct {
 accfem_status accfem_batch_serve(accfem_batch* b, const accfem_request* requests, int32_t n_requests,
                                  int32_t chunk_iters, int64_t hbm_cap_bytes, accfem_response* responses);
 
+/* Autotuning of the work packing.  The batch's phase kernels are persistent; they can run on
+ * their full resident grid or on 1/2, 1/4 or 1/8 of it (more units per block, fewer idle blocks).
+ * After this call the next 4 x trials advances take the four variants in turn, each timed on the
+ * device per Newton iteration, and the fastest is kept; results do not depend on the variant. */
+accfem_status accfem_batch_autotune(accfem_batch* b, int32_t trials);
+
+/* Variant in use (0..3: grids divided by 2^variant; -1 while tuning) and, if ms_per_pass is not NULL,
+ * the measured milliseconds per Newton iteration of each variant (4 values, -1 if not measured). */
+accfem_status accfem_batch_tuning(const accfem_batch* b, int32_t* variant, double* ms_per_pass);
+
 /* Work stream of the batch's calls (a cudaStream_t; NULL = the batch's own stream). */
 accfem_status accfem_batch_set_stream(accfem_batch* b, void* stream);
 
@@ -305,8 +318,10 @@ const char* accfem_batch_last_error(const accfem_batch* b);
 void accfem_batch_destroy(accfem_batch* b);
 
 /* Sizes of the contact problem in the last Newton iteration of the handle's last solve: constraint
- * rows, rows of the working set, active rows (y > 0); any pointer may be NULL. */
-accfem_status accfem_solve_stats(const accfem_handle* h, int32_t* rows, int32_t* working_rows, int32_t* active_rows);
+ * rows, rows of the working set, active rows (y > 0); and 1 in *fp64_fallback when that solve, in
+ * mixed precision, switched to the FP64 tangent.  Any pointer may be NULL. */
+accfem_status accfem_solve_stats(const accfem_handle* h, int32_t* rows, int32_t* working_rows, int32_t* active_rows,
+                                 int32_t* fp64_fallback);
 
 /* Device memory held by the handle, in bytes. */
 accfem_status accfem_device_bytes(const accfem_handle* h, int64_t* bytes);

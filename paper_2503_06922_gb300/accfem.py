@@ -76,7 +76,8 @@ EXPORTS = ["accfem_default_options", "accfem_create", "accfem_solve", "accfem_so
            "accfem_batch_create", "accfem_batch_begin", "accfem_batch_advance", "accfem_batch_poll",
            "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream", "accfem_batch_transfer_bytes",
            "accfem_batch_kernel_launches", "accfem_batch_last_error", "accfem_batch_destroy", "accfem_batch_serve",
-           "accfem_device_bytes", "accfem_solve_stats", "accfem_set_precision"]
+           "accfem_device_bytes", "accfem_solve_stats", "accfem_set_precision", "accfem_batch_autotune",
+           "accfem_batch_tuning"]
 
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 
@@ -136,8 +137,10 @@ def load(path=LIB_PATH):
     lib.accfem_batch_serve.argtypes = [B, ctypes.POINTER(accfem_request), ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int64, ctypes.POINTER(accfem_response)]
     lib.accfem_device_bytes.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
-    lib.accfem_solve_stats.argtypes = [H, _ip, _ip, _ip]
+    lib.accfem_solve_stats.argtypes = [H, _ip, _ip, _ip, _ip]
     lib.accfem_set_precision.argtypes = [H, ctypes.c_int32]
+    lib.accfem_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    lib.accfem_batch_tuning.argtypes = [ctypes.c_void_p, _ip, _dp]
     lib.accfem_batch_destroy.argtypes = [B]
     lib.accfem_batch_destroy.restype = None
     for name in ("accfem_default_options", "accfem_create", "accfem_solve", "accfem_solve_tip_load",
@@ -145,7 +148,8 @@ def load(path=LIB_PATH):
                  "accfem_transfer_bytes", "accfem_time_kernel", "accfem_detect_contacts_noalloc",
                  "accfem_batch_create", "accfem_batch_begin", "accfem_batch_advance", "accfem_batch_poll",
                  "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream",
-                 "accfem_batch_transfer_bytes", "accfem_batch_serve", "accfem_device_bytes", "accfem_solve_stats", "accfem_set_precision"):
+                 "accfem_batch_transfer_bytes", "accfem_batch_serve", "accfem_device_bytes", "accfem_solve_stats", "accfem_set_precision",
+                 "accfem_batch_autotune", "accfem_batch_tuning"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -298,10 +302,10 @@ class AccFem:
         return int(self._lib.accfem_set_precision(self.h, int(mode)))
 
     def accfem_solve_stats(self):
-        """(constraint rows, working-set rows, active rows) of the last Newton iteration."""
-        a, b, c = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
-        self._lib.accfem_solve_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
-        return int(a.value), int(b.value), int(c.value)
+        """(constraint rows, working-set rows, active rows, FP64-tangent fallback) of the last solve."""
+        a, b, c, f = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        self._lib.accfem_solve_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(f))
+        return int(a.value), int(b.value), int(c.value), int(f.value)
 
     def accfem_device_bytes(self):
         v = ctypes.c_int64(0)
@@ -415,6 +419,16 @@ class AccFemBatch:
                "n_contacts": resp["n_contacts"].copy()}
         out["latency"] = out["t_end"] - np.asarray(arrivals, dtype=np.float64)
         return out
+
+    def accfem_batch_autotune(self, trials):
+        return int(self._lib.accfem_batch_autotune(self.b, int(trials)))
+
+    def accfem_batch_tuning(self):
+        """(variant in use or -1 while tuning, ms per Newton iteration of each of the 4 variants)."""
+        v = ctypes.c_int32(0)
+        ms = np.zeros(4)
+        self._lib.accfem_batch_tuning(self.b, ctypes.byref(v), _ptr(ms))
+        return int(v.value), ms
 
     def accfem_batch_set_stream(self, stream_ptr):
         return int(self._lib.accfem_batch_set_stream(self.b, ctypes.c_void_p(int(stream_ptr)) if stream_ptr else None))

@@ -714,13 +714,15 @@ accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t
   return ACCFEM_OK;
 }
 
-accfem_status accfem_solve_stats(const accfem_handle* h, int32_t* rows, int32_t* working_rows, int32_t* active_rows) {
+accfem_status accfem_solve_stats(const accfem_handle* h, int32_t* rows, int32_t* working_rows, int32_t* active_rows,
+                                 int32_t* fp64_fallback) {
   if (!h) return ACCFEM_E_INVALID_ARG;
   const Ctl& c = *h->h_ctl;
   const bool it = c.nf > 0 && c.iter > 0;
   if (rows) *rows = it ? c.m : 0;
   if (working_rows) *working_rows = it ? c.mc : 0;
   if (active_rows) *active_rows = it ? c.n_active : 0;
+  if (fp64_fallback) *fp64_fallback = c.fp64_tangent;
   return ACCFEM_OK;
 }
 

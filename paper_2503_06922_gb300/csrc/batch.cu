@@ -101,43 +101,56 @@ int enqueue_batch_iteration(accfem_batch* b, cudaStream_t st, cudaGraphCondition
   return n;
 }
 
-bool build_graph(accfem_batch* b) {
+// Persistent grids of the phase kernels at the full resident size (units: the largest number of
+// units the members can produce).
+void full_grids(accfem_batch* b, int* grid) {
   long long units[kPhases] = {};
   for (accfem_handle* h : b->members)
     for (int ph = 0; ph < kPhases; ++ph) units[ph] += (long long)phase_gx(ph, h->p.M) * phase_gy(ph);
-  b->grid[PH_ELEM] = persistent_grid(element_batch, 32 * kWarpsPerElemBlock, units[PH_ELEM]);
-  b->grid[PH_COLL] = persistent_grid(collide_batch, 128, units[PH_COLL]);
-  b->grid[PH_COMPACT] = persistent_grid(compact_batch, 1024, units[PH_COMPACT]);
-  b->grid[PH_ASM] = persistent_grid(assemble_rhs_batch, 192, units[PH_ASM]);
-  b->grid[PH_ELIM1] = persistent_grid(bcr_elim_batch, 64, units[PH_ELIM1]);
-  b->grid[PH_CONTACT] = persistent_grid(contact_batch, 256, units[PH_CONTACT]);
-  b->grid[PH_STEP] = persistent_grid(step_batch, 192, units[PH_STEP]);
-  b->grid[PH_APPLY] = persistent_grid(apply_batch, 128, units[PH_APPLY]);
+  for (int ph = 0; ph < kPhases; ++ph) grid[ph] = 1;
+  grid[PH_ELEM] = persistent_grid(element_batch, 32 * kWarpsPerElemBlock, units[PH_ELEM]);
+  grid[PH_COLL] = persistent_grid(collide_batch, 128, units[PH_COLL]);
+  grid[PH_COMPACT] = persistent_grid(compact_batch, 1024, units[PH_COMPACT]);
+  grid[PH_ASM] = persistent_grid(assemble_rhs_batch, 192, units[PH_ASM]);
+  grid[PH_ELIM1] = persistent_grid(bcr_elim_batch, 64, units[PH_ELIM1]);
+  grid[PH_CONTACT] = persistent_grid(contact_batch, 256, units[PH_CONTACT]);
+  grid[PH_STEP] = persistent_grid(step_batch, 192, units[PH_STEP]);
+  grid[PH_APPLY] = persistent_grid(apply_batch, 128, units[PH_APPLY]);
   for (int j = 0; j < b->levels; ++j) {
-    b->grid[PH_LEV0 + j] = persistent_grid(bcr_level_batch, 192, units[PH_LEV0 + j]);
-    b->grid[PH_BWD0 + j] = persistent_grid(bcr_bwd_batch, 192, units[PH_BWD0 + j]);
+    grid[PH_LEV0 + j] = persistent_grid(bcr_level_batch, 192, units[PH_LEV0 + j]);
+    grid[PH_BWD0 + j] = persistent_grid(bcr_bwd_batch, 192, units[PH_BWD0 + j]);
   }
+}
+
+// Graph of variant v: every persistent grid divided by 2^v (at least one block).
+bool build_graph(accfem_batch* b, int v) {
+  accfem_batch::Variant& g = b->variants[v];
+  if (g.exec) return true;
+  int full[kPhases];
+  full_grids(b, full);
+  for (int ph = 0; ph < kPhases; ++ph) b->grid[ph] = std::max(1, full[ph] >> v);
   cudaGraphConditionalHandle cond;
   cudaGraphNodeParams cp = {};
   cudaGraphNode_t node;
-  if (!bok(b, cudaGraphCreate(&b->graph, 0), "cudaGraphCreate") ||
-      !bok(b, cudaGraphConditionalHandleCreate(&cond, b->graph, 1, cudaGraphCondAssignDefault), "conditional handle"))
+  if (!bok(b, cudaGraphCreate(&g.graph, 0), "cudaGraphCreate") ||
+      !bok(b, cudaGraphConditionalHandleCreate(&cond, g.graph, 1, cudaGraphCondAssignDefault), "conditional handle"))
     return false;
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = cond;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
-  if (!bok(b, cudaGraphAddNode(&node, b->graph, nullptr, nullptr, 0, &cp), "conditional node")) return false;
+  if (!bok(b, cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &cp), "conditional node")) return false;
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   cudaStream_t st = b->stream;
   if (!bok(b, cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed), "begin capture"))
     return false;
   b->body_kernels = enqueue_batch_iteration(b, st, cond, 1);
   cudaError_t ce = cudaStreamEndCapture(st, &body);
-  if (!bok(b, ce, "end capture") || !bok(b, cudaGraphInstantiate(&b->exec, b->graph, 0), "instantiate graph")) {
+  if (!bok(b, ce, "end capture") || !bok(b, cudaGraphInstantiate(&g.exec, g.graph, 0), "instantiate graph")) {
     cudaGetLastError();
     return false;
   }
+  for (int ph = 0; ph < kPhases; ++ph) g.grid[ph] = b->grid[ph];
   return true;
 }
 
@@ -171,8 +184,12 @@ extern "C" {
 void accfem_batch_destroy(accfem_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto& g : b->variants) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+  }
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
   for (void* p : {(void*)b->d_tab, (void*)b->d_plan, (void*)b->d_ctl, (void*)b->d_stage, (void*)b->d_begin,
                   (void*)b->d_members, (void*)b->d_off, (void*)b->d_pack, (void*)b->d_tips})
     if (p) cudaFree(p);
@@ -228,7 +245,8 @@ accfem_status accfem_batch_create(accfem_handle* const* members, int32_t n_membe
     tab[i].d.ctl = b->d_ctl + i;
   }
   if (!bok(b, cudaMemcpy(b->d_tab, tab.data(), sizeof(Inst) * b->n, cudaMemcpyHostToDevice), "upload batch table") ||
-      !build_graph(b)) {
+      !bok(b, cudaEventCreate(&b->ev0), "event") || !bok(b, cudaEventCreate(&b->ev1), "event") ||
+      !build_graph(b, 0)) {
     accfem_batch_destroy(b);
     return ACCFEM_E_CUDA;
   }
@@ -296,11 +314,19 @@ accfem_status accfem_batch_advance(accfem_batch* b, int32_t max_iters, int32_t* 
     b->n_begin = 0;
   }
   int flying = 0;
+  int tuned_variant = -1;
   for (int i = 0; i < b->n; ++i) flying += b->state[i] == 2;
   if (flying > 0) {
     batch_plan_kernel<<<1, 1024, 0, st>>>(b->d_tab, b->d_plan, b->n, 0, max_iters, cudaGraphConditionalHandle(), 0);
     ++b->launches;
     if (!bok(b, cudaGetLastError(), "kernel launch")) return ACCFEM_E_CUDA;
+    int v = b->variant;
+    if (b->tune_left > 0) {                 // autotuning: the variants take turns, one advance each
+      v = b->tune_next;
+      b->tune_next = (b->tune_next + 1) % accfem_batch::kVariants;
+      if (!build_graph(b, v)) return ACCFEM_E_CUDA;
+    }
+    for (int ph = 0; ph < kPhases; ++ph) b->grid[ph] = b->variants[v].grid[ph];
     if (b->stream_mode) {
       // host-driven passes (kernels visible to profilers): stop when nothing iterates
       for (int pass = 0; pass < max_iters; ++pass) {
@@ -311,8 +337,13 @@ accfem_status accfem_batch_advance(accfem_batch* b, int32_t max_iters, int32_t* 
           return ACCFEM_E_CUDA;
         if (b->h_passes[1] == 0) break;
       }
-    } else if (!bok(b, cudaGraphLaunch(b->exec, st), "launch batch graph")) {
-      return ACCFEM_E_CUDA;
+    } else {
+      const bool timed = b->tune_left > 0;
+      if ((timed && !bok(b, cudaEventRecord(b->ev0, st), "event")) ||
+          !bok(b, cudaGraphLaunch(b->variants[v].exec, st), "launch batch graph") ||
+          (timed && !bok(b, cudaEventRecord(b->ev1, st), "event")))
+        return ACCFEM_E_CUDA;
+      tuned_variant = timed ? v : -1;
     }
   }
   if (!bok(b, cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(Ctl) * b->n, cudaMemcpyDeviceToHost, st), "read control") ||
@@ -321,6 +352,20 @@ accfem_status accfem_batch_advance(accfem_batch* b, int32_t max_iters, int32_t* 
     return ACCFEM_E_CUDA;
   b->d2h += sizeof(Ctl) * b->n + sizeof(int);
   if (flying > 0 && !b->stream_mode) b->launches += (int64_t)b->body_kernels * std::max(*b->h_passes, 1);
+  if (tuned_variant >= 0) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+    b->tune_ms[tuned_variant] += ms;
+    b->tune_passes[tuned_variant] += std::max(*b->h_passes, 1);
+    if (--b->tune_left == 0) {               // keep the variant with the least time per pass
+      int best = 0;
+      for (int k = 1; k < accfem_batch::kVariants; ++k)
+        if (b->tune_passes[k] > 0 &&
+            b->tune_ms[k] / b->tune_passes[k] < b->tune_ms[best] / std::max<int64_t>(b->tune_passes[best], 1))
+          best = k;
+      b->variant = best;
+    }
+  }
   int left = 0;
   for (int i = 0; i < b->n; ++i) {
     if (b->state[i] != 2) {
@@ -464,6 +509,23 @@ accfem_status accfem_batch_solve(accfem_batch* b, const double* cable_tensions, 
     }
   }
   return first;
+}
+
+accfem_status accfem_batch_autotune(accfem_batch* b, int32_t trials) {
+  if (!b || trials < 1 || trials > 1000) return bfail(b, ACCFEM_E_INVALID_ARG, "trials must be in 1..1000");
+  for (int k = 0; k < accfem_batch::kVariants; ++k) { b->tune_ms[k] = 0.0; b->tune_passes[k] = 0; }
+  b->tune_left = trials * accfem_batch::kVariants;
+  b->tune_next = 0;
+  return ACCFEM_OK;
+}
+
+accfem_status accfem_batch_tuning(const accfem_batch* b, int32_t* variant, double* ms_per_pass) {
+  if (!b || !variant) return ACCFEM_E_INVALID_ARG;
+  *variant = b->tune_left > 0 ? -1 : b->variant;
+  if (ms_per_pass)
+    for (int k = 0; k < accfem_batch::kVariants; ++k)
+      ms_per_pass[k] = b->tune_passes[k] > 0 ? b->tune_ms[k] / b->tune_passes[k] : -1.0;
+  return ACCFEM_OK;
 }
 
 accfem_status accfem_batch_transfer_bytes(const accfem_batch* b, int64_t* h2d, int64_t* d2h) {

@@ -34,8 +34,20 @@ struct accfem_batch {
   int n_begin = 0;
   std::vector<int> state;           // 0 idle, 1 staged, 2 in flight
   std::vector<int> solved;          // member finished at least one solve in this batch
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  // graph variants: persistent grids at 1, 1/2, 1/4, 1/8 of the resident size (built on first use)
+  static constexpr int kVariants = 4;
+  struct Variant {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int grid[accfem::kPhases] = {};
+  };
+  Variant variants[kVariants];
+  int variant = 0;                  // variant in use
+  int tune_left = 0;                // advances left in the autotuning round
+  int tune_next = 0;
+  double tune_ms[kVariants] = {};
+  int64_t tune_passes[kVariants] = {};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int body_kernels = 0;
   bool stream_mode = false;         // ACCFEM_LAUNCH=stream: host-driven passes (kernels visible to profilers)
   int grid[accfem::kPhases] = {};

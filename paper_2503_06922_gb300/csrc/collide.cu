@@ -28,8 +28,8 @@ namespace accfem {
 __device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int bx) {
   __shared__ int s_list[4][kSurvCap];                 // sorted slots kept for the FP64 test
   __shared__ Surv s_surv[4][kSurvCap];
-  __shared__ int s_cand[4][kCandCap];                 // slots whose bounding sphere reaches thr
-  __shared__ float s_cd[4][kCandCap];                 // their FP32 distances (negative: near-inside flag)
+  __shared__ int s_cand[4][kCandCap];                 // candidate slots (FP32 distance within thr + eps_d)
+  __shared__ float s_cd[4][kCandCap];                 // their FP32 distances (negative: near-the-face flag)
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   Ctl* ctl = d.ctl;
@@ -48,82 +48,90 @@ __device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int 
   }
   const int ncell = nc3[0] * nc3[1] * nc3[2];
   const float thr32 = (float)(thr + p.eps_d);
-  // ---- one sweep: cell ranges loaded by the lanes, triangles by the lanes, candidates compacted
-  int nca = 0;
-  for (int c0 = 0; c0 < ncell; c0 += 32) {
-    int cs0 = 0, cs1 = 0, cx = 0, cy = 0, cz = 0;
-    if (c0 + lane < ncell) {
-      int q = c0 + lane;
-      cx = lo[0] + q % nc3[0];
-      cy = lo[1] + (q / nc3[0]) % nc3[1];
-      cz = lo[2] + q / (nc3[0] * nc3[1]);
-      int cell = (cz * p.g_dim[1] + cy) * p.g_dim[0] + cx;
-      cs0 = d.cell_start[cell];
-      cs1 = d.cell_start[cell + 1];
-    }
-    unsigned nonempty = __ballot_sync(0xffffffffu, cs1 > cs0);
-    while (nonempty) {
-      const int src = __ffs(nonempty) - 1;
-      nonempty &= nonempty - 1;
-      const int s0 = __shfl_sync(0xffffffffu, cs0, src), s1 = __shfl_sync(0xffffffffu, cs1, src);
-      const int gx = __shfl_sync(0xffffffffu, cx, src), gy = __shfl_sync(0xffffffffu, cy, src),
-                gz = __shfl_sync(0xffffffffu, cz, src);
-      const float pc[3] = {(float)(pn[0] - (p.g_org[0] + (gx + 0.5) * p.g_h)),
-                           (float)(pn[1] - (p.g_org[1] + (gy + 0.5) * p.g_h)),
-                           (float)(pn[2] - (p.g_org[2] + (gz + 0.5) * p.g_h))};
-      for (int s0l = s0; s0l < s1; s0l += 32) {
-        const int s = s0l + lane;
-        bool keep = false;
-        float code = 0.f;
-        if (s < s1) {
-          float4 sp = reinterpret_cast<const float4*>(d.sph32)[s];
-          float dx = pc[0] - sp.x, dy = pc[1] - sp.y, dz = pc[2] - sp.z, rr = thr32 + sp.w;
-          if (dx * dx + dy * dy + dz * dz <= rr * rr) {
-            float va, vb, vc;
-            float dd = sqrtf(tri_dist2_f32(pc, d.tri32 + (size_t)s * 9, va, vb, vc));
-            float tol = -((float)kFaceBand + p.eps_b) * (va + vb + vc);
-            bool near_in = (va >= tol) && (vb >= tol) && (vc >= tol);
-            keep = dd <= thr32;
-            code = near_in ? -1.f - dd : dd;             // sign carries the near-the-face flag
+  // Walk of the cells around the node: cell ranges loaded by the lanes, triangles by the lanes; for
+  // every 32 slots visit(slot, within, dd, near) is called by the whole warp (within: FP32 distance
+  // dd <= r_o + gap + eps_d; near: FP32 barycentrics inside the face band up to eps_b).
+  auto walk = [&](auto&& visit) {
+    for (int c0 = 0; c0 < ncell; c0 += 32) {
+      int cs0 = 0, cs1 = 0, cx = 0, cy = 0, cz = 0;
+      if (c0 + lane < ncell) {
+        int q = c0 + lane;
+        cx = lo[0] + q % nc3[0];
+        cy = lo[1] + (q / nc3[0]) % nc3[1];
+        cz = lo[2] + q / (nc3[0] * nc3[1]);
+        int cell = (cz * p.g_dim[1] + cy) * p.g_dim[0] + cx;
+        cs0 = d.cell_start[cell];
+        cs1 = d.cell_start[cell + 1];
+      }
+      unsigned nonempty = __ballot_sync(0xffffffffu, cs1 > cs0);
+      while (nonempty) {
+        const int src = __ffs(nonempty) - 1;
+        nonempty &= nonempty - 1;
+        const int s0 = __shfl_sync(0xffffffffu, cs0, src), s1 = __shfl_sync(0xffffffffu, cs1, src);
+        const int gx = __shfl_sync(0xffffffffu, cx, src), gy = __shfl_sync(0xffffffffu, cy, src),
+                  gz = __shfl_sync(0xffffffffu, cz, src);
+        const float pc[3] = {(float)(pn[0] - (p.g_org[0] + (gx + 0.5) * p.g_h)),
+                             (float)(pn[1] - (p.g_org[1] + (gy + 0.5) * p.g_h)),
+                             (float)(pn[2] - (p.g_org[2] + (gz + 0.5) * p.g_h))};
+        for (int s0l = s0; s0l < s1; s0l += 32) {
+          const int s = s0l + lane;
+          bool within = false, near_in = false;
+          float dd = 0.f;
+          if (s < s1) {
+            float4 sp = reinterpret_cast<const float4*>(d.sph32)[s];
+            float dx = pc[0] - sp.x, dy = pc[1] - sp.y, dz = pc[2] - sp.z, rr = thr32 + sp.w;
+            if (dx * dx + dy * dy + dz * dz <= rr * rr) {
+              float va, vb, vc;
+              dd = sqrtf(tri_dist2_f32(pc, d.tri32 + (size_t)s * 9, va, vb, vc));
+              float tol = -((float)kFaceBand + p.eps_b) * (va + vb + vc);
+              near_in = (va >= tol) && (vb >= tol) && (vc >= tol);
+              within = dd <= thr32;
+            }
           }
+          visit(s, within, dd, near_in);
         }
-        unsigned mk = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-          int pos = nca + __popc(mk & lt_mask);
-          if (pos < kCandCap) { s_cand[wib][pos] = s; s_cd[wib][pos] = code; }
-        }
-        nca += __popc(mk);
       }
     }
-  }
-  __syncwarp();
-  if (nca > kCandCap) {
-    if (lane == 0) flag_capacity(ctl, CAP_CANDIDATES);
-    return;
-  }
-  // ---- FP32 minimum and the exact-test filter
+  };
+  // ---- pass 1: FP32 candidates (kept in shared memory up to kCandCap) and their minimum distance
+  int nca = 0;
   float dmin = 3.0e38f;
-  for (int i = lane; i < nca; i += 32) {
-    float c = s_cd[wib][i];
-    dmin = fminf(dmin, c < 0.f ? -1.f - c : c);
-  }
+  walk([&](int s, bool within, float dd, bool near_in) {
+    unsigned mk = __ballot_sync(0xffffffffu, within);
+    if (within) {
+      dmin = fminf(dmin, dd);
+      int pos = nca + __popc(mk & lt_mask);
+      if (pos < kCandCap) { s_cand[wib][pos] = s; s_cd[wib][pos] = near_in ? -1.f - dd : dd; }
+    }
+    nca += __popc(mk);
+  });
+  __syncwarp();
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
   const float dmin_keep = dmin + (float)(2.0 * p.eps_d);
+  // ---- survivors for the exact test: near the face, or within 2 eps_d of the minimum
   int ns = 0;
-  for (int i0 = 0; i0 < nca; i0 += 32) {
-    const int i = i0 + lane;
-    bool keep = false;
-    if (i < nca) {
-      float c = s_cd[wib][i];
-      keep = c < 0.f || c <= dmin_keep;
-    }
+  auto survive = [&](bool keep, int slot) {
     unsigned mk = __ballot_sync(0xffffffffu, keep);
     if (keep) {
       int pos = ns + __popc(mk & lt_mask);
-      if (pos < kSurvCap) s_list[wib][pos] = s_cand[wib][i];
+      if (pos < kSurvCap) s_list[wib][pos] = slot;
     }
     ns += __popc(mk);
+  };
+  if (nca <= kCandCap) {
+    for (int i0 = 0; i0 < nca; i0 += 32) {
+      const int i = i0 + lane;
+      bool keep = false;
+      if (i < nca) {
+        float c = s_cd[wib][i];
+        keep = c < 0.f || c <= dmin_keep;
+      }
+      survive(keep, i < nca ? s_cand[wib][i] : 0);
+    }
+  } else {
+    // more candidates than fit: walk the cells again and filter on the fly
+    walk([&](int s, bool within, float dd, bool near_in) { survive(within && (near_in || dd <= dmin_keep), s); });
   }
   __syncwarp();
   if (ns > kSurvCap) {

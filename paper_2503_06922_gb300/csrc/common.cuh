@@ -6,9 +6,9 @@
 namespace accfem {
 
 constexpr int kMaxCables = 8;
-constexpr int kCpn = 8;            // constraint rows per node (locally closest wall features)
+constexpr int kCpn = 16;           // constraint rows per node (wall features the node lies over)
 constexpr int kSurvCap = 64;       // FP64 candidates per node after the FP32 prefilter
-constexpr int kCandCap = 768;      // triangles per node within the activation distance (FP32)
+constexpr int kCandCap = 256;      // candidates per node kept in shared memory (more: a second cell walk)
 constexpr int kElemStride = 96;    // doubles per element record: 78 K (upper) + 12 F + pad
 constexpr int kWarpsPerElemBlock = 2;
 constexpr int kRhsSplit = 4;       // blocks per node that share the RHS columns (chunks of 32)
@@ -76,7 +76,7 @@ struct Ctl {
   int cap_code;          // CAP_* cause of an ST_CAPACITY status
   int mc;                // rows of the working set (RHS columns 1..mc)
   int incomplete;        // a row outside the working set is violated by this iteration's step
-  int pad3;
+  int fp64_tangent;      // mixed precision: this solve fell back to the FP64 element tangent
   double delta;          // insertion of the resident state
   double tension[kMaxCables];
   double tip_f[3], tip_m[3];

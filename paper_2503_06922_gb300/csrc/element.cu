@@ -250,14 +250,19 @@ __device__ __forceinline__ void element_body(const Params& p, const Dev& d, int 
   }
 }
 
+// The FP32 tangent unless the handle computes in FP64 or this solve fell back to FP64.
+__device__ __forceinline__ bool mixed_tangent(const Params& p, const Dev& d) {
+  return p.precision == kPrecisionMixed && !d.ctl->fp64_tangent;
+}
+
 __global__ void __launch_bounds__(32 * kWarpsPerElemBlock) element_kernel(Params p, Dev d) {
-  if (p.precision == kPrecisionMixed) element_body<true>(p, d, blockIdx.x);
+  if (mixed_tangent(p, d)) element_body<true>(p, d, blockIdx.x);
   else element_body<false>(p, d, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(32 * kWarpsPerElemBlock) element_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
   for_units(tab, plan, PH_ELEM, [](const Inst& in, int bx, int) {
-    if (in.p.precision == kPrecisionMixed) element_body<true>(in.p, in.d, bx);
+    if (mixed_tangent(in.p, in.d)) element_body<true>(in.p, in.d, bx);
     else element_body<false>(in.p, in.d, bx);
   });
 }

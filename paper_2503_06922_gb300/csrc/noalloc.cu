@@ -13,13 +13,14 @@
 namespace accfem {
 
 constexpr int kNoAllocMaxNodes = 4096;
+constexpr int kNoAllocCpn = 8;        // rows per node in the fixed array (more: capacity status)
 
 struct NoAllocScratch {
   int ncon[kNoAllocMaxNodes];
-  int tri[kNoAllocMaxNodes * kCpn];
-  double pt[kNoAllocMaxNodes * kCpn * 3];
-  double nrm[kNoAllocMaxNodes * kCpn * 3];
-  double gap[kNoAllocMaxNodes * kCpn];
+  int tri[kNoAllocMaxNodes * kNoAllocCpn];
+  double pt[kNoAllocMaxNodes * kNoAllocCpn * 3];
+  double nrm[kNoAllocMaxNodes * kNoAllocCpn * 3];
+  double gap[kNoAllocMaxNodes * kNoAllocCpn];
   int status;     // 0, or ST_CAPACITY when a node has too many candidates or rows
   int n_rows;     // rows of the last call
 };
@@ -120,10 +121,10 @@ __global__ void __launch_bounds__(128) detect_noalloc_kernel(Params p, Dev d, co
     ord[j] = i;
   }
   int nc = 0;
-  int* ctri = sc->tri + (size_t)f * kCpn;
-  double* cpt = sc->pt + (size_t)f * kCpn * 3;
-  double* cn = sc->nrm + (size_t)f * kCpn * 3;
-  double* cg = sc->gap + (size_t)f * kCpn;
+  int* ctri = sc->tri + (size_t)f * kNoAllocCpn;
+  double* cpt = sc->pt + (size_t)f * kNoAllocCpn * 3;
+  double* cn = sc->nrm + (size_t)f * kNoAllocCpn * 3;
+  double* cg = sc->gap + (size_t)f * kNoAllocCpn;
   for (int oi = 0; oi < ns; ++oi) {
     const Surv& sv = s_surv[wib][ord[oi]];
     double dist = sqrt(sv.d2);
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(128) detect_noalloc_kernel(Params p, Dev d, co
       if (sqrt(dx * dx + dy * dy + dz * dz) <= 1e-12) { dup = true; break; }
     }
     if (dup) continue;
-    if (nc >= kCpn) { atomicCAS(&sc->status, 0, ST_CAPACITY); break; }
+    if (nc >= kNoAllocCpn) { atomicCAS(&sc->status, 0, ST_CAPACITY); break; }
     const double* nf = d.nface + 3 * (size_t)sv.t;
     double nv[3];
     double cmp[3] = {sv.c[0] - pn[0], sv.c[1] - pn[1], sv.c[2] - pn[2]};

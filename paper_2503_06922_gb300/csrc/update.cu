@@ -140,6 +140,13 @@ __global__ void __launch_bounds__(128) apply_batch(const Inst* __restrict__ tab,
 // iterations; a separate count of loop passes bounds the loop whatever the other kernels did.
 __device__ __forceinline__ void ctl_update(const Params& p, const Dev& d) {
   Ctl* c = d.ctl;
+  // mixed precision: a non-positive pivot of the FP32 tangent (its condition number grows like the
+  // cube of the element count) switches this solve to the FP64 tangent; the failed iteration
+  // applied no step and is repeated
+  if (c->status == ST_NOT_SPD && p.precision == kPrecisionMixed && !c->fp64_tangent) {
+    c->status = 0;
+    c->fp64_tangent = 1;
+  }
   if (c->status == 0 && !c->converged) {
     double rho, alpha;
     limiter(p, d, c, &rho, &alpha);

@@ -80,6 +80,32 @@ def test_batch_sweep_equals_solves_alone(af):
         h.close()
 
 
+def test_autotuned_packing_keeps_results(af):
+    """Autotuning takes the four grid variants in turn; every member still equals its solve alone."""
+    ws = _mixed_workloads()
+    alone = _alone(af, ws)
+    hs = [af.AccFem(w.robot, w.lumen) for w in ws]
+    b = af.AccFemBatch(hs)
+    assert b.accfem_batch_autotune(0) == af.E_INVALID_ARG
+    assert b.accfem_batch_autotune(1) == af.OK
+    assert b.accfem_batch_tuning()[0] == -1
+    for s in range(8):
+        for i, w in enumerate(ws):
+            assert b.accfem_batch_begin(i, w.tensions[s], w.insertions[s]) == af.OK
+        left = 1
+        while left:
+            st, left = b.accfem_batch_advance(3)
+            assert st == af.OK
+        res = b.accfem_batch_results(list(range(len(ws))))
+        for i in range(len(ws)):
+            _same(res[i], alone[i][s], "member %d step %d" % (i, s))
+    v, ms = b.accfem_batch_tuning()
+    assert 0 <= v < 4 and np.all(ms > 0.0)
+    b.close()
+    for h in hs:
+        h.close()
+
+
 def test_continuous_admission_equals_alone(af):
     """Members start at different iterations of the others (continuous batching): each member
     begins its next step as soon as its previous one finished, advancing a few iterations at a
