@@ -188,12 +188,12 @@ __global__ void __launch_bounds__(1024) rows_noalloc_kernel(int n, int cap, NoAl
     for (int r = 0; r < sc->ncon[f]; ++r, ++row) {
       if (row >= cap) continue;
       row_node[row] = f;
-      row_tri[row] = sc->tri[f * kCpn + r];
+      row_tri[row] = sc->tri[f * kNoAllocCpn + r];
       for (int c = 0; c < 3; ++c) {
-        row_point[3 * row + c] = sc->pt[(f * kCpn + r) * 3 + c];
-        row_normal[3 * row + c] = sc->nrm[(f * kCpn + r) * 3 + c];
+        row_point[3 * row + c] = sc->pt[(f * kNoAllocCpn + r) * 3 + c];
+        row_normal[3 * row + c] = sc->nrm[(f * kNoAllocCpn + r) * 3 + c];
       }
-      row_gap[row] = sc->gap[f * kCpn + r];
+      row_gap[row] = sc->gap[f * kNoAllocCpn + r];
     }
   if (tid == 0) {
     sc->n_rows = s_warp[31];
