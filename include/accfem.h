@@ -77,10 +77,10 @@ typedef struct {
  * LCP pivoting), max_newton_iters 200, max_contact_iters 1000, max_contacts 256 (constraint
  * rows, at most 8192), tangent_mode 0 (material tangent K = B^T K_l B; the only mode on the GPU).
  * The contact solve of a Newton iteration runs over a working set of at most min(max_contacts, 512)
- * rows: the rows active, in the working set or violated in the previous iteration of the solve and
- * the rows whose gap is at most step_limit / 2; every other row is checked against the step (a
- * violated row joins the working set and the iteration cannot converge), so a converged solve
- * solves the contact problem of all rows. */
+ * rows: the rows active or violated in the previous iteration and the rows whose gap is at most
+ * step_limit / 5; every other row is checked against the applied step (a violated row joins the
+ * working set and the iteration cannot converge), so a converged solve solves the contact problem
+ * of all rows. */
 typedef struct {
   double activation_gap, step_limit, newton_tol, contact_tol;
   int32_t max_newton_iters, max_contact_iters, max_contacts, tangent_mode;

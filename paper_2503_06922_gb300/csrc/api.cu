@@ -196,7 +196,7 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
   p.m_cap = opt.max_contacts;
   p.ws_cap = std::min(opt.max_contacts, kMaxWorking);
   p.nrhs_cap = p.ws_cap + 1;
-  p.ws_gap = 0.5 * opt.step_limit;
+  p.ws_gap = 0.2 * opt.step_limit;
   p.eps_d = 1e-6;
   p.eps_b = 1e-3f;
   p.max_newton = opt.max_newton_iters;

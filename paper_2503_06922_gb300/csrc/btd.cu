@@ -53,8 +53,8 @@ __device__ __forceinline__ int block_excl_scan_1024(int v, int* s_warp, int* tot
 
 // One CTA: exclusive scan of the per-node row counts, row arrays in (node, triangle) order,
 // comparison with the previous iteration's rows (flags carried by identity), the working set of
-// the contact solve, copy to "previous".  Working set: rows that were in it, active or violated in
-// the previous iteration of this solve (so it only grows), and rows whose gap is at most ws_gap;
+// the contact solve, copy to "previous".  Working set: rows active in the previous iteration, rows
+// violated by an applied step in this solve (they stay), and rows whose gap is at most ws_gap;
 // slots follow the row order.
 __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   __shared__ int s_warp[32];
@@ -113,10 +113,14 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   // working set: contiguous row chunks per thread, slots in row order
   const int rper = (m + 1023) / 1024;
   const int r0 = min(tid * rper, m), r1 = min(r0 + rper, m);
+  const int keep_mask = RF_ACTIVE | RF_VIOLATED | RF_STICKY;
+  // no applied step of this iteration moves a node farther than the limiter's bound, at most
+  // min(1.5 rho, beta0): rows with a larger gap cannot be violated by it
+  const double ws_gap = fmin(p.ws_gap, fmin(1.5 * ctl->rho, p.beta0));
   int nw = 0;
   for (int r = r0; r < r1; ++r) {
     const int fl = d.init_flag[r];
-    nw += ((fl > 0) || d.c_gap[r] <= p.ws_gap) ? 1 : 0;
+    nw += ((fl > 0 && (fl & keep_mask)) || d.c_gap[r] <= ws_gap) ? 1 : 0;
   }
   int mc = 0;
   int slot = block_excl_scan_1024(nw, s_warp, &mc);
@@ -126,7 +130,7 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   }
   for (int r = r0; r < r1; ++r) {
     const int fl = d.init_flag[r];
-    if ((fl > 0) || d.c_gap[r] <= p.ws_gap) {
+    if ((fl > 0 && (fl & keep_mask)) || d.c_gap[r] <= ws_gap) {
       d.wrow[slot] = r;
       d.rslot[r] = slot++;
     } else {
@@ -135,9 +139,10 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   }
   __syncthreads();
   for (int r = tid; r < m; r += 1024) {
+    const int fl = d.init_flag[r];
     d.p_node[r] = d.c_node[r];
     d.p_tri[r] = d.c_tri[r];
-    d.p_flag[r] = d.rslot[r] >= 0 ? RF_WORKING : 0;
+    d.p_flag[r] = d.rslot[r] >= 0 ? (RF_WORKING | ((fl > 0 && (fl & (RF_VIOLATED | RF_STICKY))) ? RF_STICKY : 0)) : 0;
   }
   if (tid == 0) { ctl->same_set = s_same; ctl->m = m; ctl->m_prev = m; ctl->mc = mc; }
 }

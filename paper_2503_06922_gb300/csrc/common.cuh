@@ -26,8 +26,10 @@ enum : int { ST_OK = 0, ST_INVALID = 1, ST_NOMEM = 2, ST_CUDA = 3, ST_NOT_CONVER
 enum : int { CAP_ROWS = 1, CAP_CANDIDATES = 2, CAP_SURVIVORS = 3, CAP_NODE_ROWS = 4, CAP_LCP_ROWS = 5,
              CAP_WORKING = 6 };
 
-// Flags of a constraint row, carried from one Newton iteration to the next by (node, triangle).
-enum : int { RF_ACTIVE = 1, RF_WORKING = 2, RF_VIOLATED = 4 };
+// Flags of a constraint row, carried from one Newton iteration to the next by (node, triangle):
+// active (y > 0), in the working set, violated by the last applied step, violated at some
+// iteration of this solve (such a row stays in the working set).
+enum : int { RF_ACTIVE = 1, RF_WORKING = 2, RF_VIOLATED = 4, RF_STICKY = 8 };
 
 // Constants of one handle, passed by value to every kernel.
 struct Params {

@@ -289,7 +289,7 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
     const bool a = S.inP[i] && S.y[i] > 0.0;
     const int row = d.wrow[i];
     d.y[row] = a ? S.y[i] : 0.0;
-    d.p_flag[row] = RF_WORKING | (a ? RF_ACTIVE : 0);
+    d.p_flag[row] = (d.p_flag[row] & RF_STICKY) | RF_WORKING | (a ? RF_ACTIVE : 0);
   }
   __syncthreads();
   if (tid == 0) {

@@ -5,9 +5,7 @@
 namespace accfem {
 
 // dx = dx_free - X y over the active working-set slots; per-node maxima of |du|,
-// max(|du|, r_o |dtheta|) and of the residual g + A^T y; every row outside the working set is
-// checked against the step: w = b - n . du < -tol marks it violated (it joins the working set in
-// the next iteration, and this iteration cannot converge).  Block: 32 nodes x 6 components.
+// max(|du|, r_o |dtheta|) and of the residual g + A^T y.  Block: 32 nodes x 6 components.
 __device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx) {
   __shared__ double s_dx[32][6];
   __shared__ double s_r[32][6];
@@ -34,17 +32,6 @@ __device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx)
     s_r[fl][c] = fabs(r);
   }
   __syncthreads();
-  if (act && c == 0) {
-    for (int row = d.c_first[f]; row < d.c_first[f + 1]; ++row) {
-      if (d.rslot[row] >= 0) continue;
-      const double* n = d.c_n + 3 * row;
-      const double w = d.c_gap[row] - fma(n[0], s_dx[fl][0], fma(n[1], s_dx[fl][1], n[2] * s_dx[fl][2]));
-      if (w < -p.tol) {
-        d.p_flag[row] = RF_VIOLATED;
-        ctl->incomplete = 1;
-      }
-    }
-  }
   double rr_node = 0.0;
   if (act && c == 0)
     rr_node = fmax(fmax(fmax(s_r[fl][0], s_r[fl][1]), fmax(s_r[fl][2], s_r[fl][3])), fmax(s_r[fl][4], s_r[fl][5]));
@@ -97,7 +84,9 @@ __device__ __forceinline__ void limiter(const Params& p, const Dev& d, const Ctl
   *alpha = a;
 }
 
-// x <- x + alpha du, T <- exp([alpha dtheta]x) T.
+// x <- x + alpha du, T <- exp([alpha dtheta]x) T.  Every row of the node outside the working set is
+// checked against the applied step: w = b - alpha n . du < -tol marks it violated (it joins the
+// working set in the next iteration, and this iteration cannot converge; at convergence alpha = 1).
 __device__ __forceinline__ void apply_body(const Params& p, const Dev& d, int bx) {
   __shared__ double s_alpha;
   Ctl* ctl = d.ctl;
@@ -113,6 +102,15 @@ __device__ __forceinline__ void apply_body(const Params& p, const Dev& d, int bx
   if (f < nf) {
     const int node = ctl->k + 1 + f;
     const double* dx = d.dx + (size_t)f * 6;
+    for (int row = d.c_first[f]; row < d.c_first[f + 1]; ++row) {
+      if (d.rslot[row] >= 0) continue;
+      const double* n = d.c_n + 3 * row;
+      const double w = d.c_gap[row] - alpha * fma(n[0], dx[0], fma(n[1], dx[1], n[2] * dx[2]));
+      if (w < -p.tol) {
+        d.p_flag[row] = RF_VIOLATED;
+        ctl->incomplete = 1;
+      }
+    }
     d.px[node] += alpha * dx[0];
     d.py[node] += alpha * dx[1];
     d.pz[node] += alpha * dx[2];
