@@ -21,7 +21,11 @@ One call of ``Model.solve`` is one quasi-static step at a given cable tension an
     that step (so the step is at most halved, and a repeating cycle shrinks geometrically);
     otherwise rho grows by 1.5 back towards beta0.  (A fixed beta0 lets a node on a faceted wall
     overshoot the crease between two facets forever, and the material tangent overshoots the
-    twist of a long bent span by ~2x.)
+    twist of a long bent span by ~2x.)  The material tangent also converges linearly on a slow
+    monotone mode (steps shrinking by ~0.86 per iteration on a long compressed span): after a
+    full step, an unclipped step with the same contact rows, pointing the same way (cosine
+    >= 0.99) and shrinking by lam in [0.5, 0.98], is extended to the secant estimate of the limit,
+    alpha = min(1 / (1 - lam), 8, rho / max|du|).
   * convergence: unscaled step max_i max(|du_i|, r_o |dtheta_i|) <= tol and the same contact
     set as the previous iteration.
   * warm start (follow the path): with a resident state at insertion delta_old, material
@@ -193,6 +197,8 @@ class Model:
         residual = 0.0
         rho = opt.step_limit           # step bound of the limiter (shrinks when consecutive steps reverse)
         du_prev = None
+        nrm2_prev = 0.0
+        alpha_prev = 0.0
         status = E_NOT_CONVERGED
         base_reaction = np.zeros(6)
         if nf == 0:
@@ -253,14 +259,29 @@ class Model:
             dth = dx.reshape(nf, 6)[:, 3:]
             umax = float(np.sqrt((du * du).sum(axis=1)).max())
             step = float(max(umax, r_o * np.sqrt((dth * dth).sum(axis=1)).max()))
-            reverse = du_prev is not None and float(np.sum(du * du_prev)) < 0.0
+            key = tuple((rec["node"], rec["tri"]) for rec in contacts)
+            nrm2 = float(np.sum(du * du))
+            dot = float(np.sum(du * du_prev)) if du_prev is not None else 0.0
+            reverse = du_prev is not None and dot < 0.0
             if du_prev is not None:
                 if reverse:
                     rho = max(0.5 * min(rho, umax), opt.step_limit * 2.0 ** -40)
                 else:
                     rho = min(1.5 * rho, opt.step_limit)
-            du_prev = du.copy()
             alpha = 1.0 if umax <= rho else rho / umax
+            # over-relaxation of a slow monotone mode: after a full step, an unclipped step with the
+            # same rows pointing the same way (cosine >= 0.99) and shrinking by lam in [0.5, 0.98]
+            # is extended to the secant estimate of the limit, 1 / (1 - lam) times (at most 8, and
+            # within the bound rho)
+            if (du_prev is not None and not reverse and alpha_prev == 1.0 and alpha == 1.0 and key == prev_key
+                    and nrm2_prev > 0.0 and nrm2 > 0.0):
+                lam = math.sqrt(nrm2 / nrm2_prev)
+                cosang = dot / math.sqrt(nrm2 * nrm2_prev)
+                if cosang >= 0.99 and 0.5 <= lam <= 0.98:
+                    alpha = min(1.0 / (1.0 - lam), 8.0, rho / umax)
+            du_prev = du.copy()
+            nrm2_prev = nrm2
+            alpha_prev = alpha
             for j, i in enumerate(free):
                 x[i] = x[i] + alpha * du[j]
                 R[i] = expm(alpha * dth[j]) @ R[i]
@@ -272,7 +293,6 @@ class Model:
                 jmax = int(np.argmax(np.sqrt((du * du).sum(axis=1))))
                 act = [(rec["node"], rec["tri"], round(float(yy), 4)) for rec, yy in zip(contacts, y) if yy > 0]
                 self.trace_detail.append((free[jmax], du[jmax].copy(), act))
-            key = tuple((rec["node"], rec["tri"]) for rec in contacts)
             if step <= opt.newton_tol and key == prev_key:
                 status = OK
                 break

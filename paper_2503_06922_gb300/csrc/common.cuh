@@ -71,8 +71,9 @@ struct Ctl {
   int load_mode;         // 0 cables, 1 dead tip load (global), 2 follower tip load (tip frame)
   int loops;             // passes of the device-side Newton loop
   unsigned long long umax_bits, step_bits, res_bits;   // atomicMax on non-negative doubles
-  double alpha;
+  double alpha;          // alpha of the last applied step
   double rho;            // step bound of the limiter (starts at beta0)
+  double nrm2_prev;      // sum of |du|^2 of the previous step
   int has_prev;          // a previous Newton step exists in this solve
   int live;              // batch: a solve of this instance is in flight
   int cap_code;          // CAP_* cause of an ST_CAPACITY status
@@ -126,6 +127,7 @@ struct Dev {
   double* dx;                                        // nf_cap * 6 : Newton step
   double* du_prev;                                   // nf_cap * 3 : previous Newton step (translations)
   double* rev_part;                                  // per step_kernel block: sum du . du_prev
+  double* nrm_part;                                  // per step_kernel block: sum |du|^2
   // contact LCP
   double *W, *y, *gj;                                // ws_cap^2 (slots), m_cap (rows), ws_cap*(ws_cap+2)
   int *plist;                                        // ws_cap: active slots

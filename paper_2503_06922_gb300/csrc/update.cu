@@ -43,9 +43,13 @@ __device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx)
   }
   __syncthreads();
   if (threadIdx.x == 0 && threadIdx.y == 0) {
-    double rev = 0.0;
-    for (int k = 0; k < 32 && bx * 32 + k < nf; ++k) rev += s_r[k][0] + s_r[k][1] + s_r[k][2];
+    double rev = 0.0, nrm = 0.0;
+    for (int k = 0; k < 32 && bx * 32 + k < nf; ++k) {
+      rev += s_r[k][0] + s_r[k][1] + s_r[k][2];
+      nrm += fma(s_dx[k][0], s_dx[k][0], fma(s_dx[k][1], s_dx[k][1], s_dx[k][2] * s_dx[k][2]));
+    }
     d.rev_part[bx] = rev;
+    d.nrm_part[bx] = nrm;
   }
   if (act && c == 0) {
     double du = sqrt(s_dx[fl][0] * s_dx[fl][0] + s_dx[fl][1] * s_dx[fl][1] + s_dx[fl][2] * s_dx[fl][2]);
@@ -67,11 +71,18 @@ __global__ void __launch_bounds__(192) step_batch(const Inst* __restrict__ tab, 
 // points against the previous one (sum_i du_i . du_i^prev < 0, summed over the step blocks in a
 // fixed order) is an overshoot: rho drops to half of min(rho, max |du|), so the step is at most
 // halved and a repeating cycle shrinks geometrically; otherwise rho grows by 1.5 back towards
-// beta0.  Every reader evaluates this from the same inputs.
-__device__ __forceinline__ void limiter(const Params& p, const Dev& d, const Ctl* ctl, double* rho_new, double* alpha) {
+// beta0.  Over-relaxation of a slow monotone mode: after a full step, an unclipped step with the
+// same constraint rows, pointing the same way as the previous one (cosine >= 0.99) and shrinking
+// by lam = |du| / |du_prev| in [0.5, 0.98], is extended to the secant estimate of the limit,
+// alpha = min(1 / (1 - lam), 8, rho / max |du|).  Every reader evaluates this from the same inputs.
+__device__ __forceinline__ void limiter(const Params& p, const Dev& d, const Ctl* ctl, double* rho_new, double* alpha,
+                                        double* nrm2_out) {
   const int nb = (ctl->nf + 31) / 32;
-  double rev = 0.0;
-  for (int b = 0; b < nb; ++b) rev += d.rev_part[b];
+  double rev = 0.0, nrm2 = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    rev += d.rev_part[b];
+    nrm2 += d.nrm_part[b];
+  }
   double rho = ctl->rho;
   const double umax = __longlong_as_double((long long)ctl->umax_bits);
   const bool reverse = ctl->has_prev && rev < 0.0;
@@ -79,9 +90,15 @@ __device__ __forceinline__ void limiter(const Params& p, const Dev& d, const Ctl
     if (reverse) rho = fmax(0.5 * fmin(rho, umax), p.beta0 * 9.094947017729282e-13);   // beta0 / 2^40
     else rho = fmin(1.5 * rho, p.beta0);
   }
-  const double a = umax <= rho ? 1.0 : rho / umax;
+  double a = umax <= rho ? 1.0 : rho / umax;
+  if (ctl->has_prev && !reverse && ctl->alpha == 1.0 && a == 1.0 && ctl->same_set && ctl->nrm2_prev > 0.0 && nrm2 > 0.0) {
+    const double lam = sqrt(nrm2 / ctl->nrm2_prev);
+    const double cosang = rev / sqrt(nrm2 * ctl->nrm2_prev);
+    if (cosang >= 0.99 && lam >= 0.5 && lam <= 0.98) a = fmin(fmin(1.0 / (1.0 - lam), 8.0), rho / umax);
+  }
   *rho_new = rho;
   *alpha = a;
+  *nrm2_out = nrm2;
 }
 
 // x <- x + alpha du, T <- exp([alpha dtheta]x) T.  Every row of the node outside the working set is
@@ -93,8 +110,8 @@ __device__ __forceinline__ void apply_body(const Params& p, const Dev& d, int bx
   if (ctl->status != 0 || ctl->converged) return;
   const int nf = ctl->nf;
   if (threadIdx.x == 0) {
-    double rho;
-    limiter(p, d, ctl, &rho, &s_alpha);
+    double rho, nrm2;
+    limiter(p, d, ctl, &rho, &s_alpha, &nrm2);
   }
   __syncthreads();
   const double alpha = s_alpha;
@@ -146,11 +163,12 @@ __device__ __forceinline__ void ctl_update(const Params& p, const Dev& d) {
     c->fp64_tangent = 1;
   }
   if (c->status == 0 && !c->converged) {
-    double rho, alpha;
-    limiter(p, d, c, &rho, &alpha);
+    double rho, alpha, nrm2;
+    limiter(p, d, c, &rho, &alpha, &nrm2);
     const double step = __longlong_as_double((long long)c->step_bits);
     c->rho = rho;
     c->alpha = alpha;
+    c->nrm2_prev = nrm2;
     c->has_prev = 1;
     c->iter += 1;
     if (step <= p.tol && c->same_set && !c->incomplete) c->converged = 1;
