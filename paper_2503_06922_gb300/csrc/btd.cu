@@ -239,7 +239,7 @@ __device__ bool team_inverse6(double* sA, int tid, double* s_piv) {
     __syncthreads();
     double akk = sA[k * 6 + k];
     if (!(akk > 0.0)) return false;
-    double pk = 1.0 / akk;
+    double pk = __drcp_rn(akk);             // correctly rounded, as 1.0 / akk
     double v = 0.0;
     if (tid < 36) {
       double aij = sA[r * 6 + c], aik = sA[r * 6 + k], akj = sA[k * 6 + c];

@@ -61,7 +61,7 @@ static __device__ double tri_closest_f64(const double* p, const double* A, const
   *interior = 0;
   if (va >= 0.0 && vb >= 0.0 && vc >= 0.0) {
     *interior = 1;
-    double den = 1.0 / (va + vb + vc);
+    double den = __drcp_rn(va + vb + vc);
     double v = vb * den, w = vc * den;
     q[0] = v * ab[0] + w * ac[0]; q[1] = v * ab[1] + w * ac[1]; q[2] = v * ab[2] + w * ac[2];
   } else if (d1 <= 0.0 && d2 <= 0.0) { q[0] = 0.0; q[1] = 0.0; q[2] = 0.0; }

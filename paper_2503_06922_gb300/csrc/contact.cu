@@ -142,7 +142,7 @@ __device__ bool solve_on_set(const Dev& d, LcpShared& S, int m) {
     __syncthreads();
     const double akk = G[(size_t)k * ldg + k];
     if (!(akk > 0.0)) return false;
-    const double rp = 1.0 / akk;
+    const double rp = __drcp_rn(akk);
     for (int c = k + 1 + tid; c < ldg; c += nt) G[(size_t)k * ldg + c] *= rp;
     __syncthreads();
     const int wdt = ldg - k - 1;

@@ -68,7 +68,7 @@ __device__ __forceinline__ void element_body(const Params& p, const Dev& d, int 
   const double dv[3] = {d.px[b] - xa[0], d.py[b] - xa[1], d.pz[b] - xa[2]};
   const double l2 = dot3(dv, dv);
   const double l = sqrt(l2);
-  const double il = 1.0 / l;
+  const double il = __drcp_rn(l);
   const double e1[3] = {dv[0] * il, dv[1] * il, dv[2] * il};
   const double qv[3] = {0.5 * (S.T[0][1] + S.T[1][1]), 0.5 * (S.T[0][4] + S.T[1][4]), 0.5 * (S.T[0][7] + S.T[1][7])};
   double v3[3];
@@ -102,7 +102,7 @@ __device__ __forceinline__ void element_body(const Params& p, const Dev& d, int 
   __syncwarp();
   const double u = (l2 - p.l0 * p.l0) / (l + p.l0);
   const double qb1 = dot3(e1, qv), qb2 = dot3(e2, qv);   // local components of q (third is 0)
-  const double iq2 = 1.0 / qb2;
+  const double iq2 = __drcp_rn(qb2);
   const double* tha = S.th[0];
   const double* thb = S.th[1];
   const double* Tia = S.Ti[0];
