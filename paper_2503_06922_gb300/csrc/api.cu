@@ -129,6 +129,9 @@ void accfem_destroy(accfem_handle* h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
   if (h->h_stage) cudaFreeHost(h->h_stage);
+  if (h->fork) cudaEventDestroy(h->fork);
+  if (h->join) cudaEventDestroy(h->join);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -292,7 +295,10 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
   }
 
   // ---- device memory
-  if (!cuda_ok(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate")) {
+  if (!cuda_ok(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate") ||
+      !cuda_ok(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking), "cudaStreamCreate") ||
+      !cuda_ok(h, cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming), "cudaEventCreate") ||
+      !cuda_ok(h, cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming), "cudaEventCreate")) {
     accfem_destroy(h);
     return ACCFEM_E_CUDA;
   }
@@ -380,9 +386,15 @@ int enqueue_iteration(accfem_handle* h, int nf, cudaStream_t st, cudaGraphCondit
   Dev& d = h->d;
   int n = 0;
   auto grid = [nf](int ph) { return dim3(phase_gx(ph, nf), phase_gy(ph)); };
-  element_kernel<<<grid(PH_ELEM), 32 * kWarpsPerElemBlock, 0, st>>>(p, d); ++n;
+  // the element kernel and the collision + compaction both only read the poses: two branches that
+  // join before the assembly (captured as parallel graph nodes)
+  cudaEventRecord(h->fork, st);
+  cudaStreamWaitEvent(h->side, h->fork, 0);
+  element_kernel<<<grid(PH_ELEM), 32 * kWarpsPerElemBlock, 0, h->side>>>(p, d); ++n;
+  cudaEventRecord(h->join, h->side);
   collide_kernel<<<grid(PH_COLL), 128, 0, st>>>(p, d); ++n;
   compact_kernel<<<1, 1024, 0, st>>>(p, d); ++n;
+  cudaStreamWaitEvent(st, h->join, 0);
   n += enqueue_factor(p, d, nf, st);
   contact_kernel<<<1, 256, 0, st>>>(p, d); ++n;
   step_kernel<<<grid(PH_STEP), dim3(32, 6), 0, st>>>(p, d); ++n;

@@ -87,9 +87,14 @@ int enqueue_batch_iteration(accfem_batch* b, cudaStream_t st, cudaGraphCondition
   Plan* plan = b->d_plan;
   const int* g = b->grid;
   int n = 0;
-  element_batch<<<g[PH_ELEM], 32 * kWarpsPerElemBlock, 0, st>>>(tab, plan); ++n;
+  // the element phase and the collision + compaction phases both only read the poses: two branches
+  cudaEventRecord(b->fork, st);
+  cudaStreamWaitEvent(b->side, b->fork, 0);
+  element_batch<<<g[PH_ELEM], 32 * kWarpsPerElemBlock, 0, b->side>>>(tab, plan); ++n;
+  cudaEventRecord(b->join, b->side);
   collide_batch<<<g[PH_COLL], 128, 0, st>>>(tab, plan); ++n;
   compact_batch<<<g[PH_COMPACT], 1024, 0, st>>>(tab, plan); ++n;
+  cudaStreamWaitEvent(st, b->join, 0);
   assemble_rhs_batch<<<g[PH_ASM], dim3(32, 6), 0, st>>>(tab, plan); ++n;
   bcr_elim_batch<<<g[PH_ELIM1], 64, 0, st>>>(tab, plan); ++n;
   for (int j = 0; j < b->levels; ++j) { bcr_level_batch<<<g[PH_LEV0 + j], 192, 0, st>>>(tab, plan, j); ++n; }
@@ -196,6 +201,9 @@ void accfem_batch_destroy(accfem_batch* b) {
   for (void* p : {(void*)b->h_ctl, (void*)b->h_stage, (void*)b->h_begin, (void*)b->h_members, (void*)b->h_off,
                   (void*)b->h_pack, (void*)b->h_passes, (void*)b->h_tips})
     if (p) cudaFreeHost(p);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
+  if (b->side) cudaStreamDestroy(b->side);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -228,6 +236,9 @@ accfem_status accfem_batch_create(accfem_handle* const* members, int32_t n_membe
     b->stream_mode = lm && std::strcmp(lm, "stream") == 0;
   }
   bool ok = bok(b, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "cudaStreamCreate") &&
+            bok(b, cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking), "cudaStreamCreate") &&
+            bok(b, cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "cudaEventCreate") &&
+            bok(b, cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming), "cudaEventCreate") &&
             balloc(b, &b->d_tab, b->n) && balloc(b, &b->d_plan, 1) && balloc(b, &b->d_ctl, b->n) &&
             balloc(b, &b->d_stage, b->n) && balloc(b, &b->d_begin, b->n) && balloc(b, &b->d_members, b->n) &&
             balloc(b, &b->d_off, b->n) && balloc(b, &b->d_pack, pack) && balloc(b, &b->d_tips, (size_t)8 * b->n) &&

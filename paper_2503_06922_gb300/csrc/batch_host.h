@@ -12,6 +12,8 @@ struct accfem_batch {
   int max_nodes = 0;
   int levels = 0;
   cudaStream_t stream = nullptr, user_stream = nullptr;
+  cudaStream_t side = nullptr;      // second branch of an iteration (element phase beside collision)
+  cudaEvent_t fork = nullptr, join = nullptr;
   accfem::Inst* d_tab = nullptr;
   accfem::Plan* d_plan = nullptr;
   Ctl* d_ctl = nullptr;             // control block of member i (the batch's own)

@@ -16,6 +16,8 @@ struct accfem_handle {
   Params p;
   Dev d;
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;       // second branch of an iteration (element kernel beside collision)
+  cudaEvent_t fork = nullptr, join = nullptr;
   std::vector<void*> allocs;
   Ctl* h_ctl = nullptr;            // pinned host mirror of the control block
   double* h_stage = nullptr;       // pinned staging for results
