@@ -20,16 +20,31 @@ import numpy as np
 from .rotation import expm, logm, skew, tsinv
 
 
-def section_constants(robot):
+def section_constants(robot, youngs_modulus=None):
     """Hollow circular section: A = pi (ro^2 - ri^2), I = pi (ro^4 - ri^4)/4, J = 2 I,
-    G = E / (2 (1 + nu)).  Returns EA, EI, GJ and the element length l0 = L / M (Sec. II.B)."""
+    G = E / (2 (1 + nu)).  Returns EA, EI, GJ and the element length l0 = L / M (Sec. II.B).
+    E is the robot's modulus unless youngs_modulus is given."""
+    E = robot.youngs_modulus if youngs_modulus is None else float(youngs_modulus)
     ro, ri = robot.outer_radius, robot.inner_radius
     A = math.pi * (ro ** 2 - ri ** 2)
     I = math.pi * (ro ** 4 - ri ** 4) / 4.0
     J = 2.0 * I
-    G = robot.youngs_modulus / (2.0 * (1.0 + robot.poisson_ratio))
-    return {"EA": robot.youngs_modulus * A, "EI": robot.youngs_modulus * I, "GJ": G * J,
-            "l0": robot.length / robot.n_elements}
+    G = E / (2.0 * (1.0 + robot.poisson_ratio))
+    return {"EA": E * A, "EI": E * I, "GJ": G * J, "l0": robot.length / robot.n_elements}
+
+
+def element_sections(robot):
+    """Section constants of every element, base to tip.  The robot of Sec. II.A is not uniform: a
+    distal section is much less rigid than the rest, so each element may carry its own Young's
+    modulus (robot.element_youngs, one per element; None = the robot's modulus everywhere).  The
+    section geometry and Poisson's ratio are the robot's."""
+    Es = getattr(robot, "element_youngs", None)
+    if Es is None:
+        sec = section_constants(robot)
+        return [sec] * robot.n_elements
+    Es = np.asarray(Es, float)
+    assert Es.shape == (robot.n_elements,) and np.all(Es > 0.0)
+    return [section_constants(robot, E) for E in Es]
 
 
 def local_stiffness(sec):
@@ -173,6 +188,6 @@ def spin_update(T, dtheta):
     return expm(dtheta) @ T
 
 
-__all__ = ["section_constants", "local_stiffness", "corotated_frame", "local_deformation", "strain_energy",
+__all__ = ["section_constants", "element_sections", "local_stiffness", "corotated_frame", "local_deformation", "strain_energy",
            "B_local", "internal_force", "material_tangent", "consistent_tangent", "linear_beam_stiffness",
            "spin_update", "skew"]

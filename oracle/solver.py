@@ -101,7 +101,7 @@ class Model:
         self.robot = robot
         self.lumen = lumen
         self.opt = options or Options()
-        self.sec = beam.section_constants(robot)
+        self.secs = beam.element_sections(robot)
         self.M = robot.n_elements
         self.L = robot.length
         self.l0 = self.L / self.M
@@ -154,12 +154,12 @@ class Model:
         u = 11
         ab = np.zeros((u + 1, 6 * nf))
         for e in range(k, M):
-            Fe = beam.internal_force(x[e], R[e], x[e + 1], R[e + 1], self.sec)
+            Fe = beam.internal_force(x[e], R[e], x[e + 1], R[e + 1], self.secs[e])
             F[6 * e:6 * e + 12] += Fe
             if mode == 0:
-                Ke = beam.material_tangent(x[e], R[e], x[e + 1], R[e + 1], self.sec)
+                Ke = beam.material_tangent(x[e], R[e], x[e + 1], R[e + 1], self.secs[e])
             else:
-                Kt = beam.consistent_tangent(x[e], R[e], x[e + 1], R[e + 1], self.sec)
+                Kt = beam.consistent_tangent(x[e], R[e], x[e + 1], R[e + 1], self.secs[e])
                 Ke = 0.5 * (Kt + Kt.T)
             base = 6 * (e - (k + 1))          # free dof index of element dof 0
             for i in range(12):

@@ -26,7 +26,7 @@ import numpy as np
 __all__ = [
     "RobotDesc", "LumenDesc", "Workload", "robot_desc", "tube_mesh",
     "bent_tube_centerline", "catmull_rom_centerline", "bent_tube_workload",
-    "catmull_rom_workload", "plane_lumen", "random_tensions",
+    "catmull_rom_workload", "plane_lumen", "random_tensions", "soft_tip_moduli", "with_soft_tip",
 ]
 
 
@@ -42,6 +42,7 @@ class RobotDesc:
     n_cables: int = 3
     cable_radius: float = 1.5e-3
     cable_angles: np.ndarray = field(default_factory=lambda: np.array([0.0, 2 * math.pi / 3, 4 * math.pi / 3]))
+    element_youngs: np.ndarray | None = None   # (n_elements,) per-element modulus, base to tip; None = uniform
 
 
 @dataclass
@@ -68,6 +69,23 @@ def robot_desc(length, n_elements, outer_radius=2e-3, inner_radius=1e-3, youngs_
     return RobotDesc(length=float(length), outer_radius=float(outer_radius), inner_radius=float(inner_radius),
                      youngs_modulus=float(youngs_modulus), poisson_ratio=float(poisson_ratio),
                      n_elements=int(n_elements), cable_radius=float(cable_radius))
+
+
+def soft_tip_moduli(robot: RobotDesc, soft_length=0.07, soft_ratio=0.1) -> np.ndarray:
+    """Per-element Young's moduli of a robot whose distal soft_length (70 mm on the robot of Sec. II.A)
+    is softer by soft_ratio (the paper gives no value; 0.1 is this generator's choice).  An element
+    is soft when its midpoint lies within soft_length of the tip."""
+    M, l0 = robot.n_elements, robot.length / robot.n_elements
+    mid = (np.arange(M) + 0.5) * l0
+    E = np.full(M, robot.youngs_modulus)
+    E[mid > robot.length - soft_length] *= soft_ratio
+    return E
+
+
+def with_soft_tip(robot: RobotDesc, soft_length=0.07, soft_ratio=0.1) -> RobotDesc:
+    """A copy of robot with the soft distal section of soft_tip_moduli."""
+    from dataclasses import replace
+    return replace(robot, element_youngs=soft_tip_moduli(robot, soft_length, soft_ratio))
 
 
 def _rmf(points: np.ndarray, t0_normal: np.ndarray):
