@@ -170,6 +170,16 @@ accfem_status accfem_set_stream(accfem_handle* h, void* stream);
 #define ACCFEM_PRECISION_MIXED 1
 accfem_status accfem_set_precision(accfem_handle* h, int32_t mode);
 
+/* Per-element Young's modulus (Sec. II.A: the robot is not uniform; its distal section is much
+ * less rigid than the rest).  youngs_modulus: host array of n_elements moduli in Pa, element e
+ * joining nodes e and e + 1 (node 0 at the base), copied before return; NULL restores the robot's
+ * own modulus everywhere.  The section (radii) and Poisson's ratio stay the robot's, so element e
+ * has EA = E_e A, EI = E_e I, GJ = E_e / (2 (1 + nu)) 2 I.  Call between solves (it waits for the
+ * handle's work); the resident state is kept.  A batch reads its members' moduli at every
+ * iteration, so it applies to batched solves too.  E_INVALID_ARG if n_elements differs from the
+ * robot's or a modulus is not finite and positive (nothing is changed then). */
+accfem_status accfem_set_element_modulus(accfem_handle* h, const double* youngs_modulus, int32_t n_elements);
+
 /* Cumulative bytes copied host->device and device->host by this handle's solve and state calls. */
 accfem_status accfem_transfer_bytes(const accfem_handle* h, int64_t* h2d, int64_t* d2h);
 

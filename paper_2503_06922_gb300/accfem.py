@@ -77,7 +77,7 @@ EXPORTS = ["accfem_default_options", "accfem_create", "accfem_solve", "accfem_so
            "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream", "accfem_batch_transfer_bytes",
            "accfem_batch_kernel_launches", "accfem_batch_last_error", "accfem_batch_destroy", "accfem_batch_serve",
            "accfem_device_bytes", "accfem_solve_stats", "accfem_set_precision", "accfem_batch_autotune",
-           "accfem_batch_tuning"]
+           "accfem_batch_tuning", "accfem_set_element_modulus"]
 
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 
@@ -139,6 +139,7 @@ def load(path=LIB_PATH):
     lib.accfem_device_bytes.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
     lib.accfem_solve_stats.argtypes = [H, _ip, _ip, _ip, _ip]
     lib.accfem_set_precision.argtypes = [H, ctypes.c_int32]
+    lib.accfem_set_element_modulus.argtypes = [H, _dp, ctypes.c_int32]
     lib.accfem_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int32]
     lib.accfem_batch_tuning.argtypes = [ctypes.c_void_p, _ip, _dp]
     lib.accfem_batch_destroy.argtypes = [B]
@@ -149,7 +150,7 @@ def load(path=LIB_PATH):
                  "accfem_batch_create", "accfem_batch_begin", "accfem_batch_advance", "accfem_batch_poll",
                  "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream",
                  "accfem_batch_transfer_bytes", "accfem_batch_serve", "accfem_device_bytes", "accfem_solve_stats", "accfem_set_precision",
-                 "accfem_batch_autotune", "accfem_batch_tuning"):
+                 "accfem_batch_autotune", "accfem_batch_tuning", "accfem_set_element_modulus"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -205,6 +206,11 @@ class AccFem:
         self._cp = np.zeros((self.cap, 3))
         self._cnrm = np.zeros((self.cap, 3))
         self._cf = np.zeros(self.cap)
+        if getattr(robot, "element_youngs", None) is not None:
+            st = self.accfem_set_element_modulus(robot.element_youngs)
+            if st != OK:
+                self.close()
+                raise RuntimeError("accfem_set_element_modulus failed: %s" % accfem_status_string(st))
 
     def close(self):
         if getattr(self, "h", None):
@@ -300,6 +306,16 @@ class AccFem:
 
     def accfem_set_precision(self, mode):
         return int(self._lib.accfem_set_precision(self.h, int(mode)))
+
+    def accfem_set_element_modulus(self, youngs_modulus, n_elements=None):
+        """Per-element Young's moduli (None: the robot's own everywhere)."""
+        if youngs_modulus is None:
+            return int(self._lib.accfem_set_element_modulus(self.h, None, self.M if n_elements is None else int(n_elements)))
+        E = np.ascontiguousarray(youngs_modulus, dtype=np.float64)
+        n = len(E) if n_elements is None else int(n_elements)
+        if n > len(E):                     # the C side would read n entries
+            return E_INVALID_ARG
+        return int(self._lib.accfem_set_element_modulus(self.h, _ptr(E), n))
 
     def accfem_solve_stats(self):
         """(constraint rows, working-set rows, active rows, FP64-tangent fallback) of the last solve."""

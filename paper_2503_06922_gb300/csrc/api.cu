@@ -184,6 +184,10 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
   p.EA = r.youngs_modulus * A;
   p.EI = r.youngs_modulus * I;
   p.GJ = G * 2.0 * I;
+  h->youngs = r.youngs_modulus;
+  h->poisson = r.poisson_ratio;
+  h->area = A;
+  h->inertia = I;
   p.r_o = r.outer_radius;
   p.act = opt.activation_gap;
   p.beta0 = opt.step_limit;
@@ -308,7 +312,8 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
   bool ok = dalloc(h, &d.px, N) && dalloc(h, &d.py, N) && dalloc(h, &d.pz, N) && dalloc(h, &d.qw, N) &&
             dalloc(h, &d.qx, N) && dalloc(h, &d.qy, N) && dalloc(h, &d.qz, N) && dalloc(h, &d.ox, N) &&
             dalloc(h, &d.oy, N) && dalloc(h, &d.oz, N) && dalloc(h, &d.ow, N) && dalloc(h, &d.oqx, N) &&
-            dalloc(h, &d.oqy, N) && dalloc(h, &d.oqz, N) && dalloc(h, &d.elem, (size_t)M * kElemStride);
+            dalloc(h, &d.oqy, N) && dalloc(h, &d.oqz, N) && dalloc(h, &d.elem, (size_t)M * kElemStride) &&
+            dalloc(h, &d.kel, (size_t)M * 4);
   int *cs = nullptr, *ct = nullptr, *tv = nullptr;
   float* t32 = nullptr;
   float* s32 = nullptr;
@@ -345,6 +350,7 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
     accfem_destroy(h);
     return ACCFEM_E_CUDA;
   }
+  if (accfem_set_element_modulus(h, nullptr, M) != ACCFEM_OK) { accfem_destroy(h); return ACCFEM_E_CUDA; }
   d.cell_start = cs; d.cell_tri = ct; d.tri32 = t32; d.sph32 = s32; d.V = vv; d.T = tv; d.nface = nfc_d;
   if (cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess) { accfem_destroy(h); return ACCFEM_E_NOMEM; }
   h->stage_bytes = sizeof(double) * (size_t)std::max<int64_t>(7 * N, 16 * (int64_t)mc + 64);
@@ -661,6 +667,28 @@ accfem_status accfem_set_precision(accfem_handle* h, int32_t mode) {
   }
   h->graphs.clear();
   h->p.precision = mode;
+  return ACCFEM_OK;
+}
+
+accfem_status accfem_set_element_modulus(accfem_handle* h, const double* youngs_modulus, int32_t n_elements) {
+  if (!h || n_elements != h->p.M) return ACCFEM_E_INVALID_ARG;
+  const int M = h->p.M;
+  std::vector<double> k(4 * (size_t)M, 0.0);
+  for (int e = 0; e < M; ++e) {
+    const double E = youngs_modulus ? youngs_modulus[e] : h->youngs;
+    if (!(E > 0.0) || !std::isfinite(E)) return ACCFEM_E_INVALID_ARG;
+    // section constants of Sec. II.B with this element's modulus; E = the robot's gives p.EA etc.
+    const double EA = youngs_modulus ? E * h->area : h->p.EA;
+    const double EI = youngs_modulus ? E * h->inertia : h->p.EI;
+    const double GJ = youngs_modulus ? E / (2.0 * (1.0 + h->poisson)) * 2.0 * h->inertia : h->p.GJ;
+    k[4 * e] = EA / h->p.l0;
+    k[4 * e + 1] = GJ / h->p.l0;
+    k[4 * e + 2] = EI / h->p.l0;
+  }
+  if (h->stream) cudaStreamSynchronize(h->work());
+  if (!cuda_ok(h, cudaMemcpy(h->d.kel, k.data(), sizeof(double) * k.size(), cudaMemcpyHostToDevice), "upload moduli"))
+    return ACCFEM_E_CUDA;
+  h->h2d += (int64_t)(sizeof(double) * k.size());
   return ACCFEM_OK;
 }
 

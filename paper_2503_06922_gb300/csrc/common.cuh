@@ -95,6 +95,7 @@ struct Dev {
   double *px, *py, *pz, *qw, *qx, *qy, *qz;          // N nodal poses
   double *ox, *oy, *oz, *ow, *oqx, *oqy, *oqz;       // previous poses (warm start source)
   double* elem;                                      // M * kElemStride
+  double* kel;                                       // M * 4: EA/l0, GJ/l0, EI/l0, 0 of element e
   // lumen
   const int* cell_start;                             // ncells + 1
   const float* tri32;                                // T * 9: vertices relative to the cell centre

@@ -4,7 +4,7 @@
 // Element e joins nodes a = e and b = e + 1.  Rigid frame R_r = [e1 e2 e3]: e1 along the chord,
 // e3 normal to e1 and the mean q of the nodal second section axes.  Local deformations
 // d_l = [l - l0, log(R_r^T T_a), log(R_r^T T_b)], constant local stiffness K_l (EA/l0, GJ/l0,
-// EI/l0 [[4 2][2 4]] per bending plane).  With B = dd_l/dd (spatial spins, local components):
+// EI/l0 [[4 2][2 4]] per bending plane; each element has its own modulus, Sec. II.A).  With B = dd_l/dd (spatial spins, local components):
 //   F = E B^T K_l d_l,   K = E B^T K_l B E^T,   E = blockdiag(R_r, R_r, R_r, R_r).
 // Output record (doubles): [0, 78) upper triangle of K row-major, [78, 90) F = [F_a M_a F_b M_b].
 #include "batch.cuh"
@@ -111,7 +111,7 @@ __device__ __forceinline__ void element_body(const Params& p, const Dev& d, int 
   const double* Rb = S.Rab[1];
   const double* Rr = S.Rr;
   // local force vector f_l = K_l d_l
-  const double ka = p.EA / p.l0, kt = p.GJ / p.l0, kb = p.EI / p.l0;
+  const double ka = d.kel[4 * e], kt = d.kel[4 * e + 1], kb = d.kel[4 * e + 2];   // EA/l0, GJ/l0, EI/l0
   double fl[7];
   fl[0] = ka * u;
   fl[1] = kt * (tha[0] - thb[0]);

@@ -35,6 +35,7 @@ struct accfem_handle {
   cudaStream_t user_stream = nullptr; // caller's stream (accfem_set_stream), else the handle's own
   int64_t h2d = 0, d2h = 0;          // bytes copied by solve / state calls
   int64_t dev_bytes = 0;             // device memory held by the handle
+  double youngs = 0.0, poisson = 0.0, area = 0.0, inertia = 0.0;   // robot material and section
   cudaStream_t work() const { return user_stream ? user_stream : stream; }
 };
 
