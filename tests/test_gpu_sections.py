@@ -75,7 +75,10 @@ def test_piecewise_closed_forms(af):
 
 def test_soft_tip_sweep_matches_oracle(af):
     """Bent tube with a 70 mm distal section at a tenth of the modulus, 10 insertion steps with
-    contacts: positions 1e-9 relative, the same contact nodes, net contact force per node 1e-6."""
+    contacts: positions 1e-9 relative, the same contact nodes, net contact force per node within
+    1e-6 of the largest one or the force that the Newton tolerance leaves open, whichever is
+    larger: both sides stop at a residual up to tol max(1, |F_a|, max y), and a residual moment of
+    that size acting over one element length l0 moves a contact force by tol max(1, sum tau) / l0."""
     w = wl.bent_tube_workload(0, n_steps=10)
     rob = wl.with_soft_tip(w.robot)
     gpu = af.AccFem(rob, w.lumen)
@@ -94,8 +97,9 @@ def test_soft_tip_sweep_matches_oracle(af):
         for c in g["contacts"]:
             fg[c["node"]] = fg.get(c["node"], 0.0) + c["force"] * np.asarray(c["normal"])
         fmax = max([np.linalg.norm(f) for f in fo.values()] + [1e-300])
+        ftol = max(1e-6 * fmax, 1e-10 * max(1.0, float(np.sum(w.tensions[s]))) / (rob.length / rob.n_elements))
         for n in fo:
-            assert np.linalg.norm(fo[n] - fg[n]) <= 1e-6 * fmax, (s, n)
+            assert np.linalg.norm(fo[n] - fg[n]) <= ftol, (s, n, np.linalg.norm(fo[n] - fg[n]), ftol)
         n_rows += len(g["contacts"])
     assert n_rows > 0
     # the soft tip changes the answer: the uniform robot ends elsewhere
