@@ -26,7 +26,6 @@ __global__ void start_kernel(Params p, Dev d, int mode, double delta, double del
 __global__ void ctl_kernel(Params p, Dev d, cudaGraphConditionalHandle h, int max_iter, int set_cond);
 __global__ void assemble_rhs_kernel(Params p, Dev d);
 __global__ void bcr_level_kernel(Params p, Dev d, int s);
-__global__ void bcr_tail_kernel(Params p, Dev d);
 void upload_element_tables();
 }  // namespace accfem
 
@@ -383,7 +382,6 @@ int enqueue_factor(const Params& p, const Dev& d, int nf, cudaStream_t st) {
   int levels = 0;
   while (levels < kMaxLevels && phase_gx(PH_LEV0 + levels, nf) > 0) ++levels;
   for (int j = 0; j < levels; ++j) { bcr_level_kernel<<<grid(PH_LEV0 + j), 192, 0, st>>>(p, d, 1 << j); ++n; }
-  bcr_tail_kernel<<<grid(PH_TAIL), 192, 0, st>>>(p, d); ++n;
   for (int j = levels - 1; j >= 0; --j)
     if (phase_gx(PH_BWD0 + j, nf) > 0) { bcr_bwd_kernel<<<grid(PH_BWD0 + j), 192, 0, st>>>(p, d, 1 << j); ++n; }
   return n;

@@ -23,7 +23,6 @@ __global__ void assemble_rhs_batch(const Inst* __restrict__ tab, const Plan* __r
 __global__ void bcr_elim_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
 __global__ void bcr_level_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j);
 __global__ void bcr_bwd_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j);
-__global__ void bcr_tail_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
 __global__ void contact_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
 __global__ void step_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
 __global__ void apply_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
@@ -99,7 +98,6 @@ int enqueue_batch_iteration(accfem_batch* b, cudaStream_t st, cudaGraphCondition
   assemble_rhs_batch<<<g[PH_ASM], dim3(32, 6), 0, st>>>(tab, plan); ++n;
   bcr_elim_batch<<<g[PH_ELIM1], 64, 0, st>>>(tab, plan); ++n;
   for (int j = 0; j < b->levels; ++j) { bcr_level_batch<<<g[PH_LEV0 + j], 192, 0, st>>>(tab, plan, j); ++n; }
-  bcr_tail_batch<<<g[PH_TAIL], 192, 0, st>>>(tab, plan); ++n;
   for (int j = b->levels - 1; j >= 0; --j) { bcr_bwd_batch<<<g[PH_BWD0 + j], 192, 0, st>>>(tab, plan, j); ++n; }
   contact_batch<<<g[PH_CONTACT], 256, 0, st>>>(tab, plan); ++n;
   step_batch<<<g[PH_STEP], dim3(32, 6), 0, st>>>(tab, plan); ++n;
@@ -123,7 +121,6 @@ void full_grids(accfem_batch* b, int* grid) {
   grid[PH_CONTACT] = persistent_grid(contact_batch, 256, units[PH_CONTACT]);
   grid[PH_STEP] = persistent_grid(step_batch, 192, units[PH_STEP]);
   grid[PH_APPLY] = persistent_grid(apply_batch, 128, units[PH_APPLY]);
-  grid[PH_TAIL] = persistent_grid(bcr_tail_batch, 192, units[PH_TAIL]);
   for (int j = 0; j < b->levels; ++j) {
     grid[PH_LEV0 + j] = persistent_grid(bcr_level_batch, 192, units[PH_LEV0 + j]);
     grid[PH_BWD0 + j] = persistent_grid(bcr_bwd_batch, 192, units[PH_BWD0 + j]);

@@ -11,7 +11,6 @@ namespace accfem {
 
 constexpr int kMaxBatch = 1024;     // instances per batch
 constexpr int kMaxLevels = 21;      // reduction strides 1 .. 2^20 (n_elements <= 2^20)
-constexpr int kTailNodes = 16;      // the reduction finishes in one CTA once at most this many nodes remain
 
 struct Inst {
   Params p;
@@ -20,7 +19,7 @@ struct Inst {
 
 // Phases of one Newton iteration; level j of the reduction has stride s = 2^j.
 enum : int {
-  PH_ELEM = 0, PH_COLL, PH_COMPACT, PH_ASM, PH_ELIM1, PH_CONTACT, PH_STEP, PH_APPLY, PH_TAIL,
+  PH_ELEM = 0, PH_COLL, PH_COMPACT, PH_ASM, PH_ELIM1, PH_CONTACT, PH_STEP, PH_APPLY,
   PH_LEV0,
   PH_BWD0 = PH_LEV0 + kMaxLevels,
   kPhases = PH_BWD0 + kMaxLevels
@@ -43,15 +42,6 @@ struct BatchBegin {
   double delta, delta_old;
 };
 
-// First level of the reduction's tail for nf >= 1 free nodes: the smallest j with at most
-// kTailNodes nodes left at stride 2^j (nodes 0, 2^j, 2 2^j, ..; ceil(nf / 2^j) of them).  Levels
-// j' >= j, the root and their back substitution run in one kernel (bcr_tail).
-__host__ __device__ inline int tail_level(int nf) {
-  int j = 0;
-  while (((nf - 1) >> j) + 1 > kTailNodes) ++j;
-  return j;
-}
-
 // Blocks in x of phase ph for nf free nodes (the single-instance launch uses the same grid).
 __host__ __device__ inline int phase_gx(int ph, int nf) {
   if (nf <= 0) return 0;
@@ -64,25 +54,24 @@ __host__ __device__ inline int phase_gx(int ph, int nf) {
     case PH_CONTACT: return 1;
     case PH_STEP: return (nf + 31) / 32;
     case PH_APPLY: return (nf + 127) / 128;
-    case PH_TAIL: return 1;
     default: break;
   }
-  if (ph >= PH_LEV0 && ph < PH_BWD0) {          // levels below the tail (then s < nf)
+  if (ph >= PH_LEV0 && ph < PH_BWD0) {
     const int j = ph - PH_LEV0;
     const long long s = 1ll << j;
-    return j < tail_level(nf) ? (int)((nf - 1) / (2 * s) + 1) : 0;
+    if (s < nf) return (int)((nf - 1) / (2 * s) + 1);
+    return (j == 0 && nf == 1) ? 1 : 0;       // a single free node: the root step alone
   }
   if (ph >= PH_BWD0 && ph < kPhases) {
-    const int j = ph - PH_BWD0;
-    const long long s = 1ll << j;
-    return j < tail_level(nf) ? (int)((nf - s - 1) / (2 * s) + 1) : 0;
+    const long long s = 1ll << (ph - PH_BWD0);
+    return s < nf ? (int)((nf - s - 1) / (2 * s) + 1) : 0;
   }
   return 0;
 }
 
 // Blocks in y (RHS column split) of phase ph.
 __host__ __device__ inline int phase_gy(int ph) {
-  return (ph == PH_ASM || ph == PH_TAIL || (ph >= PH_LEV0 && ph < kPhases)) ? kRhsSplit : 1;
+  return (ph == PH_ASM || (ph >= PH_LEV0 && ph < kPhases)) ? kRhsSplit : 1;
 }
 
 // Persistent loop over the units of phase ph: body(inst, bx, by) for every unit assigned to this

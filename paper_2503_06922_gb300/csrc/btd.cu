@@ -11,10 +11,8 @@
 // R_j = U_j^T P_j.  For kept i: D_i -= R_{i-s} U_{i-s} + L_{i+s} U_i^T, U_i <- -L_{i+s} U_{i+s}.
 // Solve: forward b_i -= R_{i-s} b_{i-s} + L_{i+s} b_{i+s} (kept), root x_0 = P_0 b_0, backward
 // x_j = P_j b_j - L_j^T x_{j-s} - R_j^T x_{j+s} (eliminated).  Launches per factor-and-solve:
-// bcr_elim_kernel (level 1), one bcr_level_kernel per level while more than kTailNodes nodes remain
-// (kept-node update + next level's eliminations + forward RHS), bcr_tail_kernel (the remaining
-// levels, the root and their back substitution in one CTA per RHS split, from shared memory), one
-// bcr_bwd_kernel per level below the tail.
+// bcr_elim_kernel (level 1), one bcr_level_kernel per level (kept-node update + next level's
+// eliminations + forward RHS; root at the last level), one bcr_bwd_kernel per level.
 #include "batch.cuh"
 
 namespace accfem {
@@ -302,8 +300,8 @@ __global__ void __launch_bounds__(64) bcr_elim_batch(const Inst* __restrict__ ta
 // y = RHS split), 192 threads.  Block y == 0: Schur update of D_i and U_i (kept nodes i: D_i and U_i as above);
 // when i = 2s (mod 4s) it then eliminates i at level 2s: its new left coupling
 // U_{i-2s} <- -L_{i-s} U_{i-s} is rebuilt from level-s data, P_i = D_i^{-1}, L_i = U_{i-2s} P_i,
-// R_i = U_i^T P_i.  Every block applies the level-s forward reduction to its RHS chunks.  Only
-// levels below the tail run here (more than kTailNodes nodes left, so 2s < nf: never the root).
+// R_i = U_i^T P_i.  Every block applies the level-s forward reduction to its RHS chunks.  When
+// 2s >= nf only node 0 is kept: every block inverts D_0 itself (root) and solves x_0 = P_0 b_0.
 __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, int bx, int by, int s) {
   __shared__ double sRl[36], sUl[36], sLr[36], sUi[36], sUr[36], sA[36], sX[36], sY[36];
   __shared__ double s_piv[1];
@@ -314,7 +312,8 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
   if (i >= nf) return;
   const int tid = threadIdx.x;
   const bool hl = i >= s, hr = i + s < nf, hr2 = i + 2 * s < nf;
-  const bool elim2 = (i % (4 * s)) == 2 * s;           // i is eliminated at level 2s
+  const bool root = 2 * s >= nf;                       // only node 0 remains after this level
+  const bool elim2 = !root && (i % (4 * s)) == 2 * s;   // i is eliminated at level 2s
   if (tid < 36) {
     sRl[tid] = hl ? d.Rm[(size_t)(i - s) * 36 + tid] : 0.0;
     sUl[tid] = hl ? d.U[(size_t)(i - s) * 36 + tid] : 0.0;
@@ -323,7 +322,8 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
     sUr[tid] = hr2 ? d.U[(size_t)(i + s) * 36 + tid] : 0.0;
   }
   __syncthreads();
-  if (tid < 36 && by == 0) {
+  const bool matrix = by == 0 || root;
+  if (tid < 36 && matrix) {
     const int r = tid / 6, c = tid % 6;
     double dd = d.D[(size_t)i * 36 + tid];
     double un = 0.0;
@@ -335,8 +335,12 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
     }
     sA[tid] = dd;
     sY[tid] = hr2 ? un : 0.0;                        // new U_i = K_{i, i+2s}
-    d.D[(size_t)i * 36 + tid] = dd;
-    if (hr) d.U[(size_t)i * 36 + tid] = hr2 ? un : 0.0;
+    // the root's D_0 and U_0 are read by every block of this level and needed by no later step:
+    // only non-root levels store the updated blocks (for the next level's kernel)
+    if (by == 0 && !root) {
+      d.D[(size_t)i * 36 + tid] = dd;
+      if (hr) d.U[(size_t)i * 36 + tid] = hr2 ? un : 0.0;
+    }
   }
   if (elim2 && by == 0) {
     // new left coupling K_{i-2s, i} = -L_{i-s} U_{i-s}: node i-s was eliminated at level s
@@ -370,19 +374,58 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
   const int lane = tid & 31, c = tid >> 5;
   const int nrhs = ctl->mc + 1;
   const size_t ld = p.nrhs_cap;
-  for (int r = by * 32 + lane; r < nrhs; r += 32 * kRhsSplit) {
-    double acc = d.B[((size_t)i * 6 + c) * ld + r];
-    if (hl) {
-      const double* b = d.B + (size_t)(i - s) * 6 * ld + r;
+  if (!root) {
+    for (int r = by * 32 + lane; r < nrhs; r += 32 * kRhsSplit) {
+      double acc = d.B[((size_t)i * 6 + c) * ld + r];
+      if (hl) {
+        const double* b = d.B + (size_t)(i - s) * 6 * ld + r;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) acc = fma(-sRl[c * 6 + k], b[k * ld], acc);
-    }
-    if (hr) {
-      const double* b = d.B + (size_t)(i + s) * 6 * ld + r;
+        for (int k = 0; k < 6; ++k) acc = fma(-sRl[c * 6 + k], b[k * ld], acc);
+      }
+      if (hr) {
+        const double* b = d.B + (size_t)(i + s) * 6 * ld + r;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) acc = fma(-sLr[c * 6 + k], b[k * ld], acc);
+        for (int k = 0; k < 6; ++k) acc = fma(-sLr[c * 6 + k], b[k * ld], acc);
+      }
+      d.B[((size_t)i * 6 + c) * ld + r] = acc;
     }
-    d.B[((size_t)i * 6 + c) * ld + r] = acc;
+    return;
+  }
+  // root: node 0 after its last update; every block inverts D_0 and solves its chunks
+  __syncthreads();
+  const bool ok = team_inverse6(sA, tid, s_piv);
+  if (!ok) {
+    if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
+    return;
+  }
+  if (tid < 36 && by == 0) d.P[tid] = sA[tid];
+  for (int r0 = by * 32; r0 < nrhs; r0 += 32 * kRhsSplit) {
+    const int r = r0 + lane;
+    const bool act = r < nrhs;
+    double acc0 = 0.0;
+    if (act) {
+      acc0 = d.B[(size_t)c * ld + r];
+      if (hr) {
+        const double* b = d.B + (size_t)s * 6 * ld + r;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc0 = fma(-sLr[c * 6 + k], b[k * ld], acc0);
+      }
+    }
+    __syncthreads();
+    if (act) d.B[(size_t)c * ld + r] = acc0;          // b_0 after the last forward step
+    __syncthreads();
+    double bb[6];
+    if (act)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) bb[k] = d.B[(size_t)k * ld + r];
+    __syncthreads();
+    if (act) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc = fma(sA[c * 6 + k], bb[k], acc);
+      d.B[(size_t)c * ld + r] = acc;
+    }
+    __syncthreads();
   }
 }
 
@@ -393,214 +436,6 @@ __global__ void __launch_bounds__(192) bcr_level_kernel(Params p, Dev d, int s) 
 // level j (stride 2^j) of every iterating instance
 __global__ void __launch_bounds__(192) bcr_level_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j) {
   for_units(tab, plan, PH_LEV0 + j, [j](const Inst& in, int bx, int by) { bcr_level_body(in.p, in.d, bx, by, 1 << j); });
-}
-
-// Tail of the reduction: the levels from stride S = 2^tail_level(nf) up, the root and the back
-// substitution down to stride S, in one CTA per RHS split (blocks y, 192 threads).  At entry the
-// n = ceil(nf / S) nodes a S (slot a) are those of level S: even slots kept with their updated D, U;
-// odd slots eliminated at level S (P, L, R computed).  Every block repeats the matrix work on
-// shared-memory copies (nothing of it is stored) and reduces, solves and back-substitutes its own
-// RHS chunks.  Each entry takes the same operations in the same order as the per-level kernels.
-__device__ __forceinline__ void bcr_tail_body(const Params& p, const Dev& d, int by) {
-  constexpr int T = kTailNodes, H = kTailNodes / 2;
-  __shared__ double sD[T][36], sU[T][36], sP[T][36], sL[T][36], sR[T][36];
-  __shared__ double sN[H][36], sX[H][36];
-  __shared__ int s_go, s_bad;
-  Ctl* ctl = d.ctl;
-  const int tid = threadIdx.x;
-  if (tid == 0) { s_go = (ctl->status == 0 && !ctl->converged) ? 1 : 0; s_bad = 0; }
-  __syncthreads();
-  if (!s_go) return;
-  const int nf = ctl->nf;
-  const int jt = tail_level(nf);
-  const int S = 1 << jt;
-  const int n = ((nf - 1) >> jt) + 1;
-  for (int e = tid; e < n * 36; e += blockDim.x) {
-    const int a = e / 36, q = e % 36;
-    const size_t i = (size_t)a * S;
-    sU[a][q] = a + 1 < n ? d.U[i * 36 + q] : 0.0;
-    if ((a & 1) == 0) {
-      sD[a][q] = d.D[i * 36 + q];
-    } else {
-      sP[a][q] = d.P[i * 36 + q];
-      sL[a][q] = d.Lm[i * 36 + q];
-      sR[a][q] = a + 1 < n ? d.Rm[i * 36 + q] : 0.0;
-    }
-  }
-  __syncthreads();
-  const int lane = tid & 31, c = tid >> 5;       // RHS: column lane of a 32-column chunk, component c
-  const int nrhs = ctl->mc + 1;
-  const size_t ld = p.nrhs_cap;
-  auto bcol = [&](int a, int k, int r) -> double* { return d.B + ((size_t)a * S * 6 + k) * ld + r; };
-  int sig = 1;
-  for (;; sig <<= 1) {
-    const bool root = 2 * sig >= n;
-    const int nk = (n - 1) / (2 * sig) + 1;      // kept slots 2 sig t, t < nk
-    // Schur update of the kept slots (D_i -= R_{i-s} U_{i-s} + L_{i+s} U_i^T, new U_i = -L_{i+s} U_{i+s})
-    for (int e = tid; e < nk * 36; e += blockDim.x) {
-      const int t = e / 36, q = e % 36, r = q / 6, cc = q % 6, a = 2 * sig * t;
-      const bool hl = a >= sig, hr = a + sig < n, hr2 = a + 2 * sig < n;
-      double dd = sD[a][q], un = 0.0;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const double rl = hl ? sR[a - sig][r * 6 + k] : 0.0, ul = hl ? sU[a - sig][k * 6 + cc] : 0.0;
-        const double lr = hr ? sL[a + sig][r * 6 + k] : 0.0, ui = hr ? sU[a][cc * 6 + k] : 0.0;
-        const double ur = hr2 ? sU[a + sig][k * 6 + cc] : 0.0;
-        dd = fma(-rl, ul, dd);
-        dd = fma(-lr, ui, dd);
-        un = fma(-lr, ur, un);
-      }
-      sD[a][q] = dd;
-      sN[t][q] = hr2 ? un : 0.0;
-    }
-    // forward reduction of this level's RHS (reads the eliminated slots only)
-    if (!root) {
-      for (int t = 0; t < nk; ++t) {
-        const int a = 2 * sig * t;
-        const bool hl = a >= sig, hr = a + sig < n;
-        for (int r = by * 32 + lane; r < nrhs; r += 32 * kRhsSplit) {
-          double acc = *bcol(a, c, r);
-          if (hl)
-#pragma unroll
-            for (int k = 0; k < 6; ++k) acc = fma(-sR[a - sig][c * 6 + k], *bcol(a - sig, k, r), acc);
-          if (hr)
-#pragma unroll
-            for (int k = 0; k < 6; ++k) acc = fma(-sL[a + sig][c * 6 + k], *bcol(a + sig, k, r), acc);
-          *bcol(a, c, r) = acc;
-        }
-      }
-    }
-    __syncthreads();
-    // new couplings of the kept slots; the slots eliminated at level 2 sig get their left coupling
-    // K_{i-2s, i} = -L_{i-s} U_{i-s}
-    for (int e = tid; e < nk * 36; e += blockDim.x) {
-      const int t = e / 36, q = e % 36, r = q / 6, cc = q % 6, a = 2 * sig * t;
-      if (!root && (a % (4 * sig)) == 2 * sig) {
-        double v = 0.0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) v = fma(-sL[a - sig][r * 6 + k], sU[a - sig][k * 6 + cc], v);
-        sX[t][q] = v;
-      }
-    }
-    __syncthreads();
-    for (int e = tid; e < nk * 36; e += blockDim.x) {
-      const int t = e / 36, q = e % 36, a = 2 * sig * t;
-      if (a + sig < n) sU[a][q] = sN[t][q];
-    }
-    // inverses: P of the slots eliminated at level 2 sig, or of the root (Gauss-Jordan as team_inverse6)
-    for (int k = 0; k < 6; ++k) {
-      __syncthreads();
-      double v[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int e = tid + h * blockDim.x;
-        const int t = e / 36, q = e % 36, r = q / 6, cc = q % 6, a = 2 * sig * t;
-        v[h] = 0.0;
-        if (t < nk && (root || (a % (4 * sig)) == 2 * sig)) {
-          const double akk = sD[a][k * 6 + k];
-          if (!(akk > 0.0)) s_bad = 1;
-          const double pk = __drcp_rn(akk);
-          const double aij = sD[a][r * 6 + cc], aik = sD[a][r * 6 + k], akj = sD[a][k * 6 + cc];
-          if (r == k && cc == k) v[h] = pk;
-          else if (r == k) v[h] = akj * pk;
-          else if (cc == k) v[h] = -aik * pk;
-          else v[h] = aij - aik * akj * pk;
-        }
-      }
-      __syncthreads();
-      if (s_bad) {
-        if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
-        return;
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int e = tid + h * blockDim.x;
-        const int t = e / 36, q = e % 36, a = 2 * sig * t;
-        if (t < nk && (root || (a % (4 * sig)) == 2 * sig)) sD[a][q] = v[h];
-      }
-    }
-    __syncthreads();
-    if (root) break;
-    // L_i = K_{i-2s, i} P_i, R_i = U_i^T P_i for the slots eliminated at level 2 sig
-    for (int e = tid; e < nk * 36; e += blockDim.x) {
-      const int t = e / 36, q = e % 36, r = q / 6, cc = q % 6, a = 2 * sig * t;
-      if ((a % (4 * sig)) == 2 * sig) {
-        double l = 0.0, rr = 0.0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          l = fma(sX[t][r * 6 + k], sD[a][k * 6 + cc], l);
-          rr = fma(sN[t][k * 6 + r], sD[a][k * 6 + cc], rr);
-        }
-        sL[a][q] = l;
-        sR[a][q] = rr;
-        sP[a][q] = sD[a][q];
-      }
-    }
-    __syncthreads();
-  }
-  // root: b_0 after the last forward step, x_0 = P_0 b_0 (P_0 in sD[0])
-  {
-    const bool hr = sig < n;
-    for (int r0 = by * 32; r0 < nrhs; r0 += 32 * kRhsSplit) {
-      const int r = r0 + lane;
-      const bool act = r < nrhs;
-      double acc0 = 0.0;
-      if (act) {
-        acc0 = *bcol(0, c, r);
-        if (hr)
-#pragma unroll
-          for (int k = 0; k < 6; ++k) acc0 = fma(-sL[sig][c * 6 + k], *bcol(sig, k, r), acc0);
-      }
-      __syncthreads();
-      if (act) *bcol(0, c, r) = acc0;
-      __syncthreads();
-      double bb[6];
-      if (act)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) bb[k] = *bcol(0, k, r);
-      __syncthreads();
-      if (act) {
-        double acc = 0.0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) acc = fma(sD[0][c * 6 + k], bb[k], acc);
-        *bcol(0, c, r) = acc;
-      }
-      __syncthreads();
-    }
-  }
-  // back substitution, strides sig .. 1 (slot units): x_a = P_a b_a - L_a^T x_{a-sig} - R_a^T x_{a+sig}
-  for (; sig >= 1; sig >>= 1) {
-    for (int a = sig; a < n; a += 2 * sig) {
-      const bool hr = a + sig < n;
-      for (int r0 = by * 32; r0 < nrhs; r0 += 32 * kRhsSplit) {
-        const int r = r0 + lane;
-        const bool act = r < nrhs;
-        double b[6];
-        if (act)
-#pragma unroll
-          for (int k = 0; k < 6; ++k) b[k] = *bcol(a, k, r);
-        __syncthreads();
-        if (act) {
-          double acc = 0.0;
-#pragma unroll
-          for (int k = 0; k < 6; ++k) acc = fma(sP[a][c * 6 + k], b[k], acc);
-#pragma unroll
-          for (int k = 0; k < 6; ++k) acc = fma(-sL[a][k * 6 + c], *bcol(a - sig, k, r), acc);
-          if (hr)
-#pragma unroll
-            for (int k = 0; k < 6; ++k) acc = fma(-sR[a][k * 6 + c], *bcol(a + sig, k, r), acc);
-          *bcol(a, c, r) = acc;
-        }
-        __syncthreads();
-      }
-    }
-  }
-}
-
-__global__ void __launch_bounds__(192) bcr_tail_kernel(Params p, Dev d) { bcr_tail_body(p, d, blockIdx.y); }
-
-__global__ void __launch_bounds__(192) bcr_tail_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
-  for_units(tab, plan, PH_TAIL, [](const Inst& in, int, int by) { bcr_tail_body(in.p, in.d, by); });
 }
 
 // Back substitution at stride s for eliminated nodes j = s + 2 s blockIdx.x (192 threads).
