@@ -180,6 +180,17 @@ accfem_status accfem_set_precision(accfem_handle* h, int32_t mode);
  * robot's or a modulus is not finite and positive (nothing is changed then). */
 accfem_status accfem_set_element_modulus(accfem_handle* h, const double* youngs_modulus, int32_t n_elements);
 
+/* Frame mode: the paper's real-time scheme, one linearisation per frame (Eq. 20-23 at x_t, the
+ * limited step of Eq. 25-27 gives x_{t+1}).  iters_per_frame > 0: every later solve performs at most
+ * that many Newton iterations and returns ACCFEM_OK when it reaches them, with the state after the
+ * last iteration resident and reported (newton_iters tells how many ran; a solve that converges
+ * earlier stops there).  Each iteration then solves the QP over every detected constraint row (the
+ * working set is all rows), so a frame's state is the paper's step from the previous frame's, and
+ * max_contacts is bounded by the working-set cap (512).  0 restores solves to convergence with the
+ * options' iteration cap.  Call between solves; a batch takes each member's mode when the batch is
+ * created.  E_INVALID_ARG for a negative count or one above 10^6. */
+accfem_status accfem_set_frame_mode(accfem_handle* h, int32_t iters_per_frame);
+
 /* Cumulative bytes copied host->device and device->host by this handle's solve and state calls. */
 accfem_status accfem_transfer_bytes(const accfem_handle* h, int64_t* h2d, int64_t* d2h);
 

@@ -209,9 +209,11 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
   p.max_newton = opt.max_newton_iters;
   h->nf_cap = p.M;
   h->max_newton = opt.max_newton_iters;
+  h->max_newton_opt = opt.max_newton_iters;
   {
     const char* lm = std::getenv("ACCFEM_LAUNCH");
     h->stream_mode = lm && std::strcmp(lm, "stream") == 0;
+    h->pdl = pdl_default();
     const char* tr = std::getenv("ACCFEM_TRACE");
     h->trace = tr && tr[0] == '1';
   }
@@ -374,16 +376,16 @@ namespace {
 // Assembly and RHS columns, then the block cyclic reduction: level-1 eliminations, one kernel per
 // level s that updates the kept nodes, eliminates the next level's nodes (or the root) and reduces
 // the RHS, and the back substitution.  Returns the number of kernels.
-int enqueue_factor(const Params& p, const Dev& d, int nf, cudaStream_t st) {
+int enqueue_factor(const Params& p, const Dev& d, int nf, cudaStream_t st, bool pdl) {
   int n = 0;
   auto grid = [nf](int ph) { return dim3(phase_gx(ph, nf), phase_gy(ph)); };
-  assemble_rhs_kernel<<<grid(PH_ASM), dim3(32, 6), 0, st>>>(p, d); ++n;
-  if (nf >= 2) { bcr_elim_kernel<<<grid(PH_ELIM1), 64, 0, st>>>(p, d, 1); ++n; }
+  launch_k(pdl, assemble_rhs_kernel, grid(PH_ASM), dim3(32, 6), st, p, d); ++n;
+  if (nf >= 2) { launch_k(pdl, bcr_elim_kernel, grid(PH_ELIM1), dim3(64), st, p, d, 1); ++n; }
   int levels = 0;
   while (levels < kMaxLevels && phase_gx(PH_LEV0 + levels, nf) > 0) ++levels;
-  for (int j = 0; j < levels; ++j) { bcr_level_kernel<<<grid(PH_LEV0 + j), 192, 0, st>>>(p, d, 1 << j); ++n; }
+  for (int j = 0; j < levels; ++j) { launch_k(pdl, bcr_level_kernel, grid(PH_LEV0 + j), dim3(192), st, p, d, 1 << j); ++n; }
   for (int j = levels - 1; j >= 0; --j)
-    if (phase_gx(PH_BWD0 + j, nf) > 0) { bcr_bwd_kernel<<<grid(PH_BWD0 + j), 192, 0, st>>>(p, d, 1 << j); ++n; }
+    if (phase_gx(PH_BWD0 + j, nf) > 0) { launch_k(pdl, bcr_bwd_kernel, grid(PH_BWD0 + j), dim3(192), st, p, d, 1 << j); ++n; }
   return n;
 }
 
@@ -396,16 +398,17 @@ int enqueue_iteration(accfem_handle* h, int nf, cudaStream_t st, cudaGraphCondit
   // join before the assembly (captured as parallel graph nodes)
   cudaEventRecord(h->fork, st);
   cudaStreamWaitEvent(h->side, h->fork, 0);
-  element_kernel<<<grid(PH_ELEM), 32 * kWarpsPerElemBlock, 0, h->side>>>(p, d); ++n;
+  const bool pdl = h->pdl;
+  launch_k(pdl, element_kernel, grid(PH_ELEM), dim3(32 * kWarpsPerElemBlock), h->side, p, d); ++n;
   cudaEventRecord(h->join, h->side);
-  collide_kernel<<<grid(PH_COLL), 128, 0, st>>>(p, d); ++n;
-  compact_kernel<<<1, 1024, 0, st>>>(p, d); ++n;
+  launch_k(pdl, collide_kernel, grid(PH_COLL), dim3(128), st, p, d); ++n;
+  launch_k(pdl, compact_kernel, dim3(1), dim3(1024), st, p, d); ++n;
   cudaStreamWaitEvent(st, h->join, 0);
-  n += enqueue_factor(p, d, nf, st);
-  contact_kernel<<<1, 256, 0, st>>>(p, d); ++n;
-  step_kernel<<<grid(PH_STEP), dim3(32, 6), 0, st>>>(p, d); ++n;
-  apply_kernel<<<grid(PH_APPLY), 128, 0, st>>>(p, d); ++n;
-  ctl_kernel<<<1, 1, 0, st>>>(p, d, cond, h->max_newton, h->stream_mode ? 0 : 1); ++n;
+  n += enqueue_factor(p, d, nf, st, pdl);
+  launch_k(pdl, contact_kernel, dim3(1), dim3(256), st, p, d); ++n;
+  launch_k(pdl, step_kernel, grid(PH_STEP), dim3(32, 6), st, p, d); ++n;
+  launch_k(pdl, apply_kernel, grid(PH_APPLY), dim3(128), st, p, d); ++n;
+  launch_k(pdl, ctl_kernel, dim3(1), dim3(1), st, p, d, cond, h->max_newton, h->stream_mode ? 0 : 1); ++n;
   return n;
 }
 
@@ -440,6 +443,11 @@ const accfem_handle::LoopGraph* newton_graph(accfem_handle* h, int nf) {
   if (!cuda_ok(h, ce, "end capture") || !cuda_ok(h, cudaGraphInstantiate(&lg.exec, lg.graph, 0), "instantiate graph")) {
     cudaGetLastError();
     cudaGraphDestroy(lg.graph);
+    if (h->pdl) {                 // programmatic edges refused inside the loop body: capture without them
+      std::fprintf(stderr, "accfem: programmatic dependent launch refused in the Newton graph; plain launches\n");
+      h->pdl = false;
+      return newton_graph(h, nf);
+    }
     return nullptr;
   }
   auto res = h->graphs.emplace(nf, lg);
@@ -462,6 +470,7 @@ accfem_status run_solve(accfem_handle* h, int load_mode, const double* tensions_
   c.rho = p.beta0;
   c.load_mode = load_mode;
   c.delta = insertion;
+  c.frame = h->frame_iters > 0 ? 1 : 0;
   if (load_mode == 0 && tensions_host) {
     for (int j = 0; j < p.n_cables; ++j) {
       if (!(tensions_host[j] >= 0.0) || !std::isfinite(tensions_host[j]))
@@ -531,6 +540,7 @@ accfem_status run_solve(accfem_handle* h, int load_mode, const double* tensions_
       }
       if (c.converged) { status = ACCFEM_OK; break; }
     }
+    if (status == ACCFEM_E_NOT_CONVERGED && c.frame) status = ACCFEM_OK;
   } else if (nf > 0) {
     const accfem_handle::LoopGraph* lg = newton_graph(h, nf);
     if (!lg) return ACCFEM_E_CUDA;
@@ -541,7 +551,7 @@ accfem_status run_solve(accfem_handle* h, int load_mode, const double* tensions_
     h->d2h += sizeof(Ctl);
     h->launches += (int64_t)c.loops * lg->body_kernels;
     if (c.status != 0) status = (accfem_status)c.status;
-    else if (c.converged) status = ACCFEM_OK;
+    else if (c.converged || c.frame) status = ACCFEM_OK;
     else status = ACCFEM_E_NOT_CONVERGED;
     if (status != ACCFEM_OK) h->err = accfem_solve_message(c, status);
   } else {
@@ -670,6 +680,22 @@ accfem_status accfem_set_precision(accfem_handle* h, int32_t mode) {
   return ACCFEM_OK;
 }
 
+accfem_status accfem_set_frame_mode(accfem_handle* h, int32_t iters_per_frame) {
+  if (!h || iters_per_frame < 0 || iters_per_frame > 1000000) return ACCFEM_E_INVALID_ARG;
+  if (h->frame_iters == iters_per_frame) return ACCFEM_OK;
+  if (h->stream) cudaStreamSynchronize(h->work());
+  for (auto& kv : h->graphs) {     // the Newton graphs captured the iteration cap and the constants
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  h->graphs.clear();
+  h->frame_iters = iters_per_frame;
+  h->max_newton = iters_per_frame > 0 ? iters_per_frame : h->max_newton_opt;
+  h->p.max_newton = h->max_newton;
+  h->p.ws_all = iters_per_frame > 0 ? 1 : 0;
+  return ACCFEM_OK;
+}
+
 accfem_status accfem_set_element_modulus(accfem_handle* h, const double* youngs_modulus, int32_t n_elements) {
   if (!h || n_elements != h->p.M) return ACCFEM_E_INVALID_ARG;
   const int M = h->p.M;
@@ -732,7 +758,7 @@ accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t
       case ACCFEM_KERNEL_COLLIDE: collide_kernel<<<phase_gx(PH_COLL, nf), 128, 0, st>>>(p, d); break;
       case ACCFEM_KERNEL_ASSEMBLE:
         assemble_rhs_kernel<<<dim3(phase_gx(PH_ASM, nf), phase_gy(PH_ASM)), dim3(32, 6), 0, st>>>(p, d); break;
-      case ACCFEM_KERNEL_FACTOR: per_launch = enqueue_factor(p, d, nf, st); break;
+      case ACCFEM_KERNEL_FACTOR: per_launch = enqueue_factor(p, d, nf, st, h->pdl); break;
       default: contact_kernel<<<1, 256, 0, st>>>(p, d); break;
     }
   };

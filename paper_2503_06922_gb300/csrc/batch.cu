@@ -5,6 +5,7 @@
 // stages a solve, accfem_batch_advance starts the staged solves and runs a bounded number of
 // iterations of everything in flight inside one CUDA graph (a conditional WHILE node whose body
 // ends with the plan kernel), and finished members are collected with one gather and one copy.
+#include <cstdio>
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -90,19 +91,20 @@ int enqueue_batch_iteration(accfem_batch* b, cudaStream_t st, cudaGraphCondition
   // the element phase and the collision + compaction phases both only read the poses: two branches
   cudaEventRecord(b->fork, st);
   cudaStreamWaitEvent(b->side, b->fork, 0);
-  element_batch<<<g[PH_ELEM], 32 * kWarpsPerElemBlock, 0, b->side>>>(tab, plan); ++n;
+  const bool pdl = b->pdl;
+  launch_k(pdl, element_batch, dim3(g[PH_ELEM]), dim3(32 * kWarpsPerElemBlock), b->side, tab, plan); ++n;
   cudaEventRecord(b->join, b->side);
-  collide_batch<<<g[PH_COLL], 128, 0, st>>>(tab, plan); ++n;
-  compact_batch<<<g[PH_COMPACT], 1024, 0, st>>>(tab, plan); ++n;
+  launch_k(pdl, collide_batch, dim3(g[PH_COLL]), dim3(128), st, tab, plan); ++n;
+  launch_k(pdl, compact_batch, dim3(g[PH_COMPACT]), dim3(1024), st, tab, plan); ++n;
   cudaStreamWaitEvent(st, b->join, 0);
-  assemble_rhs_batch<<<g[PH_ASM], dim3(32, 6), 0, st>>>(tab, plan); ++n;
-  bcr_elim_batch<<<g[PH_ELIM1], 64, 0, st>>>(tab, plan); ++n;
-  for (int j = 0; j < b->levels; ++j) { bcr_level_batch<<<g[PH_LEV0 + j], 192, 0, st>>>(tab, plan, j); ++n; }
-  for (int j = b->levels - 1; j >= 0; --j) { bcr_bwd_batch<<<g[PH_BWD0 + j], 192, 0, st>>>(tab, plan, j); ++n; }
-  contact_batch<<<g[PH_CONTACT], 256, 0, st>>>(tab, plan); ++n;
-  step_batch<<<g[PH_STEP], dim3(32, 6), 0, st>>>(tab, plan); ++n;
-  apply_batch<<<g[PH_APPLY], 128, 0, st>>>(tab, plan); ++n;
-  batch_plan_kernel<<<1, 1024, 0, st>>>(tab, plan, b->n, 1, 0, cond, set_cond); ++n;
+  launch_k(pdl, assemble_rhs_batch, dim3(g[PH_ASM]), dim3(32, 6), st, tab, plan); ++n;
+  launch_k(pdl, bcr_elim_batch, dim3(g[PH_ELIM1]), dim3(64), st, tab, plan); ++n;
+  for (int j = 0; j < b->levels; ++j) { launch_k(pdl, bcr_level_batch, dim3(g[PH_LEV0 + j]), dim3(192), st, tab, plan, j); ++n; }
+  for (int j = b->levels - 1; j >= 0; --j) { launch_k(pdl, bcr_bwd_batch, dim3(g[PH_BWD0 + j]), dim3(192), st, tab, plan, j); ++n; }
+  launch_k(pdl, contact_batch, dim3(g[PH_CONTACT]), dim3(256), st, tab, plan); ++n;
+  launch_k(pdl, step_batch, dim3(g[PH_STEP]), dim3(32, 6), st, tab, plan); ++n;
+  launch_k(pdl, apply_batch, dim3(g[PH_APPLY]), dim3(128), st, tab, plan); ++n;
+  launch_k(pdl, batch_plan_kernel, dim3(1), dim3(1024), st, tab, plan, b->n, 1, 0, cond, set_cond); ++n;
   return n;
 }
 
@@ -153,6 +155,14 @@ bool build_graph(accfem_batch* b, int v) {
   cudaError_t ce = cudaStreamEndCapture(st, &body);
   if (!bok(b, ce, "end capture") || !bok(b, cudaGraphInstantiate(&g.exec, g.graph, 0), "instantiate graph")) {
     cudaGetLastError();
+    cudaGraphDestroy(g.graph);
+    g.graph = nullptr;
+    g.exec = nullptr;
+    if (b->pdl) {                 // programmatic edges refused inside the loop body: capture without them
+      std::fprintf(stderr, "accfem: programmatic dependent launch refused in the batch graph; plain launches\n");
+      b->pdl = false;
+      return build_graph(b, v);
+    }
     return false;
   }
   for (int ph = 0; ph < kPhases; ++ph) g.grid[ph] = b->grid[ph];
@@ -234,6 +244,7 @@ accfem_status accfem_batch_create(accfem_handle* const* members, int32_t n_membe
   {
     const char* lm = std::getenv("ACCFEM_LAUNCH");
     b->stream_mode = lm && std::strcmp(lm, "stream") == 0;
+    b->pdl = pdl_default();
   }
   bool ok = bok(b, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "cudaStreamCreate") &&
             bok(b, cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking), "cudaStreamCreate") &&
@@ -292,6 +303,7 @@ accfem_status accfem_batch_begin(accfem_batch* b, int32_t member, const double* 
   c.load_mode = 0;
   c.delta = insertion;
   c.live = c.nf > 0 ? 1 : 0;
+  c.frame = h->frame_iters > 0 ? 1 : 0;
   for (int j = 0; j < p.n_cables; ++j) c.tension[j] = cable_tensions[j];
   BatchBegin& g = b->h_begin[b->n_begin];
   g.member = member;

@@ -80,6 +80,7 @@ __host__ __device__ inline int phase_gy(int ph) {
 template <class Body>
 __device__ __forceinline__ void for_units(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int ph, Body body) {
   __shared__ int s_pre[kMaxBatch + 1];
+  pdl_enter();
   const int na = plan->n_act;
   const int total = plan->pre[ph][na];
   if ((int)blockIdx.x >= total) return;

@@ -52,6 +52,7 @@ struct accfem_batch {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int body_kernels = 0;
   bool stream_mode = false;         // ACCFEM_LAUNCH=stream: host-driven passes (kernels visible to profilers)
+  bool pdl = false;                 // programmatic dependent launch of the phase kernels (ACCFEM_PDL=1)
   int grid[accfem::kPhases] = {};
   int64_t launches = 0, h2d = 0, d2h = 0;
   std::string err;
@@ -72,6 +73,6 @@ inline bool bok(accfem_batch* b, cudaError_t e, const char* what) {
 // Outcome of a finished solve from its control block.
 inline accfem_status outcome(const Ctl& c) {
   if (c.status != 0) return (accfem_status)c.status;
-  if (c.nf == 0 || c.converged) return ACCFEM_OK;
+  if (c.nf == 0 || c.converged || c.frame) return ACCFEM_OK;
   return ACCFEM_E_NOT_CONVERGED;
 }

@@ -54,7 +54,8 @@ __device__ __forceinline__ int block_excl_scan_1024(int v, int* s_warp, int* tot
 // One CTA: exclusive scan of the per-node row counts, row arrays in (node, triangle) order,
 // comparison with the previous iteration's rows (flags carried by identity), the working set of
 // the contact solve, copy to "previous".  Working set: rows active in the previous iteration, rows
-// violated by an applied step in this solve (they stay), and rows whose gap is at most ws_gap;
+// violated by an applied step in this solve (they stay), and rows whose gap is at most ws_gap (all
+// rows in frame mode, where every iteration is a reported state and solves the QP of Eq. 23 whole);
 // slots follow the row order.
 __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   __shared__ int s_warp[32];
@@ -120,7 +121,7 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   int nw = 0;
   for (int r = r0; r < r1; ++r) {
     const int fl = d.init_flag[r];
-    nw += ((fl > 0 && (fl & keep_mask)) || d.c_gap[r] <= ws_gap) ? 1 : 0;
+    nw += (p.ws_all || (fl > 0 && (fl & keep_mask)) || d.c_gap[r] <= ws_gap) ? 1 : 0;
   }
   int mc = 0;
   int slot = block_excl_scan_1024(nw, s_warp, &mc);
@@ -130,7 +131,7 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   }
   for (int r = r0; r < r1; ++r) {
     const int fl = d.init_flag[r];
-    if ((fl > 0 && (fl & keep_mask)) || d.c_gap[r] <= ws_gap) {
+    if (p.ws_all || (fl > 0 && (fl & keep_mask)) || d.c_gap[r] <= ws_gap) {
       d.wrow[slot] = r;
       d.rslot[r] = slot++;
     } else {
@@ -147,7 +148,10 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   if (tid == 0) { ctl->same_set = s_same; ctl->m = m; ctl->m_prev = m; ctl->mc = mc; }
 }
 
-__global__ void __launch_bounds__(1024) compact_kernel(Params p, Dev d) { compact_body(p, d); }
+__global__ void __launch_bounds__(1024) compact_kernel(Params p, Dev d) {
+  pdl_enter();
+  compact_body(p, d);
+}
 
 __global__ void __launch_bounds__(1024) compact_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
   for_units(tab, plan, PH_COMPACT, [](const Inst& in, int, int) { compact_body(in.p, in.d); });
@@ -223,6 +227,7 @@ __device__ __forceinline__ void assemble_rhs_body(const Params& p, const Dev& d,
 }
 
 __global__ void __launch_bounds__(192) assemble_rhs_kernel(Params p, Dev d) {
+  pdl_enter();
   assemble_rhs_body(p, d, blockIdx.x, blockIdx.y);
 }
 
@@ -290,7 +295,10 @@ __device__ __forceinline__ void bcr_elim_body(const Params& p, const Dev& d, int
   }
 }
 
-__global__ void __launch_bounds__(64) bcr_elim_kernel(Params p, Dev d, int s) { bcr_elim_body(p, d, blockIdx.x, s); }
+__global__ void __launch_bounds__(64) bcr_elim_kernel(Params p, Dev d, int s) {
+  pdl_enter();
+  bcr_elim_body(p, d, blockIdx.x, s);
+}
 
 __global__ void __launch_bounds__(64) bcr_elim_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
   for_units(tab, plan, PH_ELIM1, [](const Inst& in, int bx, int) { bcr_elim_body(in.p, in.d, bx, 1); });
@@ -430,6 +438,7 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
 }
 
 __global__ void __launch_bounds__(192) bcr_level_kernel(Params p, Dev d, int s) {
+  pdl_enter();
   bcr_level_body(p, d, blockIdx.x, blockIdx.y, s);
 }
 
@@ -483,7 +492,10 @@ __device__ __forceinline__ void bcr_bwd_body(const Params& p, const Dev& d, int 
   }
 }
 
-__global__ void __launch_bounds__(192) bcr_bwd_kernel(Params p, Dev d, int s) { bcr_bwd_body(p, d, blockIdx.x, blockIdx.y, s); }
+__global__ void __launch_bounds__(192) bcr_bwd_kernel(Params p, Dev d, int s) {
+  pdl_enter();
+  bcr_bwd_body(p, d, blockIdx.x, blockIdx.y, s);
+}
 
 __global__ void __launch_bounds__(192) bcr_bwd_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j) {
   for_units(tab, plan, PH_BWD0 + j, [j](const Inst& in, int bx, int by) { bcr_bwd_body(in.p, in.d, bx, by, 1 << j); });

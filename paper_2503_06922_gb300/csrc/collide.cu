@@ -241,7 +241,10 @@ __device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int 
   if (lane == 0) d.ncon[f] = nc;
 }
 
-__global__ void __launch_bounds__(128) collide_kernel(Params p, Dev d) { collide_body(p, d, blockIdx.x); }
+__global__ void __launch_bounds__(128) collide_kernel(Params p, Dev d) {
+  pdl_enter();
+  collide_body(p, d, blockIdx.x);
+}
 
 __global__ void __launch_bounds__(128) collide_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
   for_units(tab, plan, PH_COLL, [](const Inst& in, int bx, int) { collide_body(in.p, in.d, bx); });

@@ -52,6 +52,7 @@ struct Params {
   int ws_cap;                    // max rows of the working set (<= kMaxWorking)
   int nrhs_cap;                  // 1 + ws_cap RHS columns
   double ws_gap;                 // a row whose gap is at most this joins the working set
+  int ws_all;                    // every constraint row is in the working set (frame mode)
   int max_newton;                // Newton iteration cap of a solve
   int precision;                 // kPrecisionFP64 or kPrecisionMixed (FP32 element tangent)
 };
@@ -80,10 +81,21 @@ struct Ctl {
   int mc;                // rows of the working set (RHS columns 1..mc)
   int incomplete;        // a row outside the working set is violated by this iteration's step
   int fp64_tangent;      // mixed precision: this solve fell back to the FP64 element tangent
+  int frame;             // frame mode: reaching the iteration cap is the normal end of a solve
   double delta;          // insertion of the resident state
   double tension[kMaxCables];
   double tip_f[3], tip_m[3];
 };
+
+// Programmatic dependent launch.  A kernel launched with programmatic stream serialization may
+// start while its predecessor in the stream is still running: pdl_wait() blocks until that
+// predecessor has completed and its writes are visible (a no-op for a kernel launched without the
+// attribute), so every such kernel calls it before its first access to global memory.
+// pdl_trigger() then lets the successor launch and wait in turn, so that at most one kernel waits
+// ahead of the running one.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() { pdl_wait(); pdl_trigger(); }
 
 // Flags ST_CAPACITY (the first error of an iteration wins) and records its cause.
 __device__ __forceinline__ void flag_capacity(Ctl* c, int code) {

@@ -303,7 +303,10 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
   }
 }
 
-__global__ void __launch_bounds__(kLcpThreads) contact_kernel(Params p, Dev d) { contact_body(p, d); }
+__global__ void __launch_bounds__(kLcpThreads) contact_kernel(Params p, Dev d) {
+  pdl_enter();
+  contact_body(p, d);
+}
 
 __global__ void __launch_bounds__(kLcpThreads) contact_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
   for_units(tab, plan, PH_CONTACT, [](const Inst& in, int, int) { contact_body(in.p, in.d); });

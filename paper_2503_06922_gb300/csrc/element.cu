@@ -256,6 +256,7 @@ __device__ __forceinline__ bool mixed_tangent(const Params& p, const Dev& d) {
 }
 
 __global__ void __launch_bounds__(32 * kWarpsPerElemBlock) element_kernel(Params p, Dev d) {
+  pdl_enter();
   if (mixed_tangent(p, d)) element_body<true>(p, d, blockIdx.x);
   else element_body<false>(p, d, blockIdx.x);
 }

@@ -61,7 +61,10 @@ __device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx)
   }
 }
 
-__global__ void __launch_bounds__(192) step_kernel(Params p, Dev d) { step_body(p, d, blockIdx.x); }
+__global__ void __launch_bounds__(192) step_kernel(Params p, Dev d) {
+  pdl_enter();
+  step_body(p, d, blockIdx.x);
+}
 
 __global__ void __launch_bounds__(192) step_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
   for_units(tab, plan, PH_STEP, [](const Inst& in, int bx, int) { step_body(in.p, in.d, bx); });
@@ -141,7 +144,10 @@ __device__ __forceinline__ void apply_body(const Params& p, const Dev& d, int bx
   }
 }
 
-__global__ void __launch_bounds__(128) apply_kernel(Params p, Dev d) { apply_body(p, d, blockIdx.x); }
+__global__ void __launch_bounds__(128) apply_kernel(Params p, Dev d) {
+  pdl_enter();
+  apply_body(p, d, blockIdx.x);
+}
 
 __global__ void __launch_bounds__(128) apply_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
   for_units(tab, plan, PH_APPLY, [](const Inst& in, int bx, int) { apply_body(in.p, in.d, bx); });
@@ -177,6 +183,7 @@ __device__ __forceinline__ void ctl_update(const Params& p, const Dev& d) {
 }
 
 __global__ void ctl_kernel(Params p, Dev d, cudaGraphConditionalHandle h, int max_iter, int set_cond) {
+  pdl_enter();
   Ctl* c = d.ctl;
   ctl_update(p, d);
   if (set_cond) {
@@ -277,6 +284,7 @@ __global__ void __launch_bounds__(1024) batch_plan_kernel(const Inst* __restrict
                                                           int max_passes, cudaGraphConditionalHandle h, int set_cond) {
   __shared__ int s_warp[32];
   __shared__ int s_nf[kMaxBatch];
+  pdl_enter();
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   int go = 0, nf = 0;
   if (tid < n_inst) {
