@@ -54,7 +54,9 @@ def parse():
                     help="run the first N solves of the sweep once (for profilers) and exit")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="run N instances of the batched workload through their first steps (for profilers) and exit")
-    ap.add_argument("--no-extra", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched, served, tree-precision and frame-mode measurements")
+    ap.add_argument("--frames-only", action="store_true", help="run the frame-mode measurement alone and exit")
     ap.add_argument("--serve-requests", type=int, default=1200, help="requests of each served request stream")
     return ap.parse_args()
 
@@ -412,6 +414,61 @@ def tree_precision_run(af):
     return out
 
 
+def frames_run(af, node_counts=(100, 200, 300, 400), frames_per_step=5):
+    """The paper's per-timestep experiment (Sec. IV.A: computation time per timestep against the
+    number of contacts, robots of 100, 200, 300 and 400 nodes) in frame mode, one linearisation of
+    Eq. 20-23 per frame: the 600 mm robot with 99..399 elements in the benchmark's Catmull-Rom tube,
+    insertion swept 0 -> 600 mm in 60 steps of frames_per_step frames each.  Per frame: the device
+    time of one accfem_solve_resident call (CUDA events on the library's stream; graph launch,
+    iteration and control read-back) and the rows active in its contact solve."""
+    import torch
+    from dataclasses import replace
+    w0 = workload()
+    S = len(w0.insertions)
+    tens = torch.tensor(w0.tensions, dtype=torch.float64, device="cuda")
+    row_bytes = 8 * tens.shape[1]
+    bins = ((0, 0), (1, 4), (5, 9), (10, 19), (20, 10 ** 6))
+    out = {}
+    for nn in node_counts:
+        rob = replace(w0.robot, n_elements=nn - 1)
+        h = af.AccFem(rob, w0.lumen, max_contacts=512)
+        h.accfem_set_frame_mode(1)
+        stream = torch.cuda.Stream()
+        h.accfem_set_stream(stream.cuda_stream)
+        recs = []
+        with torch.cuda.stream(stream):
+            for rep in range(2):                 # the first pass captures the graphs
+                h.accfem_reset()
+                for s in range(S):
+                    for f in range(frames_per_step):
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        st, it = h.accfem_solve_resident(tens.data_ptr() + s * row_bytes, float(w0.insertions[s]))
+                        e1.record(stream)
+                        e1.synchronize()
+                        if rep == 1:
+                            rows, working, active, _ = h.accfem_solve_stats()
+                            recs.append((e0.elapsed_time(e1), active, rows, st))
+        h.close()
+        ms = np.array([r[0] for r in recs])
+        act = np.array([r[1] for r in recs])
+        by = {}
+        for lo, hi in bins:
+            sel = (act >= lo) & (act <= hi)
+            if sel.any():
+                by["%d-%d" % (lo, hi) if hi < 10 ** 6 else "%d+" % lo] = {"frames": int(sel.sum()),
+                                                                          "ms_mean": float(ms[sel].mean())}
+        out[str(nn)] = {"frames": len(recs), "ms_per_frame": float(ms.mean()), "ms_p50": float(np.percentile(ms, 50)),
+                        "ms_p99": float(np.percentile(ms, 99)), "frames_per_s": float(1e3 / ms.mean()),
+                        "max_active": int(act.max()), "max_rows": int(max(r[2] for r in recs)),
+                        "failed": int(sum(r[3] != af.OK for r in recs)), "ms_by_active_contacts": by}
+        progress("frames: %d nodes, %.3f ms per frame, up to %d active contacts" % (nn, ms.mean(), act.max()))
+    out["workload"] = ("600 mm robot in %s, insertion 0->600 mm in %d steps x %d frames, one Newton iteration per "
+                       "frame (frame mode)" % (w0.name, S, frames_per_step))
+    return out
+
+
 def profile_batch_run(args):
     """The first 6 steps of the first N instances of the batched workload, in one batch (for ncu
     captures; with ACCFEM_LAUNCH=stream the phase kernels are launched from a host loop)."""
@@ -598,6 +655,7 @@ def ours(args, rank, world, local_rank):
         extra["batched"] = batched_run(af)
         extra["served"] = served_run(af, requests=args.serve_requests)
         extra["precision_tree"] = tree_precision_run(af)
+        extra["frames"] = frames_run(af)
     if rank == 0:
         cpu_n, cpu_dt = oracle_sample(w, 15.0)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -653,6 +711,11 @@ def main():
         return profile_run(args)
     if args.profile_batch:
         return profile_batch_run(args)
+    if args.frames_only:
+        from paper_2503_06922_gb300 import accfem as af
+        af.load()
+        print(json.dumps({"frames": frames_run(af)}), flush=True)
+        return 0
     return ours(args, rank, world, local_rank)
 
 
