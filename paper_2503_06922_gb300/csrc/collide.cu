@@ -48,48 +48,73 @@ __device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int 
   }
   const int ncell = nc3[0] * nc3[1] * nc3[2];
   const float thr32 = (float)(thr + p.eps_d);
-  // Walk of the cells around the node: cell ranges loaded by the lanes, triangles by the lanes; for
-  // every 32 slots visit(slot, within, dd, near) is called by the whole warp (within: FP32 distance
-  // dd <= r_o + gap + eps_d; near: FP32 barycentrics inside the face band up to eps_b).
+  // Walk of the cells around the node: up to 32 cells at a time, their slot ranges loaded by the
+  // lanes and scanned into one index space, so that every round tests 32 slots of any cells (lane
+  // j finds its slot's cell by a binary search over the scanned counts) and two rounds' loads are
+  // in flight together.  For every 32 slots visit(slot, within, dd, near) is called by the whole
+  // warp (within: FP32 distance dd <= r_o + gap + eps_d; near: FP32 barycentrics inside the face
+  // band up to eps_b; slots past the end come with within = false).
   auto walk = [&](auto&& visit) {
     for (int c0 = 0; c0 < ncell; c0 += 32) {
-      int cs0 = 0, cs1 = 0, cx = 0, cy = 0, cz = 0;
+      int cs0 = 0, cnt = 0;
+      float pcx = 0.f, pcy = 0.f, pcz = 0.f;
       if (c0 + lane < ncell) {
-        int q = c0 + lane;
-        cx = lo[0] + q % nc3[0];
-        cy = lo[1] + (q / nc3[0]) % nc3[1];
-        cz = lo[2] + q / (nc3[0] * nc3[1]);
-        int cell = (cz * p.g_dim[1] + cy) * p.g_dim[0] + cx;
+        const int q = c0 + lane;
+        const int cx = lo[0] + q % nc3[0];
+        const int cy = lo[1] + (q / nc3[0]) % nc3[1];
+        const int cz = lo[2] + q / (nc3[0] * nc3[1]);
+        const int cell = (cz * p.g_dim[1] + cy) * p.g_dim[0] + cx;
         cs0 = d.cell_start[cell];
-        cs1 = d.cell_start[cell + 1];
+        cnt = d.cell_start[cell + 1] - cs0;
+        pcx = (float)(pn[0] - (p.g_org[0] + (cx + 0.5) * p.g_h));
+        pcy = (float)(pn[1] - (p.g_org[1] + (cy + 0.5) * p.g_h));
+        pcz = (float)(pn[2] - (p.g_org[2] + (cz + 0.5) * p.g_h));
       }
-      unsigned nonempty = __ballot_sync(0xffffffffu, cs1 > cs0);
-      while (nonempty) {
-        const int src = __ffs(nonempty) - 1;
-        nonempty &= nonempty - 1;
-        const int s0 = __shfl_sync(0xffffffffu, cs0, src), s1 = __shfl_sync(0xffffffffu, cs1, src);
-        const int gx = __shfl_sync(0xffffffffu, cx, src), gy = __shfl_sync(0xffffffffu, cy, src),
-                  gz = __shfl_sync(0xffffffffu, cz, src);
-        const float pc[3] = {(float)(pn[0] - (p.g_org[0] + (gx + 0.5) * p.g_h)),
-                             (float)(pn[1] - (p.g_org[1] + (gy + 0.5) * p.g_h)),
-                             (float)(pn[2] - (p.g_org[2] + (gz + 0.5) * p.g_h))};
-        for (int s0l = s0; s0l < s1; s0l += 32) {
-          const int s = s0l + lane;
-          bool within = false, near_in = false;
-          float dd = 0.f;
-          if (s < s1) {
-            float4 sp = reinterpret_cast<const float4*>(d.sph32)[s];
-            float dx = pc[0] - sp.x, dy = pc[1] - sp.y, dz = pc[2] - sp.z, rr = thr32 + sp.w;
+      int incl = cnt;                              // inclusive scan of the slot counts over the lanes
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      const int excl = incl - cnt;
+      for (int j0 = 0; j0 < total; j0 += 64) {
+        int s[2];
+        bool within[2] = {false, false}, near_in[2] = {false, false};
+        float dd[2] = {0.f, 0.f}, pc[2][3];
+        float4 sp[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = j0 + 32 * h + lane;
+          const int jc = min(j, total - 1);
+          int own = 0;                             // lanes (cells) whose slots all precede jc
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            const int v = __shfl_sync(0xffffffffu, incl, own + step - 1);
+            if (v <= jc) own += step;
+          }
+          s[h] = __shfl_sync(0xffffffffu, cs0, own) + (jc - __shfl_sync(0xffffffffu, excl, own));
+          pc[h][0] = __shfl_sync(0xffffffffu, pcx, own);
+          pc[h][1] = __shfl_sync(0xffffffffu, pcy, own);
+          pc[h][2] = __shfl_sync(0xffffffffu, pcz, own);
+          if (j < total) sp[h] = reinterpret_cast<const float4*>(d.sph32)[s[h]];
+          if (j >= total) s[h] = -1;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (s[h] >= 0) {
+            float dx = pc[h][0] - sp[h].x, dy = pc[h][1] - sp[h].y, dz = pc[h][2] - sp[h].z, rr = thr32 + sp[h].w;
             if (dx * dx + dy * dy + dz * dz <= rr * rr) {
               float va, vb, vc;
-              dd = sqrtf(tri_dist2_f32(pc, d.tri32 + (size_t)s * 9, va, vb, vc));
+              dd[h] = sqrtf(tri_dist2_f32(pc[h], d.tri32 + (size_t)s[h] * 9, va, vb, vc));
               float tol = -((float)kFaceBand + p.eps_b) * (va + vb + vc);
-              near_in = (va >= tol) && (vb >= tol) && (vc >= tol);
-              within = dd <= thr32;
+              near_in[h] = (va >= tol) && (vb >= tol) && (vc >= tol);
+              within[h] = dd[h] <= thr32;
             }
           }
-          visit(s, within, dd, near_in);
         }
+        visit(s[0], within[0], dd[0], near_in[0]);
+        if (j0 + 32 < total) visit(s[1], within[1], dd[1], near_in[1]);
       }
     }
   };
