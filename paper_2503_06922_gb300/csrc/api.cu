@@ -327,7 +327,7 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
        dalloc(h, &d.con_pt, (size_t)nfc * kCpn * 3) && dalloc(h, &d.con_n, (size_t)nfc * kCpn * 3) &&
        dalloc(h, &d.con_gap, (size_t)nfc * kCpn) && dalloc(h, &d.c_node, mc) && dalloc(h, &d.c_tri, mc) &&
        dalloc(h, &d.c_pt, 3 * mc) && dalloc(h, &d.c_n, 3 * mc) && dalloc(h, &d.c_gap, mc) &&
-       dalloc(h, &d.c_first, nfc + 1) && dalloc(h, &d.p_node, mc) && dalloc(h, &d.p_tri, mc) &&
+       dalloc(h, &d.c_first, nfc + 1) && dalloc(h, &d.p_node, mc) && dalloc(h, &d.p_tri, mc) && dalloc(h, &d.p_first, nfc + 1) &&
        dalloc(h, &d.p_flag, mc) && dalloc(h, &d.init_flag, mc) && dalloc(h, &d.wrow, wc) &&
        dalloc(h, &d.rslot, mc) &&
        dalloc(h, &d.D, (size_t)nfc * 36) && dalloc(h, &d.U, (size_t)nfc * 36) && dalloc(h, &d.P, (size_t)nfc * 36) &&

@@ -93,14 +93,16 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   if (tid == 0) d.c_first[nf] = m;
   __syncthreads();
   const int mp = ctl->m_prev;
-  // flags of the same row (node, triangle) in the previous iteration; -1 for a new row
+  // flags of the same row (node, triangle) in the previous iteration; -1 for a new row.  The node's
+  // previous rows are [p_first[f], p_first[f+1]) (at most kCpn; none before the first compaction)
   for (int r = tid; r < m; r += 1024) {
-    int nd = d.c_node[r], tr = d.c_tri[r], lo = 0, hi = mp - 1, found = -1;
-    while (lo <= hi) {                       // previous rows are ordered by (node, triangle)
-      int mid = (lo + hi) >> 1;
-      int pn = d.p_node[mid], pt = d.p_tri[mid];
-      if (pn == nd && pt == tr) { found = mid; break; }
-      if (pn < nd || (pn == nd && pt < tr)) lo = mid + 1; else hi = mid - 1;
+    const int nd = d.c_node[r], tr = d.c_tri[r];
+    int found = -1;
+    if (mp >= 0) {
+      const int q0 = d.p_first[nd], q1 = d.p_first[nd + 1];
+#pragma unroll 4
+      for (int q = q0; q < q1; ++q)
+        if (d.p_tri[q] == tr) found = q;
     }
     d.init_flag[r] = found >= 0 ? d.p_flag[found] : -1;
   }
@@ -139,6 +141,7 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
     }
   }
   __syncthreads();
+  for (int f = tid; f <= nf; f += 1024) d.p_first[f] = d.c_first[f];
   for (int r = tid; r < m; r += 1024) {
     const int fl = d.init_flag[r];
     d.p_node[r] = d.c_node[r];
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(64) bcr_elim_batch(const Inst* __restrict__ ta
 // R_i = U_i^T P_i.  Every block applies the level-s forward reduction to its RHS chunks.  When
 // 2s >= nf only node 0 is kept: every block inverts D_0 itself (root) and solves x_0 = P_0 b_0.
 __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, int bx, int by, int s) {
-  __shared__ double sRl[36], sUl[36], sLr[36], sUi[36], sUr[36], sA[36], sX[36], sY[36];
+  __shared__ double sRl[36], sUl[36], sLl[36], sLr[36], sUi[36], sUr[36], sA[36], sX[36], sY[36];
   __shared__ double s_piv[1];
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
@@ -322,9 +325,26 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
   const bool hl = i >= s, hr = i + s < nf, hr2 = i + 2 * s < nf;
   const bool root = 2 * s >= nf;                       // only node 0 remains after this level
   const bool elim2 = !root && (i % (4 * s)) == 2 * s;   // i is eliminated at level 2s
+  // RHS values of this block's first column chunk, loaded with the blocks so that the two
+  // latencies overlap (the columns of nodes i +- s are not written at this level)
+  const int lane = tid & 31, c = tid >> 5;
+  const int nrhs = ctl->mc + 1;
+  const size_t ld = p.nrhs_cap;
+  const int r_first = by * 32 + lane;
+  double b_own = 0.0, b_l[6], b_r[6];
+  auto load_rhs = [&](int r) {
+    b_own = d.B[((size_t)i * 6 + c) * ld + r];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      b_l[k] = hl ? d.B[((size_t)(i - s) * 6 + k) * ld + r] : 0.0;
+      b_r[k] = hr ? d.B[((size_t)(i + s) * 6 + k) * ld + r] : 0.0;
+    }
+  };
+  if (r_first < nrhs) load_rhs(r_first);
   if (tid < 36) {
     sRl[tid] = hl ? d.Rm[(size_t)(i - s) * 36 + tid] : 0.0;
     sUl[tid] = hl ? d.U[(size_t)(i - s) * 36 + tid] : 0.0;
+    sLl[tid] = (hl && elim2) ? d.Lm[(size_t)(i - s) * 36 + tid] : 0.0;
     sLr[tid] = hr ? d.Lm[(size_t)(i + s) * 36 + tid] : 0.0;
     sUi[tid] = hr ? d.U[(size_t)i * 36 + tid] : 0.0;
     sUr[tid] = hr2 ? d.U[(size_t)(i + s) * 36 + tid] : 0.0;
@@ -353,13 +373,11 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
   if (elim2 && by == 0) {
     // new left coupling K_{i-2s, i} = -L_{i-s} U_{i-s}: node i-s was eliminated at level s
     __syncthreads();
-    if (tid < 36) {
+    if (tid < 36) {                                 // L_{i-s} and U_{i-s} are in shared memory
       const int r = tid / 6, c = tid % 6;
-      const double* Lm1 = d.Lm + (size_t)(i - s) * 36;
-      const double* Um1 = d.U + (size_t)(i - s) * 36;
       double v = 0.0;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) v = fma(-Lm1[r * 6 + k], Um1[k * 6 + c], v);
+      for (int k = 0; k < 6; ++k) v = fma(-sLl[r * 6 + k], sUl[k * 6 + c], v);
       sX[tid] = v;
     }
     const bool ok = team_inverse6(sA, tid, s_piv);
@@ -379,21 +397,17 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
     }
   }
   // forward reduction of level s: b_i -= R_{i-s} b_{i-s} + L_{i+s} b_{i+s}
-  const int lane = tid & 31, c = tid >> 5;
-  const int nrhs = ctl->mc + 1;
-  const size_t ld = p.nrhs_cap;
   if (!root) {
-    for (int r = by * 32 + lane; r < nrhs; r += 32 * kRhsSplit) {
-      double acc = d.B[((size_t)i * 6 + c) * ld + r];
+    for (int r = r_first; r < nrhs; r += 32 * kRhsSplit) {
+      if (r != r_first) load_rhs(r);
+      double acc = b_own;
       if (hl) {
-        const double* b = d.B + (size_t)(i - s) * 6 * ld + r;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) acc = fma(-sRl[c * 6 + k], b[k * ld], acc);
+        for (int k = 0; k < 6; ++k) acc = fma(-sRl[c * 6 + k], b_l[k], acc);
       }
       if (hr) {
-        const double* b = d.B + (size_t)(i + s) * 6 * ld + r;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) acc = fma(-sLr[c * 6 + k], b[k * ld], acc);
+        for (int k = 0; k < 6; ++k) acc = fma(-sLr[c * 6 + k], b_r[k], acc);
       }
       d.B[((size_t)i * 6 + c) * ld + r] = acc;
     }
@@ -412,11 +426,11 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
     const bool act = r < nrhs;
     double acc0 = 0.0;
     if (act) {
-      acc0 = d.B[(size_t)c * ld + r];
+      if (r0 != by * 32) load_rhs(r);               // i = 0 here; the first chunk was loaded above
+      acc0 = b_own;
       if (hr) {
-        const double* b = d.B + (size_t)s * 6 * ld + r;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) acc0 = fma(-sLr[c * 6 + k], b[k * ld], acc0);
+        for (int k = 0; k < 6; ++k) acc0 = fma(-sLr[c * 6 + k], b_r[k], acc0);
       }
     }
     __syncthreads();
@@ -457,34 +471,43 @@ __device__ __forceinline__ void bcr_bwd_body(const Params& p, const Dev& d, int 
   if (j >= nf) return;
   const int tid = threadIdx.x;
   const bool hr = j + s < nf;
+  const int lane = tid & 31, c = tid >> 5;
+  const int nrhs = ctl->mc + 1;
+  const size_t ld = p.nrhs_cap;
+  // b_j, x_{j-s}, x_{j+s} of the column this thread reads in a chunk (the first chunk's loaded with
+  // the blocks, so that the two latencies overlap; x_{j+-s} are not written at this level)
+  double b[6], xl[6], xr[6];
+  auto load = [&](int r) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      b[k] = d.B[((size_t)j * 6 + k) * ld + r];
+      xl[k] = d.B[((size_t)(j - s) * 6 + k) * ld + r];
+      xr[k] = hr ? d.B[((size_t)(j + s) * 6 + k) * ld + r] : 0.0;
+    }
+  };
+  if (by * 32 + lane < nrhs) load(by * 32 + lane);
   if (tid < 36) {
     sP[tid] = d.P[(size_t)j * 36 + tid];
     sL[tid] = d.Lm[(size_t)j * 36 + tid];
     sR[tid] = hr ? d.Rm[(size_t)j * 36 + tid] : 0.0;
   }
   __syncthreads();
-  const int lane = tid & 31, c = tid >> 5;
-  const int nrhs = ctl->mc + 1;
-  const size_t ld = p.nrhs_cap;
   for (int r0 = by * 32; r0 < nrhs; r0 += 32 * kRhsSplit) {
     const int r = r0 + lane;
     const bool act = r < nrhs;
-    double b[6];
-    if (act)
-#pragma unroll
-      for (int k = 0; k < 6; ++k) b[k] = d.B[((size_t)j * 6 + k) * ld + r];
-    __syncthreads();
+    if (r0 != by * 32) {
+      if (act) load(r);
+      __syncthreads();                          // every read of b_j's column before its writes
+    }
     if (act) {
       double acc = 0.0;
 #pragma unroll
       for (int k = 0; k < 6; ++k) acc = fma(sP[c * 6 + k], b[k], acc);
-      const double* x = d.B + (size_t)(j - s) * 6 * ld + r;     // - L_j^T x_{j-s}
 #pragma unroll
-      for (int k = 0; k < 6; ++k) acc = fma(-sL[k * 6 + c], x[k * ld], acc);
+      for (int k = 0; k < 6; ++k) acc = fma(-sL[k * 6 + c], xl[k], acc);    // - L_j^T x_{j-s}
       if (hr) {
-        const double* x2 = d.B + (size_t)(j + s) * 6 * ld + r;  // - R_j^T x_{j+s}
 #pragma unroll
-        for (int k = 0; k < 6; ++k) acc = fma(-sR[k * 6 + c], x2[k * ld], acc);
+        for (int k = 0; k < 6; ++k) acc = fma(-sR[k * 6 + c], xr[k], acc);  // - R_j^T x_{j+s}
       }
       d.B[((size_t)j * 6 + c) * ld + r] = acc;
     }

@@ -128,6 +128,7 @@ struct Dev {
   double *c_pt, *c_n, *c_gap;                        // m_cap * 3, * 3, * 1
   int *c_first;                                      // nf_cap + 1: rows of node f = [c_first[f], c_first[f+1])
   int *p_node, *p_tri;                               // previous iteration's rows
+  int *p_first;                                      // nf_cap + 1: previous rows of node f = [p_first[f], p_first[f+1])
   int *p_flag;                                       // previous rows: RF_* flags
   int *init_flag;                                    // current rows: flags of the same row in the previous iteration, -1 new
   int *wrow;                                         // ws_cap: row of working-set slot k (rows in order)
