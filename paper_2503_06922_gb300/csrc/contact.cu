@@ -84,6 +84,7 @@ struct LcpShared {
   double q[kLcpSmemRows], y[kLcpSmemRows], z[kLcpSmemRows];
   int inP[kLcpSmemRows], wcol[kLcpSmemRows], plist[kLcpSmemRows];
   double gj[kLcpSmemGJ * (kLcpSmemGJ + 1)];
+  double prow[kLcpSmemRows + 1];         // scaled pivot row of the Gauss-Jordan step
   double red[33];
   int ired[33];
   int np;
@@ -114,14 +115,20 @@ __device__ void ensure_columns(const Dev& d, LcpShared& S, int m, size_t ld, dou
   __syncthreads();
 }
 
-// Rebuilds the active list from the flags (thread 0; rows in increasing order).
+// Rebuilds the active list from the flags (warp 0, ballot compaction; rows in increasing order).
 __device__ void rebuild_plist(LcpShared& S, int m) {
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
     int np = 0;
-    for (int i = 0; i < m; ++i)
-      if (S.inP[i]) S.plist[np++] = i;
-    S.np = np;
+    for (int i0 = 0; i0 < m; i0 += 32) {
+      const int i = i0 + lane;
+      const bool in = i < m && S.inP[i];
+      const unsigned mk = __ballot_sync(0xffffffffu, in);
+      if (in) S.plist[np + __popc(mk & ((1u << lane) - 1u))] = i;
+      np += __popc(mk);
+    }
+    if (lane == 0) S.np = np;
   }
   __syncthreads();
 }
@@ -142,14 +149,17 @@ __device__ bool solve_on_set(const Dev& d, LcpShared& S, int m) {
     __syncthreads();
     const double akk = G[(size_t)k * ldg + k];
     if (!(akk > 0.0)) return false;
-    const double rp = __drcp_rn(akk);
-    for (int c = k + 1 + tid; c < ldg; c += nt) G[(size_t)k * ldg + c] *= rp;
+    // warp 0 scales the pivot row (one reciprocal per pivot, not one per warp: a warp's FP64
+    // instructions occupy its SMSP's FP64 pipe whatever its lane mask)
+    if (tid < 32) {
+      const double rp = __drcp_rn(akk);
+      for (int c = k + 1 + tid; c < ldg; c += 32) S.prow[c] = G[(size_t)k * ldg + c] * rp;
+    }
     __syncthreads();
     const int wdt = ldg - k - 1;
     for (int idx = tid; idx < np * wdt; idx += nt) {
       int r = idx / wdt, c = k + 1 + idx % wdt;
-      if (r == k) continue;
-      G[(size_t)r * ldg + c] = fma(-G[(size_t)r * ldg + k], G[(size_t)k * ldg + c], G[(size_t)r * ldg + c]);
+      G[(size_t)r * ldg + c] = r == k ? S.prow[c] : fma(-G[(size_t)r * ldg + k], S.prow[c], G[(size_t)r * ldg + c]);
     }
   }
   __syncthreads();
