@@ -76,21 +76,24 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
     return;
   }
   int row = excl;
-  for (int f = f0; f < f1; ++f) {
+  for (int f = f0; f < f1; ++f) {             // row ranges and the node of every row
     d.c_first[f] = row;
-    int nc = d.ncon[f];
-    for (int r = 0; r < nc; ++r, ++row) {
-      d.c_node[row] = f;
-      d.c_tri[row] = d.con_tri[f * kCpn + r];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        d.c_pt[3 * row + c] = d.con_pt[(f * kCpn + r) * 3 + c];
-        d.c_n[3 * row + c] = d.con_n[(f * kCpn + r) * 3 + c];
-      }
-      d.c_gap[row] = d.con_gap[f * kCpn + r];
-    }
+    const int nc = d.ncon[f];
+    for (int r = 0; r < nc; ++r, ++row) d.c_node[row] = f;
   }
   if (tid == 0) d.c_first[nf] = m;
+  __syncthreads();
+  for (int r = tid; r < m; r += 1024) {       // row payloads, one thread per row
+    const int f = d.c_node[r];
+    const int src = f * kCpn + (r - d.c_first[f]);
+    d.c_tri[r] = d.con_tri[src];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      d.c_pt[3 * r + c] = d.con_pt[src * 3 + c];
+      d.c_n[3 * r + c] = d.con_n[src * 3 + c];
+    }
+    d.c_gap[r] = d.con_gap[src];
+  }
   __syncthreads();
   const int mp = ctl->m_prev;
   // flags of the same row (node, triangle) in the previous iteration; -1 for a new row.  The node's

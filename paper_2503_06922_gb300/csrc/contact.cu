@@ -302,14 +302,21 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
     d.p_flag[row] = (d.p_flag[row] & RF_STICKY) | RF_WORKING | (a ? RF_ACTIVE : 0);
   }
   __syncthreads();
-  if (tid == 0) {
-    ctl->lcp_pivots += solves;
-    if (fail) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
-    else if (!done) atomicCAS(&ctl->status, 0, ST_TIMEOUT);
+  if (tid < 32) {                     // active slots in increasing order (ballot compaction)
     int na = 0;
-    for (int i = 0; i < m; ++i)
-      if (S.inP[i] && S.y[i] > 0.0) d.plist[na++] = i;
-    ctl->n_active = na;
+    for (int i0 = 0; i0 < m; i0 += 32) {
+      const int i = i0 + tid;
+      const bool a = i < m && S.inP[i] && S.y[i] > 0.0;
+      const unsigned mk = __ballot_sync(0xffffffffu, a);
+      if (a) d.plist[na + __popc(mk & ((1u << tid) - 1u))] = i;
+      na += __popc(mk);
+    }
+    if (tid == 0) {
+      ctl->lcp_pivots += solves;
+      if (fail) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
+      else if (!done) atomicCAS(&ctl->status, 0, ST_TIMEOUT);
+      ctl->n_active = na;
+    }
   }
 }
 

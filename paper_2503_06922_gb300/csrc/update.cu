@@ -9,6 +9,8 @@ namespace accfem {
 __device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx) {
   __shared__ double s_dx[32][6];
   __shared__ double s_r[32][6];
+  __shared__ int s_j[kMaxWorking];            // active working-set slots and their multipliers
+  __shared__ double s_y[kMaxWorking];
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
   const int nf = ctl->nf;
@@ -16,13 +18,17 @@ __device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx)
   const int f = bx * 32 + fl;
   const bool act = f < nf;
   const size_t ld = p.nrhs_cap;
+  const int na = ctl->n_active;
+  for (int a = threadIdx.y * 32 + threadIdx.x; a < na; a += 192) {
+    const int j = d.plist[a];
+    s_j[a] = j;
+    s_y[a] = d.y[d.wrow[j]];
+  }
+  __syncthreads();
   if (act) {
     double v = d.B[((size_t)f * 6 + c) * ld];
-    const int na = ctl->n_active;
-    for (int a = 0; a < na; ++a) {
-      const int j = d.plist[a];
-      v = fma(-d.B[((size_t)f * 6 + c) * ld + 1 + j], d.y[d.wrow[j]], v);
-    }
+    const double* bx_col = d.B + ((size_t)f * 6 + c) * ld + 1;
+    for (int a = 0; a < na; ++a) v = fma(-bx_col[s_j[a]], s_y[a], v);
     s_dx[fl][c] = v;
     d.dx[(size_t)f * 6 + c] = v;
     double r = d.g[(size_t)f * 6 + c];
