@@ -311,11 +311,12 @@ __global__ void __launch_bounds__(64) bcr_elim_batch(const Inst* __restrict__ ta
 }
 
 // Level s of the reduction, fused with the elimination at level 2s.  Blocks (kept node i = 2 s x,
-// y = RHS split), 192 threads.  Block y == 0: Schur update of D_i and U_i (kept nodes i: D_i and U_i as above);
+// y), 192 threads.  Block y == 0: Schur update of D_i and U_i (kept nodes i: D_i and U_i as above);
 // when i = 2s (mod 4s) it then eliminates i at level 2s: its new left coupling
 // U_{i-2s} <- -L_{i-s} U_{i-s} is rebuilt from level-s data, P_i = D_i^{-1}, L_i = U_{i-2s} P_i,
-// R_i = U_i^T P_i.  Every block applies the level-s forward reduction to its RHS chunks.  When
-// 2s >= nf only node 0 is kept: every block inverts D_0 itself (root) and solves x_0 = P_0 b_0.
+// R_i = U_i^T P_i.  Blocks y >= 1 apply the level-s forward reduction to their RHS chunks (chunk
+// y - 1 + kRhsSplit q).  When 2s >= nf only node 0 is kept: every block inverts D_0 itself (root)
+// and blocks y >= 1 solve x_0 = P_0 b_0 for their chunks.
 __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, int bx, int by, int s) {
   __shared__ double sRl[36], sUl[36], sLl[36], sLr[36], sUi[36], sUr[36], sA[36], sX[36], sY[36];
   __shared__ double s_piv[1];
@@ -333,7 +334,10 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
   const int lane = tid & 31, c = tid >> 5;
   const int nrhs = ctl->mc + 1;
   const size_t ld = p.nrhs_cap;
-  const int r_first = by * 32 + lane;
+  // block y == 0 does the 6x6 block work only; blocks y >= 1 reduce the RHS column chunks y - 1,
+  // y - 1 + kRhsSplit, .. (so the launch takes the longer of the two paths, not their sum)
+  const int chunk0 = by > 0 ? (by - 1) * 32 : nrhs;
+  const int r_first = chunk0 + lane;
   double b_own = 0.0, b_l[6], b_r[6];
   auto load_rhs = [&](int r) {
     b_own = d.B[((size_t)i * 6 + c) * ld + r];
@@ -424,12 +428,12 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
     return;
   }
   if (tid < 36 && by == 0) d.P[tid] = sA[tid];
-  for (int r0 = by * 32; r0 < nrhs; r0 += 32 * kRhsSplit) {
+  for (int r0 = chunk0; r0 < nrhs; r0 += 32 * kRhsSplit) {
     const int r = r0 + lane;
     const bool act = r < nrhs;
     double acc0 = 0.0;
     if (act) {
-      if (r0 != by * 32) load_rhs(r);               // i = 0 here; the first chunk was loaded above
+      if (r0 != chunk0) load_rhs(r);                // i = 0 here; the first chunk was loaded above
       acc0 = b_own;
       if (hr) {
 #pragma unroll
