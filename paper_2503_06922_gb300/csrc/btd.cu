@@ -276,18 +276,18 @@ __device__ __forceinline__ void bcr_elim_body(const Params& p, const Dev& d, int
   const int j = s + 2 * s * bx;
   if (j >= nf) return;
   const int tid = threadIdx.x;
-  if (tid < 36) sA[tid] = d.D[(size_t)j * 36 + tid];
+  if (tid < 36) {                                               // the couplings load with D_j
+    sA[tid] = d.D[(size_t)j * 36 + tid];
+    sX[tid] = d.U[(size_t)(j - s) * 36 + tid];                  // U_{j-s} = K_{j-s, j}
+    sY[tid] = (j + s < nf) ? d.U[(size_t)j * 36 + tid] : 0.0;   // U_j = K_{j, j+s}
+  }
   bool ok = team_inverse6(sA, tid, s_piv);
   if (!ok) {
     if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
     return;
   }
   const int r = tid / 6, c = tid % 6;
-  if (tid < 36) {
-    d.P[(size_t)j * 36 + tid] = sA[tid];
-    sX[tid] = d.U[(size_t)(j - s) * 36 + tid];                  // U_{j-s} = K_{j-s, j}
-    sY[tid] = (j + s < nf) ? d.U[(size_t)j * 36 + tid] : 0.0;   // U_j = K_{j, j+s}
-  }
+  if (tid < 36) d.P[(size_t)j * 36 + tid] = sA[tid];
   __syncthreads();
   if (tid < 36) {
     double l = 0.0, rr = 0.0;
@@ -348,6 +348,7 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
     }
   };
   if (r_first < nrhs) load_rhs(r_first);
+  const double d_own = (tid < 36 && (by == 0 || root)) ? d.D[(size_t)i * 36 + tid] : 0.0;   // with the blocks
   if (tid < 36) {
     sRl[tid] = hl ? d.Rm[(size_t)(i - s) * 36 + tid] : 0.0;
     sUl[tid] = hl ? d.U[(size_t)(i - s) * 36 + tid] : 0.0;
@@ -360,7 +361,7 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
   const bool matrix = by == 0 || root;
   if (tid < 36 && matrix) {
     const int r = tid / 6, c = tid % 6;
-    double dd = d.D[(size_t)i * 36 + tid];
+    double dd = d_own;
     double un = 0.0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
