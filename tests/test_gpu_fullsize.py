@@ -1,0 +1,79 @@
+"""Parity at the benchmark's full size and launch configuration: the 600 mm robot with 300 elements
+in the 63,840-triangle Catmull-Rom tube, the 60-solve insertion sweep through accfem_solve (the
+device-side Newton graph) with max_contacts = 4096, as bench.py runs it.  The oracle cannot redo
+the whole sweep in seconds, so sampled solves are checked one by one: started at the GPU's answer,
+the oracle's Newton iteration (Eq. 20-23, all rows, all triangles) must stay there -- its own
+convergence test passes within three iterations, the state moves by less than 1e-9 relative, and
+its constraint rows and per-node net contact forces are the GPU's."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import solver
+from oracle.rotation import from_quat
+
+pytestmark = pytest.mark.gpu
+
+SAMPLES = (19, 39, 59)
+
+
+@pytest.fixture(scope="module")
+def af():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_06922_gb300 import accfem
+    import os
+    if not os.path.exists(accfem.LIB_PATH):
+        from paper_2503_06922_gb300 import build
+        build.build()
+    accfem.load()
+    return accfem
+
+
+def _net_forces(contacts):
+    f = {}
+    for c in contacts:
+        f[c["node"]] = f.get(c["node"], 0.0) + c["force"] * np.asarray(c["normal"])
+    return f
+
+
+def test_full_size_sweep_samples_are_oracle_equilibria(af):
+    w = wl.catmull_rom_workload(lumen_seed=1, tension_seed=2, n_steps=60)
+    gpu = af.AccFem(w.robot, w.lumen, max_contacts=4096)
+    got = {}
+    for s in range(len(w.insertions)):
+        g = gpu.accfem_solve(w.tensions[s], w.insertions[s])
+        assert g["status"] == af.OK, (s, g["error"])
+        if s in SAMPLES:
+            got[s] = g
+    gpu.close()
+    l0 = w.robot.length / w.robot.n_elements
+    act = w.robot.outer_radius + 1.0e-3
+    for s in SAMPLES:
+        g = got[s]
+        R = np.array([from_quat(q) for q in g["node_quat"]])
+        ref = solver.Model(w.robot, w.lumen, solver.Options(max_contacts=4096, max_newton_iters=3))
+        o = ref.solve(w.tensions[s], w.insertions[s], warm=(g["node_pos"].copy(), R))
+        assert o.status == solver.OK and o.newton_iters <= 3, (s, o.status, o.newton_iters)
+        err = np.abs(o.node_pos - g["node_pos"]).max() / np.abs(o.node_pos).max()
+        assert err <= 1e-9, (s, err)
+        # rows as (node, closest point within 1e-9 m); only rows at the activation distance may differ
+        def unmatched(a, b):
+            out = []
+            for c in a:
+                pc = np.asarray(c["point"])
+                if not any(e["node"] == c["node"] and np.linalg.norm(np.asarray(e["point"]) - pc) <= 1e-9 for e in b):
+                    out.append((c["node"], pc))
+            return out
+        for node, pt in unmatched(g["contacts"], o.contacts) + unmatched(o.contacts, g["contacts"]):
+            d = np.linalg.norm(pt - o.node_pos[node])
+            assert abs(d - act) <= 1e-9, (s, "rows differ", node, d)
+        if s == SAMPLES[-1]:
+            assert len(g["contacts"]) > 100
+        # per-node net contact force: 1e-6 of the largest, or what the Newton tolerance leaves open
+        fo, fg = _net_forces(o.contacts), _net_forces(g["contacts"])
+        fmax = max([np.linalg.norm(v) for v in fo.values()] + [1e-300])
+        ftol = max(1e-6 * fmax, 1e-10 * max(1.0, float(np.sum(w.tensions[s]))) / l0)
+        for n in set(fo) | set(fg):
+            assert np.linalg.norm(fo.get(n, 0.0) - fg.get(n, 0.0)) <= ftol, (s, n)
