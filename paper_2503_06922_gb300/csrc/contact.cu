@@ -96,16 +96,22 @@ struct LcpShared {
 __device__ void ensure_columns(const Dev& d, LcpShared& S, int m, size_t ld, double eps_w) {
   const int tid = threadIdx.x, nt = blockDim.x;
   __syncthreads();
-  for (int a = 0; a < S.np; ++a) {
-    const int j = S.plist[a];
-    if (S.wcol[j]) continue;
-    for (int i = tid; i < m; i += nt) {
-      const int row = d.wrow[i];
-      const int fi = d.c_node[row];
-      const double* n = d.c_n + 3 * row;
+  // a thread owns rows i (its node's RHS entries and normal loaded once) and forms their entries of
+  // every new column; the RHS columns are read-only here, so the loads of different columns overlap
+  for (int i = tid; i < m; i += nt) {
+    const int row = d.wrow[i];
+    const int fi = d.c_node[row];
+    const double n0 = d.c_n[3 * row], n1 = d.c_n[3 * row + 1], n2 = d.c_n[3 * row + 2];
+    const double* b0 = d.B + ((size_t)fi * 6) * ld + 1;
+    const double* b1 = b0 + ld;
+    const double* b2 = b1 + ld;
+    for (int a = 0; a < S.np; ++a) {
+      const int j = S.plist[a];
+      if (S.wcol[j]) continue;
       double s = 0.0;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) s = fma(n[c], d.B[((size_t)fi * 6 + c) * ld + 1 + j], s);
+      s = fma(n0, __ldg(b0 + j), s);
+      s = fma(n1, __ldg(b1 + j), s);
+      s = fma(n2, __ldg(b2 + j), s);
       if (i == j) s += eps_w;
       d.W[(size_t)i * m + j] = s;
     }
