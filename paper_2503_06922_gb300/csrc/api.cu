@@ -385,7 +385,7 @@ int enqueue_factor(const Params& p, const Dev& d, int nf, cudaStream_t st, bool 
   while (levels < kMaxLevels && phase_gx(PH_LEV0 + levels, nf) > 0) ++levels;
   for (int j = 0; j < levels; ++j) { launch_k(pdl, bcr_level_kernel, grid(PH_LEV0 + j), dim3(192), st, p, d, 1 << j); ++n; }
   for (int j = levels - 1; j >= 0; --j)
-    if (phase_gx(PH_BWD0 + j, nf) > 0) { launch_k(pdl, bcr_bwd_kernel, grid(PH_BWD0 + j), dim3(192), st, p, d, 1 << j); ++n; }
+    if (phase_gx(PH_BWD0 + j, nf) > 0) { launch_k(pdl, bcr_bwd_kernel, grid(PH_BWD0 + j), dim3(96), st, p, d, 1 << j); ++n; }
   return n;
 }
 

@@ -100,7 +100,7 @@ int enqueue_batch_iteration(accfem_batch* b, cudaStream_t st, cudaGraphCondition
   launch_k(pdl, assemble_rhs_batch, dim3(g[PH_ASM]), dim3(32, 6), st, tab, plan); ++n;
   launch_k(pdl, bcr_elim_batch, dim3(g[PH_ELIM1]), dim3(64), st, tab, plan); ++n;
   for (int j = 0; j < b->levels; ++j) { launch_k(pdl, bcr_level_batch, dim3(g[PH_LEV0 + j]), dim3(192), st, tab, plan, j); ++n; }
-  for (int j = b->levels - 1; j >= 0; --j) { launch_k(pdl, bcr_bwd_batch, dim3(g[PH_BWD0 + j]), dim3(192), st, tab, plan, j); ++n; }
+  for (int j = b->levels - 1; j >= 0; --j) { launch_k(pdl, bcr_bwd_batch, dim3(g[PH_BWD0 + j]), dim3(96), st, tab, plan, j); ++n; }
   launch_k(pdl, contact_batch, dim3(g[PH_CONTACT]), dim3(256), st, tab, plan); ++n;
   launch_k(pdl, step_batch, dim3(g[PH_STEP]), dim3(32, 6), st, tab, plan); ++n;
   launch_k(pdl, apply_batch, dim3(g[PH_APPLY]), dim3(128), st, tab, plan); ++n;
@@ -125,7 +125,7 @@ void full_grids(accfem_batch* b, int* grid) {
   grid[PH_APPLY] = persistent_grid(apply_batch, 128, units[PH_APPLY]);
   for (int j = 0; j < b->levels; ++j) {
     grid[PH_LEV0 + j] = persistent_grid(bcr_level_batch, 192, units[PH_LEV0 + j]);
-    grid[PH_BWD0 + j] = persistent_grid(bcr_bwd_batch, 192, units[PH_BWD0 + j]);
+    grid[PH_BWD0 + j] = persistent_grid(bcr_bwd_batch, 96, units[PH_BWD0 + j]);
   }
 }
 

@@ -73,7 +73,8 @@ __host__ __device__ inline int phase_gx(int ph, int nf) {
 // 6x6 block work of its node while the others reduce the RHS.
 __host__ __device__ inline int phase_gy(int ph) {
   if (ph >= PH_LEV0 && ph < PH_BWD0) return kRhsSplit + 1;
-  return (ph == PH_ASM || (ph >= PH_BWD0 && ph < kPhases)) ? kRhsSplit : 1;
+  if (ph >= PH_BWD0 && ph < kPhases) return kBwdSplit;
+  return ph == PH_ASM ? kRhsSplit : 1;
 }
 
 // Persistent loop over the units of phase ph: body(inst, bx, by) for every unit assigned to this

@@ -377,31 +377,32 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
       d.D[(size_t)i * 36 + tid] = dd;
       if (hr) d.U[(size_t)i * 36 + tid] = hr2 ? un : 0.0;
     }
+  } else if (elim2 && by == 0 && tid < 72) {
+    // beside the Schur update: new left coupling K_{i-2s, i} = -L_{i-s} U_{i-s} (node i-s was
+    // eliminated at level s; L_{i-s} and U_{i-s} are in shared memory)
+    const int q = tid - 36, r = q / 6, c = q % 6;
+    double v = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v = fma(-sLl[r * 6 + k], sUl[k * 6 + c], v);
+    sX[q] = v;
   }
   if (elim2 && by == 0) {
-    // new left coupling K_{i-2s, i} = -L_{i-s} U_{i-s}: node i-s was eliminated at level s
-    __syncthreads();
-    if (tid < 36) {                                 // L_{i-s} and U_{i-s} are in shared memory
-      const int r = tid / 6, c = tid % 6;
-      double v = 0.0;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) v = fma(-sLl[r * 6 + k], sUl[k * 6 + c], v);
-      sX[tid] = v;
-    }
-    const bool ok = team_inverse6(sA, tid, s_piv);
+    const bool ok = team_inverse6(sA, tid, s_piv);   // begins with a barrier
     if (!ok) {
       if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
-    } else if (tid < 36) {
-      const int r = tid / 6, c = tid % 6;
-      d.P[(size_t)i * 36 + tid] = sA[tid];
-      double l = 0.0, rr = 0.0;
+    } else if (tid < 72) {                           // L on threads 0..35, R on 36..71
+      const int q = tid % 36, r = q / 6, c = q % 6;
+      double v = 0.0;
+      if (tid < 36) {
+        d.P[(size_t)i * 36 + q] = sA[q];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        l = fma(sX[r * 6 + k], sA[k * 6 + c], l);     // U_{i-2s} P_i
-        rr = fma(sY[k * 6 + r], sA[k * 6 + c], rr);   // U_i^T P_i
+        for (int k = 0; k < 6; ++k) v = fma(sX[r * 6 + k], sA[k * 6 + c], v);    // U_{i-2s} P_i
+        d.Lm[(size_t)i * 36 + q] = v;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v = fma(sY[k * 6 + r], sA[k * 6 + c], v);    // U_i^T P_i
+        d.Rm[(size_t)i * 36 + q] = v;
       }
-      d.Lm[(size_t)i * 36 + tid] = l;
-      d.Rm[(size_t)i * 36 + tid] = rr;
     }
   }
   // forward reduction of level s: b_i -= R_{i-s} b_{i-s} + L_{i+s} b_{i+s}
@@ -469,7 +470,10 @@ __global__ void __launch_bounds__(192) bcr_level_batch(const Inst* __restrict__ 
   for_units(tab, plan, PH_LEV0 + j, [j](const Inst& in, int bx, int by) { bcr_level_body(in.p, in.d, bx, by, 1 << j); });
 }
 
-// Back substitution at stride s for eliminated nodes j = s + 2 s blockIdx.x (192 threads).
+// Back substitution at stride s for eliminated nodes j = s + 2 s blockIdx.x.  96 threads: 16 columns
+// x 6 components, one warp per SMSP (a warp's FP64 instruction holds its SMSP's FP64 pipe for 64
+// cycles, so two warps on one SMSP would serialise); block y takes the 16-column chunks y,
+// y + kBwdSplit, ...
 __device__ __forceinline__ void bcr_bwd_body(const Params& p, const Dev& d, int bx, int by, int s) {
   __shared__ double sP[36], sL[36], sR[36];
   Ctl* ctl = d.ctl;
@@ -479,7 +483,7 @@ __device__ __forceinline__ void bcr_bwd_body(const Params& p, const Dev& d, int 
   if (j >= nf) return;
   const int tid = threadIdx.x;
   const bool hr = j + s < nf;
-  const int lane = tid & 31, c = tid >> 5;
+  const int lane = tid & 15, c = tid >> 4;
   const int nrhs = ctl->mc + 1;
   const size_t ld = p.nrhs_cap;
   // b_j, x_{j-s}, x_{j+s} of the column this thread reads in a chunk (the first chunk's loaded with
@@ -493,17 +497,17 @@ __device__ __forceinline__ void bcr_bwd_body(const Params& p, const Dev& d, int 
       xr[k] = hr ? d.B[((size_t)(j + s) * 6 + k) * ld + r] : 0.0;
     }
   };
-  if (by * 32 + lane < nrhs) load(by * 32 + lane);
+  if (by * 16 + lane < nrhs) load(by * 16 + lane);
   if (tid < 36) {
     sP[tid] = d.P[(size_t)j * 36 + tid];
     sL[tid] = d.Lm[(size_t)j * 36 + tid];
     sR[tid] = hr ? d.Rm[(size_t)j * 36 + tid] : 0.0;
   }
   __syncthreads();
-  for (int r0 = by * 32; r0 < nrhs; r0 += 32 * kRhsSplit) {
+  for (int r0 = by * 16; r0 < nrhs; r0 += 16 * kBwdSplit) {
     const int r = r0 + lane;
     const bool act = r < nrhs;
-    if (r0 != by * 32) {
+    if (r0 != by * 16) {
       if (act) load(r);
       __syncthreads();                          // every read of b_j's column before its writes
     }
@@ -523,12 +527,12 @@ __device__ __forceinline__ void bcr_bwd_body(const Params& p, const Dev& d, int 
   }
 }
 
-__global__ void __launch_bounds__(192) bcr_bwd_kernel(Params p, Dev d, int s) {
+__global__ void __launch_bounds__(96) bcr_bwd_kernel(Params p, Dev d, int s) {
   pdl_enter();
   bcr_bwd_body(p, d, blockIdx.x, blockIdx.y, s);
 }
 
-__global__ void __launch_bounds__(192) bcr_bwd_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j) {
+__global__ void __launch_bounds__(96) bcr_bwd_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j) {
   for_units(tab, plan, PH_BWD0 + j, [j](const Inst& in, int bx, int by) { bcr_bwd_body(in.p, in.d, bx, by, 1 << j); });
 }
 

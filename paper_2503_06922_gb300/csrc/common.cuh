@@ -12,6 +12,7 @@ constexpr int kCandCap = 256;      // candidates per node kept in shared memory 
 constexpr int kElemStride = 96;    // doubles per element record: 78 K (upper) + 12 F + pad
 constexpr int kWarpsPerElemBlock = 2;
 constexpr int kRhsSplit = 4;       // blocks per node that share the RHS columns (chunks of 32)
+constexpr int kBwdSplit = 8;       // back substitution: blocks per node (chunks of 16 columns, 96 threads)
 constexpr int kMaxWorking = 512;   // rows of the contact working set (RHS columns, LCP size)
 constexpr int kPrecisionFP64 = 0, kPrecisionMixed = 1;
 // A triangle whose plane projection of the node lies inside it enlarged by this barycentric margin
