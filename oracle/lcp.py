@@ -73,3 +73,67 @@ def enumerate_lcp(W, q, tol=1e-12):
         if (y >= -tol * scale).all() and (w >= -tol * scale).all():
             sols.append((y, w))
     return sols
+
+
+def admm(W, q, rho=None, sigma=1.0e-6, alpha=1.6, eps_abs=0.0, eps_rel=1.0e-3, max_iter=4000, check_every=10):
+    """OSQP's ADMM (Stellato et al., "OSQP: an operator splitting solver for quadratic programs",
+    2020, the solver the paper uses for Eq. 23) on the contact-space form of the QP,
+        min 1/2 y^T W y + q^T y   s.t.  0 <= y,
+    i.e. OSQP's problem with P = W, constraint matrix I, l = 0, u = +inf.  One iteration with the
+    step sizes sigma, rho and the relaxation alpha:
+        (W + (sigma + rho) I) yt = sigma y - q + rho z - lam      (the matrix is factored once)
+        y <- alpha yt + (1 - alpha) y
+        zh = alpha yt + (1 - alpha) z
+        z <- max(zh + lam / rho, 0),   lam <- lam + rho (zh - z)
+    stopped when the primal residual |y - z|_inf and the dual residual |W y + q + lam|_inf are
+    below eps_abs + eps_rel times the scale of their terms.  rho defaults to 0.1 max(diag W).
+    Returns (y, z, lam, iterations)."""
+    m = len(q)
+    if m == 0:
+        return np.zeros(0), np.zeros(0), np.zeros(0), 0
+    W = np.asarray(W, float)
+    q = np.asarray(q, float)
+    if rho is None:
+        rho = 0.1 * float(np.max(np.diag(W)))
+    c = sla.cho_factor(W + (sigma + rho) * np.eye(m))
+    y = np.zeros(m)
+    z = np.zeros(m)
+    lam = np.zeros(m)
+    it = 0
+    while it < max_iter:
+        it += 1
+        yt = sla.cho_solve(c, sigma * y - q + rho * z - lam)
+        y = alpha * yt + (1.0 - alpha) * y
+        zh = alpha * yt + (1.0 - alpha) * z
+        z = np.maximum(zh + lam / rho, 0.0)
+        lam = lam + rho * (zh - z)
+        if it % check_every == 0:
+            Wy = W @ y
+            r_prim = np.abs(y - z).max()
+            r_dual = np.abs(Wy + q + lam).max()
+            if (r_prim <= eps_abs + eps_rel * max(np.abs(y).max(), np.abs(z).max()) and
+                    r_dual <= eps_abs + eps_rel * max(np.abs(Wy).max(), np.abs(lam).max(), np.abs(q).max())):
+                break
+    return y, z, lam, it
+
+
+def admm_polish(W, q, **admm_args):
+    """The paper's solve of Eq. 23 (OSQP) carried to the exact solution: ADMM gives the guess of
+    the rows whose bound y >= 0 is not binding (z_i > -lam_i: the projection did not clip), the
+    equality-constrained problem on them, W_FF y_F = -q_F with y = 0 elsewhere, is solved exactly
+    ("polish"), and the result is accepted when it satisfies the LCP (y_F > 0, w = W y + q >= 0 on
+    the other rows, to a relative tolerance of 1e-12); otherwise the exact active-set solution of
+    qp_nnls is returned.  Returns (y, w, admm_iterations, polished)."""
+    m = len(q)
+    if m == 0:
+        return np.zeros(0), np.zeros(0), 0, True
+    y, z, lam, it = admm(W, q, **admm_args)
+    F = z > -lam
+    yp = _solve_set(W, q, F)
+    w = W @ yp + q
+    scale_y = max(np.abs(yp).max(), 1e-300)
+    scale_w = max(np.abs(q).max(), 1e-300)
+    if (yp[F] > 0.0).all() and (w[~F] >= -1e-12 * scale_w).all() and (np.abs(yp[~F]) <= 1e-12 * scale_y).all():
+        return yp, w, it, True
+    ye, we, _ = qp_nnls(W, q)
+    return ye, we, it, False

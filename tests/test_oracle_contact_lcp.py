@@ -213,3 +213,37 @@ def test_murty_kkt_larger():
         y, w, piv = lcp.murty(W, q)
         ww = W @ y + q
         assert y.min() >= 0 and ww.min() >= -1e-11 and np.abs(np.minimum(y, ww)).max() <= 1e-11
+
+
+def test_admm_polish_matches_enumeration_and_pivoting():
+    """OSQP-style ADMM on the contact-space QP, then the exact polish on its guess of the free rows:
+    the unique LCP solution (enumeration for m <= 10, Murty's pivoting beyond), and the polish
+    accepts the ADMM guess without falling back."""
+    rng = np.random.default_rng(17)
+    fallbacks = 0
+    for m in list(range(1, 11)) + [20, 40]:
+        for _ in range(5):
+            W = _spd(rng, m)
+            q = rng.normal(size=m)
+            y, w, it, polished = lcp.admm_polish(W, q)
+            ye = lcp.enumerate_lcp(W, q)[0][0] if m <= 10 else lcp.murty(W, q)[0]
+            assert np.allclose(y, ye, atol=1e-11), (m, np.abs(y - ye).max())
+            assert y.min() >= 0 and w.min() >= -1e-11 and abs(y @ w) <= 1e-10
+            fallbacks += not polished
+    assert fallbacks == 0
+
+
+def test_admm_iterates_approach_the_solution():
+    """The ADMM iterates themselves converge: at tighter tolerances y and z approach the exact
+    solution and the multiplier lam approaches -w (the slack of the bound y >= 0)."""
+    rng = np.random.default_rng(18)
+    for m in (5, 12, 30):
+        W = _spd(rng, m)
+        q = rng.normal(size=m)
+        ye, we, _ = lcp.murty(W, q)
+        errs = []
+        for eps in (1e-2, 1e-4, 1e-6):
+            y, z, lam, _ = lcp.admm(W, q, eps_rel=eps, max_iter=100000)
+            errs.append(np.abs(z - ye).max())
+            assert np.abs(lam + we).max() <= 100 * eps * max(1.0, np.abs(q).max())
+        assert errs[-1] <= 1e-4 * max(1.0, np.abs(ye).max()) and errs[-1] <= errs[0]
