@@ -588,6 +588,31 @@ def ours(args, rank, world, local_rank):
         co_us = h.accfem_time_kernel(af.KERNEL_COLLIDE, 20)
         ct_us = h.accfem_time_kernel(af.KERNEL_CONTACT, 20)
         fa_us = h.accfem_time_kernel(af.KERNEL_FACTOR, 20)
+        # ---- the paper's contact scheme (OSQP's ADMM guess, then the exact polish): the same sweep,
+        #      timed like `value`, and the contact kernel on the final state of the sweep
+        progress("contact solver: ADMM sweep")
+        h.accfem_set_contact_solver(af.CONTACT_ADMM)
+        admm_ms, admm_fail, admm_iters = 0.0, 0, 0
+        with torch.cuda.stream(stream):
+            sweep_resident()
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            admm_fail, admm_iters = sweep_resident()
+            t1.record(stream)
+            t1.synchronize()
+            admm_ms = t0.elapsed_time(t1)
+        admm_ct_us = h.accfem_time_kernel(af.KERNEL_CONTACT, 5)
+        h.accfem_set_contact_solver(af.CONTACT_ACTIVE_SET)
+        contact_admm = {"scheme": "OSQP ADMM on the contact-space QP over the working set (W + (sigma + rho) I "
+                                  "inverted once), guess of the free rows polished by the exact active-set method",
+                        "solves_per_s": S / (admm_ms * 1e-3), "ms_per_step": admm_ms,
+                        "newton_iters_per_solve": admm_iters / S, "failed_solves": int(admm_fail),
+                        "contact_kernel_us_final_state": admm_ct_us, "active_set_contact_kernel_us": ct_us}
+        progress("contact solver: ADMM %.1f solves/s, contact kernel %.0f us (active set %.0f us)"
+                 % (contact_admm["solves_per_s"], admm_ct_us, ct_us))
         # ---- mixed precision: the same sweep with the FP32 element tangent, timed like `value`, and
         #      every solve compared with the FP64 solve of the same step
         progress("precision: mixed sweep")
@@ -689,6 +714,7 @@ def ours(args, rank, world, local_rank):
                                  "sample": "first %d solves of the sweep (insertion 10..%d mm), %.1f s, numpy FP64 "
                                            "oracle, single thread" % (cpu_n, 10 * cpu_n, cpu_dt)}}
         line["precision"] = precision
+        line["contact_admm"] = contact_admm
         line.update(extra)
         print(json.dumps(line), flush=True)
     if dist:

@@ -191,6 +191,18 @@ accfem_status accfem_set_element_modulus(accfem_handle* h, const double* youngs_
  * created.  E_INVALID_ARG for a negative count or one above 10^6. */
 accfem_status accfem_set_frame_mode(accfem_handle* h, int32_t iters_per_frame);
 
+/* Contact solver of each Newton iteration (the QP of Eq. 23 in contact space, min 1/2 y^T W y + q^T y
+ * over y >= 0, W = A K^{-1} A^T over the working set).  Both return its exact solution.
+ * ACCFEM_CONTACT_ACTIVE_SET (the default): a primal active-set method started from the rows active
+ * in the previous iteration.  ACCFEM_CONTACT_ADMM: the paper's scheme (Sec. III.B: the MLCP as a QP
+ * solved by OSQP): OSQP's ADMM iteration (sigma 1e-6, rho 0.1 max diag W, relaxation 1.6, relative
+ * tolerance 1e-3, at most 4000 iterations) on the whole working-set W, factored once, whose guess
+ * of the free rows the active-set method then polishes to the exact solution.  Call between
+ * solves; a batch takes each member's solver when the batch is created.  E_INVALID_ARG otherwise. */
+#define ACCFEM_CONTACT_ACTIVE_SET 0
+#define ACCFEM_CONTACT_ADMM 1
+accfem_status accfem_set_contact_solver(accfem_handle* h, int32_t solver);
+
 /* Cumulative bytes copied host->device and device->host by this handle's solve and state calls. */
 accfem_status accfem_transfer_bytes(const accfem_handle* h, int64_t* h2d, int64_t* d2h);
 

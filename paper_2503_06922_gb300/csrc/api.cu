@@ -207,6 +207,8 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
   p.eps_d = 1e-6;
   p.eps_b = 1e-3f;
   p.max_newton = opt.max_newton_iters;
+  p.lcp_mode = kLcpActiveSet;
+  p.admm_iters = 4000;
   h->nf_cap = p.M;
   h->max_newton = opt.max_newton_iters;
   h->max_newton_opt = opt.max_newton_iters;
@@ -677,6 +679,19 @@ accfem_status accfem_set_precision(accfem_handle* h, int32_t mode) {
   }
   h->graphs.clear();
   h->p.precision = mode;
+  return ACCFEM_OK;
+}
+
+accfem_status accfem_set_contact_solver(accfem_handle* h, int32_t solver) {
+  if (!h || (solver != ACCFEM_CONTACT_ACTIVE_SET && solver != ACCFEM_CONTACT_ADMM)) return ACCFEM_E_INVALID_ARG;
+  if (h->p.lcp_mode == solver) return ACCFEM_OK;
+  if (h->stream) cudaStreamSynchronize(h->work());
+  for (auto& kv : h->graphs) {     // the Newton graphs captured the handle's constants
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  h->graphs.clear();
+  h->p.lcp_mode = solver == ACCFEM_CONTACT_ADMM ? kLcpAdmm : kLcpActiveSet;
   return ACCFEM_OK;
 }
 

@@ -15,6 +15,7 @@ constexpr int kRhsSplit = 4;       // blocks per node that share the RHS columns
 constexpr int kBwdSplit = 8;       // back substitution: blocks per node (chunks of 16 columns, 96 threads)
 constexpr int kMaxWorking = 512;   // rows of the contact working set (RHS columns, LCP size)
 constexpr int kPrecisionFP64 = 0, kPrecisionMixed = 1;
+constexpr int kLcpActiveSet = 0, kLcpAdmm = 1;
 // A triangle whose plane projection of the node lies inside it enlarged by this barycentric margin
 // ("over the face") gives a constraint row; the same value is used by the CPU oracle.
 constexpr double kFaceBand = 0.1;
@@ -56,6 +57,8 @@ struct Params {
   int ws_all;                    // every constraint row is in the working set (frame mode)
   int max_newton;                // Newton iteration cap of a solve
   int precision;                 // kPrecisionFP64 or kPrecisionMixed (FP32 element tangent)
+  int lcp_mode;                  // kLcpActiveSet, or kLcpAdmm (OSQP's ADMM guess, then the exact polish)
+  int admm_iters;                // ADMM iteration cap
 };
 
 // Control block, resident on the device; one per handle.
@@ -82,6 +85,7 @@ struct Ctl {
   int mc;                // rows of the working set (RHS columns 1..mc)
   int incomplete;        // a row outside the working set is violated by this iteration's step
   int fp64_tangent;      // mixed precision: this solve fell back to the FP64 element tangent
+  int admm_iters;        // ADMM iterations of this solve (contact solver kLcpAdmm)
   int frame;             // frame mode: reaching the iteration cap is the normal end of a solve
   double delta;          // insertion of the resident state
   double tension[kMaxCables];

@@ -176,6 +176,108 @@ __device__ bool solve_on_set(const Dev& d, LcpShared& S, int m) {
   return true;
 }
 
+// OSQP's ADMM (Stellato et al., 2020: the solver the paper uses for Eq. 23) on the contact-space QP
+// min 1/2 y^T W y + q^T y, y >= 0 over the working set (OSQP's P = W, constraint matrix I, l = 0,
+// u = inf), with step sizes sigma = 1e-6, rho = 0.1 max(diag W) and relaxation alpha = 1.6:
+//   (W + (sigma + rho) I) yt = sigma y - q + rho z - lam
+//   y <- alpha yt + (1 - alpha) y,  zh = alpha yt + (1 - alpha) z,
+//   z <- max(zh + lam / rho, 0),    lam <- lam + rho (zh - z),
+// stopped when |y - z| <= 1e-3 max(|y|, |z|) and |W y + q + lam| <= 1e-3 max(|W y|, |lam|, |q|)
+// (infinity norms, tested every 10 iterations) or after p.admm_iters iterations.  The matrix is
+// inverted once by Gauss-Jordan in global memory; an iteration is one product with the inverse
+// (a warp per row) and the projection.  Its guess of the free rows (z > -lam) starts the exact
+// active-set method, which polishes it.  Returns false on a non-positive pivot.
+__device__ bool admm_guess(const Params& p, const Dev& d, LcpShared& S, int m, size_t ld, double eps_w, double qmax,
+                           int* iters) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int i = tid; i < m; i += nt) S.inP[i] = 1;
+  rebuild_plist(S, m);
+  ensure_columns(d, S, m, ld, eps_w);           // every column of W over the working set
+  double wd = 0.0;
+  for (int i = tid; i < m; i += nt) wd = fmax(wd, d.W[(size_t)i * m + i]);
+  wd = block_max(wd, S.red);
+  const double sigma = 1.0e-6, alpha = 1.6, eps_rel = 1.0e-3;
+  const double rho = 0.1 * wd, irho = __drcp_rn(rho);
+  double* G = d.gj;                             // (W + (sigma + rho) I)^-1, m x m row-major
+  for (int idx = tid; idx < m * m; idx += nt)
+    G[idx] = d.W[idx] + ((idx / m) == (idx % m) ? sigma + rho : 0.0);
+  for (int k = 0; k < m; ++k) {
+    __syncthreads();
+    const double akk = G[(size_t)k * m + k];
+    if (!(akk > 0.0)) return false;
+    if (tid < 32) {                             // scaled pivot row (one reciprocal per pivot)
+      const double pk = __drcp_rn(akk);
+      for (int j = tid; j < m; j += 32) S.prow[j] = j == k ? pk : G[(size_t)k * m + j] * pk;
+    }
+    for (int i = tid; i < m; i += nt) S.z[i] = G[(size_t)i * m + k];   // pivot column
+    __syncthreads();
+    const double pk = S.prow[k];
+    for (int idx = tid; idx < m * m; idx += nt) {
+      const int i = idx / m, j = idx % m;
+      if (i == k) G[idx] = S.prow[j];
+      else if (j == k) G[idx] = -S.z[i] * pk;
+      else G[idx] = fma(-S.z[i], S.prow[j], G[idx]);
+    }
+  }
+  __syncthreads();
+  double* lam = S.prow;                         // free again
+  double* rv = S.gj;                            // right-hand side of the linear step
+  for (int i = tid; i < m; i += nt) { S.y[i] = 0.0; S.z[i] = 0.0; lam[i] = 0.0; }
+  int it = 0;
+  while (it < p.admm_iters) {
+    ++it;
+    __syncthreads();
+    for (int i = tid; i < m; i += nt) rv[i] = ((sigma * S.y[i] - S.q[i]) + rho * S.z[i]) - lam[i];
+    __syncthreads();
+    for (int i = wid; i < m; i += nw) {          // a warp per row: yt_i = (G rv)_i
+      const double* gi = G + (size_t)i * m;
+      double s = 0.0;
+      for (int j = lane; j < m; j += 32) s = fma(gi[j], rv[j], s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) {
+        const double zh = alpha * s + (1.0 - alpha) * S.z[i];
+        const double zn = fmax(zh + lam[i] * irho, 0.0);
+        S.y[i] = alpha * s + (1.0 - alpha) * S.y[i];
+        lam[i] = lam[i] + rho * (zh - zn);
+        S.z[i] = zn;
+      }
+    }
+    if (it % 10 == 0) {
+      __syncthreads();
+      double rpri = 0.0, rdua = 0.0, ym = 0.0, wym = 0.0, lm = 0.0;
+      for (int i = wid; i < m; i += nw) {
+        const double* wi = d.W + (size_t)i * m;
+        double s = 0.0;
+        for (int j = lane; j < m; j += 32) s = fma(wi[j], S.y[j], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+          rpri = fmax(rpri, fabs(S.y[i] - S.z[i]));
+          rdua = fmax(rdua, fabs(s + S.q[i] + lam[i]));
+          ym = fmax(ym, fmax(fabs(S.y[i]), fabs(S.z[i])));
+          wym = fmax(wym, fabs(s));
+          lm = fmax(lm, fabs(lam[i]));
+        }
+      }
+      rpri = block_max(rpri, S.red);
+      rdua = block_max(rdua, S.red);
+      ym = block_max(ym, S.red);
+      wym = block_max(wym, S.red);
+      lm = block_max(lm, S.red);
+      if (rpri <= eps_rel * ym && rdua <= eps_rel * fmax(fmax(wym, lm), qmax)) break;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < m; i += nt) {
+    S.inP[i] = S.z[i] > -lam[i] ? 1 : 0;
+    S.y[i] = 0.0;
+  }
+  __syncthreads();
+  *iters = it;
+  return true;
+}
+
 // LCP by a primal active-set method for the bound-constrained QP min 1/2 y^T W y + q^T y, y >= 0
 // (the Lawson-Hanson NNLS scheme with W SPD): keep y feasible with y_P > 0; add the row of most
 // negative w = W y + q; when the subproblem solution z_P has non-positive entries, step from y
@@ -226,8 +328,10 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
   const double tol_w = p.lcp_tol * fmax(qmax, 1e-300);
   int solves = 0;
   bool done = false, fail = false;
+  int admm_it = 0;
+  if (p.lcp_mode == kLcpAdmm) fail = !admm_guess(p, d, S, m, ld, eps_w, qmax, &admm_it);
   // ---- feasible start: drop warm rows until the subproblem solution is positive
-  for (;;) {
+  while (!fail) {
     if (solves >= p.max_lcp_iters) break;
     rebuild_plist(S, m);
     ensure_columns(d, S, m, ld, eps_w);
@@ -319,6 +423,7 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
     }
     if (tid == 0) {
       ctl->lcp_pivots += solves;
+      ctl->admm_iters += admm_it;
       if (fail) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
       else if (!done) atomicCAS(&ctl->status, 0, ST_TIMEOUT);
       ctl->n_active = na;
