@@ -65,6 +65,21 @@ def workload():
     return wl.catmull_rom_workload(lumen_seed=1, tension_seed=2, n_steps=60)
 
 
+def replica_totals(total_ms, e2e_s, units_per_rank, world, dist=None, device="cuda"):
+    """Whole-job throughput of independent replicas (one handle per rank, no data-path collective):
+    every rank processed units_per_rank solves; the job takes the slowest rank's time, the maximum
+    over ranks of the device-timed and end-to-end times (one all_reduce on `device`).  Returns
+    (t_max_ms, e2e_max_s, value, e2e_value) with value = all ranks' solves / t_max."""
+    t_max, e2e_max = float(total_ms), float(e2e_s)
+    if dist is not None and world > 1:
+        import torch
+        tt = torch.tensor([t_max, e2e_max], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max, e2e_max = float(tt[0]), float(tt[1])
+    n = units_per_rank * world
+    return t_max, e2e_max, n / (t_max / 1000.0), n / e2e_max
+
+
 def config_dict(w, extra=None):
     c = {"workload": "%s insertion sweep 0->600 mm, 60 warm-started solves" % w.name,
          "n_elements": int(w.robot.n_elements), "n_triangles": int(len(w.lumen.triangles)),
@@ -659,16 +674,7 @@ def ours(args, rank, world, local_rank):
                      "vs_fp64_gpu": {"solves_compared": both_ok, "max_tip_error_m": tip_err,
                                      "max_node_force_rel_error": force_err, "identical_contact_sets": int(same_sets)}}
         progress("precision: %.1f solves/s, tip error %.2e m" % (precision["solves_per_s"], tip_err))
-    # max over ranks
-    t_max = total_ms
-    e2e_max = e2e_s
-    if dist:
-        tt = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max, e2e_max = float(tt[0]), float(tt[1])
-    n_solves = S * args.steps * world
-    value = n_solves / (t_max / 1000.0)
-    e2e_value = n_solves / e2e_max
+    t_max, e2e_max, value, e2e_value = replica_totals(total_ms, e2e_s, S * args.steps, world, dist, "cuda")
     nf = w.robot.n_elements
     el_achieved = ELEMENT_FLOPS * nf / (el_us * 1e-6) / 1e12
     ct_achieved = contact_flops(mc_last, np_last) / (ct_us * 1e-6) / 1e12
