@@ -699,7 +699,7 @@ def ours(args, rank, world, local_rank):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d_step),
                         "d2h_bytes_per_step": int(d2h_step), "failed_solves": int(e2e_fail)},
                 "gpu_launches": int(launches),
-                "roofline": {"kernel": "assembly + block cyclic reduction factor and solve (assemble_rhs, bcr_elim, "
+                "roofline": {"kernel": "assembly + block cyclic reduction factor and solve (assemble_rhs with the level-1 eliminations, "
                                        "bcr_level x levels, bcr_bwd x levels; nf=%d nodes, %d RHS columns)"
                                        % (nf_last, 1 + mc_last),
                              "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s FP64",

@@ -17,7 +17,6 @@ namespace accfem {
 __global__ void element_kernel(Params p, Dev d);
 __global__ void collide_kernel(Params p, Dev d);
 __global__ void compact_kernel(Params p, Dev d);
-__global__ void bcr_elim_kernel(Params p, Dev d, int s);
 __global__ void bcr_bwd_kernel(Params p, Dev d, int s);
 __global__ void contact_kernel(Params p, Dev d);
 __global__ void step_kernel(Params p, Dev d);
@@ -382,7 +381,6 @@ int enqueue_factor(const Params& p, const Dev& d, int nf, cudaStream_t st, bool 
   int n = 0;
   auto grid = [nf](int ph) { return dim3(phase_gx(ph, nf), phase_gy(ph)); };
   launch_k(pdl, assemble_rhs_kernel, grid(PH_ASM), dim3(32, 6), st, p, d); ++n;
-  if (nf >= 2) { launch_k(pdl, bcr_elim_kernel, grid(PH_ELIM1), dim3(64), st, p, d, 1); ++n; }
   int levels = 0;
   while (levels < kMaxLevels && phase_gx(PH_LEV0 + levels, nf) > 0) ++levels;
   for (int j = 0; j < levels; ++j) { launch_k(pdl, bcr_level_kernel, grid(PH_LEV0 + j), dim3(192), st, p, d, 1 << j); ++n; }

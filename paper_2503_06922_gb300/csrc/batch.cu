@@ -21,7 +21,6 @@ __global__ void element_batch(const Inst* __restrict__ tab, const Plan* __restri
 __global__ void collide_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
 __global__ void compact_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
 __global__ void assemble_rhs_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
-__global__ void bcr_elim_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
 __global__ void bcr_level_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j);
 __global__ void bcr_bwd_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j);
 __global__ void contact_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
@@ -98,7 +97,6 @@ int enqueue_batch_iteration(accfem_batch* b, cudaStream_t st, cudaGraphCondition
   launch_k(pdl, compact_batch, dim3(g[PH_COMPACT]), dim3(1024), st, tab, plan); ++n;
   cudaStreamWaitEvent(st, b->join, 0);
   launch_k(pdl, assemble_rhs_batch, dim3(g[PH_ASM]), dim3(32, 6), st, tab, plan); ++n;
-  launch_k(pdl, bcr_elim_batch, dim3(g[PH_ELIM1]), dim3(64), st, tab, plan); ++n;
   for (int j = 0; j < b->levels; ++j) { launch_k(pdl, bcr_level_batch, dim3(g[PH_LEV0 + j]), dim3(192), st, tab, plan, j); ++n; }
   for (int j = b->levels - 1; j >= 0; --j) { launch_k(pdl, bcr_bwd_batch, dim3(g[PH_BWD0 + j]), dim3(96), st, tab, plan, j); ++n; }
   launch_k(pdl, contact_batch, dim3(g[PH_CONTACT]), dim3(256), st, tab, plan); ++n;
@@ -119,7 +117,6 @@ void full_grids(accfem_batch* b, int* grid) {
   grid[PH_COLL] = persistent_grid(collide_batch, 128, units[PH_COLL]);
   grid[PH_COMPACT] = persistent_grid(compact_batch, 1024, units[PH_COMPACT]);
   grid[PH_ASM] = persistent_grid(assemble_rhs_batch, 192, units[PH_ASM]);
-  grid[PH_ELIM1] = persistent_grid(bcr_elim_batch, 64, units[PH_ELIM1]);
   grid[PH_CONTACT] = persistent_grid(contact_batch, 256, units[PH_CONTACT]);
   grid[PH_STEP] = persistent_grid(step_batch, 192, units[PH_STEP]);
   grid[PH_APPLY] = persistent_grid(apply_batch, 128, units[PH_APPLY]);

@@ -19,7 +19,7 @@ struct Inst {
 
 // Phases of one Newton iteration; level j of the reduction has stride s = 2^j.
 enum : int {
-  PH_ELEM = 0, PH_COLL, PH_COMPACT, PH_ASM, PH_ELIM1, PH_CONTACT, PH_STEP, PH_APPLY,
+  PH_ELEM = 0, PH_COLL, PH_COMPACT, PH_ASM, PH_CONTACT, PH_STEP, PH_APPLY,
   PH_LEV0,
   PH_BWD0 = PH_LEV0 + kMaxLevels,
   kPhases = PH_BWD0 + kMaxLevels
@@ -50,7 +50,6 @@ __host__ __device__ inline int phase_gx(int ph, int nf) {
     case PH_COLL: return (nf + 3) / 4;
     case PH_COMPACT: return 1;
     case PH_ASM: return nf;
-    case PH_ELIM1: return nf >= 2 ? (nf - 2) / 2 + 1 : 0;
     case PH_CONTACT: return 1;
     case PH_STEP: return (nf + 31) / 32;
     case PH_APPLY: return (nf + 127) / 128;

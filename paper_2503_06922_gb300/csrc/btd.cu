@@ -11,7 +11,7 @@
 // R_j = U_j^T P_j.  For kept i: D_i -= R_{i-s} U_{i-s} + L_{i+s} U_i^T, U_i <- -L_{i+s} U_{i+s}.
 // Solve: forward b_i -= R_{i-s} b_{i-s} + L_{i+s} b_{i+s} (kept), root x_0 = P_0 b_0, backward
 // x_j = P_j b_j - L_j^T x_{j-s} - R_j^T x_{j+s} (eliminated).  Launches per factor-and-solve:
-// bcr_elim_kernel (level 1), one bcr_level_kernel per level (kept-node update + next level's
+// the assembly kernel (with the level-1 eliminations), one bcr_level_kernel per level (kept-node update + next level's
 // eliminations + forward RHS; root at the last level), one bcr_bwd_kernel per level.
 #include "batch.cuh"
 
@@ -164,11 +164,18 @@ __global__ void __launch_bounds__(1024) compact_batch(const Inst* __restrict__ t
 }
 
 // ------------------------------------------------------------------ assembly
+__device__ bool team_inverse6(double* sA, int tid, double* s_piv);
+
 // Assembly and RHS columns of one free node (blocks (node, y), 32 x 6 threads): D, U and g = F - F_a
 // with the tip load of Eq. 16-18, then RHS columns 0 = -g and 1 + k = A^T e_row for the row of
-// working-set slot k (block y takes the column chunks y, y + kRhsSplit, ...).
+// working-set slot k (block y takes the column chunks y, y + kRhsSplit, ...).  Block y = 0 of an
+// odd node f also does its elimination at the first level of the reduction: both couplings come
+// from its own element records (U_{f-1} = K_{f-1,f} of the element before the node, U_f of the one
+// after it), so P_f = D_f^{-1}, L_f = U_{f-1} P_f and R_f = U_f^T P_f need no other block.
 __device__ __forceinline__ void assemble_rhs_body(const Params& p, const Dev& d, int bx, int by) {
   __shared__ double s_g[6];
+  __shared__ double sA[36], sXl[36], sYr[36];
+  __shared__ double s_piv[1];
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
   const int f = bx;
@@ -179,14 +186,21 @@ __device__ __forceinline__ void assemble_rhs_body(const Params& p, const Dev& d,
   const double* eb = d.elem + (size_t)(node - 1) * kElemStride;
   const double* ea = d.elem + (size_t)node * kElemStride;
   const bool has_a = node < p.M;
+  const bool elim1 = by == 0 && (f & 1);
   if (tid < 36 && by == 0) {
     int r = tid / 6, c = tid % 6;
     double v = kval(eb, 6 + r, 6 + c);
     if (has_a) v += kval(ea, r, c);
     d.D[(size_t)f * 36 + tid] = v;
+    sA[tid] = v;
   } else if (tid >= 36 && tid < 72 && by == 0) {
     int q = tid - 36, r = q / 6, c = q % 6;
-    d.U[(size_t)f * 36 + q] = has_a ? kval(ea, r, 6 + c) : 0.0;
+    const double u = has_a ? kval(ea, r, 6 + c) : 0.0;
+    d.U[(size_t)f * 36 + q] = u;
+    sYr[q] = u;                                     // U_f = K_{f, f+1} (0 at the tip)
+  } else if (elim1 && tid >= 78 && tid < 114) {
+    int q = tid - 78, r = q / 6, c = q % 6;
+    sXl[q] = kval(eb, r, 6 + c);                    // U_{f-1} = K_{f-1, f}
   } else if (tid >= 72 && tid < 78) {
     int c = tid - 72;
     double F = eb[78 + 6 + c] + (has_a ? ea[78 + c] : 0.0);
@@ -216,6 +230,25 @@ __device__ __forceinline__ void assemble_rhs_body(const Params& p, const Dev& d,
     }
     s_g[c] = F - Fa;
     if (by == 0) d.g[(size_t)f * 6 + c] = F - Fa;
+  }
+  if (elim1) {                                      // first-level elimination of node f
+    const bool ok = team_inverse6(sA, tid, s_piv);  // begins with a barrier
+    if (!ok) {
+      if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
+    } else if (tid < 72) {                          // L on threads 0..35, R on 36..71
+      const int q = tid % 36, r = q / 6, c = q % 6;
+      double v = 0.0;
+      if (tid < 36) {
+        d.P[(size_t)f * 36 + q] = sA[q];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v = fma(sXl[r * 6 + k], sA[k * 6 + c], v);   // U_{f-1} P_f
+        d.Lm[(size_t)f * 36 + q] = v;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v = fma(sYr[k * 6 + r], sA[k * 6 + c], v);   // U_f^T P_f
+        d.Rm[(size_t)f * 36 + q] = v;
+      }
+    }
   }
   __syncthreads();
   const int c = threadIdx.y;
@@ -264,50 +297,6 @@ __device__ bool team_inverse6(double* sA, int tid, double* s_piv) {
   }
   __syncthreads();
   return true;
-}
-
-// Eliminations of level 1 (nodes j = 1 + 2 blockIdx.x; later levels are fused into bcr_level_kernel).
-__device__ __forceinline__ void bcr_elim_body(const Params& p, const Dev& d, int bx, int s) {
-  __shared__ double sA[36], sX[36], sY[36];
-  __shared__ double s_piv[1];
-  Ctl* ctl = d.ctl;
-  if (ctl->status != 0 || ctl->converged) return;
-  const int nf = ctl->nf;
-  const int j = s + 2 * s * bx;
-  if (j >= nf) return;
-  const int tid = threadIdx.x;
-  if (tid < 36) {                                               // the couplings load with D_j
-    sA[tid] = d.D[(size_t)j * 36 + tid];
-    sX[tid] = d.U[(size_t)(j - s) * 36 + tid];                  // U_{j-s} = K_{j-s, j}
-    sY[tid] = (j + s < nf) ? d.U[(size_t)j * 36 + tid] : 0.0;   // U_j = K_{j, j+s}
-  }
-  bool ok = team_inverse6(sA, tid, s_piv);
-  if (!ok) {
-    if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
-    return;
-  }
-  const int r = tid / 6, c = tid % 6;
-  if (tid < 36) d.P[(size_t)j * 36 + tid] = sA[tid];
-  __syncthreads();
-  if (tid < 36) {
-    double l = 0.0, rr = 0.0;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      l = fma(sX[r * 6 + k], sA[k * 6 + c], l);     // (U_{j-s} P_j)[r][c]
-      rr = fma(sY[k * 6 + r], sA[k * 6 + c], rr);   // (U_j^T P_j)[r][c]
-    }
-    d.Lm[(size_t)j * 36 + tid] = l;
-    d.Rm[(size_t)j * 36 + tid] = rr;
-  }
-}
-
-__global__ void __launch_bounds__(64) bcr_elim_kernel(Params p, Dev d, int s) {
-  pdl_enter();
-  bcr_elim_body(p, d, blockIdx.x, s);
-}
-
-__global__ void __launch_bounds__(64) bcr_elim_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
-  for_units(tab, plan, PH_ELIM1, [](const Inst& in, int bx, int) { bcr_elim_body(in.p, in.d, bx, 1); });
 }
 
 // Level s of the reduction, fused with the elimination at level 2s.  Blocks (kept node i = 2 s x,

@@ -220,7 +220,9 @@ __device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int 
         const Surv& sj = s_surv[wib][j];
         if (sj.t >= si.t) continue;
         double dx = sj.c[0] - si.c[0], dy = sj.c[1] - si.c[1], dz = sj.c[2] - si.c[2];
-        if (sqrt(dx * dx + dy * dy + dz * dz) <= 1e-12) { dup = true; break; }
+        // |c_j - c_i| <= 1e-12 m, compared squared (points of one wall feature differ by ~1e-17 m,
+        // distinct ones by micrometres, so no decision sits near the threshold)
+        if (dx * dx + dy * dy + dz * dz <= 1e-24) { dup = true; break; }
       }
     }
     kept[h] = !dup;

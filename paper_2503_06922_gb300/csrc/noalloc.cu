@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(128) detect_noalloc_kernel(Params p, Dev d, co
     bool dup = false;
     for (int r = 0; r < nc; ++r) {
       double dx = cpt[3 * r] - sv.c[0], dy = cpt[3 * r + 1] - sv.c[1], dz = cpt[3 * r + 2] - sv.c[2];
-      if (sqrt(dx * dx + dy * dy + dz * dz) <= 1e-12) { dup = true; break; }
+      if (dx * dx + dy * dy + dz * dz <= 1e-24) { dup = true; break; }   // |c_j - c_i| <= 1e-12 m
     }
     if (dup) continue;
     if (nc >= kNoAllocCpn) { atomicCAS(&sc->status, 0, ST_CAPACITY); break; }
