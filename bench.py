@@ -160,16 +160,46 @@ def oracle_sample(w, budget_s):
     return n, dt
 
 
+def _oracle_worker(budget_s, q):
+    """One worker of the multi-core CPU baseline (a fresh interpreter: one BLAS thread)."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    q.put(oracle_sample(workload(), budget_s))
+
+
+def oracle_sample_parallel(budget_s, procs=None):
+    """Throughput of the oracle on the host's cores: procs independent worker processes (spawned,
+    one BLAS thread each; default one per core), each running the single-thread sample on its own
+    model.  Returns (solves of all workers, the slowest worker's seconds, procs), or None when a
+    worker did not report (its processes are then terminated)."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(budget_s, q)) for _ in range(procs)]
+    for p in ps:
+        p.start()
+    try:
+        res = [q.get(timeout=budget_s * 4 + 300) for _ in ps]
+    except Exception:
+        for p in ps:
+            p.terminate()
+        return None
+    for p in ps:
+        p.join(timeout=60)
+    return sum(n for n, _ in res), max(dt for _, dt in res), procs
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return 0
     w = workload()
     per_step = 6.0
     for _ in range(args.warmup):
-        oracle_sample(w, per_step)
-    times, solves = [], 0
+        oracle_sample(w, 1.0)
+    times, solves, procs = [], 0, 1
     for _ in range(args.steps):
-        n, dt = oracle_sample(w, per_step)
+        n, dt, procs = oracle_sample_parallel(per_step) or (oracle_sample(w, per_step) + (1,))
         times.append(dt)
         solves += n
     total = sum(times)
@@ -178,15 +208,16 @@ def reference_arm(args, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(w),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "first solves of the 60-solve sweep (insertion 10 mm upward) for ~%.0f s per "
-                                       "step; numpy FP64 oracle, single thread" % per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                             "sample": "per step, %d independent worker processes (one per host core, one BLAS thread "
+                                       "each) solving the first solves of the 60-solve sweep (insertion 10 mm upward) "
+                                       "for ~%.0f s; numpy FP64 oracle" % (procs, per_step)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-# Algorithmic FP64 flops per unit (formulas in the design doc, roofline section):
+# Algorithmic FP64 flops per unit:
 #  element kernel, per element: B (7x12) from Tsinv and G, B E^T, K_l B E^T, the 78 tangent entries
 #  and the 12 forces;
 #  contact kernel, per launch with m rows and np active rows: the active W columns 6 m np, the
@@ -689,6 +720,7 @@ def ours(args, rank, world, local_rank):
         extra["frames"] = frames_run(af)
     if rank == 0:
         cpu_n, cpu_dt = oracle_sample(w, 15.0)
+        par_n, par_dt, par_p = oracle_sample_parallel(15.0) or (cpu_n, cpu_dt, 1)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -716,9 +748,13 @@ def ours(args, rank, world, local_rank):
                 "element_roofline": {"achieved": el_achieved, "peak": peak, "unit": "TFLOP/s FP64",
                                      "frac": el_achieved / peak, "flops_per_element": ELEMENT_FLOPS},
                 "clocks": clk.summary(),
-                "cpu_baseline": {"value": cpu_n / cpu_dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": "first %d solves of the sweep (insertion 10..%d mm), %.1f s, numpy FP64 "
-                                           "oracle, single thread" % (cpu_n, 10 * cpu_n, cpu_dt)}}
+                "cpu_baseline": {"value": par_n / par_dt, "unit": UNIT, "cores": par_p, "kind": "oracle",
+                                 "sample": "%d independent worker processes (one per host core, one BLAS thread each), "
+                                           "each solving the first solves of the sweep from 10 mm for ~15 s: %d solves "
+                                           "in %.1f s (slowest worker); numpy FP64 oracle" % (par_p, par_n, par_dt),
+                                 "single_thread": {"value": cpu_n / cpu_dt, "cores": 1,
+                                                   "sample": "first %d solves of the sweep (insertion 10..%d mm), %.1f s"
+                                                             % (cpu_n, 10 * cpu_n, cpu_dt)}}}
         line["precision"] = precision
         line["contact_admm"] = contact_admm
         line.update(extra)
