@@ -174,16 +174,19 @@ def oracle_sample_parallel(budget_s, procs=None):
     worker did not report (its processes are then terminated)."""
     import multiprocessing as mp
     procs = procs or os.cpu_count() or 1
-    ctx = mp.get_context("spawn")
-    q = ctx.Queue()
-    ps = [ctx.Process(target=_oracle_worker, args=(budget_s, q)) for _ in range(procs)]
-    for p in ps:
-        p.start()
+    ps = []
     try:
-        res = [q.get(timeout=budget_s * 4 + 300) for _ in ps]
+        ctx = mp.get_context("spawn")
+        q = ctx.Queue()
+        ps = [ctx.Process(target=_oracle_worker, args=(budget_s, q)) for _ in range(procs)]
+        for p in ps:
+            p.start()
+        # a solve started just before the budget ends may take a few seconds more
+        res = [q.get(timeout=budget_s + 120) for _ in ps]
     except Exception:
         for p in ps:
-            p.terminate()
+            if p.is_alive():
+                p.terminate()
         return None
     for p in ps:
         p.join(timeout=60)
