@@ -38,7 +38,7 @@ from dataclasses import dataclass
 import numpy as np
 import scipy.linalg as sla
 
-from . import beam, contact, lcp
+from . import beam, contact, lcp, segment
 from .rotation import expm, logm, to_quat
 
 CONTACT_COMPLIANCE = 1e-12
@@ -56,6 +56,7 @@ class Options:
     max_contact_iters: int = 4000
     max_contacts: int = 256
     tangent_mode: int = 0          # 0: material tangent K_M; 1: symmetric part of K_T (K_M if not PD)
+    contact_model: str = "node"    # "node": rows at the nodes (xi = 0); "segment": Eq. 3-7 at any xi
 
 
 @dataclass
@@ -225,7 +226,12 @@ class Model:
                 _, ab = self.assemble(x, R, k, 0)
                 c = sla.cholesky_banded(ab, lower=False)
             solve = lambda rhs: sla.cho_solve_banded((c, False), rhs)
-            contacts = contact.detect(x, free, self.V, self.T, r_o, opt.activation_gap) if len(self.T) else []
+            if not len(self.T):
+                contacts = []
+            elif opt.contact_model == "segment":
+                contacts = segment.detect_elements(x, k, self.V, self.T, r_o, opt.activation_gap)
+            else:
+                contacts = contact.detect(x, free, self.V, self.T, r_o, opt.activation_gap)
             m = len(contacts)
             if m > opt.max_contacts:
                 status = E_CONTACT_CAPACITY
@@ -235,8 +241,18 @@ class Model:
                 A = np.zeros((m, 6 * nf))
                 b = np.zeros(m)
                 for i, rec in enumerate(contacts):
-                    col = 6 * (rec["node"] - (k + 1))
-                    A[i, col:col + 3] = rec["normal"]
+                    if "elem" in rec:
+                        # segment row (Eq. 3, 9): n^T du(xi), du(xi) = R_r N(xi) [R_r^T du_a; R_r^T du_b]
+                        e = rec["elem"]
+                        _, Rr = beam.corotated_frame(x[e], R[e], x[e + 1], R[e + 1])
+                        row = rec["normal"] @ segment.row_weights(Rr, rec["s"] * self.l0, self.l0)
+                        for j, node in enumerate((e, e + 1)):
+                            if node > k:
+                                col = 6 * (node - (k + 1))
+                                A[i, col:col + 3] = row[3 * j:3 * j + 3]
+                    else:
+                        col = 6 * (rec["node"] - (k + 1))
+                        A[i, col:col + 3] = rec["normal"]
                     b[i] = rec["gap"]
                 X = solve(A.T)
                 W = A @ X
@@ -259,7 +275,7 @@ class Model:
             dth = dx.reshape(nf, 6)[:, 3:]
             umax = float(np.sqrt((du * du).sum(axis=1)).max())
             step = float(max(umax, r_o * np.sqrt((dth * dth).sum(axis=1)).max()))
-            key = tuple((rec["node"], rec["tri"]) for rec in contacts)
+            key = tuple((rec["node"] if "node" in rec else -1 - rec["elem"], rec["tri"]) for rec in contacts)
             nrm2 = float(np.sum(du * du))
             dot = float(np.sum(du * du_prev)) if du_prev is not None else 0.0
             reverse = du_prev is not None and dot < 0.0
