@@ -137,3 +137,52 @@ def admm_polish(W, q, **admm_args):
         return yp, w, it, True
     ye, we, _ = qp_nnls(W, q)
     return ye, we, it, False
+
+
+def primal_admm(solve_M, K_mul, g, A, b, rho, sigma=1.0e-6, alpha=1.6, eps_rel=1.0e-3, max_iter=4000,
+                check_every=10):
+    """OSQP's ADMM (Stellato et al. 2020) on the primal QP of Eq. 23,
+        min 1/2 dx^T K dx + g^T dx   s.t.  A dx <= b,
+    i.e. OSQP's problem with P = K, l = -inf, u = b.  solve_M applies (K + sigma I + rho A^T A)^-1
+    (factored once by the caller), K_mul applies K.  One iteration:
+        xt = (K + sigma I + rho A^T A)^-1 (sigma x - g + A^T (rho z - lam)),  zt = A xt
+        x <- alpha xt + (1 - alpha) x,  zh = alpha zt + (1 - alpha) z
+        z <- min(zh + lam / rho, b),    lam <- lam + rho (zh - z)
+    stopped when |A x - z| <= eps_rel max(|A x|, |z|) and |K x + g + A^T lam| <= eps_rel max(|K x|,
+    |A^T lam|, |g|) (infinity norms, tested every check_every iterations).  Returns (x, z, lam, iters)."""
+    n, m = len(g), len(b)
+    x = np.zeros(n)
+    z = np.zeros(m)
+    lam = np.zeros(m)
+    it = 0
+    while it < max_iter:
+        it += 1
+        xt = solve_M(sigma * x - g + A.T @ (rho * z - lam))
+        zt = A @ xt
+        x = alpha * xt + (1.0 - alpha) * x
+        zh = alpha * zt + (1.0 - alpha) * z
+        z = np.minimum(zh + lam / rho, b)
+        lam = lam + rho * (zh - z)
+        if it % check_every == 0:
+            Ax, Kx, Atl = A @ x, K_mul(x), A.T @ lam
+            if (np.abs(Ax - z).max() <= eps_rel * max(np.abs(Ax).max(), np.abs(z).max()) and
+                    np.abs(Kx + g + Atl).max() <= eps_rel * max(np.abs(Kx).max(), np.abs(Atl).max(), np.abs(g).max())):
+                break
+    return x, z, lam, it
+
+
+def primal_admm_polish(solve_M, K_mul, g, A, b, rho, W, q, **kw):
+    """The primal ADMM's guess of the active rows (lam > 0: the upper bound z <= b binds), polished
+    exactly: the multipliers of those rows from the contact-space equations W_AA y_A = -q_A
+    (W = A K^-1 A^T, q = b + A K^-1 g, as the caller forms them) and y = 0 elsewhere, accepted when
+    y_A > 0 and every other row keeps A dx <= b (relative 1e-12); otherwise the exact contact-space
+    solution (qp_nnls).  Returns (y, admm_iterations, polished); dx = -K^-1 (g + A^T y)."""
+    x, z, lam, it = primal_admm(solve_M, K_mul, g, A, b, rho, **kw)
+    act = lam > 0.0
+    y = _solve_set(W, q, act)
+    w = W @ y + q
+    sw = max(np.abs(q).max(), 1e-300)
+    if (y[act] > 0.0).all() and (w[~act] >= -1e-12 * sw).all():
+        return y, it, True
+    y, _, _ = qp_nnls(W, q)
+    return y, it, False

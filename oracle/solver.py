@@ -57,6 +57,7 @@ class Options:
     max_contacts: int = 256
     tangent_mode: int = 0          # 0: material tangent K_M; 1: symmetric part of K_T (K_M if not PD)
     contact_model: str = "node"    # "node": rows at the nodes (xi = 0); "segment": Eq. 3-7 at any xi
+    qp_solver: str = "contact"     # "contact": exact contact-space LCP; "primal_admm": OSQP's ADMM on Eq. 23, polished
 
 
 @dataclass
@@ -95,6 +96,17 @@ def cable_load(T_tip, tensions, robot):
         F += T_tip @ F_j
         Mo += T_tip @ np.cross(d_j, F_j)
     return F, Mo
+
+
+def _band_mul(ab, v):
+    """K v for K in symmetric upper banded form ab (ab[u + i - j, j] = K[i, j], i <= j)."""
+    u = ab.shape[0] - 1
+    n = len(v)
+    out = ab[u] * v
+    for d in range(1, u + 1):
+        out[:n - d] += ab[u - d, d:] * v[d:]      # K[i, i + d] v[i + d]
+        out[d:] += ab[u - d, d:] * v[:n - d]      # K[i + d, i] v[i]
+    return out
 
 
 class Model:
@@ -261,7 +273,25 @@ class Model:
                 # makes the LCP uniquely solvable (interpenetration at most eps * y)
                 W = W + CONTACT_COMPLIANCE * np.max(np.diag(W)) * np.eye(m)
                 q = b - A @ dxf
-                y, w, piv = lcp.qp_nnls(W, q)
+                if opt.qp_solver == "primal_admm":
+                    # OSQP on the primal QP: K + sigma I + rho A^T A keeps K's band (a row touches
+                    # the translations of one node, or of the two nodes of an element)
+                    u = ab.shape[0] - 1
+                    rho_admm = 0.1 * float(np.max(ab[u]))
+                    mb = ab.copy()
+                    mb[u] += 1.0e-6
+                    for i in range(m):
+                        nz = np.nonzero(A[i])[0]
+                        for p_ in nz:
+                            for q_ in nz:
+                                if p_ <= q_:
+                                    mb[u + p_ - q_, q_] += rho_admm * A[i, p_] * A[i, q_]
+                    cm = sla.cholesky_banded(mb, lower=False)
+                    y, piv, _ = lcp.primal_admm_polish(
+                        lambda r_: sla.cho_solve_banded((cm, False), r_), lambda v: _band_mul(ab, v),
+                        g, A, b, rho_admm, W, q)
+                else:
+                    y, w, piv = lcp.qp_nnls(W, q)
                 piv_total += piv
                 dx = dxf - X @ y
                 r = g + A.T @ y

@@ -247,3 +247,51 @@ def test_admm_iterates_approach_the_solution():
             errs.append(np.abs(z - ye).max())
             assert np.abs(lam + we).max() <= 100 * eps * max(1.0, np.abs(q).max())
         assert errs[-1] <= 1e-4 * max(1.0, np.abs(ye).max()) and errs[-1] <= errs[0]
+
+
+def test_primal_admm_on_eq23_matches_the_contact_space_solution():
+    """OSQP's ADMM on the primal QP of Eq. 23 (variables dx, rows A dx <= b), polished exactly: the
+    step and the multipliers of the exact contact-space solution; its iterates themselves approach
+    it as the tolerance tightens."""
+    rng = np.random.default_rng(19)
+    for trial in range(25):
+        n = int(rng.integers(4, 30))
+        m = int(rng.integers(1, min(n, 12) + 1))
+        X = rng.normal(size=(n, n + 3))
+        K = X @ X.T / n + 0.1 * np.eye(n)
+        g = rng.normal(size=n)
+        A = rng.normal(size=(m, n))
+        b = rng.normal(size=m) * 0.3
+        rho = 0.1 * np.max(np.diag(K))
+        Mi = np.linalg.inv(K + 1e-6 * np.eye(n) + rho * A.T @ A)
+        Xk = np.linalg.solve(K, A.T)
+        dxf = -np.linalg.solve(K, g)
+        W = A @ Xk
+        q = b - A @ dxf
+        y, it, polished = lcp.primal_admm_polish(lambda r: Mi @ r, lambda v: K @ v, g, A, b, rho, W, q)
+        ye = lcp.murty(W, q)[0]
+        assert np.allclose(y, ye, atol=1e-10), trial
+        dx = dxf - Xk @ y
+        assert (A @ dx <= b + 1e-10).all()
+        if trial < 5:
+            xs, zs, lams, _ = lcp.primal_admm(lambda r: Mi @ r, lambda v: K @ v, g, A, b, rho, eps_rel=1e-9,
+                                              max_iter=200000)
+            assert np.abs(xs - (dxf - Xk @ ye)).max() <= 1e-6 * max(1.0, np.abs(dx).max())
+            assert np.abs(lams - ye).max() <= 1e-6 * max(1.0, np.abs(ye).max())
+
+
+def test_solver_with_primal_admm_equals_the_default():
+    """The Newton solve with the primal ADMM as its QP solver reaches the same states in the same
+    iterations as with the exact contact-space solver (bent tube, contacts from step 5)."""
+    from oracle import solver
+    w = wl.bent_tube_workload(0, n_steps=10)
+    a = solver.Model(w.robot, w.lumen)
+    b = solver.Model(w.robot, w.lumen, solver.Options(qp_solver="primal_admm"))
+    rows = 0
+    for s in range(len(w.insertions)):
+        ra = a.solve(w.tensions[s], w.insertions[s])
+        rb = b.solve(w.tensions[s], w.insertions[s])
+        assert ra.status == rb.status == solver.OK and ra.newton_iters == rb.newton_iters, s
+        assert np.abs(ra.node_pos - rb.node_pos).max() <= 1e-12 * np.abs(ra.node_pos).max(), s
+        rows += len(rb.contacts)
+    assert rows > 0
