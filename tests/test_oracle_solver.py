@@ -173,3 +173,33 @@ def test_non_penetration_and_complementarity(bent_sweep):
             p = r.node_pos[c["node"]]
             gap = np.dot(c["normal"], c["point"] - p) - w.robot.outer_radius
             assert abs(gap) <= 1e-9
+
+
+def test_base_reaction_balances_every_external_load():
+    """The reported base reaction is F(x) at the last prescribed node: the strain energy is invariant
+    under rigid motions, so the internal forces of the chain sum to zero and the clamp's reaction
+    balances every external load on the free nodes -- force -(sum f) and moment -(sum (x_i - x_k) x f_i
+    + sum m_i) -- at any deflection, with contacts included."""
+    f = np.array([0.0, 0.8, 0.3])
+    mo = np.array([0.01, 0.0, 0.02])
+    r = _model(step_limit=5e-3).solve(delta=L, tip_load=(tuple(f), tuple(mo), False))
+    assert r.status == solver.OK
+    assert np.allclose(r.base_reaction[:3], -f, atol=1e-10)
+    assert np.allclose(r.base_reaction[3:], -(np.cross(r.node_pos[-1] - r.node_pos[0], f) + mo), atol=1e-10)
+    # bent tube: follower cable load of Eq. 16-18 and the contact forces -y_i n_i
+    w = wl.bent_tube_workload(0, n_steps=10)
+    m = solver.Model(w.robot, w.lumen)
+    for s in range(len(w.insertions)):
+        rb = m.solve(w.tensions[s], w.insertions[s])
+    assert rb.status == solver.OK and len(rb.contacts) > 0
+    k = solver.n_prescribed_last(w.robot.length, w.robot.n_elements, w.insertions[-1])
+    xk = rb.node_pos[k]
+    fc, mc = solver.cable_load(from_quat(rb.node_quat[-1]), w.tensions[-1], w.robot)
+    F = fc.copy()
+    Mo = np.cross(rb.node_pos[-1] - xk, fc) + mc
+    for c in rb.contacts:
+        fi = -c["force"] * np.asarray(c["normal"])
+        F += fi
+        Mo += np.cross(rb.node_pos[c["node"]] - xk, fi)
+    assert np.allclose(rb.base_reaction[:3], -F, atol=1e-6)
+    assert np.allclose(rb.base_reaction[3:], -Mo, atol=1e-8)
