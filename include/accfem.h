@@ -210,7 +210,7 @@ accfem_status accfem_transfer_bytes(const accfem_handle* h, int64_t* h2d, int64_
 typedef enum {
   ACCFEM_KERNEL_ELEMENT = 0,    /* corotational force + tangent, one warp per element            */
   ACCFEM_KERNEL_COLLIDE = 1,    /* node-vs-triangle detection, one warp per free node            */
-  ACCFEM_KERNEL_ASSEMBLE = 2,   /* block-tridiagonal assembly and RHS columns                     */
+  ACCFEM_KERNEL_ASSEMBLE = 2,   /* block-tridiagonal assembly, RHS columns, level-1 eliminations  */
   ACCFEM_KERNEL_CONTACT = 3,    /* W = A K^-1 A^T and the contact LCP (needs a completed solve)  */
   ACCFEM_KERNEL_FACTOR = 4      /* assembly + block cyclic reduction factor and multi-RHS solve:
                                    every launch of one iteration's sequence, timed as one unit   */
