@@ -76,3 +76,18 @@ def test_invalid_descriptors_are_rejected_before_any_device_work(lib):
         af.AccFem(w.robot, w.lumen, tangent_mode=1)
     H = ctypes.c_void_p()
     assert lib.accfem_create(None, None, None, ctypes.byref(H)) == af.E_INVALID_ARG
+
+
+def test_setters_and_queries_reject_a_null_handle(lib):
+    """Every entry point taking a handle answers E_INVALID_ARG for NULL before touching a device."""
+    from paper_2503_06922_gb300 import accfem as af
+    E = np.zeros(20)
+    assert lib.accfem_set_precision(None, 0) == af.E_INVALID_ARG
+    assert lib.accfem_set_frame_mode(None, 1) == af.E_INVALID_ARG
+    assert lib.accfem_set_contact_solver(None, 0) == af.E_INVALID_ARG
+    assert lib.accfem_set_element_modulus(None, E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 20) == af.E_INVALID_ARG
+    assert lib.accfem_set_stream(None, None) == af.E_INVALID_ARG
+    assert lib.accfem_reset(None) == af.E_INVALID_ARG
+    n = ctypes.c_int64()
+    assert lib.accfem_device_bytes(None, ctypes.byref(n)) == af.E_INVALID_ARG
+    assert lib.accfem_batch_autotune(None, 1) == af.E_INVALID_ARG
