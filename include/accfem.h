@@ -123,7 +123,10 @@ accfem_status accfem_default_options(accfem_options* out);
 
 /* Creates a handle on the current CUDA device: copies robot and lumen, builds the lumen's
  * uniform grid, allocates all device memory for M elements and max_contacts rows.
- * options may be NULL (defaults).  On failure *out is NULL and the status says why. */
+ * options may be NULL (defaults).  On failure *out is NULL and the status says why.  The handle
+ * records its device: calls that launch work on it (solves, state reads, kernel timing, the
+ * allocation-free query, batches of it) return ACCFEM_E_INVALID_ARG with a message when another
+ * device is current. */
 accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_desc* lumen,
                             const accfem_options* options, accfem_handle** out);
 
@@ -222,21 +225,24 @@ typedef enum {
  * in *us, measured with CUDA events on the handle's stream.  For measurement. */
 accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t reps, double* us);
 
-/* Collision query that allocates no memory, for callers that cannot call cudaMalloc while they run
- * (for example code inside CUDA stream capture, where allocation calls are not allowed, or a
- * real-time loop running under a fixed device-memory budget).  The paper has no counterpart: it is
- * the constraint detection of accfem_solve for n_nodes caller positions (device memory, 3 doubles
- * each, node i = entry i) against the handle's lumen, with the same rule and results as the rows
- * accfem_solve reports.  Inputs and outputs are caller-owned DEVICE buffers: up to row_capacity
- * rows are written in (node, triangle) order to row_node, row_tri, row_point (3 per row),
- * row_normal (3 per row) and row_gap (the b_i of Eq. 10); *n_rows (device int32) receives the
- * total row count.  The work runs on stream (a cudaStream_t; NULL = the handle's stream) and the
- * call waits for it.  Per-node scratch lives in one fixed device array of the library sized for
- * n_nodes <= 4096 (about 2 MB, held by every GPU that loads the library until the process exits);
- * larger n_nodes returns ACCFEM_E_INVALID_ARG.  ACCFEM_E_CONTACT_CAPACITY when a node has more
- * candidates or rows than the fixed per-node limits or the rows exceed row_capacity.  The first
- * call on a device looks up the array's device address; make that first call before any stream
- * capture.  All calls share the one array: calls that overlap on the GPU (other streams or
+/* Collision query that allocates no memory.  The paper has no counterpart: this entry point exists
+ * for callers that must not call cudaMalloc (or any allocating routine) once they run, for example a
+ * real-time control loop that reserves all of its device memory at start-up and may not grow it, or
+ * a host application that hands this library a fixed device-memory budget and owns every allocation
+ * itself.  It is the constraint detection of accfem_solve for n_nodes caller positions (device memory,
+ * 3 doubles each, node i = entry i) against the handle's lumen, with the same rule, the same
+ * per-node limits (at most 64 triangles reach the exact FP64 test and at most 16 rows per node) and
+ * the same rows as accfem_solve reports.  Inputs and outputs are caller-owned DEVICE buffers: up to
+ * row_capacity rows are written in (node, triangle) order to row_node, row_tri, row_point (3 per row),
+ * row_normal (3 per row) and row_gap (the b_i of Eq. 10); *n_rows (device int32) receives the total
+ * row count.  The work runs on stream (a cudaStream_t; NULL = the handle's stream) and the call waits
+ * for it.  Per-node scratch lives in one fixed device array of the library sized for n_nodes <= 4096
+ * (about 4 MB, held by every GPU that loads the library until the process exits); larger n_nodes
+ * returns ACCFEM_E_INVALID_ARG, as does a current device other than the handle's.
+ * ACCFEM_E_CONTACT_CAPACITY when a node exceeds the per-node limits above or the rows exceed
+ * row_capacity.  The first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.  All calls share the
+ * one array, which keeps the last call's contents: calls that overlap on the GPU (other streams or
  * threads) race and must not be issued concurrently. */
 accfem_status accfem_detect_contacts_noalloc(accfem_handle* h, const double* node_pos, int32_t n_nodes,
                                              int32_t row_capacity, int32_t* row_node, int32_t* row_tri,
@@ -321,9 +327,14 @@ typedef struct {
  * footprint: the batch's own memory, then members in index order while the total stays within
  * hbm_cap_bytes (<= 0: no cap); requests of members left out are answered ACCFEM_E_NOMEM without a
  * solve.  Returns when every request is answered (responses[k] for requests[k]); all members must
- * be idle at the call. */
+ * be idle at the call.  results (may be NULL): n_requests caller-owned results with buffers sized for
+ * each request's member, as for accfem_solve; when given, every solved request's full result (poses,
+ * constraint rows, contact forces, base reaction, counts) is also written to results[k], gathered with
+ * the other solves that finished in the same launch (one more kernel and copy per launch, before the
+ * answers of that launch are ready). */
 accfem_status accfem_batch_serve(accfem_batch* b, const accfem_request* requests, int32_t n_requests,
-                                 int32_t chunk_iters, int64_t hbm_cap_bytes, accfem_response* responses);
+                                 int32_t chunk_iters, int64_t hbm_cap_bytes, accfem_response* responses,
+                                 accfem_result* results);
 
 /* Autotuning of the work packing.  The batch's phase kernels are persistent; they can run on
  * their full resident grid or on 1/2, 1/4 or 1/8 of it (more units per block, fewer idle blocks).

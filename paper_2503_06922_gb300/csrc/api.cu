@@ -302,7 +302,8 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
   }
 
   // ---- device memory
-  if (!cuda_ok(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate") ||
+  if (!cuda_ok(h, cudaGetDevice(&h->device), "cudaGetDevice") ||
+      !cuda_ok(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate") ||
       !cuda_ok(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking), "cudaStreamCreate") ||
       !cuda_ok(h, cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming), "cudaEventCreate") ||
       !cuda_ok(h, cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming), "cudaEventCreate")) {
@@ -459,6 +460,7 @@ accfem_status run_solve(accfem_handle* h, int load_mode, const double* tensions_
                         const double* tip_f, const double* tip_m, double insertion, const accfem_state* warm) {
   Params& p = h->p;
   Dev& d = h->d;
+  if (!accfem_on_device(h, "solve")) return ACCFEM_E_INVALID_ARG;
   if (!(insertion >= 0.0 && insertion <= p.L)) return fail(h, ACCFEM_E_INVALID_ARG, "insertion outside [0, length]");
   const int k = std::min(std::max(accfem_last_prescribed(p.L, p.M, insertion), 0), p.M);
   const int nf = p.M - k;
@@ -746,6 +748,7 @@ accfem_status accfem_transfer_bytes(const accfem_handle* h, int64_t* h2d, int64_
 
 accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t reps, double* us) {
   if (!h || !us || reps < 1) return fail(h, ACCFEM_E_INVALID_ARG, "NULL argument or reps < 1");
+  if (!accfem_on_device(h, "accfem_time_kernel")) return ACCFEM_E_INVALID_ARG;
   Params& p = h->p;
   Dev& d = h->d;
   Ctl& c = *h->h_ctl;
@@ -813,6 +816,7 @@ accfem_status accfem_device_bytes(const accfem_handle* h, int64_t* bytes) {
 
 accfem_status accfem_get_state(accfem_handle* h, double* node_pos, double* node_quat) {
   if (!h || !node_pos || !node_quat) return fail(h, ACCFEM_E_INVALID_ARG, "NULL argument");
+  if (!accfem_on_device(h, "accfem_get_state")) return ACCFEM_E_INVALID_ARG;
   accfem_result r;
   std::memset(&r, 0, sizeof(r));
   r.node_pos = node_pos;
@@ -838,3 +842,5 @@ bool accfem_internal_views(accfem_handle* h, Params* p, Dev* d, cudaStream_t* st
 void accfem_internal_set_error(accfem_handle* h, const char* msg) {
   if (h) h->err = msg ? msg : "";
 }
+
+bool accfem_internal_on_device(accfem_handle* h, const char* who) { return h && accfem_on_device(h, who); }

@@ -223,6 +223,8 @@ accfem_status accfem_batch_create(accfem_handle* const* members, int32_t n_membe
     if (!members[i]) return ACCFEM_E_INVALID_ARG;
     for (int j = 0; j < i; ++j)
       if (members[j] == members[i]) return ACCFEM_E_INVALID_ARG;
+    // every member on the current device: the batch's kernels read all members' buffers
+    if (!accfem_on_device(members[i], "accfem_batch_create")) return ACCFEM_E_INVALID_ARG;
   }
   accfem_batch* b = new accfem_batch();
   b->members.assign(members, members + n_members);
@@ -319,6 +321,8 @@ accfem_status accfem_batch_begin(accfem_batch* b, int32_t member, const double* 
 accfem_status accfem_batch_advance(accfem_batch* b, int32_t max_iters, int32_t* n_in_flight) {
   if (!b || max_iters < 1) return bfail(b, ACCFEM_E_INVALID_ARG, "NULL batch or max_iters < 1");
   b->err.clear();
+  if (!accfem_on_device(b->members[0], "accfem_batch_advance"))
+    return bfail(b, ACCFEM_E_INVALID_ARG, b->members[0]->err);
   cudaStream_t st = b->work();
   if (b->n_begin > 0) {
     const int nb = b->n_begin;

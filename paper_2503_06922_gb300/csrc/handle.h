@@ -39,6 +39,7 @@ struct accfem_handle {
   cudaStream_t user_stream = nullptr; // caller's stream (accfem_set_stream), else the handle's own
   int64_t h2d = 0, d2h = 0;          // bytes copied by solve / state calls
   int64_t dev_bytes = 0;             // device memory held by the handle
+  int device = -1;                   // CUDA device the handle was created on (all its memory lives there)
   double youngs = 0.0, poisson = 0.0, area = 0.0, inertia = 0.0;   // robot material and section
   cudaStream_t work() const { return user_stream ? user_stream : stream; }
 };
@@ -68,6 +69,17 @@ inline void launch_k(bool pdl, void (*kernel)(K...), dim3 grid, dim3 block, cuda
 inline bool pdl_default() {
   const char* v = std::getenv("ACCFEM_PDL");
   return v && v[0] == '1';
+}
+
+// True when the current CUDA device is the one the handle was created on; otherwise records a message
+// naming `who` and returns false (kernels launched on another device would read this handle's
+// pointers as foreign addresses).
+inline bool accfem_on_device(accfem_handle* h, const char* who) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev == h->device) return true;
+  h->err = std::string(who) + ": the current CUDA device (" + std::to_string(dev) +
+           ") is not the device the handle was created on (" + std::to_string(h->device) + ")";
+  return false;
 }
 
 // Last prescribed node at insertion delta: nodes 0..k sit in the feeder, k = floor((L - delta) M / L).

@@ -3,7 +3,8 @@
 // Same constraint rule and the same two-pass FP32 prefilter / exact FP64 test as collide_kernel,
 // for node positions the caller passes, with the per-node row lists kept in one file-scope
 // device array instead of memory owned by the handle.  Sized for at most kNoAllocMaxNodes nodes
-// (about 2 MB); every GPU that loads the library holds this array until the process exits.
+// and kCpn rows per node, the solve's own per-node limit (about 4 MB); every GPU that loads the
+// library holds this array until the process exits.
 #include <cstring>
 
 #include "../../include/accfem.h"
@@ -13,7 +14,8 @@
 namespace accfem {
 
 constexpr int kNoAllocMaxNodes = 4096;
-constexpr int kNoAllocCpn = 8;        // rows per node in the fixed array (more: capacity status)
+constexpr int kNoAllocCpn = kCpn;     // rows per node in the fixed array, as in collide_kernel
+static_assert(kNoAllocCpn == kCpn, "the query keeps the solve's per-node row limit");
 
 struct NoAllocScratch {
   int ncon[kNoAllocMaxNodes];
@@ -208,6 +210,7 @@ using namespace accfem;
 // Internal views of a handle (defined with the handle in api.cu).
 bool accfem_internal_views(accfem_handle* h, Params* p, Dev* d, cudaStream_t* stream);
 void accfem_internal_set_error(accfem_handle* h, const char* msg);
+bool accfem_internal_on_device(accfem_handle* h, const char* who);
 
 namespace {
 constexpr int kMaxDevices = 64;
@@ -228,6 +231,7 @@ extern "C" accfem_status accfem_detect_contacts_noalloc(accfem_handle* h, const 
     accfem_internal_set_error(h, "accfem_detect_contacts_noalloc: NULL buffer or negative capacity");
     return ACCFEM_E_INVALID_ARG;
   }
+  if (!accfem_internal_on_device(h, "accfem_detect_contacts_noalloc")) return ACCFEM_E_INVALID_ARG;
   Params p;
   Dev d;
   cudaStream_t own;
@@ -249,7 +253,13 @@ extern "C" accfem_status accfem_detect_contacts_noalloc(accfem_handle* h, const 
     g_scratch_addr[dev] = (NoAllocScratch*)addr;
   }
   NoAllocScratch* sc = g_scratch_addr[dev];
-  if (cudaMemsetAsync(&sc->status, 0, sizeof(int), st) != cudaSuccess) return ACCFEM_E_CUDA;
+  {
+    cudaError_t e = cudaMemsetAsync(&sc->status, 0, sizeof(int), st);
+    if (e != cudaSuccess) {
+      accfem_internal_set_error(h, cudaGetErrorString(e));
+      return ACCFEM_E_CUDA;
+    }
+  }
   if (n_nodes > 0) detect_noalloc_kernel<<<(n_nodes + 3) / 4, 128, 0, st>>>(p, d, node_pos, n_nodes, sc);
   rows_noalloc_kernel<<<1, 1024, 0, st>>>(n_nodes, row_capacity, sc, row_node, row_tri, row_point, row_normal, row_gap,
                                           n_rows);
@@ -261,7 +271,9 @@ extern "C" accfem_status accfem_detect_contacts_noalloc(accfem_handle* h, const 
     return ACCFEM_E_CUDA;
   }
   if (res[0] != 0 || res[1] > row_capacity) {
-    accfem_internal_set_error(h, "accfem_detect_contacts_noalloc: more candidates or rows than capacity");
+    accfem_internal_set_error(h, res[0] != 0 ? "accfem_detect_contacts_noalloc: a node has more than 64 triangles for "
+                                               "the exact test or more than 16 rows"
+                                             : "accfem_detect_contacts_noalloc: more rows than row_capacity");
     return ACCFEM_E_CONTACT_CAPACITY;
   }
   return ACCFEM_OK;
