@@ -137,7 +137,7 @@ def load(path=LIB_PATH):
     lib.accfem_batch_last_error.argtypes = [B]
     lib.accfem_batch_last_error.restype = ctypes.c_char_p
     lib.accfem_batch_serve.argtypes = [B, ctypes.POINTER(accfem_request), ctypes.c_int32, ctypes.c_int32,
-                                       ctypes.c_int64, ctypes.POINTER(accfem_response)]
+                                       ctypes.c_int64, ctypes.POINTER(accfem_response), ctypes.POINTER(accfem_result)]
     lib.accfem_device_bytes.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
     lib.accfem_solve_stats.argtypes = [H, _ip, _ip, _ip, _ip]
     lib.accfem_set_precision.argtypes = [H, ctypes.c_int32]
@@ -426,10 +426,12 @@ class AccFemBatch:
             out = {i: self.members[i]._pack(statuses[i], rs[i]) for i in sel}
         return int(st), statuses, out
 
-    def accfem_batch_serve(self, arrivals, members, tensions, insertions, chunk_iters=4, hbm_cap_bytes=0):
+    def accfem_batch_serve(self, arrivals, members, tensions, insertions, chunk_iters=4, hbm_cap_bytes=0,
+                           full_results=False):
         """Serves the requests (arrays of equal length, arrival-sorted) in real time; returns a dict of
         numpy arrays: status, newton_iters, t_begin, t_end, latency, tip (k, 7), n_contacts, and the
-        call's status."""
+        call's status; with full_results, also "results": one dict per request (keys as
+        AccFem.accfem_solve) holding the full answer of that request's solve."""
         k = len(arrivals)
         req = np.zeros(max(k, 1), dtype=REQUEST_DTYPE)
         if k:
@@ -439,14 +441,39 @@ class AccFemBatch:
             req["cable_tensions"][:k, :ta.shape[1]] = ta
             req["insertion"][:k] = insertions
         resp = np.zeros(max(k, 1), dtype=RESPONSE_DTYPE)
+        rs, bufs = None, None
+        if full_results and k:
+            rs = (accfem_result * k)()
+            bufs = []
+            for j in range(k):
+                m = self.members[int(req["member"][j])]
+                cap = m.cap
+                b = {"pos": np.zeros((m.N, 3)), "quat": np.zeros((m.N, 4)), "cn": np.zeros(cap, np.int32),
+                     "ct": np.zeros(cap, np.int32), "cp": np.zeros((cap, 3)), "cnrm": np.zeros((cap, 3)),
+                     "cf": np.zeros(cap), "cap": cap}
+                rs[j] = accfem_result(_ptr(b["pos"]), _ptr(b["quat"]), cap, 0, _ptr(b["cn"], _ip), _ptr(b["ct"], _ip),
+                                      _ptr(b["cp"]), _ptr(b["cnrm"]), _ptr(b["cf"]))
+                bufs.append(b)
         st = self._lib.accfem_batch_serve(self.b, req.ctypes.data_as(ctypes.POINTER(accfem_request)), k,
                                           int(chunk_iters), int(hbm_cap_bytes),
-                                          resp.ctypes.data_as(ctypes.POINTER(accfem_response)))
+                                          resp.ctypes.data_as(ctypes.POINTER(accfem_response)), rs)
         resp = resp[:k]
         out = {"call_status": int(st), "status": resp["status"].copy(), "newton_iters": resp["newton_iters"].copy(),
                "t_begin": resp["t_begin"].copy(), "t_end": resp["t_end"].copy(), "tip": resp["tip"].copy(),
                "n_contacts": resp["n_contacts"].copy()}
         out["latency"] = out["t_end"] - np.asarray(arrivals, dtype=np.float64)
+        if full_results:
+            full = []
+            for j in range(k):
+                b, r = bufs[j], rs[j]
+                m = min(int(r.n_contacts), b["cap"])
+                full.append({"status": int(resp["status"][j]), "node_pos": b["pos"], "node_quat": b["quat"],
+                             "n_contacts": int(r.n_contacts),
+                             "contacts": [{"node": int(b["cn"][i]), "tri": int(b["ct"][i]), "point": b["cp"][i].copy(),
+                                           "normal": b["cnrm"][i].copy(), "force": float(b["cf"][i])} for i in range(m)],
+                             "base_reaction": np.array(r.base_reaction[:]), "newton_iters": int(r.newton_iters),
+                             "contact_iters": int(r.contact_iters), "residual": float(r.residual)})
+            out["results"] = full
         return out
 
     def accfem_batch_autotune(self, trials):

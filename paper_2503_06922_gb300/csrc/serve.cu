@@ -3,7 +3,8 @@
 // started from that scene's resident state; requests of one scene run in arrival order, requests of
 // different scenes overlap on the device.  The loop admits the requests that have arrived into idle
 // scenes, advances everything in flight by a few Newton iterations (one batch graph launch), and
-// answers the solves that finished with their tip pose, gathered in one kernel and one copy.
+// answers the solves that finished with their tip pose, gathered in one kernel and one copy (and, when
+// the caller asks for them, their full results through the batch's result gather).
 #include <chrono>
 #include <deque>
 #include <thread>
@@ -33,7 +34,7 @@ using namespace accfem;
 extern "C" {
 
 accfem_status accfem_batch_serve(accfem_batch* b, const accfem_request* requests, int32_t n_requests, int32_t chunk_iters,
-                                 int64_t hbm_cap_bytes, accfem_response* responses) {
+                                 int64_t hbm_cap_bytes, accfem_response* responses, accfem_result* results) {
   if (!b) return ACCFEM_E_INVALID_ARG;
   b->err.clear();
   if (n_requests < 0 || chunk_iters < 1 || (n_requests > 0 && (!requests || !responses)))
@@ -117,6 +118,16 @@ accfem_status accfem_batch_serve(accfem_batch* b, const accfem_request* requests
       return ACCFEM_E_CUDA;
     b->h2d += sizeof(int) * nf;
     b->d2h += sizeof(double) * 8 * nf;
+    if (results) {
+      // full answers (poses, rows, forces) of the finished solves, into the callers' result buffers
+      std::vector<accfem_result> full(nf);
+      std::vector<accfem_status> fst(nf);
+      for (int j = 0; j < nf; ++j) full[j] = results[current[fin[j]]];
+      const accfem_status r = accfem_batch_results(b, fin.data(), nf, full.data(), fst.data());
+      if (r == ACCFEM_E_CUDA || r == ACCFEM_E_INVALID_ARG) return r;
+      b->err.clear();
+      for (int j = 0; j < nf; ++j) results[current[fin[j]]] = full[j];
+    }
     const double te = now();
     for (int j = 0; j < nf; ++j) {
       const int i = fin[j], k = current[i];
