@@ -39,6 +39,18 @@ UNIT = "solves/s"
 T_START = time.perf_counter()
 
 
+def _measured_hbm_gbs():
+    """HBM copy bandwidth measured on the GB300s (MEASURED_PEAKS.json), else 6800 GB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
+MEASURED_HBM_GBS = _measured_hbm_gbs()
+
+
 def progress(msg):
     """Timestamped progress on stderr (the JSON line alone goes to stdout)."""
     print("[bench %7.1fs] %s" % (time.perf_counter() - T_START, msg), file=sys.stderr, flush=True)
@@ -54,6 +66,9 @@ def parse():
                     help="run the first N solves of the sweep once (for profilers) and exit")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="run N instances of the batched workload through their first steps (for profilers) and exit")
+    ap.add_argument("--profile-steps", type=int, default=6, help="steps of --profile-batch")
+    ap.add_argument("--profile-factor", action="store_true",
+                    help="run the sweep, then launch the factor group twice on its final state (for profilers) and exit")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched, served, tree-precision and frame-mode measurements")
     ap.add_argument("--frames-only", action="store_true", help="run the frame-mode measurement alone and exit")
@@ -146,43 +161,62 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(w, budget_s):
-    """The CPU oracle, as it stands, on the first solves of the sweep until budget_s elapses."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    from oracle import solver
-    m = solver.Model(w.robot, w.lumen)
-    n = 0
-    t0 = time.perf_counter()
-    while n < len(w.insertions) and time.perf_counter() - t0 < budget_s:
-        m.solve(w.tensions[n], w.insertions[n])
-        n += 1
-    dt = time.perf_counter() - t0
-    return n, dt
+RECORD = os.path.join(ROOT, "oracle", "records", "catmull_rom_600mm_M300_sweep.npz")
 
 
-def _oracle_worker(budget_s, q):
-    """One worker of the multi-core CPU baseline (a fresh interpreter: one BLAS thread)."""
+def _oracle_iteration_worker(s, n_iters, record, q):
+    """One worker of the CPU baseline (a fresh interpreter, one BLAS thread): the oracle, as it stands,
+    starts solve s of the sweep from its own recorded state after solve s - 1 and runs n_iters Newton
+    iterations; reports (s, seconds per iteration)."""
     os.environ["OMP_NUM_THREADS"] = "1"
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
-    q.put(oracle_sample(workload(), budget_s))
+    from oracle import solver
+    w = workload()
+    rec = np.load(record)
+    m = solver.Model(w.robot, w.lumen, solver.Options(max_newton_iters=n_iters))
+    if s > 0:
+        m.state = (rec["pos"][s - 1].copy(), rec["rot"][s - 1].copy(), float(w.insertions[s - 1]))
+    t0 = time.perf_counter()
+    r = m.solve(w.tensions[s], w.insertions[s])
+    q.put((s, (time.perf_counter() - t0) / max(r.newton_iters, 1)))
 
 
-def oracle_sample_parallel(budget_s, procs=None):
-    """Throughput of the oracle on the host's cores: procs independent worker processes (spawned,
-    one BLAS thread each; default one per core), each running the single-thread sample on its own
-    model.  Returns (solves of all workers, the slowest worker's seconds, procs), or None when a
-    worker did not report (its processes are then terminated)."""
+def oracle_sweep_baseline(procs=None, n_iters=1, offset=0.5, picks=None):
+    """Throughput of the oracle over the whole 60-solve sweep on the host's cores, from a stratified
+    sample: procs worker processes (spawned, one per core, one BLAS thread each) run at the same time,
+    worker k timing n_iters Newton iterations of solve s_k = floor((k + offset) S / procs), started
+    from the oracle's recorded state after the previous solve (oracle/record_sweep.py).  The seconds
+    per iteration are interpolated over the sweep and weighted by the oracle's own iteration count of
+    every solve (from the record): T = sum_s iters_s t(s) is the oracle's time for the whole sweep on
+    one of procs busy cores, and procs independent sweeps give procs S / T solves/s.  Returns a dict
+    or None when a worker did not report."""
     import multiprocessing as mp
     procs = procs or os.cpu_count() or 1
+    if not os.path.exists(RECORD):
+        return None
+    rec = np.load(RECORD)
+    S = len(rec["insertions"])
+    if not np.all(rec["status"] == 0):
+        return None
+    if picks is None:
+        picks = sorted({min(S - 1, int(math.floor((k + offset) * S / procs))) for k in range(procs)})
     ps = []
     try:
         ctx = mp.get_context("spawn")
         q = ctx.Queue()
-        ps = [ctx.Process(target=_oracle_worker, args=(budget_s, q)) for _ in range(procs)]
+        t0 = time.perf_counter()
+        ps = [ctx.Process(target=_oracle_iteration_worker, args=(s, n_iters, RECORD, q)) for s in picks]
         for p in ps:
             p.start()
-        # a solve started just before the budget ends may take a few seconds more
-        res = [q.get(timeout=budget_s + 120) for _ in ps]
+        res = {}
+        while len(res) < len(ps):
+            try:
+                k, v = q.get(timeout=5.0)
+                res[k] = v
+            except Exception:
+                if not any(p.is_alive() for p in ps) and q.empty():
+                    raise RuntimeError("a CPU baseline worker exited without reporting")
+        wall = time.perf_counter() - t0
     except Exception:
         for p in ps:
             if p.is_alive():
@@ -190,31 +224,44 @@ def oracle_sample_parallel(budget_s, procs=None):
         return None
     for p in ps:
         p.join(timeout=60)
-    return sum(n for n, _ in res), max(dt for _, dt in res), procs
+    xs = np.array(sorted(res))
+    t_it = np.interp(np.arange(S), xs, np.array([res[x] for x in xs]))
+    T = float(np.sum(rec["newton_iters"] * t_it))
+    return {"value": len(picks) * S / T, "cores": len(picks), "sweep_seconds_one_core": T,
+            "sampled_solves": [int(x) for x in xs], "seconds_per_iteration": [float(res[x]) for x in xs],
+            "wall_s": wall, "oracle_iters_per_solve": float(np.mean(rec["newton_iters"]))}
 
 
 def reference_arm(args, rank):
+    """The oracle as it stands on the host cores (the reference of this comparison): each step one
+    stratified sample of the whole sweep (oracle_sweep_baseline, the sample points shifted from step
+    to step); the line's value is the mean of the steps' estimates."""
     if rank != 0:
         return 0
     w = workload()
-    per_step = 6.0
-    for _ in range(args.warmup):
-        oracle_sample(w, 1.0)
-    times, solves, procs = [], 0, 1
-    for _ in range(args.steps):
-        n, dt, procs = oracle_sample_parallel(per_step) or (oracle_sample(w, per_step) + (1,))
-        times.append(dt)
-        solves += n
-    total = sum(times)
-    value = solves / total
+    for k in range(args.warmup):           # every step spawns fresh workers: warm the file cache only
+        oracle_sweep_baseline(n_iters=1, picks=[0])
+    vals, walls, last = [], [], None
+    for k in range(args.steps):
+        last = oracle_sweep_baseline(n_iters=1, offset=(k + 0.5) / max(args.steps, 1))
+        if last is None:
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle's sweep record is missing or a worker "
+                                                                  "did not report"}), flush=True)
+            return 0
+        vals.append(last["value"])
+        walls.append(last["wall_s"])
+    value = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * float(np.mean(walls)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(w),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
-                             "sample": "per step, %d independent worker processes (one per host core, one BLAS thread "
-                                       "each) solving the first solves of the 60-solve sweep (insertion 10 mm upward) "
-                                       "for ~%.0f s; numpy FP64 oracle" % (procs, per_step)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                             "sample": "per step, %d worker processes (one per host core, one BLAS thread each) at "
+                                       "once, each timing one Newton iteration of one solve of the 60-solve sweep "
+                                       "(stratified over the sweep, shifted per step) from the oracle's recorded "
+                                       "state; seconds per iteration interpolated over the sweep and weighted by the "
+                                       "oracle's recorded iterations per solve (%.1f on average); numpy FP64 oracle"
+                                       % (last["cores"], last["oracle_iters_per_solve"])},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -307,6 +354,53 @@ def _one_launch_vs_sequential(af, b, hs, ws, seed=5):
             "max_tip_difference_m": tip}
 
 
+# Algorithmic bytes per item of the batched phases (HBM roofline):
+#  element, per element: the node frame it adds to the sweep (7 doubles, each node read by two
+#  elements counted once), its stiffness constants (3 doubles) and its record (78 tangent entries and
+#  12 forces): (7 + 3 + 90) x 8 = 800 B;
+#  assembly, per free node: the element record it reads (90 doubles; each record serves two nodes,
+#  counted once) and its block row written (6x6 diagonal block, 6x6 coupling, 6 residual values):
+#  (90 + 36 + 36 + 6) x 8 = 1344 B.
+PHASE_BYTES = {"element": 800.0, "assemble": 1344.0}
+# DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum) of the committed
+# kernels on the same batch, first Newton iteration of all 256 members (profiles/batch256_phase_dram.md);
+# None where no capture of the current kernel exists.
+PHASE_DRAM_BYTES = {"element": None, "collide": None, "assemble": None}
+
+
+def _batch_phase_rooflines(af, b, hs, ws, seed=6):
+    """HBM fractions of the element, collision and assembly phases of the batch: every member starts one
+    more solve (a tension increment from its resident state), the batch advances one Newton iteration,
+    and each phase kernel is timed on the plan of the next iteration (all members still iterating, L2
+    flushed before every launch); then the solves finish."""
+    rng = np.random.default_rng(seed)
+    for i, w in enumerate(ws):
+        t = np.maximum(np.asarray(w.tensions[-1]) + rng.uniform(-0.2, 0.2, 3), 0.0)
+        b.accfem_batch_begin(i, t, w.insertions[-1])
+    st, left = b.accfem_batch_advance(1)
+    out = {}
+    peak = MEASURED_HBM_GBS
+    for name, k in (("element", af.KERNEL_ELEMENT), ("collide", af.KERNEL_COLLIDE), ("assemble", af.KERNEL_ASSEMBLE)):
+        s2, us, items = b.accfem_batch_time_phase(k, 5)
+        if s2 != af.OK:
+            out[name] = {"error": b.accfem_batch_last_error()}
+            continue
+        e = {"us_per_launch": us, "items": items, "members_iterating": left}
+        if name in PHASE_BYTES:
+            byt = PHASE_BYTES[name] * items
+            e.update({"algorithmic_bytes": byt, "bytes_per_item": PHASE_BYTES[name],
+                      "achieved_gbs": byt / (us * 1e-6) / 1e9, "peak_gbs": peak,
+                      "frac": byt / (us * 1e-6) / 1e9 / peak})
+        if PHASE_DRAM_BYTES.get(name) is not None:
+            e["traffic"] = PHASE_DRAM_BYTES[name]
+            e["dram_gbs"] = PHASE_DRAM_BYTES[name] / (us * 1e-6) / 1e9
+        out[name] = e
+    while left:
+        st, left = b.accfem_batch_advance(200)
+    out["note"] = "L2 flushed before each launch; peak = measured copy bandwidth (of measured)"
+    return out
+
+
 def batched_run(af, n_inst=256, chunk=8, seq_sample=16):
     """Uneven batched workload: n_inst instances (element counts log-uniform 50-2000, own lumens,
     target insertion U[0.3, 1] x 600 mm in ~10 mm warm-started steps), every step of every
@@ -345,11 +439,14 @@ def batched_run(af, n_inst=256, chunk=8, seq_sample=16):
         one = _one_launch_vs_sequential(af, b, hs, ws)
         progress("batched %s: one launch of %d solves %.3f s, sequential %.3f s" % (name, n_inst, one["batched_s"],
                                                                                   one["sequential_s"]))
-        out[name] = {"solves_per_s": total / dt, "seconds": dt,
+        phases = _batch_phase_rooflines(af, b, hs, ws) if name == "fp64" else None
+        out[name] = {"solves_per_s": total / dt, "seconds": dt, "phase_roofline": phases,
                      "autotune": {"variant": variant, "grid_divisor": 2 ** max(variant, 0),
                                   "ms_per_iteration_by_variant": [float(x) for x in ms_pass]},
                      "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
                      "newton_iters_per_solve": float(np.mean(res["newton_iters"])), "failed_solves": fails,
+                     "status_counts": {af.accfem_status_string(int(k)): int(v)
+                                       for k, v in zip(*np.unique(res["status"], return_counts=True))},
                      "gpu_launches": int(launches), "one_launch_vs_sequential": one}
         b.close()
     for h in hs:
@@ -447,6 +544,8 @@ def served_run(af, rates=(100.0, 200.0, 2000.0, 5000.0, 10000.0), requests=1200,
                          "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": p99},
                          "newton_iters_per_solve": float(res["newton_iters"].mean()),
                          "failed_solves": int(np.sum(res["status"] != af.OK)),
+                         "status_counts": {af.accfem_status_string(int(k)): int(v)
+                                           for k, v in zip(*np.unique(res["status"], return_counts=True))},
                          "throughput_multiple_over_plain_fp64": sps / pl["capacity_solves_per_s"],
                          "p99_multiple_of_plain_fp64": p99 / pl["latency_ms"]["p99"]})
             progress("served %s: rate %.0f, %d requests, %.0f solves/s, p99 %.1f ms" % (name, rate, len(arr), sps, p99))
@@ -509,7 +608,8 @@ def tree_precision_run(af):
         out["fp64" if mode == af.PRECISION_FP64 else "mixed"] = {
             "solves_per_s": len(res) / dt, "newton_iters_per_solve": float(np.mean([r["newton_iters"] for r in res])),
             "failed_solves": int(sum(r["status"] != af.OK for r in res)),
-            "max_rows": int(max(r["n_contacts"] for r in res)), "fp64_tangent_fallbacks": int(fb)}
+            "max_rows": int(max(r["n_contacts"] for r in res)), "fp64_tangent_fallbacks": int(fb),
+            "per_solve": [[int(r["status"]), int(r["newton_iters"]), int(r["n_contacts"])] for r in res]}
         h.close()
     tip, ferr, same, both = 0.0, 0.0, 0, 0
     for r6, rm in zip(runs[af.PRECISION_FP64], runs[af.PRECISION_MIXED]):
@@ -637,15 +737,32 @@ def config0_run(af, seeds=100):
             "active_contacts_at_100mm": {"min": int(min(act)), "max": int(max(act)), "seeds": len(act)}}
 
 
+def profile_factor_run(args):
+    """The whole sweep in the device-side graph loop (kernels hidden from profilers), then the factor
+    group (assembly, reduction levels, back substitution) launched twice from the host on the final
+    state of the sweep, as bench's roofline times it (for ncu captures of that group)."""
+    import torch
+    from paper_2503_06922_gb300 import accfem as af
+    w = workload()
+    h = af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS)
+    for s in range(len(w.insertions)):
+        h.accfem_solve(w.tensions[s], w.insertions[s])
+    print("factor group: %.1f us per launch, rows %s" % (h.accfem_time_kernel(af.KERNEL_FACTOR, 1),
+                                                         h.accfem_solve_stats()), flush=True)
+    torch.cuda.synchronize()
+    h.close()
+    return 0
+
+
 def profile_batch_run(args):
-    """The first 6 steps of the first N instances of the batched workload, in one batch (for ncu
+    """The first steps of the first N instances of the batched workload, in one batch (for ncu
     captures; with ACCFEM_LAUNCH=stream the phase kernels are launched from a host loop)."""
     import torch
     from paper_2503_06922_gb300 import accfem as af
     ws = wl.batch_workloads(n_instances=256, count=args.profile_batch)
     hs = [af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS) for w in ws]
     b = af.AccFemBatch(hs)
-    for s in range(6):
+    for s in range(args.profile_steps):
         st, sts, _ = b.accfem_batch_solve([w.tensions[s] for w in ws], [w.insertions[s] for w in ws], results=False)
         print("step %d status %d launches %d" % (s, st, b.accfem_batch_kernel_launches()), flush=True)
     torch.cuda.synchronize()
@@ -845,8 +962,7 @@ def ours(args, rank, world, local_rank):
         extra["precision_tree"] = tree_precision_run(af)
         extra["frames"] = frames_run(af)
     if rank == 0:
-        cpu_n, cpu_dt = oracle_sample(w, 15.0)
-        par_n, par_dt, par_p = oracle_sample_parallel(15.0) or (cpu_n, cpu_dt, 1)
+        cpu = oracle_sweep_baseline(n_iters=2)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -877,13 +993,16 @@ def ours(args, rank, world, local_rank):
                 "element_roofline": {"achieved": el_achieved, "peak": peak, "unit": "TFLOP/s FP64",
                                      "frac": el_achieved / peak, "flops_per_element": ELEMENT_FLOPS},
                 "clocks": clk.summary(),
-                "cpu_baseline": {"value": par_n / par_dt, "unit": UNIT, "cores": par_p, "kind": "oracle",
-                                 "sample": "%d independent worker processes (one per host core, one BLAS thread each), "
-                                           "each solving the first solves of the sweep from 10 mm for ~15 s: %d solves "
-                                           "in %.1f s (slowest worker); numpy FP64 oracle" % (par_p, par_n, par_dt),
-                                 "single_thread": {"value": cpu_n / cpu_dt, "cores": 1,
-                                                   "sample": "first %d solves of the sweep (insertion 10..%d mm), %.1f s"
-                                                             % (cpu_n, 10 * cpu_n, cpu_dt)}}}
+                "cpu_baseline": None if cpu is None else {
+                    "value": cpu["value"], "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
+                    "sample": "%d worker processes (one per host core, one BLAS thread each) at once, each timing 2 "
+                              "Newton iterations of one solve of the 60-solve sweep (solves %s, stratified) from the "
+                              "oracle's recorded state after the solve before; seconds per iteration interpolated "
+                              "over the sweep and weighted by the oracle's recorded iterations per solve (%.1f on "
+                              "average): the whole sweep takes %.0f s on one core; numpy FP64 oracle"
+                              % (cpu["cores"], cpu["sampled_solves"], cpu["oracle_iters_per_solve"],
+                                 cpu["sweep_seconds_one_core"]),
+                    "seconds_per_iteration": cpu["seconds_per_iteration"]}}
         line["precision"] = precision
         line["contact_admm"] = contact_admm
         line.update(extra)
@@ -920,6 +1039,8 @@ def main():
         return profile_run(args)
     if args.profile_batch:
         return profile_batch_run(args)
+    if args.profile_factor:
+        return profile_factor_run(args)
     if args.frames_only:
         from paper_2503_06922_gb300 import accfem as af
         af.load()

@@ -346,6 +346,15 @@ accfem_status accfem_batch_autotune(accfem_batch* b, int32_t trials);
  * the measured milliseconds per Newton iteration of each variant (4 values, -1 if not measured). */
 accfem_status accfem_batch_tuning(const accfem_batch* b, int32_t* variant, double* ms_per_pass);
 
+/* Times one phase kernel of the batch (ACCFEM_KERNEL_ELEMENT, _COLLIDE or _ASSEMBLE) on the work plan of
+ * the next iteration: call it after an accfem_batch_advance that left solves in flight.  The kernel
+ * runs reps times (1..1000) on the members still iterating, each launch after a 256 MiB write that
+ * evicts the L2 cache (a temporary device buffer of that size is allocated for the call), timed with
+ * CUDA events on the batch's stream; *us receives the mean microseconds per launch and *items (may be
+ * NULL) the free nodes the launch covers (elements for the element phase).  These phases only read the
+ * poses and rewrite their own outputs, which the next iteration recomputes.  For measurement. */
+accfem_status accfem_batch_time_phase(accfem_batch* b, accfem_kernel kernel, int32_t reps, double* us, int64_t* items);
+
 /* Work stream of the batch's calls (a cudaStream_t; NULL = the batch's own stream). */
 accfem_status accfem_batch_set_stream(accfem_batch* b, void* stream);
 

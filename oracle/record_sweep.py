@@ -1,0 +1,66 @@
+"""Writes the oracle's record of the 600 mm insertion sweep (test and benchmark infrastructure).
+
+The CPU baseline of the benchmark times the oracle on a stratified sample of that sweep: each sampled
+solve starts from the oracle's own converged state of the solve before it.  This script runs the
+oracle, alone, through the whole 60-solve sweep (300 elements, the 63,840-triangle Catmull-Rom tube,
+lumen seed 1, tension seed 2, insertion 10 -> 600 mm) and stores, for every solve, the converged
+poses, the status, the Newton iterations, the number of constraint rows and the seconds it took on
+the machine that wrote it.  Nothing in it comes from the CUDA path.
+
+    python -m oracle.record_sweep [--out PATH] [--resume]
+
+It takes hours on one core (the oracle tests every node against every triangle); --resume continues
+a partial record.
+"""
+import argparse
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DEFAULT_OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "records", "catmull_rom_600mm_M300_sweep.npz")
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=DEFAULT_OUT)
+    ap.add_argument("--resume", action="store_true")
+    args = ap.parse_args(argv)
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import workloads as wl
+    from oracle import solver
+    w = wl.catmull_rom_workload(lumen_seed=1, tension_seed=2, n_steps=60)
+    m = solver.Model(w.robot, w.lumen)
+    S, N = len(w.insertions), w.robot.n_elements + 1
+    rec = {"pos": np.zeros((S, N, 3)), "rot": np.zeros((S, N, 3, 3)), "status": np.full(S, -1, np.int32),
+           "newton_iters": np.zeros(S, np.int32), "rows": np.zeros(S, np.int32), "seconds": np.zeros(S),
+           "insertions": np.asarray(w.insertions, dtype=np.float64), "tensions": np.asarray(w.tensions, dtype=np.float64)}
+    start = 0
+    if args.resume and os.path.exists(args.out):
+        old = np.load(args.out)
+        done = int(np.sum(old["status"] >= 0))
+        for k in rec:
+            rec[k][:done] = old[k][:done]
+        start = done
+        if start > 0:
+            m.state = (rec["pos"][start - 1].copy(), rec["rot"][start - 1].copy(), float(w.insertions[start - 1]))
+    os.makedirs(os.path.dirname(args.out), exist_ok=True)
+    for s in range(start, S):
+        t0 = time.perf_counter()
+        r = m.solve(w.tensions[s], w.insertions[s])
+        rec["seconds"][s] = time.perf_counter() - t0
+        rec["pos"][s], rec["rot"][s] = m.state[0], m.state[1]
+        rec["status"][s], rec["newton_iters"][s], rec["rows"][s] = r.status, r.newton_iters, len(r.contacts)
+        np.savez_compressed(args.out, **rec)
+        print("solve %d status %d newton %d rows %d %.1f s" % (s, r.status, r.newton_iters, len(r.contacts),
+                                                                rec["seconds"][s]), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

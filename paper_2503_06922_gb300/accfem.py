@@ -78,7 +78,7 @@ EXPORTS = ["accfem_default_options", "accfem_create", "accfem_solve", "accfem_so
            "accfem_batch_kernel_launches", "accfem_batch_last_error", "accfem_batch_destroy", "accfem_batch_serve",
            "accfem_device_bytes", "accfem_solve_stats", "accfem_set_precision", "accfem_batch_autotune",
            "accfem_batch_tuning", "accfem_set_element_modulus", "accfem_set_frame_mode",
-           "accfem_set_contact_solver"]
+           "accfem_set_contact_solver", "accfem_batch_time_phase"]
 
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 CONTACT_ACTIVE_SET, CONTACT_ADMM = 0, 1
@@ -146,6 +146,7 @@ def load(path=LIB_PATH):
     lib.accfem_set_contact_solver.argtypes = [H, ctypes.c_int32]
     lib.accfem_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int32]
     lib.accfem_batch_tuning.argtypes = [ctypes.c_void_p, _ip, _dp]
+    lib.accfem_batch_time_phase.argtypes = [B, ctypes.c_int, ctypes.c_int32, _dp, ctypes.POINTER(ctypes.c_int64)]
     lib.accfem_batch_destroy.argtypes = [B]
     lib.accfem_batch_destroy.restype = None
     for name in ("accfem_default_options", "accfem_create", "accfem_solve", "accfem_solve_tip_load",
@@ -155,7 +156,7 @@ def load(path=LIB_PATH):
                  "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream",
                  "accfem_batch_transfer_bytes", "accfem_batch_serve", "accfem_device_bytes", "accfem_solve_stats", "accfem_set_precision",
                  "accfem_batch_autotune", "accfem_batch_tuning", "accfem_set_element_modulus",
-                 "accfem_set_frame_mode", "accfem_set_contact_solver"):
+                 "accfem_set_frame_mode", "accfem_set_contact_solver", "accfem_batch_time_phase"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -475,6 +476,13 @@ class AccFemBatch:
                              "contact_iters": int(r.contact_iters), "residual": float(r.residual)})
             out["results"] = full
         return out
+
+    def accfem_batch_time_phase(self, kernel, reps=5):
+        """(status, mean microseconds per launch after an L2 flush, free nodes covered) of one phase kernel
+        on the plan of the next iteration (KERNEL_ELEMENT, KERNEL_COLLIDE or KERNEL_ASSEMBLE)."""
+        us, items = ctypes.c_double(0.0), ctypes.c_int64(0)
+        st = self._lib.accfem_batch_time_phase(self.b, int(kernel), int(reps), ctypes.byref(us), ctypes.byref(items))
+        return int(st), float(us.value), int(items.value)
 
     def accfem_batch_autotune(self, trials):
         return int(self._lib.accfem_batch_autotune(self.b, int(trials)))

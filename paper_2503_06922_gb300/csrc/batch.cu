@@ -535,6 +535,59 @@ accfem_status accfem_batch_solve(accfem_batch* b, const double* cable_tensions, 
   return first;
 }
 
+accfem_status accfem_batch_time_phase(accfem_batch* b, accfem_kernel kernel, int32_t reps, double* us, int64_t* items) {
+  if (!b || !us || reps < 1 || reps > 1000) return bfail(b, ACCFEM_E_INVALID_ARG, "NULL argument or reps outside 1..1000");
+  if (kernel != ACCFEM_KERNEL_ELEMENT && kernel != ACCFEM_KERNEL_COLLIDE && kernel != ACCFEM_KERNEL_ASSEMBLE)
+    return bfail(b, ACCFEM_E_INVALID_ARG, "only the element, collision and assembly phases can be timed");
+  if (!accfem_on_device(b->members[0], "accfem_batch_time_phase"))
+    return bfail(b, ACCFEM_E_INVALID_ARG, b->members[0]->err);
+  cudaStream_t st = b->work();
+  // the plan of the next iteration: members still iterating after the last advance
+  int n_act = 0;
+  if (!bok(b, cudaMemcpyAsync(&n_act, &b->d_plan->n_act, sizeof(int), cudaMemcpyDeviceToHost, st), "read plan") ||
+      !bok(b, cudaStreamSynchronize(st), "read plan"))
+    return ACCFEM_E_CUDA;
+  if (n_act <= 0) return bfail(b, ACCFEM_E_INVALID_ARG, "no member is iterating (advance with solves in flight first)");
+  std::vector<int> act(n_act);
+  if (!bok(b, cudaMemcpy(act.data(), b->d_plan->act, sizeof(int) * n_act, cudaMemcpyDeviceToHost), "read plan"))
+    return ACCFEM_E_CUDA;
+  int64_t n_items = 0;
+  for (int i : act) n_items += std::max(b->h_ctl[i].nf, 0);
+  // a 256 MiB buffer written before every timed launch evicts the 129 MB L2
+  const size_t flush_bytes = (size_t)256 << 20;
+  void* flush = nullptr;
+  if (!bok(b, cudaMalloc(&flush, flush_bytes), "flush buffer")) return ACCFEM_E_NOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int* g = b->variants[b->variant].grid;
+  double total = 0.0;
+  bool ok = true;
+  for (int r = 0; r < reps && ok; ++r) {
+    ok = bok(b, cudaMemsetAsync(flush, r & 0xff, flush_bytes, st), "flush L2");
+    cudaEventRecord(e0, st);
+    switch (kernel) {
+      case ACCFEM_KERNEL_ELEMENT:
+        element_batch<<<g[PH_ELEM], 32 * kWarpsPerElemBlock, 0, st>>>(b->d_tab, b->d_plan); break;
+      case ACCFEM_KERNEL_COLLIDE: collide_batch<<<g[PH_COLL], 128, 0, st>>>(b->d_tab, b->d_plan); break;
+      default: assemble_rhs_batch<<<g[PH_ASM], dim3(32, 6), 0, st>>>(b->d_tab, b->d_plan); break;
+    }
+    cudaEventRecord(e1, st);
+    ++b->launches;
+    float ms = 0.f;
+    ok = ok && bok(b, cudaGetLastError(), "phase launch") && bok(b, cudaEventSynchronize(e1), "time phase");
+    cudaEventElapsedTime(&ms, e0, e1);
+    total += ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(flush);
+  if (!ok) return ACCFEM_E_CUDA;
+  *us = 1000.0 * total / reps;
+  if (items) *items = n_items;
+  return ACCFEM_OK;
+}
+
 accfem_status accfem_batch_autotune(accfem_batch* b, int32_t trials) {
   if (!b || trials < 1 || trials > 1000) return bfail(b, ACCFEM_E_INVALID_ARG, "trials must be in 1..1000");
   for (int k = 0; k < accfem_batch::kVariants; ++k) { b->tune_ms[k] = 0.0; b->tune_passes[k] = 0; }

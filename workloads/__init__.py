@@ -238,14 +238,11 @@ def _straight_tube(start, d, length, radius, n_around, ds, back=0.0):
     return verts, tris.astype(np.int32)
 
 
-def branching_tree_lumen(seed: int = 3, radii=(0.008, 0.0055, 0.004), n_around=80, ds=0.00025, overlap=1.5):
-    """Seeded 3-generation binary tube tree: a root segment along +x from the origin; each segment
-    ends in two children turned by U[25, 45] deg from its axis, on either side of a random plane
-    through it; segment lengths U[60, 120] mm; radii by generation.  Each tube is meshed with rings
-    every ds and n_around vertices per ring (outward winding); a child's tube starts `overlap`
-    parent radii back inside its parent, and every triangle whose centroid lies inside another tube
-    (within its radius of its axis, between its end rings) is removed.  Returns the lumen and the
-    root-to-leaf path lengths (sum of segment lengths)."""
+def _tree_segments(seed, radii):
+    """Seeded 3-generation binary tree of straight segments: a root along +x from the origin; each
+    segment ends in two children turned by U[25, 45] deg from its axis, on either side of a random
+    plane through it; lengths U[60, 120] mm; radius by generation.  Entries (start, unit direction,
+    length, radius, parent index)."""
     rng = np.random.default_rng(seed)
     segs = []
 
@@ -262,29 +259,152 @@ def branching_tree_lumen(seed: int = 3, radii=(0.008, 0.0055, 0.004), n_around=8
                 add(end, math.cos(ang) * d + sgn * math.sin(ang) * a, gen + 1, me)
 
     add(np.zeros(3), np.array([1.0, 0.0, 0.0]), 0, -1)
-    tubes = []
-    for start, d, length, r, parent in segs:
-        back = overlap * segs[parent][3] if parent >= 0 else 0.0
-        v, t = _straight_tube(start, d, length, r, n_around, ds, back)
-        tubes.append((v, t, start, d, length, r, back))
-    V, T = [], []
-    off = 0
-    for i, (v, t, *_rest) in enumerate(tubes):
-        cen = v[t].mean(axis=1)
-        keep = np.ones(len(t), dtype=bool)
-        for j, (_v, _t, s_j, d_j, l_j, r_j, b_j) in enumerate(tubes):
-            if j == i:
-                continue
-            rel = cen - s_j[None, :]
-            ax = rel @ d_j
-            rad = np.linalg.norm(rel - ax[:, None] * d_j[None, :], axis=1)
-            keep &= ~((ax > -b_j) & (ax < l_j) & (rad < r_j))
-        V.append(v)
-        T.append(t[keep] + off)
-        off += len(v)
-    V = np.concatenate(V)
-    T = np.concatenate(T).astype(np.int32)
-    # root-to-leaf path lengths
+    return segs
+
+
+def _capsule_field(segs, root_back):
+    """Signed distance-like field of the lumen, the union of one capsule per segment (the set of
+    points within the segment's radius of its axis segment): f(x) = min_j (|x - proj_j(x)| - r_j),
+    negative inside.  The root capsule starts root_back before the origin, so the entrance plane
+    x = 0 cuts a straight stretch.  Returns f(points) -> (values, gradients)."""
+    A = np.array([s[0] - (root_back if s[4] < 0 else 0.0) * s[1] for s in segs])
+    D = np.array([s[1] for s in segs])
+    Lj = np.array([s[2] + (root_back if s[4] < 0 else 0.0) for s in segs])
+    R = np.array([s[3] for s in segs])
+
+    def f(P):
+        best = np.full(len(P), np.inf)
+        grad = np.zeros_like(P)
+        for a, d, l, r in zip(A, D, Lj, R):
+            t = np.clip((P - a) @ d, 0.0, l)
+            q = a[None, :] + t[:, None] * d[None, :]
+            v = P - q
+            dist = np.linalg.norm(v, axis=1)
+            val = dist - r
+            upd = val < best
+            best = np.where(upd, val, best)
+            grad[upd] = v[upd] / np.maximum(dist[upd], 1e-300)[:, None]
+        return best, grad
+    return f, A, D, Lj, R
+
+
+def branching_tree_lumen(seed: int = 3, radii=(0.008, 0.0055, 0.004), h=0.00038, root_back=0.030, entrance_cut=0.020):
+    """Seeded 3-generation binary tube tree (segments as _tree_segments), meshed as one closed
+    surface: the boundary of the union of the segments' capsules (hemispherical ends, so every
+    junction is a clean, watertight intersection of tube walls and the leaves are capped), contoured
+    by surface nets on a cubic grid of spacing h restricted to a narrow band around the tube walls:
+    one vertex per grid cell that the surface crosses (the mean of its edge crossings, then moved onto
+    the surface along the field's gradient), one quad (two triangles, the shorter diagonal) per grid
+    edge that the surface crosses, wound outward.  The root starts root_back before the origin and
+    triangles behind x = -entrance_cut are dropped, which opens the entrance.  Returns the lumen and
+    the root-to-leaf path lengths (sum of segment lengths)."""
+    segs = _tree_segments(seed, radii)
+    f, A, D, Lj, R = _capsule_field(segs, root_back)
+    pts_all = np.concatenate([A, A + Lj[:, None] * D])
+    lo = pts_all.min(axis=0) - R.max() - 3 * h
+    hi = pts_all.max(axis=0) + R.max() + 3 * h
+    dims = np.ceil((hi - lo) / h).astype(np.int64) + 1
+    # candidate cells: centres within sqrt(3) h of some capsule wall (narrow band), tube by tube
+    band = math.sqrt(3.0) * h
+    cells = []
+    for a, d, l, r in zip(A, D, Lj, R):
+        blo = np.floor((np.minimum(a, a + l * d) - r - 2 * h - lo) / h).astype(np.int64)
+        bhi = np.ceil((np.maximum(a, a + l * d) + r + 2 * h - lo) / h).astype(np.int64)
+        blo = np.maximum(blo, 0)
+        bhi = np.minimum(bhi, dims - 2)
+        ii = np.arange(blo[0], bhi[0] + 1)
+        for j0 in range(blo[1], bhi[1] + 1, 64):
+            jj = np.arange(j0, min(j0 + 64, bhi[1] + 1))
+            kk = np.arange(blo[2], bhi[2] + 1)
+            I, J, K = np.meshgrid(ii, jj, kk, indexing="ij")
+            I, J, K = I.ravel(), J.ravel(), K.ravel()
+            C = lo[None, :] + (np.stack([I, J, K], axis=1) + 0.5) * h
+            t = np.clip((C - a) @ d, 0.0, l)
+            dist = np.linalg.norm(C - (a[None, :] + t[:, None] * d[None, :]), axis=1)
+            sel = np.abs(dist - r) <= band
+            cells.append((I[sel] * dims[1] + J[sel]) * dims[2] + K[sel])
+    cells = np.unique(np.concatenate(cells))
+    ci, cj, ck = cells // (dims[1] * dims[2]), (cells // dims[2]) % dims[1], cells % dims[2]
+    # field at the cells' corners (each grid point once)
+    offs = np.array([[a_, b_, c_] for a_ in (0, 1) for b_ in (0, 1) for c_ in (0, 1)])
+    corner = ((ci[:, None] + offs[None, :, 0]) * dims[1] + (cj[:, None] + offs[None, :, 1])) * dims[2] \
+        + (ck[:, None] + offs[None, :, 2])
+    gp, inv = np.unique(corner.ravel(), return_inverse=True)
+    gi, gj, gk = gp // (dims[1] * dims[2]), (gp // dims[2]) % dims[1], gp % dims[2]
+    fv = np.empty(len(gp))
+    for c0 in range(0, len(gp), 1 << 20):
+        P = lo[None, :] + np.stack([gi[c0:c0 + (1 << 20)], gj[c0:c0 + (1 << 20)], gk[c0:c0 + (1 << 20)]], axis=1) * h
+        fv[c0:c0 + (1 << 20)] = f(P)[0]
+    fv[fv == 0.0] = 1e-18                     # no grid point exactly on the surface
+    fc = fv[inv].reshape(-1, 8)
+    cross = (fc.min(axis=1) < 0.0) & (fc.max(axis=1) > 0.0)
+    cells, ci, cj, ck, fc = cells[cross], ci[cross], cj[cross], ck[cross], fc[cross]
+    # one vertex per crossed cell: mean of the crossings of its 12 edges
+    edges = [(a_, b_) for a_ in range(8) for b_ in range(8) if a_ < b_ and np.sum(np.abs(offs[a_] - offs[b_])) == 1]
+    acc = np.zeros((len(cells), 3))
+    cnt = np.zeros(len(cells))
+    for a_, b_ in edges:
+        fa, fb = fc[:, a_], fc[:, b_]
+        m = (fa < 0.0) != (fb < 0.0)
+        t = np.where(m, fa / np.where(m, fa - fb, 1.0), 0.0)
+        p = offs[a_][None, :] + t[:, None] * (offs[b_] - offs[a_])[None, :]
+        acc[m] += p[m]
+        cnt[m] += 1
+    V = lo[None, :] + (np.stack([ci, cj, ck], axis=1) + acc / cnt[:, None]) * h
+    for _ in range(3):                        # onto the surface along the gradient
+        val, g = f(V)
+        V = V - val[:, None] * g
+    # one quad per crossed grid edge; the edge from grid point (i, j, k) along axis ax is the min-corner
+    # edge of cell (i, j, k), which is then crossed, and of three more cells around it
+    order = np.argsort(cells)
+    cells_sorted = cells[order]
+
+    def cell_index(I, J, K):
+        key = (I * dims[1] + J) * dims[2] + K
+        pos = np.searchsorted(cells_sorted, key)
+        pos = np.minimum(pos, len(cells_sorted) - 1)
+        ok = cells_sorted[pos] == key
+        return order[pos], ok
+
+    tris = []
+    f0 = fc[:, 0]
+    for ax, (u, w) in enumerate(((1, 2), (2, 0), (0, 1))):
+        nb = [4, 2, 1][ax]                    # corner index of the far end of the axis edge
+        f1 = fc[:, nb]
+        m = (f0 < 0.0) != (f1 < 0.0)
+        base = np.stack([ci[m], cj[m], ck[m]], axis=1)
+        inside_first = f0[m] < 0.0
+        quad = []
+        ok_all = np.ones(len(base), dtype=bool)
+        for du, dw in ((0, 0), (-1, 0), (-1, -1), (0, -1)):
+            q = base.copy()
+            q[:, u] += du
+            q[:, w] += dw
+            idx, ok = cell_index(q[:, 0], q[:, 1], q[:, 2])
+            quad.append(idx)
+            ok_all &= ok
+        quad = np.stack(quad, axis=1)[ok_all]
+        inside_first = inside_first[ok_all]
+        # counter-clockwise around +axis; reversed when the outside lies towards -axis
+        quad[~inside_first] = quad[~inside_first][:, ::-1]
+        a_, b_, c_, d_ = quad.T
+        diag_ac = np.linalg.norm(V[a_] - V[c_], axis=1) <= np.linalg.norm(V[b_] - V[d_], axis=1)
+        t1 = np.where(diag_ac[:, None], np.stack([a_, b_, c_], 1), np.stack([a_, b_, d_], 1))
+        t2 = np.where(diag_ac[:, None], np.stack([a_, c_, d_], 1), np.stack([b_, c_, d_], 1))
+        tris += [t1, t2]
+    T = np.concatenate(tris)
+    nrm = np.cross(V[T[:, 1]] - V[T[:, 0]], V[T[:, 2]] - V[T[:, 0]])
+    area2 = np.linalg.norm(nrm, axis=1)
+    cen = V[T].mean(axis=1)
+    # drop degenerate triangles, and the few slivers folded over by the projection at the sharp ridge
+    # of a carina (their winding disagrees with the field's outward gradient; each is < 0.1 mm^2)
+    _, gc = f(cen)
+    T = T[(area2 > 1e-16) & (np.sum(nrm * gc, axis=1) > 0.0) & (cen[:, 0] >= -entrance_cut)]
+    used = np.unique(T)
+    remap = np.full(len(V), -1, dtype=np.int64)
+    remap[used] = np.arange(len(used))
+    V = V[used]
+    T = remap[T].astype(np.int32)
     paths = []
     for i, (start, d, length, r, parent) in enumerate(segs):
         if any(p == i for *_x, p in segs):
