@@ -67,8 +67,12 @@ def parse():
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="run N instances of the batched workload through their first steps (for profilers) and exit")
     ap.add_argument("--profile-steps", type=int, default=6, help="steps of --profile-batch")
-    ap.add_argument("--profile-factor", action="store_true",
-                    help="run the sweep, then launch the factor group twice on its final state (for profilers) and exit")
+    ap.add_argument("--profile-kernels", action="store_true",
+                    help="run the sweep, then launch the factor group and the contact, element and collision kernels "
+                         "twice each on its final state (for profilers) and exit")
+    ap.add_argument("--profile-phases", action="store_true",
+                    help="run the batched workload, then its element, collision and assembly phases as bench times "
+                         "them (for profilers) and exit")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched, served, tree-precision and frame-mode measurements")
     ap.add_argument("--frames-only", action="store_true", help="run the frame-mode measurement alone and exit")
@@ -737,20 +741,68 @@ def config0_run(af, seeds=100):
             "active_contacts_at_100mm": {"min": int(min(act)), "max": int(max(act)), "seeds": len(act)}}
 
 
-def profile_factor_run(args):
-    """The whole sweep in the device-side graph loop (kernels hidden from profilers), then the factor
-    group (assembly, reduction levels, back substitution) launched twice from the host on the final
-    state of the sweep, as bench's roofline times it (for ncu captures of that group)."""
+def profile_kernels_run(args):
+    """The whole sweep in the device-side graph loop (kernels hidden from profilers), then, launched
+    from the host on the final state of the sweep as bench times them, the factor group (assembly,
+    reduction levels, back substitution) and the contact, element and collision kernels, twice each
+    (for ncu captures)."""
     import torch
     from paper_2503_06922_gb300 import accfem as af
     w = workload()
     h = af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS)
     for s in range(len(w.insertions)):
         h.accfem_solve(w.tensions[s], w.insertions[s])
-    print("factor group: %.1f us per launch, rows %s" % (h.accfem_time_kernel(af.KERNEL_FACTOR, 1),
-                                                         h.accfem_solve_stats()), flush=True)
+    for name, k in (("factor group", af.KERNEL_FACTOR), ("contact", af.KERNEL_CONTACT), ("element", af.KERNEL_ELEMENT),
+                    ("collide", af.KERNEL_COLLIDE)):
+        print("%s: %.1f us per launch" % (name, h.accfem_time_kernel(k, 1)), flush=True)
+    print("rows, working set, active: %s" % (h.accfem_solve_stats(),), flush=True)
     torch.cuda.synchronize()
     h.close()
+    return 0
+
+
+def profile_phases_run(args):
+    """The batched workload (256 uneven instances, all steps, continuous batching in the graph loop);
+    then a second batch over the same members with host-launched phase kernels (visible to
+    profilers): every member begins a tension increment, one Newton iteration of all of them runs
+    inside the NVTX range "iteration", and the element, collision and assembly phases are timed on
+    the next iteration's plan as the bench's phase roofline does, inside the range "phases"."""
+    import torch
+    from paper_2503_06922_gb300 import accfem as af
+    ws = wl.batch_workloads(n_instances=256)
+    hs = [af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS) for w in ws]
+    b = af.AccFemBatch(hs)
+    mem = np.concatenate([np.full(len(w.insertions), i) for i, w in enumerate(ws)])
+    step = np.concatenate([np.arange(len(w.insertions)) for w in ws])
+    ten = np.array([ws[i].tensions[k] for i, k in zip(mem, step)])
+    ins = np.array([ws[i].insertions[k] for i, k in zip(mem, step)])
+    b.accfem_batch_serve(np.zeros(len(mem)), mem, ten, ins, chunk_iters=8)
+    b.close()
+    os.environ["ACCFEM_LAUNCH"] = "stream"
+    b2 = af.AccFemBatch(hs)
+    del os.environ["ACCFEM_LAUNCH"]
+    rng = np.random.default_rng(7)
+    for i, w in enumerate(ws):
+        b2.accfem_batch_begin(i, np.maximum(np.asarray(w.tensions[-1]) + rng.uniform(-0.2, 0.2, 3), 0.0), w.insertions[-1])
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("iteration")
+    st, left = b2.accfem_batch_advance(1)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print("one iteration of %d members, %d left" % (len(ws), left), flush=True)
+    torch.cuda.nvtx.range_push("phases")
+    out = {}
+    for name, k in (("element", af.KERNEL_ELEMENT), ("collide", af.KERNEL_COLLIDE), ("assemble", af.KERNEL_ASSEMBLE)):
+        st, us, items = b2.accfem_batch_time_phase(k, 3)
+        out[name] = {"status": st, "us": us, "items": items}
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps(out), flush=True)
+    while left:
+        st, left = b2.accfem_batch_advance(200)
+    b2.close()
+    for h in hs:
+        h.close()
     return 0
 
 
@@ -1039,8 +1091,10 @@ def main():
         return profile_run(args)
     if args.profile_batch:
         return profile_batch_run(args)
-    if args.profile_factor:
-        return profile_factor_run(args)
+    if args.profile_kernels:
+        return profile_kernels_run(args)
+    if args.profile_phases:
+        return profile_phases_run(args)
     if args.frames_only:
         from paper_2503_06922_gb300 import accfem as af
         af.load()

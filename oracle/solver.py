@@ -21,11 +21,17 @@ One call of ``Model.solve`` is one quasi-static step at a given cable tension an
     that step (so the step is at most halved, and a repeating cycle shrinks geometrically);
     otherwise rho grows by 1.5 back towards beta0.  (A fixed beta0 lets a node on a faceted wall
     overshoot the crease between two facets forever, and the material tangent overshoots the
-    twist of a long bent span by ~2x.)  The material tangent also converges linearly on a slow
-    monotone mode (steps shrinking by ~0.86 per iteration on a long compressed span): after a
-    full step, an unclipped step with the same contact rows, pointing the same way (cosine
-    >= 0.99) and shrinking by lam in [0.5, 0.98], is extended to the secant estimate of the limit,
-    alpha = min(1 / (1 - lam), 8, rho / max|du|).
+    twist of a long bent span by ~2x.)  The material tangent also converges only linearly (a slow
+    bending or twist mode of a long compressed span shrinks by ~0.3-0.9 per iteration), so while
+    the contact rows and the number of active rows stay the same and the step is not clipped, the
+    iteration x <- x (+) dx(x) is accelerated by Anderson's method of depth ACCEL_DEPTH (Walker & Ni
+    2011, "Anderson acceleration for fixed-point iterations"): with f_j the unscaled step of
+    iterate j and d_j the increment applied there, gamma minimises |W (f_k - sum_j gamma_j
+    (f_{k-j} - f_{k-j-1}))| (W weighs rotations by r_o), and the increment is
+    f_k - sum_j gamma_j (d_{k-j-1} + f_{k-j} - f_{k-j-1}); it is taken only when its largest nodal
+    translation, bounded by max|f_k| + sum_j |gamma_j| (max|d_{k-j}| + max|f_{k-j+1} - f_{k-j}|), stays
+    within beta0 and sum |gamma_j| <= ACCEL_GAMMA_MAX; a reversal right after an accelerated
+    step does not shrink rho (extrapolation overshoots by design).
   * convergence: unscaled step max_i max(|du_i|, r_o |dtheta_i|) <= tol and the same contact
     set as the previous iteration.
   * warm start (follow the path): with a resident state at insertion delta_old, material
@@ -42,6 +48,8 @@ from . import beam, contact, lcp, segment
 from .rotation import expm, logm, to_quat
 
 CONTACT_COMPLIANCE = 1e-12
+ACCEL_DEPTH = 3            # Anderson acceleration: previous iterates used
+ACCEL_GAMMA_MAX = 10.0     # largest sum |gamma_j| of an accepted accelerated step
 
 OK, E_INVALID_ARG, E_NOMEM, E_CUDA, E_NOT_CONVERGED, E_CONTACT_CAPACITY, E_NOT_SPD, E_TIMEOUT, E_PENETRATION = range(9)
 
@@ -58,6 +66,7 @@ class Options:
     tangent_mode: int = 0          # 0: material tangent K_M; 1: symmetric part of K_T (K_M if not PD)
     contact_model: str = "node"    # "node": rows at the nodes (xi = 0); "segment": Eq. 3-7 at any xi
     qp_solver: str = "contact"     # "contact": exact contact-space LCP; "primal_admm": OSQP's ADMM on Eq. 23, polished
+    accel_depth: int = ACCEL_DEPTH  # Anderson acceleration of the Newton iteration (0: off)
 
 
 @dataclass
@@ -210,8 +219,10 @@ class Model:
         residual = 0.0
         rho = opt.step_limit           # step bound of the limiter (shrinks when consecutive steps reverse)
         du_prev = None
-        nrm2_prev = 0.0
-        alpha_prev = 0.0
+        hist_f, hist_d, hist_m = [], [], []   # previous iterates: unscaled steps, applied increments and
+                                              # a bound on each increment's largest nodal translation
+        accel_prev = False
+        n_active_prev = -1
         status = E_NOT_CONVERGED
         base_reaction = np.zeros(6)
         if nf == 0:
@@ -306,31 +317,54 @@ class Model:
             umax = float(np.sqrt((du * du).sum(axis=1)).max())
             step = float(max(umax, r_o * np.sqrt((dth * dth).sum(axis=1)).max()))
             key = tuple((rec["node"] if "node" in rec else -1 - rec["elem"], rec["tri"]) for rec in contacts)
-            nrm2 = float(np.sum(du * du))
+            n_active = int(np.sum(y > 0.0)) if m else 0
             dot = float(np.sum(du * du_prev)) if du_prev is not None else 0.0
-            reverse = du_prev is not None and dot < 0.0
+            # a step against the previous one is an overshoot, unless the previous one was extrapolated
+            reverse = du_prev is not None and dot < 0.0 and not accel_prev
             if du_prev is not None:
                 if reverse:
                     rho = max(0.5 * min(rho, umax), opt.step_limit * 2.0 ** -40)
                 else:
                     rho = min(1.5 * rho, opt.step_limit)
             alpha = 1.0 if umax <= rho else rho / umax
-            # over-relaxation of a slow monotone mode: after a full step, an unclipped step with the
-            # same rows pointing the same way (cosine >= 0.99) and shrinking by lam in [0.5, 0.98]
-            # is extended to the secant estimate of the limit, 1 / (1 - lam) times (at most 8, and
-            # within the bound rho)
-            if (du_prev is not None and not reverse and alpha_prev == 1.0 and alpha == 1.0 and key == prev_key
-                    and nrm2_prev > 0.0 and nrm2 > 0.0):
-                lam = math.sqrt(nrm2 / nrm2_prev)
-                cosang = dot / math.sqrt(nrm2 * nrm2_prev)
-                if cosang >= 0.99 and 0.5 <= lam <= 0.98:
-                    alpha = min(1.0 / (1.0 - lam), 8.0, rho / umax)
+            inc = alpha * dx
+            # Anderson acceleration while the rows, the number of active rows and the full step persist
+            steady = du_prev is not None and alpha == 1.0 and key == prev_key and n_active == n_active_prev
+            accel = False
+            bound = alpha * umax
+            if steady and opt.accel_depth > 0 and hist_f:
+                wgt = np.tile(np.array([1.0, 1.0, 1.0, r_o, r_o, r_o]), nf)
+                F = np.array(hist_f + [dx])
+                dF = np.diff(F, axis=0).T                      # columns f_{i+1} - f_i, oldest first
+                dD = np.array(hist_d).T                        # matching increments d_i
+                Wd = dF * wgt[:, None]
+                G = Wd.T @ Wd
+                if np.max(np.diag(G)) > 0.0:
+                    G = G + 1e-10 * np.max(np.diag(G)) * np.eye(len(G))
+                    gam = np.linalg.solve(G, Wd.T @ (dx * wgt))
+                    if np.all(np.isfinite(gam)) and np.sum(np.abs(gam)) <= ACCEL_GAMMA_MAX:
+                        # bound on the largest nodal translation of the accelerated increment
+                        cu = dF.T.reshape(len(gam), nf, 6)[:, :, :3]
+                        cmax = np.sqrt((cu * cu).sum(axis=2)).max(axis=1)
+                        bnd = umax + float(np.sum(np.abs(gam) * (np.array(hist_m) + cmax)))
+                        if bnd <= opt.step_limit:
+                            inc, accel, bound = dx - (dD + dF) @ gam, True, bnd
+            if not steady:
+                hist_f, hist_d, hist_m = [], [], []
+            hist_f.append(dx.copy())
+            hist_d.append(inc.copy())
+            hist_m.append(bound)
+            if len(hist_f) > opt.accel_depth:
+                hist_f.pop(0)
+                hist_d.pop(0)
+                hist_m.pop(0)
             du_prev = du.copy()
-            nrm2_prev = nrm2
-            alpha_prev = alpha
+            accel_prev = accel
+            n_active_prev = n_active
+            incr = inc.reshape(nf, 6)
             for j, i in enumerate(free):
-                x[i] = x[i] + alpha * du[j]
-                R[i] = expm(alpha * dth[j]) @ R[i]
+                x[i] = x[i] + incr[j, :3]
+                R[i] = expm(incr[j, 3:]) @ R[i]
             # Eq. 27 scales the multipliers of a limited step by alpha; the reported forces are the
             # multipliers of the last (converged, sub-tolerance) step, i.e. the equilibrium forces
             if self.trace is not None:

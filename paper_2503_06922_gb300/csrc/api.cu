@@ -336,7 +336,8 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
        dalloc(h, &d.Lm, (size_t)nfc * 36) && dalloc(h, &d.Rm, (size_t)nfc * 36) &&
        dalloc(h, &d.B, (size_t)nfc * 6 * p.nrhs_cap) && dalloc(h, &d.g, (size_t)nfc * 6) &&
        dalloc(h, &d.dx, (size_t)nfc * 6) && dalloc(h, &d.du_prev, (size_t)nfc * 3) &&
-       dalloc(h, &d.rev_part, (size_t)nfc / 32 + 2) && dalloc(h, &d.nrm_part, (size_t)nfc / 32 + 2) && dalloc(h, &d.W, (size_t)wc * wc) &&
+       dalloc(h, &d.rev_part, (size_t)nfc / 32 + 2) && dalloc(h, &d.aa_part, ((size_t)nfc / 32 + 2) * kAccelParts) &&
+       dalloc(h, &d.aa_f, (size_t)kAccelDepth * nfc * 6) && dalloc(h, &d.aa_d, (size_t)kAccelDepth * nfc * 6) && dalloc(h, &d.W, (size_t)wc * wc) &&
        dalloc(h, &d.y, mc) && dalloc(h, &d.gj, (size_t)wc * (wc + 2)) && dalloc(h, &d.plist, wc) &&
        dalloc(h, &d.ctl, 1);
   if (!ok) {

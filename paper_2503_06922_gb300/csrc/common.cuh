@@ -15,6 +15,11 @@ constexpr int kRhsSplit = 4;       // blocks per node that share the RHS columns
 constexpr int kBwdSplit = 8;       // back substitution: blocks per node (chunks of 16 columns, 96 threads)
 constexpr int kMaxWorking = 512;   // rows of the contact working set (RHS columns, LCP size)
 constexpr int kPrecisionFP64 = 0, kPrecisionMixed = 1;
+// Anderson acceleration of the Newton iteration: previous iterates used, and the largest
+// sum |gamma_j| of an accepted accelerated step (the same values are used by the CPU oracle).
+constexpr int kAccelDepth = 3;
+constexpr double kAccelGammaMax = 10.0;
+constexpr int kAccelParts = 9;     // per step block: G (6 upper entries) and b (3) of the least squares
 constexpr int kLcpActiveSet = 0, kLcpAdmm = 1;
 // A triangle whose plane projection of the node lies inside it enlarged by this barycentric margin
 // ("over the face") gives a constraint row; the same value is used by the CPU oracle.
@@ -78,8 +83,15 @@ struct Ctl {
   unsigned long long umax_bits, step_bits, res_bits;   // atomicMax on non-negative doubles
   double alpha;          // alpha of the last applied step
   double rho;            // step bound of the limiter (starts at beta0)
-  double nrm2_prev;      // sum of |du|^2 of the previous step
   int has_prev;          // a previous Newton step exists in this solve
+  int aa_n;              // previous iterates held for the acceleration (0..kAccelDepth)
+  int aa_prev;           // the last applied step was an accelerated one
+  int n_active_prev;     // active rows of the previous iteration
+  double aa_dmax[kAccelDepth];                  // bound on the largest nodal translation of each held increment
+  unsigned long long aa_cmax_bits[kAccelDepth]; // this iteration: largest nodal translation of f_{k-j+1} - f_{k-j}
+  // limiter decision of the current iteration, written by the first apply block for the control update
+  double lim_rho, lim_alpha, lim_bound;
+  int lim_accel, lim_steady;
   int live;              // batch: a solve of this instance is in flight
   int cap_code;          // CAP_* cause of an ST_CAPACITY status
   int mc;                // rows of the working set (RHS columns 1..mc)
@@ -146,7 +158,9 @@ struct Dev {
   double* dx;                                        // nf_cap * 6 : Newton step
   double* du_prev;                                   // nf_cap * 3 : previous Newton step (translations)
   double* rev_part;                                  // per step_kernel block: sum du . du_prev
-  double* nrm_part;                                  // per step_kernel block: sum |du|^2
+  double* aa_part;                                   // per step_kernel block: kAccelParts least-squares sums
+  double* aa_f;                                      // kAccelDepth * nf_cap * 6: unscaled steps of previous iterates
+  double* aa_d;                                      // kAccelDepth * nf_cap * 6: increments applied there
   // contact LCP
   double *W, *y, *gj;                                // ws_cap^2 (slots), m_cap (rows), ws_cap*(ws_cap+2)
   int *plist;                                        // ws_cap: active slots

@@ -40,6 +40,8 @@ __device__ __forceinline__ void element_body(const Params& p, const Dev& d, int 
   Ctl* ctl = d.ctl;
   if (bx == 0 && threadIdx.x == 0) {                 // reset the per-iteration reductions
     ctl->umax_bits = 0ull; ctl->step_bits = 0ull; ctl->res_bits = 0ull;
+#pragma unroll
+    for (int j = 0; j < kAccelDepth; ++j) ctl->aa_cmax_bits[j] = 0ull;
     ctl->incomplete = 0;
   }
   const int e = ctl->k + bx * kWarpsPerElemBlock + wib;

@@ -11,6 +11,8 @@ __device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx)
   __shared__ double s_r[32][6];
   __shared__ int s_j[kMaxWorking];            // active working-set slots and their multipliers
   __shared__ double s_y[kMaxWorking];
+  __shared__ double s_aac[kAccelDepth][32][3];  // translations of the step differences c_j
+  __shared__ double s_aap[6][kAccelParts];      // least-squares sums per component warp
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
   const int nf = ctl->nf;
@@ -41,6 +43,45 @@ __device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx)
   double rr_node = 0.0;
   if (act && c == 0)
     rr_node = fmax(fmax(fmax(s_r[fl][0], s_r[fl][1]), fmax(s_r[fl][2], s_r[fl][3])), fmax(s_r[fl][4], s_r[fl][5]));
+  // Anderson acceleration: differences c_j = f_{k-j+1} - f_{k-j} of this step and the held ones,
+  // least-squares sums (weight 1 on translations, r_o^2 on rotations) and their nodal translations
+  {
+    const int n_h = ctl->aa_n, k_it = ctl->iter;
+    double cj[kAccelDepth] = {0.0, 0.0, 0.0};
+    if (act) {
+      double prev = s_dx[fl][c];
+      for (int j = 1; j <= n_h; ++j) {
+        const double h = d.aa_f[((size_t)((k_it - j) % kAccelDepth) * p.M + f) * 6 + c];
+        cj[j - 1] = prev - h;
+        prev = h;
+      }
+      if (c < 3)
+        for (int j = 0; j < kAccelDepth; ++j) s_aac[j][fl][c] = cj[j];
+    }
+    const double wv = c < 3 ? 1.0 : p.r_o * p.r_o;
+    const double fk = act ? s_dx[fl][c] : 0.0;
+    double part[kAccelParts] = {wv * cj[0] * cj[0], wv * cj[0] * cj[1], wv * cj[0] * cj[2], wv * cj[1] * cj[1],
+                                wv * cj[1] * cj[2], wv * cj[2] * cj[2], wv * cj[0] * fk, wv * cj[1] * fk, wv * cj[2] * fk};
+#pragma unroll
+    for (int i = 0; i < kAccelParts; ++i) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part[i] += __shfl_xor_sync(0xffffffffu, part[i], o);
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int i = 0; i < kAccelParts; ++i) s_aap[c][i] = part[i];
+  }
+  __syncthreads();
+  if (threadIdx.y == 0 && threadIdx.x < kAccelParts) {
+    double v = 0.0;
+    for (int w = 0; w < 6; ++w) v += s_aap[w][threadIdx.x];
+    d.aa_part[(size_t)bx * kAccelParts + threadIdx.x] = v;
+  }
+  if (act && c == 0)
+    for (int j = 0; j < ctl->aa_n; ++j) {
+      const double n2 = fma(s_aac[j][fl][0], s_aac[j][fl][0], fma(s_aac[j][fl][1], s_aac[j][fl][1], s_aac[j][fl][2] * s_aac[j][fl][2]));
+      atomicMax(&ctl->aa_cmax_bits[j], dbits(sqrt(n2)));
+    }
   __syncthreads();
   if (act && c < 3) {
     // reversal test of the limiter: this step against the previous one (translations)
@@ -49,13 +90,9 @@ __device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx)
   }
   __syncthreads();
   if (threadIdx.x == 0 && threadIdx.y == 0) {
-    double rev = 0.0, nrm = 0.0;
-    for (int k = 0; k < 32 && bx * 32 + k < nf; ++k) {
-      rev += s_r[k][0] + s_r[k][1] + s_r[k][2];
-      nrm += fma(s_dx[k][0], s_dx[k][0], fma(s_dx[k][1], s_dx[k][1], s_dx[k][2] * s_dx[k][2]));
-    }
+    double rev = 0.0;
+    for (int k = 0; k < 32 && bx * 32 + k < nf; ++k) rev += s_r[k][0] + s_r[k][1] + s_r[k][2];
     d.rev_part[bx] = rev;
-    d.nrm_part[bx] = nrm;
   }
   if (act && c == 0) {
     double du = sqrt(s_dx[fl][0] * s_dx[fl][0] + s_dx[fl][1] * s_dx[fl][1] + s_dx[fl][2] * s_dx[fl][2]);
@@ -78,69 +115,171 @@ __global__ void __launch_bounds__(192) step_batch(const Inst* __restrict__ tab, 
 
 // Step limiter (Eq. 25-27 with an adaptive bound): alpha = min(1, rho / max |du|).  A step that
 // points against the previous one (sum_i du_i . du_i^prev < 0, summed over the step blocks in a
-// fixed order) is an overshoot: rho drops to half of min(rho, max |du|), so the step is at most
-// halved and a repeating cycle shrinks geometrically; otherwise rho grows by 1.5 back towards
-// beta0.  Over-relaxation of a slow monotone mode: after a full step, an unclipped step with the
-// same constraint rows, pointing the same way as the previous one (cosine >= 0.99) and shrinking
-// by lam = |du| / |du_prev| in [0.5, 0.98], is extended to the secant estimate of the limit,
-// alpha = min(1 / (1 - lam), 8, rho / max |du|).  Every reader evaluates this from the same inputs.
-__device__ __forceinline__ void limiter(const Params& p, const Dev& d, const Ctl* ctl, double* rho_new, double* alpha,
-                                        double* nrm2_out) {
+// fixed order) is an overshoot, unless the previous step was an accelerated one: rho drops to half of
+// min(rho, max |du|), so the step is at most halved and a repeating cycle shrinks geometrically;
+// otherwise rho grows by 1.5 back towards beta0.
+// Anderson acceleration (depth kAccelDepth) of the iteration x <- x (+) f(x), f the unscaled Newton
+// step: while the constraint rows and the number of active rows stay those of the previous iteration
+// and the step is not clipped ("steady"), gamma minimises |W (f_k - sum_j gamma_j c_j)| over the n held
+// differences c_j = f_{k-j+1} - f_{k-j} (W: weight r_o on rotations; a relative ridge 1e-10 max G_jj),
+// and the increment f_k - sum_j gamma_j (d_{k-j} + c_j), d_{k-j} the increment applied at iterate k-j,
+// is taken when sum |gamma_j| <= kAccelGammaMax and a bound on its largest nodal translation,
+// max|f_k| + sum_j |gamma_j| (max|d_{k-j}| + max|c_j|), stays within beta0 (the step limit that keeps
+// a node from crossing an undetected wall; the adaptive rho only damps overshoots, which the
+// extrapolation itself removes).  The block's threads reduce
+// the per-step-block partial sums; thread 0 evaluates the rule.
+struct LimOut {
+  double rho, alpha, bound, gamma[kAccelDepth];
+  int accel, steady;
+};
+
+__device__ void limiter_block(const Params& p, const Dev& d, const Ctl* ctl, LimOut* out) {
+  __shared__ double s_red[kAccelParts + 1][4];
   const int nb = (ctl->nf + 31) / 32;
-  double rev = 0.0, nrm2 = 0.0;
-  for (int b = 0; b < nb; ++b) {
-    rev += d.rev_part[b];
-    nrm2 += d.nrm_part[b];
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x, nthr = blockDim.x * blockDim.y;
+  const int lane = tid & 31, w = tid >> 5;
+  double acc[kAccelParts + 1];
+#pragma unroll
+  for (int i = 0; i <= kAccelParts; ++i) acc[i] = 0.0;
+  for (int b = tid; b < nb; b += nthr) {
+    acc[0] += d.rev_part[b];
+#pragma unroll
+    for (int i = 0; i < kAccelParts; ++i) acc[i + 1] += d.aa_part[(size_t)b * kAccelParts + i];
   }
-  double rho = ctl->rho;
-  const double umax = __longlong_as_double((long long)ctl->umax_bits);
-  const bool reverse = ctl->has_prev && rev < 0.0;
-  if (ctl->has_prev) {
-    if (reverse) rho = fmax(0.5 * fmin(rho, umax), p.beta0 * 9.094947017729282e-13);   // beta0 / 2^40
-    else rho = fmin(1.5 * rho, p.beta0);
+#pragma unroll
+  for (int i = 0; i <= kAccelParts; ++i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
   }
-  double a = umax <= rho ? 1.0 : rho / umax;
-  if (ctl->has_prev && !reverse && ctl->alpha == 1.0 && a == 1.0 && ctl->same_set && ctl->nrm2_prev > 0.0 && nrm2 > 0.0) {
-    const double lam = sqrt(nrm2 / ctl->nrm2_prev);
-    const double cosang = rev / sqrt(nrm2 * ctl->nrm2_prev);
-    if (cosang >= 0.99 && lam >= 0.5 && lam <= 0.98) a = fmin(fmin(1.0 / (1.0 - lam), 8.0), rho / umax);
+  if (lane == 0 && w < 4)
+#pragma unroll
+    for (int i = 0; i <= kAccelParts; ++i) s_red[i][w] = acc[i];
+  __syncthreads();
+  if (tid == 0) {
+    const int nw = min((nthr + 31) / 32, 4);
+    double S[kAccelParts + 1];
+    for (int i = 0; i <= kAccelParts; ++i) {
+      S[i] = 0.0;
+      for (int k = 0; k < nw; ++k) S[i] += s_red[i][k];
+    }
+    const double rev = S[0];
+    double rho = ctl->rho;
+    const double umax = __longlong_as_double((long long)ctl->umax_bits);
+    const bool reverse = ctl->has_prev && rev < 0.0 && !ctl->aa_prev;
+    if (ctl->has_prev) {
+      if (reverse) rho = fmax(0.5 * fmin(rho, umax), p.beta0 * 9.094947017729282e-13);   // beta0 / 2^40
+      else rho = fmin(1.5 * rho, p.beta0);
+    }
+    const double a = umax <= rho ? 1.0 : rho / umax;
+    const int n = ctl->aa_n;
+    out->steady = (ctl->has_prev && a == 1.0 && ctl->same_set && ctl->n_active == ctl->n_active_prev) ? 1 : 0;
+    out->accel = 0;
+    out->bound = 0.0;
+    for (int j = 0; j < kAccelDepth; ++j) out->gamma[j] = 0.0;
+    if (out->steady && n >= 1) {
+      // normal equations (G + ridge) gamma = b, n <= 3, by Gaussian elimination (G symmetric positive)
+      double G[3][3] = {{S[1], S[2], S[3]}, {S[2], S[4], S[5]}, {S[3], S[5], S[6]}};
+      double bv[3] = {S[7], S[8], S[9]};
+      double dmx = 0.0;
+      for (int j = 0; j < n; ++j) dmx = fmax(dmx, G[j][j]);
+      for (int j = 0; j < n; ++j) G[j][j] += 1e-10 * dmx;
+      bool ok = dmx > 0.0;
+      for (int c = 0; c < n && ok; ++c) {
+        if (!(G[c][c] > 0.0)) { ok = false; break; }
+        for (int r = c + 1; r < n; ++r) {
+          const double fct = G[r][c] / G[c][c];
+          for (int q = c; q < n; ++q) G[r][q] = fma(-fct, G[c][q], G[r][q]);
+          bv[r] = fma(-fct, bv[c], bv[r]);
+        }
+      }
+      double gam[3] = {0.0, 0.0, 0.0};
+      if (ok)
+        for (int c = n - 1; c >= 0; --c) {
+          double v = bv[c];
+          for (int q = c + 1; q < n; ++q) v = fma(-G[c][q], gam[q], v);
+          gam[c] = v / G[c][c];
+        }
+      double gsum = 0.0;
+      for (int j = 0; j < n; ++j) gsum += fabs(gam[j]);
+      if (ok && isfinite(gsum) && gsum <= kAccelGammaMax) {
+        double bound = umax;
+        for (int j = 1; j <= n; ++j)
+          bound = fma(fabs(gam[j - 1]),
+                      ctl->aa_dmax[(ctl->iter - j) % kAccelDepth] + __longlong_as_double((long long)ctl->aa_cmax_bits[j - 1]),
+                      bound);
+        if (bound <= p.beta0) {
+          out->accel = 1;
+          out->bound = bound;
+          for (int j = 0; j < n; ++j) out->gamma[j] = gam[j];
+        }
+      }
+    }
+    out->rho = rho;
+    out->alpha = a;
   }
-  *rho_new = rho;
-  *alpha = a;
-  *nrm2_out = nrm2;
+  __syncthreads();
 }
 
 // x <- x + alpha du, T <- exp([alpha dtheta]x) T.  Every row of the node outside the working set is
 // checked against the applied step: w = b - alpha n . du < -tol marks it violated (it joins the
 // working set in the next iteration, and this iteration cannot converge; at convergence alpha = 1).
 __device__ __forceinline__ void apply_body(const Params& p, const Dev& d, int bx) {
-  __shared__ double s_alpha;
+  __shared__ LimOut s_lim;
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
   const int nf = ctl->nf;
-  if (threadIdx.x == 0) {
-    double rho, nrm2;
-    limiter(p, d, ctl, &rho, &s_alpha, &nrm2);
+  limiter_block(p, d, ctl, &s_lim);
+  if (bx == 0 && threadIdx.x == 0) {             // the decision, for the control update
+    ctl->lim_rho = s_lim.rho;
+    ctl->lim_alpha = s_lim.alpha;
+    ctl->lim_bound = s_lim.bound;
+    ctl->lim_accel = s_lim.accel;
+    ctl->lim_steady = s_lim.steady;
   }
-  __syncthreads();
-  const double alpha = s_alpha;
+  const double alpha = s_lim.alpha;
+  const int accel = s_lim.accel;
   const int f = bx * 128 + threadIdx.x;
   if (f < nf) {
     const int node = ctl->k + 1 + f;
+    const int k_it = ctl->iter, n_h = ctl->aa_n;
     const double* dx = d.dx + (size_t)f * 6;
+    double inc[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) inc[c] = alpha * dx[c];
+    if (accel) {
+      // f_k - sum_j gamma_j (d_{k-j} + f_{k-j+1} - f_{k-j})
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        double v = dx[c], prev = dx[c];
+        for (int j = 1; j <= n_h; ++j) {
+          const size_t at = ((size_t)((k_it - j) % kAccelDepth) * p.M + f) * 6 + c;
+          const double h = d.aa_f[at];
+          v = fma(-s_lim.gamma[j - 1], d.aa_d[at] + (prev - h), v);
+          prev = h;
+        }
+        inc[c] = v;
+      }
+    }
+    // this iterate joins the held ones (its slot held the oldest, already read above)
+    const size_t at = ((size_t)(k_it % kAccelDepth) * p.M + f) * 6;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      d.aa_f[at + c] = dx[c];
+      d.aa_d[at + c] = inc[c];
+    }
     for (int row = d.c_first[f]; row < d.c_first[f + 1]; ++row) {
       if (d.rslot[row] >= 0) continue;
       const double* n = d.c_n + 3 * row;
-      const double w = d.c_gap[row] - alpha * fma(n[0], dx[0], fma(n[1], dx[1], n[2] * dx[2]));
+      const double w = d.c_gap[row] - fma(n[0], inc[0], fma(n[1], inc[1], n[2] * inc[2]));
       if (w < -p.tol) {
         d.p_flag[row] = RF_VIOLATED;
         ctl->incomplete = 1;
       }
     }
-    d.px[node] += alpha * dx[0];
-    d.py[node] += alpha * dx[1];
-    d.pz[node] += alpha * dx[2];
-    double th[3] = {alpha * dx[3], alpha * dx[4], alpha * dx[5]};
+    d.px[node] += inc[0];
+    d.py[node] += inc[1];
+    d.pz[node] += inc[2];
+    double th[3] = {inc[3], inc[4], inc[5]};
     double dq[4], q[4] = {d.qw[node], d.qx[node], d.qy[node], d.qz[node]}, r[4];
     quat_exp(th, dq);
     quat_mul(dq, q, r);
@@ -175,12 +314,15 @@ __device__ __forceinline__ void ctl_update(const Params& p, const Dev& d) {
     c->fp64_tangent = 1;
   }
   if (c->status == 0 && !c->converged) {
-    double rho, alpha, nrm2;
-    limiter(p, d, c, &rho, &alpha, &nrm2);
     const double step = __longlong_as_double((long long)c->step_bits);
-    c->rho = rho;
-    c->alpha = alpha;
-    c->nrm2_prev = nrm2;
+    const double umax = __longlong_as_double((long long)c->umax_bits);
+    c->rho = c->lim_rho;
+    c->alpha = c->lim_alpha;
+    // the held iterates: this one joins them while the iteration is steady, else it alone remains
+    c->aa_dmax[c->iter % kAccelDepth] = c->lim_accel ? c->lim_bound : c->lim_alpha * umax;
+    c->aa_n = c->lim_steady ? min(c->aa_n + 1, kAccelDepth) : 1;
+    c->aa_prev = c->lim_accel;
+    c->n_active_prev = c->n_active;
     c->has_prev = 1;
     c->iter += 1;
     if (step <= p.tol && c->same_set && !c->incomplete) c->converged = 1;
