@@ -369,7 +369,10 @@ PHASE_BYTES = {"element": 800.0, "assemble": 1344.0}
 # DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum) of the committed
 # kernels on the same batch, first Newton iteration of all 256 members (profiles/batch256_phase_dram.md);
 # None where no capture of the current kernel exists.
-PHASE_DRAM_BYTES = {"element": None, "collide": None, "assemble": None}
+PHASE_DRAM_BYTES = {"element": 7.9e6 + 9.0e6, "collide": 165.1e6 + 4.2e6, "assemble": 172.7e6 + 699.0e6}
+# DRAM traffic per launch of the factor group on the final state of the sweep, cold cache (ncu,
+# profiles/factor_group_sweep600_M300_dram.md; assemble_rhs + 9 level + 9 back-substitution launches).
+FACTOR_DRAM_BYTES = 7.378e6
 
 
 def _batch_phase_rooflines(af, b, hs, ws, seed=6):
@@ -1029,7 +1032,9 @@ def ours(args, rank, world, local_rank):
                                        "bcr_level x levels, bcr_bwd x levels; nf=%d nodes, %d RHS columns)"
                                        % (nf_last, 1 + mc_last),
                              "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s FP64",
-                             "frac": achieved / peak, "traffic": None, "launch_us": fa_us,
+                             "frac": achieved / peak, "traffic": FACTOR_DRAM_BYTES, "launch_us": fa_us,
+                             "traffic_note": "ncu dram bytes per group launch at cold cache (the timed loop keeps "
+                                             "the 11 MB working set in L2)",
                              "flops_per_launch": fa_flops, "executed_flops_per_launch": fa_exec,
                              "flops_rule": "560 flop per free node (6x6-block Cholesky) + 230 flop per node per RHS "
                                            "column (forward + backward solve); the reduction executes %.2fx that"

@@ -7,10 +7,13 @@ lumen seed 1, tension seed 2, insertion 10 -> 600 mm) and stores, for every solv
 poses, the status, the Newton iterations, the number of constraint rows and the seconds it took on
 the machine that wrote it.  Nothing in it comes from the CUDA path.
 
-    python -m oracle.record_sweep [--out PATH] [--resume]
+    python -m oracle.record_sweep [--out PATH] [--resume] [--recount [--procs P]]
 
 It takes hours on one core (the oracle tests every node against every triangle); --resume continues
-a partial record.
+a partial record.  --recount re-runs every solve of a complete record with the oracle as it stands,
+each from the recorded state of the solve before it, in P worker processes, and replaces the
+recorded status, Newton iterations, rows and seconds (the converged states do not depend on the
+iteration's path, so the recorded states stay).
 """
 import argparse
 import os
@@ -26,12 +29,48 @@ if ROOT not in sys.path:
 DEFAULT_OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "records", "catmull_rom_600mm_M300_sweep.npz")
 
 
+def _recount_one(args):
+    """Solve s of the sweep with the oracle as it stands, from the recorded state after solve s - 1."""
+    path, s = args
+    os.environ["OMP_NUM_THREADS"] = "1"
+    import workloads as wl
+    from oracle import solver
+    rec = np.load(path)
+    w = wl.catmull_rom_workload(lumen_seed=1, tension_seed=2, n_steps=60)
+    m = solver.Model(w.robot, w.lumen)
+    if s > 0:
+        m.state = (rec["pos"][s - 1].copy(), rec["rot"][s - 1].copy(), float(w.insertions[s - 1]))
+    t0 = time.perf_counter()
+    r = m.solve(w.tensions[s], w.insertions[s])
+    return s, r.status, r.newton_iters, len(r.contacts), time.perf_counter() - t0
+
+
+def recount(path, procs):
+    import multiprocessing as mp
+    rec = dict(np.load(path))
+    S = len(rec["insertions"])
+    if not np.all(rec["status"] >= 0):
+        raise SystemExit("the record is not complete")
+    ctx = mp.get_context("spawn")
+    order = list(range(S - 1, -1, -1))            # the long solves first
+    with ctx.Pool(procs) as pool:
+        for s, st, it, rows, sec in pool.imap_unordered(_recount_one, [(path, s) for s in order]):
+            rec["status"][s], rec["newton_iters"][s], rec["rows"][s], rec["seconds"][s] = st, it, rows, sec
+            print("recount solve %d status %d newton %d rows %d %.1f s" % (s, st, it, rows, sec), flush=True)
+    np.savez_compressed(path, **rec)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=DEFAULT_OUT)
     ap.add_argument("--resume", action="store_true")
+    ap.add_argument("--recount", action="store_true")
+    ap.add_argument("--procs", type=int, default=max(1, (os.cpu_count() or 2) - 1))
     args = ap.parse_args(argv)
     os.environ.setdefault("OMP_NUM_THREADS", "1")
+    if args.recount:
+        recount(args.out, args.procs)
+        return 0
     import workloads as wl
     from oracle import solver
     w = wl.catmull_rom_workload(lumen_seed=1, tension_seed=2, n_steps=60)

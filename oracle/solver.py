@@ -22,8 +22,9 @@ One call of ``Model.solve`` is one quasi-static step at a given cable tension an
     otherwise rho grows by 1.5 back towards beta0.  (A fixed beta0 lets a node on a faceted wall
     overshoot the crease between two facets forever, and the material tangent overshoots the
     twist of a long bent span by ~2x.)  The material tangent also converges only linearly (a slow
-    bending or twist mode of a long compressed span shrinks by ~0.3-0.9 per iteration), so while
-    the contact rows and the number of active rows stay the same and the step is not clipped, the
+    bending or twist mode of a long compressed span shrinks by ~0.3-0.96 per iteration), so in the
+    first ACCEL_ITERS iterations of a solve, while the active contact rows stay the same and the
+    step is not clipped, the
     iteration x <- x (+) dx(x) is accelerated by Anderson's method of depth ACCEL_DEPTH (Walker & Ni
     2011, "Anderson acceleration for fixed-point iterations"): with f_j the unscaled step of
     iterate j and d_j the increment applied there, gamma minimises |W (f_k - sum_j gamma_j
@@ -31,7 +32,10 @@ One call of ``Model.solve`` is one quasi-static step at a given cable tension an
     f_k - sum_j gamma_j (d_{k-j-1} + f_{k-j} - f_{k-j-1}); it is taken only when its largest nodal
     translation, bounded by max|f_k| + sum_j |gamma_j| (max|d_{k-j}| + max|f_{k-j+1} - f_{k-j}|), stays
     within beta0 and sum |gamma_j| <= ACCEL_GAMMA_MAX; a reversal right after an accelerated
-    step does not shrink rho (extrapolation overshoots by design).
+    step does not shrink rho (extrapolation overshoots by design).  Later iterations (a solve that
+    has not converged by then) use the 1-D secant over-relaxation instead: after a full step, an
+    unclipped step with the same contact rows, pointing the same way (cosine >= 0.99) and shrinking
+    by lam in [0.5, 0.98], is extended to alpha = min(1 / (1 - lam), 8, rho / max|du|).
   * convergence: unscaled step max_i max(|du_i|, r_o |dtheta_i|) <= tol and the same contact
     set as the previous iteration.
   * warm start (follow the path): with a resident state at insertion delta_old, material
@@ -50,6 +54,7 @@ from .rotation import expm, logm, to_quat
 CONTACT_COMPLIANCE = 1e-12
 ACCEL_DEPTH = 3            # Anderson acceleration: previous iterates used
 ACCEL_GAMMA_MAX = 10.0     # largest sum |gamma_j| of an accepted accelerated step
+ACCEL_ITERS = 100          # iterations of a solve that may take accelerated steps (then the secant rule)
 
 OK, E_INVALID_ARG, E_NOMEM, E_CUDA, E_NOT_CONVERGED, E_CONTACT_CAPACITY, E_NOT_SPD, E_TIMEOUT, E_PENETRATION = range(9)
 
@@ -222,7 +227,9 @@ class Model:
         hist_f, hist_d, hist_m = [], [], []   # previous iterates: unscaled steps, applied increments and
                                               # a bound on each increment's largest nodal translation
         accel_prev = False
-        n_active_prev = -1
+        act_key_prev = None
+        nrm2_prev = 0.0
+        alpha_prev = 0.0
         status = E_NOT_CONVERGED
         base_reaction = np.zeros(6)
         if nf == 0:
@@ -317,7 +324,7 @@ class Model:
             umax = float(np.sqrt((du * du).sum(axis=1)).max())
             step = float(max(umax, r_o * np.sqrt((dth * dth).sum(axis=1)).max()))
             key = tuple((rec["node"] if "node" in rec else -1 - rec["elem"], rec["tri"]) for rec in contacts)
-            n_active = int(np.sum(y > 0.0)) if m else 0
+            act_key = tuple(key[i] for i in range(m) if y[i] > 0.0) if m else ()
             dot = float(np.sum(du * du_prev)) if du_prev is not None else 0.0
             # a step against the previous one is an overshoot, unless the previous one was extrapolated
             reverse = du_prev is not None and dot < 0.0 and not accel_prev
@@ -328,11 +335,21 @@ class Model:
                     rho = min(1.5 * rho, opt.step_limit)
             alpha = 1.0 if umax <= rho else rho / umax
             inc = alpha * dx
-            # Anderson acceleration while the rows, the number of active rows and the full step persist
-            steady = du_prev is not None and alpha == 1.0 and key == prev_key and n_active == n_active_prev
+            # Anderson acceleration while the active rows and the full step persist
+            anderson = opt.accel_depth > 0 and it <= ACCEL_ITERS
+            steady = anderson and du_prev is not None and alpha == 1.0 and act_key == act_key_prev
+            # after that (or without acceleration) the secant over-relaxation of a slow monotone mode
+            nrm2 = float(np.sum(du * du))
+            if (not anderson and du_prev is not None and not reverse and alpha_prev == 1.0 and alpha == 1.0
+                    and key == prev_key and nrm2_prev > 0.0 and nrm2 > 0.0):
+                lam = math.sqrt(nrm2 / nrm2_prev)
+                cosang = dot / math.sqrt(nrm2 * nrm2_prev)
+                if cosang >= 0.99 and 0.5 <= lam <= 0.98:
+                    alpha = min(1.0 / (1.0 - lam), 8.0, rho / umax)
+                    inc = alpha * dx
             accel = False
             bound = alpha * umax
-            if steady and opt.accel_depth > 0 and hist_f:
+            if steady and hist_f:
                 wgt = np.tile(np.array([1.0, 1.0, 1.0, r_o, r_o, r_o]), nf)
                 F = np.array(hist_f + [dx])
                 dF = np.diff(F, axis=0).T                      # columns f_{i+1} - f_i, oldest first
@@ -360,7 +377,9 @@ class Model:
                 hist_m.pop(0)
             du_prev = du.copy()
             accel_prev = accel
-            n_active_prev = n_active
+            act_key_prev = act_key
+            nrm2_prev = nrm2
+            alpha_prev = alpha
             incr = inc.reshape(nf, 6)
             for j, i in enumerate(free):
                 x[i] = x[i] + incr[j, :3]

@@ -19,7 +19,10 @@ constexpr int kPrecisionFP64 = 0, kPrecisionMixed = 1;
 // sum |gamma_j| of an accepted accelerated step (the same values are used by the CPU oracle).
 constexpr int kAccelDepth = 3;
 constexpr double kAccelGammaMax = 10.0;
-constexpr int kAccelParts = 9;     // per step block: G (6 upper entries) and b (3) of the least squares
+constexpr int kAccelParts = 10;    // per step block: G (6 upper entries) and b (3) of the least squares, sum |du|^2
+// Iterations of a solve that may take Anderson steps; later ones (and the FP32 tangent's) fall back to
+// the 1-D secant over-relaxation of a slow monotone mode.
+constexpr int kAccelIters = 100;
 constexpr int kLcpActiveSet = 0, kLcpAdmm = 1;
 // A triangle whose plane projection of the node lies inside it enlarged by this barycentric margin
 // ("over the face") gives a constraint row; the same value is used by the CPU oracle.
@@ -87,10 +90,12 @@ struct Ctl {
   int aa_n;              // previous iterates held for the acceleration (0..kAccelDepth)
   int aa_prev;           // the last applied step was an accelerated one
   int n_active_prev;     // active rows of the previous iteration
+  int same_active;       // the active rows are those of the previous iteration (by node and triangle)
+  double nrm2_prev;      // sum of |du|^2 of the previous step (secant over-relaxation)
   double aa_dmax[kAccelDepth];                  // bound on the largest nodal translation of each held increment
   unsigned long long aa_cmax_bits[kAccelDepth]; // this iteration: largest nodal translation of f_{k-j+1} - f_{k-j}
   // limiter decision of the current iteration, written by the first apply block for the control update
-  double lim_rho, lim_alpha, lim_bound;
+  double lim_rho, lim_alpha, lim_bound, lim_nrm2;
   int lim_accel, lim_steady;
   int live;              // batch: a solve of this instance is in flight
   int cap_code;          // CAP_* cause of an ST_CAPACITY status

@@ -295,7 +295,10 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
   for (int r = tid; r < ctl->m; r += nt)
     if (d.rslot[r] < 0) d.y[r] = 0.0;
   if (m == 0) {
-    if (tid == 0) ctl->n_active = 0;
+    if (tid == 0) {
+      ctl->n_active = 0;
+      ctl->same_active = ctl->n_active_prev == 0 ? 1 : 0;
+    }
     return;
   }
   if (m > kLcpSmemRows) {
@@ -404,10 +407,16 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
     }
   }
   __syncthreads();
-  // ---- results: multipliers (by row), active flags for the next iteration, active slots
+  // ---- results: multipliers (by row), active flags for the next iteration, active slots; and how
+  // many rows active now were active in the previous iteration (same active set: all of them)
+  __shared__ int s_kept;
+  if (tid == 0) s_kept = 0;
+  __syncthreads();
   for (int i = tid; i < m; i += nt) {
     const bool a = S.inP[i] && S.y[i] > 0.0;
     const int row = d.wrow[i];
+    const int fl = d.init_flag[row];
+    if (a && fl >= 0 && (fl & RF_ACTIVE)) atomicAdd(&s_kept, 1);
     d.y[row] = a ? S.y[i] : 0.0;
     d.p_flag[row] = (d.p_flag[row] & RF_STICKY) | RF_WORKING | (a ? RF_ACTIVE : 0);
   }
@@ -427,6 +436,7 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
       if (fail) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
       else if (!done) atomicCAS(&ctl->status, 0, ST_TIMEOUT);
       ctl->n_active = na;
+      ctl->same_active = (s_kept == na && na == ctl->n_active_prev) ? 1 : 0;
     }
   }
 }

@@ -61,7 +61,8 @@ __device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx)
     const double wv = c < 3 ? 1.0 : p.r_o * p.r_o;
     const double fk = act ? s_dx[fl][c] : 0.0;
     double part[kAccelParts] = {wv * cj[0] * cj[0], wv * cj[0] * cj[1], wv * cj[0] * cj[2], wv * cj[1] * cj[1],
-                                wv * cj[1] * cj[2], wv * cj[2] * cj[2], wv * cj[0] * fk, wv * cj[1] * fk, wv * cj[2] * fk};
+                                wv * cj[1] * cj[2], wv * cj[2] * cj[2], wv * cj[0] * fk, wv * cj[1] * fk, wv * cj[2] * fk,
+                                c < 3 ? fk * fk : 0.0};
 #pragma unroll
     for (int i = 0; i < kAccelParts; ++i) {
 #pragma unroll
@@ -119,8 +120,9 @@ __global__ void __launch_bounds__(192) step_batch(const Inst* __restrict__ tab, 
 // min(rho, max |du|), so the step is at most halved and a repeating cycle shrinks geometrically;
 // otherwise rho grows by 1.5 back towards beta0.
 // Anderson acceleration (depth kAccelDepth) of the iteration x <- x (+) f(x), f the unscaled Newton
-// step: while the constraint rows and the number of active rows stay those of the previous iteration
-// and the step is not clipped ("steady"), gamma minimises |W (f_k - sum_j gamma_j c_j)| over the n held
+// step, in the first kAccelIters iterations of a solve with the FP64 tangent: while the active rows (by
+// node and triangle) stay those of the previous iteration and the step is not clipped ("steady"; rows
+// that enter or leave the detection without becoming active do not change the step), gamma minimises |W (f_k - sum_j gamma_j c_j)| over the n held
 // differences c_j = f_{k-j+1} - f_{k-j} (W: weight r_o on rotations; a relative ridge 1e-10 max G_jj),
 // and the increment f_k - sum_j gamma_j (d_{k-j} + c_j), d_{k-j} the increment applied at iterate k-j,
 // is taken when sum |gamma_j| <= kAccelGammaMax and a bound on its largest nodal translation,
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(192) step_batch(const Inst* __restrict__ tab, 
 // extrapolation itself removes).  The block's threads reduce
 // the per-step-block partial sums; thread 0 evaluates the rule.
 struct LimOut {
-  double rho, alpha, bound, gamma[kAccelDepth];
+  double rho, alpha, bound, nrm2, gamma[kAccelDepth];
   int accel, steady;
 };
 
@@ -170,11 +172,26 @@ __device__ void limiter_block(const Params& p, const Dev& d, const Ctl* ctl, Lim
       if (reverse) rho = fmax(0.5 * fmin(rho, umax), p.beta0 * 9.094947017729282e-13);   // beta0 / 2^40
       else rho = fmin(1.5 * rho, p.beta0);
     }
-    const double a = umax <= rho ? 1.0 : rho / umax;
+    double a = umax <= rho ? 1.0 : rho / umax;
     const int n = ctl->aa_n;
-    out->steady = (ctl->has_prev && a == 1.0 && ctl->same_set && ctl->n_active == ctl->n_active_prev) ? 1 : 0;
+    // Anderson steps only in the first kAccelIters iterations and with the FP64 tangent (the FP32
+    // tangent's error in the soft modes is of order one, so its successive steps are not samples of
+    // one smooth map)
+    const bool anderson = ctl->iter < kAccelIters && !(p.precision == kPrecisionMixed && !ctl->fp64_tangent);
+    out->steady = (ctl->has_prev && a == 1.0 && ctl->same_active && anderson) ? 1 : 0;
     out->accel = 0;
     out->bound = 0.0;
+    // otherwise the secant over-relaxation of a slow monotone mode: after a full step, an unclipped step
+    // with the same constraint rows, pointing the same way as the previous one (cosine >= 0.99) and
+    // shrinking by lam = |du| / |du_prev| in [0.5, 0.98], is extended to alpha = min(1 / (1 - lam), 8, rho / max|du|)
+    const double nrm2 = S[10];
+    if (!anderson && ctl->has_prev && !reverse && ctl->alpha == 1.0 && a == 1.0 && ctl->same_set &&
+        ctl->nrm2_prev > 0.0 && nrm2 > 0.0) {
+      const double lam = sqrt(nrm2 / ctl->nrm2_prev);
+      const double cosang = rev / sqrt(nrm2 * ctl->nrm2_prev);
+      if (cosang >= 0.99 && lam >= 0.5 && lam <= 0.98) a = fmin(fmin(1.0 / (1.0 - lam), 8.0), rho / umax);
+    }
+    out->nrm2 = nrm2;
     for (int j = 0; j < kAccelDepth; ++j) out->gamma[j] = 0.0;
     if (out->steady && n >= 1) {
       // normal equations (G + ridge) gamma = b, n <= 3, by Gaussian elimination (G symmetric positive)
@@ -235,6 +252,7 @@ __device__ __forceinline__ void apply_body(const Params& p, const Dev& d, int bx
     ctl->lim_bound = s_lim.bound;
     ctl->lim_accel = s_lim.accel;
     ctl->lim_steady = s_lim.steady;
+    ctl->lim_nrm2 = s_lim.nrm2;
   }
   const double alpha = s_lim.alpha;
   const int accel = s_lim.accel;
@@ -310,10 +328,13 @@ __device__ __forceinline__ void ctl_update(const Params& p, const Dev& d) {
   // cube of the element count) switches this solve to the FP64 tangent; the failed iteration
   // applied no step and is repeated
   if (c->status == ST_NOT_SPD && p.precision == kPrecisionMixed && !c->fp64_tangent) {
+    // the failed iteration ran no step or apply kernel: it counts, and the held iterates restart
     c->status = 0;
     c->fp64_tangent = 1;
-  }
-  if (c->status == 0 && !c->converged) {
+    c->aa_n = 0;
+    c->aa_prev = 0;
+    c->iter += 1;
+  } else if (c->status == 0 && !c->converged) {
     const double step = __longlong_as_double((long long)c->step_bits);
     const double umax = __longlong_as_double((long long)c->umax_bits);
     c->rho = c->lim_rho;
@@ -323,6 +344,7 @@ __device__ __forceinline__ void ctl_update(const Params& p, const Dev& d) {
     c->aa_n = c->lim_steady ? min(c->aa_n + 1, kAccelDepth) : 1;
     c->aa_prev = c->lim_accel;
     c->n_active_prev = c->n_active;
+    c->nrm2_prev = c->lim_nrm2;
     c->has_prev = 1;
     c->iter += 1;
     if (step <= p.tol && c->same_set && !c->incomplete) c->converged = 1;
