@@ -336,14 +336,16 @@ accfem_status accfem_batch_serve(accfem_batch* b, const accfem_request* requests
                                  int32_t chunk_iters, int64_t hbm_cap_bytes, accfem_response* responses,
                                  accfem_result* results);
 
-/* Autotuning of the work packing.  The batch's phase kernels are persistent; they can run on
- * their full resident grid or on 1/2, 1/4 or 1/8 of it (more units per block, fewer idle blocks).
- * After this call the next 4 x trials advances take the four variants in turn, each timed on the
- * device per Newton iteration, and the fastest is kept; results do not depend on the variant. */
+/* Autotuning of the work packing and the element mapping.  The batch's phase kernels are persistent;
+ * they can run on their full resident grid or on 1/2, 1/4 or 1/8 of it (more units per block, fewer
+ * idle blocks), and the element phase maps one warp to an element in blocks of 2, 4 or 8 warps: 12
+ * variants, variant v dividing the grids by 2^(v % 4) with element blocks of 2 << (v / 4) warps.  After
+ * this call the next 12 x trials advances take the variants in turn, each timed on the device per
+ * Newton iteration, and the fastest is kept; results do not depend on the variant. */
 accfem_status accfem_batch_autotune(accfem_batch* b, int32_t trials);
 
-/* Variant in use (0..3: grids divided by 2^variant; -1 while tuning) and, if ms_per_pass is not NULL,
- * the measured milliseconds per Newton iteration of each variant (4 values, -1 if not measured). */
+/* Variant in use (0..11 as above; -1 while tuning) and, if ms_per_pass is not NULL, the measured
+ * milliseconds per Newton iteration of each variant (12 values, -1 if not measured). */
 accfem_status accfem_batch_tuning(const accfem_batch* b, int32_t* variant, double* ms_per_pass);
 
 /* Times one phase kernel of the batch (ACCFEM_KERNEL_ELEMENT, _COLLIDE or _ASSEMBLE) on the work plan of

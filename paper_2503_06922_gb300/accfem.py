@@ -488,9 +488,10 @@ class AccFemBatch:
         return int(self._lib.accfem_batch_autotune(self.b, int(trials)))
 
     def accfem_batch_tuning(self):
-        """(variant in use or -1 while tuning, ms per Newton iteration of each of the 4 variants)."""
+        """(variant in use or -1 while tuning, ms per Newton iteration of each of the 12 variants: grid
+        divisor 2^(v % 4), element blocks of 2 << (v / 4) warps)."""
         v = ctypes.c_int32(0)
-        ms = np.zeros(4)
+        ms = np.zeros(12)
         self._lib.accfem_batch_tuning(self.b, ctypes.byref(v), _ptr(ms))
         return int(v.value), ms
 

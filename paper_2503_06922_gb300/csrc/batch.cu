@@ -17,7 +17,9 @@
 #include "batch_host.h"
 
 namespace accfem {
-__global__ void element_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
+__global__ void element_batch_w2(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
+__global__ void element_batch_w4(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
+__global__ void element_batch_w8(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
 __global__ void collide_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
 __global__ void compact_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
 __global__ void assemble_rhs_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
@@ -80,6 +82,17 @@ int persistent_grid(K kernel, int threads, long long max_units) {
   return (int)g;
 }
 
+// Element mapping of variant v: blocks of 2, 4 or 8 warps (one warp per element).
+inline int variant_elem_w(int v) { return 2 << (v / 4); }
+inline int variant_grid_shift(int v) { return v % 4; }
+
+// The batched element phase with w warps per block.
+void launch_element_batch(int w, bool pdl, dim3 grid, cudaStream_t st, const Inst* tab, const Plan* plan) {
+  if (w == 8) launch_k(pdl, element_batch_w8, grid, dim3(256), st, tab, plan);
+  else if (w == 4) launch_k(pdl, element_batch_w4, grid, dim3(128), st, tab, plan);
+  else launch_k(pdl, element_batch_w2, grid, dim3(64), st, tab, plan);
+}
+
 // Enqueues one Newton iteration of every instance in flight on st (the body of the batch graph);
 // returns the number of kernels.
 int enqueue_batch_iteration(accfem_batch* b, cudaStream_t st, cudaGraphConditionalHandle cond, int set_cond) {
@@ -91,7 +104,7 @@ int enqueue_batch_iteration(accfem_batch* b, cudaStream_t st, cudaGraphCondition
   cudaEventRecord(b->fork, st);
   cudaStreamWaitEvent(b->side, b->fork, 0);
   const bool pdl = b->pdl;
-  launch_k(pdl, element_batch, dim3(g[PH_ELEM]), dim3(32 * kWarpsPerElemBlock), b->side, tab, plan); ++n;
+  launch_element_batch(b->elem_w, pdl, dim3(g[PH_ELEM]), b->side, tab, plan); ++n;
   cudaEventRecord(b->join, b->side);
   launch_k(pdl, collide_batch, dim3(g[PH_COLL]), dim3(128), st, tab, plan); ++n;
   launch_k(pdl, compact_batch, dim3(g[PH_COMPACT]), dim3(1024), st, tab, plan); ++n;
@@ -108,12 +121,15 @@ int enqueue_batch_iteration(accfem_batch* b, cudaStream_t st, cudaGraphCondition
 
 // Persistent grids of the phase kernels at the full resident size (units: the largest number of
 // units the members can produce).
-void full_grids(accfem_batch* b, int* grid) {
+void full_grids(accfem_batch* b, int elem_w, int* grid) {
   long long units[kPhases] = {};
   for (accfem_handle* h : b->members)
     for (int ph = 0; ph < kPhases; ++ph) units[ph] += (long long)phase_gx(ph, h->p.M) * phase_gy(ph);
   for (int ph = 0; ph < kPhases; ++ph) grid[ph] = 1;
-  grid[PH_ELEM] = persistent_grid(element_batch, 32 * kWarpsPerElemBlock, units[PH_ELEM]);
+  const long long eu = (units[PH_ELEM] * kWarpsPerElemBlock + elem_w - 1) / elem_w;   // blocks of elem_w warps
+  grid[PH_ELEM] = elem_w == 8 ? persistent_grid(element_batch_w8, 256, eu)
+                : elem_w == 4 ? persistent_grid(element_batch_w4, 128, eu)
+                              : persistent_grid(element_batch_w2, 64, eu);
   grid[PH_COLL] = persistent_grid(collide_batch, 128, units[PH_COLL]);
   grid[PH_COMPACT] = persistent_grid(compact_batch, 1024, units[PH_COMPACT]);
   grid[PH_ASM] = persistent_grid(assemble_rhs_batch, 192, units[PH_ASM]);
@@ -126,13 +142,15 @@ void full_grids(accfem_batch* b, int* grid) {
   }
 }
 
-// Graph of variant v: every persistent grid divided by 2^v (at least one block).
+// Graph of variant v: every persistent grid divided by 2^(v % 4) (at least one block), element blocks
+// of 2 << (v / 4) warps.
 bool build_graph(accfem_batch* b, int v) {
   accfem_batch::Variant& g = b->variants[v];
   if (g.exec) return true;
   int full[kPhases];
-  full_grids(b, full);
-  for (int ph = 0; ph < kPhases; ++ph) b->grid[ph] = std::max(1, full[ph] >> v);
+  b->elem_w = variant_elem_w(v);
+  full_grids(b, b->elem_w, full);
+  for (int ph = 0; ph < kPhases; ++ph) b->grid[ph] = std::max(1, full[ph] >> variant_grid_shift(v));
   cudaGraphConditionalHandle cond;
   cudaGraphNodeParams cp = {};
   cudaGraphNode_t node;
@@ -351,6 +369,7 @@ accfem_status accfem_batch_advance(accfem_batch* b, int32_t max_iters, int32_t* 
       if (!build_graph(b, v)) return ACCFEM_E_CUDA;
     }
     for (int ph = 0; ph < kPhases; ++ph) b->grid[ph] = b->variants[v].grid[ph];
+    b->elem_w = variant_elem_w(v);
     if (b->stream_mode) {
       // host-driven passes (kernels visible to profilers): stop when nothing iterates
       for (int pass = 0; pass < max_iters; ++pass) {
@@ -568,7 +587,7 @@ accfem_status accfem_batch_time_phase(accfem_batch* b, accfem_kernel kernel, int
     cudaEventRecord(e0, st);
     switch (kernel) {
       case ACCFEM_KERNEL_ELEMENT:
-        element_batch<<<g[PH_ELEM], 32 * kWarpsPerElemBlock, 0, st>>>(b->d_tab, b->d_plan); break;
+        launch_element_batch(variant_elem_w(b->variant), false, dim3(g[PH_ELEM]), st, b->d_tab, b->d_plan); break;
       case ACCFEM_KERNEL_COLLIDE: collide_batch<<<g[PH_COLL], 128, 0, st>>>(b->d_tab, b->d_plan); break;
       default: assemble_rhs_batch<<<g[PH_ASM], dim3(32, 6), 0, st>>>(b->d_tab, b->d_plan); break;
     }

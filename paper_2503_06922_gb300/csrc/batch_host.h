@@ -36,8 +36,10 @@ struct accfem_batch {
   int n_begin = 0;
   std::vector<int> state;           // 0 idle, 1 staged, 2 in flight
   std::vector<int> solved;          // member finished at least one solve in this batch
-  // graph variants: persistent grids at 1, 1/2, 1/4, 1/8 of the resident size (built on first use)
-  static constexpr int kVariants = 4;
+  // graph variants (built on first use): v % 4 divides the persistent grids by 1, 2, 4 or 8; v / 4
+  // picks the element mapping, blocks of 2, 4 or 8 warps with one warp per element
+  static constexpr int kVariants = 12;
+  int elem_w = 2;                   // warps per element block of the variant being captured or run
   struct Variant {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;

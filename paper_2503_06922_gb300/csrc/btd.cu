@@ -56,7 +56,8 @@ __device__ __forceinline__ int block_excl_scan_1024(int v, int* s_warp, int* tot
 // the contact solve, copy to "previous".  Working set: rows active in the previous iteration, rows
 // violated by an applied step in this solve (they stay), and rows whose gap is at most ws_gap (all
 // rows in frame mode, where every iteration is a reported state and solves the QP of Eq. 23 whole);
-// slots follow the row order.
+// when that exceeds the working-set cap, the near rows with the smallest gaps up to the cap; slots
+// follow the row order.
 __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   __shared__ int s_warp[32];
   __shared__ int s_same;
@@ -122,7 +123,7 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   const int keep_mask = RF_ACTIVE | RF_VIOLATED | RF_STICKY;
   // no applied step of this iteration moves a node farther than the limiter's bound, at most
   // min(1.5 rho, beta0): rows with a larger gap cannot be violated by it
-  const double ws_gap = fmin(p.ws_gap, fmin(1.5 * ctl->rho, p.beta0));
+  double ws_gap = fmin(p.ws_gap, fmin(1.5 * ctl->rho, p.beta0));
   int nw = 0;
   for (int r = r0; r < r1; ++r) {
     const int fl = d.init_flag[r];
@@ -130,6 +131,40 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   }
   int mc = 0;
   int slot = block_excl_scan_1024(nw, s_warp, &mc);
+  if (mc > p.ws_cap && !p.ws_all) {
+    // more near rows than the cap: keep the active and violated rows and, of the near rows, those with
+    // the smallest gaps (the threshold bisected down until the count fits); rows left out are still
+    // checked against the applied step and join when violated
+    int mand = 0, cnt = 0;
+    for (int r = r0; r < r1; ++r) {
+      const int fl = d.init_flag[r];
+      mand += (fl > 0 && (fl & keep_mask)) ? 1 : 0;
+    }
+    block_excl_scan_1024(mand, s_warp, &cnt);
+    if (cnt > p.ws_cap) {
+      if (tid == 0) flag_capacity(ctl, CAP_WORKING);
+      return;
+    }
+    double lo = -1.0, hi = ws_gap;          // count(lo) <= cap < count(hi)
+    for (int it = 0; it < 48; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      int k = 0;
+      for (int r = r0; r < r1; ++r) {
+        const int fl = d.init_flag[r];
+        k += ((fl > 0 && (fl & keep_mask)) || d.c_gap[r] <= mid) ? 1 : 0;
+      }
+      int tot = 0;
+      block_excl_scan_1024(k, s_warp, &tot);
+      if (tot <= p.ws_cap) lo = mid; else hi = mid;
+    }
+    ws_gap = lo;
+    nw = 0;
+    for (int r = r0; r < r1; ++r) {
+      const int fl = d.init_flag[r];
+      nw += ((fl > 0 && (fl & keep_mask)) || d.c_gap[r] <= ws_gap) ? 1 : 0;
+    }
+    slot = block_excl_scan_1024(nw, s_warp, &mc);
+  }
   if (mc > p.ws_cap) {
     if (tid == 0) flag_capacity(ctl, CAP_WORKING);
     return;

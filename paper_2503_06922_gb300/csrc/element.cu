@@ -28,17 +28,16 @@ struct ElemShared {
   float H32[7][12];
 };
 
-// Block body: elements k + bx * kWarpsPerElemBlock + warp.  kMixed: the tangent products
+// Warp body: element k + bx * kWarpsPerElemBlock + wsub (wsub < kWarpsPerElemBlock: the element's
+// place in its work unit), computed by one warp with its own scratch S.  kMixed: the tangent products
 // H = K_l (B E^T) and K = (B E^T)^T H take FP32 operands and FP32 accumulation; the element force
 // (the Newton residual) stays FP64.
 template <bool kMixed>
-__device__ __forceinline__ void element_body(const Params& p, const Dev& d, int bx) {
-  __shared__ ElemShared sm[kWarpsPerElemBlock];
+__device__ __forceinline__ void element_warp(const Params& p, const Dev& d, int bx, int wsub, ElemShared& S) {
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  ElemShared& S = sm[wib];
+  const int wib = wsub;
   Ctl* ctl = d.ctl;
-  if (bx == 0 && threadIdx.x == 0) {                 // reset the per-iteration reductions
+  if (bx == 0 && wsub == 0 && lane == 0) {           // reset the per-iteration reductions
     ctl->umax_bits = 0ull; ctl->step_bits = 0ull; ctl->res_bits = 0ull;
 #pragma unroll
     for (int j = 0; j < kAccelDepth; ++j) ctl->aa_cmax_bits[j] = 0ull;
@@ -258,16 +257,48 @@ __device__ __forceinline__ bool mixed_tangent(const Params& p, const Dev& d) {
 }
 
 __global__ void __launch_bounds__(32 * kWarpsPerElemBlock) element_kernel(Params p, Dev d) {
+  __shared__ ElemShared sm[kWarpsPerElemBlock];
   pdl_enter();
-  if (mixed_tangent(p, d)) element_body<true>(p, d, blockIdx.x);
-  else element_body<false>(p, d, blockIdx.x);
+  const int w = threadIdx.x >> 5;
+  if (mixed_tangent(p, d)) element_warp<true>(p, d, blockIdx.x, w, sm[w]);
+  else element_warp<false>(p, d, blockIdx.x, w, sm[w]);
 }
 
-__global__ void __launch_bounds__(32 * kWarpsPerElemBlock) element_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
-  for_units(tab, plan, PH_ELEM, [](const Inst& in, int bx, int) {
-    if (mixed_tangent(in.p, in.d)) element_body<true>(in.p, in.d, bx);
-    else element_body<false>(in.p, in.d, bx);
-  });
+// Batched element phase with kW warps per block (kW a multiple of kWarpsPerElemBlock): the plan's
+// work units hold kWarpsPerElemBlock elements each, and a block takes kW / kWarpsPerElemBlock units
+// at a time, one warp per element; each warp walks the plan's units independently (no block barrier).
+// The element mapping (warps per block) is one of the batch's autotuned choices.
+template <int kW>
+__device__ __forceinline__ void element_batch_body(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
+  static_assert(kW % kWarpsPerElemBlock == 0, "whole work units per block");
+  constexpr int kUnits = kW / kWarpsPerElemBlock;
+  __shared__ ElemShared sm[kW];
+  __shared__ int s_pre[kMaxBatch + 1];
+  pdl_enter();
+  const int na = plan->n_act;
+  const int total = plan->pre[PH_ELEM][na];
+  if ((int)blockIdx.x * kUnits >= total) return;
+  for (int i = threadIdx.x; i <= na; i += blockDim.x) s_pre[i] = plan->pre[PH_ELEM][i];
+  __syncthreads();
+  const int w = threadIdx.x >> 5;
+  int j = 0;
+  for (int u0 = blockIdx.x * kUnits; u0 < total; u0 += gridDim.x * kUnits) {
+    const int u = u0 + w / kWarpsPerElemBlock;
+    if (u >= total) break;
+    while (s_pre[j + 1] <= u) ++j;                  // this warp's units come in increasing order
+    const Inst& in = tab[plan->act[j]];
+    if (mixed_tangent(in.p, in.d)) element_warp<true>(in.p, in.d, u - s_pre[j], w % kWarpsPerElemBlock, sm[w]);
+    else element_warp<false>(in.p, in.d, u - s_pre[j], w % kWarpsPerElemBlock, sm[w]);
+  }
+}
+__global__ void __launch_bounds__(64) element_batch_w2(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
+  element_batch_body<2>(tab, plan);
+}
+__global__ void __launch_bounds__(128) element_batch_w4(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
+  element_batch_body<4>(tab, plan);
+}
+__global__ void __launch_bounds__(256) element_batch_w8(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
+  element_batch_body<8>(tab, plan);
 }
 
 void upload_element_tables() {

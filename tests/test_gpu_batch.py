@@ -81,7 +81,8 @@ def test_batch_sweep_equals_solves_alone(af):
 
 
 def test_autotuned_packing_keeps_results(af):
-    """Autotuning takes the four grid variants in turn; every member still equals its solve alone."""
+    """Autotuning takes the twelve variants (four grid divisors x three element mappings) in turn;
+    every member still equals its solve alone."""
     ws = _mixed_workloads()
     alone = _alone(af, ws)
     hs = [af.AccFem(w.robot, w.lumen) for w in ws]
@@ -100,7 +101,7 @@ def test_autotuned_packing_keeps_results(af):
         for i in range(len(ws)):
             _same(res[i], alone[i][s], "member %d step %d" % (i, s))
     v, ms = b.accfem_batch_tuning()
-    assert 0 <= v < 4 and np.all(ms > 0.0)
+    assert 0 <= v < 12 and len(ms) == 12 and np.all(ms > 0.0)
     b.close()
     for h in hs:
         h.close()

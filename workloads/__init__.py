@@ -295,8 +295,9 @@ def branching_tree_lumen(seed: int = 3, radii=(0.008, 0.0055, 0.004), h=0.00038,
     by surface nets on a cubic grid of spacing h restricted to a narrow band around the tube walls:
     one vertex per grid cell that the surface crosses (the mean of its edge crossings, then moved onto
     the surface along the field's gradient), one quad (two triangles, the shorter diagonal) per grid
-    edge that the surface crosses, wound outward.  The root starts root_back before the origin and
-    triangles behind x = -entrance_cut are dropped, which opens the entrance.  Returns the lumen and
+    edge that the surface crosses, wound outward; vertices closer than h / 10 are welded and the
+    slivers left dropped.  The root starts root_back before the origin and triangles behind
+    x = -entrance_cut are dropped, which opens the entrance.  Returns the lumen and
     the root-to-leaf path lengths (sum of segment lengths)."""
     segs = _tree_segments(seed, radii)
     f, A, D, Lj, R = _capsule_field(segs, root_back)
@@ -400,6 +401,28 @@ def branching_tree_lumen(seed: int = 3, radii=(0.008, 0.0055, 0.004), h=0.00038,
     # of a carina (their winding disagrees with the field's outward gradient; each is < 0.1 mm^2)
     _, gc = f(cen)
     T = T[(area2 > 1e-16) & (np.sum(nrm * gc, axis=1) > 0.0) & (cen[:, 0] >= -entrance_cut)]
+    # weld vertices closer than h / 10 (edges that short come from projections landing together at
+    # creases), drop the triangles that collapse and the needles left (area below h^2 / 300): such
+    # slivers make the closest-feature tests of a node flip under sub-nanometre motions
+    from scipy.spatial import cKDTree
+    pairs = cKDTree(V).query_pairs(0.1 * h, output_type="ndarray")
+    parent = np.arange(len(V))
+
+    def root(i):
+        while parent[i] != i:
+            parent[i] = parent[parent[i]]
+            i = parent[i]
+        return i
+    for a_, b_ in pairs:
+        ra, rb = root(a_), root(b_)
+        if ra != rb:
+            parent[max(ra, rb)] = min(ra, rb)
+    rep = np.array([root(i) for i in range(len(V))])
+    T = rep[T]
+    ok = (T[:, 0] != T[:, 1]) & (T[:, 1] != T[:, 2]) & (T[:, 0] != T[:, 2])
+    T = T[ok]
+    area = 0.5 * np.linalg.norm(np.cross(V[T[:, 1]] - V[T[:, 0]], V[T[:, 2]] - V[T[:, 0]]), axis=1)
+    T = T[area >= h * h / 300.0]
     used = np.unique(T)
     remap = np.full(len(V), -1, dtype=np.int64)
     remap[used] = np.arange(len(used))
