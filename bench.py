@@ -434,14 +434,18 @@ def batched_run(af, n_inst=256, chunk=8, seq_sample=16):
             h.accfem_reset()
             h.accfem_set_precision(mode)
         b = af.AccFemBatch(hs)
-        # autotuning before the timed run: the first steps of every instance, two Newton iterations
-        # per launch, until every variant has been timed twice; then the instances start over
+        # autotuning before the timed run, on work of the run's own size: every instance solves its
+        # last step (full insertion) from the straight pose, two Newton iterations per launch, until
+        # every variant has been timed twice; then the instances start over
         b.accfem_batch_autotune(2)
-        for s0 in range(12):
-            sel = np.nonzero(step == s0)[0]
+        last = np.array([len(w.insertions) - 1 for w in ws])
+        sel = np.array([np.nonzero((mem == i) & (step == last[i]))[0][0] for i in range(len(ws))])
+        for _ in range(4):
             b.accfem_batch_serve(np.zeros(len(sel)), mem[sel], ten[sel], ins[sel], chunk_iters=2)
             if b.accfem_batch_tuning()[0] >= 0:
                 break
+            for h in hs:
+                h.accfem_reset()
         for h in hs:
             h.accfem_reset()
         l0 = b.accfem_batch_kernel_launches()
@@ -963,6 +967,29 @@ def ours(args, rank, world, local_rank):
                         "contact_kernel_us_final_state": admm_ct_us, "active_set_contact_kernel_us": ct_us}
         progress("contact solver: ADMM %.1f solves/s, contact kernel %.0f us (active set %.0f us)"
                  % (contact_admm["solves_per_s"], admm_ct_us, ct_us))
+        # ---- segment contacts (Eq. 3-7 at any point of an element): the same sweep, timed like `value`
+        progress("segment contacts: sweep")
+        h.accfem_set_contact_model(af.CONTACT_SEGMENT)
+        with torch.cuda.stream(stream):
+            sweep_resident()
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            seg_fail, seg_iters = sweep_resident()
+            t1.record(stream)
+            t1.synchronize()
+            seg_ms = t0.elapsed_time(t1)
+        seg_rows = h.accfem_solve_stats()
+        seg_coll_us = h.accfem_time_kernel(af.KERNEL_COLLIDE, 20)
+        h.accfem_set_contact_model(af.CONTACT_NODE)
+        segment_contacts = {"model": "contact points anywhere on an element's chord, displacement by N(xi) of Eq. 4-6 "
+                                     "in the element frame; rows per element (chord against triangles)",
+                            "solves_per_s": S / (seg_ms * 1e-3), "ms_per_step": seg_ms,
+                            "newton_iters_per_solve": seg_iters / S, "failed_solves": int(seg_fail),
+                            "rows_working_active_final": list(seg_rows[:3]), "collide_us_final_state": seg_coll_us}
+        progress("segment contacts: %.1f solves/s, %d failed" % (segment_contacts["solves_per_s"], seg_fail))
         # ---- mixed precision: the same sweep with the FP32 element tangent, timed like `value`, and
         #      every solve compared with the FP64 solve of the same step
         progress("precision: mixed sweep")
@@ -1072,6 +1099,7 @@ def ours(args, rank, world, local_rank):
                     "seconds_per_iteration": cpu["seconds_per_iteration"]}}
         line["precision"] = precision
         line["contact_admm"] = contact_admm
+        line["segment_contacts"] = segment_contacts
         line.update(extra)
         if "batched" in extra and "served" in extra:
             bt, sv = extra["batched"], extra["served"]

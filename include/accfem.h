@@ -206,6 +206,21 @@ accfem_status accfem_set_frame_mode(accfem_handle* h, int32_t iters_per_frame);
 #define ACCFEM_CONTACT_ADMM 1
 accfem_status accfem_set_contact_solver(accfem_handle* h, int32_t solver);
 
+/* Contact model (Eq. 3-7).  ACCFEM_CONTACT_NODE (the default): a contact point sits at a node (xi = 0 of
+ * an element; Sec. III.C pairs nodes with triangles), one constraint row per wall feature the node lies
+ * over.  ACCFEM_CONTACT_SEGMENT: a contact point may lie anywhere on an element's chord, at chord
+ * fraction s, and its displacement is interpolated from the element's two nodal translations by N(xi)
+ * of Eq. 4-6 in the element frame (axial P1, P2 along the chord, transverse P3, P4 across it); one row
+ * per wall feature the chord lies over (the node rule with the chord's closest point for the node), a
+ * row at a shared node kept once, on the lower element; per element at most 144 triangles reach the
+ * exact test and 32 rows are kept (ACCFEM_E_CONTACT_CAPACITY beyond).  In segment mode a result's contact_node is the
+ * element's far node (element contact_node - 1 joins nodes contact_node - 1 and contact_node) and
+ * contact_point the wall point.  Call between solves; a batch takes each member's model when the batch
+ * is created.  The allocation-free query always detects node rows.  E_INVALID_ARG otherwise. */
+#define ACCFEM_CONTACT_NODE 0
+#define ACCFEM_CONTACT_SEGMENT 1
+accfem_status accfem_set_contact_model(accfem_handle* h, int32_t model);
+
 /* Cumulative bytes copied host->device and device->host by this handle's solve and state calls. */
 accfem_status accfem_transfer_bytes(const accfem_handle* h, int64_t* h2d, int64_t* d2h);
 

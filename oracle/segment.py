@@ -140,11 +140,19 @@ def detect_elements(x, k, V, T, r_o, act, nf=None):
         nf = np.cross(B - A, C - A)
         nf = nf / np.linalg.norm(nf, axis=1, keepdims=True)
     thr = r_o + act
+    # a triangle lies within its bounding sphere (centroid, farthest vertex), so one whose sphere is
+    # farther than thr from the chord has no point within thr of it and gives no row: skipping it
+    # changes nothing (when every triangle is farther than thr, the element has no row anyway)
+    cen = V[T].mean(axis=1)
+    rad = np.max(np.linalg.norm(V[T] - cen[:, None, :], axis=2), axis=1)
     rows = []
     for e in range(max(k, 0), M):
         xa, xb = x[e], x[e + 1]
+        ab = xb - xa
+        sc = np.clip(((cen - xa) @ ab) / (ab @ ab), 0.0, 1.0)
+        dc = np.linalg.norm(cen - (xa[None, :] + sc[:, None] * ab[None, :]), axis=1)
         cands = []
-        for t in range(len(T)):
+        for t in np.nonzero(dc - rad <= thr * (1.0 + 1e-9) + 1e-12)[0]:
             a, b, c = V[T[t, 0]], V[T[t, 1]], V[T[t, 2]]
             s, q, w, d, interior = closest_segment_triangle(xa, xb, a, b, c)
             cands.append((d, t, s, q, w, interior, a, b, c))

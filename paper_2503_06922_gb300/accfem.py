@@ -78,10 +78,11 @@ EXPORTS = ["accfem_default_options", "accfem_create", "accfem_solve", "accfem_so
            "accfem_batch_kernel_launches", "accfem_batch_last_error", "accfem_batch_destroy", "accfem_batch_serve",
            "accfem_device_bytes", "accfem_solve_stats", "accfem_set_precision", "accfem_batch_autotune",
            "accfem_batch_tuning", "accfem_set_element_modulus", "accfem_set_frame_mode",
-           "accfem_set_contact_solver", "accfem_batch_time_phase"]
+           "accfem_set_contact_solver", "accfem_batch_time_phase", "accfem_set_contact_model"]
 
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 CONTACT_ACTIVE_SET, CONTACT_ADMM = 0, 1
+CONTACT_NODE, CONTACT_SEGMENT = 0, 1
 
 MAX_CABLES = 8
 
@@ -144,6 +145,7 @@ def load(path=LIB_PATH):
     lib.accfem_set_element_modulus.argtypes = [H, _dp, ctypes.c_int32]
     lib.accfem_set_frame_mode.argtypes = [H, ctypes.c_int32]
     lib.accfem_set_contact_solver.argtypes = [H, ctypes.c_int32]
+    lib.accfem_set_contact_model.argtypes = [H, ctypes.c_int32]
     lib.accfem_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int32]
     lib.accfem_batch_tuning.argtypes = [ctypes.c_void_p, _ip, _dp]
     lib.accfem_batch_time_phase.argtypes = [B, ctypes.c_int, ctypes.c_int32, _dp, ctypes.POINTER(ctypes.c_int64)]
@@ -156,7 +158,8 @@ def load(path=LIB_PATH):
                  "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream",
                  "accfem_batch_transfer_bytes", "accfem_batch_serve", "accfem_device_bytes", "accfem_solve_stats", "accfem_set_precision",
                  "accfem_batch_autotune", "accfem_batch_tuning", "accfem_set_element_modulus",
-                 "accfem_set_frame_mode", "accfem_set_contact_solver", "accfem_batch_time_phase"):
+                 "accfem_set_frame_mode", "accfem_set_contact_solver", "accfem_batch_time_phase",
+                 "accfem_set_contact_model"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -316,6 +319,10 @@ class AccFem:
     def accfem_set_contact_solver(self, solver):
         """CONTACT_ACTIVE_SET (default) or CONTACT_ADMM (OSQP's ADMM guess, then the exact polish)."""
         return int(self._lib.accfem_set_contact_solver(self.h, int(solver)))
+
+    def accfem_set_contact_model(self, model):
+        """CONTACT_NODE (default) or CONTACT_SEGMENT (Eq. 3-7 at any point of an element)."""
+        return int(self._lib.accfem_set_contact_model(self.h, int(model)))
 
     def accfem_set_frame_mode(self, iters_per_frame):
         """Frame mode: at most iters_per_frame Newton iterations per solve, OK at the cap (0: off)."""

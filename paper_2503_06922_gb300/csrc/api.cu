@@ -16,6 +16,7 @@
 namespace accfem {
 __global__ void element_kernel(Params p, Dev d);
 __global__ void collide_kernel(Params p, Dev d);
+__global__ void collide_segment_kernel(Params p, Dev d);
 __global__ void compact_kernel(Params p, Dev d);
 __global__ void bcr_bwd_kernel(Params p, Dev d, int s);
 __global__ void contact_kernel(Params p, Dev d);
@@ -325,9 +326,11 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
   ok = ok && dalloc(h, &cs, ncell + 1) && dalloc(h, &ct, std::max<int64_t>(T, 1)) && dalloc(h, &t32, tri32.size()) && dalloc(h, &s32, sph32.size()) &&
        dalloc(h, &vv, std::max<int64_t>(3 * NV, 1)) && dalloc(h, &tv, std::max<int64_t>(3 * T, 1)) &&
        dalloc(h, &nfc_d, std::max<int64_t>(3 * T, 1));
-  ok = ok && dalloc(h, &d.ncon, nfc) && dalloc(h, &d.con_tri, (size_t)nfc * kCpn) &&
-       dalloc(h, &d.con_pt, (size_t)nfc * kCpn * 3) && dalloc(h, &d.con_n, (size_t)nfc * kCpn * 3) &&
-       dalloc(h, &d.con_gap, (size_t)nfc * kCpn) && dalloc(h, &d.c_node, mc) && dalloc(h, &d.c_tri, mc) &&
+  ok = ok && dalloc(h, &d.ncon, nfc) && dalloc(h, &d.con_tri, (size_t)nfc * kListCap) &&
+       dalloc(h, &d.con_pt, (size_t)nfc * kListCap * 3) && dalloc(h, &d.con_n, (size_t)nfc * kListCap * 3) &&
+       dalloc(h, &d.con_gap, (size_t)nfc * kListCap) && dalloc(h, &d.c_node, mc) && dalloc(h, &d.c_tri, mc) &&
+       dalloc(h, &d.con_s, (size_t)nfc * kListCap) && dalloc(h, &d.con_keep, nfc) && dalloc(h, &d.c_node2, mc) && dalloc(h, &d.c_w1, (size_t)mc * 3) &&
+       dalloc(h, &d.c_w2, (size_t)mc * 3) && dalloc(h, &d.c_s, mc) &&
        dalloc(h, &d.c_pt, 3 * mc) && dalloc(h, &d.c_n, 3 * mc) && dalloc(h, &d.c_gap, mc) &&
        dalloc(h, &d.c_first, nfc + 1) && dalloc(h, &d.p_node, mc) && dalloc(h, &d.p_tri, mc) && dalloc(h, &d.p_first, nfc + 1) &&
        dalloc(h, &d.p_flag, mc) && dalloc(h, &d.init_flag, mc) && dalloc(h, &d.wrow, wc) &&
@@ -337,7 +340,7 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
        dalloc(h, &d.B, (size_t)nfc * 6 * p.nrhs_cap) && dalloc(h, &d.g, (size_t)nfc * 6) &&
        dalloc(h, &d.dx, (size_t)nfc * 6) && dalloc(h, &d.du_prev, (size_t)nfc * 3) &&
        dalloc(h, &d.rev_part, (size_t)nfc / 32 + 2) && dalloc(h, &d.aa_part, ((size_t)nfc / 32 + 2) * kAccelParts) &&
-       dalloc(h, &d.aa_f, (size_t)kAccelDepth * nfc * 6) && dalloc(h, &d.aa_d, (size_t)kAccelDepth * nfc * 6) && dalloc(h, &d.W, (size_t)wc * wc) &&
+       dalloc(h, &d.aa_f, (size_t)kAccelSlots * nfc * 6) && dalloc(h, &d.aa_d, (size_t)kAccelSlots * nfc * 6) && dalloc(h, &d.W, (size_t)wc * wc) &&
        dalloc(h, &d.y, mc) && dalloc(h, &d.gj, (size_t)wc * (wc + 2)) && dalloc(h, &d.plist, wc) &&
        dalloc(h, &d.ctl, 1);
   if (!ok) {
@@ -403,7 +406,9 @@ int enqueue_iteration(accfem_handle* h, int nf, cudaStream_t st, cudaGraphCondit
   const bool pdl = h->pdl;
   launch_k(pdl, element_kernel, grid(PH_ELEM), dim3(32 * kWarpsPerElemBlock), h->side, p, d); ++n;
   cudaEventRecord(h->join, h->side);
-  launch_k(pdl, collide_kernel, grid(PH_COLL), dim3(128), st, p, d); ++n;
+  if (p.contact_model == kContactSegment) launch_k(pdl, collide_segment_kernel, grid(PH_COLL), dim3(128), st, p, d);
+  else launch_k(pdl, collide_kernel, grid(PH_COLL), dim3(128), st, p, d);
+  ++n;
   launch_k(pdl, compact_kernel, dim3(1), dim3(1024), st, p, d); ++n;
   cudaStreamWaitEvent(st, h->join, 0);
   n += enqueue_factor(p, d, nf, st, pdl);
@@ -696,6 +701,19 @@ accfem_status accfem_set_contact_solver(accfem_handle* h, int32_t solver) {
   return ACCFEM_OK;
 }
 
+accfem_status accfem_set_contact_model(accfem_handle* h, int32_t model) {
+  if (!h || (model != ACCFEM_CONTACT_NODE && model != ACCFEM_CONTACT_SEGMENT)) return ACCFEM_E_INVALID_ARG;
+  if (h->p.contact_model == model) return ACCFEM_OK;
+  if (h->stream) cudaStreamSynchronize(h->work());
+  for (auto& kv : h->graphs) {     // the Newton graphs captured the collision kernel of the model
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  h->graphs.clear();
+  h->p.contact_model = model == ACCFEM_CONTACT_SEGMENT ? kContactSegment : kContactNode;
+  return ACCFEM_OK;
+}
+
 accfem_status accfem_set_frame_mode(accfem_handle* h, int32_t iters_per_frame) {
   if (!h || iters_per_frame < 0 || iters_per_frame > 1000000) return ACCFEM_E_INVALID_ARG;
   if (h->frame_iters == iters_per_frame) return ACCFEM_OK;
@@ -772,7 +790,10 @@ accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t
     switch (kernel) {
       case ACCFEM_KERNEL_ELEMENT:
         element_kernel<<<phase_gx(PH_ELEM, nf), 32 * kWarpsPerElemBlock, 0, st>>>(p, d); break;
-      case ACCFEM_KERNEL_COLLIDE: collide_kernel<<<phase_gx(PH_COLL, nf), 128, 0, st>>>(p, d); break;
+      case ACCFEM_KERNEL_COLLIDE:
+        if (p.contact_model == kContactSegment) collide_segment_kernel<<<phase_gx(PH_COLL, nf), 128, 0, st>>>(p, d);
+        else collide_kernel<<<phase_gx(PH_COLL, nf), 128, 0, st>>>(p, d);
+        break;
       case ACCFEM_KERNEL_ASSEMBLE:
         assemble_rhs_kernel<<<dim3(phase_gx(PH_ASM, nf), phase_gy(PH_ASM)), dim3(32, 6), 0, st>>>(p, d); break;
       case ACCFEM_KERNEL_FACTOR: per_launch = enqueue_factor(p, d, nf, st, h->pdl); break;

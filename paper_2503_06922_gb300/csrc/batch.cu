@@ -21,6 +21,7 @@ __global__ void element_batch_w2(const Inst* __restrict__ tab, const Plan* __res
 __global__ void element_batch_w4(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
 __global__ void element_batch_w8(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
 __global__ void collide_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
+__global__ void collide_segment_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
 __global__ void compact_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
 __global__ void assemble_rhs_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan);
 __global__ void bcr_level_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j);
@@ -107,6 +108,7 @@ int enqueue_batch_iteration(accfem_batch* b, cudaStream_t st, cudaGraphCondition
   launch_element_batch(b->elem_w, pdl, dim3(g[PH_ELEM]), b->side, tab, plan); ++n;
   cudaEventRecord(b->join, b->side);
   launch_k(pdl, collide_batch, dim3(g[PH_COLL]), dim3(128), st, tab, plan); ++n;
+  if (b->has_segment) { launch_k(pdl, collide_segment_batch, dim3(g[PH_COLL]), dim3(128), st, tab, plan); ++n; }
   launch_k(pdl, compact_batch, dim3(g[PH_COMPACT]), dim3(1024), st, tab, plan); ++n;
   cudaStreamWaitEvent(st, b->join, 0);
   launch_k(pdl, assemble_rhs_batch, dim3(g[PH_ASM]), dim3(32, 6), st, tab, plan); ++n;
@@ -253,6 +255,7 @@ accfem_status accfem_batch_create(accfem_handle* const* members, int32_t n_membe
   int max_m = 0;
   for (accfem_handle* h : b->members) {
     b->max_nodes = std::max(b->max_nodes, h->p.N);
+    b->has_segment = b->has_segment || h->p.contact_model == kContactSegment;
     max_m = std::max(max_m, h->p.M);
     pack += (size_t)7 * h->p.N + 6 + (size_t)9 * h->p.m_cap;
   }

@@ -40,6 +40,7 @@ struct accfem_batch {
   // picks the element mapping, blocks of 2, 4 or 8 warps with one warp per element
   static constexpr int kVariants = 12;
   int elem_w = 2;                   // warps per element block of the variant being captured or run
+  bool has_segment = false;         // a member uses segment contacts (their collision kernel is launched too)
   struct Variant {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;

@@ -67,6 +67,47 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   const int tid = threadIdx.x;
   const int per = (nf + 1023) / 1024;
   const int f0 = tid * per, f1 = min(f0 + per, nf);
+  if (p.contact_model == kContactSegment) {
+    // a contact at a shared node appears on both elements (s = 1 of element f - 1, s = 0 of element
+    // f, the same wall point): keep the lower element's row
+    for (int f = f0; f < f1; ++f) {
+      unsigned keep = 0u;
+      const int nc = d.ncon[f];
+      for (int r = 0; r < nc; ++r) {
+        const int src = f * kListCap + r;
+        bool drop = false;
+        if (f > 0 && d.con_s[src] == 0.0) {
+          const int np = d.ncon[f - 1];
+          for (int q = 0; q < np && !drop; ++q) {
+            const int o = (f - 1) * kListCap + q;
+            if (d.con_s[o] != 1.0) continue;
+            const double dx = d.con_pt[3 * o] - d.con_pt[3 * src], dy = d.con_pt[3 * o + 1] - d.con_pt[3 * src + 1],
+                         dz = d.con_pt[3 * o + 2] - d.con_pt[3 * src + 2];
+            drop = sqrt(dx * dx + dy * dy + dz * dz) <= 1e-12;
+          }
+        }
+        if (!drop) keep |= 1u << r;
+      }
+      d.con_keep[f] = (int)keep;
+    }
+    __syncthreads();
+    for (int f = f0; f < f1; ++f) {              // compact each element's list in place
+      const unsigned keep = (unsigned)d.con_keep[f];
+      int o = 0;
+      for (int r = 0; r < d.ncon[f]; ++r) {
+        if (!(keep & (1u << r))) continue;
+        const int a = f * kListCap + r, b = f * kListCap + o;
+        if (a != b) {
+          d.con_tri[b] = d.con_tri[a];
+          d.con_gap[b] = d.con_gap[a];
+          d.con_s[b] = d.con_s[a];
+          for (int c = 0; c < 3; ++c) { d.con_pt[3 * b + c] = d.con_pt[3 * a + c]; d.con_n[3 * b + c] = d.con_n[3 * a + c]; }
+        }
+        ++o;
+      }
+      d.ncon[f] = o;
+    }
+  }
   int loc = 0;
   for (int f = f0; f < f1; ++f) loc += d.ncon[f];
   if (tid == 0) s_same = 1;
@@ -86,19 +127,45 @@ __device__ __forceinline__ void compact_body(const Params& p, const Dev& d) {
   __syncthreads();
   for (int r = tid; r < m; r += 1024) {       // row payloads, one thread per row
     const int f = d.c_node[r];
-    const int src = f * kCpn + (r - d.c_first[f]);
+    const int src = f * kListCap + (r - d.c_first[f]);
     d.c_tri[r] = d.con_tri[src];
+    double n[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       d.c_pt[3 * r + c] = d.con_pt[src * 3 + c];
-      d.c_n[3 * r + c] = d.con_n[src * 3 + c];
+      n[c] = d.con_n[src * 3 + c];
+      d.c_n[3 * r + c] = n[c];
     }
     d.c_gap[r] = d.con_gap[src];
+    if (p.contact_model == kContactSegment) {
+      // Eq. 4-6 in the element frame: du(xi) = R_r N(xi) [R_r^T du_a; R_r^T du_b], axial weights P1, P2
+      // along the chord e1 and transverse weights P3, P4 across it, so
+      // n^T du(xi) = (P3 n + (P1 - P3)(n.e1) e1) . du_a + (P4 n + (P2 - P4)(n.e1) e1) . du_b
+      const int na = ctl->k + f, nb = na + 1;
+      double e1[3] = {d.px[nb] - d.px[na], d.py[nb] - d.py[na], d.pz[nb] - d.pz[na]};
+      const double il = 1.0 / sqrt(dot3(e1, e1));
+      e1[0] *= il; e1[1] *= il; e1[2] *= il;
+      const double rr = d.con_s[src];
+      const double P1 = 1.0 - rr, P2 = rr, P3 = 1.0 - 3.0 * rr * rr + 2.0 * rr * rr * rr, P4 = 3.0 * rr * rr - 2.0 * rr * rr * rr;
+      const double ne = dot3(n, e1);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        d.c_w1[3 * r + c] = P4 * n[c] + (P2 - P4) * ne * e1[c];    // the element's far node (free node f)
+        d.c_w2[3 * r + c] = P3 * n[c] + (P1 - P3) * ne * e1[c];    // its near node (free node f - 1)
+      }
+      d.c_node2[r] = f > 0 ? f - 1 : -1;
+      d.c_s[r] = rr;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { d.c_w1[3 * r + c] = n[c]; d.c_w2[3 * r + c] = 0.0; }
+      d.c_node2[r] = -1;
+      d.c_s[r] = 0.0;
+    }
   }
   __syncthreads();
   const int mp = ctl->m_prev;
   // flags of the same row (node, triangle) in the previous iteration; -1 for a new row.  The node's
-  // previous rows are [p_first[f], p_first[f+1]) (at most kCpn; none before the first compaction)
+  // previous rows are [p_first[f], p_first[f+1]) (at most kListCap; none before the first compaction)
   for (int r = tid; r < m; r += 1024) {
     const int nd = d.c_node[r], tr = d.c_tri[r];
     int found = -1;
@@ -294,7 +361,9 @@ __device__ __forceinline__ void assemble_rhs_body(const Params& p, const Dev& d,
       v = -s_g[c];
     } else {
       const int row = d.wrow[r - 1];
-      v = (d.c_node[row] == f && c < 3) ? d.c_n[3 * row + c] : 0.0;
+      if (c >= 3) v = 0.0;
+      else if (p.contact_model == kContactNode) v = d.c_node[row] == f ? d.c_w1[3 * row + c] : 0.0;
+      else v = d.c_node[row] == f ? d.c_w1[3 * row + c] : (d.c_node2[row] == f ? d.c_w2[3 * row + c] : 0.0);
     }
     d.B[((size_t)f * 6 + c) * p.nrhs_cap + r] = v;
   }

@@ -234,10 +234,10 @@ __device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int 
     if (lane == 0) flag_capacity(ctl, CAP_NODE_ROWS);
     return;
   }
-  int* ctri = d.con_tri + (size_t)f * kCpn;
-  double* cpt = d.con_pt + (size_t)f * kCpn * 3;
-  double* cn = d.con_n + (size_t)f * kCpn * 3;
-  double* cg = d.con_gap + (size_t)f * kCpn;
+  int* ctri = d.con_tri + (size_t)f * kListCap;
+  double* cpt = d.con_pt + (size_t)f * kListCap * 3;
+  double* cn = d.con_n + (size_t)f * kListCap * 3;
+  double* cg = d.con_gap + (size_t)f * kListCap;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     if (!kept[h]) continue;
@@ -273,8 +273,11 @@ __global__ void __launch_bounds__(128) collide_kernel(Params p, Dev d) {
   collide_body(p, d, blockIdx.x);
 }
 
+// Node rows of the batch's members with the node contact model (segment members: segment.cu).
 __global__ void __launch_bounds__(128) collide_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan) {
-  for_units(tab, plan, PH_COLL, [](const Inst& in, int bx, int) { collide_body(in.p, in.d, bx); });
+  for_units(tab, plan, PH_COLL, [](const Inst& in, int bx, int) {
+    if (in.p.contact_model == kContactNode) collide_body(in.p, in.d, bx);
+  });
 }
 
 }  // namespace accfem

@@ -7,6 +7,8 @@ namespace accfem {
 
 constexpr int kMaxCables = 8;
 constexpr int kCpn = 16;           // constraint rows per node (wall features the node lies over)
+constexpr int kSegCpn = 32;        // constraint rows per element in the segment model (a chord lies over more)
+constexpr int kListCap = 32;       // slots of a per-owner constraint list (>= kCpn, kSegCpn)
 constexpr int kSurvCap = 64;       // FP64 candidates per node after the FP32 prefilter
 constexpr int kCandCap = 256;      // candidates per node kept in shared memory (more: a second cell walk)
 constexpr int kElemStride = 96;    // doubles per element record: 78 K (upper) + 12 F + pad
@@ -18,12 +20,15 @@ constexpr int kPrecisionFP64 = 0, kPrecisionMixed = 1;
 // Anderson acceleration of the Newton iteration: previous iterates used, and the largest
 // sum |gamma_j| of an accepted accelerated step (the same values are used by the CPU oracle).
 constexpr int kAccelDepth = 3;
+constexpr int kAccelSlots = kAccelDepth + 1;   // ring of held iterates: the slot written in iteration k is
+                                              // none of the k - 1 .. k - kAccelDepth that are read then
 constexpr double kAccelGammaMax = 10.0;
 constexpr int kAccelParts = 10;    // per step block: G (6 upper entries) and b (3) of the least squares, sum |du|^2
 // Iterations of a solve that may take Anderson steps; later ones (and the FP32 tangent's) fall back to
 // the 1-D secant over-relaxation of a slow monotone mode.
 constexpr int kAccelIters = 100;
 constexpr int kLcpActiveSet = 0, kLcpAdmm = 1;
+constexpr int kContactNode = 0, kContactSegment = 1;
 // A triangle whose plane projection of the node lies inside it enlarged by this barycentric margin
 // ("over the face") gives a constraint row; the same value is used by the CPU oracle.
 constexpr double kFaceBand = 0.1;
@@ -67,6 +72,7 @@ struct Params {
   int precision;                 // kPrecisionFP64 or kPrecisionMixed (FP32 element tangent)
   int lcp_mode;                  // kLcpActiveSet, or kLcpAdmm (OSQP's ADMM guess, then the exact polish)
   int admm_iters;                // ADMM iteration cap
+  int contact_model;             // kContactNode (rows at nodes) or kContactSegment (rows anywhere on an element)
 };
 
 // Control block, resident on the device; one per handle.
@@ -138,16 +144,25 @@ struct Dev {
   const double* V;                                   // n_vertices * 3
   const int* T;                                      // n_tri * 3
   const double* nface;                               // n_tri * 3 outward unit normals
-  // per free node constraint lists (index f = node - k - 1)
+  // per owner constraint lists: owner f = free node f (node rows; node = k + 1 + f) or free element f
+  // (segment rows; element k + f, joining nodes k + f and k + 1 + f)
   int* ncon;                                         // nf_cap
-  int* con_tri;                                      // nf_cap * kCpn
-  double* con_pt;                                    // nf_cap * kCpn * 3
-  double* con_n;                                     // nf_cap * kCpn * 3
-  double* con_gap;                                   // nf_cap * kCpn
-  // compacted constraint rows
-  int* c_node;                                       // free-node index f of row
+  int* con_tri;                                      // nf_cap * kListCap
+  double* con_pt;                                    // nf_cap * kListCap * 3 (wall point)
+  double* con_n;                                     // nf_cap * kListCap * 3
+  double* con_gap;                                   // nf_cap * kListCap
+  double* con_s;                                     // nf_cap * kListCap: chord fraction of a segment row
+  int* con_keep;                                     // nf_cap: rows of an element kept after the shared-node merge
+  // compacted constraint rows.  Row r constrains n^T du(contact point) = w1 . du_{c_node} + w2 . du_{c_node2}
+  // (free-node indices; c_node2 = -1: one node): a node row has w1 = n; a segment row of element
+  // k + f has c_node = f (the element's far node), c_node2 = f - 1 (-1 when prescribed) and the
+  // weights of Eq. 4-6 in the element frame
+  int* c_node;                                       // owner f of row (its free node, or the element's far node)
   int* c_tri;
   double *c_pt, *c_n, *c_gap;                        // m_cap * 3, * 3, * 1
+  int* c_node2;                                      // m_cap: second node of a segment row, else -1
+  double *c_w1, *c_w2;                               // m_cap * 3 each: weights on the two nodes' translations
+  double* c_s;                                       // m_cap: chord fraction of a segment row (0 for node rows)
   int *c_first;                                      // nf_cap + 1: rows of node f = [c_first[f], c_first[f+1])
   int *p_node, *p_tri;                               // previous iteration's rows
   int *p_first;                                      // nf_cap + 1: previous rows of node f = [p_first[f], p_first[f+1])
@@ -164,8 +179,8 @@ struct Dev {
   double* du_prev;                                   // nf_cap * 3 : previous Newton step (translations)
   double* rev_part;                                  // per step_kernel block: sum du . du_prev
   double* aa_part;                                   // per step_kernel block: kAccelParts least-squares sums
-  double* aa_f;                                      // kAccelDepth * nf_cap * 6: unscaled steps of previous iterates
-  double* aa_d;                                      // kAccelDepth * nf_cap * 6: increments applied there
+  double* aa_f;                                      // kAccelSlots * nf_cap * 6: unscaled steps of previous iterates
+  double* aa_d;                                      // kAccelSlots * nf_cap * 6: increments applied there
   // contact LCP
   double *W, *y, *gj;                                // ws_cap^2 (slots), m_cap (rows), ws_cap*(ws_cap+2)
   int *plist;                                        // ws_cap: active slots

@@ -100,20 +100,40 @@ __device__ void ensure_columns(const Dev& d, LcpShared& S, int m, size_t ld, dou
   // every new column; the RHS columns are read-only here, so the loads of different columns overlap
   for (int i = tid; i < m; i += nt) {
     const int row = d.wrow[i];
-    const int fi = d.c_node[row];
-    const double n0 = d.c_n[3 * row], n1 = d.c_n[3 * row + 1], n2 = d.c_n[3 * row + 2];
+    const int fi = d.c_node[row], fi2 = d.c_node2[row];
+    const double n0 = d.c_w1[3 * row], n1 = d.c_w1[3 * row + 1], n2 = d.c_w1[3 * row + 2];
     const double* b0 = d.B + ((size_t)fi * 6) * ld + 1;
     const double* b1 = b0 + ld;
     const double* b2 = b1 + ld;
-    for (int a = 0; a < S.np; ++a) {
-      const int j = S.plist[a];
-      if (S.wcol[j]) continue;
-      double s = 0.0;
-      s = fma(n0, __ldg(b0 + j), s);
-      s = fma(n1, __ldg(b1 + j), s);
-      s = fma(n2, __ldg(b2 + j), s);
-      if (i == j) s += eps_w;
-      d.W[(size_t)i * m + j] = s;
+    if (fi2 < 0) {
+      for (int a = 0; a < S.np; ++a) {
+        const int j = S.plist[a];
+        if (S.wcol[j]) continue;
+        double s = 0.0;
+        s = fma(n0, __ldg(b0 + j), s);
+        s = fma(n1, __ldg(b1 + j), s);
+        s = fma(n2, __ldg(b2 + j), s);
+        if (i == j) s += eps_w;
+        d.W[(size_t)i * m + j] = s;
+      }
+    } else {                                       // a segment row also weighs the element's near node
+      const double m0 = d.c_w2[3 * row], m1 = d.c_w2[3 * row + 1], m2 = d.c_w2[3 * row + 2];
+      const double* c0 = d.B + ((size_t)fi2 * 6) * ld + 1;
+      const double* c1 = c0 + ld;
+      const double* c2 = c1 + ld;
+      for (int a = 0; a < S.np; ++a) {
+        const int j = S.plist[a];
+        if (S.wcol[j]) continue;
+        double s = 0.0;
+        s = fma(n0, __ldg(b0 + j), s);
+        s = fma(n1, __ldg(b1 + j), s);
+        s = fma(n2, __ldg(b2 + j), s);
+        s = fma(m0, __ldg(c0 + j), s);
+        s = fma(m1, __ldg(c1 + j), s);
+        s = fma(m2, __ldg(c2 + j), s);
+        if (i == j) s += eps_w;
+        d.W[(size_t)i * m + j] = s;
+      }
     }
   }
   __syncthreads();
@@ -309,13 +329,21 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
   double wd = 0.0, qmax = 0.0;
   for (int i = tid; i < m; i += nt) {
     const int row = d.wrow[i];
-    const int fi = d.c_node[row];
-    const double* n = d.c_n + 3 * row;
+    const int fi = d.c_node[row], fi2 = d.c_node2[row];
+    const double* n = d.c_w1 + 3 * row;
     double s = 0.0, wii = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       s = fma(n[c], d.B[((size_t)fi * 6 + c) * ld], s);
       wii = fma(n[c], d.B[((size_t)fi * 6 + c) * ld + 1 + i], wii);
+    }
+    if (fi2 >= 0) {
+      const double* n2 = d.c_w2 + 3 * row;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        s = fma(n2[c], d.B[((size_t)fi2 * 6 + c) * ld], s);
+        wii = fma(n2[c], d.B[((size_t)fi2 * 6 + c) * ld + 1 + i], wii);
+      }
     }
     const int fl = d.init_flag[row];
     S.q[i] = d.c_gap[row] - s;

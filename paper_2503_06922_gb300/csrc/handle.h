@@ -95,7 +95,7 @@ inline std::string accfem_solve_message(const Ctl& c, accfem_status s) {
       case accfem::CAP_ROWS: m += ": constraint rows above max_contacts"; break;
       case accfem::CAP_CANDIDATES: m += ": a node has more than 768 triangles within the activation distance"; break;
       case accfem::CAP_SURVIVORS: m += ": a node has more than 64 triangles for the exact distance test"; break;
-      case accfem::CAP_NODE_ROWS: m += ": a node has more than 16 constraint rows"; break;
+      case accfem::CAP_NODE_ROWS: m += ": a node has more than 16 constraint rows (an element more than 32 in the segment model)"; break;
       case accfem::CAP_LCP_ROWS: m += ": working-set rows above the contact solver's 512"; break;
       case accfem::CAP_WORKING: m += ": working-set rows above min(max_contacts, 512)"; break;
       default: break;

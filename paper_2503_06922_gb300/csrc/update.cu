@@ -35,7 +35,10 @@ __device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx)
     d.dx[(size_t)f * 6 + c] = v;
     double r = d.g[(size_t)f * 6 + c];
     if (c < 3) {
-      for (int row = d.c_first[f]; row < d.c_first[f + 1]; ++row) r = fma(d.c_n[3 * row + c], d.y[row], r);
+      for (int row = d.c_first[f]; row < d.c_first[f + 1]; ++row) r = fma(d.c_w1[3 * row + c], d.y[row], r);
+      if (p.contact_model == kContactSegment && f + 1 < nf)   // segment rows of the next element weigh this node too
+        for (int row = d.c_first[f + 1]; row < d.c_first[f + 2]; ++row)
+          if (d.c_node2[row] == f) r = fma(d.c_w2[3 * row + c], d.y[row], r);
     }
     s_r[fl][c] = fabs(r);
   }
@@ -51,7 +54,7 @@ __device__ __forceinline__ void step_body(const Params& p, const Dev& d, int bx)
     if (act) {
       double prev = s_dx[fl][c];
       for (int j = 1; j <= n_h; ++j) {
-        const double h = d.aa_f[((size_t)((k_it - j) % kAccelDepth) * p.M + f) * 6 + c];
+        const double h = d.aa_f[((size_t)((k_it - j) % kAccelSlots) * p.M + f) * 6 + c];
         cj[j - 1] = prev - h;
         prev = h;
       }
@@ -260,26 +263,29 @@ __device__ __forceinline__ void apply_body(const Params& p, const Dev& d, int bx
   if (f < nf) {
     const int node = ctl->k + 1 + f;
     const int k_it = ctl->iter, n_h = ctl->aa_n;
-    const double* dx = d.dx + (size_t)f * 6;
-    double inc[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) inc[c] = alpha * dx[c];
-    if (accel) {
-      // f_k - sum_j gamma_j (d_{k-j} + f_{k-j+1} - f_{k-j})
+    // the increment of free node g: alpha dx, or f_k - sum_j gamma_j (d_{k-j} + f_{k-j+1} - f_{k-j})
+    auto increment = [&](int g, double* out) {
+      const double* dxg = d.dx + (size_t)g * 6;
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
-        double v = dx[c], prev = dx[c];
-        for (int j = 1; j <= n_h; ++j) {
-          const size_t at = ((size_t)((k_it - j) % kAccelDepth) * p.M + f) * 6 + c;
-          const double h = d.aa_f[at];
-          v = fma(-s_lim.gamma[j - 1], d.aa_d[at] + (prev - h), v);
-          prev = h;
+        double v = accel ? dxg[c] : alpha * dxg[c];
+        if (accel) {
+          double prev = dxg[c];
+          for (int j = 1; j <= n_h; ++j) {
+            const size_t at = ((size_t)((k_it - j) % kAccelSlots) * p.M + g) * 6 + c;
+            const double h = d.aa_f[at];
+            v = fma(-s_lim.gamma[j - 1], d.aa_d[at] + (prev - h), v);
+            prev = h;
+          }
         }
-        inc[c] = v;
+        out[c] = v;
       }
-    }
+    };
+    const double* dx = d.dx + (size_t)f * 6;
+    double inc[6];
+    increment(f, inc);
     // this iterate joins the held ones (its slot held the oldest, already read above)
-    const size_t at = ((size_t)(k_it % kAccelDepth) * p.M + f) * 6;
+    const size_t at = ((size_t)(k_it % kAccelSlots) * p.M + f) * 6;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       d.aa_f[at + c] = dx[c];
@@ -287,8 +293,15 @@ __device__ __forceinline__ void apply_body(const Params& p, const Dev& d, int bx
     }
     for (int row = d.c_first[f]; row < d.c_first[f + 1]; ++row) {
       if (d.rslot[row] >= 0) continue;
-      const double* n = d.c_n + 3 * row;
-      const double w = d.c_gap[row] - fma(n[0], inc[0], fma(n[1], inc[1], n[2] * inc[2]));
+      const double* n = d.c_w1 + 3 * row;
+      double an = fma(n[0], inc[0], fma(n[1], inc[1], n[2] * inc[2]));
+      if (d.c_node2[row] >= 0) {                    // a segment row: the element's near node moves too
+        double inc2[6];
+        increment(d.c_node2[row], inc2);
+        const double* n2 = d.c_w2 + 3 * row;
+        an = fma(n2[0], inc2[0], fma(n2[1], inc2[1], fma(n2[2], inc2[2], an)));
+      }
+      const double w = d.c_gap[row] - an;
       if (w < -p.tol) {
         d.p_flag[row] = RF_VIOLATED;
         ctl->incomplete = 1;
