@@ -177,7 +177,7 @@ def _oracle_iteration_worker(s, n_iters, record, q):
     from oracle import solver
     w = workload()
     rec = np.load(record)
-    m = solver.Model(w.robot, w.lumen, solver.Options(max_newton_iters=n_iters))
+    m = solver.Model(w.robot, w.lumen, solver.Options(max_newton_iters=n_iters, max_contacts=MAX_CONTACTS))
     if s > 0:
         m.state = (rec["pos"][s - 1].copy(), rec["rot"][s - 1].copy(), float(w.insertions[s - 1]))
     t0 = time.perf_counter()

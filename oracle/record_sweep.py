@@ -26,6 +26,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+MAX_CONTACTS = 4096      # constraint-row capacity, as the benchmark's handles (the sweep's end has ~330 rows)
 DEFAULT_OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "records", "catmull_rom_600mm_M300_sweep.npz")
 
 
@@ -37,7 +38,7 @@ def _recount_one(args):
     from oracle import solver
     rec = np.load(path)
     w = wl.catmull_rom_workload(lumen_seed=1, tension_seed=2, n_steps=60)
-    m = solver.Model(w.robot, w.lumen)
+    m = solver.Model(w.robot, w.lumen, solver.Options(max_contacts=MAX_CONTACTS))
     if s > 0:
         m.state = (rec["pos"][s - 1].copy(), rec["rot"][s - 1].copy(), float(w.insertions[s - 1]))
     t0 = time.perf_counter()
@@ -49,7 +50,7 @@ def recount(path, procs):
     import multiprocessing as mp
     rec = dict(np.load(path))
     S = len(rec["insertions"])
-    if not np.all(rec["status"] >= 0):
+    if not np.all(rec["status"] == 0):
         raise SystemExit("the record is not complete")
     ctx = mp.get_context("spawn")
     order = list(range(S - 1, -1, -1))            # the long solves first
@@ -74,7 +75,7 @@ def main(argv=None):
     import workloads as wl
     from oracle import solver
     w = wl.catmull_rom_workload(lumen_seed=1, tension_seed=2, n_steps=60)
-    m = solver.Model(w.robot, w.lumen)
+    m = solver.Model(w.robot, w.lumen, solver.Options(max_contacts=MAX_CONTACTS))
     S, N = len(w.insertions), w.robot.n_elements + 1
     rec = {"pos": np.zeros((S, N, 3)), "rot": np.zeros((S, N, 3, 3)), "status": np.full(S, -1, np.int32),
            "newton_iters": np.zeros(S, np.int32), "rows": np.zeros(S, np.int32), "seconds": np.zeros(S),
@@ -82,7 +83,8 @@ def main(argv=None):
     start = 0
     if args.resume and os.path.exists(args.out):
         old = np.load(args.out)
-        done = int(np.sum(old["status"] >= 0))
+        bad = np.nonzero(old["status"] != 0)[0]           # resume at the first solve that is not OK
+        done = int(bad[0]) if len(bad) else len(old["status"])
         for k in rec:
             rec[k][:done] = old[k][:done]
         start = done
