@@ -859,7 +859,7 @@ def ours(args, rank, world, local_rank):
     S = len(w.insertions)
     row_bytes = 8 * tens_dev.shape[1]
 
-    def sweep_resident(lat=None):
+    def sweep_resident(lat=None, admm=None):
         h.accfem_reset()
         bad = 0
         its = 0
@@ -872,6 +872,8 @@ def ours(args, rank, world, local_rank):
             if lat is not None:
                 e1.record(stream)
                 lat.append((e0, e1))
+            if admm is not None:
+                admm.append(h.accfem_solve_admm_iterations())
             bad += st != af.OK
             its += it
         return bad, its
@@ -946,9 +948,9 @@ def ours(args, rank, world, local_rank):
         #      timed like `value`, and the contact kernel on the final state of the sweep
         progress("contact solver: ADMM sweep")
         h.accfem_set_contact_solver(af.CONTACT_ADMM)
-        admm_ms, admm_fail, admm_iters = 0.0, 0, 0
+        admm_ms, admm_fail, admm_iters, admm_inner = 0.0, 0, 0, []
         with torch.cuda.stream(stream):
-            sweep_resident()
+            sweep_resident(admm=admm_inner)      # warm-up, and the ADMM iterations of every solve
             flush.fill_(1.0)
             torch.cuda.synchronize()
             t0 = torch.cuda.Event(enable_timing=True)
@@ -960,10 +962,12 @@ def ours(args, rank, world, local_rank):
             admm_ms = t0.elapsed_time(t1)
         admm_ct_us = h.accfem_time_kernel(af.KERNEL_CONTACT, 5)
         h.accfem_set_contact_solver(af.CONTACT_ACTIVE_SET)
-        contact_admm = {"scheme": "OSQP ADMM on the contact-space QP over the working set (W + (sigma + rho) I "
-                                  "inverted once), guess of the free rows polished by the exact active-set method",
+        contact_admm = {"scheme": "OSQP ADMM on the contact-space QP over the working set (FP32 iterations, "
+                                  "W + (sigma + rho) I inverted once), guess of the free rows polished by the "
+                                  "exact FP64 active-set method",
                         "solves_per_s": S / (admm_ms * 1e-3), "ms_per_step": admm_ms,
                         "newton_iters_per_solve": admm_iters / S, "failed_solves": int(admm_fail),
+                        "admm_iters_per_newton_iter": sum(admm_inner) / max(admm_iters, 1),
                         "contact_kernel_us_final_state": admm_ct_us, "active_set_contact_kernel_us": ct_us}
         progress("contact solver: ADMM %.1f solves/s, contact kernel %.0f us (active set %.0f us)"
                  % (contact_admm["solves_per_s"], admm_ct_us, ct_us))

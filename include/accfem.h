@@ -393,6 +393,11 @@ void accfem_batch_destroy(accfem_batch* b);
 accfem_status accfem_solve_stats(const accfem_handle* h, int32_t* rows, int32_t* working_rows, int32_t* active_rows,
                                  int32_t* fp64_fallback);
 
+/* ADMM iterations of the handle's last solve, summed over its Newton iterations (0 unless the
+ * contact solver is ACCFEM_CONTACT_ADMM; the scheme of Sec. III.B, accfem_set_contact_solver).
+ * ACCFEM_E_INVALID_ARG for NULL pointers. */
+accfem_status accfem_solve_admm_iterations(const accfem_handle* h, int32_t* iters);
+
 /* Device memory held by the handle, in bytes. */
 accfem_status accfem_device_bytes(const accfem_handle* h, int64_t* bytes);
 

@@ -76,7 +76,8 @@ EXPORTS = ["accfem_default_options", "accfem_create", "accfem_solve", "accfem_so
            "accfem_batch_create", "accfem_batch_begin", "accfem_batch_advance", "accfem_batch_poll",
            "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream", "accfem_batch_transfer_bytes",
            "accfem_batch_kernel_launches", "accfem_batch_last_error", "accfem_batch_destroy", "accfem_batch_serve",
-           "accfem_device_bytes", "accfem_solve_stats", "accfem_set_precision", "accfem_batch_autotune",
+           "accfem_device_bytes", "accfem_solve_stats", "accfem_solve_admm_iterations", "accfem_set_precision",
+           "accfem_batch_autotune",
            "accfem_batch_tuning", "accfem_set_element_modulus", "accfem_set_frame_mode",
            "accfem_set_contact_solver", "accfem_batch_time_phase", "accfem_set_contact_model"]
 
@@ -141,6 +142,7 @@ def load(path=LIB_PATH):
                                        ctypes.c_int64, ctypes.POINTER(accfem_response), ctypes.POINTER(accfem_result)]
     lib.accfem_device_bytes.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
     lib.accfem_solve_stats.argtypes = [H, _ip, _ip, _ip, _ip]
+    lib.accfem_solve_admm_iterations.argtypes = [H, _ip]
     lib.accfem_set_precision.argtypes = [H, ctypes.c_int32]
     lib.accfem_set_element_modulus.argtypes = [H, _dp, ctypes.c_int32]
     lib.accfem_set_frame_mode.argtypes = [H, ctypes.c_int32]
@@ -156,7 +158,7 @@ def load(path=LIB_PATH):
                  "accfem_transfer_bytes", "accfem_time_kernel", "accfem_detect_contacts_noalloc",
                  "accfem_batch_create", "accfem_batch_begin", "accfem_batch_advance", "accfem_batch_poll",
                  "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream",
-                 "accfem_batch_transfer_bytes", "accfem_batch_serve", "accfem_device_bytes", "accfem_solve_stats", "accfem_set_precision",
+                 "accfem_batch_transfer_bytes", "accfem_batch_serve", "accfem_device_bytes", "accfem_solve_stats", "accfem_solve_admm_iterations", "accfem_set_precision",
                  "accfem_batch_autotune", "accfem_batch_tuning", "accfem_set_element_modulus",
                  "accfem_set_frame_mode", "accfem_set_contact_solver", "accfem_batch_time_phase",
                  "accfem_set_contact_model"):
@@ -343,6 +345,12 @@ class AccFem:
         a, b, c, f = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
         self._lib.accfem_solve_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(f))
         return int(a.value), int(b.value), int(c.value), int(f.value)
+
+    def accfem_solve_admm_iterations(self):
+        """ADMM iterations of the last solve (contact solver CONTACT_ADMM)."""
+        v = ctypes.c_int32(0)
+        self._lib.accfem_solve_admm_iterations(self.h, ctypes.byref(v))
+        return int(v.value)
 
     def accfem_device_bytes(self):
         v = ctypes.c_int64(0)

@@ -311,6 +311,12 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
     accfem_destroy(h);
     return ACCFEM_E_CUDA;
   }
+  // the ADMM contact solver's FP32 inverse in dynamic shared memory (beside the LCP's static arrays)
+  if (!cuda_ok(h, cudaFuncSetAttribute(contact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdmmSmemBytes),
+               "contact kernel shared memory")) {
+    accfem_destroy(h);
+    return ACCFEM_E_CUDA;
+  }
   upload_element_tables();
   Dev& d = h->d;
   const int N = p.N, M = p.M, nfc = h->nf_cap, mc = p.m_cap, wc = p.ws_cap;
@@ -412,7 +418,7 @@ int enqueue_iteration(accfem_handle* h, int nf, cudaStream_t st, cudaGraphCondit
   launch_k(pdl, compact_kernel, dim3(1), dim3(1024), st, p, d); ++n;
   cudaStreamWaitEvent(st, h->join, 0);
   n += enqueue_factor(p, d, nf, st, pdl);
-  launch_k(pdl, contact_kernel, dim3(1), dim3(256), st, p, d); ++n;
+  launch_ks(pdl, contact_kernel, dim3(1), dim3(256), p.lcp_mode == kLcpAdmm ? kAdmmSmemBytes : 0u, st, p, d); ++n;
   launch_k(pdl, step_kernel, grid(PH_STEP), dim3(32, 6), st, p, d); ++n;
   launch_k(pdl, apply_kernel, grid(PH_APPLY), dim3(128), st, p, d); ++n;
   launch_k(pdl, ctl_kernel, dim3(1), dim3(1), st, p, d, cond, h->max_newton, h->stream_mode ? 0 : 1); ++n;
@@ -797,7 +803,7 @@ accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t
       case ACCFEM_KERNEL_ASSEMBLE:
         assemble_rhs_kernel<<<dim3(phase_gx(PH_ASM, nf), phase_gy(PH_ASM)), dim3(32, 6), 0, st>>>(p, d); break;
       case ACCFEM_KERNEL_FACTOR: per_launch = enqueue_factor(p, d, nf, st, h->pdl); break;
-      default: contact_kernel<<<1, 256, 0, st>>>(p, d); break;
+      default: contact_kernel<<<1, 256, p.lcp_mode == kLcpAdmm ? kAdmmSmemBytes : 0u, st>>>(p, d); break;
     }
   };
   launch();
@@ -827,6 +833,12 @@ accfem_status accfem_solve_stats(const accfem_handle* h, int32_t* rows, int32_t*
   if (working_rows) *working_rows = it ? c.mc : 0;
   if (active_rows) *active_rows = it ? c.n_active : 0;
   if (fp64_fallback) *fp64_fallback = c.fp64_tangent;
+  return ACCFEM_OK;
+}
+
+accfem_status accfem_solve_admm_iterations(const accfem_handle* h, int32_t* iters) {
+  if (!h || !iters) return ACCFEM_E_INVALID_ARG;
+  *iters = h->h_ctl->admm_iters;
   return ACCFEM_OK;
 }
 

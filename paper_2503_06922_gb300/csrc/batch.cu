@@ -114,7 +114,7 @@ int enqueue_batch_iteration(accfem_batch* b, cudaStream_t st, cudaGraphCondition
   launch_k(pdl, assemble_rhs_batch, dim3(g[PH_ASM]), dim3(32, 6), st, tab, plan); ++n;
   for (int j = 0; j < b->levels; ++j) { launch_k(pdl, bcr_level_batch, dim3(g[PH_LEV0 + j]), dim3(192), st, tab, plan, j); ++n; }
   for (int j = b->levels - 1; j >= 0; --j) { launch_k(pdl, bcr_bwd_batch, dim3(g[PH_BWD0 + j]), dim3(96), st, tab, plan, j); ++n; }
-  launch_k(pdl, contact_batch, dim3(g[PH_CONTACT]), dim3(256), st, tab, plan); ++n;
+  launch_ks(pdl, contact_batch, dim3(g[PH_CONTACT]), dim3(256), b->has_admm ? kAdmmSmemBytes : 0u, st, tab, plan); ++n;
   launch_k(pdl, step_batch, dim3(g[PH_STEP]), dim3(32, 6), st, tab, plan); ++n;
   launch_k(pdl, apply_batch, dim3(g[PH_APPLY]), dim3(128), st, tab, plan); ++n;
   launch_k(pdl, batch_plan_kernel, dim3(1), dim3(1024), st, tab, plan, b->n, 1, 0, cond, set_cond); ++n;
@@ -256,6 +256,7 @@ accfem_status accfem_batch_create(accfem_handle* const* members, int32_t n_membe
   for (accfem_handle* h : b->members) {
     b->max_nodes = std::max(b->max_nodes, h->p.N);
     b->has_segment = b->has_segment || h->p.contact_model == kContactSegment;
+    b->has_admm = b->has_admm || h->p.lcp_mode == kLcpAdmm;
     max_m = std::max(max_m, h->p.M);
     pack += (size_t)7 * h->p.N + 6 + (size_t)9 * h->p.m_cap;
   }
@@ -266,7 +267,9 @@ accfem_status accfem_batch_create(accfem_handle* const* members, int32_t n_membe
     b->stream_mode = lm && std::strcmp(lm, "stream") == 0;
     b->pdl = pdl_default();
   }
-  bool ok = bok(b, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "cudaStreamCreate") &&
+  bool ok = bok(b, cudaFuncSetAttribute(contact_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdmmSmemBytes),
+                "contact kernel shared memory") &&
+            bok(b, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "cudaStreamCreate") &&
             bok(b, cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking), "cudaStreamCreate") &&
             bok(b, cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "cudaEventCreate") &&
             bok(b, cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming), "cudaEventCreate") &&

@@ -41,6 +41,7 @@ struct accfem_batch {
   static constexpr int kVariants = 12;
   int elem_w = 2;                   // warps per element block of the variant being captured or run
   bool has_segment = false;         // a member uses segment contacts (their collision kernel is launched too)
+  bool has_admm = false;            // a member uses the ADMM contact solver (contact kernel with its shared memory)
   struct Variant {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;

@@ -28,6 +28,10 @@ constexpr int kAccelParts = 10;    // per step block: G (6 upper entries) and b 
 // the 1-D secant over-relaxation of a slow monotone mode.
 constexpr int kAccelIters = 100;
 constexpr int kLcpActiveSet = 0, kLcpAdmm = 1;
+// The ADMM contact solver inverts its FP32 matrix in dynamic shared memory for working sets of up
+// to kAdmmSmemRows rows (larger ones in global memory); its kernels are launched with this many bytes.
+constexpr int kAdmmSmemRows = 192;
+constexpr unsigned kAdmmSmemBytes = kAdmmSmemRows * kAdmmSmemRows * 4u;
 constexpr int kContactNode = 0, kContactSegment = 1;
 // A triangle whose plane projection of the node lies inside it enlarged by this barycentric margin
 // ("over the face") gives a constraint row; the same value is used by the CPU oracle.

@@ -203,99 +203,152 @@ __device__ bool solve_on_set(const Dev& d, LcpShared& S, int m) {
 //   y <- alpha yt + (1 - alpha) y,  zh = alpha yt + (1 - alpha) z,
 //   z <- max(zh + lam / rho, 0),    lam <- lam + rho (zh - z),
 // stopped when |y - z| <= 1e-3 max(|y|, |z|) and |W y + q + lam| <= 1e-3 max(|W y|, |lam|, |q|)
-// (infinity norms, tested every 10 iterations) or after p.admm_iters iterations.  The matrix is
-// inverted once by Gauss-Jordan in global memory; an iteration is one product with the inverse
-// (a warp per row) and the projection.  Its guess of the free rows (z > -lam) starts the exact
-// active-set method, which polishes it.  Returns false on a non-positive pivot.
-__device__ bool admm_guess(const Params& p, const Dev& d, LcpShared& S, int m, size_t ld, double eps_w, double qmax,
-                           int* iters) {
+// (infinity norms, tested every 10 iterations) or after p.admm_iters iterations.  Its only product
+// is the guess of the free rows (z > -lam) that starts the exact FP64 active-set method, which
+// polishes it to the unique solution; so the ADMM runs in FP32, where a warp instruction costs one
+// issue cycle instead of the FP64 pipe's 64: W + (sigma + rho) I (condition number below about 10 m,
+// since rho is a tenth of the largest diagonal entry) is inverted once by Gauss-Jordan in shared
+// memory (global memory past kAdmmSmemRows rows), an iteration is one product with the inverse (tpr
+// threads per row, the rows' updates in parallel) and the projection.  A non-positive FP32 pivot drops the guess: the exact method then
+// starts from the empty set.
+// Partial dot product of column i of the symmetric m x m matrix A (row-major) with x over the
+// entries j = t, t + tpr, ...; four independent FP32 sums, so that the loads run ahead of the FMAs.
+__device__ __forceinline__ float col_dot(const float* A, const float* x, int m, int i, int t, int tpr) {
+  float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+  const float* a = A + i;
+  int j = t;
+  for (; j + 3 * tpr < m; j += 4 * tpr) {
+    s0 = fmaf(a[j * m], x[j], s0);
+    s1 = fmaf(a[(j + tpr) * m], x[j + tpr], s1);
+    s2 = fmaf(a[(j + 2 * tpr) * m], x[j + 2 * tpr], s2);
+    s3 = fmaf(a[(j + 3 * tpr) * m], x[j + 3 * tpr], s3);
+  }
+  for (; j < m; j += tpr) s0 = fmaf(a[j * m], x[j], s0);
+  return (s0 + s1) + (s2 + s3);
+}
+
+__device__ void admm_guess(const Params& p, const Dev& d, LcpShared& S, int m, size_t ld, double eps_w, int* iters) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   for (int i = tid; i < m; i += nt) S.inP[i] = 1;
   rebuild_plist(S, m);
-  ensure_columns(d, S, m, ld, eps_w);           // every column of W over the working set
+  ensure_columns(d, S, m, ld, eps_w);           // every column of W over the working set (FP64)
   double wd = 0.0;
   for (int i = tid; i < m; i += nt) wd = fmax(wd, d.W[(size_t)i * m + i]);
   wd = block_max(wd, S.red);
-  const double sigma = 1.0e-6, alpha = 1.6, eps_rel = 1.0e-3;
-  const double rho = 0.1 * wd, irho = __drcp_rn(rho);
-  double* G = d.gj;                             // (W + (sigma + rho) I)^-1, m x m row-major
-  for (int idx = tid; idx < m * m; idx += nt)
-    G[idx] = d.W[idx] + ((idx / m) == (idx % m) ? sigma + rho : 0.0);
+  const float sigma = 1.0e-6f, alpha = 1.6f, eps_rel = 1.0e-3f;
+  const float rho = (float)(0.1 * wd), irho = 1.0f / rho;
+  // FP32 state in the shared Gauss-Jordan area (unused until the polish)
+  float* fq = reinterpret_cast<float*>(S.gj);
+  float* fy = fq + kLcpSmemRows;
+  float* fz = fy + kLcpSmemRows;
+  float* fl = fz + kLcpSmemRows;
+  float* frv = fl + kLcpSmemRows;
+  float* frow = frv + kLcpSmemRows;             // scaled pivot row
+  float* fcol = frow + kLcpSmemRows;            // pivot column
+  // (W + (sigma + rho) I)^-1, m x m row-major: in the launch's dynamic shared memory when it fits
+  // (kernels launched for the ADMM solver), else in global memory; W in FP32 for the residual test
+  extern __shared__ float s_admm[];
+  unsigned dyn_bytes;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
+  const bool in_smem = (size_t)m * m * sizeof(float) <= dyn_bytes;
+  float* G = in_smem ? s_admm : reinterpret_cast<float*>(d.gj);
+  float* W32 = reinterpret_cast<float*>(d.gj) + (in_smem ? 0 : (size_t)m * m);
+  for (int i = wid; i < m; i += nw)
+    for (int j = lane; j < m; j += 32) {
+      const double w = d.W[(size_t)i * m + j];
+      W32[(size_t)i * m + j] = (float)w;
+      G[(size_t)i * m + j] = (float)(i == j ? w + (1.0e-6 + 0.1 * wd) : w);
+    }
+  for (int i = tid; i < m; i += nt) { fq[i] = (float)S.q[i]; fy[i] = 0.0f; fz[i] = 0.0f; fl[i] = 0.0f; }
+  bool ok = true;
   for (int k = 0; k < m; ++k) {
     __syncthreads();
-    const double akk = G[(size_t)k * m + k];
-    if (!(akk > 0.0)) return false;
-    if (tid < 32) {                             // scaled pivot row (one reciprocal per pivot)
-      const double pk = __drcp_rn(akk);
-      for (int j = tid; j < m; j += 32) S.prow[j] = j == k ? pk : G[(size_t)k * m + j] * pk;
+    const float akk = G[(size_t)k * m + k];
+    if (!(akk > 0.0f)) { ok = false; break; }   // the same value for every thread
+    if (tid < 32) {
+      const float pk = 1.0f / akk;
+      for (int j = tid; j < m; j += 32) frow[j] = j == k ? pk : G[(size_t)k * m + j] * pk;
     }
-    for (int i = tid; i < m; i += nt) S.z[i] = G[(size_t)i * m + k];   // pivot column
+    for (int i = tid; i < m; i += nt) fcol[i] = G[(size_t)i * m + k];
     __syncthreads();
-    const double pk = S.prow[k];
-    for (int idx = tid; idx < m * m; idx += nt) {
-      const int i = idx / m, j = idx % m;
-      if (i == k) G[idx] = S.prow[j];
-      else if (j == k) G[idx] = -S.z[i] * pk;
-      else G[idx] = fma(-S.z[i], S.prow[j], G[idx]);
+    const float pk = frow[k];
+    for (int i = wid; i < m; i += nw) {
+      float* gi = G + (size_t)i * m;
+      const float ci = fcol[i];
+      for (int j = lane; j < m; j += 32) {
+        if (i == k) gi[j] = frow[j];
+        else if (j == k) gi[j] = -ci * pk;
+        else gi[j] = fmaf(-ci, frow[j], gi[j]);
+      }
     }
   }
   __syncthreads();
-  double* lam = S.prow;                         // free again
-  double* rv = S.gj;                            // right-hand side of the linear step
-  for (int i = tid; i < m; i += nt) { S.y[i] = 0.0; S.z[i] = 0.0; lam[i] = 0.0; }
   int it = 0;
-  while (it < p.admm_iters) {
-    ++it;
-    __syncthreads();
-    for (int i = tid; i < m; i += nt) rv[i] = ((sigma * S.y[i] - S.q[i]) + rho * S.z[i]) - lam[i];
-    __syncthreads();
-    for (int i = wid; i < m; i += nw) {          // a warp per row: yt_i = (G rv)_i
-      const double* gi = G + (size_t)i * m;
-      double s = 0.0;
-      for (int j = lane; j < m; j += 32) s = fma(gi[j], rv[j], s);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) {
-        const double zh = alpha * s + (1.0 - alpha) * S.z[i];
-        const double zn = fmax(zh + lam[i] * irho, 0.0);
-        S.y[i] = alpha * s + (1.0 - alpha) * S.y[i];
-        lam[i] = lam[i] + rho * (zh - zn);
-        S.z[i] = zn;
-      }
-    }
-    if (it % 10 == 0) {
+  if (ok) {
+    // tpr threads per row (a power of two dividing 32, with nt / tpr >= m when m is small)
+    int tpr = 1;
+    while (tpr < 32 && (nt / (2 * tpr)) >= m) tpr *= 2;
+    const int g = tid / tpr, t = tid % tpr, ng = nt / tpr;
+    while (it < p.admm_iters) {
+      ++it;
+      for (int i = tid; i < m; i += nt) frv[i] = ((sigma * fy[i] - fq[i]) + rho * fz[i]) - fl[i];
       __syncthreads();
-      double rpri = 0.0, rdua = 0.0, ym = 0.0, wym = 0.0, lm = 0.0;
-      for (int i = wid; i < m; i += nw) {
-        const double* wi = d.W + (size_t)i * m;
-        double s = 0.0;
-        for (int j = lane; j < m; j += 32) s = fma(wi[j], S.y[j], s);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-          rpri = fmax(rpri, fabs(S.y[i] - S.z[i]));
-          rdua = fmax(rdua, fabs(s + S.q[i] + lam[i]));
-          ym = fmax(ym, fmax(fabs(S.y[i]), fabs(S.z[i])));
-          wym = fmax(wym, fabs(s));
-          lm = fmax(lm, fabs(lam[i]));
+      for (int i0 = 0; i0 < m; i0 += ng) {       // the same trip count for every thread
+        const int i = i0 + g;
+        float s = i < m ? col_dot(G, frv, m, i, t, tpr) : 0.0f;   // (G rv)_i, G symmetric
+        for (int o = tpr >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (i < m && t == 0) {
+          const float zh = alpha * s + (1.0f - alpha) * fz[i];
+          const float zn = fmaxf(zh + fl[i] * irho, 0.0f);
+          fy[i] = alpha * s + (1.0f - alpha) * fy[i];
+          fl[i] = fl[i] + rho * (zh - zn);
+          fz[i] = zn;
         }
       }
-      rpri = block_max(rpri, S.red);
-      rdua = block_max(rdua, S.red);
-      ym = block_max(ym, S.red);
-      wym = block_max(wym, S.red);
-      lm = block_max(lm, S.red);
-      if (rpri <= eps_rel * ym && rdua <= eps_rel * fmax(fmax(wym, lm), qmax)) break;
+      __syncthreads();
+      if (it % 10 == 0) {
+        float rpri = 0.0f, rdua = 0.0f, ym = 0.0f, wym = 0.0f, lm = 0.0f, qm = 0.0f;
+        for (int i0 = 0; i0 < m; i0 += ng) {
+          const int i = i0 + g;
+          float s = i < m ? col_dot(W32, fy, m, i, t, tpr) : 0.0f;   // (W y)_i
+          for (int o = tpr >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if (i < m && t == 0) {
+            rpri = fmaxf(rpri, fabsf(fy[i] - fz[i]));
+            rdua = fmaxf(rdua, fabsf(s + fq[i] + fl[i]));
+            ym = fmaxf(ym, fmaxf(fabsf(fy[i]), fabsf(fz[i])));
+            wym = fmaxf(wym, fabsf(s));
+            lm = fmaxf(lm, fabsf(fl[i]));
+            qm = fmaxf(qm, fabsf(fq[i]));
+          }
+        }
+        // the six maxima over the block in one pass
+        float v[6] = {rpri, rdua, ym, wym, lm, qm};
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v[k] = fmaxf(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+        float* sred = reinterpret_cast<float*>(S.red);   // 66 floats
+        if (lane == 0)
+#pragma unroll
+          for (int k = 0; k < 6; ++k) sred[k * 8 + wid] = v[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          float x = 0.0f;
+          for (int w2 = 0; w2 < nw; ++w2) x = fmaxf(x, sred[k * 8 + w2]);
+          v[k] = x;
+        }
+        __syncthreads();
+        if (v[0] <= eps_rel * v[2] && v[1] <= eps_rel * fmaxf(fmaxf(v[3], v[4]), v[5])) break;
+      }
     }
   }
-  __syncthreads();
   for (int i = tid; i < m; i += nt) {
-    S.inP[i] = S.z[i] > -lam[i] ? 1 : 0;
+    S.inP[i] = (ok && fz[i] > -fl[i]) ? 1 : 0;
     S.y[i] = 0.0;
   }
   __syncthreads();
   *iters = it;
-  return true;
 }
 
 // LCP by a primal active-set method for the bound-constrained QP min 1/2 y^T W y + q^T y, y >= 0
@@ -360,7 +413,7 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
   int solves = 0;
   bool done = false, fail = false;
   int admm_it = 0;
-  if (p.lcp_mode == kLcpAdmm) fail = !admm_guess(p, d, S, m, ld, eps_w, qmax, &admm_it);
+  if (p.lcp_mode == kLcpAdmm) admm_guess(p, d, S, m, ld, eps_w, &admm_it);
   // ---- feasible start: drop warm rows until the subproblem solution is positive
   while (!fail) {
     if (solves >= p.max_lcp_iters) break;

@@ -44,22 +44,27 @@ struct accfem_handle {
   cudaStream_t work() const { return user_stream ? user_stream : stream; }
 };
 
-// Launches kernel<<<grid, block, 0, st>>>(args...); with pdl, as a programmatic dependent launch
+// Launches kernel<<<grid, block, smem, st>>>(args...); with pdl, as a programmatic dependent launch
 // (the kernel may start while its predecessor in st finishes; every kernel of the Newton iteration
 // waits for its predecessor in its first instruction, pdl_wait).
 template <typename... K, typename... A>
-inline void launch_k(bool pdl, void (*kernel)(K...), dim3 grid, dim3 block, cudaStream_t st, A... args) {
+inline void launch_ks(bool pdl, void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A... args) {
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cfg.attrs = pdl ? attr : nullptr;
   cfg.numAttrs = pdl ? 1 : 0;
   cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <typename... K, typename... A>
+inline void launch_k(bool pdl, void (*kernel)(K...), dim3 grid, dim3 block, cudaStream_t st, A... args) {
+  launch_ks(pdl, kernel, grid, block, 0, st, args...);
 }
 
 // Programmatic dependent launch of the iteration kernels: off unless ACCFEM_PDL=1.  Measured on the

@@ -85,3 +85,28 @@ def test_contact_solver_arguments(af):
     r1 = h.accfem_solve(w.tensions[1], w.insertions[1])
     assert np.array_equal(r0["node_pos"], r1["node_pos"])
     h.close()
+
+
+def test_admm_member_in_a_batch_equals_alone(af):
+    """A batch mixing an ADMM member (the bent tube, rows from step 5 on) with an active-set member:
+    the ADMM member's results equal its solves alone bit for bit, and it ran ADMM iterations."""
+    w = wl.bent_tube_workload(0, n_steps=10)
+    other = wl.bent_tube_workload(7, n_steps=10)
+    alone = af.AccFem(w.robot, w.lumen)
+    alone.accfem_set_contact_solver(af.CONTACT_ADMM)
+    ref, admm = [], 0
+    for s in range(len(w.insertions)):
+        ref.append(alone.accfem_solve(w.tensions[s], w.insertions[s]))
+        admm += alone.accfem_solve_admm_iterations()
+    assert all(r["status"] == af.OK for r in ref) and admm > 0
+    hs = [af.AccFem(w.robot, w.lumen), af.AccFem(other.robot, other.lumen)]
+    hs[0].accfem_set_contact_solver(af.CONTACT_ADMM)
+    b = af.AccFemBatch(hs)
+    for s in range(len(w.insertions)):
+        st, sts, res = b.accfem_batch_solve([w.tensions[s], other.tensions[s]], [w.insertions[s], other.insertions[s]])
+        assert sts[0] == af.OK and sts[1] == af.OK
+        assert np.array_equal(res[0]["node_pos"], ref[s]["node_pos"]), s
+        assert res[0]["newton_iters"] == ref[s]["newton_iters"], s
+    b.close()
+    for h in hs + [alone]:
+        h.close()
