@@ -90,8 +90,9 @@ def _record(p, t, c, dist, face, n_face, r_o):
             "dist": dist, "face": bool(face)}
 
 
-def detect_node(p, V, T, r_o, activation_gap, nf=None):
-    """Contact constraints of one node against all triangles (Eq. 3, 8-10).
+def detect_node(p, V, T, r_o, activation_gap, nf=None, tri=None):
+    """Contact constraints of one node against all triangles (Eq. 3, 8-10), or against the sorted
+    triangle indices `tri` when given (see ``detect``).
 
     With c_t the closest point of triangle t, d_t = |c_t - p| and g the triangle of smallest
     d_t (lowest index on ties), the pair (node, t) is a constraint when d_t <= r_o + activation
@@ -108,15 +109,19 @@ def detect_node(p, V, T, r_o, activation_gap, nf=None):
         return []
     if nf is None:
         nf = face_normals(V, T)
-    A, B, C = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
+    idx = np.arange(len(T)) if tri is None else np.asarray(tri, dtype=np.int64)
+    if len(idx) == 0:
+        return []
+    A, B, C = V[T[idx, 0]], V[T[idx, 1]], V[T[idx, 2]]
     cp, d, inside, near = closest_points_all(p, A, B, C)
-    g = int(np.argmin(d))
+    g = int(idx[int(np.argmin(d))])
     thr = r_o + activation_gap
     recs = []
-    for t in np.where(d <= thr)[0]:
-        if not (near[t] or t == g):
+    for k in np.where(d <= thr)[0]:
+        t = int(idx[k])
+        if not (near[k] or t == g):
             continue
-        rec = _record(p, t, cp[t], d[t], bool(inside[t]), nf[t], r_o)
+        rec = _record(p, t, cp[k], d[k], bool(inside[k]), nf[t], r_o)
         if any(np.linalg.norm(r["point"] - rec["point"]) <= 1e-12 for r in recs):
             continue
         recs.append(rec)
@@ -124,13 +129,26 @@ def detect_node(p, V, T, r_o, activation_gap, nf=None):
 
 
 def detect(positions, node_ids, V, T, r_o, activation_gap):
-    """Contact constraints of the listed nodes, ordered by (node, triangle)."""
+    """Contact constraints of the listed nodes, ordered by (node, triangle).
+
+    A triangle lies within its bounding sphere (centroid, farthest vertex), so one whose sphere is
+    farther than r_o + activation gap from the node has no point that near and gives no row; and
+    the node's closest triangle g only matters when it is that near, in which case every triangle
+    tied with it is kept too.  Each node is therefore tested against the triangles whose sphere
+    reaches the activation distance (in increasing index order), which gives the rows of the
+    all-triangle test."""
     if len(T) == 0:
         return []
     nf = face_normals(V, T)
+    VT = V[T]
+    cen = VT.mean(axis=1)
+    rad = np.max(np.linalg.norm(VT - cen[:, None, :], axis=2), axis=1)
+    thr = r_o + activation_gap
     out = []
     for i in node_ids:
-        for rec in detect_node(positions[i], V, T, r_o, activation_gap, nf):
+        p = positions[i]
+        tri = np.nonzero(np.linalg.norm(cen - p, axis=1) - rad <= thr * (1.0 + 1e-9) + 1e-12)[0]
+        for rec in detect_node(p, V, T, r_o, activation_gap, nf, tri):
             rec["node"] = int(i)
             out.append(rec)
     return out

@@ -167,6 +167,29 @@ def test_detect_matches_naive_loop_on_small_mesh():
         assert got.shape == exp.shape and np.allclose(got, exp, atol=1e-12)
 
 
+def test_detect_prefilter_equals_all_triangles():
+    """detect tests each node only against the triangles whose bounding sphere reaches the
+    activation distance: the rows (triangle, point, normal, gap) equal the all-triangle test of
+    detect_node, for nodes near, on, beyond and far from the wall of a bent tube."""
+    pts = wl.bent_tube_centerline(straight=0.01, arc_angle=0.5, bend_radius=0.02, ds=0.002)
+    V, T, _, _ = wl.tube_mesh(pts, 0.005, 8)
+    nf = contact.face_normals(V, T)
+    rng = np.random.default_rng(31)
+    x = np.array([pts[rng.integers(len(pts))] + rng.normal(size=3) * s
+                  for s in (0.0005, 0.002, 0.004, 0.006, 0.02) for _ in range(12)])
+    got = contact.detect(x, range(len(x)), V, T, 0.002, 0.001)
+    exp = []
+    for i in range(len(x)):
+        for r in contact.detect_node(x[i], V, T, 0.002, 0.001, nf):
+            r["node"] = i
+            exp.append(r)
+    assert len(exp) > 20 and len(got) == len(exp)
+    for a, b in zip(got, exp):
+        assert (a["node"], a["tri"]) == (b["node"], b["tri"])
+        assert np.array_equal(a["point"], b["point"]) and np.array_equal(a["normal"], b["normal"])
+        assert a["gap"] == b["gap"]
+
+
 def _spd(rng, m):
     X = rng.normal(size=(m, m + 2))
     return X @ X.T / m + 0.05 * np.eye(m)
