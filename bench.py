@@ -168,12 +168,21 @@ class ClockSampler:
 RECORD = os.path.join(ROOT, "oracle", "records", "catmull_rom_600mm_M300_sweep.npz")
 
 
+BLAS_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _restore_env(saved):
+    for v, x in saved.items():
+        if x is None:
+            os.environ.pop(v, None)
+        else:
+            os.environ[v] = x
+
+
 def _oracle_iteration_worker(s, n_iters, record, q):
-    """One worker of the CPU baseline (a fresh interpreter, one BLAS thread): the oracle, as it stands,
-    starts solve s of the sweep from its own recorded state after solve s - 1 and runs n_iters Newton
-    iterations; reports (s, seconds per iteration)."""
-    os.environ["OMP_NUM_THREADS"] = "1"
-    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    """One worker of the CPU baseline (a fresh interpreter, spawned with one BLAS thread): the oracle,
+    as it stands, starts solve s of the sweep from its own recorded state after solve s - 1 and runs
+    n_iters Newton iterations; reports (s, seconds per iteration)."""
     from oracle import solver
     w = workload()
     rec = np.load(record)
@@ -205,13 +214,17 @@ def oracle_sweep_baseline(procs=None, n_iters=1, offset=0.5, picks=None):
     if picks is None:
         picks = sorted({min(S - 1, int(math.floor((k + offset) * S / procs))) for k in range(procs)})
     ps = []
+    # one BLAS thread per worker: a spawned interpreter reads these when it imports numpy
+    saved = {v: os.environ.get(v) for v in BLAS_THREAD_VARS}
     try:
+        os.environ.update({v: "1" for v in BLAS_THREAD_VARS})
         ctx = mp.get_context("spawn")
         q = ctx.Queue()
         t0 = time.perf_counter()
         ps = [ctx.Process(target=_oracle_iteration_worker, args=(s, n_iters, RECORD, q)) for s in picks]
         for p in ps:
             p.start()
+        _restore_env(saved)
         res = {}
         while len(res) < len(ps):
             try:
@@ -222,6 +235,7 @@ def oracle_sweep_baseline(procs=None, n_iters=1, offset=0.5, picks=None):
                     raise RuntimeError("a CPU baseline worker exited without reporting")
         wall = time.perf_counter() - t0
     except Exception:
+        _restore_env(saved)
         for p in ps:
             if p.is_alive():
                 p.terminate()

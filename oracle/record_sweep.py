@@ -20,7 +20,9 @@ import os
 import sys
 import time
 
-import numpy as np
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")      # one BLAS thread, read when numpy loads (workers inherit it)
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
@@ -33,7 +35,6 @@ DEFAULT_OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "records"
 def _recount_one(args):
     """Solve s of the sweep with the oracle as it stands, from the recorded state after solve s - 1."""
     path, s = args
-    os.environ["OMP_NUM_THREADS"] = "1"
     import workloads as wl
     from oracle import solver
     rec = np.load(path)
@@ -68,7 +69,6 @@ def main(argv=None):
     ap.add_argument("--recount", action="store_true")
     ap.add_argument("--procs", type=int, default=max(1, (os.cpu_count() or 2) - 1))
     args = ap.parse_args(argv)
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
     if args.recount:
         recount(args.out, args.procs)
         return 0
