@@ -261,7 +261,7 @@ def reference_arm(args, rank):
         oracle_sweep_baseline(n_iters=1, picks=[0])
     vals, walls, last = [], [], None
     for k in range(args.steps):
-        last = oracle_sweep_baseline(n_iters=1, offset=(k + 0.5) / max(args.steps, 1))
+        last = oracle_sweep_baseline(n_iters=2, offset=(k + 0.5) / max(args.steps, 1))
         if last is None:
             print(json.dumps({"impl": "reference", "unavailable": "the oracle's sweep record is missing or a worker "
                                                                   "did not report"}), flush=True)
@@ -275,7 +275,7 @@ def reference_arm(args, rank):
             "data": "synthetic", "config": config_dict(w),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
                              "sample": "per step, %d worker processes (one per host core, one BLAS thread each) at "
-                                       "once, each timing one Newton iteration of one solve of the 60-solve sweep "
+                                       "once, each timing two Newton iterations of one solve of the 60-solve sweep "
                                        "(stratified over the sweep, shifted per step) from the oracle's recorded "
                                        "state; seconds per iteration interpolated over the sweep and weighted by the "
                                        "oracle's recorded iterations per solve (%.1f on average); numpy FP64 oracle"

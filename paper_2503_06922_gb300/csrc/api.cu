@@ -412,7 +412,7 @@ int enqueue_iteration(accfem_handle* h, int nf, cudaStream_t st, cudaGraphCondit
   const bool pdl = h->pdl;
   launch_k(pdl, element_kernel, grid(PH_ELEM), dim3(32 * kWarpsPerElemBlock), h->side, p, d); ++n;
   cudaEventRecord(h->join, h->side);
-  if (p.contact_model == kContactSegment) launch_k(pdl, collide_segment_kernel, grid(PH_COLL), dim3(128), st, p, d);
+  if (p.contact_model == kContactSegment) launch_k(pdl, collide_segment_kernel, dim3(nf), dim3(128), st, p, d);
   else launch_k(pdl, collide_kernel, grid(PH_COLL), dim3(128), st, p, d);
   ++n;
   launch_k(pdl, compact_kernel, dim3(1), dim3(1024), st, p, d); ++n;
@@ -797,7 +797,7 @@ accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t
       case ACCFEM_KERNEL_ELEMENT:
         element_kernel<<<phase_gx(PH_ELEM, nf), 32 * kWarpsPerElemBlock, 0, st>>>(p, d); break;
       case ACCFEM_KERNEL_COLLIDE:
-        if (p.contact_model == kContactSegment) collide_segment_kernel<<<phase_gx(PH_COLL, nf), 128, 0, st>>>(p, d);
+        if (p.contact_model == kContactSegment) collide_segment_kernel<<<nf, 128, 0, st>>>(p, d);
         else collide_kernel<<<phase_gx(PH_COLL, nf), 128, 0, st>>>(p, d);
         break;
       case ACCFEM_KERNEL_ASSEMBLE:
