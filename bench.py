@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--profile-kernels", action="store_true",
                     help="run the sweep, then launch the factor group and the contact, element and collision kernels "
                          "twice each on its final state (for profilers) and exit")
+    ap.add_argument("--segment", action="store_true", help="with --profile-kernels: segment contacts")
+    ap.add_argument("--admm", action="store_true", help="with --profile-kernels: the ADMM contact solver")
     ap.add_argument("--profile-phases", action="store_true",
                     help="run the batched workload, then its element, collision and assembly phases as bench times "
                          "them (for profilers) and exit")
@@ -781,6 +783,10 @@ def profile_kernels_run(args):
     from paper_2503_06922_gb300 import accfem as af
     w = workload()
     h = af.AccFem(w.robot, w.lumen, max_contacts=MAX_CONTACTS)
+    if args.segment:
+        h.accfem_set_contact_model(af.CONTACT_SEGMENT)
+    if args.admm:
+        h.accfem_set_contact_solver(af.CONTACT_ADMM)
     for s in range(len(w.insertions)):
         h.accfem_solve(w.tensions[s], w.insertions[s])
     for name, k in (("factor group", af.KERNEL_FACTOR), ("contact", af.KERNEL_CONTACT), ("element", af.KERNEL_ELEMENT),
