@@ -378,67 +378,26 @@ __global__ void __launch_bounds__(192) assemble_rhs_batch(const Inst* __restrict
   for_units(tab, plan, PH_ASM, [](const Inst& in, int bx, int by) { assemble_rhs_body(in.p, in.d, bx, by); });
 }
 
-// ------------------------------------------------------------------ 6x6 helpers
-// In-place inverse of the SPD matrix in sA (6x6, row-major) by its 3x3 blocks [A B; B^T C]:
-// A^-1 = adj(A) / det A, T = A^-1 B, the Schur complement S = C - B^T T, S^-1 = adj(S) / det S, and
-// D^-1 = [A^-1 + T S^-1 T^T, -T S^-1; -S^-1 T^T, S^-1].  Two reciprocals on the dependent path
-// instead of the six pivots of a Gauss-Jordan elimination.  The blocks hold the translational and
-// the rotational DOFs, each homogeneous in its units.  Returns false (for all threads) unless the six
-// leading principal minors (a00, the leading 2x2 minor and det of A, then det A times those of S)
-// are positive, i.e. unless D is SPD; begins and ends with a block barrier.
+// ------------------------------------------------------------------ 6x6 helpers (64-thread team)
+// In-place Gauss-Jordan inverse of the SPD matrix in sA (6x6, row-major); threads 0..35 own one
+// entry each.  Returns false (for all threads) when a pivot is not positive.
 __device__ bool team_inverse6(double* sA, int tid, double* s_piv) {
-  __shared__ double sM[9], sT[9], sS[9], sN[9], sY[9], sTL[9];
-  const int r = tid / 3, c = tid % 3;
-  const int r1 = (r + 1) % 3, r2 = (r + 2) % 3, c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-  auto A = [&](int i, int j) { return sA[i * 6 + j]; };
-  auto B = [&](int i, int j) { return sA[i * 6 + 3 + j]; };
-  __syncthreads();
-  if (tid < 9) sM[tid] = fma(A(r1, c1), A(r2, c2), -(A(r1, c2) * A(r2, c1)));   // cofactors of A
-  __syncthreads();
-  if (tid == 0) {
-    const double det = fma(A(0, 0), sM[0], fma(A(0, 1), sM[1], A(0, 2) * sM[2]));
-    s_piv[0] = (A(0, 0) > 0.0 && sM[8] > 0.0 && det > 0.0) ? __drcp_rn(det) : 0.0;
-  }
-  __syncthreads();
-  const double ra = s_piv[0];
-  if (!(ra > 0.0)) return false;
-  double ainv = 0.0;
-  if (tid < 9) ainv = sM[c * 3 + r] * ra;                                        // (A^-1)_rc
-  __syncthreads();
-  if (tid < 9) sM[tid] = ainv;
-  __syncthreads();
-  if (tid < 9) sT[tid] = fma(sM[r * 3], B(0, c), fma(sM[r * 3 + 1], B(1, c), sM[r * 3 + 2] * B(2, c)));   // T = A^-1 B
-  __syncthreads();
-  if (tid < 9)                                                                    // S = C - B^T T
-    sS[tid] = fma(-B(0, r), sT[c], fma(-B(1, r), sT[3 + c], fma(-B(2, r), sT[6 + c], sA[(3 + r) * 6 + 3 + c])));
-  __syncthreads();
-  if (tid < 9) sN[tid] = fma(sS[r1 * 3 + c1], sS[r2 * 3 + c2], -(sS[r1 * 3 + c2] * sS[r2 * 3 + c1]));   // cofactors of S
-  __syncthreads();
-  if (tid == 0) {
-    const double det = fma(sS[0], sN[0], fma(sS[1], sN[1], sS[2] * sN[2]));
-    s_piv[0] = (sS[0] > 0.0 && sN[8] > 0.0 && det > 0.0) ? __drcp_rn(det) : 0.0;
-  }
-  __syncthreads();
-  const double rs = s_piv[0];
-  if (!(rs > 0.0)) return false;
-  double sinv = 0.0;
-  if (tid < 9) sinv = sN[c * 3 + r] * rs;                                        // (S^-1)_rc
-  __syncthreads();
-  if (tid < 9) sN[tid] = sinv;
-  __syncthreads();
-  if (tid < 9) sY[tid] = -fma(sT[r * 3], sN[c], fma(sT[r * 3 + 1], sN[3 + c], sT[r * 3 + 2] * sN[6 + c]));   // -T S^-1
-  __syncthreads();
-  if (tid < 9)                                                                    // A^-1 + T S^-1 T^T
-    sTL[tid] = fma(-sY[r * 3], sT[c * 3], fma(-sY[r * 3 + 1], sT[c * 3 + 1], fma(-sY[r * 3 + 2], sT[c * 3 + 2], sM[tid])));
-  __syncthreads();
-  if (tid < 36) {
-    const int i = tid / 6, j = tid % 6;
-    double v;
-    if (i < 3 && j < 3) v = sTL[i * 3 + j];
-    else if (i < 3) v = sY[i * 3 + (j - 3)];
-    else if (j < 3) v = sY[j * 3 + (i - 3)];
-    else v = sN[(i - 3) * 3 + (j - 3)];
-    sA[tid] = v;
+  const int r = tid / 6, c = tid % 6;
+  for (int k = 0; k < 6; ++k) {
+    __syncthreads();
+    double akk = sA[k * 6 + k];
+    if (!(akk > 0.0)) return false;
+    double pk = __drcp_rn(akk);             // correctly rounded, as 1.0 / akk
+    double v = 0.0;
+    if (tid < 36) {
+      double aij = sA[r * 6 + c], aik = sA[r * 6 + k], akj = sA[k * 6 + c];
+      if (r == k && c == k) v = pk;
+      else if (r == k) v = akj * pk;
+      else if (c == k) v = -aik * pk;
+      else v = aij - aik * akj * pk;
+    }
+    __syncthreads();
+    if (tid < 36) sA[r * 6 + c] = v;
   }
   __syncthreads();
   return true;
