@@ -77,3 +77,25 @@ def test_full_size_sweep_samples_are_oracle_equilibria(af):
         ftol = max(1e-6 * fmax, 1e-10 * max(1.0, float(np.sum(w.tensions[s]))) / l0)
         for n in set(fo) | set(fg):
             assert np.linalg.norm(fo.get(n, 0.0) - fg.get(n, 0.0)) <= ftol, (s, n)
+
+
+def test_full_size_sweep_follows_the_oracles_own_sweep(af):
+    """The GPU sweep against the oracle's own, independent sweep of the same 60 solves (its record,
+    written by oracle/record_sweep.py: each oracle solve started from the oracle's previous
+    equilibrium): every solve converges, and the nodal positions of every solve agree with the
+    oracle's to 1e-9 relative."""
+    import os
+    rec = np.load(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                               "oracle", "records", "catmull_rom_600mm_M300_sweep.npz"))
+    w = wl.catmull_rom_workload(lumen_seed=1, tension_seed=2, n_steps=60)
+    assert np.array_equal(rec["insertions"], np.asarray(w.insertions)) and np.all(rec["status"] == 0)
+    gpu = af.AccFem(w.robot, w.lumen, max_contacts=4096)
+    worst = (0.0, -1)
+    for s in range(len(w.insertions)):
+        g = gpu.accfem_solve(w.tensions[s], w.insertions[s])
+        assert g["status"] == af.OK, (s, g["error"])
+        err = np.abs(g["node_pos"] - rec["pos"][s]).max() / np.abs(rec["pos"][s]).max()
+        worst = max(worst, (err, s))
+    gpu.close()
+    print("worst relative position error against the oracle's sweep: %.2e (solve %d)" % worst)
+    assert worst[0] <= 1e-9, worst
