@@ -159,8 +159,9 @@ __device__ void rebuild_plist(LcpShared& S, int m) {
   __syncthreads();
 }
 
-// Solves W_PP z_P = -q_P for the active list (Gauss-Jordan over the CTA, FP64; shared memory for up
-// to kLcpSmemGJ rows) and writes z (0 outside P).  Returns false on a non-positive pivot.
+// Solves W_PP z_P = -q_P for the active list (Gauss-Jordan with 2x2 block pivots over the CTA, FP64;
+// shared memory for up to kLcpSmemGJ rows) and writes z (0 outside P).  Returns false on a
+// non-positive pivot.
 __device__ bool solve_on_set(const Dev& d, LcpShared& S, int m) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int np = S.np;
@@ -171,21 +172,52 @@ __device__ bool solve_on_set(const Dev& d, LcpShared& S, int m) {
     int i = S.plist[r];
     G[idx] = (c < np) ? d.W[(size_t)i * m + S.plist[c]] : -S.q[i];
   }
-  for (int k = 0; k < np; ++k) {
+  // 2x2 block pivots (rows k, k + 1): the block's inverse from its determinant (one reciprocal for
+  // two rows), both pivot rows scaled by it, every other row updated by both at once; a last single
+  // row takes a scalar pivot.  The block is SPD exactly when its two scalar pivots (a, det / a) are
+  // positive.
+  double* q1 = S.z;                                // second scaled pivot row (S.z is written at the end)
+  const int step = ldg <= kLcpSmemRows ? 2 : 1;    // (S.z holds kLcpSmemRows entries)
+  for (int k = 0; k < np; k += step) {
     __syncthreads();
-    const double akk = G[(size_t)k * ldg + k];
-    if (!(akk > 0.0)) return false;
-    // warp 0 scales the pivot row (one reciprocal per pivot, not one per warp: a warp's FP64
-    // instructions occupy its SMSP's FP64 pipe whatever its lane mask)
+    if (k + 1 == np || step == 1) {
+      const double akk = G[(size_t)k * ldg + k];
+      if (!(akk > 0.0)) return false;
+      if (tid < 32) {
+        const double rp = __drcp_rn(akk);
+        for (int c = k + 1 + tid; c < ldg; c += 32) S.prow[c] = G[(size_t)k * ldg + c] * rp;
+      }
+      __syncthreads();
+      const int wdt = ldg - k - 1;
+      for (int idx = tid; idx < np * wdt; idx += nt) {
+        int r = idx / wdt, c = k + 1 + idx % wdt;
+        G[(size_t)r * ldg + c] = r == k ? S.prow[c] : fma(-G[(size_t)r * ldg + k], S.prow[c], G[(size_t)r * ldg + c]);
+      }
+      continue;
+    }
+    const double a = G[(size_t)k * ldg + k], b = G[(size_t)k * ldg + k + 1];
+    const double b2 = G[(size_t)(k + 1) * ldg + k], cc = G[(size_t)(k + 1) * ldg + k + 1];
+    const double det = fma(a, cc, -(b * b2));
+    if (!(a > 0.0) || !(det > 0.0)) return false;
+    // warp 0 forms the block inverse and both scaled pivot rows (one reciprocal per block)
     if (tid < 32) {
-      const double rp = __drcp_rn(akk);
-      for (int c = k + 1 + tid; c < ldg; c += 32) S.prow[c] = G[(size_t)k * ldg + c] * rp;
+      const double rd = __drcp_rn(det);
+      const double i00 = cc * rd, i01 = -b * rd, i10 = -b2 * rd, i11 = a * rd;
+      for (int c = k + 2 + tid; c < ldg; c += 32) {
+        const double g0 = G[(size_t)k * ldg + c], g1 = G[(size_t)(k + 1) * ldg + c];
+        S.prow[c] = fma(i00, g0, i01 * g1);
+        q1[c] = fma(i10, g0, i11 * g1);
+      }
     }
     __syncthreads();
-    const int wdt = ldg - k - 1;
+    const int wdt = ldg - k - 2;
     for (int idx = tid; idx < np * wdt; idx += nt) {
-      int r = idx / wdt, c = k + 1 + idx % wdt;
-      G[(size_t)r * ldg + c] = r == k ? S.prow[c] : fma(-G[(size_t)r * ldg + k], S.prow[c], G[(size_t)r * ldg + c]);
+      int r = idx / wdt, c = k + 2 + idx % wdt;
+      double v;
+      if (r == k) v = S.prow[c];
+      else if (r == k + 1) v = q1[c];
+      else v = fma(-G[(size_t)r * ldg + k], S.prow[c], fma(-G[(size_t)r * ldg + k + 1], q1[c], G[(size_t)r * ldg + c]));
+      G[(size_t)r * ldg + c] = v;
     }
   }
   __syncthreads();
