@@ -382,19 +382,34 @@ __global__ void __launch_bounds__(192) assemble_rhs_batch(const Inst* __restrict
 // In-place Gauss-Jordan inverse of the SPD matrix in sA (6x6, row-major); threads 0..35 own one
 // entry each.  Returns false (for all threads) when a pivot is not positive.
 __device__ bool team_inverse6(double* sA, int tid, double* s_piv) {
+  // Gauss-Jordan with 2x2 block pivots (DOFs k, k + 1 for k = 0, 2, 4): the block's inverse from its
+  // determinant, one reciprocal for two DOFs; the block is SPD exactly when its two scalar pivots (a,
+  // det / a) are positive.  Only the 36 entry threads compute (a warp's FP64 instructions hold its
+  // SMSP's FP64 pipe whatever its lane mask, and the other warps share SMSPs with these two).
   const int r = tid / 6, c = tid % 6;
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < 6; k += 2) {
     __syncthreads();
-    double akk = sA[k * 6 + k];
-    if (!(akk > 0.0)) return false;
-    double pk = __drcp_rn(akk);             // correctly rounded, as 1.0 / akk
+    const double a = sA[k * 6 + k], b = sA[k * 6 + k + 1], b2 = sA[(k + 1) * 6 + k], cc = sA[(k + 1) * 6 + k + 1];
+    const double det = fma(a, cc, -(b * b2));
+    if (!(a > 0.0) || !(det > 0.0)) return false;
     double v = 0.0;
     if (tid < 36) {
-      double aij = sA[r * 6 + c], aik = sA[r * 6 + k], akj = sA[k * 6 + c];
-      if (r == k && c == k) v = pk;
-      else if (r == k) v = akj * pk;
-      else if (c == k) v = -aik * pk;
-      else v = aij - aik * akj * pk;
+      const double rd = __drcp_rn(det);
+      const double i00 = cc * rd, i01 = -b * rd, i10 = -b2 * rd, i11 = a * rd;
+      const bool pr = r == k || r == k + 1, pc = c == k || c == k + 1;
+      if (pr && pc) {
+        v = r == k ? (c == k ? i00 : i01) : (c == k ? i10 : i11);
+      } else if (pr) {                               // pivot rows: Binv [a_kc; a_k+1,c]
+        const double e0 = r == k ? i00 : i10, e1 = r == k ? i01 : i11;
+        v = fma(e0, sA[k * 6 + c], e1 * sA[(k + 1) * 6 + c]);
+      } else if (pc) {                               // pivot columns: -[a_rk, a_r,k+1] Binv[:, c]
+        const double e0 = c == k ? i00 : i01, e1 = c == k ? i10 : i11;
+        v = -fma(sA[r * 6 + k], e0, sA[r * 6 + k + 1] * e1);
+      } else {                                       // a_rc - [a_rk, a_r,k+1] Binv [a_kc; a_k+1,c]
+        const double p0 = fma(i00, sA[k * 6 + c], i01 * sA[(k + 1) * 6 + c]);
+        const double p1 = fma(i10, sA[k * 6 + c], i11 * sA[(k + 1) * 6 + c]);
+        v = fma(-sA[r * 6 + k], p0, fma(-sA[r * 6 + k + 1], p1, sA[r * 6 + c]));
+      }
     }
     __syncthreads();
     if (tid < 36) sA[r * 6 + c] = v;
@@ -559,7 +574,7 @@ __global__ void __launch_bounds__(192) bcr_level_kernel(Params p, Dev d, int s) 
 }
 
 // level j (stride 2^j) of every iterating instance
-__global__ void __launch_bounds__(192) bcr_level_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j) {
+__global__ void __launch_bounds__(192, 3) bcr_level_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j) {
   for_units(tab, plan, PH_LEV0 + j, [j](const Inst& in, int bx, int by) { bcr_level_body(in.p, in.d, bx, by, 1 << j); });
 }
 
