@@ -351,11 +351,11 @@ MODES = (("fp64", 0), ("mixed", 1))      # name, accfem precision mode
 
 
 def _one_launch_vs_sequential(af, b, hs, ws, seed=5):
-    """BASELINE's batching comparison: one lock-step batched solve of every member (each a tension
-    increment U[-0.2, 0.2] N per cable from its resident state, insertion unchanged) against the same
-    solves issued one after another on the single-instance path (accfem_solve from the same start
-    pose); both through the public API with host buffers.  Returns times and the largest tip
-    difference between the two (the same kernels, so it should be zero)."""
+    """The batching comparison of the 256-instance workload: one lock-step batched solve of every
+    member (each a tension increment U[-0.2, 0.2] N per cable from its resident state, insertion
+    unchanged) against the same solves issued one after another on the single-instance path
+    (accfem_solve from the same start pose); both through the public API with host buffers.  Returns
+    the times and the largest tip difference between the two."""
     rng = np.random.default_rng(seed)
     n = len(hs)
     saved = [h.accfem_get_state() for h in hs]
