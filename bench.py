@@ -672,13 +672,14 @@ def tree_precision_run(af):
     return out
 
 
-def frames_run(af, node_counts=(100, 200, 300, 400), frames_per_step=5):
+def frames_run(af, node_counts=(100, 200, 300, 400), frames_per_step=5, solver=None):
     """The paper's per-timestep experiment (Sec. IV.A: computation time per timestep against the
     number of contacts, robots of 100, 200, 300 and 400 nodes) in frame mode, one linearisation of
     Eq. 20-23 per frame: the 600 mm robot with 99..399 elements in the benchmark's Catmull-Rom tube,
     insertion swept 0 -> 600 mm in 60 steps of frames_per_step frames each.  Per frame: the device
     time of one accfem_solve_resident call (CUDA events on the library's stream; graph launch,
-    iteration and control read-back) and the rows active in its contact solve."""
+    iteration and control read-back) and the rows active in its contact solve.  solver: the contact
+    solver (default the active-set method); with the ADMM solvers, the ADMM iterations per frame."""
     import torch
     from dataclasses import replace
     w0 = workload()
@@ -691,6 +692,8 @@ def frames_run(af, node_counts=(100, 200, 300, 400), frames_per_step=5):
         rob = replace(w0.robot, n_elements=nn - 1)
         h = af.AccFem(rob, w0.lumen, max_contacts=512)
         h.accfem_set_frame_mode(1)
+        if solver is not None:
+            h.accfem_set_contact_solver(solver)
         stream = torch.cuda.Stream()
         h.accfem_set_stream(stream.cuda_stream)
         recs = []
@@ -707,7 +710,7 @@ def frames_run(af, node_counts=(100, 200, 300, 400), frames_per_step=5):
                         e1.synchronize()
                         if rep == 1:
                             rows, working, active, _ = h.accfem_solve_stats()
-                            recs.append((e0.elapsed_time(e1), active, rows, st))
+                            recs.append((e0.elapsed_time(e1), active, rows, st, h.accfem_solve_admm_iterations()))
         h.close()
         ms = np.array([r[0] for r in recs])
         act = np.array([r[1] for r in recs])
@@ -715,8 +718,9 @@ def frames_run(af, node_counts=(100, 200, 300, 400), frames_per_step=5):
         for lo, hi in bins:
             sel = (act >= lo) & (act <= hi)
             if sel.any():
-                by["%d-%d" % (lo, hi) if hi < 10 ** 6 else "%d+" % lo] = {"frames": int(sel.sum()),
-                                                                          "ms_mean": float(ms[sel].mean())}
+                by["%d-%d" % (lo, hi) if hi < 10 ** 6 else "%d+" % lo] = {
+                    "frames": int(sel.sum()), "ms_mean": float(ms[sel].mean()),
+                    "admm_iters_mean": float(np.mean([recs[i][4] for i in np.nonzero(sel)[0]]))}
         out[str(nn)] = {"frames": len(recs), "ms_per_frame": float(ms.mean()), "ms_p50": float(np.percentile(ms, 50)),
                         "ms_p99": float(np.percentile(ms, 99)), "frames_per_s": float(1e3 / ms.mean()),
                         "max_active": int(act.max()), "max_rows": int(max(r[2] for r in recs)),
@@ -1077,6 +1081,13 @@ def ours(args, rank, world, local_rank):
         extra["served"] = served_run(af, requests=args.serve_requests)
         extra["precision_tree"] = tree_precision_run(af)
         extra["frames"] = frames_run(af)
+        # the paper's own solver of Eq. 23 (OSQP on the primal QP), frame by frame: its time per frame
+        # against the number of contacts (the claim of Sec. IV.A)
+        fp = frames_run(af, node_counts=(100,), frames_per_step=1, solver=af.CONTACT_PRIMAL_ADMM)
+        fp["solver"] = ("OSQP's ADMM on the primal QP of Eq. 23 (K + sigma I + rho A^T A factored per frame by a "
+                        "one-CTA block cyclic reduction, one 1-column solve per ADMM iteration), guess polished "
+                        "exactly by the active-set method")
+        extra["frames_primal_admm"] = fp
     if rank == 0:
         cpu = oracle_sweep_baseline(n_iters=2)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -200,10 +200,18 @@ accfem_status accfem_set_frame_mode(accfem_handle* h, int32_t iters_per_frame);
  * in the previous iteration.  ACCFEM_CONTACT_ADMM: the paper's scheme (Sec. III.B: the MLCP as a QP
  * solved by OSQP): OSQP's ADMM iteration (sigma 1e-6, rho 0.1 max diag W, relaxation 1.6, relative
  * tolerance 1e-3, at most 4000 iterations) on the whole working-set W, factored once, whose guess
- * of the free rows the active-set method then polishes to the exact solution.  Call between
- * solves; a batch takes each member's solver when the batch is created.  E_INVALID_ARG otherwise. */
+ * of the free rows the active-set method then polishes to the exact solution.
+ * ACCFEM_CONTACT_PRIMAL_ADMM: OSQP's ADMM on the primal QP of Eq. 23 as the paper states it (min
+ * 1/2 dx^T K dx + g^T dx subject to A dx <= b over every constraint row; sigma 1e-6, rho 0.1 max diag
+ * K, relaxation 1.6, tolerance 1e-3, at most 4000 iterations): K + sigma I + rho A^T A keeps K's
+ * block-tridiagonal form and is factored once per Newton iteration, each ADMM iteration is one
+ * solve with that factor, and the rows whose multiplier is positive start the active-set method,
+ * which gives the exact solution; node contacts only (E_INVALID_ARG with the segment model), and not
+ * in batches (accfem_batch_create refuses such members).  Call between solves; a batch takes each
+ * member's solver when the batch is created.  E_INVALID_ARG otherwise. */
 #define ACCFEM_CONTACT_ACTIVE_SET 0
 #define ACCFEM_CONTACT_ADMM 1
+#define ACCFEM_CONTACT_PRIMAL_ADMM 2
 accfem_status accfem_set_contact_solver(accfem_handle* h, int32_t solver);
 
 /* Contact model (Eq. 3-7).  ACCFEM_CONTACT_NODE (the default): a contact point sits at a node (xi = 0 of
@@ -394,7 +402,8 @@ accfem_status accfem_solve_stats(const accfem_handle* h, int32_t* rows, int32_t*
                                  int32_t* fp64_fallback);
 
 /* ADMM iterations of the handle's last solve, summed over its Newton iterations (0 unless the
- * contact solver is ACCFEM_CONTACT_ADMM; the scheme of Sec. III.B, accfem_set_contact_solver).
+ * contact solver is ACCFEM_CONTACT_ADMM or ACCFEM_CONTACT_PRIMAL_ADMM; the scheme of Sec. III.B,
+ * accfem_set_contact_solver).
  * ACCFEM_E_INVALID_ARG for NULL pointers. */
 accfem_status accfem_solve_admm_iterations(const accfem_handle* h, int32_t* iters);
 

@@ -140,7 +140,7 @@ def admm_polish(W, q, **admm_args):
 
 
 def primal_admm(solve_M, K_mul, g, A, b, rho, sigma=1.0e-6, alpha=1.6, eps_rel=1.0e-3, max_iter=4000,
-                check_every=10):
+                check_every=10, refactor=None):
     """OSQP's ADMM (Stellato et al. 2020) on the primal QP of Eq. 23,
         min 1/2 dx^T K dx + g^T dx   s.t.  A dx <= b,
     i.e. OSQP's problem with P = K, l = -inf, u = b.  solve_M applies (K + sigma I + rho A^T A)^-1
@@ -149,7 +149,10 @@ def primal_admm(solve_M, K_mul, g, A, b, rho, sigma=1.0e-6, alpha=1.6, eps_rel=1
         x <- alpha xt + (1 - alpha) x,  zh = alpha zt + (1 - alpha) z
         z <- min(zh + lam / rho, b),    lam <- lam + rho (zh - z)
     stopped when |A x - z| <= eps_rel max(|A x|, |z|) and |K x + g + A^T lam| <= eps_rel max(|K x|,
-    |A^T lam|, |g|) (infinity norms, tested every check_every iterations).  Returns (x, z, lam, iters)."""
+    |A^T lam|, |g|) (infinity norms, tested every check_every iterations).  With refactor (rho ->
+    a new solve_M), rho adapts as in OSQP (the same paper, Sec. 5.2): at each test, with the two
+    residuals relative to their scales, rho_new = rho sqrt(primal / dual), taken (and the matrix
+    refactored) when it differs from rho by more than a factor 5.  Returns (x, z, lam, iters)."""
     n, m = len(g), len(b)
     x = np.zeros(n)
     z = np.zeros(m)
@@ -165,9 +168,15 @@ def primal_admm(solve_M, K_mul, g, A, b, rho, sigma=1.0e-6, alpha=1.6, eps_rel=1
         lam = lam + rho * (zh - z)
         if it % check_every == 0:
             Ax, Kx, Atl = A @ x, K_mul(x), A.T @ lam
-            if (np.abs(Ax - z).max() <= eps_rel * max(np.abs(Ax).max(), np.abs(z).max()) and
-                    np.abs(Kx + g + Atl).max() <= eps_rel * max(np.abs(Kx).max(), np.abs(Atl).max(), np.abs(g).max())):
+            rp, sp = np.abs(Ax - z).max(), max(np.abs(Ax).max(), np.abs(z).max())
+            rd, sd = np.abs(Kx + g + Atl).max(), max(np.abs(Kx).max(), np.abs(Atl).max(), np.abs(g).max())
+            if rp <= eps_rel * sp and rd <= eps_rel * sd:
                 break
+            if refactor is not None and rp > 0.0 and rd > 0.0 and sp > 0.0 and sd > 0.0:
+                rho_new = rho * np.sqrt((rp / sp) / (rd / sd))
+                if rho_new > 5.0 * rho or rho_new < rho / 5.0:
+                    rho = rho_new
+                    solve_M = refactor(rho)
     return x, z, lam, it
 
 

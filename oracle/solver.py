@@ -296,18 +296,20 @@ class Model:
                     # the translations of one node, or of the two nodes of an element)
                     u = ab.shape[0] - 1
                     rho_admm = 0.1 * float(np.max(ab[u]))
-                    mb = ab.copy()
-                    mb[u] += 1.0e-6
-                    for i in range(m):
-                        nz = np.nonzero(A[i])[0]
-                        for p_ in nz:
-                            for q_ in nz:
-                                if p_ <= q_:
-                                    mb[u + p_ - q_, q_] += rho_admm * A[i, p_] * A[i, q_]
-                    cm = sla.cholesky_banded(mb, lower=False)
+
+                    def factor(rho_):
+                        mb = ab.copy()
+                        mb[u] += 1.0e-6
+                        for i in range(m):
+                            nz = np.nonzero(A[i])[0]
+                            for p_ in nz:
+                                for q_ in nz:
+                                    if p_ <= q_:
+                                        mb[u + p_ - q_, q_] += rho_ * A[i, p_] * A[i, q_]
+                        cm = sla.cholesky_banded(mb, lower=False)
+                        return lambda r_: sla.cho_solve_banded((cm, False), r_)
                     y, piv, _ = lcp.primal_admm_polish(
-                        lambda r_: sla.cho_solve_banded((cm, False), r_), lambda v: _band_mul(ab, v),
-                        g, A, b, rho_admm, W, q)
+                        factor(rho_admm), lambda v: _band_mul(ab, v), g, A, b, rho_admm, W, q, refactor=factor)
                 else:
                     y, w, piv = lcp.qp_nnls(W, q)
                 piv_total += piv

@@ -82,7 +82,7 @@ EXPORTS = ["accfem_default_options", "accfem_create", "accfem_solve", "accfem_so
            "accfem_set_contact_solver", "accfem_batch_time_phase", "accfem_set_contact_model"]
 
 PRECISION_FP64, PRECISION_MIXED = 0, 1
-CONTACT_ACTIVE_SET, CONTACT_ADMM = 0, 1
+CONTACT_ACTIVE_SET, CONTACT_ADMM, CONTACT_PRIMAL_ADMM = 0, 1, 2
 CONTACT_NODE, CONTACT_SEGMENT = 0, 1
 
 MAX_CABLES = 8

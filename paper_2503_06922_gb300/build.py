@@ -11,7 +11,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libaccfem.so")
-UNITS = ["element", "collide", "segment", "btd", "contact", "update", "api", "batch", "serve", "noalloc"]
+UNITS = ["element", "collide", "segment", "btd", "contact", "primal", "update", "api", "batch", "serve", "noalloc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no implicit contraction of a * b + c into a fused multiply-add; every FMA of the
 # kernels is an explicit fma() in the source, so the rounding of each expression is fixed by the

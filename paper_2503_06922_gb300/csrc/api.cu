@@ -26,6 +26,7 @@ __global__ void start_kernel(Params p, Dev d, int mode, double delta, double del
 __global__ void ctl_kernel(Params p, Dev d, cudaGraphConditionalHandle h, int max_iter, int set_cond);
 __global__ void assemble_rhs_kernel(Params p, Dev d);
 __global__ void bcr_level_kernel(Params p, Dev d, int s);
+__global__ void primal_admm_kernel(Params p, Dev d);
 void upload_element_tables();
 }  // namespace accfem
 
@@ -348,6 +349,10 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
        dalloc(h, &d.rev_part, (size_t)nfc / 32 + 2) && dalloc(h, &d.aa_part, ((size_t)nfc / 32 + 2) * kAccelParts) &&
        dalloc(h, &d.aa_f, (size_t)kAccelSlots * nfc * 6) && dalloc(h, &d.aa_d, (size_t)kAccelSlots * nfc * 6) && dalloc(h, &d.W, (size_t)wc * wc) &&
        dalloc(h, &d.y, mc) && dalloc(h, &d.gj, (size_t)wc * (wc + 2)) && dalloc(h, &d.plist, wc) &&
+       dalloc(h, &d.pa_D, (size_t)nfc * 36) && dalloc(h, &d.pa_E, (size_t)nfc * 36) && dalloc(h, &d.pa_P, (size_t)nfc * 36) &&
+       dalloc(h, &d.pa_EL, (size_t)nfc * 36) && dalloc(h, &d.pa_ER, (size_t)nfc * 36) && dalloc(h, &d.pa_x, (size_t)nfc * 6) &&
+       dalloc(h, &d.pa_xt, (size_t)nfc * 6) && dalloc(h, &d.pa_w, (size_t)nfc * 6) && dalloc(h, &d.pa_v, (size_t)nfc * 6) &&
+       dalloc(h, &d.pa_z, mc) && dalloc(h, &d.pa_lam, mc) && dalloc(h, &d.pa_guess, mc) &&
        dalloc(h, &d.ctl, 1);
   if (!ok) {
     accfem_destroy(h);
@@ -392,6 +397,8 @@ int enqueue_factor(const Params& p, const Dev& d, int nf, cudaStream_t st, bool 
   int n = 0;
   auto grid = [nf](int ph) { return dim3(phase_gx(ph, nf), phase_gy(ph)); };
   launch_k(pdl, assemble_rhs_kernel, grid(PH_ASM), dim3(32, 6), st, p, d); ++n;
+  // the paper's OSQP on the primal QP: its guess of the active rows, before the reduction overwrites D
+  if (p.lcp_mode == kLcpPrimalAdmm) { launch_k(pdl, primal_admm_kernel, dim3(1), dim3(1024), st, p, d); ++n; }
   int levels = 0;
   while (levels < kMaxLevels && phase_gx(PH_LEV0 + levels, nf) > 0) ++levels;
   for (int j = 0; j < levels; ++j) { launch_k(pdl, bcr_level_kernel, grid(PH_LEV0 + j), dim3(192), st, p, d, 1 << j); ++n; }
@@ -695,7 +702,10 @@ accfem_status accfem_set_precision(accfem_handle* h, int32_t mode) {
 }
 
 accfem_status accfem_set_contact_solver(accfem_handle* h, int32_t solver) {
-  if (!h || (solver != ACCFEM_CONTACT_ACTIVE_SET && solver != ACCFEM_CONTACT_ADMM)) return ACCFEM_E_INVALID_ARG;
+  if (!h || (solver != ACCFEM_CONTACT_ACTIVE_SET && solver != ACCFEM_CONTACT_ADMM && solver != ACCFEM_CONTACT_PRIMAL_ADMM))
+    return ACCFEM_E_INVALID_ARG;
+  if (solver == ACCFEM_CONTACT_PRIMAL_ADMM && h->p.contact_model != kContactNode)
+    return fail(h, ACCFEM_E_INVALID_ARG, "the primal ADMM takes node contacts only");
   if (h->p.lcp_mode == solver) return ACCFEM_OK;
   if (h->stream) cudaStreamSynchronize(h->work());
   for (auto& kv : h->graphs) {     // the Newton graphs captured the handle's constants
@@ -703,12 +713,14 @@ accfem_status accfem_set_contact_solver(accfem_handle* h, int32_t solver) {
     if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
   }
   h->graphs.clear();
-  h->p.lcp_mode = solver == ACCFEM_CONTACT_ADMM ? kLcpAdmm : kLcpActiveSet;
+  h->p.lcp_mode = solver == ACCFEM_CONTACT_ADMM ? kLcpAdmm : solver == ACCFEM_CONTACT_PRIMAL_ADMM ? kLcpPrimalAdmm : kLcpActiveSet;
   return ACCFEM_OK;
 }
 
 accfem_status accfem_set_contact_model(accfem_handle* h, int32_t model) {
   if (!h || (model != ACCFEM_CONTACT_NODE && model != ACCFEM_CONTACT_SEGMENT)) return ACCFEM_E_INVALID_ARG;
+  if (model == ACCFEM_CONTACT_SEGMENT && h->p.lcp_mode == kLcpPrimalAdmm)
+    return fail(h, ACCFEM_E_INVALID_ARG, "the primal ADMM takes node contacts only");
   if (h->p.contact_model == model) return ACCFEM_OK;
   if (h->stream) cudaStreamSynchronize(h->work());
   for (auto& kv : h->graphs) {     // the Newton graphs captured the collision kernel of the model

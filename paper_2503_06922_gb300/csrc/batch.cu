@@ -245,6 +245,7 @@ accfem_status accfem_batch_create(accfem_handle* const* members, int32_t n_membe
       if (members[j] == members[i]) return ACCFEM_E_INVALID_ARG;
     // every member on the current device: the batch's kernels read all members' buffers
     if (!accfem_on_device(members[i], "accfem_batch_create")) return ACCFEM_E_INVALID_ARG;
+    if (members[i]->p.lcp_mode == kLcpPrimalAdmm) return ACCFEM_E_INVALID_ARG;   // single-instance solver only
   }
   accfem_batch* b = new accfem_batch();
   b->members.assign(members, members + n_members);

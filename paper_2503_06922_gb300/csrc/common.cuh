@@ -27,7 +27,7 @@ constexpr int kAccelParts = 10;    // per step block: G (6 upper entries) and b 
 // Iterations of a solve that may take Anderson steps; later ones (and the FP32 tangent's) fall back to
 // the 1-D secant over-relaxation of a slow monotone mode.
 constexpr int kAccelIters = 100;
-constexpr int kLcpActiveSet = 0, kLcpAdmm = 1;
+constexpr int kLcpActiveSet = 0, kLcpAdmm = 1, kLcpPrimalAdmm = 2;
 // The ADMM contact solver inverts its FP32 matrix in dynamic shared memory for working sets of up
 // to kAdmmSmemRows rows (larger ones in global memory); its kernels are launched with this many bytes.
 constexpr int kAdmmSmemRows = 192;
@@ -188,6 +188,11 @@ struct Dev {
   // contact LCP
   double *W, *y, *gj;                                // ws_cap^2 (slots), m_cap (rows), ws_cap*(ws_cap+2)
   int *plist;                                        // ws_cap: active slots
+  // primal ADMM (contact solver kLcpPrimalAdmm, primal.cu): the reduction of K + sigma I + rho A^T A
+  double *pa_D, *pa_E, *pa_P, *pa_EL, *pa_ER;        // nf_cap * 36 each
+  double *pa_x, *pa_xt, *pa_w, *pa_v;                // nf_cap * 6 each: x, the solve's result, RHS, scratch
+  double *pa_z, *pa_lam;                             // m_cap: z and the multipliers of every row
+  int* pa_guess;                                     // m_cap: 1 where the multiplier is positive (the guess)
   Ctl* ctl;
 };
 

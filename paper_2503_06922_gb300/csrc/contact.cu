@@ -434,7 +434,8 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
     S.q[i] = d.c_gap[row] - s;
     S.y[i] = 0.0;
     S.wcol[i] = 0;
-    S.inP[i] = (fl > 0 && (fl & RF_ACTIVE)) ? 1 : 0;
+    // the start: the rows active in the previous iteration, or the primal ADMM's guess
+    S.inP[i] = p.lcp_mode == kLcpPrimalAdmm ? (d.pa_guess[row] ? 1 : 0) : ((fl > 0 && (fl & RF_ACTIVE)) ? 1 : 0);
     wd = fmax(wd, wii);
     qmax = fmax(qmax, fabs(S.q[i]));
   }

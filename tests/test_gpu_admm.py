@@ -74,7 +74,7 @@ def test_admm_equals_active_set_on_an_uneven_instance(af):
 def test_contact_solver_arguments(af):
     w = wl.bent_tube_workload(0, n_steps=2)
     h = af.AccFem(w.robot, w.lumen)
-    assert h.accfem_set_contact_solver(2) == af.E_INVALID_ARG
+    assert h.accfem_set_contact_solver(3) == af.E_INVALID_ARG
     assert h.accfem_set_contact_solver(-1) == af.E_INVALID_ARG
     r0 = h.accfem_solve(w.tensions[1], w.insertions[1])
     h.accfem_reset()
@@ -110,3 +110,61 @@ def test_admm_member_in_a_batch_equals_alone(af):
     b.close()
     for h in hs + [alone]:
         h.close()
+
+
+def test_primal_admm_bent_tube_matches_oracle(af):
+    """ACCFEM_CONTACT_PRIMAL_ADMM (the paper's OSQP on the primal QP of Eq. 23, K + sigma I + rho A^T A
+    factored by the one-CTA reduction) against the oracle's primal ADMM (solver.Options(qp_solver=
+    "primal_admm")): the same states, contact nodes and net forces, and ADMM iterations were run."""
+    w = wl.bent_tube_workload(0, n_steps=10)
+    gpu = af.AccFem(w.robot, w.lumen)
+    assert gpu.accfem_set_contact_solver(af.CONTACT_PRIMAL_ADMM) == af.OK
+    ref = solver.Model(w.robot, w.lumen, solver.Options(qp_solver="primal_admm"))
+    rows = iters = 0
+    for s in range(len(w.insertions)):
+        g = gpu.accfem_solve(w.tensions[s], w.insertions[s])
+        o = ref.solve(w.tensions[s], w.insertions[s])
+        assert g["status"] == af.OK and o.status == solver.OK, (s, g["error"])
+        err = np.abs(g["node_pos"] - o.node_pos).max() / np.abs(o.node_pos).max()
+        assert err <= 1e-9, (s, err)
+        assert sorted({c["node"] for c in g["contacts"]}) == sorted({c["node"] for c in o.contacts}), s
+        fo, fg = _forces(o.contacts), _forces(g["contacts"])
+        fmax = max([np.linalg.norm(v) for v in fo.values()] + [1e-300])
+        for n in fo:
+            assert np.linalg.norm(fo[n] - fg[n]) <= 1e-6 * fmax, (s, n)
+        rows += len(g["contacts"])
+        iters += gpu.accfem_solve_admm_iterations()
+    assert rows > 0 and iters > 0
+    gpu.close()
+
+
+def test_primal_admm_equals_active_set_on_the_sweep_start(af):
+    """The first 40 solves of the 600 mm sweep (up to 200 free nodes, rows from solve 8 on) with the
+    primal ADMM and with the default solver: the same states (the exact polish gives the unique
+    contact solution either way)."""
+    w = wl.catmull_rom_workload(lumen_seed=1, tension_seed=2, n_steps=60)
+    a = af.AccFem(w.robot, w.lumen, max_contacts=4096)
+    b = af.AccFem(w.robot, w.lumen, max_contacts=4096)
+    assert b.accfem_set_contact_solver(af.CONTACT_PRIMAL_ADMM) == af.OK
+    for s in range(40):
+        ra = a.accfem_solve(w.tensions[s], w.insertions[s])
+        rb = b.accfem_solve(w.tensions[s], w.insertions[s])
+        assert ra["status"] == af.OK and rb["status"] == af.OK, (s, rb["error"])
+        err = np.abs(ra["node_pos"] - rb["node_pos"]).max() / np.abs(ra["node_pos"]).max()
+        assert err <= 1e-9, (s, err)
+    a.close()
+    b.close()
+
+
+def test_primal_admm_arguments(af):
+    w = wl.bent_tube_workload(0, n_steps=2)
+    h = af.AccFem(w.robot, w.lumen)
+    assert h.accfem_set_contact_model(af.CONTACT_SEGMENT) == af.OK
+    assert h.accfem_set_contact_solver(af.CONTACT_PRIMAL_ADMM) == af.E_INVALID_ARG   # node contacts only
+    assert h.accfem_set_contact_model(af.CONTACT_NODE) == af.OK
+    assert h.accfem_set_contact_solver(af.CONTACT_PRIMAL_ADMM) == af.OK
+    assert h.accfem_set_contact_model(af.CONTACT_SEGMENT) == af.E_INVALID_ARG
+    with pytest.raises(RuntimeError):                                                  # not in batches
+        af.AccFemBatch([h])
+    assert h.accfem_set_contact_solver(3) == af.E_INVALID_ARG
+    h.close()
