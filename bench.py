@@ -1083,7 +1083,7 @@ def ours(args, rank, world, local_rank):
         extra["frames"] = frames_run(af)
         # the paper's own solver of Eq. 23 (OSQP on the primal QP), frame by frame: its time per frame
         # against the number of contacts (the claim of Sec. IV.A)
-        fp = frames_run(af, node_counts=(100,), frames_per_step=1, solver=af.CONTACT_PRIMAL_ADMM)
+        fp = frames_run(af, node_counts=(100, 300), frames_per_step=1, solver=af.CONTACT_PRIMAL_ADMM)
         fp["solver"] = ("OSQP's ADMM on the primal QP of Eq. 23 (K + sigma I + rho A^T A factored per frame by a "
                         "one-CTA block cyclic reduction, one 1-column solve per ADMM iteration), guess polished "
                         "exactly by the active-set method")
