@@ -72,6 +72,8 @@ def parse():
                          "twice each on its final state (for profilers) and exit")
     ap.add_argument("--segment", action="store_true", help="with --profile-kernels: segment contacts")
     ap.add_argument("--admm", action="store_true", help="with --profile-kernels: the ADMM contact solver")
+    ap.add_argument("--primal", action="store_true",
+                    help="with --profile-kernels: the primal ADMM contact solver (first 39 solves of the sweep)")
     ap.add_argument("--profile-phases", action="store_true",
                     help="run the batched workload, then its element, collision and assembly phases as bench times "
                          "them (for profilers) and exit")
@@ -791,7 +793,10 @@ def profile_kernels_run(args):
         h.accfem_set_contact_model(af.CONTACT_SEGMENT)
     if args.admm:
         h.accfem_set_contact_solver(af.CONTACT_ADMM)
-    for s in range(len(w.insertions)):
+    if args.primal:
+        h.accfem_set_contact_solver(af.CONTACT_PRIMAL_ADMM)
+    n_solves = 39 if args.primal else len(w.insertions)   # the primal ADMM takes ~80 ms per solve
+    for s in range(n_solves):
         h.accfem_solve(w.tensions[s], w.insertions[s])
     for name, k in (("factor group", af.KERNEL_FACTOR), ("contact", af.KERNEL_CONTACT), ("element", af.KERNEL_ELEMENT),
                     ("collide", af.KERNEL_COLLIDE)):
