@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(1024) compact_batch(const Inst* __restrict__ t
 }
 
 // ------------------------------------------------------------------ assembly
-__device__ bool team_inverse6(double* sA, int tid, double* s_piv);
+__device__ bool team_inverse6(double* sA, int tid);
 
 // Assembly and RHS columns of one free node (blocks (node, y), 32 x 6 threads): D, U and g = F - F_a
 // with the tip load of Eq. 16-18, then RHS columns 0 = -g and 1 + k = A^T e_row for the row of
@@ -277,7 +277,6 @@ __device__ bool team_inverse6(double* sA, int tid, double* s_piv);
 __device__ __forceinline__ void assemble_rhs_body(const Params& p, const Dev& d, int bx, int by) {
   __shared__ double s_g[6];
   __shared__ double sA[36], sXl[36], sYr[36];
-  __shared__ double s_piv[1];
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
   const int f = bx;
@@ -334,7 +333,7 @@ __device__ __forceinline__ void assemble_rhs_body(const Params& p, const Dev& d,
     if (by == 0) d.g[(size_t)f * 6 + c] = F - Fa;
   }
   if (elim1) {                                      // first-level elimination of node f
-    const bool ok = team_inverse6(sA, tid, s_piv);  // begins with a barrier
+    const bool ok = team_inverse6(sA, tid);  // begins with a barrier
     if (!ok) {
       if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
     } else if (tid < 72) {                          // L on threads 0..35, R on 36..71
@@ -378,10 +377,10 @@ __global__ void __launch_bounds__(192) assemble_rhs_batch(const Inst* __restrict
   for_units(tab, plan, PH_ASM, [](const Inst& in, int bx, int by) { assemble_rhs_body(in.p, in.d, bx, by); });
 }
 
-// ------------------------------------------------------------------ 6x6 helpers (64-thread team)
+// ------------------------------------------------------------------ 6x6 helpers
 // In-place Gauss-Jordan inverse of the SPD matrix in sA (6x6, row-major); threads 0..35 own one
 // entry each.  Returns false (for all threads) when a pivot is not positive.
-__device__ bool team_inverse6(double* sA, int tid, double* s_piv) {
+__device__ bool team_inverse6(double* sA, int tid) {
   // Gauss-Jordan with 2x2 block pivots (DOFs k, k + 1 for k = 0, 2, 4): the block's inverse from its
   // determinant, one reciprocal for two DOFs; the block is SPD exactly when its two scalar pivots (a,
   // det / a) are positive.  Only the 36 entry threads compute (a warp's FP64 instructions hold its
@@ -427,7 +426,6 @@ __device__ bool team_inverse6(double* sA, int tid, double* s_piv) {
 // and blocks y >= 1 solve x_0 = P_0 b_0 for their chunks.
 __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, int bx, int by, int s) {
   __shared__ double sRl[36], sUl[36], sLl[36], sLr[36], sUi[36], sUr[36], sA[36], sX[36], sY[36];
-  __shared__ double s_piv[1];
   Ctl* ctl = d.ctl;
   if (ctl->status != 0 || ctl->converged) return;
   const int nf = ctl->nf;
@@ -495,7 +493,7 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
     sX[q] = v;
   }
   if (elim2 && by == 0) {
-    const bool ok = team_inverse6(sA, tid, s_piv);   // begins with a barrier
+    const bool ok = team_inverse6(sA, tid);   // begins with a barrier
     if (!ok) {
       if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
     } else if (tid < 72) {                           // L on threads 0..35, R on 36..71
@@ -532,7 +530,7 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
   }
   // root: node 0 after its last update; every block inverts D_0 and solves its chunks
   __syncthreads();
-  const bool ok = team_inverse6(sA, tid, s_piv);
+  const bool ok = team_inverse6(sA, tid);
   if (!ok) {
     if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
     return;
