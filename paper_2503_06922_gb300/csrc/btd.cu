@@ -267,6 +267,8 @@ __global__ void __launch_bounds__(1024) compact_batch(const Inst* __restrict__ t
 
 // ------------------------------------------------------------------ assembly
 __device__ bool team_inverse6(double* sA, int tid);
+__device__ __forceinline__ void team_lr6(const double* sX, const double* sY, const double* sP, double* P, double* L,
+                                         double* R, int tid);
 
 // Assembly and RHS columns of one free node (blocks (node, y), 32 x 6 threads): D, U and g = F - F_a
 // with the tip load of Eq. 16-18, then RHS columns 0 = -g and 1 + k = A^T e_row for the row of
@@ -336,19 +338,8 @@ __device__ __forceinline__ void assemble_rhs_body(const Params& p, const Dev& d,
     const bool ok = team_inverse6(sA, tid);  // begins with a barrier
     if (!ok) {
       if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
-    } else if (tid < 72) {                          // L on threads 0..35, R on 36..71
-      const int q = tid % 36, r = q / 6, c = q % 6;
-      double v = 0.0;
-      if (tid < 36) {
-        d.P[(size_t)f * 36 + q] = sA[q];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) v = fma(sXl[r * 6 + k], sA[k * 6 + c], v);   // U_{f-1} P_f
-        d.Lm[(size_t)f * 36 + q] = v;
-      } else {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) v = fma(sYr[k * 6 + r], sA[k * 6 + c], v);   // U_f^T P_f
-        d.Rm[(size_t)f * 36 + q] = v;
-      }
+    } else {                                        // P_f, L_f = U_{f-1} P_f, R_f = U_f^T P_f
+      team_lr6(sXl, sYr, sA, d.P + (size_t)f * 36, d.Lm + (size_t)f * 36, d.Rm + (size_t)f * 36, tid);
     }
   }
   __syncthreads();
@@ -378,30 +369,51 @@ __global__ void __launch_bounds__(192) assemble_rhs_batch(const Inst* __restrict
 }
 
 // ------------------------------------------------------------------ 6x6 helpers
-// In-place Gauss-Jordan inverse of the SPD matrix in sA (6x6, row-major); threads 0..35 own one
-// entry each.  Returns false (for all threads) when a pivot is not positive.
+// The FP64 pipe of an SMSP takes a warp instruction every 64 cycles whatever its lane mask, so the
+// helpers below give each class of entries (each with its own formula) a warp of its own: no warp
+// runs the instructions of another class, and the classes run on different SMSPs in parallel (warp
+// w of a block sits on SMSP w mod 4).  The arithmetic of every entry is the same as one thread per
+// entry would do.
+
+// In-place Gauss-Jordan inverse of the SPD matrix in sA (6x6, row-major), called by every thread of
+// a block of at least 128 threads.  Returns false (for all threads) when a pivot is not positive.
+// 2x2 block pivots (DOFs k, k + 1 for k = 0, 2, 4): the block's inverse from its determinant, one
+// reciprocal for two DOFs; the block is SPD exactly when its two scalar pivots (a, det / a) are
+// positive.  Entries of a pivot step: the 16 outside the pivot rows and columns (warp 0), the 8 of
+// the pivot rows outside the pivot columns (warp 1), the 8 of the pivot columns outside the pivot
+// rows (warp 2) and the 4 of the block (warp 3).
 __device__ bool team_inverse6(double* sA, int tid) {
-  // Gauss-Jordan with 2x2 block pivots (DOFs k, k + 1 for k = 0, 2, 4): the block's inverse from its
-  // determinant, one reciprocal for two DOFs; the block is SPD exactly when its two scalar pivots (a,
-  // det / a) are positive.  Only the 36 entry threads compute (a warp's FP64 instructions hold its
-  // SMSP's FP64 pipe whatever its lane mask, and the other warps share SMSPs with these two).
-  const int r = tid / 6, c = tid % 6;
+  const int w = tid >> 5, l = tid & 31;
   for (int k = 0; k < 6; k += 2) {
     __syncthreads();
     const double a = sA[k * 6 + k], b = sA[k * 6 + k + 1], b2 = sA[(k + 1) * 6 + k], cc = sA[(k + 1) * 6 + k + 1];
     const double det = fma(a, cc, -(b * b2));
     if (!(a > 0.0) || !(det > 0.0)) return false;
+    // this thread's entry (r, c) of the step, r = -1 for none; t -> t + 2 (t >= k) maps 0..3 onto
+    // the indices outside the pivot pair
+    int r = -1, c = -1;
+    if (w == 0 && l < 16) {
+      r = l >> 2; c = l & 3;
+      r += r >= k ? 2 : 0; c += c >= k ? 2 : 0;
+    } else if (w == 1 && l < 8) {
+      r = k + (l >> 2); c = l & 3;
+      c += c >= k ? 2 : 0;
+    } else if (w == 2 && l < 8) {
+      r = l >> 1; c = k + (l & 1);
+      r += r >= k ? 2 : 0;
+    } else if (w == 3 && l < 4) {
+      r = k + (l >> 1); c = k + (l & 1);
+    }
     double v = 0.0;
-    if (tid < 36) {
+    if (r >= 0) {
       const double rd = __drcp_rn(det);
       const double i00 = cc * rd, i01 = -b * rd, i10 = -b2 * rd, i11 = a * rd;
-      const bool pr = r == k || r == k + 1, pc = c == k || c == k + 1;
-      if (pr && pc) {
+      if (w == 3) {                                  // the block: Binv
         v = r == k ? (c == k ? i00 : i01) : (c == k ? i10 : i11);
-      } else if (pr) {                               // pivot rows: Binv [a_kc; a_k+1,c]
+      } else if (w == 1) {                           // pivot rows: Binv [a_kc; a_k+1,c]
         const double e0 = r == k ? i00 : i10, e1 = r == k ? i01 : i11;
         v = fma(e0, sA[k * 6 + c], e1 * sA[(k + 1) * 6 + c]);
-      } else if (pc) {                               // pivot columns: -[a_rk, a_r,k+1] Binv[:, c]
+      } else if (w == 2) {                           // pivot columns: -[a_rk, a_r,k+1] Binv[:, c]
         const double e0 = c == k ? i00 : i01, e1 = c == k ? i10 : i11;
         v = -fma(sA[r * 6 + k], e0, sA[r * 6 + k + 1] * e1);
       } else {                                       // a_rc - [a_rk, a_r,k+1] Binv [a_kc; a_k+1,c]
@@ -411,10 +423,36 @@ __device__ bool team_inverse6(double* sA, int tid) {
       }
     }
     __syncthreads();
-    if (tid < 36) sA[r * 6 + c] = v;
+    if (r >= 0) sA[r * 6 + c] = v;
   }
   __syncthreads();
   return true;
+}
+
+// The products of an elimination with P = sP (6x6 row-major, shared): L = X P and R = Y^T P (X, Y
+// in shared memory) to L and R, P itself to P (global).  Entries 0..31 of L in warp 0, of R in warp
+// 1, the last four of each in warp 2, so that every SMSP runs at most six FMA instructions.
+__device__ __forceinline__ void team_lr6(const double* sX, const double* sY, const double* sP, double* P, double* L,
+                                         double* R, int tid) {
+  const int w = tid >> 5, l = tid & 31;
+  int t = -1;                                        // 0..35: entry of L, 36..71: entry t - 36 of R
+  if (w == 0) t = l;
+  else if (w == 1) t = 36 + l;
+  else if (w == 2 && l < 8) t = l < 4 ? 32 + l : 64 + l;
+  if (t < 0) return;
+  const bool isL = t < 36;
+  const int q = isL ? t : t - 36, r = q / 6, c = q % 6;
+  const double* A = isL ? sX + r * 6 : sY + r;       // row r of X, or column r of Y
+  const int st = isL ? 1 : 6;
+  double v = 0.0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) v = fma(A[k * st], sP[k * 6 + c], v);
+  if (isL) {
+    P[q] = sP[q];
+    L[q] = v;
+  } else {
+    R[q] = v;
+  }
 }
 
 // Level s of the reduction, fused with the elimination at level 2s.  Blocks (kept node i = 2 s x,
@@ -465,50 +503,47 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
   }
   __syncthreads();
   const bool matrix = by == 0 || root;
-  if (tid < 36 && matrix) {
+  // the root's D_0 and U_0 are read by every block of this level and needed by no later step: only
+  // non-root levels store the updated blocks (for the next level's kernel)
+  const bool store = by == 0 && !root;
+  if (tid < 36 && matrix) {                          // Schur update of D_i (warp 0, lanes 0..3 of warp 1)
     const int r = tid / 6, c = tid % 6;
     double dd = d_own;
-    double un = 0.0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       dd = fma(-sRl[r * 6 + k], sUl[k * 6 + c], dd);
       dd = fma(-sLr[r * 6 + k], sUi[c * 6 + k], dd);
-      un = fma(-sLr[r * 6 + k], sUr[k * 6 + c], un);
     }
     sA[tid] = dd;
-    sY[tid] = hr2 ? un : 0.0;                        // new U_i = K_{i, i+2s}
-    // the root's D_0 and U_0 are read by every block of this level and needed by no later step:
-    // only non-root levels store the updated blocks (for the next level's kernel)
-    if (by == 0 && !root) {
-      d.D[(size_t)i * 36 + tid] = dd;
-      if (hr) d.U[(size_t)i * 36 + tid] = hr2 ? un : 0.0;
-    }
-  } else if (elim2 && by == 0 && tid < 72) {
-    // beside the Schur update: new left coupling K_{i-2s, i} = -L_{i-s} U_{i-s} (node i-s was
-    // eliminated at level s; L_{i-s} and U_{i-s} are in shared memory)
-    const int q = tid - 36, r = q / 6, c = q % 6;
-    double v = 0.0;
+    if (store) d.D[(size_t)i * 36 + tid] = dd;
+  } else if (matrix && (tid >> 5) >= 2 && (tid >> 5) <= 3) {
+    // beside it, in warps 2 and 3: the new U_i = K_{i, i+2s} = -L_{i+s} U_{i+s} (products 0..35)
+    // and, for an elimination at level 2s, the new left coupling K_{i-2s, i} = -L_{i-s} U_{i-s}
+    // (products 36..71; node i-s was eliminated at level s): warp 2 takes products lane and 64 +
+    // lane, warp 3 products 32 + lane
+    const int nprod = (elim2 && by == 0) ? 72 : 36;
+    for (int t = (tid >> 5) == 2 ? lane : 32 + lane; t < nprod; t += 64) {
+      const bool isU = t < 36;
+      const int q = isU ? t : t - 36, r = q / 6, c = q % 6;
+      const double* A = isU ? sLr : sLl;
+      const double* B = isU ? sUr : sUl;
+      double v = 0.0;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) v = fma(-sLl[r * 6 + k], sUl[k * 6 + c], v);
-    sX[q] = v;
+      for (int k = 0; k < 6; ++k) v = fma(-A[r * 6 + k], B[k * 6 + c], v);
+      if (isU) {
+        sY[q] = hr2 ? v : 0.0;
+        if (store && hr) d.U[(size_t)i * 36 + q] = hr2 ? v : 0.0;
+      } else {
+        sX[q] = v;
+      }
+    }
   }
   if (elim2 && by == 0) {
     const bool ok = team_inverse6(sA, tid);   // begins with a barrier
     if (!ok) {
       if (tid == 0) atomicCAS(&ctl->status, 0, ST_NOT_SPD);
-    } else if (tid < 72) {                           // L on threads 0..35, R on 36..71
-      const int q = tid % 36, r = q / 6, c = q % 6;
-      double v = 0.0;
-      if (tid < 36) {
-        d.P[(size_t)i * 36 + q] = sA[q];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) v = fma(sX[r * 6 + k], sA[k * 6 + c], v);    // U_{i-2s} P_i
-        d.Lm[(size_t)i * 36 + q] = v;
-      } else {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) v = fma(sY[k * 6 + r], sA[k * 6 + c], v);    // U_i^T P_i
-        d.Rm[(size_t)i * 36 + q] = v;
-      }
+    } else {                                         // P_i, L_i = U_{i-2s} P_i, R_i = U_i^T P_i
+      team_lr6(sX, sY, sA, d.P + (size_t)i * 36, d.Lm + (size_t)i * 36, d.Rm + (size_t)i * 36, tid);
     }
   }
   // forward reduction of level s: b_i -= R_{i-s} b_{i-s} + L_{i+s} b_{i+s}
