@@ -969,10 +969,16 @@ def ours(args, rank, world, local_rank):
         m_last, mc_last, np_last, _fb = h.accfem_solve_stats()
         nf_last = w.robot.n_elements - int(math.floor((w.robot.length - w.insertions[last_ok]) * w.robot.n_elements
                                                       / w.robot.length + 1e-6))
-        el_us = h.accfem_time_kernel(af.KERNEL_ELEMENT, 50)
-        co_us = h.accfem_time_kernel(af.KERNEL_COLLIDE, 20)
-        ct_us = h.accfem_time_kernel(af.KERNEL_CONTACT, 20)
-        fa_us = h.accfem_time_kernel(af.KERNEL_FACTOR, 20)
+        # replayed from one CUDA graph (the kernels chained as in the Newton loop) for the rooflines;
+        # host-issued launches beside them, for comparison
+        el_us = h.accfem_time_kernel_graph(af.KERNEL_ELEMENT, 50)
+        co_us = h.accfem_time_kernel_graph(af.KERNEL_COLLIDE, 20)
+        ct_us = h.accfem_time_kernel_graph(af.KERNEL_CONTACT, 20)
+        fa_us = h.accfem_time_kernel_graph(af.KERNEL_FACTOR, 20)
+        host_us = {"element": h.accfem_time_kernel(af.KERNEL_ELEMENT, 50),
+                   "collide": h.accfem_time_kernel(af.KERNEL_COLLIDE, 20),
+                   "contact": h.accfem_time_kernel(af.KERNEL_CONTACT, 20),
+                   "factor_group": h.accfem_time_kernel(af.KERNEL_FACTOR, 20)}
         # ---- the paper's contact scheme (OSQP's ADMM guess, then the exact polish): the same sweep,
         #      timed like `value`, and the contact kernel on the final state of the sweep
         progress("contact solver: ADMM sweep")
@@ -1110,6 +1116,9 @@ def ours(args, rank, world, local_rank):
                                        % (nf_last, 1 + mc_last),
                              "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s FP64",
                              "frac": achieved / peak, "traffic": FACTOR_DRAM_BYTES, "launch_us": fa_us,
+                             "launch_timing": "CUDA events around one replay of a CUDA graph holding 20 group "
+                                              "launches in sequence, as the Newton loop chains them (%.1f us per "
+                                              "group with host-issued launches)" % host_us["factor_group"],
                              "traffic_note": "ncu dram bytes per group launch at cold cache (the timed loop keeps "
                                              "the 11 MB working set in L2)",
                              "flops_per_launch": fa_flops, "executed_flops_per_launch": fa_exec,
@@ -1123,7 +1132,9 @@ def ours(args, rank, world, local_rank):
                                                % (m_last, mc_last, np_last),
                                      "achieved": ct_achieved, "peak": peak, "unit": "TFLOP/s FP64",
                                      "frac": ct_achieved / peak},
-                "kernel_us": {"element": el_us, "collide": co_us, "contact": ct_us, "factor_group": fa_us},
+                "kernel_us": {"element": el_us, "collide": co_us, "contact": ct_us, "factor_group": fa_us,
+                              "timing": "graph-replayed launches on the final state of the sweep",
+                              "host_launched": host_us},
                 "element_roofline": {"achieved": el_achieved, "peak": peak, "unit": "TFLOP/s FP64",
                                      "frac": el_achieved / peak, "flops_per_element": ELEMENT_FLOPS},
                 "clocks": clk.summary(),

@@ -248,6 +248,14 @@ typedef enum {
  * in *us, measured with CUDA events on the handle's stream.  For measurement. */
 accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t reps, double* us);
 
+/* As accfem_time_kernel, but the reps launches (sequences) are captured, one after another, into
+ * one CUDA graph that is replayed once untimed and once timed: the kernels then follow each other
+ * through graph dependencies, as inside the device-side Newton loop, without the host's launch
+ * overhead.  *us is the mean device time of one launch (sequence) of the timed replay.  The handle's
+ * stream must not be capturing already; ACCFEM_E_CUDA (with the message in accfem_last_error) when
+ * the capture or the replay fails.  For measurement. */
+accfem_status accfem_time_kernel_graph(accfem_handle* h, accfem_kernel kernel, int32_t reps, double* us);
+
 /* Collision query that allocates no memory.  The paper has no counterpart: this entry point exists
  * for callers that must not call cudaMalloc (or any allocating routine) once they run, for example a
  * real-time control loop that reserves all of its device memory at start-up and may not grow it, or

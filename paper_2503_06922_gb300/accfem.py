@@ -71,7 +71,8 @@ class accfem_state(ctypes.Structure):
 
 EXPORTS = ["accfem_default_options", "accfem_create", "accfem_solve", "accfem_solve_tip_load",
            "accfem_solve_resident", "accfem_reset", "accfem_set_stream", "accfem_transfer_bytes",
-           "accfem_time_kernel", "accfem_get_state", "accfem_kernel_launches", "accfem_destroy",
+           "accfem_time_kernel", "accfem_time_kernel_graph", "accfem_get_state", "accfem_kernel_launches",
+           "accfem_destroy",
            "accfem_status_string", "accfem_last_error", "accfem_detect_contacts_noalloc",
            "accfem_batch_create", "accfem_batch_begin", "accfem_batch_advance", "accfem_batch_poll",
            "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream", "accfem_batch_transfer_bytes",
@@ -113,6 +114,7 @@ def load(path=LIB_PATH):
     lib.accfem_set_stream.argtypes = [H, ctypes.c_void_p]
     lib.accfem_transfer_bytes.argtypes = [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.accfem_time_kernel.argtypes = [H, ctypes.c_int, ctypes.c_int32, _dp]
+    lib.accfem_time_kernel_graph.argtypes = [H, ctypes.c_int, ctypes.c_int32, _dp]
     lib.accfem_detect_contacts_noalloc.argtypes = [H, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                    ctypes.c_void_p, ctypes.c_void_p]
@@ -155,7 +157,8 @@ def load(path=LIB_PATH):
     lib.accfem_batch_destroy.restype = None
     for name in ("accfem_default_options", "accfem_create", "accfem_solve", "accfem_solve_tip_load",
                  "accfem_solve_resident", "accfem_get_state", "accfem_reset", "accfem_set_stream",
-                 "accfem_transfer_bytes", "accfem_time_kernel", "accfem_detect_contacts_noalloc",
+                 "accfem_transfer_bytes", "accfem_time_kernel", "accfem_time_kernel_graph",
+                 "accfem_detect_contacts_noalloc",
                  "accfem_batch_create", "accfem_batch_begin", "accfem_batch_advance", "accfem_batch_poll",
                  "accfem_batch_results", "accfem_batch_solve", "accfem_batch_set_stream",
                  "accfem_batch_transfer_bytes", "accfem_batch_serve", "accfem_device_bytes", "accfem_solve_stats", "accfem_solve_admm_iterations", "accfem_set_precision",
@@ -302,6 +305,13 @@ class AccFem:
         st = self._lib.accfem_time_kernel(self.h, int(kernel), int(reps), ctypes.byref(us))
         if st != OK:
             raise RuntimeError("accfem_time_kernel failed: %s" % self.accfem_last_error())
+        return float(us.value)
+
+    def accfem_time_kernel_graph(self, kernel, reps=20):
+        us = ctypes.c_double(0.0)
+        st = self._lib.accfem_time_kernel_graph(self.h, int(kernel), int(reps), ctypes.byref(us))
+        if st != OK:
+            raise RuntimeError("accfem_time_kernel_graph failed: %s" % self.accfem_last_error())
         return float(us.value)
 
     def accfem_detect_contacts_noalloc(self, node_pos, n_nodes, row_capacity, row_node, row_tri, row_point,

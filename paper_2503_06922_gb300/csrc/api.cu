@@ -783,9 +783,17 @@ accfem_status accfem_transfer_bytes(const accfem_handle* h, int64_t* h2d, int64_
   return ACCFEM_OK;
 }
 
-accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t reps, double* us) {
+}  // extern "C"
+
+namespace {
+
+// accfem_time_kernel (graph = false: reps host launches of the kernel or sequence) and
+// accfem_time_kernel_graph (graph = true: reps copies captured in sequence into one CUDA graph,
+// replayed once untimed and once timed).
+accfem_status time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t reps, double* us, bool graph) {
+  const char* who = graph ? "accfem_time_kernel_graph" : "accfem_time_kernel";
   if (!h || !us || reps < 1) return fail(h, ACCFEM_E_INVALID_ARG, "NULL argument or reps < 1");
-  if (!accfem_on_device(h, "accfem_time_kernel")) return ACCFEM_E_INVALID_ARG;
+  if (!accfem_on_device(h, who)) return ACCFEM_E_INVALID_ARG;
   Params& p = h->p;
   Dev& d = h->d;
   Ctl& c = *h->h_ctl;
@@ -819,21 +827,55 @@ accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t
     }
   };
   launch();
-  cudaEventRecord(e0, st);
-  for (int i = 0; i < reps; ++i) launch();
-  cudaEventRecord(e1, st);
-  h->launches += (int64_t)(reps + 1) * per_launch;
-  bool ok = cuda_ok(h, cudaEventSynchronize(e1), "time kernel");
+  bool ok = true;
+  if (!graph) {
+    cudaEventRecord(e0, st);
+    for (int i = 0; i < reps; ++i) launch();
+    cudaEventRecord(e1, st);
+    h->launches += (int64_t)(reps + 1) * per_launch;
+  } else {
+    // the capture records the launches without running them; the graph then runs twice
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    ok = cuda_ok(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (ok) {
+      for (int i = 0; i < reps; ++i) launch();
+      ok = cuda_ok(h, cudaStreamEndCapture(st, &g), "end capture") &&
+           cuda_ok(h, cudaGraphInstantiate(&ge, g, 0), "instantiate graph") &&
+           cuda_ok(h, cudaGraphLaunch(ge, st), "graph launch");
+      if (ok) {
+        cudaEventRecord(e0, st);
+        ok = cuda_ok(h, cudaGraphLaunch(ge, st), "graph launch");
+        cudaEventRecord(e1, st);
+      }
+    }
+    h->launches += (int64_t)(2 * reps + 1) * per_launch;
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+  }
+  ok = ok && cuda_ok(h, cudaEventSynchronize(e1), "time kernel");
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
+  if (ok) cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  // restore the control block of the solve
-  ok = ok && cuda_ok(h, cudaMemcpyAsync(d.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st), "restore control") &&
-       cuda_ok(h, cudaStreamSynchronize(st), "restore control");
-  if (!ok) return ACCFEM_E_CUDA;
+  // restore the control block of the solve (also after a failed capture)
+  const bool restored = cuda_ok(h, cudaMemcpyAsync(d.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st), "restore control") &&
+                        cuda_ok(h, cudaStreamSynchronize(st), "restore control");
+  if (!ok || !restored) return ACCFEM_E_CUDA;
   *us = 1000.0 * ms / reps;
   return ACCFEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+accfem_status accfem_time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t reps, double* us) {
+  return time_kernel(h, kernel, reps, us, false);
+}
+
+accfem_status accfem_time_kernel_graph(accfem_handle* h, accfem_kernel kernel, int32_t reps, double* us) {
+  return time_kernel(h, kernel, reps, us, true);
 }
 
 accfem_status accfem_solve_stats(const accfem_handle* h, int32_t* rows, int32_t* working_rows, int32_t* active_rows,
