@@ -375,14 +375,22 @@ __global__ void __launch_bounds__(192) assemble_rhs_batch(const Inst* __restrict
 // w of a block sits on SMSP w mod 4).  The arithmetic of every entry is the same as one thread per
 // entry would do.
 
+// Named barrier `id` over n threads: the producers arrive without waiting, the consumers wait (the
+// producers' earlier shared-memory writes are then visible to the consumers).
+__device__ __forceinline__ void named_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
 // In-place Gauss-Jordan inverse of the SPD matrix in sA (6x6, row-major), called by every thread of
-// a block of at least 128 threads.  Returns false (for all threads) when a pivot is not positive.
-// 2x2 block pivots (DOFs k, k + 1 for k = 0, 2, 4): the block's inverse from its determinant, one
-// reciprocal for two DOFs; the block is SPD exactly when its two scalar pivots (a, det / a) are
-// positive.  Entries of a pivot step: the 16 outside the pivot rows and columns (warp 0), the 8 of
-// the pivot rows outside the pivot columns (warp 1), the 8 of the pivot columns outside the pivot
-// rows (warp 2) and the 4 of the block (warp 3).
+// a block of at least 128 threads (named barrier 1 is used between warps 0 and 1).  Returns false
+// (for all threads) when a pivot is not positive.  2x2 block pivots (DOFs k, k + 1 for k = 0, 2,
+// 4): the block's inverse Binv from its determinant, one reciprocal for two DOFs; the block is SPD
+// exactly when its two scalar pivots (a, det / a) are positive.  Entries of a pivot step: the 8 of
+// the pivot rows outside the pivot columns (warp 1: Binv times the two rows, which it also hands to
+// warp 0), the 16 outside the pivot rows and columns (warp 0: the entry less the row's two pivot-
+// column entries times those scaled rows), the 8 of the pivot columns outside the pivot rows (warp
+// 2) and the 4 of the block (warp 3).  Each lane forms only the entries of Binv its formula uses.
 __device__ bool team_inverse6(double* sA, int tid) {
+  __shared__ double s_piv[2][4];                   // the scaled pivot rows, outside the pivot columns
   const int w = tid >> 5, l = tid & 31;
   for (int k = 0; k < 6; k += 2) {
     __syncthreads();
@@ -405,21 +413,24 @@ __device__ bool team_inverse6(double* sA, int tid) {
       r = k + (l >> 1); c = k + (l & 1);
     }
     double v = 0.0;
-    if (r >= 0) {
-      const double rd = __drcp_rn(det);
-      const double i00 = cc * rd, i01 = -b * rd, i10 = -b2 * rd, i11 = a * rd;
-      if (w == 3) {                                  // the block: Binv
-        v = r == k ? (c == k ? i00 : i01) : (c == k ? i10 : i11);
-      } else if (w == 1) {                           // pivot rows: Binv [a_kc; a_k+1,c]
-        const double e0 = r == k ? i00 : i10, e1 = r == k ? i01 : i11;
+    if (w == 1) {                                    // pivot rows: Binv [a_kc; a_k+1,c]
+      if (r >= 0) {
+        const double rd = __drcp_rn(det);
+        const double e0 = (r == k ? cc : -b2) * rd, e1 = (r == k ? -b : a) * rd;
         v = fma(e0, sA[k * 6 + c], e1 * sA[(k + 1) * 6 + c]);
-      } else if (w == 2) {                           // pivot columns: -[a_rk, a_r,k+1] Binv[:, c]
-        const double e0 = c == k ? i00 : i01, e1 = c == k ? i10 : i11;
+        s_piv[l >> 2][l & 3] = v;
+      }
+      named_arrive(1, 64);
+    } else if (w == 0) {                             // a_rc - [a_rk, a_r,k+1] Binv [a_kc; a_k+1,c]
+      named_sync(1, 64);
+      if (r >= 0) v = fma(-sA[r * 6 + k], s_piv[0][l & 3], fma(-sA[r * 6 + k + 1], s_piv[1][l & 3], sA[r * 6 + c]));
+    } else if (r >= 0) {
+      const double rd = __drcp_rn(det);
+      if (w == 2) {                                  // pivot columns: -[a_rk, a_r,k+1] Binv[:, c]
+        const double e0 = (c == k ? cc : -b) * rd, e1 = (c == k ? -b2 : a) * rd;
         v = -fma(sA[r * 6 + k], e0, sA[r * 6 + k + 1] * e1);
-      } else {                                       // a_rc - [a_rk, a_r,k+1] Binv [a_kc; a_k+1,c]
-        const double p0 = fma(i00, sA[k * 6 + c], i01 * sA[(k + 1) * 6 + c]);
-        const double p1 = fma(i10, sA[k * 6 + c], i11 * sA[(k + 1) * 6 + c]);
-        v = fma(-sA[r * 6 + k], p0, fma(-sA[r * 6 + k + 1], p1, sA[r * 6 + c]));
+      } else {                                       // the block: Binv
+        v = (r == k ? (c == k ? cc : -b) : (c == k ? -b2 : a)) * rd;
       }
     }
     __syncthreads();
