@@ -199,14 +199,17 @@ __device__ bool solve_on_set(const Dev& d, LcpShared& S, int m) {
     const double b2 = G[(size_t)(k + 1) * ldg + k], cc = G[(size_t)(k + 1) * ldg + k + 1];
     const double det = fma(a, cc, -(b * b2));
     if (!(a > 0.0) || !(det > 0.0)) return false;
-    // warp 0 forms the block inverse and both scaled pivot rows (one reciprocal per block)
-    if (tid < 32) {
+    // the two scaled pivot rows, Binv [a_k; a_k+1] (one reciprocal per block): the first by warp 0,
+    // the second by warp 1, each from the two entries of Binv it uses (a warp's FP64 instruction
+    // holds its SMSP's FP64 pipe for 64 cycles, so the two rows run on two SMSPs at once)
+    if (tid < 64) {
+      const bool second = tid >= 32;
       const double rd = __drcp_rn(det);
-      const double i00 = cc * rd, i01 = -b * rd, i10 = -b2 * rd, i11 = a * rd;
-      for (int c = k + 2 + tid; c < ldg; c += 32) {
+      const double e0 = (second ? -b2 : cc) * rd, e1 = (second ? a : -b) * rd;
+      double* dst = second ? q1 : S.prow;
+      for (int c = k + 2 + (tid & 31); c < ldg; c += 32) {
         const double g0 = G[(size_t)k * ldg + c], g1 = G[(size_t)(k + 1) * ldg + c];
-        S.prow[c] = fma(i00, g0, i01 * g1);
-        q1[c] = fma(i10, g0, i11 * g1);
+        dst[c] = fma(e0, g0, e1 * g1);
       }
     }
     __syncthreads();

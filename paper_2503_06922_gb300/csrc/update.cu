@@ -151,17 +151,22 @@ __device__ void limiter_block(const Params& p, const Dev& d, const Ctl* ctl, Lim
 #pragma unroll
     for (int i = 0; i < kAccelParts; ++i) acc[i + 1] += d.aa_part[(size_t)b * kAccelParts + i];
   }
+  // Threads from `live` on hold +0.0.  The butterfly rounds whose partners all hold +0.0 (o >= live)
+  // and the sums of the warps without data are left out: adding +0.0 changes no bit of a total that
+  // starts from +0.0, and each left-out addition costs the SMSP's FP64 pipe 64 cycles.
+  const int live = min(nb, nthr);
 #pragma unroll
   for (int i = 0; i <= kAccelParts; ++i) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+    for (int o = 16; o > 0; o >>= 1)
+      if (o < live) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
   }
   if (lane == 0 && w < 4)
 #pragma unroll
     for (int i = 0; i <= kAccelParts; ++i) s_red[i][w] = acc[i];
   __syncthreads();
   if (tid == 0) {
-    const int nw = min((nthr + 31) / 32, 4);
+    const int nw = min(min((nthr + 31) / 32, 4), (live + 31) / 32);
     double S[kAccelParts + 1];
     for (int i = 0; i <= kAccelParts; ++i) {
       S[i] = 0.0;
