@@ -10,7 +10,8 @@
 // merged, keeping the lowest index.
 //
 // Work split: triangles are binned by centroid in a uniform grid; a node scans the cells of the
-// box p +- (r_o + gap + max triangle radius).  A triangle whose FP32 bounding sphere stays beyond
+// box p +- (r_o + gap + max triangle radius) that come within that distance of p (the box's corner
+// cells often do not: about a quarter of the slots).  A triangle whose FP32 bounding sphere stays beyond
 // the activation distance (+ eps_d) is skipped.  Pass 1 computes FP32 distances (coordinates
 // relative to the cell centre, so |x| is a few mm and the FP32 error a few 1e-9 m) and their
 // warp minimum; pass 2 keeps a triangle for the exact FP64 test when its FP32 distance is within
@@ -48,6 +49,12 @@ __device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int 
   }
   const int ncell = nc3[0] * nc3[1] * nc3[2];
   const float thr32 = (float)(thr + p.eps_d);
+  // cell culling: the largest bounding sphere reaches at most g_rq - (r_o + gap) from its centroid;
+  // the margin eps_d + 1e-6 m covers the activation margin of the sphere test and the FP32 rounding
+  // of the cell-relative coordinates (~1e-9 m)
+  const float half_h = (float)(0.5 * p.g_h);
+  const float cull_r = (float)(p.g_rq + p.eps_d + 1e-6);
+  const float cull_r2 = cull_r * cull_r;
   // Walk of the cells around the node: up to 32 cells at a time, their slot ranges loaded by the
   // lanes and scanned into one index space, so that every round tests 32 slots of any cells (lane
   // j finds its slot's cell by a binary search over the scanned counts) and two rounds' loads are
@@ -63,12 +70,18 @@ __device__ __forceinline__ void collide_body(const Params& p, const Dev& d, int 
         const int cx = lo[0] + q % nc3[0];
         const int cy = lo[1] + (q / nc3[0]) % nc3[1];
         const int cz = lo[2] + q / (nc3[0] * nc3[1]);
-        const int cell = (cz * p.g_dim[1] + cy) * p.g_dim[0] + cx;
-        cs0 = d.cell_start[cell];
-        cnt = d.cell_start[cell + 1] - cs0;
         pcx = (float)(pn[0] - (p.g_org[0] + (cx + 0.5) * p.g_h));
         pcy = (float)(pn[1] - (p.g_org[1] + (cy + 0.5) * p.g_h));
         pcz = (float)(pn[2] - (p.g_org[2] + (cz + 0.5) * p.g_h));
+        // a cell whose box lies farther than cull_r from the node holds no triangle whose bounding
+        // sphere reaches the activation distance (its centroid is in the box): its slots are skipped
+        const float ex = fmaxf(fabsf(pcx) - half_h, 0.f), ey = fmaxf(fabsf(pcy) - half_h, 0.f),
+                    ez = fmaxf(fabsf(pcz) - half_h, 0.f);
+        if (ex * ex + ey * ey + ez * ez <= cull_r2) {
+          const int cell = (cz * p.g_dim[1] + cy) * p.g_dim[0] + cx;
+          cs0 = d.cell_start[cell];
+          cnt = d.cell_start[cell + 1] - cs0;
+        }
       }
       int incl = cnt;                              // inclusive scan of the slot counts over the lanes
 #pragma unroll
