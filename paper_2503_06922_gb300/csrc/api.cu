@@ -18,14 +18,14 @@ __global__ void element_kernel(Params p, Dev d);
 __global__ void collide_kernel(Params p, Dev d);
 __global__ void collide_segment_kernel(Params p, Dev d);
 __global__ void compact_kernel(Params p, Dev d);
-__global__ void bcr_bwd_kernel(Params p, Dev d, int s);
+__global__ void bcr_bwd_kernel(Params p, Dev d, int s, int nf);
 __global__ void contact_kernel(Params p, Dev d);
 __global__ void step_kernel(Params p, Dev d);
 __global__ void apply_kernel(Params p, Dev d);
 __global__ void start_kernel(Params p, Dev d, int mode, double delta, double delta_old, int k);
 __global__ void ctl_kernel(Params p, Dev d, cudaGraphConditionalHandle h, int max_iter, int set_cond);
 __global__ void assemble_rhs_kernel(Params p, Dev d);
-__global__ void bcr_level_kernel(Params p, Dev d, int s);
+__global__ void bcr_level_kernel(Params p, Dev d, int s, int nf);
 __global__ void primal_admm_kernel(Params p, Dev d);
 void upload_element_tables();
 }  // namespace accfem
@@ -401,9 +401,9 @@ int enqueue_factor(const Params& p, const Dev& d, int nf, cudaStream_t st, bool 
   if (p.lcp_mode == kLcpPrimalAdmm) { launch_k(pdl, primal_admm_kernel, dim3(1), dim3(1024), st, p, d); ++n; }
   int levels = 0;
   while (levels < kMaxLevels && phase_gx(PH_LEV0 + levels, nf) > 0) ++levels;
-  for (int j = 0; j < levels; ++j) { launch_k(pdl, bcr_level_kernel, grid(PH_LEV0 + j), dim3(192), st, p, d, 1 << j); ++n; }
+  for (int j = 0; j < levels; ++j) { launch_k(pdl, bcr_level_kernel, grid(PH_LEV0 + j), dim3(192), st, p, d, 1 << j, nf); ++n; }
   for (int j = levels - 1; j >= 0; --j)
-    if (phase_gx(PH_BWD0 + j, nf) > 0) { launch_k(pdl, bcr_bwd_kernel, grid(PH_BWD0 + j), dim3(96), st, p, d, 1 << j); ++n; }
+    if (phase_gx(PH_BWD0 + j, nf) > 0) { launch_k(pdl, bcr_bwd_kernel, grid(PH_BWD0 + j), dim3(96), st, p, d, 1 << j, nf); ++n; }
   return n;
 }
 

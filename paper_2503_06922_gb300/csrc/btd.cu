@@ -473,11 +473,15 @@ __device__ __forceinline__ void team_lr6(const double* sX, const double* sY, con
 // R_i = U_i^T P_i.  Blocks y >= 1 apply the level-s forward reduction to their RHS chunks (chunk
 // y - 1 + kRhsSplit q).  When 2s >= nf only node 0 is kept: every block inverts D_0 itself (root)
 // and blocks y >= 1 solve x_0 = P_0 b_0 for their chunks.
-__device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, int bx, int by, int s) {
+// kLate: nf comes from the launch, and the control block's status is read beside the block and
+// RHS loads (tested after the first barrier, before any store), so that the loads need not wait for
+// it; the first RHS chunk is then loaded up to the column capacity.  Otherwise the caller has tested
+// the status and read nf.
+template <bool kLate>
+__device__ __forceinline__ void bcr_level_run(const Params& p, const Dev& d, int nf, int bx, int by, int s) {
   __shared__ double sRl[36], sUl[36], sLl[36], sLr[36], sUi[36], sUr[36], sA[36], sX[36], sY[36];
+  __shared__ int s_go;
   Ctl* ctl = d.ctl;
-  if (ctl->status != 0 || ctl->converged) return;
-  const int nf = ctl->nf;
   const int i = 2 * s * bx;
   if (i >= nf) return;
   const int tid = threadIdx.x;
@@ -487,11 +491,12 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
   // RHS values of this block's first column chunk, loaded with the blocks so that the two
   // latencies overlap (the columns of nodes i +- s are not written at this level)
   const int lane = tid & 31, c = tid >> 5;
+  if (kLate && tid == 0) s_go = ctl->status == 0 && !ctl->converged;
   const int nrhs = ctl->mc + 1;
   const size_t ld = p.nrhs_cap;
   // block y == 0 does the 6x6 block work only; blocks y >= 1 reduce the RHS column chunks y - 1,
   // y - 1 + kRhsSplit, .. (so the launch takes the longer of the two paths, not their sum)
-  const int chunk0 = by > 0 ? (by - 1) * 32 : nrhs;
+  const int chunk0 = by > 0 ? (by - 1) * 32 : (1 << 30);
   const int r_first = chunk0 + lane;
   double b_own = 0.0, b_l[6], b_r[6];
   auto load_rhs = [&](int r) {
@@ -502,7 +507,7 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
       b_r[k] = hr ? d.B[((size_t)(i + s) * 6 + k) * ld + r] : 0.0;
     }
   };
-  if (r_first < nrhs) load_rhs(r_first);
+  if (r_first < (kLate ? (int)p.nrhs_cap : nrhs)) load_rhs(r_first);
   const double d_own = (tid < 36 && (by == 0 || root)) ? d.D[(size_t)i * 36 + tid] : 0.0;   // with the blocks
   if (tid < 36) {
     sRl[tid] = hl ? d.Rm[(size_t)(i - s) * 36 + tid] : 0.0;
@@ -513,6 +518,7 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
     sUr[tid] = hr2 ? d.U[(size_t)(i + s) * 36 + tid] : 0.0;
   }
   __syncthreads();
+  if (kLate && !s_go) return;
   const bool matrix = by == 0 || root;
   // the root's D_0 and U_0 are read by every block of this level and needed by no later step: only
   // non-root levels store the updated blocks (for the next level's kernel)
@@ -612,9 +618,16 @@ __device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, in
   }
 }
 
-__global__ void __launch_bounds__(192) bcr_level_kernel(Params p, Dev d, int s) {
+__device__ __forceinline__ void bcr_level_body(const Params& p, const Dev& d, int bx, int by, int s) {
+  const Ctl* ctl = d.ctl;
+  if (ctl->status != 0 || ctl->converged) return;
+  bcr_level_run<false>(p, d, ctl->nf, bx, by, s);
+}
+
+// nf: the free nodes of the Newton graph this launch belongs to (fixed during a solve)
+__global__ void __launch_bounds__(192) bcr_level_kernel(Params p, Dev d, int s, int nf) {
   pdl_enter();
-  bcr_level_body(p, d, blockIdx.x, blockIdx.y, s);
+  bcr_level_run<true>(p, d, nf, blockIdx.x, blockIdx.y, s);
 }
 
 // level j (stride 2^j) of every iterating instance
@@ -626,16 +639,18 @@ __global__ void __launch_bounds__(192, 3) bcr_level_batch(const Inst* __restrict
 // x 6 components, one warp per SMSP (a warp's FP64 instruction holds its SMSP's FP64 pipe for 64
 // cycles, so two warps on one SMSP would serialise); block y takes the 16-column chunks y,
 // y + kBwdSplit, ...
-__device__ __forceinline__ void bcr_bwd_body(const Params& p, const Dev& d, int bx, int by, int s) {
+// kLate as in bcr_level_run.
+template <bool kLate>
+__device__ __forceinline__ void bcr_bwd_run(const Params& p, const Dev& d, int nf, int bx, int by, int s) {
   __shared__ double sP[36], sL[36], sR[36];
-  Ctl* ctl = d.ctl;
-  if (ctl->status != 0 || ctl->converged) return;
-  const int nf = ctl->nf;
+  __shared__ int s_go;
+  const Ctl* ctl = d.ctl;
   const int j = s + 2 * s * bx;
   if (j >= nf) return;
   const int tid = threadIdx.x;
   const bool hr = j + s < nf;
   const int lane = tid & 15, c = tid >> 4;
+  if (kLate && tid == 0) s_go = ctl->status == 0 && !ctl->converged;
   const int nrhs = ctl->mc + 1;
   const size_t ld = p.nrhs_cap;
   // b_j, x_{j-s}, x_{j+s} of the column this thread reads in a chunk (the first chunk's loaded with
@@ -649,13 +664,14 @@ __device__ __forceinline__ void bcr_bwd_body(const Params& p, const Dev& d, int 
       xr[k] = hr ? d.B[((size_t)(j + s) * 6 + k) * ld + r] : 0.0;
     }
   };
-  if (by * 16 + lane < nrhs) load(by * 16 + lane);
+  if (by * 16 + lane < (kLate ? (int)p.nrhs_cap : nrhs)) load(by * 16 + lane);
   if (tid < 36) {
     sP[tid] = d.P[(size_t)j * 36 + tid];
     sL[tid] = d.Lm[(size_t)j * 36 + tid];
     sR[tid] = hr ? d.Rm[(size_t)j * 36 + tid] : 0.0;
   }
   __syncthreads();
+  if (kLate && !s_go) return;
   for (int r0 = by * 16; r0 < nrhs; r0 += 16 * kBwdSplit) {
     const int r = r0 + lane;
     const bool act = r < nrhs;
@@ -679,9 +695,15 @@ __device__ __forceinline__ void bcr_bwd_body(const Params& p, const Dev& d, int 
   }
 }
 
-__global__ void __launch_bounds__(96) bcr_bwd_kernel(Params p, Dev d, int s) {
+__device__ __forceinline__ void bcr_bwd_body(const Params& p, const Dev& d, int bx, int by, int s) {
+  const Ctl* ctl = d.ctl;
+  if (ctl->status != 0 || ctl->converged) return;
+  bcr_bwd_run<false>(p, d, ctl->nf, bx, by, s);
+}
+
+__global__ void __launch_bounds__(96) bcr_bwd_kernel(Params p, Dev d, int s, int nf) {
   pdl_enter();
-  bcr_bwd_body(p, d, blockIdx.x, blockIdx.y, s);
+  bcr_bwd_run<true>(p, d, nf, blockIdx.x, blockIdx.y, s);
 }
 
 __global__ void __launch_bounds__(96) bcr_bwd_batch(const Inst* __restrict__ tab, const Plan* __restrict__ plan, int j) {
