@@ -61,10 +61,11 @@ OK, E_INVALID_ARG, E_NOMEM, E_CUDA, E_NOT_CONVERGED, E_CONTACT_CAPACITY, E_NOT_S
 
 @dataclass
 class Options:
+    # The C ABI's contact_tol (the relative sign tolerance of its active-set LCP) has no counterpart
+    # here: the oracle's LCP solvers take their own tolerances (lcp.py).
     activation_gap: float = 1.0e-3
     step_limit: float = 5.0e-4
     newton_tol: float = 1.0e-11
-    contact_tol: float = 1.0e-9
     max_newton_iters: int = 200
     max_contact_iters: int = 4000
     max_contacts: int = 256
