@@ -390,7 +390,7 @@ PHASE_BYTES = {"element": 800.0, "assemble": 1344.0}
 PHASE_DRAM_BYTES = {"element": 7.9e6 + 9.0e6, "collide": 165.1e6 + 4.2e6, "assemble": 172.7e6 + 699.0e6}
 # DRAM traffic per launch of the factor group on the final state of the sweep, cold cache (ncu,
 # profiles/factor_group_sweep600_M300_dram.md; assemble_rhs + 9 level + 9 back-substitution launches).
-FACTOR_DRAM_BYTES = 7.490e6
+FACTOR_DRAM_BYTES = 7.476e6
 
 
 def _batch_phase_rooflines(af, b, hs, ws, seed=6):

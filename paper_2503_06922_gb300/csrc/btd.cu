@@ -473,10 +473,10 @@ __device__ __forceinline__ void team_lr6(const double* sX, const double* sY, con
 // R_i = U_i^T P_i.  Blocks y >= 1 apply the level-s forward reduction to their RHS chunks (chunk
 // y - 1 + kRhsSplit q).  When 2s >= nf only node 0 is kept: every block inverts D_0 itself (root)
 // and blocks y >= 1 solve x_0 = P_0 b_0 for their chunks.
-// kLate: nf comes from the launch, and the control block's status is read beside the block and
-// RHS loads (tested after the first barrier, before any store), so that the loads need not wait for
-// it; the first RHS chunk is then loaded up to the column capacity.  Otherwise the caller has tested
-// the status and read nf.
+// kLate: nf comes from the launch, and the control block's status is read beside the 6x6 block
+// loads (tested after the first barrier, before any store), so that those loads need not wait for
+// it (the RHS loads still wait for the column count).  Otherwise the caller has tested the status
+// and read nf.
 template <bool kLate>
 __device__ __forceinline__ void bcr_level_run(const Params& p, const Dev& d, int nf, int bx, int by, int s) {
   __shared__ double sRl[36], sUl[36], sLl[36], sLr[36], sUi[36], sUr[36], sA[36], sX[36], sY[36];
@@ -507,7 +507,7 @@ __device__ __forceinline__ void bcr_level_run(const Params& p, const Dev& d, int
       b_r[k] = hr ? d.B[((size_t)(i + s) * 6 + k) * ld + r] : 0.0;
     }
   };
-  if (r_first < (kLate ? (int)p.nrhs_cap : nrhs)) load_rhs(r_first);
+  if (r_first < nrhs) load_rhs(r_first);
   const double d_own = (tid < 36 && (by == 0 || root)) ? d.D[(size_t)i * 36 + tid] : 0.0;   // with the blocks
   if (tid < 36) {
     sRl[tid] = hl ? d.Rm[(size_t)(i - s) * 36 + tid] : 0.0;
@@ -664,7 +664,7 @@ __device__ __forceinline__ void bcr_bwd_run(const Params& p, const Dev& d, int n
       xr[k] = hr ? d.B[((size_t)(j + s) * 6 + k) * ld + r] : 0.0;
     }
   };
-  if (by * 16 + lane < (kLate ? (int)p.nrhs_cap : nrhs)) load(by * 16 + lane);
+  if (by * 16 + lane < nrhs) load(by * 16 + lane);
   if (tid < 36) {
     sP[tid] = d.P[(size_t)j * 36 + tid];
     sL[tid] = d.Lm[(size_t)j * 36 + tid];
