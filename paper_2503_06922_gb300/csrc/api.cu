@@ -425,7 +425,7 @@ int enqueue_iteration(accfem_handle* h, int nf, cudaStream_t st, cudaGraphCondit
   launch_k(pdl, compact_kernel, dim3(1), dim3(1024), st, p, d); ++n;
   cudaStreamWaitEvent(st, h->join, 0);
   n += enqueue_factor(p, d, nf, st, pdl);
-  launch_ks(pdl, contact_kernel, dim3(1), dim3(256), p.lcp_mode == kLcpAdmm ? kAdmmSmemBytes : 0u, st, p, d); ++n;
+  launch_ks(pdl, contact_kernel, dim3(1), dim3(256), kAdmmSmemBytes, st, p, d); ++n;
   launch_k(pdl, step_kernel, grid(PH_STEP), dim3(32, 6), st, p, d); ++n;
   launch_k(pdl, apply_kernel, grid(PH_APPLY), dim3(128), st, p, d); ++n;
   launch_k(pdl, ctl_kernel, dim3(1), dim3(1), st, p, d, cond, h->max_newton, h->stream_mode ? 0 : 1); ++n;
@@ -823,7 +823,7 @@ accfem_status time_kernel(accfem_handle* h, accfem_kernel kernel, int32_t reps, 
       case ACCFEM_KERNEL_ASSEMBLE:
         assemble_rhs_kernel<<<dim3(phase_gx(PH_ASM, nf), phase_gy(PH_ASM)), dim3(32, 6), 0, st>>>(p, d); break;
       case ACCFEM_KERNEL_FACTOR: per_launch = enqueue_factor(p, d, nf, st, h->pdl); break;
-      default: contact_kernel<<<1, 256, p.lcp_mode == kLcpAdmm ? kAdmmSmemBytes : 0u, st>>>(p, d); break;
+      default: contact_kernel<<<1, 256, kAdmmSmemBytes, st>>>(p, d); break;
     }
   };
   launch();

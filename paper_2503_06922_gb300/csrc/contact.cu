@@ -93,7 +93,8 @@ struct LcpShared {
 // Forms column j of W = A X (with the compliance eps on its diagonal) for every active slot j whose
 // column is not formed yet: W_ij = n_i . X_j[node_i] over the working-set slots i (row wrow[i]).
 // W is symmetric, so the rows of the active columns give every entry the active-set method reads.
-__device__ void ensure_columns(const Dev& d, LcpShared& S, int m, size_t ld, double eps_w) {
+// W: m x m row-major, in shared or global memory.
+__device__ void ensure_columns(const Dev& d, LcpShared& S, int m, size_t ld, double eps_w, double* W) {
   const int tid = threadIdx.x, nt = blockDim.x;
   __syncthreads();
   // a thread owns rows i (its node's RHS entries and normal loaded once) and forms their entries of
@@ -114,7 +115,7 @@ __device__ void ensure_columns(const Dev& d, LcpShared& S, int m, size_t ld, dou
         s = fma(n1, __ldg(b1 + j), s);
         s = fma(n2, __ldg(b2 + j), s);
         if (i == j) s += eps_w;
-        d.W[(size_t)i * m + j] = s;
+        W[(size_t)i * m + j] = s;
       }
     } else {                                       // a segment row also weighs the element's near node
       const double m0 = d.c_w2[3 * row], m1 = d.c_w2[3 * row + 1], m2 = d.c_w2[3 * row + 2];
@@ -132,7 +133,7 @@ __device__ void ensure_columns(const Dev& d, LcpShared& S, int m, size_t ld, dou
         s = fma(m1, __ldg(c1 + j), s);
         s = fma(m2, __ldg(c2 + j), s);
         if (i == j) s += eps_w;
-        d.W[(size_t)i * m + j] = s;
+        W[(size_t)i * m + j] = s;
       }
     }
   }
@@ -162,7 +163,7 @@ __device__ void rebuild_plist(LcpShared& S, int m) {
 // Solves W_PP z_P = -q_P for the active list (Gauss-Jordan with 2x2 block pivots over the CTA, FP64;
 // shared memory for up to kLcpSmemGJ rows) and writes z (0 outside P).  Returns false on a
 // non-positive pivot.
-__device__ bool solve_on_set(const Dev& d, LcpShared& S, int m) {
+__device__ bool solve_on_set(const Dev& d, LcpShared& S, int m, const double* W) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int np = S.np;
   const int ldg = np + 1;
@@ -170,7 +171,7 @@ __device__ bool solve_on_set(const Dev& d, LcpShared& S, int m) {
   for (int idx = tid; idx < np * ldg; idx += nt) {
     int r = idx / ldg, c = idx % ldg;
     int i = S.plist[r];
-    G[idx] = (c < np) ? d.W[(size_t)i * m + S.plist[c]] : -S.q[i];
+    G[idx] = (c < np) ? W[(size_t)i * m + S.plist[c]] : -S.q[i];
   }
   // 2x2 block pivots (rows k, k + 1): the block's inverse from its determinant (one reciprocal for
   // two rows), both pivot rows scaled by it, every other row updated by both at once; a last single
@@ -266,7 +267,7 @@ __device__ void admm_guess(const Params& p, const Dev& d, LcpShared& S, int m, s
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   for (int i = tid; i < m; i += nt) S.inP[i] = 1;
   rebuild_plist(S, m);
-  ensure_columns(d, S, m, ld, eps_w);           // every column of W over the working set (FP64)
+  ensure_columns(d, S, m, ld, eps_w, d.W);      // every column of W over the working set (FP64)
   double wd = 0.0;
   for (int i = tid; i < m; i += nt) wd = fmax(wd, d.W[(size_t)i * m + i]);
   wd = block_max(wd, S.red);
@@ -450,13 +451,19 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
   bool done = false, fail = false;
   int admm_it = 0;
   if (p.lcp_mode == kLcpAdmm) admm_guess(p, d, S, m, ld, eps_w, &admm_it);
+  // W in the launch's dynamic shared memory when it fits (kernels launched with it), except after
+  // the contact-space ADMM, whose inverse holds that memory and which formed W in global memory
+  extern __shared__ __align__(16) double s_wdyn[];
+  unsigned dyn_bytes;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
+  double* W = (p.lcp_mode != kLcpAdmm && (size_t)m * m * sizeof(double) <= dyn_bytes) ? s_wdyn : d.W;
   // ---- feasible start: drop warm rows until the subproblem solution is positive
   while (!fail) {
     if (solves >= p.max_lcp_iters) break;
     rebuild_plist(S, m);
-    ensure_columns(d, S, m, ld, eps_w);
+    ensure_columns(d, S, m, ld, eps_w, W);
     ++solves;
-    if (!solve_on_set(d, S, m)) { fail = true; break; }
+    if (!solve_on_set(d, S, m, W)) { fail = true; break; }
     int nneg = 0;
     for (int a = tid; a < S.np; a += nt) {
       const int i = S.plist[a];
@@ -479,7 +486,7 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
       double s = S.q[i];
       for (int a = 0; a < S.np; ++a) {
         const int j = S.plist[a];
-        s = fma(d.W[(size_t)i * m + j], S.y[j], s);
+        s = fma(W[(size_t)i * m + j], S.y[j], s);
       }
       if (s < -tol_w && (s < best || (s == best && i < bi))) { best = s; bi = i; }
     }
@@ -490,9 +497,9 @@ __device__ __forceinline__ void contact_body(const Params& p, const Dev& d) {
     for (;;) {
       if (solves >= p.max_lcp_iters) break;
       rebuild_plist(S, m);
-      ensure_columns(d, S, m, ld, eps_w);
+      ensure_columns(d, S, m, ld, eps_w, W);
       ++solves;
-      if (!solve_on_set(d, S, m)) { fail = true; break; }
+      if (!solve_on_set(d, S, m, W)) { fail = true; break; }
       // alpha = min over P with z_i <= 0 of y_i / (y_i - z_i)
       double amin = 1.0e300;
       int dummy = 0;
