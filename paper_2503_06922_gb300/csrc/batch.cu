@@ -114,7 +114,7 @@ int enqueue_batch_iteration(accfem_batch* b, cudaStream_t st, cudaGraphCondition
   launch_k(pdl, assemble_rhs_batch, dim3(g[PH_ASM]), dim3(32, 6), st, tab, plan); ++n;
   for (int j = 0; j < b->levels; ++j) { launch_k(pdl, bcr_level_batch, dim3(g[PH_LEV0 + j]), dim3(192), st, tab, plan, j); ++n; }
   for (int j = b->levels - 1; j >= 0; --j) { launch_k(pdl, bcr_bwd_batch, dim3(g[PH_BWD0 + j]), dim3(96), st, tab, plan, j); ++n; }
-  launch_ks(pdl, contact_batch, dim3(g[PH_CONTACT]), dim3(256), b->has_admm ? kAdmmSmemBytes : 0u, st, tab, plan); ++n;
+  launch_ks(pdl, contact_batch, dim3(g[PH_CONTACT]), dim3(256), b->has_admm ? kAdmmSmemBytes : kBatchWSmemBytes, st, tab, plan); ++n;
   launch_k(pdl, step_batch, dim3(g[PH_STEP]), dim3(32, 6), st, tab, plan); ++n;
   launch_k(pdl, apply_batch, dim3(g[PH_APPLY]), dim3(128), st, tab, plan); ++n;
   launch_k(pdl, batch_plan_kernel, dim3(1), dim3(1024), st, tab, plan, b->n, 1, 0, cond, set_cond); ++n;

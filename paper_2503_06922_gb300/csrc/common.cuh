@@ -32,6 +32,9 @@ constexpr int kLcpActiveSet = 0, kLcpAdmm = 1, kLcpPrimalAdmm = 2;
 // to kAdmmSmemRows rows (larger ones in global memory); its kernels are launched with this many bytes.
 constexpr int kAdmmSmemRows = 192;
 constexpr unsigned kAdmmSmemBytes = kAdmmSmemRows * kAdmmSmemRows * 4u;
+// Dynamic shared memory of the batched contact kernel without ADMM members: W of working sets up to
+// 64 rows (two blocks per SM stay resident; larger working sets keep W in global memory).
+constexpr unsigned kBatchWSmemBytes = 64u * 64u * 8u;
 constexpr int kContactNode = 0, kContactSegment = 1;
 // A triangle whose plane projection of the node lies inside it enlarged by this barycentric margin
 // ("over the face") gives a constraint row; the same value is used by the CPU oracle.
