@@ -312,7 +312,8 @@ accfem_status accfem_create(const accfem_robot_desc* robot, const accfem_lumen_d
     accfem_destroy(h);
     return ACCFEM_E_CUDA;
   }
-  // the ADMM contact solver's FP32 inverse in dynamic shared memory (beside the LCP's static arrays)
+  // dynamic shared memory of the contact kernel (beside the LCP's static arrays): W of the active-set
+  // LCP, or the contact-space ADMM's FP32 inverse
   if (!cuda_ok(h, cudaFuncSetAttribute(contact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdmmSmemBytes),
                "contact kernel shared memory")) {
     accfem_destroy(h);

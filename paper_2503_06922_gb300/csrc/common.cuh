@@ -28,8 +28,9 @@ constexpr int kAccelParts = 10;    // per step block: G (6 upper entries) and b 
 // the 1-D secant over-relaxation of a slow monotone mode.
 constexpr int kAccelIters = 100;
 constexpr int kLcpActiveSet = 0, kLcpAdmm = 1, kLcpPrimalAdmm = 2;
-// The ADMM contact solver inverts its FP32 matrix in dynamic shared memory for working sets of up
-// to kAdmmSmemRows rows (larger ones in global memory); its kernels are launched with this many bytes.
+// The single-instance contact kernel is launched with this many bytes of dynamic shared memory: the
+// ADMM contact solver inverts its FP32 matrix there for working sets of up to kAdmmSmemRows rows, the
+// active-set LCP keeps W there for up to 135 rows (larger ones in global memory).
 constexpr int kAdmmSmemRows = 192;
 constexpr unsigned kAdmmSmemBytes = kAdmmSmemRows * kAdmmSmemRows * 4u;
 // Dynamic shared memory of the batched contact kernel without ADMM members: W of working sets up to
